@@ -1,0 +1,825 @@
+/*
+ * oracle.c -- FP64 reference of the All-Mach THINC-TDU stage
+ * (Jiao, Schmidt & Adams, arXiv 2304.00140).
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  Plain loops, no blocking, no
+ * fusion: every formula is the paper's, written out in the order the paper
+ * gives it, so it can be checked against the text by eye.  Readings taken
+ * where the paper is silent or garbled are marked READING.
+ */
+#include "oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Sec. 3.1 names an explicit four-stage low-storage Runge-Kutta scheme but
+ * prints no coefficients.  READING: q^k = q^0 + a_k dt R(q^{k-1}) with
+ * a = (1/4, 1/3, 1/2, 1) (Jameson-Schmidt-Turkel). */
+static const double LSRK_A[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+
+static int nvar(const or_params* P) { return P->ndim + 2 + P->ncomp - 1; }
+static size_t ncells(const or_params* P) { return (size_t)P->n[0] * P->n[1] * P->n[2]; }
+static size_t cidx(const or_params* P, int i, int j, int k)
+{
+    return ((size_t)k * P->n[1] + j) * P->n[0] + i;
+}
+
+/* ------------------------------------------------------------------------
+ * mass fractions: the last component's is implied (Table A.1: sum = 1).
+ * READING: mass fractions entering the closure are clipped to [0, 1].
+ * --------------------------------------------------------------------- */
+static double clip01(double x) { return x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x); }
+
+static void full_Y(const or_params* P, const double* Yt, double* Y)
+{
+    int N = P->ncomp;
+    double s = 0.0;
+    for (int k = 0; k < N - 1; ++k) {
+        Y[k] = clip01(Yt[k]);
+        s += Y[k];
+    }
+    Y[N - 1] = clip01(1.0 - s);
+}
+
+/* ------------------------------------------------------------------------
+ * App. A.1: stiffened-gas / ideal-gas closure in pressure-temperature
+ * equilibrium.  Component k: p = (gamma_k - 1) rho_k (e_k - q_k)
+ * - gamma_k pinf_k (Eq. A.1.1).  READING (single temperature, App. B
+ * rho = f(p, T, xi)): e_k - q_k = cv_k T + pinf_k / rho_k, which with
+ * A.1.1 gives rho_k = (p + pinf_k) / ((gamma_k - 1) cv_k T).
+ * --------------------------------------------------------------------- */
+static double sg_rho_k(const or_comp* c, double p, double T)
+{
+    return (p + c->pinf) / ((c->gamma - 1.0) * c->cv * T);
+}
+
+static double sg_e_k(const or_comp* c, double p, double rho_k)
+{
+    /* A.1.1 solved for e */
+    return (p + c->gamma * c->pinf) / ((c->gamma - 1.0) * rho_k) + c->q;
+}
+
+static int sg_forward(const or_params* P, double p, double T, const double* Y,
+                      double* rho, double* e, double* cs, double* alpha)
+{
+    int N = P->ncomp;
+    double v = 0.0, em = 0.0, rk[OR_MAXC];
+    if (!(T > 0.0) || !isfinite(p)) return OR_ERR_NONPHYS;
+    for (int k = 0; k < N; ++k) {
+        rk[k] = 0.0;
+        if (Y[k] <= 0.0) continue;
+        if (!(p + P->comp[k].pinf > 0.0)) return OR_ERR_NONPHYS;
+        rk[k] = sg_rho_k(&P->comp[k], p, T);
+        v += Y[k] / rk[k];                                  /* Table A.1 density */
+        em += Y[k] * sg_e_k(&P->comp[k], p, rk[k]);         /* Eq. A.1.3 */
+    }
+    double r = 1.0 / v;
+    /* Eq. A.1.4 / A.1.5: alpha_k = xi_k rho / rho_k; sound speed of the
+     * mixture READING: Wood, 1/(rho c^2) = sum alpha_k / (rho_k c_k^2),
+     * rho_k c_k^2 = gamma_k (p + pinf_k) (App. A.1) */
+    double inv = 0.0;
+    for (int k = 0; k < N; ++k) {
+        double a = (Y[k] > 0.0) ? r * Y[k] / rk[k] : 0.0;
+        if (alpha) alpha[k] = a;
+        if (a > 0.0) inv += a / (P->comp[k].gamma * (p + P->comp[k].pinf));
+    }
+    if (rho) *rho = r;
+    if (e) *e = em;
+    if (cs) *cs = sqrt(1.0 / (r * inv));
+    return OR_OK;
+}
+
+/* Inverse (App. B: T = f(e, rho, xi), then p): unknowns (p, T) with
+ *   sum_k Y_k / rho_k(p, T) = 1 / rho,   sum_k Y_k e_k(p, T) = e.
+ * For a trial p the energy relation is linear in T:
+ *   T(p) = (e - sum Y_k q_k) / sum_k Y_k cv_k (p + gamma_k pinf_k)/(p + pinf_k)
+ * and the density relation leaves one residual G(p) = sum Y_k/rho_k - 1/rho.
+ * G > 0 as p -> -min pinf (over present components) and G -> -1/rho as
+ * p -> inf; the root is found by bisection to adjacent doubles. */
+static double sg_T_of_p(const or_params* P, const double* Y, double eq, double p)
+{
+    double den = 0.0;
+    for (int k = 0; k < P->ncomp; ++k) {
+        if (Y[k] <= 0.0) continue;
+        const or_comp* c = &P->comp[k];
+        den += Y[k] * c->cv * (p + c->gamma * c->pinf) / (p + c->pinf);
+    }
+    return eq / den;
+}
+
+static double sg_G(const or_params* P, const double* Y, double eq, double v, double p)
+{
+    double T = sg_T_of_p(P, Y, eq, p);
+    double s = 0.0;
+    for (int k = 0; k < P->ncomp; ++k) {
+        if (Y[k] <= 0.0) continue;
+        s += Y[k] / sg_rho_k(&P->comp[k], p, T);
+    }
+    return s - v;
+}
+
+static int sg_inverse(const or_params* P, double rho, double e, const double* Y, double* p, double* T)
+{
+    int N = P->ncomp;
+    if (!(rho > 0.0) || !isfinite(e)) return OR_ERR_NONPHYS;
+    double v = 1.0 / rho, eq = e, pimin = INFINITY;
+    for (int k = 0; k < N; ++k) {
+        eq -= Y[k] * P->comp[k].q;
+        if (Y[k] > 0.0 && P->comp[k].pinf < pimin) pimin = P->comp[k].pinf;
+    }
+    if (!(eq > 0.0) || !isfinite(pimin)) return OR_ERR_NONPHYS;
+    double lo = -pimin, w = 1.0, hi = lo + w;
+    int it = 0;
+    while (sg_G(P, Y, eq, v, hi) > 0.0) {
+        w *= 2.0;
+        hi = lo + w;
+        if (++it > 4000) return OR_ERR_NONCONV;
+    }
+    for (it = 0; it < 4000; ++it) {
+        double mid = lo + 0.5 * (hi - lo);
+        if (mid <= lo || mid >= hi) break;
+        if (sg_G(P, Y, eq, v, mid) > 0.0) lo = mid; else hi = mid;
+    }
+    double pp = 0.5 * (lo + hi);
+    if (!(pp > lo)) pp = hi;
+    *p = pp;
+    *T = sg_T_of_p(P, Y, eq, pp);
+    if (!(*T > 0.0) || !isfinite(*p)) return OR_ERR_NONPHYS;
+    return OR_OK;
+}
+
+int or_closure_forward(const or_params* P, double p, double T, const double* Yt,
+                       double* rho, double* e, double* c, double* alpha)
+{
+    double Y[OR_MAXC];
+    full_Y(P, Yt, Y);
+    for (int k = 0; k < P->ncomp; ++k)
+        if (P->comp[k].kind != OR_SG) return OR_ERR_ARG;
+    return sg_forward(P, p, T, Y, rho, e, c, alpha);
+}
+
+int or_closure_inverse(const or_params* P, double rho, double e, const double* Yt, double* p, double* T)
+{
+    double Y[OR_MAXC];
+    full_Y(P, Yt, Y);
+    for (int k = 0; k < P->ncomp; ++k)
+        if (P->comp[k].kind != OR_SG) return OR_ERR_ARG;
+    return sg_inverse(P, rho, e, Y, p, T);
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. 3.3, Table 4.2: slope limiters f(r).
+ * --------------------------------------------------------------------- */
+static double min3(double a, double b, double c) { return fmin(a, fmin(b, c)); }
+
+double or_limiter(int id, double r)
+{
+    switch (id) {
+    case OR_MINMOD: return fmax(0.0, fmin(1.0, r));                       /* Table 4.2 */
+    case OR_KOREN: return fmax(0.0, min3(2.0, 2.0 * r, (1.0 + 2.0 * r) / 3.0));
+    case OR_VANLEER: return (r + fabs(r)) / (1.0 + fabs(r));
+    case OR_VANALBADA: return (r + r * r) / (1.0 + r * r);
+    case OR_CHAKRAVARTHY: return fmax(0.0, fmin(1.0, 4.0 * r));           /* as printed */
+    case OR_MC: return fmax(0.0, min3(2.0, 2.0 * r, 0.5 * (1.0 + r)));
+    case OR_SUPERBEE: return fmax(0.0, fmax(fmin(1.0, 2.0 * r), fmin(r, 2.0)));
+    default: return 0.0;
+    }
+}
+
+/* Sec. 3.3, face between cells 2 and 3 of the stencil 1..4:
+ *   L = x2 + 1/2 f(r) (x2 - x1),  R = x3 - 1/2 f(r) (x4 - x3).
+ * READING: r = (x3 - x2)/(x2 - x1) for L and r = (x3 - x2)/(x4 - x3) for R
+ * (the ratio that makes Koren third order, as Sec. 3.3 claims); a zero
+ * denominator gives a zero slope term. */
+void or_muscl(int id, double x1, double x2, double x3, double x4, double* L, double* R)
+{
+    double dl = x2 - x1, dc = x3 - x2, dr = x4 - x3;
+    *L = x2;
+    if (dl != 0.0) *L = x2 + 0.5 * or_limiter(id, dc / dl) * dl;
+    *R = x3;
+    if (dr != 0.0) *R = x3 - 0.5 * or_limiter(id, dc / dr) * dr;
+}
+
+/* Eq. 3-3 (L, from cells 1, 2, 3) and Eq. 3-4 (R, from cells 2, 3, 4).
+ * READING: the printed denominator of F, "max + gamma", is taken as
+ * max - min + gamma (the normalisation of the cell average by the jump). */
+static double thinc_E(double theta, double beta, double F)
+{
+    return (exp(theta * beta * (2.0 * F - 1.0)) / cosh(beta) - 1.0) / tanh(beta);
+}
+
+void or_thinc(double beta, double gam, double x1, double x2, double x3, double x4, double* L, double* R)
+{
+    double mn = fmin(x1, x3), mx = fmax(x1, x3);
+    double th = (x3 >= x1) ? 1.0 : -1.0;
+    double F = (x2 - mn + gam) / (mx - mn + gam);
+    double E = thinc_E(th, beta, F);
+    *L = mn + 0.5 * (mx - mn) * (1.0 + th * (tanh(beta) + E) / (1.0 + E * tanh(beta)));
+
+    mn = fmin(x2, x4);
+    mx = fmax(x2, x4);
+    th = (x4 >= x2) ? 1.0 : -1.0;
+    F = (x3 - mn + gam) / (mx - mn + gam);
+    E = thinc_E(th, beta, F);
+    *R = mn + 0.5 * (mx - mn) * (1.0 + th * E);
+}
+
+/* Sec. 3.4 / App. D: THINC applies where eps < xi_i < 1 - eps and
+ * (xi_i - xi_{i-1})(xi_{i+1} - xi_i) > 0 (eps READING: a parameter). */
+static int thinc_eligible(double eps, double xm, double x, double xp)
+{
+    return (x > eps) && (x < 1.0 - eps) && ((x - xm) * (xp - x) > 0.0);
+}
+
+/* ------------------------------------------------------------------------
+ * One face: reconstruction (Sec. 3.3 / App. D), TDU (Eq. 3-5, App. B),
+ * all-Mach Riemann solver (Eq. 3-1, 3-2; App. D Eq. D.5, D.6) and the
+ * flux C + S of Eq. 2-2 (inviscid part).
+ * W4[c*OR_MAXV + v], c = 0..3 the cells i-1, i, i+1, i+2 along d.
+ * --------------------------------------------------------------------- */
+int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
+                 int f, double* F)
+{
+    const int nd = P->ndim, N = P->ncomp, nv = nvar(P);
+    const int ip = nd, iT = nd + 1, iY = nd + 2;
+    const double* w1 = W4;
+    const double* w2 = W4 + OR_MAXV;
+    const double* w3 = W4 + 2 * OR_MAXV;
+    const double* w4 = W4 + 3 * OR_MAXV;
+    double WL[OR_MAXV], WR[OR_MAXV];
+    const int smooth = P->iles && !f;
+
+    for (int v = 0; v < nv; ++v) {
+        if (smooth) {
+            /* Eq. D.1 for u, p, T; READING: 2nd-order central for the mass
+             * fractions, as the text after Eq. D.4 says */
+            double c = (v < iY) ? (7.0 * (w2[v] + w3[v]) - w1[v] - w4[v]) / 12.0
+                                : 0.5 * (w2[v] + w3[v]);
+            WL[v] = WR[v] = c;
+            continue;
+        }
+        int lim = (v < nd) ? P->lim_vel : P->lim_scalar;
+        or_muscl(lim, w1[v], w2[v], w3[v], w4[v], &WL[v], &WR[v]);
+        if (v >= iY && P->thinc) {
+            double tl, tr;
+            or_thinc(P->beta, P->thinc_gamma, w1[v], w2[v], w3[v], w4[v], &tl, &tr);
+            if (thinc_eligible(P->thinc_eps, w1[v], w2[v], w3[v])) WL[v] = tl;
+            if (thinc_eligible(P->thinc_eps, w2[v], w3[v], w4[v])) WR[v] = tr;
+        }
+    }
+
+    /* TDU: rho*, e*, c* = f(p*, T*, xi*) on each side */
+    double rL, eL, cL, rR, eR, cR;
+    int st = or_closure_forward(P, WL[ip], WL[iT], WL + iY, &rL, &eL, &cL, NULL);
+    if (st) return st;
+    st = or_closure_forward(P, WR[ip], WR[iT], WR + iY, &rR, &eR, &cR, NULL);
+    if (st) return st;
+
+    double pL = WL[ip], pR = WR[ip], uL = WL[d], uR = WR[d];
+    double us, ps;
+    if (P->iles) {
+        /* Eq. D.5 / D.6 with the impedances I_L, I_R of cells i, i+1 */
+        double cm = fmax(c4[1], c4[2]);
+        double IL = (3.0 * rho4[1] + rho4[2]) * cm / 4.0;
+        double IR = (rho4[1] + 3.0 * rho4[2]) * cm / 4.0;
+        if (f) {
+            us = (IL * uL + IR * uR + pL - pR) / (IL + IR);
+            ps = 0.5 * (pL + pR);
+        } else {
+            /* READING: Delta^3 p = p_{i-1} - 3 p_i + 3 p_{i+1} - p_{i+2}
+             * (sign that damps odd-even pressure modes, like the p_L - p_R
+             * term of the upwind branch), scaled by d3p_coef */
+            double d3 = P->d3p_coef * (w1[ip] - 3.0 * w2[ip] + 3.0 * w3[ip] - w4[ip]);
+            us = uL - d3 / (IL + IR);
+            ps = pL;
+        }
+    } else {
+        ps = 0.5 * (pL + pR);                                            /* Eq. 3-1 */
+        us = (rL * cL * uL + rR * cR * uR + pL - pR) / (rL * cL + rR * cR); /* Eq. 3-2 */
+    }
+
+    /* u* selects the upstream side; the convected state is that side's
+     * reconstructed (rho, rho u, rho E, rho xi) (Eq. 2-2, rho H = rho E + p) */
+    const double* Ws = (us >= 0.0) ? WL : WR;
+    double rs = (us >= 0.0) ? rL : rR;
+    double es = (us >= 0.0) ? eL : eR;
+    double ke = 0.0;
+    for (int a = 0; a < nd; ++a) ke += 0.5 * Ws[a] * Ws[a];
+    F[0] = us * rs;
+    for (int a = 0; a < nd; ++a) F[1 + a] = us * rs * Ws[a] + (a == d ? ps : 0.0);
+    F[1 + nd] = us * rs * (es + ke) + ps * us;
+    for (int k = 0; k < N - 1; ++k) F[2 + nd + k] = us * rs * Ws[iY + k];
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * cells: conserved -> primitive (Algorithm 1: "update primitive variables
+ * and thermodynamic parameters according to EOS")
+ * --------------------------------------------------------------------- */
+static int cell_prim(const or_params* P, const double* qc, double* w, double* rho_out, double* c_out,
+                     double* aliq)
+{
+    const int nd = P->ndim, N = P->ncomp;
+    double rho = qc[0];
+    if (!(rho > 0.0) || !isfinite(rho)) return OR_ERR_NONPHYS;
+    double ke = 0.0;
+    for (int a = 0; a < nd; ++a) {
+        w[a] = qc[1 + a] / rho;
+        ke += 0.5 * w[a] * w[a];
+    }
+    double e = qc[1 + nd] / rho - ke;                /* Table A.1: E = e + |u|^2/2 */
+    double Yt[OR_MAXC] = {0}, Y[OR_MAXC];
+    for (int k = 0; k < N - 1; ++k) Yt[k] = qc[2 + nd + k] / rho;
+    full_Y(P, Yt, Y);
+    for (int k = 0; k < N - 1; ++k) w[nd + 2 + k] = Y[k];
+    double p, T;
+    int st = or_closure_inverse(P, rho, e, Y, &p, &T);
+    if (st) return st;
+    w[nd] = p;
+    w[nd + 1] = T;
+    double r2, e2, c, al[OR_MAXC];
+    st = or_closure_forward(P, p, T, Y, &r2, &e2, &c, al);
+    if (st) return st;
+    if (rho_out) *rho_out = rho;
+    if (c_out) *c_out = c;
+    if (aliq) *aliq = al[P->liquid];
+    return OR_OK;
+}
+
+static void gather_q(const or_params* P, const double* q, size_t c, double* qc)
+{
+    size_t nc = ncells(P);
+    for (int v = 0; v < nvar(P); ++v) qc[v] = q[(size_t)v * nc + c];
+}
+
+/* ------------------------------------------------------------------------
+ * Boundary conditions on primitives (Algorithm 1, last line): ghost cells
+ * copy a mapped interior cell.  Periodic wraps; REFLECT mirrors
+ * (ghost -1-m <-> interior m) and flips the normal velocity; OUTFLOW is
+ * zero gradient; INFLOW (x-low only) is Dirichlet u, T, Y with
+ * zero-gradient p inside the disc and a slip wall outside it.
+ * --------------------------------------------------------------------- */
+static int map_dim(int n, int i, int bclo, int bchi, int* flip, int* inflow)
+{
+    *flip = 0;
+    *inflow = 0;
+    if (i >= 0 && i < n) return i;
+    if (i < 0) {
+        int s = -1 - i;
+        if (s > n - 1) s = n - 1;
+        switch (bclo) {
+        case OR_BC_PERIODIC: return ((i % n) + n) % n;
+        case OR_BC_REFLECT: *flip = 1; return s;
+        case OR_BC_INFLOW: *inflow = 1; return s;
+        default: return 0;
+        }
+    }
+    int s = 2 * n - 1 - i;
+    if (s < 0) s = 0;
+    switch (bchi) {
+    case OR_BC_PERIODIC: return i % n;
+    case OR_BC_REFLECT: *flip = 1; return s;
+    default: return n - 1;
+    }
+}
+
+typedef struct {
+    int lo[3], ext[3];
+    size_t cnt;
+    double* W;     /* [OR_MAXV][cnt] */
+    double* rho;
+    double* c;
+    double* al;
+    double* flag;  /* App. D cell sensor */
+} box_t;
+
+static size_t bidx(const box_t* B, int i, int j, int k)
+{
+    return ((size_t)(k - B->lo[2]) * B->ext[1] + (j - B->lo[1])) * B->ext[0] + (i - B->lo[0]);
+}
+
+static void box_free(box_t* B)
+{
+    free(B->W); free(B->rho); free(B->c); free(B->al); free(B->flag);
+}
+
+static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo, const int* hi)
+{
+    const int nd = P->ndim, nv = nvar(P);
+    B->cnt = 1;
+    for (int d = 0; d < 3; ++d) {
+        B->lo[d] = lo[d];
+        B->ext[d] = hi[d] - lo[d];
+        B->cnt *= (size_t)B->ext[d];
+    }
+    B->W = calloc(OR_MAXV * B->cnt, sizeof(double));
+    B->rho = calloc(B->cnt, sizeof(double));
+    B->c = calloc(B->cnt, sizeof(double));
+    B->al = calloc(B->cnt, sizeof(double));
+    B->flag = calloc(B->cnt, sizeof(double));
+    if (!B->W || !B->rho || !B->c || !B->al || !B->flag) return OR_ERR_ARG;
+    for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+            for (int i = lo[0]; i < hi[0]; ++i) {
+                int ijk[3] = {i, j, k}, src[3], flip[3], inflow[3];
+                for (int d = 0; d < 3; ++d) {
+                    if (d < nd) src[d] = map_dim(P->n[d], ijk[d], P->bc[d][0], P->bc[d][1], &flip[d], &inflow[d]);
+                    else { src[d] = 0; flip[d] = 0; inflow[d] = 0; }
+                }
+                int in_disc = 0;
+                if (inflow[0]) {
+                    double y = (src[1] + 0.5) * P->dx[1], z = (nd == 3) ? (src[2] + 0.5) * P->dx[2] : 0.0;
+                    double dy = y - P->in_yc, dz = (nd == 3) ? z - P->in_zc : 0.0;
+                    if (dy * dy + dz * dz <= P->in_radius * P->in_radius) {
+                        in_disc = 1;
+                        src[0] = 0;
+                        flip[0] = 0;
+                    } else {
+                        flip[0] = 1;   /* slip wall */
+                    }
+                }
+                double qc[OR_MAXV], w[OR_MAXV], r, c, al;
+                gather_q(P, q, cidx(P, src[0], src[1], src[2]), qc);
+                int st = cell_prim(P, qc, w, &r, &c, &al);
+                if (st) return st;
+                for (int d = 0; d < nd; ++d)
+                    if (flip[d]) w[d] = -w[d];
+                if (in_disc) {
+                    size_t fc = (size_t)src[2] * P->n[1] + src[1];
+                    size_t fn = (size_t)P->n[1] * P->n[2];
+                    for (int a = 0; a < nd; ++a) w[a] = P->in_u ? P->in_u[a * fn + fc] : 0.0;
+                    w[nd + 1] = P->in_T;
+                    for (int kk = 0; kk < P->ncomp - 1; ++kk) w[nd + 2 + kk] = P->in_Y[kk];
+                    double Y[OR_MAXC], e2;
+                    full_Y(P, w + nd + 2, Y);
+                    double alk[OR_MAXC];
+                    st = sg_forward(P, w[nd], w[nd + 1], Y, &r, &e2, &c, alk);
+                    if (st) return st;
+                    al = alk[P->liquid];
+                }
+                size_t b = bidx(B, i, j, k);
+                for (int v = 0; v < nv; ++v) B->W[(size_t)v * B->cnt + b] = w[v];
+                B->rho[b] = r;
+                B->c[b] = c;
+                B->al[b] = al;
+            }
+    return OR_OK;
+}
+
+/* App. D: vorticity-dilatation sensor (Ducros) and total-gas volume
+ * fraction variation; f = 1 where either exceeds its threshold (Eq. D.4).
+ * Derivatives by central differences. */
+static void box_sensor(const or_params* P, box_t* B, const int* lo, const int* hi)
+{
+    const int nd = P->ndim;
+    for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+            for (int i = lo[0]; i < hi[0]; ++i) {
+                int ijk[3] = {i, j, k};
+                double g[3][3] = {{0}};  /* g[a][b] = d u_a / d x_b */
+                double tg = 0.0;
+                size_t b0 = bidx(B, i, j, k);
+                double ag0 = 1.0 - B->al[b0];
+                for (int bd = 0; bd < nd; ++bd) {
+                    int pp[3] = {ijk[0], ijk[1], ijk[2]}, mm[3] = {ijk[0], ijk[1], ijk[2]};
+                    pp[bd] += 1;
+                    mm[bd] -= 1;
+                    size_t bp = bidx(B, pp[0], pp[1], pp[2]), bm = bidx(B, mm[0], mm[1], mm[2]);
+                    for (int a = 0; a < nd; ++a)
+                        g[a][bd] = (B->W[(size_t)a * B->cnt + bp] - B->W[(size_t)a * B->cnt + bm]) / (2.0 * P->dx[bd]);
+                    tg += fabs(ag0 - (1.0 - B->al[bm])) + fabs((1.0 - B->al[bp]) - ag0);
+                }
+                double div = 0.0;
+                for (int a = 0; a < nd; ++a) div += g[a][a];
+                double curl2;
+                if (nd == 3) {
+                    double wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
+                    curl2 = wx * wx + wy * wy + wz * wz;
+                } else if (nd == 2) {
+                    double wz = g[1][0] - g[0][1];
+                    curl2 = wz * wz;
+                } else {
+                    curl2 = 0.0;
+                }
+                double thD = div * div / (div * div + curl2 + P->eps_ducros);
+                B->flag[b0] = (thD > P->thr_ducros || tg > P->thr_gas) ? 1.0 : 0.0;
+            }
+}
+
+/* Sec. 3.5: CSF source sigma*kappa*grad(alpha) (momentum) and
+ * sigma*kappa*u.grad(alpha) (energy), Eq. 2-2 Q.
+ * alpha~ = Gaussian kernel (Eq. 3-9, 1/16 in 2D, 1/64 in 3D) applied to the
+ * liquid volume fraction; vertex gradients of alpha~ (Fig. 3.3) give unit
+ * normals n; kappa from the vertex normals.  READING: kappa = -div n so a
+ * liquid drop has kappa = +1/R; grad(alpha) = mean of the vertex gradients
+ * of the unsmoothed alpha (the Heaviside gradient decoupled from the
+ * curvature, abstract and Sec. 3.5). */
+static double smooth_at(const or_params* P, const box_t* B, int i, int j, int k)
+{
+    const int nd = P->ndim;
+    static const double w3[3] = {1.0, 2.0, 1.0};
+    double s = 0.0, norm = 0.0;
+    int rz = nd == 3 ? 1 : 0, ry = nd >= 2 ? 1 : 0;
+    for (int c = -rz; c <= rz; ++c)
+        for (int b = -ry; b <= ry; ++b)
+            for (int a = -1; a <= 1; ++a) {
+                double wt = w3[a + 1] * (ry ? w3[b + 1] : 1.0) * (rz ? w3[c + 1] : 1.0);
+                s += wt * B->al[bidx(B, i + a, j + b, k + c)];
+                norm += wt;
+            }
+    return s / norm;   /* norm = 16 in 2D, 64 in 3D */
+}
+
+static void csf_cell(const or_params* P, const box_t* B, int i, int j, int k, double* S)
+{
+    const int nd = P->ndim;
+    const int nvtx = 1 << nd;
+    const double scale = (double)(1 << (nd - 1));
+    double kappa = 0.0, galpha[3] = {0.0, 0.0, 0.0};
+    double dxmin = P->dx[0];
+    for (int d = 1; d < nd; ++d) dxmin = fmin(dxmin, P->dx[d]);
+    int ijk[3] = {i, j, k};
+    for (int vtx = 0; vtx < nvtx; ++vtx) {
+        int voff[3] = {vtx & 1, (vtx >> 1) & 1, (vtx >> 2) & 1};
+        /* vertex between cells ijk + voff - 1 and ijk + voff along each dim */
+        double gs[3] = {0, 0, 0}, gu[3] = {0, 0, 0};
+        for (int cc = 0; cc < nvtx; ++cc) {
+            int b[3] = {cc & 1, (cc >> 1) & 1, (cc >> 2) & 1};
+            int c3[3] = {0, 0, 0};
+            for (int d = 0; d < 3; ++d) c3[d] = (d < nd) ? ijk[d] + voff[d] - 1 + b[d] : ijk[d];
+            double as = smooth_at(P, B, c3[0], c3[1], c3[2]);
+            double au = B->al[bidx(B, c3[0], c3[1], c3[2])];
+            for (int d = 0; d < nd; ++d) {
+                double sg = b[d] ? 1.0 : -1.0;
+                gs[d] += sg * as / (scale * P->dx[d]);
+                gu[d] += sg * au / (scale * P->dx[d]);
+            }
+        }
+        double mag = 0.0;
+        for (int d = 0; d < nd; ++d) mag += gs[d] * gs[d];
+        mag = sqrt(mag);
+        double nrm[3] = {0, 0, 0};
+        if (mag > P->grad_eps / dxmin)
+            for (int d = 0; d < nd; ++d) nrm[d] = gs[d] / mag;
+        for (int d = 0; d < nd; ++d) {
+            double sg = voff[d] ? 1.0 : -1.0;
+            kappa -= sg * nrm[d] / (scale * P->dx[d]);
+            galpha[d] += gu[d] / nvtx;
+        }
+    }
+    size_t b0 = bidx(B, i, j, k);
+    double udg = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        S[d] = P->sigma * kappa * galpha[d];
+        udg += B->W[(size_t)d * B->cnt + b0] * galpha[d];
+    }
+    S[nd] = P->sigma * kappa * udg;
+}
+
+/* ------------------------------------------------------------------------
+ * One Runge-Kutta stage over the window [wlo, whi) (whole interior when
+ * NULL): Algorithm 1 in order.
+ * --------------------------------------------------------------------- */
+int or_stage(const or_params* P, int kst, double dt, const double* q0, const double* qprev,
+             double* qout, const int* wlo, const int* whi)
+{
+    const int nd = P->ndim, nv = nvar(P);
+    if (kst < 1 || kst > 4 || nd < 1 || nd > 3 || nv > OR_MAXV || P->ncomp < 2 || P->ncomp > OR_MAXC)
+        return OR_ERR_ARG;
+    int lo[3], hi[3], blo[3], bhi[3], slo[3], shi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = wlo ? wlo[d] : 0;
+        hi[d] = whi ? whi[d] : P->n[d];
+        if (d >= nd) { lo[d] = 0; hi[d] = 1; }
+        if (lo[d] < 0 || hi[d] > P->n[d] || lo[d] >= hi[d]) return OR_ERR_ARG;
+        blo[d] = (d < nd) ? lo[d] - 2 : 0;
+        bhi[d] = (d < nd) ? hi[d] + 2 : 1;
+        slo[d] = (d < nd) ? lo[d] - 1 : 0;
+        shi[d] = (d < nd) ? hi[d] + 1 : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    int st = box_fill(P, qprev, &B, blo, bhi);
+    if (st) { box_free(&B); return st; }
+    if (P->iles) box_sensor(P, &B, slo, shi);
+
+    int wext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+    size_t wcnt = (size_t)wext[0] * wext[1] * wext[2];
+    /* face fluxes per direction: faces c[d] = lo[d]-1 .. hi[d]-1 (face c+1/2) */
+    double* Fd[3] = {NULL, NULL, NULL};
+    int fext[3][3];
+    for (int d = 0; d < nd; ++d) {
+        for (int e = 0; e < 3; ++e) fext[d][e] = wext[e] + (e == d ? 1 : 0);
+        size_t fc = (size_t)fext[d][0] * fext[d][1] * fext[d][2];
+        Fd[d] = calloc((size_t)nv * fc, sizeof(double));
+        for (int k = 0; k < fext[d][2]; ++k)
+            for (int j = 0; j < fext[d][1]; ++j)
+                for (int i = 0; i < fext[d][0]; ++i) {
+                    int c[3] = {lo[0] + i, lo[1] + j, lo[2] + k};
+                    c[d] -= 1;   /* left cell of the face */
+                    double W4[4 * OR_MAXV], r4[4], c4[4];
+                    for (int s = 0; s < 4; ++s) {
+                        int cc[3] = {c[0], c[1], c[2]};
+                        cc[d] += s - 1;
+                        size_t b = bidx(&B, cc[0], cc[1], cc[2]);
+                        for (int v = 0; v < nv; ++v) W4[s * OR_MAXV + v] = B.W[(size_t)v * B.cnt + b];
+                        r4[s] = B.rho[b];
+                        c4[s] = B.c[b];
+                    }
+                    int f = 1;
+                    if (P->iles) {
+                        int cp[3] = {c[0], c[1], c[2]};
+                        cp[d] += 1;
+                        f = (B.flag[bidx(&B, c[0], c[1], c[2])] > 0.5 ||
+                             B.flag[bidx(&B, cp[0], cp[1], cp[2])] > 0.5) ? 1 : 0;
+                    }
+                    double F[OR_MAXV];
+                    st = or_face_flux(P, d, W4, r4, c4, f, F);
+                    if (st) goto done;
+                    size_t fi = ((size_t)k * fext[d][1] + j) * fext[d][0] + i;
+                    for (int v = 0; v < nv; ++v) Fd[d][(size_t)v * fc + fi] = F[v];
+                }
+    }
+
+    {
+        const double a = LSRK_A[kst - 1];
+        const size_t nc = ncells(P);
+        for (int k = lo[2]; k < hi[2]; ++k)
+            for (int j = lo[1]; j < hi[1]; ++j)
+                for (int i = lo[0]; i < hi[0]; ++i) {
+                    double S[OR_MAXV] = {0};
+                    if (P->sigma != 0.0) {
+                        double s4[4];
+                        csf_cell(P, &B, i, j, k, s4);
+                        for (int d = 0; d < nd; ++d) S[1 + d] = s4[d];
+                        S[1 + nd] = s4[nd];
+                    }
+                    int wi = i - lo[0], wj = j - lo[1], wk = k - lo[2];
+                    size_t c = cidx(P, i, j, k);
+                    for (int v = 0; v < nv; ++v) {
+                        double div = 0.0;
+                        for (int d = 0; d < nd; ++d) {
+                            size_t fc = (size_t)fext[d][0] * fext[d][1] * fext[d][2];
+                            int hiw[3] = {wi, wj, wk};
+                            hiw[d] += 1;
+                            size_t flo = ((size_t)wk * fext[d][1] + wj) * fext[d][0] + wi;
+                            size_t fhi = ((size_t)hiw[2] * fext[d][1] + hiw[1]) * fext[d][0] + hiw[0];
+                            div += (Fd[d][(size_t)v * fc + fhi] - Fd[d][(size_t)v * fc + flo]) / P->dx[d];
+                        }
+                        double R = S[v] - div;
+                        qout[(size_t)v * nc + c] = q0[(size_t)v * nc + c] + a * dt * R;
+                    }
+                }
+        (void)wcnt;
+    }
+done:
+    for (int d = 0; d < 3; ++d) free(Fd[d]);
+    box_free(&B);
+    return st;
+}
+
+/* ------------------------------------------------------------------------
+ * whole fields
+ * --------------------------------------------------------------------- */
+int or_prim_to_cons(const or_params* P, const double* W, double* q)
+{
+    const int nd = P->ndim, nv = nvar(P), N = P->ncomp;
+    const size_t nc = ncells(P);
+    for (size_t c = 0; c < nc; ++c) {
+        double w[OR_MAXV], r, e, cs;
+        for (int v = 0; v < nv; ++v) w[v] = W[(size_t)v * nc + c];
+        int st = or_closure_forward(P, w[nd], w[nd + 1], w + nd + 2, &r, &e, &cs, NULL);
+        if (st) return st;
+        double ke = 0.0;
+        for (int a = 0; a < nd; ++a) ke += 0.5 * w[a] * w[a];
+        q[c] = r;
+        for (int a = 0; a < nd; ++a) q[(size_t)(1 + a) * nc + c] = r * w[a];
+        q[(size_t)(1 + nd) * nc + c] = r * (e + ke);
+        for (int k = 0; k < N - 1; ++k) q[(size_t)(2 + nd + k) * nc + c] = r * w[nd + 2 + k];
+    }
+    return OR_OK;
+}
+
+int or_cons_to_prim(const or_params* P, const double* q, double* W)
+{
+    const int nv = nvar(P);
+    const size_t nc = ncells(P);
+    for (size_t c = 0; c < nc; ++c) {
+        double qc[OR_MAXV], w[OR_MAXV];
+        gather_q(P, q, c, qc);
+        int st = cell_prim(P, qc, w, NULL, NULL, NULL);
+        if (st) return st;
+        for (int v = 0; v < nv; ++v) W[(size_t)v * nc + c] = w[v];
+    }
+    return OR_OK;
+}
+
+/* READING (no CFL definition in the paper): dt = CFL / max_i sum_d
+ * (|u_d| + c) / dx_d over interior cells, from the state at the start of
+ * the step. */
+int or_dt(const or_params* P, const double* q, double cfl, double* dt)
+{
+    const int nd = P->ndim;
+    const size_t nc = ncells(P);
+    double smax = 0.0;
+    for (size_t c = 0; c < nc; ++c) {
+        double qc[OR_MAXV], w[OR_MAXV], r, cs;
+        gather_q(P, q, c, qc);
+        int st = cell_prim(P, qc, w, &r, &cs, NULL);
+        if (st) return st;
+        double s = 0.0;
+        for (int d = 0; d < nd; ++d) s += (fabs(w[d]) + cs) / P->dx[d];
+        if (s > smax) smax = s;
+    }
+    *dt = cfl / smax;
+    return OR_OK;
+}
+
+int or_step(const or_params* P, double* q, int nsteps, double cfl, double* t)
+{
+    const size_t n = (size_t)nvar(P) * ncells(P);
+    double* q0 = malloc(n * sizeof(double));
+    double* qa = malloc(n * sizeof(double));
+    double* qb = malloc(n * sizeof(double));
+    int st = OR_OK;
+    if (!q0 || !qa || !qb) { st = OR_ERR_ARG; goto out; }
+    for (int s = 0; s < nsteps; ++s) {
+        double dt;
+        st = or_dt(P, q, cfl, &dt);
+        if (st) goto out;
+        memcpy(q0, q, n * sizeof(double));
+        if ((st = or_stage(P, 1, dt, q0, q0, qa, NULL, NULL))) goto out;
+        if ((st = or_stage(P, 2, dt, q0, qa, qb, NULL, NULL))) goto out;
+        if ((st = or_stage(P, 3, dt, q0, qb, qa, NULL, NULL))) goto out;
+        if ((st = or_stage(P, 4, dt, q0, qa, q, NULL, NULL))) goto out;
+        if (t) *t += dt;
+    }
+out:
+    free(q0); free(qa); free(qb);
+    return st;
+}
+
+/* Neumaier-compensated sum of each conserved field over the interior */
+void or_totals(const or_params* P, const double* q, double* out)
+{
+    const size_t nc = ncells(P);
+    for (int v = 0; v < nvar(P); ++v) {
+        double s = 0.0, comp = 0.0;
+        for (size_t c = 0; c < nc; ++c) {
+            double x = q[(size_t)v * nc + c], t = s + x;
+            if (fabs(s) >= fabs(x)) comp += (s - t) + x; else comp += (x - t) + s;
+            s = t;
+        }
+        out[v] = s + comp;
+    }
+}
+
+int or_csf_source(const or_params* P, const double* q, double* S)
+{
+    const int nd = P->ndim;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    int st = box_fill(P, q, &B, blo, bhi);
+    if (!st) {
+        const size_t nc = ncells(P);
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) {
+                    double s4[4];
+                    csf_cell(P, &B, i, j, k, s4);
+                    for (int d = 0; d <= nd; ++d) S[(size_t)d * nc + cidx(P, i, j, k)] = s4[d];
+                }
+    }
+    box_free(&B);
+    return st;
+}
+
+int or_sensor(const or_params* P, const double* q, double* f)
+{
+    const int nd = P->ndim;
+    int blo[3], bhi[3], lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+        lo[d] = 0;
+        hi[d] = d < nd ? P->n[d] : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    int st = box_fill(P, q, &B, blo, bhi);
+    if (!st) {
+        box_sensor(P, &B, lo, hi);
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) f[cidx(P, i, j, k)] = B.flag[bidx(&B, i, j, k)];
+    }
+    box_free(&B);
+    return st;
+}

@@ -1,0 +1,100 @@
+/*
+ * oracle.h -- plain, slow FP64 reference of one explicit four-stage
+ * low-storage Runge-Kutta step of the All-Mach THINC-TDU scheme
+ * (Jiao, Schmidt & Adams, arXiv 2304.00140).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA path.
+ *
+ * Every step follows the paper in its own order (Algorithm 1, Sec. 3.1):
+ * boundary update, primitive/thermodynamic update (App. A, App. B),
+ * sensor (App. D, Eq. D.4), reconstruction (Sec. 3.3, Eq. 3-3/3-4,
+ * Table 4.2; App. D Eq. D.1-D.3), thermodynamic-dependent update
+ * (Eq. 3-5/3-6), all-Mach Riemann flux (Eq. 3-1/3-2; D.5/D.6), CSF source
+ * (Sec. 2.3, Sec. 3.5, Eq. 3-9/3-10), flux divergence and the low-storage
+ * Runge-Kutta update (Sec. 3.1).
+ *
+ * Layouts: conserved state q and primitive state W are SoA float64 arrays
+ * [nv][nz][ny][nx], x fastest, interior cells only.
+ *   q = (rho, rho u_0..rho u_{d-1}, rho E, rho Y_0..rho Y_{N-2})   (Eq. 2-1)
+ *   W = (u_0..u_{d-1}, p, T, Y_0..Y_{N-2})
+ * The mass fraction of the last component is 1 - sum of the others.
+ */
+#ifndef THINC_ORACLE_H
+#define THINC_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAXC 4
+#define OR_MAXV 10
+
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_NONPHYS = 2, OR_ERR_NONCONV = 3 };
+enum { OR_BC_PERIODIC = 0, OR_BC_REFLECT = 1, OR_BC_OUTFLOW = 2, OR_BC_INFLOW = 3 };
+enum { OR_SG = 0, OR_PR = 1 };
+enum { OR_MINMOD = 0, OR_KOREN = 1, OR_VANLEER = 2, OR_VANALBADA = 3,
+       OR_CHAKRAVARTHY = 4, OR_MC = 5, OR_SUPERBEE = 6 };
+
+typedef struct {
+    int kind;                         /* OR_SG (ideal gas when pinf = 0) or OR_PR */
+    double gamma, pinf, cv, q;        /* Eq. A.1.1 */
+    double Tc, pc, omega, M;          /* Eq. A.2.1 (M in kg/mol) */
+} or_comp;
+
+typedef struct {
+    int ndim;                         /* 1, 2 or 3 */
+    int n[3];                         /* interior cells; unused dims = 1 */
+    double dx[3];
+    int bc[3][2];                     /* OR_BC_* per dim, low/high side */
+    int ncomp;                        /* N >= 2 */
+    int liquid;                       /* component whose volume fraction feeds CSF */
+    or_comp comp[OR_MAXC];
+    int iles;                         /* 0: plain (f = 1 everywhere), 1: App. D switch */
+    int thinc;                        /* THINC for mass fractions on eligible cells */
+    double beta, thinc_eps, thinc_gamma;
+    int lim_vel, lim_scalar;          /* limiter ids for velocity and p, T, Y */
+    double thr_ducros, thr_gas, eps_ducros, d3p_coef;
+    double sigma;                     /* surface tension coefficient; 0 = off */
+    double grad_eps;                  /* |grad alpha~| * dx below this: n = 0 */
+    /* inflow disc on the x-low face (OR_BC_INFLOW) */
+    double in_yc, in_zc, in_radius, in_T;
+    double in_Y[OR_MAXC];             /* tracked mass fractions of the inflow */
+    const double* in_u;               /* [3][nz][ny] inflow velocity, or NULL */
+} or_params;
+
+/* closure, pointwise (Yt = the N-1 tracked mass fractions) */
+int or_closure_forward(const or_params* P, double p, double T, const double* Yt,
+                       double* rho, double* e, double* c, double* alpha /* N */);
+int or_closure_inverse(const or_params* P, double rho, double e, const double* Yt,
+                       double* p, double* T);
+
+/* reconstruction pieces */
+double or_limiter(int id, double r);
+void or_muscl(int id, double x1, double x2, double x3, double x4, double* L, double* R);
+void or_thinc(double beta, double gam, double x1, double x2, double x3, double x4,
+              double* L, double* R);
+
+/* one face: four cells' primitives along direction d (W[c*OR_MAXV + v]) and,
+ * for the App. D switch, the face sensor value f and cell rho, c */
+int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4,
+                 const double* c4, int f, double* F);
+
+/* whole-field operations */
+int or_prim_to_cons(const or_params* P, const double* W, double* q);
+int or_cons_to_prim(const or_params* P, const double* q, double* W);
+int or_stage(const or_params* P, int k, double dt, const double* q0, const double* qprev,
+             double* qout, const int* wlo, const int* whi);
+int or_dt(const or_params* P, const double* q, double cfl, double* dt);
+int or_step(const or_params* P, double* q, int nsteps, double cfl, double* t);
+void or_totals(const or_params* P, const double* q, double* out /* nv */);
+/* CSF source on the interior (S[d+1][cells]: momentum then energy) */
+int or_csf_source(const or_params* P, const double* q, double* S);
+/* App. D cell sensor f (0/1) on the interior */
+int or_sensor(const or_params* P, const double* q, double* f);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,344 @@
+"""Seeded synthetic workloads: grids, materials, scheme switches and initial
+primitive fields.
+
+This module is shared by the CUDA path, the tests and the benchmark.  It holds
+none of the scheme's arithmetic: it only places materials on a grid (tanh
+smoothed interfaces, a planar shock, droplets and a jet inflow disc) and draws
+the random numbers the workloads need from a splitmix64 stream.  Each consumer
+turns the primitive fields (u, p, T, Y) into conserved variables with its own
+closure.
+
+The one piece of physics it evaluates is the Rankine-Hugoniot jump of a pure
+stiffened gas (Sec. 4.2, Table 4.3 gives the ideal-gas case), written with the
+single-material relation rho = (p + pinf) / ((gamma - 1) cv T) of Eq. A.1.1.
+That is initial-condition data, not the mixture closure the scheme uses.
+
+Layouts
+-------
+* Primitive fields: float64 array ``[nv, nz, ny, nx]`` with variables
+  ``u_0 .. u_{d-1}, p, T, Y_0 .. Y_{N-2}`` (Y of the last component is
+  implied by sum Y = 1).
+* Conserved fields (produced elsewhere): ``rho, rho u_0 .. rho u_{d-1},
+  rho E, rho Y_0 .. rho Y_{N-2}`` in the same ``[nv, nz, ny, nx]`` layout,
+  x fastest.  This is the four-equation state vector of Eq. 2-1.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional
+
+import numpy as np
+
+SEED = 20230401
+MASK64 = (1 << 64) - 1
+
+# boundary kinds
+BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_INFLOW = 0, 1, 2, 3
+# limiter ids (Table 4.2 plus the Superbee form printed in Sec. 3.3)
+LIM_MINMOD, LIM_KOREN, LIM_VANLEER, LIM_VANALBADA, LIM_CHAKRAVARTHY, LIM_MC, LIM_SUPERBEE = range(7)
+# component kinds
+KIND_SG, KIND_PR = 0, 1
+
+
+# --------------------------------------------------------------------------
+# random numbers
+# --------------------------------------------------------------------------
+class SplitMix64:
+    """splitmix64 (Steele, Lea & Flood 2014): state += golden gamma, then
+    two xor-shift-multiply rounds.  ``uniform()`` maps the top 53 bits to
+    [0, 1)."""
+
+    def __init__(self, seed: int = SEED):
+        self.state = seed & MASK64
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+    def uniforms(self, n: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        return np.array([self.uniform(lo, hi) for _ in range(n)], dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# materials (parameters of Eq. A.1.1 / A.2.1)
+# --------------------------------------------------------------------------
+def comp_sg(gamma, pinf, cv, q=0.0, M=0.0):
+    return dict(kind=KIND_SG, gamma=float(gamma), pinf=float(pinf), cv=float(cv), q=float(q),
+                Tc=0.0, pc=0.0, omega=0.0, M=float(M))
+
+
+def comp_pr(Tc, pc, omega, cv, M):
+    return dict(kind=KIND_PR, gamma=0.0, pinf=0.0, cv=float(cv), q=0.0,
+                Tc=float(Tc), pc=float(pc), omega=float(omega), M=float(M))
+
+
+WATER = comp_sg(6.12, 3.43e8, 1816.0)
+AIR = comp_sg(1.4, 0.0, 718.0)
+DODECANE_SG = comp_sg(2.35, 4.0e8, 1077.0)
+N2_IG = comp_sg(1.4, 0.0, 743.0)
+CH4_IG = comp_sg(1.304, 0.0, 1709.0)
+DODECANE_PR = comp_pr(658.1, 1.817e6, 0.574, 2200.0, 0.170338)
+N2_PR = comp_pr(126.2, 3.396e6, 0.037, 743.0, 0.0280134)
+
+
+def default_scheme(**kw) -> Dict:
+    s = dict(iles=0, thinc=1, beta=1.6, thinc_eps=1e-4, thinc_gamma=1e-20,
+             lim_vel=LIM_KOREN, lim_scalar=LIM_MINMOD,
+             thr_ducros=0.95, thr_gas=0.4, eps_ducros=1e-20, d3p_coef=1.0,
+             sigma=0.0, grad_eps=1e-8, precision=0, p_ref=1e5, T_ref=300.0)
+    s.update(kw)
+    return s
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    ndim: int
+    n: List[int]                 # interior cells (nx, ny, nz); nz = 1 in 2D
+    lo: List[float]
+    hi: List[float]
+    bc: List[List[int]]          # [dim][low, high]
+    comps: List[Dict]
+    liquid: int                  # index of the liquid component (CSF, sensors)
+    scheme: Dict
+    steps: int
+    cfl: float
+    init: str                    # initial-condition recipe name
+    params: Dict = dataclasses.field(default_factory=dict)
+    inflow: Optional[Dict] = None
+
+    @property
+    def ncomp(self) -> int:
+        return len(self.comps)
+
+    @property
+    def nvar(self) -> int:
+        return self.ndim + 2 + self.ncomp - 1
+
+    @property
+    def cells(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+    @property
+    def dx(self) -> List[float]:
+        return [(self.hi[d] - self.lo[d]) / self.n[d] for d in range(3)]
+
+    def centres(self):
+        """cell-centre coordinates x[nx], y[ny], z[nz]"""
+        return [self.lo[d] + (np.arange(self.n[d]) + 0.5) * self.dx[d] for d in range(3)]
+
+    def primitives(self) -> np.ndarray:
+        return _INIT[self.init](self)
+
+
+# --------------------------------------------------------------------------
+# initial-condition helpers
+# --------------------------------------------------------------------------
+def tanh_indicator(dist, width):
+    """1 inside (dist < 0), 0 outside, smoothed by tanh over ``width``."""
+    return 0.5 * (1.0 - np.tanh(dist / width))
+
+
+def rh_post_shock_sg(p1, T1, p2, comp):
+    """Post-shock (rho2, u2, T2) of a right-moving shock into a pure
+    stiffened gas at rest (p1, T1).  Shock adiabat with p -> p + pinf:
+    rho2/rho1 = ((g+1)(p2+pi) + (g-1)(p1+pi)) / ((g-1)(p2+pi) + (g+1)(p1+pi)),
+    u2 = sqrt((p2-p1)(1/rho1 - 1/rho2))."""
+    g, pi, cv = comp["gamma"], comp["pinf"], comp["cv"]
+    rho1 = (p1 + pi) / ((g - 1.0) * cv * T1)
+    a, b = p2 + pi, p1 + pi
+    rho2 = rho1 * ((g + 1.0) * a + (g - 1.0) * b) / ((g - 1.0) * a + (g + 1.0) * b)
+    u2 = math.sqrt((p2 - p1) * (1.0 / rho1 - 1.0 / rho2))
+    T2 = (p2 + pi) / ((g - 1.0) * cv * rho2)
+    return rho1, rho2, u2, T2
+
+
+def _alloc(w: Workload):
+    return np.zeros((w.nvar, w.n[2], w.n[1], w.n[0]), dtype=np.float64)
+
+
+def _grid(w: Workload):
+    x, y, z = w.centres()
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    return X, Y, Z
+
+
+def _init_column(w: Workload):
+    """configs[0]: a water column of radius R (centred) in air, uniform p, T
+    and velocity; Y_water tanh-smoothed over ``width`` cells."""
+    P = w.params
+    X, Y, _ = _grid(w)
+    xc = 0.5 * (w.lo[0] + w.hi[0]); yc = 0.5 * (w.lo[1] + w.hi[1])
+    r = np.sqrt((X - xc) ** 2 + (Y - yc) ** 2)
+    h = tanh_indicator(r - P["R"], P["width"] * w.dx[0])     # liquid indicator
+    W = _alloc(w)
+    W[0] = P["u"][0]; W[1] = P["u"][1]
+    W[w.ndim] = P["p"]; W[w.ndim + 1] = P["T"]
+    # component 0 = air (tracked), component 1 = water (implied)
+    W[w.ndim + 2] = 1.0 - h
+    return W
+
+
+def _init_shock_bubble(w: Workload):
+    """configs[1]: planar shock in water (post-shock p2, RH states) at x_s
+    moving +x, air bubble (radius R at (xb, yb)) tanh-smoothed."""
+    P = w.params
+    X, Y, _ = _grid(w)
+    water = w.comps[1]
+    _, _, u2, T2 = rh_post_shock_sg(P["p"], P["T"], P["p2"], water)
+    r = np.sqrt((X - P["xb"]) ** 2 + (Y - P["yb"]) ** 2)
+    gas = tanh_indicator(r - P["R"], P["width"] * w.dx[0])
+    post = X < P["xs"]
+    W = _alloc(w)
+    W[0] = np.where(post, u2, 0.0)
+    W[1] = 0.0
+    W[w.ndim] = np.where(post, P["p2"], P["p"])
+    W[w.ndim + 1] = np.where(post, T2, P["T"])
+    W[w.ndim + 2] = gas
+    return W
+
+
+def _init_droplet(w: Workload):
+    """configs[3] case: a water droplet with an elliptical (mode-2) radius
+    perturbation r_i(theta) = R + A cos(2 theta), at rest, uniform p and T.
+    ``dp`` optionally presets a pressure jump inside (static-drop tests)."""
+    P = w.params
+    X, Y, _ = _grid(w)
+    xc = 0.5 * (w.lo[0] + w.hi[0]); yc = 0.5 * (w.lo[1] + w.hi[1])
+    dxx, dyy = X - xc, Y - yc
+    r = np.sqrt(dxx ** 2 + dyy ** 2)
+    th = np.arctan2(dyy, dxx)
+    ri = P["R"] + P.get("A", 0.0) * np.cos(2.0 * th)
+    h = tanh_indicator(r - ri, P["width"] * w.dx[0])
+    W = _alloc(w)
+    W[w.ndim] = P["p"] + P.get("dp", 0.0) * h
+    W[w.ndim + 1] = P["T"]
+    W[w.ndim + 2] = 1.0 - h           # air tracked, water implied
+    return W
+
+
+def _init_random(w: Workload):
+    """Smooth random state with a material interface, for stage parity: all
+    variables carry seeded perturbations so every branch (both upwind
+    signs, limiter regimes, THINC eligible and not) is exercised."""
+    P = w.params
+    rng = SplitMix64(P.get("seed", SEED))
+    X, Y, Z = _grid(w)
+    L = [w.hi[d] - w.lo[d] for d in range(3)]
+    W = _alloc(w)
+
+    def field(amp):
+        f = np.zeros_like(X)
+        for _ in range(4):
+            kx, ky, kz = (int(rng.uniform(1, 4)) for _ in range(3))
+            ph = rng.uniform(0, 2 * math.pi)
+            a = rng.uniform(-1, 1)
+            arg = 2 * math.pi * (kx * X / L[0] + ky * Y / L[1] + (kz * Z / L[2] if w.ndim == 3 else 0.0)) + ph
+            f += a * np.sin(arg)
+        return amp * f / 4.0
+
+    for d in range(w.ndim):
+        W[d] = P.get("u0", [0.0, 0.0, 0.0])[d] + field(P.get("du", 30.0))
+    W[w.ndim] = P["p"] * (1.0 + field(P.get("dp_rel", 0.2)))
+    W[w.ndim + 1] = P["T"] * (1.0 + field(P.get("dT_rel", 0.1)))
+    xc = [w.lo[d] + 0.5 * L[d] for d in range(3)]
+    r2 = (X - xc[0]) ** 2 + (Y - xc[1]) ** 2
+    if w.ndim == 3:
+        r2 = r2 + (Z - xc[2]) ** 2
+    h = tanh_indicator(np.sqrt(r2) - P["R"] * (1.0 + field(0.3)), P["width"] * w.dx[0])
+    nc = w.ncomp
+    if nc == 2:
+        W[w.ndim + 2] = 1.0 - h
+    else:
+        # gas split into two species (N2, CH4) with a smooth ratio; liquid implied
+        ratio = np.clip(0.5 + field(0.8), 0.0, 1.0)
+        W[w.ndim + 2] = (1.0 - h) * ratio
+        W[w.ndim + 3] = (1.0 - h) * (1.0 - ratio)
+    return W
+
+
+_INIT = {"column": _init_column, "shock_bubble": _init_shock_bubble,
+         "droplet": _init_droplet, "random": _init_random}
+
+
+# --------------------------------------------------------------------------
+# the workloads
+# --------------------------------------------------------------------------
+def advection(n=128, steps=200, **scheme):
+    """Plain method, 2D periodic advection of a water column in air, n x n
+    cells on [0, 1]^2 m, uniform p = 1e5 Pa, T = 300 K, u = (50, 50) m/s,
+    column radius 0.2 m, THINC on, no surface tension, CFL 0.4."""
+    nx, ny = (n, n) if isinstance(n, int) else n
+    return Workload(
+        name=f"advection_{nx}x{ny}", ndim=2, n=[nx, ny, 1], lo=[0.0, 0.0, 0.0], hi=[1.0, 1.0 * ny / nx, 1.0],
+        bc=[[BC_PERIODIC] * 2, [BC_PERIODIC] * 2, [BC_PERIODIC] * 2],
+        comps=[AIR, WATER], liquid=1, scheme=default_scheme(**scheme), steps=steps, cfl=0.4,
+        init="column", params=dict(R=0.2, width=1.5, u=(50.0, 50.0), p=1e5, T=300.0))
+
+
+def shock_bubble(nx=2048, ny=1024, steps=4000, **scheme):
+    """2D shock-bubble interaction: nx x ny cells on [0, 2] x [0, 1] mm,
+    water at 1e5 Pa / 300 K, air bubble of radius 0.2 mm at (0.6, 0.5) mm,
+    planar shock with post-shock p = 1e9 Pa at x = 0.3 mm moving +x.
+    Reflective top/bottom, outflow right (and left), CFL 0.4."""
+    L = 1e-3
+    return Workload(
+        name=f"shock_bubble_{nx}x{ny}", ndim=2, n=[nx, ny, 1], lo=[0.0, 0.0, 0.0],
+        hi=[2 * L, 2 * L * ny / nx, 1.0],
+        bc=[[BC_OUTFLOW, BC_OUTFLOW], [BC_REFLECT, BC_REFLECT], [BC_PERIODIC] * 2],
+        comps=[AIR, WATER], liquid=1, scheme=default_scheme(**scheme), steps=steps, cfl=0.4,
+        init="shock_bubble",
+        params=dict(p=1e5, T=300.0, p2=1e9, xs=0.3e-3, xb=0.6e-3, yb=0.5e-3 * (2 * ny / nx), R=0.2e-3,
+                    width=1.5))
+
+
+def droplet(n=128, A=0.1, L=1e-3, sigma=0.07, steps=500, dp=0.0, **scheme):
+    """One oscillating water droplet in air: n x n periodic cells on an
+    L x L box, R = 0.25 L, elliptical perturbation amplitude A*R, at rest,
+    p = 1e5 Pa, T = 300 K, CSF with the given sigma."""
+    nx, ny = (n, n) if isinstance(n, int) else n
+    R = 0.25 * L
+    sch = default_scheme(sigma=sigma, **scheme)
+    return Workload(
+        name=f"droplet_{nx}x{ny}", ndim=2, n=[nx, ny, 1], lo=[0.0, 0.0, 0.0], hi=[L, L * ny / nx, 1.0],
+        bc=[[BC_PERIODIC] * 2, [BC_PERIODIC] * 2, [BC_PERIODIC] * 2],
+        comps=[AIR, WATER], liquid=1, scheme=sch, steps=steps, cfl=0.4, init="droplet",
+        params=dict(R=R, A=A * R, width=1.5, p=1e5, T=300.0, dp=dp))
+
+
+DROPLET_SIDES = (64, 96, 128, 192, 256)
+
+
+def droplet_ensemble(ncases=1024, seed=SEED, steps=500, **scheme):
+    """Batched ensemble: ncases independent oscillating droplets, sides drawn
+    uniformly from {64, 96, 128, 192, 256}, amplitude uniform in
+    [0.05, 0.2] x R, sigma = 0.07 N/m.  Returns the list of cases."""
+    rng = SplitMix64(seed)
+    cases = []
+    for _ in range(ncases):
+        side = DROPLET_SIDES[min(int(rng.uniform(0, len(DROPLET_SIDES))), len(DROPLET_SIDES) - 1)]
+        amp = rng.uniform(0.05, 0.2)
+        cases.append(droplet(n=side, A=amp, steps=steps, **scheme))
+    return cases
+
+
+def random_state(n=(24, 20), ncomp=2, seed=SEED, bc=None, ndim=2, **scheme):
+    """Seeded smooth random state with a material interface for stage-level
+    parity (every branch of the stage is exercised)."""
+    nx, ny = n[0], n[1]
+    nz = n[2] if ndim == 3 else 1
+    L = 1e-3
+    comps = [AIR, WATER] if ncomp == 2 else [N2_IG, CH4_IG, DODECANE_SG]
+    bc = bc or [[BC_PERIODIC] * 2, [BC_PERIODIC] * 2, [BC_PERIODIC] * 2]
+    return Workload(
+        name=f"random_{nx}x{ny}x{nz}", ndim=ndim, n=[nx, ny, nz], lo=[0.0, 0.0, 0.0],
+        hi=[L, L * ny / nx, L * nz / nx], bc=bc, comps=comps, liquid=ncomp - 1,
+        scheme=default_scheme(**scheme), steps=1, cfl=0.4, init="random",
+        params=dict(seed=seed, p=2e6, T=320.0, R=0.3e-3, width=1.5, du=40.0))
