@@ -1,0 +1,180 @@
+/*
+ * thinc_fv.h -- C ABI of the GB300 All-Mach THINC-TDU finite-volume stage
+ * (Jiao, Schmidt & Adams, arXiv 2304.00140).
+ *
+ * One explicit low-storage Runge-Kutta stage (Sec. 3.1, Algorithm 1) of the
+ * single-fluid four-equation model (Sec. 2.1, Eq. 2-1/2-2) on structured
+ * Cartesian grids: boundary update, primitive/thermodynamic update
+ * (App. A, App. B), discontinuity sensor (App. D, Eq. D.4), face
+ * reconstruction switching between limited MUSCL (Sec. 3.3, Table 4.2),
+ * THINC (Eq. 3-3/3-4) and 4th-order central (Eq. D.1-D.3), the
+ * thermodynamic-dependent update of rho and e (Eq. 3-5/3-6), the all-Mach
+ * Riemann flux (Eq. 3-1/3-2; Eq. D.5/D.6), the CSF surface-tension source
+ * with Gaussian-smoothed curvature (Sec. 3.5, Eq. 3-9/3-10) and the
+ * flux-divergence / LSRK register update.  All arithmetic runs in CUDA
+ * kernels for sm_103a; there is no CPU path.
+ *
+ * Conventions
+ *   - State arrays are structure-of-arrays, float64, interior cells only,
+ *     [nv][nz][ny][nx] with x fastest.  nv = ndim + 2 + (ncomp - 1):
+ *       conserved  q = (rho, rho u_0..rho u_{d-1}, rho E, rho Y_0..rho Y_{N-2})
+ *       primitive  W = (u_0..u_{d-1}, p, T, Y_0..Y_{N-2})
+ *     The last component's mass fraction is 1 - sum of the others.
+ *   - Units SI.  2D grids have n[2] = 1.
+ *   - A context may hold several independent cases (a batch); per-case calls
+ *     take the case index, whole-context calls act on every case.
+ *   - Every call returns an fv_status and never aborts.  Host buffers stay
+ *     owned by the caller; device memory belongs to the context (allocated
+ *     with cudaMalloc, or carved from a caller-provided device workspace).
+ *   - Calls are asynchronous on the context's stream except where stated.
+ */
+#ifndef THINC_FV_H
+#define THINC_FV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FV_MAX_COMP 3
+#define FV_MAX_VAR 10
+
+typedef enum {
+    FV_OK = 0,
+    FV_ERR_ARG = 1,          /* invalid argument or unsupported combination */
+    FV_ERR_ALLOC = 2,        /* device memory could not be allocated */
+    FV_ERR_CUDA = 3,         /* a CUDA runtime call failed (see fv_last_error) */
+    FV_ERR_EOS_NONCONV = 4,  /* closure iteration did not converge */
+    FV_ERR_NONPHYSICAL = 5,  /* rho <= 0, p + pinf <= 0, T <= 0 or NaN met in a kernel */
+    FV_ERR_STATE = 6         /* call out of order (e.g. step before set_state) */
+} fv_status;
+
+enum { FV_BC_PERIODIC = 0, FV_BC_REFLECT = 1, FV_BC_OUTFLOW = 2, FV_BC_INFLOW = 3 };
+enum { FV_SG = 0, FV_PR = 1 };
+enum { FV_MINMOD = 0, FV_KOREN = 1, FV_VANLEER = 2, FV_VANALBADA = 3,
+       FV_CHAKRAVARTHY = 4, FV_MC = 5, FV_SUPERBEE = 6 };
+enum { FV_FP64 = 0, FV_MIXED = 1 };
+enum { FV_CONSERVED = 0, FV_PRIMITIVE = 1 };
+enum { FV_DIAG_TOTALS = 0,   /* double[nv]: compensated sums of q over the case */
+       FV_DIAG_DT = 1,       /* double: last step's dt of the case */
+       FV_DIAG_TIME = 2,     /* double: accumulated time of the case */
+       FV_DIAG_ERROR = 3 };  /* int: device error word (bit set of FV_ERRBIT_*) */
+enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2 };
+
+/* Grid of one case.  lo/hi are the box corners (m); bc[d][0] is the low
+ * side of dimension d.  FV_BC_INFLOW is accepted on the x-low side only:
+ * inside the disc (in_yc, in_zc, in_radius) the ghost cells take Dirichlet
+ * u (in_u, or in_u0 when in_u is NULL), T = in_T and Y = in_Y with
+ * zero-gradient p; outside it they are a slip wall. */
+typedef struct {
+    int ndim;                    /* 2 or 3 */
+    int n[3];                    /* interior cells per dimension (n[2] = 1 in 2D) */
+    double lo[3], hi[3];
+    int bc[3][2];
+    double in_yc, in_zc, in_radius, in_T;
+    double in_u0[3];
+    double in_Y[FV_MAX_COMP];
+    const double* in_u;          /* host [3][nz][ny] inflow velocity or NULL; copied at init */
+} fv_grid;
+
+/* One material.  FV_SG: stiffened gas p = (gamma-1) rho (e-q) - gamma pinf
+ * (Eq. A.1.1; ideal gas when pinf = 0).  FV_PR: Peng-Robinson (Eq. A.2.1)
+ * with constant ideal-gas cv; M is the molar mass in kg/mol. */
+typedef struct {
+    int kind;
+    double gamma, pinf, cv, q;
+    double Tc, pc, omega, M;
+} fv_component;
+
+typedef struct {
+    int ncomp;                   /* 2 or 3 */
+    int liquid;                  /* component whose volume fraction feeds CSF and the gas sensor */
+    fv_component comp[FV_MAX_COMP];
+} fv_components;
+
+/* Closure options and scheme switches ("eos" = closure + scheme). */
+typedef struct {
+    int iles;                    /* 0: plain (upwind/THINC everywhere), 1: App. D central switch */
+    int thinc;                   /* THINC for mass fractions on eligible cells (Sec. 3.3) */
+    double beta, thinc_eps, thinc_gamma;   /* beta of Eq. 3-3; eligibility eps; guard gamma */
+    int lim_vel, lim_scalar;     /* FV_* limiter ids for velocities and for p, T, Y */
+    double thr_ducros, thr_gas, eps_ducros, d3p_coef;   /* Eq. D.4 thresholds, D.5 scale */
+    double sigma;                /* surface tension coefficient (N/m); 0 disables CSF */
+    double grad_eps;             /* |grad alpha~| * dx below this gives a zero normal */
+    int precision;               /* FV_FP64 or FV_MIXED */
+    double p_ref, T_ref;         /* offsets carried by the FP32 arithmetic of FV_MIXED */
+} fv_eos;
+
+typedef struct fv_ctx fv_ctx;
+
+/* Bytes of device workspace fv_init_ws needs for these cases. */
+fv_status fv_workspace_size(int ncases, const fv_grid* grids, const fv_components* comps,
+                            const fv_eos* eos, size_t* bytes);
+
+/* Create a context for ncases independent cases sharing components and
+ * scheme (ncases = 1: a single grid).  fv_init allocates device memory with
+ * cudaMalloc; fv_init_ws uses the caller's device buffer of at least
+ * fv_workspace_size bytes (256-byte aligned), which must outlive the context.
+ * The context uses the current CUDA device and the legacy default stream
+ * until fv_set_stream.  Errors: FV_ERR_ARG (bad sizes, unsupported closure or
+ * boundary mix), FV_ERR_ALLOC, FV_ERR_CUDA.  On an error *out may still hold
+ * a context whose fv_last_error explains it; release it with fv_destroy. */
+fv_status fv_init(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
+                  fv_ctx** out);
+fv_status fv_init_ws(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
+                     void* dev_workspace, size_t bytes, fv_ctx** out);
+void fv_destroy(fv_ctx* ctx);
+
+/* Stream (a cudaStream_t) for all later work of the context. */
+fv_status fv_set_stream(fv_ctx* ctx, void* stream);
+
+/* Copy a case's state from/to host memory (kind FV_CONSERVED or
+ * FV_PRIMITIVE; nv * n[0]*n[1]*n[2] doubles).  Primitive input is turned
+ * into conserved variables by the closure on the device.  Synchronous:
+ * returns once the copy is complete.  get_state also reports a pending
+ * device error word as FV_ERR_NONPHYSICAL / FV_ERR_EOS_NONCONV. */
+fv_status fv_set_state(fv_ctx* ctx, int icase, int kind, const double* host);
+fv_status fv_get_state(fv_ctx* ctx, int icase, int kind, double* host);
+/* Same with device pointers; asynchronous on the context's stream. */
+fv_status fv_set_state_device(fv_ctx* ctx, int icase, int kind, const double* dev);
+fv_status fv_get_state_device(fv_ctx* ctx, int icase, int kind, double* dev);
+
+/* One Runge-Kutta stage k = 1..4 of every case with a caller-given dt
+ * (q^k = q^0 + a_k dt R(q^{k-1}); stage 1 starts from the current state,
+ * stage 4 writes the new state).  Stages must be called in order. */
+fv_status fv_rk_stage(fv_ctx* ctx, int k, double dt);
+
+/* nsteps full steps: per step dt = cfl / max(sum_d (|u_d| + c)/dx_d) of each
+ * case (computed on the device from the step's initial state), then the four
+ * stages.  The step sequence is captured once per cfl value in a CUDA graph
+ * and replayed on the context's stream.  t_out (may be NULL) receives case
+ * 0's simulated time since its last fv_set_state.  Synchronises the stream
+ * once at the end and reports a device error word (FV_ERR_NONPHYSICAL). */
+fv_status fv_step(fv_ctx* ctx, int nsteps, double cfl, double* t_out);
+/* Same without any host synchronisation or readback (for timing loops). */
+fv_status fv_step_async(fv_ctx* ctx, int nsteps, double cfl);
+
+/* Diagnostics of one case (see FV_DIAG_*); synchronous. */
+fv_status fv_get_diag(fv_ctx* ctx, int icase, int what, void* out);
+
+/* Counters of kernel launches issued so far (for launch accounting). */
+long long fv_launch_count(const fv_ctx* ctx);
+
+/* Kernel timing: with enable = 1, fv_step / fv_step_async / fv_rk_stage
+ * launch the kernels directly (no graph) and record a CUDA event pair on the
+ * context's stream around every launch; enable = 0 stops recording and frees
+ * the events.  fv_profile_read synchronises and returns, per kernel kind
+ * (FV_KERNEL_*), out[2*kind] = total milliseconds and out[2*kind+1] = number
+ * of launches since recording started. */
+enum { FV_KERNEL_PRIM = 0, FV_KERNEL_DT = 1, FV_KERNEL_STAGE = 2, FV_KERNEL_KINDS = 3 };
+fv_status fv_profile(fv_ctx* ctx, int enable);
+fv_status fv_profile_read(fv_ctx* ctx, double* out);
+
+const char* fv_last_error(const fv_ctx* ctx);
+const char* fv_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,727 @@
+// fv_api.cu -- the C ABI (include/thinc_fv.h): context set-up, device memory
+// layout, work lists, the stage sequence and its CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/thinc_fv.h"
+#include "fv_launch.h"
+
+using namespace tfv;
+
+namespace {
+
+// Jameson-Schmidt-Turkel four-stage low-storage coefficients (the paper
+// names a four-stage low-storage Runge-Kutta scheme without coefficients).
+const double LSRK_A[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t cases, items_stage, items_prim, q0, qa, qb, prim, io, smax, dt, t, err, in_u, partial, total;
+    int n_items_stage, n_items_prim;
+    long long ntot_q, ntot_p, max_cells, n_in_u;
+};
+
+int tile_x(int nd) { return nd == 2 ? TileShape<2>::X : TileShape<3>::X; }
+int tile_y(int nd) { return nd == 2 ? TileShape<2>::Y : TileShape<3>::Y; }
+int tile_z(int nd) { return nd == 2 ? TileShape<2>::Z : TileShape<3>::Z; }
+
+long long ntiles(const int* ext, int nd)
+{
+    long long t = 1;
+    const int ts[3] = {tile_x(nd), tile_y(nd), tile_z(nd)};
+    for (int d = 0; d < 3; ++d) t *= (ext[d] + ts[d] - 1) / ts[d];
+    return t;
+}
+
+}  // namespace
+
+struct fv_ctx {
+    int ncases = 0, nd = 0, nc = 0, nv = 0, nprim = 0, mixed = 0;
+    DevParams P{};
+    std::vector<fv_grid> grids;
+    std::vector<CaseDesc> cases;
+    Layout L{};
+    unsigned char* base = nullptr;
+    bool owns = false;
+    CaseDesc* d_cases = nullptr;
+    int4* d_items_stage = nullptr;
+    int4* d_items_prim = nullptr;
+    double *Q0 = nullptr, *QA = nullptr, *QB = nullptr;
+    void* prim = nullptr;
+    double* io = nullptr;
+    unsigned long long* smax = nullptr;
+    double* dt = nullptr;
+    double* t = nullptr;
+    int* err = nullptr;
+    double* in_u = nullptr;
+    double* partial = nullptr;
+    cudaStream_t stream = nullptr;          // user stream (0 = legacy default)
+    cudaStream_t cap = nullptr;             // private stream used for graph capture
+    size_t smem = 0;
+    int stage_grid = 0, prim_grid = 0;
+    std::vector<std::pair<double, cudaGraphExec_t>> graphs;
+    long long launches = 0;
+    std::string msg;
+    bool profiling = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;   // (kind, (start, stop))
+};
+
+static fv_status fail(fv_ctx* c, fv_status s, const char* fmt, const char* arg = "")
+{
+    if (c) {
+        char buf[512];
+        snprintf(buf, sizeof buf, fmt, arg);
+        c->msg = buf;
+    }
+    return s;
+}
+
+static fv_status cuda_fail(fv_ctx* c, cudaError_t e, const char* where)
+{
+    if (c) c->msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return FV_ERR_CUDA;
+}
+
+#define CK(ctx, call)                                             \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+    } while (0)
+
+// ------------------------------------------------------------------ checks
+static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm, const fv_eos* eos,
+                          std::string& why)
+{
+    if (ncases < 1 || !g || !cm || !eos) { why = "null argument or ncases < 1"; return FV_ERR_ARG; }
+    const int nd = g[0].ndim;
+    if (nd != 2 && nd != 3) { why = "ndim must be 2 or 3"; return FV_ERR_ARG; }
+    for (int c = 0; c < ncases; ++c) {
+        if (g[c].ndim != nd) { why = "all cases must share ndim"; return FV_ERR_ARG; }
+        for (int d = 0; d < 3; ++d) {
+            const int want1 = d >= nd;
+            if (g[c].n[d] < 1 || (want1 && g[c].n[d] != 1)) { why = "bad cell counts"; return FV_ERR_ARG; }
+            if (d < nd && !(g[c].hi[d] > g[c].lo[d])) { why = "hi must exceed lo"; return FV_ERR_ARG; }
+            if (d < nd) {
+                for (int s = 0; s < 2; ++s)
+                    if (g[c].bc[d][s] < 0 || g[c].bc[d][s] > 3) { why = "bad boundary kind"; return FV_ERR_ARG; }
+                if ((g[c].bc[d][0] == FV_BC_PERIODIC) != (g[c].bc[d][1] == FV_BC_PERIODIC)) {
+                    why = "periodic boundaries must pair";
+                    return FV_ERR_ARG;
+                }
+                if ((d > 0 && g[c].bc[d][0] == FV_BC_INFLOW) || g[c].bc[d][1] == FV_BC_INFLOW) {
+                    why = "inflow only on the x-low side";
+                    return FV_ERR_ARG;
+                }
+            }
+        }
+        if ((long long)g[c].n[0] * g[c].n[1] * g[c].n[2] > (1LL << 31)) { why = "case too large"; return FV_ERR_ARG; }
+    }
+    if (cm->ncomp < 2 || cm->ncomp > 3) { why = "ncomp must be 2 or 3"; return FV_ERR_ARG; }
+    if (cm->liquid < 0 || cm->liquid >= cm->ncomp) { why = "bad liquid index"; return FV_ERR_ARG; }
+    double pis[FV_MAX_COMP];
+    int npi = 0;
+    for (int k = 0; k < cm->ncomp; ++k) {
+        const fv_component& c = cm->comp[k];
+        if (c.kind != FV_SG) { why = "only stiffened-gas / ideal-gas components are supported"; return FV_ERR_ARG; }
+        if (!(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) { why = "bad component constants"; return FV_ERR_ARG; }
+        bool seen = false;
+        for (int j = 0; j < npi; ++j) seen = seen || pis[j] == c.pinf;
+        if (!seen) pis[npi++] = c.pinf;
+    }
+    if (npi > 2) { why = "at most two distinct pinf values"; return FV_ERR_ARG; }
+    if (eos->lim_vel < 0 || eos->lim_vel > 6 || eos->lim_scalar < 0 || eos->lim_scalar > 6) {
+        why = "bad limiter id";
+        return FV_ERR_ARG;
+    }
+    if (eos->precision != FV_FP64 && eos->precision != FV_MIXED) { why = "bad precision"; return FV_ERR_ARG; }
+    if (eos->thinc && !(eos->beta > 0.0)) { why = "THINC beta must be positive"; return FV_ERR_ARG; }
+    if (!(eos->sigma >= 0.0)) { why = "sigma must be >= 0"; return FV_ERR_ARG; }
+    return FV_OK;
+}
+
+static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
+{
+    DevParams& P = x->P;
+    memset(&P, 0, sizeof P);
+    P.ndim = x->nd;
+    P.ncomp = cm->ncomp;
+    P.nv = x->nv;
+    P.liquid = cm->liquid;
+    P.iles = eos->iles ? 1 : 0;
+    P.thinc = eos->thinc ? 1 : 0;
+    P.lim_vel = eos->lim_vel;
+    P.lim_scalar = eos->lim_scalar;
+    P.csf = eos->sigma > 0.0 ? 1 : 0;
+    P.aux_rc = P.iles;
+    P.aux_al = (P.csf || P.iles) ? 1 : 0;
+    int np = x->nv;
+    P.i_rho = P.i_c = P.i_al = -1;
+    if (P.aux_rc) { P.i_rho = np++; P.i_c = np++; }
+    if (P.aux_al) P.i_al = np++;
+    P.nprim = np;
+    x->nprim = np;
+    P.beta = eos->beta;
+    P.thinc_eps = eos->thinc_eps;
+    P.thinc_gamma = eos->thinc_gamma;
+    P.tb = std::tanh(eos->beta);
+    P.icb = 1.0 / std::cosh(eos->beta);
+    P.itb = eos->beta > 0 ? 1.0 / std::tanh(eos->beta) : 0.0;
+    P.thr_ducros = eos->thr_ducros;
+    P.thr_gas = eos->thr_gas;
+    P.eps_ducros = eos->eps_ducros;
+    P.d3p_coef = eos->d3p_coef;
+    P.sigma = eos->sigma;
+    P.grad_eps = eos->grad_eps;
+    P.p_ref = x->mixed ? eos->p_ref : 0.0;
+    double piA = 0.0, piB = 1e300;
+    for (int k = 0; k < cm->ncomp; ++k) {
+        piA = std::max(piA, cm->comp[k].pinf);
+        piB = std::min(piB, cm->comp[k].pinf);
+    }
+    P.single_class = piA == piB;
+    for (int k = 0; k < cm->ncomp; ++k) {
+        const fv_component& c = cm->comp[k];
+        CompDev& d = P.c[k];
+        d.gamma = c.gamma;
+        d.pinf = c.pinf;
+        d.cv = c.cv;
+        d.q = c.q;
+        d.gm1cv = (c.gamma - 1.0) * c.cv;
+        d.gcv = c.gamma * c.cv;
+        d.igamma = 1.0 / c.gamma;
+        d.classA = (c.pinf == piA && !P.single_class) ? 1 : 0;
+        d.pother = P.single_class ? 0.0 : (d.classA ? piB : piA);
+        P.Pk[k] = P.p_ref + c.pinf;
+    }
+}
+
+static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mixed, Layout& L,
+                 std::vector<CaseDesc>* cases, std::vector<int4>* items_stage, std::vector<int4>* items_prim)
+{
+    L = Layout{};
+    long long qoff = 0, poff = 0, nin = 0;
+    const int ts[3] = {tile_x(nd), tile_y(nd), tile_z(nd)};
+    for (int c = 0; c < ncases; ++c) {
+        CaseDesc C{};
+        int gx[3];
+        for (int d = 0; d < 3; ++d) {
+            C.n[d] = g[c].n[d];
+            C.g[d] = d < nd ? g[c].n[d] + 4 : 1;
+            gx[d] = C.g[d];
+            C.dx[d] = d < nd ? (g[c].hi[d] - g[c].lo[d]) / g[c].n[d] : 1.0;
+            C.idx[d] = 1.0 / C.dx[d];
+            C.bc[d][0] = d < nd ? g[c].bc[d][0] : 0;
+            C.bc[d][1] = d < nd ? g[c].bc[d][1] : 0;
+        }
+        C.qoff = qoff;
+        C.poff = poff;
+        C.inflow = g[c].bc[0][0] == FV_BC_INFLOW;
+        C.in_yc = g[c].in_yc - g[c].lo[1];
+        C.in_zc = g[c].in_zc - g[c].lo[2];
+        C.in_r2 = g[c].in_radius * g[c].in_radius;
+        C.in_T = g[c].in_T;
+        for (int d = 0; d < 3; ++d) C.in_u0[d] = g[c].in_u0[d];
+        for (int k = 0; k < FV_MAX_COMP && k < MAXC; ++k) C.in_Y[k] = g[c].in_Y[k];
+        C.in_uoff = -1;
+        if (C.inflow && g[c].in_u) {
+            C.in_uoff = nin;
+            nin += 3LL * C.n[1] * C.n[2];
+        }
+        const long long ncell = (long long)C.n[0] * C.n[1] * C.n[2];
+        qoff += ncell;
+        poff += (long long)C.g[0] * C.g[1] * C.g[2];
+        L.max_cells = std::max(L.max_cells, ncell);
+        if (cases) cases->push_back(C);
+        long long nst = ntiles(C.n, nd), npr = ntiles(gx, nd);
+        L.n_items_stage += (int)nst;
+        L.n_items_prim += (int)npr;
+        if (items_stage)
+            for (int z = 0; z < C.n[2]; z += ts[2])
+                for (int y = 0; y < C.n[1]; y += ts[1])
+                    for (int x = 0; x < C.n[0]; x += ts[0]) items_stage->push_back(make_int4(c, x, y, z));
+        if (items_prim)
+            for (int z = 0; z < gx[2]; z += ts[2])
+                for (int y = 0; y < gx[1]; y += ts[1])
+                    for (int x = 0; x < gx[0]; x += ts[0]) items_prim->push_back(make_int4(c, x, y, z));
+    }
+    L.ntot_q = qoff;
+    L.ntot_p = poff;
+    L.n_in_u = nin;
+    const size_t rsz = mixed ? sizeof(float) : sizeof(double);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o += align256(bytes); return at; };
+    L.cases = take(sizeof(CaseDesc) * ncases);
+    L.items_stage = take(sizeof(int4) * L.n_items_stage);
+    L.items_prim = take(sizeof(int4) * L.n_items_prim);
+    L.q0 = take(sizeof(double) * nv * qoff);
+    L.qa = take(sizeof(double) * nv * qoff);
+    L.qb = take(sizeof(double) * nv * qoff);
+    L.prim = take(rsz * nprim * poff);
+    L.io = take(sizeof(double) * nv * L.max_cells);
+    L.smax = take(sizeof(unsigned long long) * ncases);
+    L.dt = take(sizeof(double) * ncases);
+    L.t = take(sizeof(double) * ncases);
+    L.err = take(sizeof(int));
+    L.in_u = take(sizeof(double) * std::max(1LL, nin));
+    L.partial = take(sizeof(double) * nv * 1024);
+    L.total = o;
+}
+
+static int count_nprim(const fv_eos* eos, int nv)
+{
+    int np = nv;
+    if (eos->iles) np += 2;
+    if (eos->iles || eos->sigma > 0.0) np += 1;
+    return np;
+}
+
+extern "C" fv_status fv_workspace_size(int ncases, const fv_grid* grids, const fv_components* comps,
+                                       const fv_eos* eos, size_t* bytes)
+{
+    std::string why;
+    fv_status s = validate(ncases, grids, comps, eos, why);
+    if (s) return s;
+    const int nd = grids[0].ndim, nv = nd + comps->ncomp + 1;
+    Layout L;
+    plan(ncases, grids, nd, nv, count_nprim(eos, nv), eos->precision == FV_MIXED, L, nullptr, nullptr, nullptr);
+    if (bytes) *bytes = L.total;
+    return FV_OK;
+}
+
+static fv_status init_common(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
+                             void* ws, size_t ws_bytes, fv_ctx** out)
+{
+    if (!out) return FV_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    fv_status s = validate(ncases, grids, comps, eos, why);
+    fv_ctx* x = new (std::nothrow) fv_ctx();
+    if (!x) return FV_ERR_ALLOC;
+    if (s) {
+        x->msg = why;
+        *out = x;   // returned so the caller can read fv_last_error, then fv_destroy
+        return s;
+    }
+    x->ncases = ncases;
+    x->nd = grids[0].ndim;
+    x->nc = comps->ncomp;
+    x->nv = x->nd + x->nc + 1;
+    x->mixed = eos->precision == FV_MIXED;
+    x->grids.assign(grids, grids + ncases);
+    build_params(x, comps, eos);
+    std::vector<int4> ist, ipr;
+    plan(ncases, grids, x->nd, x->nv, x->nprim, x->mixed, x->L, &x->cases, &ist, &ipr);
+    *out = x;
+    const Layout& L = x->L;
+    x->P.ntot_q = L.ntot_q;
+    x->P.ntot_p = L.ntot_p;
+    if (ws) {
+        if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255))
+            return fail(x, FV_ERR_ARG, "workspace too small or not 256-byte aligned%s");
+        x->base = static_cast<unsigned char*>(ws);
+    } else {
+        cudaError_t e = cudaMalloc(&x->base, L.total);
+        if (e != cudaSuccess) {
+            x->base = nullptr;
+            cudaGetLastError();
+            return fail(x, FV_ERR_ALLOC, "cudaMalloc of the context workspace failed%s");
+        }
+        x->owns = true;
+    }
+    unsigned char* b = x->base;
+    x->d_cases = reinterpret_cast<CaseDesc*>(b + L.cases);
+    x->d_items_stage = reinterpret_cast<int4*>(b + L.items_stage);
+    x->d_items_prim = reinterpret_cast<int4*>(b + L.items_prim);
+    x->Q0 = reinterpret_cast<double*>(b + L.q0);
+    x->QA = reinterpret_cast<double*>(b + L.qa);
+    x->QB = reinterpret_cast<double*>(b + L.qb);
+    x->prim = b + L.prim;
+    x->io = reinterpret_cast<double*>(b + L.io);
+    x->smax = reinterpret_cast<unsigned long long*>(b + L.smax);
+    x->dt = reinterpret_cast<double*>(b + L.dt);
+    x->t = reinterpret_cast<double*>(b + L.t);
+    x->err = reinterpret_cast<int*>(b + L.err);
+    x->in_u = reinterpret_cast<double*>(b + L.in_u);
+    x->partial = reinterpret_cast<double*>(b + L.partial);
+    CK(x, cudaStreamCreateWithFlags(&x->cap, cudaStreamNonBlocking));
+    CK(x, cudaMemcpy(x->d_cases, x->cases.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice));
+    CK(x, cudaMemcpy(x->d_items_stage, ist.data(), sizeof(int4) * ist.size(), cudaMemcpyHostToDevice));
+    CK(x, cudaMemcpy(x->d_items_prim, ipr.data(), sizeof(int4) * ipr.size(), cudaMemcpyHostToDevice));
+    CK(x, cudaMemset(x->smax, 0, sizeof(unsigned long long) * ncases));
+    CK(x, cudaMemset(x->dt, 0, sizeof(double) * ncases));
+    CK(x, cudaMemset(x->t, 0, sizeof(double) * ncases));
+    CK(x, cudaMemset(x->err, 0, sizeof(int)));
+    CK(x, cudaMemset(x->Q0, 0, sizeof(double) * x->nv * L.ntot_q));
+    for (int c = 0; c < ncases; ++c)
+        if (x->cases[c].in_uoff >= 0)
+            CK(x, cudaMemcpy(x->in_u + x->cases[c].in_uoff, grids[c].in_u,
+                             sizeof(double) * 3 * grids[c].n[1] * grids[c].n[2], cudaMemcpyHostToDevice));
+    // launch shapes: persistent grids of (resident blocks per SM) x (SMs)
+    int dev = 0, nsm = 0;
+    CK(x, cudaGetDevice(&dev));
+    CK(x, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    x->smem = stage_smem(x->nd, x->nc, x->mixed, x->nprim);
+    CK(x, stage_set_smem(x->nd, x->nc, x->mixed, x->smem));
+    const int occ_s = stage_occupancy(x->nd, x->nc, x->mixed, x->smem);
+    const int occ_p = prim_occupancy(x->nd, x->nc, x->mixed);
+    x->stage_grid = std::min(L.n_items_stage, std::max(1, nsm * occ_s));
+    x->prim_grid = std::min(L.n_items_prim, std::max(1, nsm * occ_p));
+    CK(x, cudaDeviceSynchronize());
+    return FV_OK;
+}
+
+extern "C" fv_status fv_init(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
+                             fv_ctx** out)
+{
+    return init_common(ncases, grids, comps, eos, nullptr, 0, out);
+}
+
+extern "C" fv_status fv_init_ws(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
+                                void* dev_workspace, size_t bytes, fv_ctx** out)
+{
+    if (!dev_workspace) return FV_ERR_ARG;
+    return init_common(ncases, grids, comps, eos, dev_workspace, bytes, out);
+}
+
+static void prof_clear(fv_ctx* x);
+
+extern "C" void fv_destroy(fv_ctx* x)
+{
+    if (!x) return;
+    for (auto& g : x->graphs) cudaGraphExecDestroy(g.second);
+    prof_clear(x);
+    if (x->cap) cudaStreamDestroy(x->cap);
+    if (x->owns && x->base) cudaFree(x->base);
+    delete x;
+}
+
+extern "C" fv_status fv_set_stream(fv_ctx* x, void* stream)
+{
+    if (!x) return FV_ERR_ARG;
+    x->stream = static_cast<cudaStream_t>(stream);
+    return FV_OK;
+}
+
+static fv_status case_ok(fv_ctx* x, int icase)
+{
+    if (!x) return FV_ERR_ARG;
+    if (!x->base) return fail(x, FV_ERR_STATE, "context not initialised%s");
+    if (icase < 0 || icase >= x->ncases) return fail(x, FV_ERR_ARG, "case index out of range%s");
+    return FV_OK;
+}
+
+static long long case_cells(const fv_ctx* x, int c)
+{
+    return (long long)x->cases[c].n[0] * x->cases[c].n[1] * x->cases[c].n[2];
+}
+
+static fv_status read_err(fv_ctx* x)
+{
+    int e = 0;
+    CK(x, cudaMemcpy(&e, x->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e & ERR_NONCONV) return fail(x, FV_ERR_EOS_NONCONV, "closure iteration did not converge%s");
+    if (e & ERR_NONPHYS) return fail(x, FV_ERR_NONPHYSICAL, "non-physical state met in a kernel%s");
+    return FV_OK;
+}
+
+static fv_status set_state_impl(fv_ctx* x, int c, int kind, const double* src, cudaMemcpyKind mk, bool sync)
+{
+    fv_status s = case_ok(x, c);
+    if (s) return s;
+    if (!src) return fail(x, FV_ERR_ARG, "null state pointer%s");
+    const long long n = case_cells(x, c);
+    const CaseDesc& C = x->cases[c];
+    if (kind == FV_CONSERVED) {
+        CK(x, cudaMemcpy2DAsync(x->Q0 + C.qoff, sizeof(double) * x->L.ntot_q, src, sizeof(double) * n,
+                                sizeof(double) * n, x->nv, mk, x->stream));
+    } else if (kind == FV_PRIMITIVE) {
+        CK(x, cudaMemcpyAsync(x->io, src, sizeof(double) * x->nv * n, mk, x->stream));
+        IoArgs A{x->P, x->d_cases, c, n, x->io, x->Q0, x->err};
+        CK(x, launch_prim_to_cons(x->nd, x->nc, A, x->stream));
+        x->launches++;
+    } else {
+        return fail(x, FV_ERR_ARG, "bad state kind%s");
+    }
+    CK(x, cudaMemsetAsync(x->t + c, 0, sizeof(double), x->stream));
+    if (sync) {
+        CK(x, cudaStreamSynchronize(x->stream));
+        return read_err(x);
+    }
+    return FV_OK;
+}
+
+static fv_status get_state_impl(fv_ctx* x, int c, int kind, double* dst, cudaMemcpyKind mk, bool sync)
+{
+    fv_status s = case_ok(x, c);
+    if (s) return s;
+    if (!dst) return fail(x, FV_ERR_ARG, "null state pointer%s");
+    const long long n = case_cells(x, c);
+    const CaseDesc& C = x->cases[c];
+    if (kind == FV_CONSERVED) {
+        CK(x, cudaMemcpy2DAsync(dst, sizeof(double) * n, x->Q0 + C.qoff, sizeof(double) * x->L.ntot_q,
+                                sizeof(double) * n, x->nv, mk, x->stream));
+    } else if (kind == FV_PRIMITIVE) {
+        IoArgs A{x->P, x->d_cases, c, n, x->Q0, x->io, x->err};
+        CK(x, launch_cons_to_prim(x->nd, x->nc, A, x->stream));
+        x->launches++;
+        CK(x, cudaMemcpyAsync(dst, x->io, sizeof(double) * x->nv * n, mk, x->stream));
+    } else {
+        return fail(x, FV_ERR_ARG, "bad state kind%s");
+    }
+    if (sync) {
+        CK(x, cudaStreamSynchronize(x->stream));
+        return read_err(x);
+    }
+    return FV_OK;
+}
+
+extern "C" fv_status fv_set_state(fv_ctx* x, int icase, int kind, const double* host)
+{
+    if (x && x->base) CK(x, cudaMemsetAsync(x->err, 0, sizeof(int), x->stream));
+    return set_state_impl(x, icase, kind, host, cudaMemcpyHostToDevice, true);
+}
+
+extern "C" fv_status fv_get_state(fv_ctx* x, int icase, int kind, double* host)
+{
+    return get_state_impl(x, icase, kind, host, cudaMemcpyDeviceToHost, true);
+}
+
+extern "C" fv_status fv_set_state_device(fv_ctx* x, int icase, int kind, const double* dev)
+{
+    return set_state_impl(x, icase, kind, dev, cudaMemcpyDeviceToDevice, false);
+}
+
+extern "C" fv_status fv_get_state_device(fv_ctx* x, int icase, int kind, double* dev)
+{
+    return get_state_impl(x, icase, kind, dev, cudaMemcpyDeviceToDevice, false);
+}
+
+// One stage on stream s: primitives (+ per-case CFL maximum and dt when
+// cfl > 0 at stage 1), then the fused flux/update kernel.
+// event pair around one launch when profiling (never inside a capture)
+static fv_status prof_begin(fv_ctx* x, cudaStream_t s, cudaEvent_t* ev)
+{
+    ev[0] = ev[1] = nullptr;
+    if (!x->profiling || s == x->cap) return FV_OK;
+    CK(x, cudaEventCreate(&ev[0]));
+    CK(x, cudaEventCreate(&ev[1]));
+    CK(x, cudaEventRecord(ev[0], s));
+    return FV_OK;
+}
+
+static fv_status prof_end(fv_ctx* x, cudaStream_t s, cudaEvent_t* ev, int kind)
+{
+    if (!ev[0]) return FV_OK;
+    CK(x, cudaEventRecord(ev[1], s));
+    x->prof.push_back({kind, {ev[0], ev[1]}});
+    return FV_OK;
+}
+
+#define PROF(kind, launch_expr)                         \
+    do {                                                \
+        cudaEvent_t ev_[2];                             \
+        fv_status ps_ = prof_begin(x, s, ev_);          \
+        if (ps_) return ps_;                            \
+        CK(x, (launch_expr));                           \
+        ps_ = prof_end(x, s, ev_, kind);                \
+        if (ps_) return ps_;                            \
+    } while (0)
+
+static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
+{
+    const double* in = k == 1 ? x->Q0 : (k == 2 ? x->QA : (k == 3 ? x->QB : x->QA));
+    double* out = k == 1 ? x->QA : (k == 2 ? x->QB : (k == 3 ? x->QA : x->Q0));
+    const bool cfl_here = (k == 1 && cfl > 0.0);
+    PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, in, x->prim, x->in_u,
+                cfl_here ? x->smax : nullptr, x->err};
+    PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s));
+    x->launches++;
+    if (cfl_here) {
+        PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
+        x->launches++;
+    }
+    StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->L.n_items_stage, x->prim, x->Q0, out, x->dt,
+                 LSRK_A[k - 1], x->err};
+    PROF(FV_KERNEL_STAGE, launch_stage(x->nd, x->nc, x->mixed, sa, x->stage_grid, x->smem, s));
+    x->launches++;
+    return FV_OK;
+}
+
+extern "C" fv_status fv_rk_stage(fv_ctx* x, int k, double dt)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (k < 1 || k > 4) return fail(x, FV_ERR_ARG, "stage index must be 1..4%s");
+    if (k == 1) {
+        if (!(dt > 0.0)) return fail(x, FV_ERR_ARG, "dt must be positive%s");
+        CK(x, launch_fill(x->dt, x->ncases, dt, x->stream));
+        x->launches++;
+    }
+    s = enqueue_stage(x, k, 0.0, x->stream);
+    if (s) return s;
+    if (k == 4) {
+        // advance every case's clock by dt (same as fv_step does)
+        std::vector<double> tt(x->ncases);
+        CK(x, cudaMemcpyAsync(tt.data(), x->t, sizeof(double) * x->ncases, cudaMemcpyDeviceToHost, x->stream));
+        CK(x, cudaStreamSynchronize(x->stream));
+        for (auto& v : tt) v += dt;
+        CK(x, cudaMemcpyAsync(x->t, tt.data(), sizeof(double) * x->ncases, cudaMemcpyHostToDevice, x->stream));
+        CK(x, cudaStreamSynchronize(x->stream));
+    }
+    return FV_OK;
+}
+
+static fv_status step_graph(fv_ctx* x, double cfl, cudaGraphExec_t* exec)
+{
+    for (auto& g : x->graphs)
+        if (g.first == cfl) { *exec = g.second; return FV_OK; }
+    cudaGraph_t graph;
+    const long long before = x->launches;
+    CK(x, cudaStreamBeginCapture(x->cap, cudaStreamCaptureModeThreadLocal));
+    fv_status s = FV_OK;
+    for (int k = 1; k <= 4 && !s; ++k) s = enqueue_stage(x, k, cfl, x->cap);
+    cudaError_t e = cudaStreamEndCapture(x->cap, &graph);
+    x->launches = before;
+    if (s) return s;
+    if (e != cudaSuccess) return cuda_fail(x, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ge;
+    e = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(x, e, "cudaGraphInstantiate");
+    x->graphs.emplace_back(cfl, ge);
+    *exec = ge;
+    return FV_OK;
+}
+
+// kernels per step: 4 prim + 1 dt + 4 stage
+static const int LAUNCHES_PER_STEP = 9;
+
+extern "C" fv_status fv_step_async(fv_ctx* x, int nsteps, double cfl)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (nsteps < 0 || !(cfl > 0.0)) return fail(x, FV_ERR_ARG, "need nsteps >= 0 and cfl > 0%s");
+    if (x->profiling) {
+        for (int i = 0; i < nsteps; ++i)
+            for (int k = 1; k <= 4; ++k) {
+                s = enqueue_stage(x, k, cfl, x->stream);
+                if (s) return s;
+            }
+        return FV_OK;
+    }
+    cudaGraphExec_t ge;
+    s = step_graph(x, cfl, &ge);
+    if (s) return s;
+    for (int i = 0; i < nsteps; ++i) CK(x, cudaGraphLaunch(ge, x->stream));
+    x->launches += (long long)LAUNCHES_PER_STEP * nsteps;
+    return FV_OK;
+}
+
+extern "C" fv_status fv_step(fv_ctx* x, int nsteps, double cfl, double* t_out)
+{
+    fv_status s = fv_step_async(x, nsteps, cfl);
+    if (s) return s;
+    CK(x, cudaStreamSynchronize(x->stream));
+    if (t_out) CK(x, cudaMemcpy(t_out, x->t, sizeof(double), cudaMemcpyDeviceToHost));
+    return read_err(x);
+}
+
+extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
+{
+    fv_status s = case_ok(x, icase);
+    if (s) return s;
+    if (!out) return fail(x, FV_ERR_ARG, "null output%s");
+    if (what == FV_DIAG_TOTALS) {
+        const int nblk = 1024;
+        CK(x, launch_totals(x->nv, x->Q0, x->L.ntot_q, x->cases[icase].qoff, case_cells(x, icase), x->partial,
+                            nblk, x->stream));
+        x->launches++;
+        std::vector<double> part((size_t)x->nv * nblk);
+        CK(x, cudaMemcpyAsync(part.data(), x->partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
+                              x->stream));
+        CK(x, cudaStreamSynchronize(x->stream));
+        double* o = static_cast<double*>(out);
+        for (int v = 0; v < x->nv; ++v) {
+            double sum = 0.0, comp = 0.0;   // Neumaier
+            for (int b = 0; b < nblk; ++b) {
+                const double y = part[(size_t)v * nblk + b], t = sum + y;
+                comp += std::fabs(sum) >= std::fabs(y) ? (sum - t) + y : (y - t) + sum;
+                sum = t;
+            }
+            o[v] = sum + comp;
+        }
+        return FV_OK;
+    }
+    if (what == FV_DIAG_DT || what == FV_DIAG_TIME) {
+        CK(x, cudaStreamSynchronize(x->stream));
+        CK(x, cudaMemcpy(out, (what == FV_DIAG_DT ? x->dt : x->t) + icase, sizeof(double), cudaMemcpyDeviceToHost));
+        return FV_OK;
+    }
+    if (what == FV_DIAG_ERROR) {
+        CK(x, cudaStreamSynchronize(x->stream));
+        CK(x, cudaMemcpy(out, x->err, sizeof(int), cudaMemcpyDeviceToHost));
+        return FV_OK;
+    }
+    return fail(x, FV_ERR_ARG, "unknown diagnostic%s");
+}
+
+extern "C" long long fv_launch_count(const fv_ctx* x) { return x ? x->launches : 0; }
+
+static void prof_clear(fv_ctx* x)
+{
+    for (auto& p : x->prof) {
+        cudaEventDestroy(p.second.first);
+        cudaEventDestroy(p.second.second);
+    }
+    x->prof.clear();
+}
+
+extern "C" fv_status fv_profile(fv_ctx* x, int enable)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    CK(x, cudaStreamSynchronize(x->stream));
+    prof_clear(x);
+    x->profiling = enable != 0;
+    return FV_OK;
+}
+
+extern "C" fv_status fv_profile_read(fv_ctx* x, double* out)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (!out) return fail(x, FV_ERR_ARG, "null output%s");
+    CK(x, cudaStreamSynchronize(x->stream));
+    for (int k = 0; k < 2 * FV_KERNEL_KINDS; ++k) out[k] = 0.0;
+    for (auto& p : x->prof) {
+        float ms = 0.f;
+        CK(x, cudaEventElapsedTime(&ms, p.second.first, p.second.second));
+        out[2 * p.first] += ms;
+        out[2 * p.first + 1] += 1.0;
+    }
+    return FV_OK;
+}
+
+extern "C" const char* fv_last_error(const fv_ctx* x) { return x ? x->msg.c_str() : "null context"; }
+
+extern "C" const char* fv_status_string(int s)
+{
+    switch (s) {
+    case FV_OK: return "FV_OK";
+    case FV_ERR_ARG: return "FV_ERR_ARG";
+    case FV_ERR_ALLOC: return "FV_ERR_ALLOC";
+    case FV_ERR_CUDA: return "FV_ERR_CUDA";
+    case FV_ERR_EOS_NONCONV: return "FV_ERR_EOS_NONCONV";
+    case FV_ERR_NONPHYSICAL: return "FV_ERR_NONPHYSICAL";
+    case FV_ERR_STATE: return "FV_ERR_STATE";
+    default: return "unknown status";
+    }
+}

@@ -1,0 +1,339 @@
+// fv_device.cuh -- device-side data structures and the per-cell / per-face
+// arithmetic of the All-Mach THINC-TDU stage (Jiao, Schmidt & Adams,
+// arXiv 2304.00140).  Templated on the arithmetic type R: double for the
+// FP64 form, float for the mixed form (FP64 conserved registers and an FP64
+// core in the primitive recovery, FP32 everywhere else, pressure carried as
+// an offset p' = p - p_ref).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tfv {
+
+constexpr int MAXC = 4;
+constexpr int ERR_NONPHYS = 1;
+constexpr int ERR_NONCONV = 2;
+
+// Per-case geometry, copied to the device once at init.
+struct CaseDesc {
+    int n[3];            // interior cells (1 in unused dims)
+    int g[3];            // ghosted extents: n + 4 in active dims, 1 otherwise
+    long long qoff;      // first cell of this case in the conserved arrays
+    long long poff;      // first cell of this case in the primitive arrays
+    double dx[3], idx[3];
+    int bc[3][2];
+    int inflow;          // x-low side is an inflow disc
+    double in_yc, in_zc, in_r2, in_T;
+    double in_u0[3];
+    double in_Y[MAXC];
+    long long in_uoff;   // offset of this case's [3][nz][ny] inflow velocity, -1 = use in_u0
+};
+
+struct CompDev {
+    double gamma, pinf, cv, q;
+    double gm1cv;        // (gamma - 1) cv
+    double gcv;          // gamma cv
+    double igamma;       // 1 / gamma
+    double pother;       // pinf of the other pressure class (see prim recovery)
+    int classA;          // 1 if pinf == the larger class pressure
+};
+
+// Scheme constants, passed by value to every kernel (kernel-parameter bank).
+struct DevParams {
+    int ndim, ncomp, nv, nprim, liquid;
+    int iles, thinc, lim_vel, lim_scalar;
+    int csf, aux_rc, aux_al, i_rho, i_c, i_al;
+    double beta, thinc_eps, thinc_gamma, tb, icb, itb;
+    double thr_ducros, thr_gas, eps_ducros, d3p_coef;
+    double sigma, grad_eps;
+    double p_ref;        // pressure offset (0 in the FP64 form)
+    int single_class;    // every component shares one pinf
+    CompDev c[MAXC];
+    double Pk[MAXC];     // p_ref + pinf_k
+    long long ntot_q;    // interior cells of all cases (field stride of q)
+    long long ntot_p;    // ghosted cells of all cases (field stride of primitives)
+};
+
+// ---------------------------------------------------------------- helpers
+template <typename R> __device__ __forceinline__ R clip01(R x) { return x < R(0) ? R(0) : (x > R(1) ? R(1) : x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double sq_rt(double x) { return sqrt(x); }
+__device__ __forceinline__ float sq_rt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double ex(double x) { return exp(x); }
+__device__ __forceinline__ float ex(float x) { return expf(x); }
+
+// Reciprocals of N pressures.  In double one division serves all of them
+// (1/P_k = prod_{j != k} P_j / prod_j P_j); in float each is a division.
+template <int N>
+__device__ __forceinline__ void recips(const double* P, double* iP)
+{
+    if (N == 1) { iP[0] = 1.0 / P[0]; return; }
+    double pre[N], acc = 1.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) { pre[k] = acc; acc *= P[k]; }
+    double inv = 1.0 / acc, suf = 1.0;
+#pragma unroll
+    for (int k = N - 1; k >= 0; --k) { iP[k] = pre[k] * suf * inv; suf *= P[k]; }
+}
+template <int N>
+__device__ __forceinline__ void recips(const float* P, float* iP)
+{
+#pragma unroll
+    for (int k = 0; k < N; ++k) iP[k] = 1.0f / P[k];
+}
+
+// ------------------------------------------------------------ closure
+// Thermodynamic-dependent update (Eq. 3-5/3-6, App. B): from the face
+// pressure offset pp = p - p_ref, temperature T and the NC-1 tracked mass
+// fractions, the stiffened-gas / ideal-gas mixture in p-T equilibrium
+// (App. A.1) gives
+//   1/rho = T sum_k Y_k (gamma_k-1) cv_k / (p + pinf_k)
+//   e     = cp T - p / rho + sum_k Y_k q_k,     cp = sum_k Y_k gamma_k cv_k
+//   1/(rho c^2) = sum_k alpha_k / (gamma_k (p + pinf_k))   (Wood)
+// Returns false for a non-physical input (T <= 0, p + pinf_k <= 0 for a
+// present component, NaN).
+template <int NC, typename R>
+__device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, R& rho, R& e, R& c)
+{
+    R Y[NC], s = R(0);
+#pragma unroll
+    for (int k = 0; k < NC - 1; ++k) { Y[k] = clip01(Yt[k]); s += Y[k]; }
+    Y[NC - 1] = clip01(R(1) - s);
+    R Pk[NC], iP[NC];
+    bool ok = T > R(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        Pk[k] = R(P.Pk[k]) + pp;
+        if (Y[k] > R(0)) ok = ok && (Pk[k] > R(0)); else Pk[k] = R(1);
+    }
+    recips<NC>(Pk, iP);
+    R v = R(0), w = R(0), cp = R(0), eq = R(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        R a = Y[k] * R(P.c[k].gm1cv) * iP[k];
+        v += a;
+        w += a * iP[k] * R(P.c[k].igamma);
+        cp += Y[k] * R(P.c[k].gcv);
+        eq += Y[k] * R(P.c[k].q);
+    }
+    v *= T;
+    w *= T;
+    rho = R(1) / v;
+    e = cp * T - (R(P.p_ref) + pp) * v + eq;
+    c = v * rsq(w);
+    return ok && (v > R(0)) && (w > R(0));
+}
+
+// Primitive recovery (App. B "T = f(e, rho, xi), then p"): for the SG/IG
+// mixture with at most two distinct pinf (classes A and B) the p-T
+// equilibrium is the quadratic
+//   cv p^2 + b p + c = 0,  b = sum_k Y_k cv_k (E_k + pinf_other(k)),
+//                          c = sum_k Y_k cv_k pinf_other(k) E_k,
+//   E_k = gamma_k pinf_k - (gamma_k - 1) rho e
+// whose larger root is the physical one; with one class present the root is
+// p = -sum_k Y_k cv_k E_k / cv.  Then T = (rho e' + p) / (rho cp).  The E_k
+// carry the p + pinf cancellation and are always formed in FP64.
+// Outputs w = (u_0..u_{ND-1}, p - p_ref, T, Y_0..Y_{NC-2}).
+template <int ND, int NC, typename R>
+__device__ __forceinline__ bool prim_recover(const DevParams& P, const double* qc, R* w, double& rho_d,
+                                             R& T_out, R& p_abs)
+{
+    constexpr int NV = ND + NC + 1;
+    (void)NV;
+    const double rho = qc[0];
+    rho_d = rho;
+    const R rr = R(rho);
+    const R irho = R(1) / rr;
+    R ke = R(0);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        R m = R(qc[1 + d]);
+        w[d] = m * irho;
+        ke += R(0.5) * m * w[d];
+    }
+    R Y[NC], s = R(0);
+#pragma unroll
+    for (int k = 0; k < NC - 1; ++k) {
+        Y[k] = clip01(R(qc[ND + 2 + k]) * irho);
+        s += Y[k];
+        w[ND + 2 + k] = Y[k];
+    }
+    Y[NC - 1] = clip01(R(1) - s);
+    R cv = R(0), cp = R(0), b = R(0), cc = R(0), se = R(0), eq = R(0);
+    R sA = R(0), sB = R(0);
+    const double rhoe = qc[ND + 1] - double(ke);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) eq += Y[k] * R(P.c[k].q);
+    const double rhoe_q = rhoe - rho * double(eq);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const CompDev& C = P.c[k];
+        const double Ek = fma(-(C.gamma - 1.0), rhoe_q, C.gamma * C.pinf);
+        const R Yc = Y[k] * R(C.cv);
+        cv += Yc;
+        cp += Y[k] * R(C.gcv);
+        b += Yc * R(Ek + C.pother);
+        cc += Yc * R(C.pother * Ek);
+        se += Yc * R(Ek);
+        if (Y[k] > R(0)) { if (C.classA) sA += Y[k]; else sB += Y[k]; }
+    }
+    R p;
+    if (P.single_class || sA == R(0) || sB == R(0)) {
+        p = -se / cv;
+    } else {
+        const R disc = b * b - R(4) * cv * cc;
+        const R sq = sq_rt(disc > R(0) ? disc : R(0));
+        p = (b >= R(0)) ? (R(-2) * cc) / (b + sq) : (sq - b) / (R(2) * cv);
+    }
+    const R T = R(rhoe_q + double(p)) / (rr * cp);
+    w[ND] = p - R(P.p_ref);
+    w[ND + 1] = T;
+    T_out = T;
+    p_abs = p;
+    bool ok = (rho > 0.0) && (T > R(0)) && (cv > R(0));
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+        if (Y[k] > R(0)) ok = ok && (p + R(P.c[k].pinf) > R(0));
+    return ok;
+}
+
+// ---------------------------------------------------------- reconstruction
+// Sec. 3.3 / Table 4.2 limited slope term  f(r) * den  with r = num / den,
+// written without the division for Minmod and Koren.
+template <typename R>
+__device__ __forceinline__ R limited(int id, R num, R den)
+{
+    if (den == R(0)) return R(0);
+    switch (id) {
+    case 0: {  // Minmod  max(0, min(1, r))
+        if (den > R(0)) return fmax(R(0), fmin(den, num));
+        return fmin(R(0), fmax(den, num));
+    }
+    case 1: {  // Koren  max(0, min(2, 2r, (1 + 2r)/3))
+        const R t = (den + R(2) * num) * R(1.0 / 3.0);
+        if (den > R(0)) return fmax(R(0), fmin(R(2) * den, fmin(R(2) * num, t)));
+        return fmin(R(0), fmax(R(2) * den, fmax(R(2) * num, t)));
+    }
+    default: {
+        const R r = num / den;
+        R f;
+        switch (id) {
+        case 2: f = (r + fabs(r)) / (R(1) + fabs(r)); break;                        // van Leer
+        case 3: f = (r + r * r) / (R(1) + r * r); break;                            // van Albada
+        case 4: f = fmax(R(0), fmin(R(1), R(4) * r)); break;                        // Chakravarthy
+        case 5: f = fmax(R(0), fmin(R(2), fmin(R(2) * r, R(0.5) * (R(1) + r)))); break;  // MC
+        case 6: f = fmax(R(0), fmax(fmin(R(1), R(2) * r), fmin(r, R(2)))); break;     // Superbee
+        default: f = R(0);
+        }
+        return f * den;
+    }
+    }
+}
+
+// MUSCL face values of the face between cells x2 and x3 (stencil x1..x4).
+template <typename R>
+__device__ __forceinline__ void muscl(int id, R x1, R x2, R x3, R x4, R& L, R& Rv)
+{
+    const R dc = x3 - x2;
+    L = x2 + R(0.5) * limited(id, dc, x2 - x1);
+    Rv = x3 - R(0.5) * limited(id, dc, x4 - x3);
+}
+
+template <typename R>
+__device__ __forceinline__ bool eligible(R eps, R xm, R x, R xp)
+{
+    return (x > eps) && (x < R(1) - eps) && ((x - xm) * (xp - x) > R(0));
+}
+
+// THINC (Eq. 3-3 for the left state of the face between the centre cell xc
+// and xn, from (xp, xc, xn); Eq. 3-4 is the same profile read at the
+// centre cell's other face).  jump normalised by max - min + gamma.
+template <typename R>
+__device__ __forceinline__ R thinc_side(const DevParams& P, R xa, R xc, R xb, bool left)
+{
+    const R mn = fmin(xa, xb), mx = fmax(xa, xb);
+    const R th = (xb >= xa) ? R(1) : R(-1);
+    const R gam = R(P.thinc_gamma);
+    const R F = (xc - mn + gam) / (mx - mn + gam);
+    const R E = (ex(th * R(P.beta) * (R(2) * F - R(1))) * R(P.icb) - R(1)) * R(P.itb);
+    const R tb = R(P.tb);
+    const R t = left ? (tb + E) / (R(1) + E * tb) : E;
+    return mn + R(0.5) * (mx - mn) * (R(1) + th * t);
+}
+
+// --------------------------------------------------------------- face flux
+// One face between cells 1 and 2 of the stencil w[0..3] (cells i-1..i+2 along
+// direction d).  ws[s][v]: primitives (u, p', T, Y); rc[s]: (rho, c) of the
+// cells for the App. D impedances; f: App. D switch (1 in plain mode).
+// F receives (rho, rho u_0.., rho E, rho Y..) fluxes.  In the mixed form the
+// constant p_ref is left out of the normal-momentum flux (it cancels in every
+// cell's flux difference).
+template <int ND, int NC, typename R>
+__device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*ws)[ND + NC + 1], const R* rho4,
+                                          const R* c4, int f, R* F)
+{
+    constexpr int NW = ND + NC + 1;
+    constexpr int IP = ND, IT = ND + 1, IY = ND + 2;
+    R WL[NW], WR[NW];
+    const bool smooth = P.iles && !f;
+    if (smooth) {
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            const R cval = (v < IY) ? (R(7) * (ws[1][v] + ws[2][v]) - ws[0][v] - ws[3][v]) * R(1.0 / 12.0)
+                                    : R(0.5) * (ws[1][v] + ws[2][v]);
+            WL[v] = WR[v] = cval;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < NW; ++v) {
+            const int lim = (v < ND) ? P.lim_vel : P.lim_scalar;
+            muscl(lim, ws[0][v], ws[1][v], ws[2][v], ws[3][v], WL[v], WR[v]);
+            if (v >= IY && P.thinc) {
+                const R eps = R(P.thinc_eps);
+                if (eligible(eps, ws[0][v], ws[1][v], ws[2][v])) WL[v] = thinc_side(P, ws[0][v], ws[1][v], ws[2][v], true);
+                if (eligible(eps, ws[1][v], ws[2][v], ws[3][v])) WR[v] = thinc_side(P, ws[1][v], ws[2][v], ws[3][v], false);
+            }
+        }
+    }
+    R rL, eL, cL, rR, eR, cR;
+    bool ok = tdu<NC, R>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
+    ok = tdu<NC, R>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
+    const R pL = WL[IP], pR = WR[IP], uL = WL[d], uR = WR[d];
+    R us, ps;
+    if (P.iles) {
+        const R cm = fmax(c4[1], c4[2]);
+        const R IL = (R(3) * rho4[1] + rho4[2]) * cm * R(0.25);
+        const R IR = (rho4[1] + R(3) * rho4[2]) * cm * R(0.25);
+        if (f) {
+            us = (IL * uL + IR * uR + pL - pR) / (IL + IR);
+            ps = R(0.5) * (pL + pR);
+        } else {
+            const R d3 = R(P.d3p_coef) * (ws[0][IP] - R(3) * ws[1][IP] + R(3) * ws[2][IP] - ws[3][IP]);
+            us = uL - d3 / (IL + IR);
+            ps = pL;
+        }
+    } else {
+        ps = R(0.5) * (pL + pR);
+        const R zL = rL * cL, zR = rR * cR;
+        us = (zL * uL + zR * uR + pL - pR) / (zL + zR);
+    }
+    const bool up = us >= R(0);
+    const R* Ws = up ? WL : WR;
+    const R rs = up ? rL : rR;
+    const R es = up ? eL : eR;
+    R ke = R(0);
+#pragma unroll
+    for (int a = 0; a < ND; ++a) ke += R(0.5) * Ws[a] * Ws[a];
+    const R mflux = us * rs;
+    F[0] = mflux;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) F[1 + a] = mflux * Ws[a] + (a == d ? ps : R(0));
+    F[1 + ND] = mflux * (es + ke) + (R(P.p_ref) + ps) * us;
+#pragma unroll
+    for (int k = 0; k < NC - 1; ++k) F[2 + ND + k] = mflux * Ws[IY + k];
+    return ok;
+}
+
+}  // namespace tfv

@@ -1,0 +1,438 @@
+// fv_kernels.cuh -- the CUDA kernels of one low-storage Runge-Kutta stage.
+//
+//   prim_kernel   boundary update + primitive/thermodynamic update
+//                 (Algorithm 1, last two lines) over each case's ghosted box,
+//                 optionally with the per-case CFL maximum (warp shuffles,
+//                 then one atomicMax per block).
+//   stage_kernel  one fused pass per tile: halo tile of primitives in shared
+//                 memory, App. D sensor, reconstruction + TDU + all-Mach flux
+//                 for every face of the tile (all directions), CSF source,
+//                 flux divergence and the LSRK register update in FP64.
+// Both walk a work list of (case, tile origin) items so one launch serves a
+// single grid or a batch of uneven cases.
+#pragma once
+
+#include "fv_device.cuh"
+
+namespace tfv {
+
+struct PrimArgs {
+    DevParams P;
+    const CaseDesc* cases;
+    const int4* items;
+    int nitems;
+    const double* q;          // conserved register read (field stride P.ntot_q)
+    void* prim;               // R[nprim][ntot_p]
+    const double* in_u;       // inflow velocities (device) or null
+    unsigned long long* smax; // per-case max wave speed bits, or null
+    int* err;
+};
+
+struct StageArgs {
+    DevParams P;
+    const CaseDesc* cases;
+    const int4* items;
+    int nitems;
+    const void* prim;
+    const double* q0;
+    double* qout;
+    const double* dt;         // per-case dt
+    double a;                 // LSRK coefficient a_k
+    int* err;
+};
+
+template <int ND> struct TileShape;
+template <> struct TileShape<2> { static constexpr int X = 32, Y = 8, Z = 1; };
+template <> struct TileShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
+
+__device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& flip, int& inflow)
+{
+    flip = 0;
+    inflow = 0;
+    if (i >= 0 && i < n) return i;
+    if (i < 0) {
+        int s = -1 - i;
+        if (s > n - 1) s = n - 1;
+        if (bclo == 0) return ((i % n) + n) % n;
+        if (bclo == 1) { flip = 1; return s; }
+        if (bclo == 3) { inflow = 1; return s; }
+        return 0;
+    }
+    int s = 2 * n - 1 - i;
+    if (s < 0) s = 0;
+    if (bchi == 0) return i % n;
+    if (bchi == 1) { flip = 1; return s; }
+    return n - 1;
+}
+
+__device__ __forceinline__ void set_err(int* err, int bit)
+{
+    if (err) atomicOr(err, bit);
+}
+
+// ----------------------------------------------------------------- prims
+template <int ND, int NC, typename R>
+__global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
+{
+    constexpr int NV = ND + NC + 1;
+    using TS = TileShape<ND>;
+    const DevParams& P = A.P;
+    R* prim = static_cast<R*>(A.prim);
+    const int tx = threadIdx.x % TS::X, ty = (threadIdx.x / TS::X) % TS::Y, tz = threadIdx.x / (TS::X * TS::Y);
+    __shared__ double wmax[8];
+    for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+        const int4 wi = A.items[it];
+        const CaseDesc& C = A.cases[wi.x];
+        const int gc[3] = {wi.y + tx, wi.z + ty, wi.w + tz};   // ghosted coordinates
+        double speed = 0.0;
+        const bool valid = gc[0] < C.g[0] && gc[1] < C.g[1] && gc[2] < C.g[2];
+        if (valid) {
+            int src[3], flip[3], infl[3];
+            bool interior = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d < ND) {
+                    const int i = gc[d] - 2;
+                    interior = interior && i >= 0 && i < C.n[d];
+                    src[d] = map_index(C.n[d], i, C.bc[d][0], C.bc[d][1], flip[d], infl[d]);
+                } else {
+                    src[d] = 0; flip[d] = 0; infl[d] = 0;
+                }
+            }
+            bool in_disc = false;
+            if (infl[0]) {
+                const double y = (src[1] + 0.5) * C.dx[1] - C.in_yc;
+                const double z = ND == 3 ? (src[2] + 0.5) * C.dx[2] - C.in_zc : 0.0;
+                if (y * y + z * z <= C.in_r2) { in_disc = true; src[0] = 0; flip[0] = 0; }
+                else flip[0] = 1;
+            }
+            const long long sc = C.qoff + ((long long)src[2] * C.n[1] + src[1]) * C.n[0] + src[0];
+            double qc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) qc[v] = A.q[v * P.ntot_q + sc];
+            R w[NV], T, pabs;
+            double rho;
+            bool ok = prim_recover<ND, NC, R>(P, qc, w, rho, T, pabs);
+#pragma unroll
+            for (int d = 0; d < ND; ++d) if (flip[d]) w[d] = -w[d];
+            if (in_disc) {
+                const long long fc = (long long)src[2] * C.n[1] + src[1];
+                const long long fn = (long long)C.n[1] * C.n[2];
+#pragma unroll
+                for (int a = 0; a < ND; ++a) w[a] = R(C.in_uoff >= 0 ? A.in_u[C.in_uoff + a * fn + fc] : C.in_u0[a]);
+                w[ND + 1] = R(C.in_T);
+#pragma unroll
+                for (int k = 0; k < NC - 1; ++k) w[ND + 2 + k] = R(C.in_Y[k]);
+            }
+            R rr = R(rho), cs = R(0);
+            const bool need_c = P.aux_rc || A.smax || in_disc;
+            if (need_c) {
+                R e;
+                ok = tdu<NC, R>(P, w[ND], w[ND + 1], w + ND + 2, rr, e, cs) && ok;
+                if (!in_disc) rr = R(rho);
+            }
+            if (!ok) set_err(A.err, ERR_NONPHYS);
+            const long long pc = C.poff + ((long long)gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) prim[v * P.ntot_p + pc] = w[v];
+            if (P.aux_rc) {
+                prim[P.i_rho * P.ntot_p + pc] = rr;
+                prim[P.i_c * P.ntot_p + pc] = cs;
+            }
+            if (P.aux_al) {
+                // liquid volume fraction alpha_l = rho Y_l (gamma_l - 1) cv_l T / (p + pinf_l)  (Eq. A.1.4)
+                R s = R(0);
+#pragma unroll
+                for (int k = 0; k < NC - 1; ++k) s += clip01(w[ND + 2 + k]);
+                const int L = P.liquid;
+                const R Yl = (L == NC - 1) ? clip01(R(1) - s) : clip01(w[ND + 2 + L]);
+                const R al = rr * Yl * R(P.c[L].gm1cv) * w[ND + 1] / (R(P.Pk[L]) + w[ND]);
+                prim[P.i_al * P.ntot_p + pc] = al;
+            }
+            if (A.smax && interior) {
+                R s = R(0);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) s += (fabs(w[d]) + cs) * R(C.idx[d]);
+                speed = double(s);
+            }
+        }
+        if (A.smax) {
+            // block maximum, one atomic per block and case
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) speed = fmax(speed, __shfl_xor_sync(0xffffffffu, speed, o));
+            if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = speed;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double m = 0.0;
+                for (int i = 0; i < 8; ++i) m = fmax(m, wmax[i]);
+                // positive doubles order like their bit patterns
+                atomicMax(A.smax + wi.x, (unsigned long long)__double_as_longlong(m));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------------ stage
+template <int ND, int NC, typename R>
+__global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
+{
+    constexpr int NV = ND + NC + 1;
+    using TS = TileShape<ND>;
+    constexpr int TX = TS::X, TY = TS::Y, TZ = TS::Z;
+    constexpr int NT = TX * TY * TZ;
+    constexpr int HX = TX + 4, HY = TY + 4, HZ = (ND == 3) ? TZ + 4 : 1;
+    constexpr int HC = HX * HY * HZ;
+    constexpr int SX = 1, SY = HX, SZ = HX * HY;
+    const DevParams& P = A.P;
+    const R* prim = static_cast<const R*>(A.prim);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sp = reinterpret_cast<R*>(smem_raw);                 // [nprim][HC]
+    R* sf[3];                                               // fluxes per direction [NV][faces]
+    constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
+    sf[0] = sp + P.nprim * HC;
+    sf[1] = sf[0] + NV * NFX;
+    sf[2] = sf[1] + NV * NFY;
+    R* extra = sf[ND - 1] + NV * (ND == 2 ? NFY : NFZ);
+    // CSF scratch: smoothed alpha on the tile +1 halo and vertex normals
+    constexpr int AX = TX + 2, AY = TY + 2, AZ = (ND == 3) ? TZ + 2 : 1;
+    constexpr int VX = TX + 1, VY = TY + 1, VZ = (ND == 3) ? TZ + 1 : 1;
+    R* sa = extra;                        // [AZ][AY][AX]
+    R* sn = sa + AX * AY * AZ;            // [ND][VZ][VY][VX]
+    unsigned char* sflag = reinterpret_cast<unsigned char*>(sn + ND * VX * VY * VZ);  // [HC]
+
+    const int tid = threadIdx.x;
+    for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+        const int4 wi = A.items[it];
+        const CaseDesc& C = A.cases[wi.x];
+        const int x0 = wi.y, y0 = wi.z, z0 = wi.w;
+        const int vx = min(TX, C.n[0] - x0), vy = min(TY, C.n[1] - y0), vz = (ND == 3) ? min(TZ, C.n[2] - z0) : 1;
+        // ---- halo tile of primitives (ghosted coordinates x0 .. x0+HX-1)
+        for (int h = tid; h < HC; h += NT) {
+            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+            const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
+            const bool ok = gx < C.g[0] && gy < C.g[1] && gz < C.g[2];
+            const long long pc = C.poff + ((long long)gz * C.g[1] + gy) * C.g[0] + gx;
+            for (int v = 0; v < P.nprim; ++v) sp[v * HC + h] = ok ? prim[v * P.ntot_p + pc] : R(0);
+        }
+        __syncthreads();
+        // ---- App. D cell sensor on the tile + 1 halo
+        if (P.iles) {
+            for (int h = tid; h < HC; h += NT) {
+                const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+                unsigned char fl = 0;
+                const bool in = hx >= 1 && hx <= vx + 2 && hy >= 1 && hy <= vy + 2 &&
+                                (ND == 2 || (hz >= 1 && hz <= vz + 2));
+                if (in) {
+                    R g[3][3];
+                    R tg = R(0);
+                    const R ag0 = R(1) - sp[P.i_al * HC + h];
+                    const int st[3] = {SX, SY, SZ};
+#pragma unroll
+                    for (int bd = 0; bd < ND; ++bd) {
+                        const int hp = h + st[bd], hm = h - st[bd];
+                        const R inv2dx = R(0.5 * C.idx[bd]);
+#pragma unroll
+                        for (int a = 0; a < ND; ++a) g[a][bd] = (sp[a * HC + hp] - sp[a * HC + hm]) * inv2dx;
+                        tg += fabs(ag0 - (R(1) - sp[P.i_al * HC + hm])) + fabs((R(1) - sp[P.i_al * HC + hp]) - ag0);
+                    }
+                    R div = R(0);
+#pragma unroll
+                    for (int a = 0; a < ND; ++a) div += g[a][a];
+                    R curl2;
+                    if (ND == 3) {
+                        const R wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
+                        curl2 = wx * wx + wy * wy + wz * wz;
+                    } else {
+                        const R wz = g[1][0] - g[0][1];
+                        curl2 = wz * wz;
+                    }
+                    const R d2 = div * div;
+                    const R thD = d2 / (d2 + curl2 + R(P.eps_ducros));
+                    fl = (thD > R(P.thr_ducros) || tg > R(P.thr_gas)) ? 1 : 0;
+                }
+                sflag[h] = fl;
+            }
+        }
+        // ---- CSF: smoothed alpha (Eq. 3-9) on tile + 1 halo
+        if (P.csf) {
+            for (int h = tid; h < AX * AY * AZ; h += NT) {
+                const int ax = h % AX, ay = (h / AX) % AY, az = h / (AX * AY);
+                const int hc = (ax + 1) * SX + (ay + 1) * SY + (ND == 3 ? (az + 1) * SZ : 0);
+                const R* al = sp + P.i_al * HC;
+                R s = R(0);
+                if (ND == 2) {
+#pragma unroll
+                    for (int b = -1; b <= 1; ++b) {
+                        const R wb = (b == 0) ? R(2) : R(1);
+                        s += wb * (al[hc + b * SY - 1] + R(2) * al[hc + b * SY] + al[hc + b * SY + 1]);
+                    }
+                    s *= R(1.0 / 16.0);
+                } else {
+#pragma unroll
+                    for (int c = -1; c <= 1; ++c) {
+                        const R wc = (c == 0) ? R(2) : R(1);
+#pragma unroll
+                        for (int b = -1; b <= 1; ++b) {
+                            const R wb = (b == 0) ? R(2) : R(1);
+                            const int o = hc + c * SZ + b * SY;
+                            s += wc * wb * (al[o - 1] + R(2) * al[o] + al[o + 1]);
+                        }
+                    }
+                    s *= R(1.0 / 64.0);
+                }
+                sa[h] = s;
+            }
+        }
+        __syncthreads();
+        // ---- faces of all directions
+        const int nfx = (vx + 1) * vy * vz, nfy = vx * (vy + 1) * vz, nfz = (ND == 3) ? vx * vy * (vz + 1) : 0;
+        const int nf_total = nfx + nfy + nfz;
+        for (int f = tid; f < nf_total; f += NT) {
+            int d, fx, fy, fz, lx, ly;
+            if (f < nfx) { d = 0; lx = vx + 1; ly = vy; fx = f % lx; fy = (f / lx) % ly; fz = f / (lx * ly); }
+            else if (f < nfx + nfy) { const int g = f - nfx; d = 1; lx = vx; ly = vy + 1; fx = g % lx; fy = (g / lx) % ly; fz = g / (lx * ly); }
+            else { const int g = f - nfx - nfy; d = 2; lx = vx; ly = vy; fx = g % lx; fy = (g / lx) % ly; fz = g / (lx * ly); }
+            // cell i-1 of the stencil in halo coordinates
+            int hx = fx + 2, hy = fy + 2, hz = (ND == 3) ? fz + 2 : 0;
+            int st;
+            if (d == 0) { hx -= 2; st = SX; } else if (d == 1) { hy -= 2; st = SY; } else { hz -= 2; st = SZ; }
+            const int h0 = hx * SX + hy * SY + hz * SZ;
+            R ws[4][NV];
+            R r4[4], c4[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) ws[s][v] = sp[v * HC + h0 + s * st];
+            }
+            int fl = 1;
+            if (P.iles) {
+#pragma unroll
+                for (int s = 1; s <= 2; ++s) {
+                    r4[s] = sp[P.i_rho * HC + h0 + s * st];
+                    c4[s] = sp[P.i_c * HC + h0 + s * st];
+                }
+                fl = (sflag[h0 + st] | sflag[h0 + 2 * st]) ? 1 : 0;
+            }
+            R F[NV];
+            const bool ok = face_flux<ND, NC, R>(P, d, ws, r4, c4, fl, F);
+            if (!ok) set_err(A.err, ERR_NONPHYS);
+            // store at face index (fx, fy, fz) of the full tile face array
+            int fi;
+            if (d == 0) fi = (fz * TY + fy) * (TX + 1) + fx;
+            else if (d == 1) fi = (fz * (TY + 1) + fy) * TX + fx;
+            else fi = (fz * TY + fy) * TX + fx;
+            const int nfd = d == 0 ? NFX : (d == 1 ? NFY : NFZ);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sf[d][v * nfd + fi] = F[v];
+        }
+        // ---- CSF vertex normals from the smoothed alpha (Fig. 3.3)
+        if (P.csf) {
+            R dxmin = R(C.dx[0]);
+#pragma unroll
+            for (int d = 1; d < ND; ++d) dxmin = fmin(dxmin, R(C.dx[d]));
+            const R gthr = R(P.grad_eps) / dxmin;
+            for (int h = tid; h < VX * VY * VZ; h += NT) {
+                const int ix = h % VX, iy = (h / VX) % VY, iz = h / (VX * VY);
+                // vertex between smoothed cells (ix-1+1 .. ix+1) in sa coordinates: cells ix, ix+1
+                R g[3] = {R(0), R(0), R(0)};
+                const int nc = 1 << ND;
+#pragma unroll
+                for (int cc = 0; cc < (1 << ND); ++cc) {
+                    const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
+                    const R a = sa[((ND == 3 ? iz + bz : 0) * AY + iy + by) * AX + ix + bx];
+                    g[0] += bx ? a : -a;
+                    g[1] += by ? a : -a;
+                    if (ND == 3) g[2] += bz ? a : -a;
+                }
+                R mag2 = R(0);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) { g[d] *= R(C.idx[d]) * R(2.0 / nc); mag2 += g[d] * g[d]; }
+                const R mag = sq_rt(mag2);
+                const R inv = (mag > gthr) ? R(1) / mag : R(0);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) sn[(d * VZ + iz) * VY * VX + iy * VX + ix] = g[d] * inv;
+            }
+        }
+        __syncthreads();
+        // ---- divergence, CSF source, LSRK update (FP64 registers)
+        {
+            const int cx = tid % TX, cy = (tid / TX) % TY, cz = tid / (TX * TY);
+            if (cx < vx && cy < vy && cz < vz) {
+                R S[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) S[v] = R(0);
+                if (P.csf) {
+                    R kappa = R(0);
+                    R ga[3] = {R(0), R(0), R(0)};
+                    const int nc = 1 << ND;
+                    const R* al = sp + P.i_al * HC;
+                    const int hc = (cx + 2) * SX + (cy + 2) * SY + (ND == 3 ? (cz + 2) * SZ : 0);
+#pragma unroll
+                    for (int vtx = 0; vtx < (1 << ND); ++vtx) {
+                        const int ox = vtx & 1, oy = (vtx >> 1) & 1, oz = (vtx >> 2) & 1;
+                        const int vi = ((ND == 3 ? cz + oz : 0) * VY + cy + oy) * VX + cx + ox;
+                        R gu[3] = {R(0), R(0), R(0)};
+#pragma unroll
+                        for (int cc = 0; cc < (1 << ND); ++cc) {
+                            const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
+                            const int o = hc + (ox - 1 + bx) * SX + (oy - 1 + by) * SY + (ND == 3 ? (oz - 1 + bz) * SZ : 0);
+                            const R a = al[o];
+                            gu[0] += bx ? a : -a;
+                            gu[1] += by ? a : -a;
+                            if (ND == 3) gu[2] += bz ? a : -a;
+                        }
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) {
+                            const R nd_ = sn[(d * VZ + (ND == 3 ? cz + oz : 0)) * VY * VX + (cy + oy) * VX + cx + ox];
+                            const int od = d == 0 ? ox : (d == 1 ? oy : oz);
+                            kappa -= (od ? nd_ : -nd_) * R(C.idx[d]) * R(2.0 / nc);
+                            ga[d] += gu[d] * R(C.idx[d]) * R(2.0 / nc);
+                        }
+                        (void)vi;
+                    }
+                    R udg = R(0);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        ga[d] *= R(1.0 / nc);
+                        S[1 + d] = R(P.sigma) * kappa * ga[d];
+                        udg += sp[d * HC + hc] * ga[d];
+                    }
+                    S[1 + ND] = R(P.sigma) * kappa * udg;
+                }
+                const long long gcell = C.qoff + ((long long)(z0 + cz) * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx);
+                const double adt = A.a * A.dt[wi.x];
+                const int fxl = (cz * TY + cy) * (TX + 1) + cx;
+                const int fyl = (cz * (TY + 1) + cy) * TX + cx;
+                const int fzl = (cz * TY + cy) * TX + cx;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    R div = (sf[0][v * NFX + fxl + 1] - sf[0][v * NFX + fxl]) * R(C.idx[0]);
+                    div += (sf[1][v * NFY + fyl + TX] - sf[1][v * NFY + fyl]) * R(C.idx[1]);
+                    if (ND == 3) div += (sf[2][v * NFZ + fzl + TX * TY] - sf[2][v * NFZ + fzl]) * R(C.idx[2]);
+                    const R Rv = S[v] - div;
+                    A.qout[v * P.ntot_q + gcell] = A.q0[v * P.ntot_q + gcell] + adt * double(Rv);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// dynamic shared memory of stage_kernel
+template <int ND, int NC, typename R>
+inline size_t stage_smem_bytes(int nprim)
+{
+    constexpr int NV = ND + NC + 1;
+    using TS = TileShape<ND>;
+    constexpr int TX = TS::X, TY = TS::Y, TZ = TS::Z;
+    constexpr int HC = (TX + 4) * (TY + 4) * ((ND == 3) ? TZ + 4 : 1);
+    constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
+    constexpr int AC = (TX + 2) * (TY + 2) * ((ND == 3) ? TZ + 2 : 1);
+    constexpr int VC = (TX + 1) * (TY + 1) * ((ND == 3) ? TZ + 1 : 1);
+    size_t n = (size_t)nprim * HC + (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC + ND * VC;
+    return n * sizeof(R) + HC + 16;
+}
+
+}  // namespace tfv

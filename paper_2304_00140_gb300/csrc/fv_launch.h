@@ -1,0 +1,39 @@
+// fv_launch.h -- host-side launchers of the templated kernels (one
+// translation unit per kernel family so the build compiles them in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fv_kernels.cuh"
+
+namespace tfv {
+
+// prim kernel and stage kernel, dispatched on (ndim, ncomp, mixed)
+cudaError_t launch_prim(int nd, int nc, int mixed, const PrimArgs& A, int grid, cudaStream_t s);
+cudaError_t launch_stage(int nd, int nc, int mixed, const StageArgs& A, int grid, size_t smem, cudaStream_t s);
+size_t stage_smem(int nd, int nc, int mixed, int nprim);
+cudaError_t stage_set_smem(int nd, int nc, int mixed, size_t smem);
+int stage_occupancy(int nd, int nc, int mixed, size_t smem);   // resident blocks per SM
+int prim_occupancy(int nd, int nc, int mixed);
+
+// state I/O and diagnostics (FP64)
+struct IoArgs {
+    DevParams P;
+    const CaseDesc* cases;
+    int icase;
+    long long ncell;            // interior cells of the case
+    const double* in;           // [nv][ncell] (primitive or conserved), case-local
+    double* out;                // [nv][ntot_q] register or [nv][ncell] case-local
+    int* err;
+};
+cudaError_t launch_prim_to_cons(int nd, int nc, const IoArgs& A, cudaStream_t s);
+cudaError_t launch_cons_to_prim(int nd, int nc, const IoArgs& A, cudaStream_t s);
+// per-block Kahan partial sums of each field of one case: partial[nv][nblk]
+cudaError_t launch_totals(int nv, const double* q, long long ntot_q, long long off, long long ncell,
+                          double* partial, int nblk, cudaStream_t s);
+// dt[c] = cfl / smax[c]; t[c] += dt[c]; smax[c] = 0   (per case)
+cudaError_t launch_dt(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err,
+                      cudaStream_t s);
+cudaError_t launch_fill(double* x, int n, double v, cudaStream_t s);
+
+}  // namespace tfv

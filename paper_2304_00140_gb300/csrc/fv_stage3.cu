@@ -1,0 +1,53 @@
+// fv_stage3.cu -- 3D instantiations of the stage kernel.
+#include "fv_launch.h"
+
+namespace tfv {
+
+template <int NC, typename R>
+static cudaError_t go3(const StageArgs& A, int grid, size_t smem, cudaStream_t s)
+{
+    stage_kernel<3, NC, R><<<grid, 256, smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <int NC, typename R>
+static cudaError_t attr3(size_t smem)
+{
+    return cudaFuncSetAttribute(stage_kernel<3, NC, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_stage3(int nc, int mixed, const StageArgs& A, int grid, size_t smem, cudaStream_t s)
+{
+    if (nc == 2) return mixed ? go3<2, float>(A, grid, smem, s) : go3<2, double>(A, grid, smem, s);
+    if (nc == 3) return mixed ? go3<3, float>(A, grid, smem, s) : go3<3, double>(A, grid, smem, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t set_smem3(int nc, int mixed, size_t smem)
+{
+    if (nc == 2) return mixed ? attr3<2, float>(smem) : attr3<2, double>(smem);
+    if (nc == 3) return mixed ? attr3<3, float>(smem) : attr3<3, double>(smem);
+    return cudaErrorInvalidValue;
+}
+
+size_t smem3(int nc, int mixed, int nprim)
+{
+    if (nc == 2) return mixed ? stage_smem_bytes<3, 2, float>(nprim) : stage_smem_bytes<3, 2, double>(nprim);
+    return mixed ? stage_smem_bytes<3, 3, float>(nprim) : stage_smem_bytes<3, 3, double>(nprim);
+}
+
+template <int NC, typename R>
+static int occ3(size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<3, NC, R>, 256, smem) != cudaSuccess) return 1;
+    return n < 1 ? 1 : n;
+}
+
+int occupancy3(int nc, int mixed, size_t smem)
+{
+    if (nc == 2) return mixed ? occ3<2, float>(smem) : occ3<2, double>(smem);
+    return mixed ? occ3<3, float>(smem) : occ3<3, double>(smem);
+}
+
+}  // namespace tfv

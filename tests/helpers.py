@@ -1,0 +1,47 @@
+"""Shared helpers of the tests: building contexts and comparing fields."""
+import numpy as np
+
+import oracle
+
+LSRK_STAGES = (1, 2, 3, 4)
+
+
+def rel_field_diff(a, b):
+    """max |a - b| / max |b| per field (first axis)."""
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    scale = np.maximum(np.abs(b).max(axis=1), 1e-300)
+    return np.abs(a - b).max(axis=1) / scale
+
+
+def rel_l1(a, b):
+    a = np.asarray(a).reshape(a.shape[0], -1)
+    b = np.asarray(b).reshape(b.shape[0], -1)
+    return np.abs(a - b).sum(axis=1) / np.maximum(np.abs(b).sum(axis=1), 1e-300)
+
+
+def oracle_step_dt(o, q, dt):
+    """one full LSRK step of the oracle with a given dt"""
+    q0 = np.ascontiguousarray(q)
+    qa = o.stage(1, dt, q0, q0)
+    qb = o.stage(2, dt, q0, qa)
+    qa = o.stage(3, dt, q0, qb)
+    return o.stage(4, dt, q0, qa)
+
+
+def oracle_step_window(o, q, dt, lo, hi):
+    """one LSRK step of the oracle on the window [lo, hi) only: stage k is
+    evaluated on the window grown by 2 (4 - k) cells (clipped to the domain),
+    which is all that stage k + 1 reads.  Returns the full array with the
+    window filled in."""
+    w = o.w
+    q0 = np.ascontiguousarray(q)
+    prev = q0
+    for k in LSRK_STAGES:
+        g = 2 * (4 - k)
+        wl_ = [max(0, lo[d] - g) if d < w.ndim else 0 for d in range(3)]
+        wh_ = [min(w.n[d], hi[d] + g) if d < w.ndim else 1 for d in range(3)]
+        out = q0.copy()
+        o.stage(k, dt, q0, prev, window=(wl_, wh_), out=out)
+        prev = out
+    return prev
