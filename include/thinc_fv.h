@@ -174,6 +174,33 @@ fv_status fv_profile_read(fv_ctx* ctx, double* out);
 const char* fv_last_error(const fv_ctx* ctx);
 const char* fv_status_string(int status);
 
+/* One Runge-Kutta stage of one grid that allocates no device memory, for
+ * callers that cannot call cudaMalloc: code that runs inside a host
+ * application owning the whole device through its own memory pool, code
+ * with a fixed memory budget set before it starts, or code on a path where
+ * an allocation (and the synchronisation it can imply) is not allowed.  The
+ * paper has no counterpart; it is the fv_rk_stage arithmetic on the same
+ * kernels with the scratch held in a static device array of
+ * FV_NOALLOC_SCRATCH_BYTES per GPU, kept from library load until exit.
+ *
+ * q0 (the step's initial state), qprev (stage k-1's output; q0 for k = 1) and
+ * qout are caller-owned device arrays in the conserved layout above; qout
+ * receives q0 + a_k dt R(qprev).  qout may alias q0 (as stage 4 does) but not
+ * qprev.  Limit: the primitive scratch of (n+4)^d ghosted cells times
+ * (ndim + ncomp + 1 + extra fields) values of 8 bytes (FV_FP64) or 4 bytes
+ * (FV_MIXED), plus small work lists, must fit the array; larger grids, a
+ * per-cell inflow array (grid->in_u) and every argument error return
+ * FV_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call uses the same array: calls that
+ * overlap on the GPU (other streams, other threads) race.  The call runs on
+ * `stream` and returns once the stage has finished, reporting a non-physical
+ * state met by the kernels as FV_ERR_NONPHYSICAL. */
+#define FV_NOALLOC_SCRATCH_BYTES (48u << 20)
+fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_components* comps, const fv_eos* eos,
+                              int k, double dt, const double* q0, const double* qprev, double* qout,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -725,3 +725,155 @@ extern "C" const char* fv_status_string(int s)
     default: return "unknown status";
     }
 }
+
+// --------------------------------------------------------------------------
+// fv_rk_stage_noalloc: one stage of one grid for callers that cannot allocate
+// device memory.  Its scratch (case descriptor, dt, error word, tile work
+// lists, primitive fields) lives in the file-scope array below, which every
+// GPU that loads the library keeps until the process exits.  Host code must
+// not hand g_noalloc_scratch to a kernel directly: in host code that name is
+// a host-side stand-in, so its device address is looked up per device with
+// cudaGetSymbolAddress.
+// --------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FV_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+__global__ void noalloc_setup_kernel(CaseDesc C, CaseDesc* dcase, double* dt, double dtv, int* err, int4* ist,
+                                     int n_st, int4* ipr, int n_pr, int tx, int ty, int tz)
+{
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0) {
+        *dcase = C;
+        *dt = dtv;
+        *err = 0;
+    }
+    // tile origins in the same x-fastest order as the context work lists
+    const int sx = (C.n[0] + tx - 1) / tx, sy = (C.n[1] + ty - 1) / ty;
+    for (int i = i0; i < n_st; i += gridDim.x * blockDim.x)
+        ist[i] = make_int4(0, (i % sx) * tx, ((i / sx) % sy) * ty, (i / (sx * sy)) * tz);
+    const int px = (C.g[0] + tx - 1) / tx, py = (C.g[1] + ty - 1) / ty;
+    for (int i = i0; i < n_pr; i += gridDim.x * blockDim.x)
+        ipr[i] = make_int4(0, (i % px) * tx, ((i / px) % py) * ty, (i / (px * py)) * tz);
+}
+
+// argument checks of the no-alloc path (no strings, nothing allocated)
+bool noalloc_args_ok(const fv_grid* g, const fv_components* cm, const fv_eos* e)
+{
+    if (!g || !cm || !e) return false;
+    const int nd = g->ndim;
+    if (nd != 2 && nd != 3) return false;
+    for (int d = 0; d < 3; ++d) {
+        if (g->n[d] < 1 || (d >= nd && g->n[d] != 1)) return false;
+        if (d < nd) {
+            if (!(g->hi[d] > g->lo[d])) return false;
+            for (int s = 0; s < 2; ++s)
+                if (g->bc[d][s] < 0 || g->bc[d][s] > 3) return false;
+            if ((g->bc[d][0] == FV_BC_PERIODIC) != (g->bc[d][1] == FV_BC_PERIODIC)) return false;
+            if ((d > 0 && g->bc[d][0] == FV_BC_INFLOW) || g->bc[d][1] == FV_BC_INFLOW) return false;
+        }
+    }
+    if (g->in_u) return false;   // per-cell inflow velocities would need device memory
+    if (cm->ncomp < 2 || cm->ncomp > 3 || cm->liquid < 0 || cm->liquid >= cm->ncomp) return false;
+    double pa = -1.0, pb = -1.0;
+    for (int k = 0; k < cm->ncomp; ++k) {
+        const fv_component& c = cm->comp[k];
+        if (c.kind != FV_SG || !(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) return false;
+        if (pa < 0.0 || c.pinf == pa) pa = c.pinf;
+        else if (pb < 0.0 || c.pinf == pb) pb = c.pinf;
+        else return false;
+    }
+    if (e->lim_vel < 0 || e->lim_vel > 6 || e->lim_scalar < 0 || e->lim_scalar > 6) return false;
+    if (e->precision != FV_FP64 && e->precision != FV_MIXED) return false;
+    if (e->thinc && !(e->beta > 0.0)) return false;
+    return e->sigma >= 0.0;
+}
+
+}  // namespace
+
+extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_components* comps, const fv_eos* eos,
+                                         int k, double dt, const double* q0, const double* qprev, double* qout,
+                                         void* stream)
+{
+    if (!noalloc_args_ok(grid, comps, eos) || k < 1 || k > 4 || !(dt > 0.0) || !q0 || !qprev || !qout)
+        return FV_ERR_ARG;
+    // per-device set-up: the device address of the scratch array
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return FV_ERR_CUDA;
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FV_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    fv_ctx x;   // parameters only: nothing below allocates
+    x.nd = grid->ndim;
+    x.nc = comps->ncomp;
+    x.nv = x.nd + x.nc + 1;
+    x.mixed = eos->precision == FV_MIXED;
+    build_params(&x, comps, eos);
+    CaseDesc C{};
+    for (int d = 0; d < 3; ++d) {
+        C.n[d] = grid->n[d];
+        C.g[d] = d < x.nd ? grid->n[d] + 4 : 1;
+        C.dx[d] = d < x.nd ? (grid->hi[d] - grid->lo[d]) / grid->n[d] : 1.0;
+        C.idx[d] = 1.0 / C.dx[d];
+        C.bc[d][0] = d < x.nd ? grid->bc[d][0] : 0;
+        C.bc[d][1] = d < x.nd ? grid->bc[d][1] : 0;
+    }
+    C.inflow = grid->bc[0][0] == FV_BC_INFLOW;
+    C.in_yc = grid->in_yc - grid->lo[1];
+    C.in_zc = grid->in_zc - grid->lo[2];
+    C.in_r2 = grid->in_radius * grid->in_radius;
+    C.in_T = grid->in_T;
+    for (int d = 0; d < 3; ++d) C.in_u0[d] = grid->in_u0[d];
+    for (int c = 0; c < FV_MAX_COMP && c < MAXC; ++c) C.in_Y[c] = grid->in_Y[c];
+    C.in_uoff = -1;
+    const long long ncell = (long long)C.n[0] * C.n[1] * C.n[2];
+    const long long nghost = (long long)C.g[0] * C.g[1] * C.g[2];
+    x.P.ntot_q = ncell;
+    x.P.ntot_p = nghost;
+    const int tx = tile_x(x.nd), ty = tile_y(x.nd), tz = tile_z(x.nd);
+    const long long n_st = ntiles(C.n, x.nd), n_pr = ntiles(C.g, x.nd);
+    // scratch layout
+    const size_t o_case = 0, o_dt = align256(sizeof(CaseDesc)), o_err = o_dt + 256, o_ist = o_err + 256;
+    const size_t o_ipr = o_ist + align256(sizeof(int4) * n_st);
+    const size_t o_prim = o_ipr + align256(sizeof(int4) * n_pr);
+    const size_t rsz = x.mixed ? sizeof(float) : sizeof(double);
+    const size_t need = o_prim + rsz * (size_t)x.nprim * (size_t)nghost;
+    if (need > (size_t)FV_NOALLOC_SCRATCH_BYTES) return FV_ERR_ARG;
+
+    CaseDesc* dcase = reinterpret_cast<CaseDesc*>(base + o_case);
+    double* ddt = reinterpret_cast<double*>(base + o_dt);
+    int* derr = reinterpret_cast<int*>(base + o_err);
+    int4* ist = reinterpret_cast<int4*>(base + o_ist);
+    int4* ipr = reinterpret_cast<int4*>(base + o_ipr);
+    void* prim = base + o_prim;
+
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FV_ERR_CUDA;
+    const size_t smem = stage_smem(x.nd, x.nc, x.mixed, x.nprim);
+    if (stage_set_smem(x.nd, x.nc, x.mixed, smem) != cudaSuccess) return FV_ERR_CUDA;
+    const int gs = (int)std::min<long long>(n_st, (long long)nsm * stage_occupancy(x.nd, x.nc, x.mixed, smem));
+    const int gp = (int)std::min<long long>(n_pr, (long long)nsm * prim_occupancy(x.nd, x.nc, x.mixed));
+    const int nsetup = (int)std::min<long long>(1024, (std::max(n_st, n_pr) + 255) / 256);
+
+    noalloc_setup_kernel<<<std::max(1, nsetup), 256, 0, s>>>(C, dcase, ddt, dt, derr, ist, (int)n_st, ipr,
+                                                            (int)n_pr, tx, ty, tz);
+    if (cudaGetLastError() != cudaSuccess) return FV_ERR_CUDA;
+    PrimArgs pa{x.P, dcase, ipr, (int)n_pr, qprev, prim, nullptr, nullptr, derr};
+    if (launch_prim(x.nd, x.nc, x.mixed, pa, gp, s) != cudaSuccess) return FV_ERR_CUDA;
+    StageArgs sa{x.P, dcase, ist, (int)n_st, prim, q0, qout, ddt, LSRK_A[k - 1], derr};
+    if (launch_stage(x.nd, x.nc, x.mixed, sa, gs, smem, s) != cudaSuccess) return FV_ERR_CUDA;
+    int e = 0;
+    if (cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FV_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FV_ERR_CUDA;
+    if (e & ERR_NONCONV) return FV_ERR_EOS_NONCONV;
+    if (e & ERR_NONPHYS) return FV_ERR_NONPHYSICAL;
+    return FV_OK;
+}

@@ -28,7 +28,7 @@ FV_DIAG_TOTALS, FV_DIAG_DT, FV_DIAG_TIME, FV_DIAG_ERROR = range(4)
 EXPORTS = ["fv_workspace_size", "fv_init", "fv_init_ws", "fv_destroy", "fv_set_stream", "fv_set_state",
            "fv_get_state", "fv_set_state_device", "fv_get_state_device", "fv_rk_stage", "fv_step",
            "fv_step_async", "fv_get_diag", "fv_launch_count", "fv_last_error", "fv_status_string",
-           "fv_profile", "fv_profile_read"]
+           "fv_profile", "fv_profile_read", "fv_rk_stage_noalloc"]
 FV_KERNEL_PRIM, FV_KERNEL_DT, FV_KERNEL_STAGE = range(3)
 
 
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
         L.fv_last_error.restype = C.c_char_p
         L.fv_profile.argtypes = [vp, C.c_int]
         L.fv_profile_read.argtypes = [vp, dp]
+        L.fv_rk_stage_noalloc.argtypes = [G, CM, E, C.c_int, C.c_double, vp, vp, vp, vp]
         L.fv_status_string.argtypes = [C.c_int]
         L.fv_status_string.restype = C.c_char_p
         _lib = L

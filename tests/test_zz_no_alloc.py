@@ -1,0 +1,69 @@
+"""fv_rk_stage_noalloc: the stage entry point for callers that cannot
+allocate device memory (a host application that owns the device through its
+own pool, a fixed memory budget, or a path where an allocation is not
+allowed).  It must give the same result as fv_rk_stage, call after call, and
+refuse grids whose scratch does not fit its static array.
+
+This file is collected last on purpose: it runs alone in a fresh process as
+well as after every other test."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2304_00140_gb300 import fv, workloads as wl
+from tests.helpers import rel_field_diff
+
+pytestmark = pytest.mark.gpu
+
+
+def _abi(w, precision):
+    g = fv.make_grid(w)
+    cm = fv.make_components(w)
+    e = fv.make_eos(dict(w.scheme, precision=precision))
+    return g, cm, e
+
+
+def _noalloc_step(L, args, dt, q0, qa, qb, stream):
+    g, cm, e = args
+    regs = [(q0, q0, qa), (q0, qa, qb), (q0, qb, qa), (q0, qa, q0)]
+    for k, (base, prev, out) in enumerate(regs, start=1):
+        st = L.fv_rk_stage_noalloc(C.byref(g), C.byref(cm), C.byref(e), k, dt, C.c_void_p(base.data_ptr()),
+                                   C.c_void_p(prev.data_ptr()), C.c_void_p(out.data_ptr()), C.c_void_p(stream))
+        assert st == fv.FV_OK, fv.status_string(st)
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_noalloc_matches_fv_rk_stage_twice(precision):
+    import torch
+    w = wl.random_state(n=(37, 23), bc=[[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2, [0, 0]])
+    s = fv.Solver(w, precision=precision)
+    s.set_state(w.primitives(), kind=fv.FV_PRIMITIVE)
+    q = s.get_state()
+    dt = 0.2 * 0.4 / (np.abs(q[1] / q[0]).max() / w.dx[0] + 5000.0 / w.dx[0])
+    refs = []
+    for _ in range(2):
+        s.step_dt(dt)
+        refs.append(s.get_state())
+    L = fv.load()
+    args = _abi(w, precision)
+    q0 = torch.from_numpy(q.copy()).cuda()
+    qa, qb = torch.empty_like(q0), torch.empty_like(q0)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        _noalloc_step(L, args, dt, q0, qa, qb, stream)
+        got = q0.cpu().numpy()
+        d = rel_field_diff(got, refs[call])
+        assert np.all(d <= 1e-12), (call, d)
+
+
+def test_noalloc_rejects_grids_beyond_its_scratch():
+    import torch
+    w = wl.random_state(n=(2048, 2048))
+    L = fv.load()
+    g, cm, e = _abi(w, fv.FV_FP64)
+    buf = torch.zeros(8, dtype=torch.float64, device="cuda")
+    p = C.c_void_p(buf.data_ptr())
+    st = L.fv_rk_stage_noalloc(C.byref(g), C.byref(cm), C.byref(e), 1, 1e-9, p, p, p,
+                               C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == fv.FV_ERR_ARG
