@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("thr_ducros", C.c_double), ("thr_gas", C.c_double), ("eps_ducros", C.c_double),
                 ("d3p_coef", C.c_double), ("sigma", C.c_double), ("grad_eps", C.c_double),
                 ("in_yc", C.c_double), ("in_zc", C.c_double), ("in_radius", C.c_double),
-                ("in_T", C.c_double), ("in_Y", C.c_double * MAXC), ("in_u", C.POINTER(C.c_double))]
+                ("in_T", C.c_double), ("in_Y", C.c_double * MAXC), ("in_u", C.POINTER(C.c_double)),
+                ("in_u0", C.c_double * 3)]
 
 
 def lib():
@@ -116,6 +117,8 @@ def make_params(w, inflow_u: np.ndarray | None = None) -> Params:
         P.in_yc, P.in_zc, P.in_radius, P.in_T = f["yc"] - w.lo[1], f["zc"] - w.lo[2], f["radius"], f["T"]
         for k, y in enumerate(f["Y"]):
             P.in_Y[k] = y
+        for d, u in enumerate(f.get("u0", (0.0, 0.0, 0.0))):
+            P.in_u0[d] = u
     return P
 
 

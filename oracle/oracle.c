@@ -449,7 +449,7 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
                 if (in_disc) {
                     size_t fc = (size_t)src[2] * P->n[1] + src[1];
                     size_t fn = (size_t)P->n[1] * P->n[2];
-                    for (int a = 0; a < nd; ++a) w[a] = P->in_u ? P->in_u[a * fn + fc] : 0.0;
+                    for (int a = 0; a < nd; ++a) w[a] = P->in_u ? P->in_u[a * fn + fc] : P->in_u0[a];
                     w[nd + 1] = P->in_T;
                     for (int kk = 0; kk < P->ncomp - 1; ++kk) w[nd + 2 + kk] = P->in_Y[kk];
                     double Y[OR_MAXC], e2;

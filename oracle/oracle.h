@@ -62,6 +62,7 @@ typedef struct {
     double in_yc, in_zc, in_radius, in_T;
     double in_Y[OR_MAXC];             /* tracked mass fractions of the inflow */
     const double* in_u;               /* [3][nz][ny] inflow velocity, or NULL */
+    double in_u0[3];                  /* uniform inflow velocity used when in_u is NULL */
 } or_params;
 
 /* closure, pointwise (Yt = the N-1 tracked mass fractions) */

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/thinc_fv.h"
@@ -201,6 +202,36 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
         d.pother = P.single_class ? 0.0 : (d.classA ? piB : piA);
         P.Pk[k] = P.p_ref + c.pinf;
     }
+    // working-precision copies of the constants
+    auto fill = [&](auto& Kt) {
+        using T = std::remove_reference_t<decltype(Kt.p_ref)>;
+        for (int k = 0; k < MAXC; ++k) {
+            const CompDev& d = P.c[k];
+            Kt.Pk[k] = T(P.Pk[k]);
+            Kt.gm1cv[k] = T(d.gm1cv);
+            Kt.igamma[k] = T(d.igamma);
+            Kt.gcv[k] = T(d.gcv);
+            Kt.cv[k] = T(d.cv);
+            Kt.q[k] = T(d.q);
+            Kt.pinf[k] = T(d.pinf);
+            Kt.pother[k] = T(d.pother);
+        }
+        Kt.p_ref = T(P.p_ref);
+        Kt.beta = T(P.beta);
+        Kt.thinc_eps = T(P.thinc_eps);
+        Kt.thinc_gamma = T(P.thinc_gamma);
+        Kt.tb = T(P.tb);
+        Kt.icb = T(P.icb);
+        Kt.itb = T(P.itb);
+        Kt.thr_ducros = T(P.thr_ducros);
+        Kt.thr_gas = T(P.thr_gas);
+        Kt.eps_ducros = T(P.eps_ducros);
+        Kt.d3p_coef = T(P.d3p_coef);
+        Kt.sigma = T(P.sigma);
+        Kt.grad_eps = T(P.grad_eps);
+    };
+    fill(P.kd);
+    fill(P.kf);
 }
 
 static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mixed, Layout& L,
@@ -218,6 +249,8 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
             gx[d] = C.g[d];
             C.dx[d] = d < nd ? (g[c].hi[d] - g[c].lo[d]) / g[c].n[d] : 1.0;
             C.idx[d] = 1.0 / C.dx[d];
+            C.fdx[d] = float(C.dx[d]);
+            C.fidx[d] = float(C.idx[d]);
             C.bc[d][0] = d < nd ? g[c].bc[d][0] : 0;
             C.bc[d][1] = d < nd ? g[c].bc[d][1] : 0;
         }
@@ -823,6 +856,8 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
         C.g[d] = d < x.nd ? grid->n[d] + 4 : 1;
         C.dx[d] = d < x.nd ? (grid->hi[d] - grid->lo[d]) / grid->n[d] : 1.0;
         C.idx[d] = 1.0 / C.dx[d];
+        C.fdx[d] = float(C.dx[d]);
+        C.fidx[d] = float(C.idx[d]);
         C.bc[d][0] = d < x.nd ? grid->bc[d][0] : 0;
         C.bc[d][1] = d < x.nd ? grid->bc[d][1] : 0;
     }

@@ -22,12 +22,23 @@ struct CaseDesc {
     long long qoff;      // first cell of this case in the conserved arrays
     long long poff;      // first cell of this case in the primitive arrays
     double dx[3], idx[3];
+    float fdx[3], fidx[3];   // float copies for the FP32 arithmetic
     int bc[3][2];
     int inflow;          // x-low side is an inflow disc
     double in_yc, in_zc, in_r2, in_T;
     double in_u0[3];
     double in_Y[MAXC];
     long long in_uoff;   // offset of this case's [3][nz][ny] inflow velocity, -1 = use in_u0
+};
+
+// Constants of the arithmetic in the working precision R (a double and a
+// float copy are kept so the FP32 arithmetic never converts at run time).
+template <typename R>
+struct ConstT {
+    R Pk[MAXC];          // p_ref + pinf_k
+    R gm1cv[MAXC], igamma[MAXC], gcv[MAXC], cv[MAXC], q[MAXC], pinf[MAXC], pother[MAXC];
+    R p_ref, beta, thinc_eps, thinc_gamma, tb, icb, itb;
+    R thr_ducros, thr_gas, eps_ducros, d3p_coef, sigma, grad_eps;
 };
 
 struct CompDev {
@@ -53,7 +64,16 @@ struct DevParams {
     double Pk[MAXC];     // p_ref + pinf_k
     long long ntot_q;    // interior cells of all cases (field stride of q)
     long long ntot_p;    // ghosted cells of all cases (field stride of primitives)
+    ConstT<double> kd;
+    ConstT<float> kf;
 };
+
+template <typename R> __device__ __forceinline__ const ConstT<R>& K(const DevParams& P);
+template <> __device__ __forceinline__ const ConstT<double>& K<double>(const DevParams& P) { return P.kd; }
+template <> __device__ __forceinline__ const ConstT<float>& K<float>(const DevParams& P) { return P.kf; }
+template <typename R> __device__ __forceinline__ R pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 // ---------------------------------------------------------------- helpers
 template <typename R> __device__ __forceinline__ R clip01(R x) { return x < R(0) ? R(0) : (x > R(1) ? R(1) : x); }
@@ -62,26 +82,28 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double sq_rt(double x) { return sqrt(x); }
 __device__ __forceinline__ float sq_rt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double ex(double x) { return exp(x); }
-__device__ __forceinline__ float ex(float x) { return expf(x); }
+__device__ __forceinline__ float ex(float x) { return __expf(x); }
+// Division and reciprocal: IEEE in double (the FP64 form matches the oracle
+// to rounding), the hardware approximation in float (a couple of ulp, well
+// inside the FP32 form's accuracy; every float denominator here is far below
+// 2^126).
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double frcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
 
-// Reciprocals of N pressures.  In double one division serves all of them
-// (1/P_k = prod_{j != k} P_j / prod_j P_j); in float each is a division.
-template <int N>
-__device__ __forceinline__ void recips(const double* P, double* iP)
+// Reciprocals of N (<= 3) pressures with one division:
+// 1/P_k = prod_{j != k} P_j / prod_j P_j (products stay far from overflow).
+template <int N, typename R>
+__device__ __forceinline__ void recips(const R* P, R* iP)
 {
-    if (N == 1) { iP[0] = 1.0 / P[0]; return; }
-    double pre[N], acc = 1.0;
+    if (N == 1) { iP[0] = frcp(P[0]); return; }
+    R pre[N], acc = R(1);
 #pragma unroll
     for (int k = 0; k < N; ++k) { pre[k] = acc; acc *= P[k]; }
-    double inv = 1.0 / acc, suf = 1.0;
+    R inv = frcp(acc), suf = R(1);
 #pragma unroll
     for (int k = N - 1; k >= 0; --k) { iP[k] = pre[k] * suf * inv; suf *= P[k]; }
-}
-template <int N>
-__device__ __forceinline__ void recips(const float* P, float* iP)
-{
-#pragma unroll
-    for (int k = 0; k < N; ++k) iP[k] = 1.0f / P[k];
 }
 
 // ------------------------------------------------------------ closure
@@ -101,27 +123,28 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
 #pragma unroll
     for (int k = 0; k < NC - 1; ++k) { Y[k] = clip01(Yt[k]); s += Y[k]; }
     Y[NC - 1] = clip01(R(1) - s);
+    const ConstT<R>& Kc = K<R>(P);
     R Pk[NC], iP[NC];
     bool ok = T > R(0);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-        Pk[k] = R(P.Pk[k]) + pp;
+        Pk[k] = Kc.Pk[k] + pp;
         if (Y[k] > R(0)) ok = ok && (Pk[k] > R(0)); else Pk[k] = R(1);
     }
-    recips<NC>(Pk, iP);
+    recips<NC, R>(Pk, iP);
     R v = R(0), w = R(0), cp = R(0), eq = R(0);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-        R a = Y[k] * R(P.c[k].gm1cv) * iP[k];
+        R a = Y[k] * Kc.gm1cv[k] * iP[k];
         v += a;
-        w += a * iP[k] * R(P.c[k].igamma);
-        cp += Y[k] * R(P.c[k].gcv);
-        eq += Y[k] * R(P.c[k].q);
+        w += a * iP[k] * Kc.igamma[k];
+        cp += Y[k] * Kc.gcv[k];
+        eq += Y[k] * Kc.q[k];
     }
     v *= T;
     w *= T;
-    rho = R(1) / v;
-    e = cp * T - (R(P.p_ref) + pp) * v + eq;
+    rho = frcp(v);
+    e = cp * T - (Kc.p_ref + pp) * v + eq;
     c = v * rsq(w);
     return ok && (v > R(0)) && (w > R(0));
 }
@@ -145,7 +168,7 @@ __device__ __forceinline__ bool prim_recover(const DevParams& P, const double* q
     const double rho = qc[0];
     rho_d = rho;
     const R rr = R(rho);
-    const R irho = R(1) / rr;
+    const R irho = frcp(rr);
     R ke = R(0);
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
@@ -161,41 +184,43 @@ __device__ __forceinline__ bool prim_recover(const DevParams& P, const double* q
         w[ND + 2 + k] = Y[k];
     }
     Y[NC - 1] = clip01(R(1) - s);
+    const ConstT<R>& Kc = K<R>(P);
     R cv = R(0), cp = R(0), b = R(0), cc = R(0), se = R(0), eq = R(0);
     R sA = R(0), sB = R(0);
     const double rhoe = qc[ND + 1] - double(ke);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) eq += Y[k] * R(P.c[k].q);
+    for (int k = 0; k < NC; ++k) eq += Y[k] * Kc.q[k];
     const double rhoe_q = rhoe - rho * double(eq);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
         const CompDev& C = P.c[k];
-        const double Ek = fma(-(C.gamma - 1.0), rhoe_q, C.gamma * C.pinf);
-        const R Yc = Y[k] * R(C.cv);
+        // the one FP64 operation per component: E_k = gamma pinf - (gamma-1) rho e
+        const R Ek = R(fma(-(C.gamma - 1.0), rhoe_q, C.gamma * C.pinf));
+        const R Yc = Y[k] * Kc.cv[k];
         cv += Yc;
-        cp += Y[k] * R(C.gcv);
-        b += Yc * R(Ek + C.pother);
-        cc += Yc * R(C.pother * Ek);
-        se += Yc * R(Ek);
+        cp += Y[k] * Kc.gcv[k];
+        b += Yc * (Ek + Kc.pother[k]);
+        cc += Yc * (Kc.pother[k] * Ek);
+        se += Yc * Ek;
         if (Y[k] > R(0)) { if (C.classA) sA += Y[k]; else sB += Y[k]; }
     }
     R p;
     if (P.single_class || sA == R(0) || sB == R(0)) {
-        p = -se / cv;
+        p = fdiv(-se, cv);
     } else {
         const R disc = b * b - R(4) * cv * cc;
         const R sq = sq_rt(disc > R(0) ? disc : R(0));
-        p = (b >= R(0)) ? (R(-2) * cc) / (b + sq) : (sq - b) / (R(2) * cv);
+        p = (b >= R(0)) ? fdiv(R(-2) * cc, b + sq) : fdiv(sq - b, R(2) * cv);
     }
-    const R T = R(rhoe_q + double(p)) / (rr * cp);
-    w[ND] = p - R(P.p_ref);
+    const R T = fdiv(R(rhoe_q) + p, rr * cp);
+    w[ND] = p - Kc.p_ref;
     w[ND + 1] = T;
     T_out = T;
     p_abs = p;
     bool ok = (rho > 0.0) && (T > R(0)) && (cv > R(0));
 #pragma unroll
     for (int k = 0; k < NC; ++k)
-        if (Y[k] > R(0)) ok = ok && (p + R(P.c[k].pinf) > R(0));
+        if (Y[k] > R(0)) ok = ok && (p + Kc.pinf[k] > R(0));
     return ok;
 }
 
@@ -217,7 +242,7 @@ __device__ __forceinline__ R limited(int id, R num, R den)
         return fmin(R(0), fmax(R(2) * den, fmax(R(2) * num, t)));
     }
     default: {
-        const R r = num / den;
+        const R r = fdiv(num, den);
         R f;
         switch (id) {
         case 2: f = (r + fabs(r)) / (R(1) + fabs(r)); break;                        // van Leer
@@ -255,11 +280,12 @@ __device__ __forceinline__ R thinc_side(const DevParams& P, R xa, R xc, R xb, bo
 {
     const R mn = fmin(xa, xb), mx = fmax(xa, xb);
     const R th = (xb >= xa) ? R(1) : R(-1);
-    const R gam = R(P.thinc_gamma);
-    const R F = (xc - mn + gam) / (mx - mn + gam);
-    const R E = (ex(th * R(P.beta) * (R(2) * F - R(1))) * R(P.icb) - R(1)) * R(P.itb);
-    const R tb = R(P.tb);
-    const R t = left ? (tb + E) / (R(1) + E * tb) : E;
+    const ConstT<R>& Kc = K<R>(P);
+    const R gam = Kc.thinc_gamma;
+    const R F = fdiv(xc - mn + gam, mx - mn + gam);
+    const R E = (ex(th * Kc.beta * (R(2) * F - R(1))) * Kc.icb - R(1)) * Kc.itb;
+    const R tb = Kc.tb;
+    const R t = left ? fdiv(tb + E, R(1) + E * tb) : E;
     return mn + R(0.5) * (mx - mn) * (R(1) + th * t);
 }
 
@@ -291,7 +317,7 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
             const int lim = (v < ND) ? P.lim_vel : P.lim_scalar;
             muscl(lim, ws[0][v], ws[1][v], ws[2][v], ws[3][v], WL[v], WR[v]);
             if (v >= IY && P.thinc) {
-                const R eps = R(P.thinc_eps);
+                const R eps = K<R>(P).thinc_eps;
                 if (eligible(eps, ws[0][v], ws[1][v], ws[2][v])) WL[v] = thinc_side(P, ws[0][v], ws[1][v], ws[2][v], true);
                 if (eligible(eps, ws[1][v], ws[2][v], ws[3][v])) WR[v] = thinc_side(P, ws[1][v], ws[2][v], ws[3][v], false);
             }
@@ -307,17 +333,17 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
         const R IL = (R(3) * rho4[1] + rho4[2]) * cm * R(0.25);
         const R IR = (rho4[1] + R(3) * rho4[2]) * cm * R(0.25);
         if (f) {
-            us = (IL * uL + IR * uR + pL - pR) / (IL + IR);
+            us = fdiv(IL * uL + IR * uR + pL - pR, IL + IR);
             ps = R(0.5) * (pL + pR);
         } else {
-            const R d3 = R(P.d3p_coef) * (ws[0][IP] - R(3) * ws[1][IP] + R(3) * ws[2][IP] - ws[3][IP]);
-            us = uL - d3 / (IL + IR);
+            const R d3 = K<R>(P).d3p_coef * (ws[0][IP] - R(3) * ws[1][IP] + R(3) * ws[2][IP] - ws[3][IP]);
+            us = uL - fdiv(d3, IL + IR);
             ps = pL;
         }
     } else {
         ps = R(0.5) * (pL + pR);
         const R zL = rL * cL, zR = rR * cR;
-        us = (zL * uL + zR * uR + pL - pR) / (zL + zR);
+        us = fdiv(zL * uL + zR * uR + pL - pR, zL + zR);
     }
     const bool up = us >= R(0);
     const R* Ws = up ? WL : WR;
@@ -330,7 +356,7 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     F[0] = mflux;
 #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] = mflux * Ws[a] + (a == d ? ps : R(0));
-    F[1 + ND] = mflux * (es + ke) + (R(P.p_ref) + ps) * us;
+    F[1 + ND] = mflux * (es + ke) + (K<R>(P).p_ref + ps) * us;
 #pragma unroll
     for (int k = 0; k < NC - 1; ++k) F[2 + ND + k] = mflux * Ws[IY + k];
     return ok;

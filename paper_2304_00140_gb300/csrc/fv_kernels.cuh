@@ -41,9 +41,12 @@ struct StageArgs {
     int* err;
 };
 
+// Tile of the stage kernel and its thread count: NT covers the tile's
+// faces ((TX+1)TY + TX(TY+1) in 2D) in two nearly full rounds.
 template <int ND> struct TileShape;
-template <> struct TileShape<2> { static constexpr int X = 32, Y = 8, Z = 1; };
-template <> struct TileShape<3> { static constexpr int X = 32, Y = 4, Z = 2; };
+template <> struct TileShape<2> { static constexpr int X = 32, Y = 8, Z = 1, NT = 288; };
+template <> struct TileShape<3> { static constexpr int X = 32, Y = 4, Z = 2, NT = 256; };
+constexpr int PRIM_THREADS = 256;   // prim kernel: one thread per ghosted cell of a 32x8 / 32x4x2 tile
 
 __device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& flip, int& inflow)
 {
@@ -146,13 +149,13 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 for (int k = 0; k < NC - 1; ++k) s += clip01(w[ND + 2 + k]);
                 const int L = P.liquid;
                 const R Yl = (L == NC - 1) ? clip01(R(1) - s) : clip01(w[ND + 2 + L]);
-                const R al = rr * Yl * R(P.c[L].gm1cv) * w[ND + 1] / (R(P.Pk[L]) + w[ND]);
+                const R al = fdiv(rr * Yl * K<R>(P).gm1cv[L] * w[ND + 1], K<R>(P).Pk[L] + w[ND]);
                 prim[P.i_al * P.ntot_p + pc] = al;
             }
             if (A.smax && interior) {
                 R s = R(0);
 #pragma unroll
-                for (int d = 0; d < ND; ++d) s += (fabs(w[d]) + cs) * R(C.idx[d]);
+                for (int d = 0; d < ND; ++d) s += (fabs(w[d]) + cs) * pick<R>(C.idx[d], C.fidx[d]);
                 speed = double(s);
             }
         }
@@ -175,12 +178,13 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 
 // ------------------------------------------------------------------ stage
 template <int ND, int NC, typename R>
-__global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
+__global__ void __launch_bounds__(TileShape<ND>::NT, 2) stage_kernel(StageArgs A)
 {
     constexpr int NV = ND + NC + 1;
     using TS = TileShape<ND>;
     constexpr int TX = TS::X, TY = TS::Y, TZ = TS::Z;
-    constexpr int NT = TX * TY * TZ;
+    constexpr int NT = TS::NT;
+    constexpr int NCELL = TX * TY * TZ;
     constexpr int HX = TX + 4, HY = TY + 4, HZ = (ND == 3) ? TZ + 4 : 1;
     constexpr int HC = HX * HY * HZ;
     constexpr int SX = 1, SY = HX, SZ = HX * HY;
@@ -189,12 +193,11 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sp = reinterpret_cast<R*>(smem_raw);                 // [nprim][HC]
-    R* sf[3];                                               // fluxes per direction [NV][faces]
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
-    sf[0] = sp + P.nprim * HC;
-    sf[1] = sf[0] + NV * NFX;
-    sf[2] = sf[1] + NV * NFY;
-    R* extra = sf[ND - 1] + NV * (ND == 2 ? NFY : NFZ);
+    R* const sfx = sp + P.nprim * HC;                       // fluxes per direction [NV][faces]
+    R* const sfy = sfx + NV * NFX;
+    R* const sfz = sfy + NV * NFY;
+    R* extra = (ND == 2) ? sfz : sfz + NV * NFZ;
     // CSF scratch: smoothed alpha on the tile +1 halo and vertex normals
     constexpr int AX = TX + 2, AY = TY + 2, AZ = (ND == 3) ? TZ + 2 : 1;
     constexpr int VX = TX + 1, VY = TY + 1, VZ = (ND == 3) ? TZ + 1 : 1;
@@ -202,12 +205,23 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
     R* sn = sa + AX * AY * AZ;            // [ND][VZ][VY][VX]
     unsigned char* sflag = reinterpret_cast<unsigned char*>(sn + ND * VX * VY * VZ);  // [HC]
 
+    const ConstT<R>& Kc = K<R>(P);
     const int tid = threadIdx.x;
     for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
         const int4 wi = A.items[it];
         const CaseDesc& C = A.cases[wi.x];
         const int x0 = wi.y, y0 = wi.z, z0 = wi.w;
         const int vx = min(TX, C.n[0] - x0), vy = min(TY, C.n[1] - y0), vz = (ND == 3) ? min(TZ, C.n[2] - z0) : 1;
+        R ci[3], cdx[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { ci[d] = pick<R>(C.idx[d], C.fidx[d]); cdx[d] = pick<R>(C.dx[d], C.fdx[d]); }
+        // this thread's cell: prefetch q0 so its latency hides behind the face work
+        const int cx = tid % TX, cy = (tid / TX) % TY, cz = tid / (TX * TY);
+        const bool own = tid < NCELL && cx < vx && cy < vy && cz < vz;
+        const long long gcell = C.qoff + ((long long)(z0 + cz) * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx);
+        double q0r[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) q0r[v] = own ? A.q0[v * P.ntot_q + gcell] : 0.0;
         // ---- halo tile of primitives (ghosted coordinates x0 .. x0+HX-1)
         for (int h = tid; h < HC; h += NT) {
             const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
@@ -232,7 +246,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
 #pragma unroll
                     for (int bd = 0; bd < ND; ++bd) {
                         const int hp = h + st[bd], hm = h - st[bd];
-                        const R inv2dx = R(0.5 * C.idx[bd]);
+                        const R inv2dx = R(0.5) * ci[bd];
 #pragma unroll
                         for (int a = 0; a < ND; ++a) g[a][bd] = (sp[a * HC + hp] - sp[a * HC + hm]) * inv2dx;
                         tg += fabs(ag0 - (R(1) - sp[P.i_al * HC + hm])) + fabs((R(1) - sp[P.i_al * HC + hp]) - ag0);
@@ -249,8 +263,8 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
                         curl2 = wz * wz;
                     }
                     const R d2 = div * div;
-                    const R thD = d2 / (d2 + curl2 + R(P.eps_ducros));
-                    fl = (thD > R(P.thr_ducros) || tg > R(P.thr_gas)) ? 1 : 0;
+                    const R thD = fdiv(d2, d2 + curl2 + Kc.eps_ducros);
+                    fl = (thD > Kc.thr_ducros || tg > Kc.thr_gas) ? 1 : 0;
                 }
                 sflag[h] = fl;
             }
@@ -324,15 +338,16 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
             else if (d == 1) fi = (fz * (TY + 1) + fy) * TX + fx;
             else fi = (fz * TY + fy) * TX + fx;
             const int nfd = d == 0 ? NFX : (d == 1 ? NFY : NFZ);
+            R* const dst = d == 0 ? sfx : (d == 1 ? sfy : sfz);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) sf[d][v * nfd + fi] = F[v];
+            for (int v = 0; v < NV; ++v) dst[v * nfd + fi] = F[v];
         }
         // ---- CSF vertex normals from the smoothed alpha (Fig. 3.3)
         if (P.csf) {
-            R dxmin = R(C.dx[0]);
+            R dxmin = cdx[0];
 #pragma unroll
-            for (int d = 1; d < ND; ++d) dxmin = fmin(dxmin, R(C.dx[d]));
-            const R gthr = R(P.grad_eps) / dxmin;
+            for (int d = 1; d < ND; ++d) dxmin = fmin(dxmin, cdx[d]);
+            const R gthr = Kc.grad_eps / dxmin;
             for (int h = tid; h < VX * VY * VZ; h += NT) {
                 const int ix = h % VX, iy = (h / VX) % VY, iz = h / (VX * VY);
                 // vertex between smoothed cells (ix-1+1 .. ix+1) in sa coordinates: cells ix, ix+1
@@ -348,9 +363,9 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
                 }
                 R mag2 = R(0);
 #pragma unroll
-                for (int d = 0; d < ND; ++d) { g[d] *= R(C.idx[d]) * R(2.0 / nc); mag2 += g[d] * g[d]; }
+                for (int d = 0; d < ND; ++d) { g[d] *= ci[d] * R(2.0 / nc); mag2 += g[d] * g[d]; }
                 const R mag = sq_rt(mag2);
-                const R inv = (mag > gthr) ? R(1) / mag : R(0);
+                const R inv = (mag > gthr) ? frcp(mag) : R(0);
 #pragma unroll
                 for (int d = 0; d < ND; ++d) sn[(d * VZ + iz) * VY * VX + iy * VX + ix] = g[d] * inv;
             }
@@ -358,8 +373,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
         __syncthreads();
         // ---- divergence, CSF source, LSRK update (FP64 registers)
         {
-            const int cx = tid % TX, cy = (tid / TX) % TY, cz = tid / (TX * TY);
-            if (cx < vx && cy < vy && cz < vz) {
+            if (own) {
                 R S[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) S[v] = R(0);
@@ -387,8 +401,8 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
                         for (int d = 0; d < ND; ++d) {
                             const R nd_ = sn[(d * VZ + (ND == 3 ? cz + oz : 0)) * VY * VX + (cy + oy) * VX + cx + ox];
                             const int od = d == 0 ? ox : (d == 1 ? oy : oz);
-                            kappa -= (od ? nd_ : -nd_) * R(C.idx[d]) * R(2.0 / nc);
-                            ga[d] += gu[d] * R(C.idx[d]) * R(2.0 / nc);
+                            kappa -= (od ? nd_ : -nd_) * ci[d] * R(2.0 / nc);
+                            ga[d] += gu[d] * ci[d] * R(2.0 / nc);
                         }
                         (void)vi;
                     }
@@ -396,23 +410,22 @@ __global__ void __launch_bounds__(256) stage_kernel(StageArgs A)
 #pragma unroll
                     for (int d = 0; d < ND; ++d) {
                         ga[d] *= R(1.0 / nc);
-                        S[1 + d] = R(P.sigma) * kappa * ga[d];
+                        S[1 + d] = Kc.sigma * kappa * ga[d];
                         udg += sp[d * HC + hc] * ga[d];
                     }
-                    S[1 + ND] = R(P.sigma) * kappa * udg;
+                    S[1 + ND] = Kc.sigma * kappa * udg;
                 }
-                const long long gcell = C.qoff + ((long long)(z0 + cz) * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx);
                 const double adt = A.a * A.dt[wi.x];
                 const int fxl = (cz * TY + cy) * (TX + 1) + cx;
                 const int fyl = (cz * (TY + 1) + cy) * TX + cx;
                 const int fzl = (cz * TY + cy) * TX + cx;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    R div = (sf[0][v * NFX + fxl + 1] - sf[0][v * NFX + fxl]) * R(C.idx[0]);
-                    div += (sf[1][v * NFY + fyl + TX] - sf[1][v * NFY + fyl]) * R(C.idx[1]);
-                    if (ND == 3) div += (sf[2][v * NFZ + fzl + TX * TY] - sf[2][v * NFZ + fzl]) * R(C.idx[2]);
+                    R div = (sfx[v * NFX + fxl + 1] - sfx[v * NFX + fxl]) * ci[0];
+                    div += (sfy[v * NFY + fyl + TX] - sfy[v * NFY + fyl]) * ci[1];
+                    if (ND == 3) div += (sfz[v * NFZ + fzl + TX * TY] - sfz[v * NFZ + fzl]) * ci[2];
                     const R Rv = S[v] - div;
-                    A.qout[v * P.ntot_q + gcell] = A.q0[v * P.ntot_q + gcell] + adt * double(Rv);
+                    A.qout[v * P.ntot_q + gcell] = q0r[v] + adt * double(Rv);
                 }
             }
         }

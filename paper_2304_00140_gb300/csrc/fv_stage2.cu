@@ -6,7 +6,7 @@ namespace tfv {
 template <int NC, typename R>
 static cudaError_t go2(const StageArgs& A, int grid, size_t smem, cudaStream_t s)
 {
-    stage_kernel<2, NC, R><<<grid, 256, smem, s>>>(A);
+    stage_kernel<2, NC, R><<<grid, TileShape<2>::NT, smem, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -40,7 +40,7 @@ template <int NC, typename R>
 static int occ2(size_t smem)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, NC, R>, 256, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<2, NC, R>, TileShape<2>::NT, smem) != cudaSuccess) return 1;
     return n < 1 ? 1 : n;
 }
 

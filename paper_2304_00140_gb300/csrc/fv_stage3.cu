@@ -6,7 +6,7 @@ namespace tfv {
 template <int NC, typename R>
 static cudaError_t go3(const StageArgs& A, int grid, size_t smem, cudaStream_t s)
 {
-    stage_kernel<3, NC, R><<<grid, 256, smem, s>>>(A);
+    stage_kernel<3, NC, R><<<grid, TileShape<3>::NT, smem, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -40,7 +40,7 @@ template <int NC, typename R>
 static int occ3(size_t smem)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<3, NC, R>, 256, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, stage_kernel<3, NC, R>, TileShape<3>::NT, smem) != cudaSuccess) return 1;
     return n < 1 ? 1 : n;
 }
 

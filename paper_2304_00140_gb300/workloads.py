@@ -264,8 +264,20 @@ def _init_random(w: Workload):
     return W
 
 
+def _init_jet(w: Workload):
+    """configs[4]: ambient N2/CH4 gas at rest filling the box; the liquid
+    enters through the inflow disc on the x-low face (boundary data)."""
+    P = w.params
+    W = _alloc(w)
+    W[w.ndim] = P["p"]
+    W[w.ndim + 1] = P["T"]
+    W[w.ndim + 2] = 1.0 - P["Y_ch4"]      # N2
+    W[w.ndim + 3] = P["Y_ch4"]            # CH4 (dodecane implied = 0)
+    return W
+
+
 _INIT = {"column": _init_column, "shock_bubble": _init_shock_bubble,
-         "droplet": _init_droplet, "random": _init_random}
+         "droplet": _init_droplet, "random": _init_random, "jet": _init_jet}
 
 
 # --------------------------------------------------------------------------
@@ -342,3 +354,43 @@ def random_state(n=(24, 20), ncomp=2, seed=SEED, bc=None, ndim=2, **scheme):
         hi=[L, L * ny / nx, L * nz / nx], bc=bc, comps=comps, liquid=ncomp - 1,
         scheme=default_scheme(**scheme), steps=1, cfl=0.4, init="random",
         params=dict(seed=seed, p=2e6, T=320.0, R=0.3e-3, width=1.5, du=40.0))
+
+
+def jet3d(n=(512, 256, 256), steps=1000, seed=SEED, **scheme):
+    """3D liquid jet primary break-up: n cells on a 4 x 2 x 2 mm box,
+    dodecane-like stiffened-gas liquid (gamma 2.35, pinf 4e8, cv 1077) at
+    363 K injected through a circular inflow of radius 16 cells (scaled with
+    ny/256) at 300 m/s, into an N2/CH4 ideal-gas mixture (Y_CH4 = 0.1) at
+    6 MPa and 900 K at rest; outflow elsewhere; App. D switch and CSF with
+    sigma = 0.025 N/m."""
+    nx, ny, nz = n
+    L = 4e-3
+    hi = [L, L * ny / nx, L * nz / nx]
+    dy = hi[1] / ny
+    radius = 16.0 * dy * ny / 256.0
+    sch = default_scheme(**dict(dict(iles=1, sigma=0.025, p_ref=6e6, T_ref=900.0), **scheme))
+    w = Workload(
+        name=f"jet3d_{nx}x{ny}x{nz}", ndim=3, n=[nx, ny, nz], lo=[0.0, 0.0, 0.0], hi=hi,
+        bc=[[BC_INFLOW, BC_OUTFLOW], [BC_OUTFLOW, BC_OUTFLOW], [BC_OUTFLOW, BC_OUTFLOW]],
+        comps=[N2_IG, CH4_IG, DODECANE_SG], liquid=2, scheme=sch, steps=steps, cfl=0.4, init="jet",
+        params=dict(p=6e6, T=900.0, Y_ch4=0.1, seed=seed, U=300.0, amp=0.05),
+        inflow=dict(yc=0.5 * hi[1], zc=0.5 * hi[2], radius=radius, T=363.0, Y=[0.0, 0.0], u0=(300.0, 0.0, 0.0)))
+    return w
+
+
+def jet_inflow_velocity(w: Workload) -> np.ndarray:
+    """[3][nz][ny] inflow velocity of the jet: U (1 + amp (sin(4 phi) / 2 +
+    r_i / 2)) along x with r_i seeded uniform in [-1, 1] per face cell and phi
+    the polar angle around the disc centre (READING: a steady 5% sinusoidal
+    plus random perturbation).  Outside the disc the values are unused."""
+    P, f = w.params, w.inflow
+    ny, nz = w.n[1], w.n[2]
+    rng = SplitMix64(P["seed"] ^ 0x4A4554)
+    rnd = np.array([rng.uniform(-1.0, 1.0) for _ in range(ny * nz)]).reshape(nz, ny)
+    y = w.lo[1] + (np.arange(ny) + 0.5) * w.dx[1] - f["yc"]
+    z = w.lo[2] + (np.arange(nz) + 0.5) * w.dx[2] - f["zc"]
+    Z, Y = np.meshgrid(z, y, indexing="ij")
+    phi = np.arctan2(Z, Y)
+    u = np.zeros((3, nz, ny))
+    u[0] = P["U"] * (1.0 + P["amp"] * (0.5 * np.sin(4.0 * phi) + 0.5 * rnd))
+    return u

@@ -1,0 +1,120 @@
+"""GPU parity with the oracle for the CSF source, the App. D switch, 3D grids,
+three components, the inflow disc, batches of droplets and the FP32-mixed
+form's accuracy."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_00140_gb300 import fv, workloads as wl
+from tests.helpers import oracle_step_dt, rel_field_diff, rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_pair(w, steps_dt=1, dt_frac=0.3, inflow_u=None, precision=fv.FV_FP64):
+    o = oracle.Oracle(w, inflow_u=inflow_u)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=precision, inflow_u=[inflow_u] if inflow_u is not None else None)
+    s.set_state(q)
+    dt = dt_frac * o.dt(q, 1.0)
+    ref = q
+    for _ in range(steps_dt):
+        s.step_dt(dt)
+        ref = oracle_step_dt(o, ref, dt)
+    return o, q, s.get_state(), ref
+
+
+def _scale_momentum(d, w, got, ref):
+    """momentum components measured against the momentum vector's scale"""
+    nd = w.ndim
+    mag = np.sqrt((ref[1:1 + nd] ** 2).sum(0)).max()
+    for a in range(nd):
+        d[1 + a] = np.abs(got[1 + a] - ref[1 + a]).max() / mag
+    return d
+
+
+def test_csf_droplet_parity():
+    w = wl.droplet(n=(40, 36), A=0.15, sigma=30.0)
+    o, q, got, ref = _run_pair(w, steps_dt=3)
+    S = o.csf_source(q)
+    assert np.abs(S).max() > 0.0
+    d = _scale_momentum(rel_field_diff(got, ref), w, got, ref)
+    assert np.all(d < 1e-11), d
+
+
+def test_iles_switch_parity_2d():
+    w = wl.random_state(n=(40, 33), iles=1)
+    o = oracle.Oracle(w)
+    f = o.sensor(o.prim_to_cons(w.primitives()))
+    assert 0.05 < f.mean() < 0.95          # both branches of Eq. D.3 are exercised
+    o, q, got, ref = _run_pair(w, steps_dt=2)
+    d = rel_field_diff(got, ref)
+    assert np.all(d < 1e-11), d
+
+
+@pytest.mark.parametrize("ncomp", [2, 3])
+def test_plain_3d_parity(ncomp):
+    w = wl.random_state(n=(20, 14, 11), ndim=3, ncomp=ncomp)
+    o, q, got, ref = _run_pair(w)
+    d = rel_field_diff(got, ref)
+    assert np.all(d < 1e-12), d
+
+
+def test_iles_csf_3d_three_components_parity():
+    w = wl.random_state(n=(18, 12, 10), ndim=3, ncomp=3, iles=1, sigma=5.0,
+                        bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_PERIODIC] * 2, [wl.BC_REFLECT, wl.BC_OUTFLOW]])
+    o, q, got, ref = _run_pair(w, steps_dt=2)
+    d = _scale_momentum(rel_field_diff(got, ref), w, got, ref)
+    assert np.all(d < 1e-11), d
+
+
+def test_jet_inflow_parity():
+    """Inflow disc, three components and CSF in 3D.  Plain mode: in the
+    quiescent gas ahead of an impulsive jet the App. D Ducros ratio is formed
+    from rounding-level velocities, so its decisions there follow rounding
+    noise (a 1e-15 perturbation of the oracle's own input flips hundreds of
+    them) and FP64 parity is only defined away from that; the switch itself is
+    checked on states with O(10 m/s) velocities above."""
+    w = wl.jet3d(n=(24, 16, 16), iles=0)
+    w.inflow["radius"] = 4.5 * w.dx[1]
+    u = wl.jet_inflow_velocity(w)
+    o, q, got, ref = _run_pair(w, steps_dt=4, inflow_u=u)
+    # the liquid has entered
+    assert (ref[2 + w.ndim, :, :, 0] / ref[0, :, :, 0]).min() < 0.5
+    d = _scale_momentum(rel_field_diff(got, ref), w, got, ref)
+    assert np.all(d < 1e-11), d
+
+
+def test_droplet_batch_matches_single_and_oracle():
+    cases = [wl.droplet(n=n, A=a, sigma=20.0) for n, a in ((24, 0.1), (40, 0.2), (33, 0.05), (16, 0.15))]
+    qs = [oracle.Oracle(c).prim_to_cons(c.primitives()) for c in cases]
+    b = fv.Solver(cases)
+    for i, q in enumerate(qs):
+        b.set_state(q, case=i)
+    b.step(4, 0.4)
+    for i, c in enumerate(cases):
+        s = fv.Solver(c)
+        s.set_state(qs[i])
+        s.step(4, 0.4)
+        assert np.array_equal(s.get_state(), b.get_state(case=i))
+    ref, _ = oracle.Oracle(cases[1]).step(qs[1], 4, 0.4)
+    got = b.get_state(case=1)
+    d = _scale_momentum(rel_field_diff(got, ref), cases[1], got, ref)
+    assert np.all(d < 1e-11), d
+
+
+def test_mixed_form_accuracy_advection():
+    """FP32-mixed 128^2 advection run (200 steps) against the FP64 oracle:
+    relative L1 per conserved field below 1e-5."""
+    w = wl.advection(n=128, steps=200)
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=fv.FV_MIXED)
+    s.set_state(q)
+    s.step(w.steps, w.cfl)
+    ref, _ = o.step(q, w.steps, w.cfl)
+    e = rel_l1(s.get_state(), ref)
+    assert np.all(e < 1e-5), e
+    W = s.get_state(fv.FV_PRIMITIVE)
+    # the low-Mach pressure survives the p + pinf cancellation in FP32
+    assert np.abs(W[2] / 1e5 - 1).max() < 1e-3
