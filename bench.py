@@ -40,9 +40,41 @@ def _peaks():
     return dict(hbm=6800.0, src="fallback")
 
 
+WORKLOADS = ("shock_bubble", "advection", "pr_shock_droplet", "droplet_ensemble", "jet3d")
+
+
+class Job:
+    """the cases of one workload (a batch for the droplet ensemble)"""
+
+    def __init__(self, name, cases, inflow=None):
+        self.name, self.cases, self.inflow = name, cases, inflow
+        self.cells = sum(c.cells for c in cases)
+        self.w = cases[0]
+        self.cfl = cases[0].cfl
+        self.nvar = cases[0].nvar
+        self.ndim = cases[0].ndim
+
+
 def _workload(args):
     from paper_2304_00140_gb300 import workloads as wl
-    return wl.shock_bubble(nx=args.nx, ny=args.ny)
+    k = args.workload
+    if k == "shock_bubble":
+        w = wl.shock_bubble(nx=args.nx, ny=args.ny)
+        return Job(w.name, [w])
+    if k == "advection":
+        w = wl.advection(n=args.nx if args.nx != 2048 else 128)
+        return Job(w.name, [w])
+    if k == "pr_shock_droplet":
+        w = wl.pr_shock_droplet(n=args.nx if args.nx != 2048 else 1024)
+        return Job(w.name, [w])
+    if k == "droplet_ensemble":
+        cases = wl.droplet_ensemble(ncases=args.ncases)
+        return Job(f"droplet_ensemble_{len(cases)}", cases)
+    if k == "jet3d":
+        n = (512, 256, 256) if args.nx == 2048 else (args.nx, args.nx // 2, args.nx // 2)
+        w = wl.jet3d(n=n)
+        return Job(w.name, [w], inflow=[wl.jet_inflow_velocity(w)])
+    raise SystemExit(f"unknown workload {k}")
 
 
 # ------------------------------------------------------------------ clocks
@@ -88,18 +120,31 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- one form
-def _algorithmic_stage_bytes(w, precision):
+def _nprim(w):
+    s = w.scheme
+    return w.nvar + (2 if s["iles"] else 0) + (1 if (s["iles"] or s["sigma"] > 0) else 0)
+
+
+def _algorithmic_stage_bytes(job, precision):
     """Compulsory HBM bytes of one stage_kernel launch: every interior cell's
     primitives read once (fp32 in the mixed form, fp64 otherwise), q^0 read
     and q^k written in FP64."""
     rs = 4 if precision == 1 else 8
-    return w.cells * (w.nvar * rs + 2 * w.nvar * 8)
+    return job.cells * (_nprim(job.w) * rs + 2 * job.nvar * 8)
 
 
-def run_form(w, W, precision, args, torch, dist, rank, world):
+def _solver(job, precision):
     from paper_2304_00140_gb300 import fv
-    s = fv.Solver(w, precision=precision)
-    s.set_state(W, kind=fv.FV_PRIMITIVE)
+    s = fv.Solver(job.cases, precision=precision, inflow_u=job.inflow)
+    for i, c in enumerate(job.cases):
+        s.set_state(job.prims[i], kind=fv.FV_PRIMITIVE, case=i)
+    return s
+
+
+def run_form(job, precision, args, torch, dist, rank, world):
+    from paper_2304_00140_gb300 import fv
+    s = _solver(job, precision)
+    w = job.w
     stream = torch.cuda.current_stream()
     s.step_async(args.warmup, w.cfl)
     torch.cuda.synchronize()
@@ -129,39 +174,41 @@ def run_form(w, W, precision, args, torch, dist, rank, world):
     s.step_async(kprof, w.cfl)
     prof = s.profile_read()
     s.profile(False)
-    state = s.get_state()
-    res = dict(ms=ms, launches=launches, clocks=clocks, err=err, prof=prof, state=state, solver=s)
-    return res
+    state = np.concatenate([s.get_state(case=i).reshape(job.nvar, -1) for i in range(len(job.cases))], axis=1)
+    s.close()
+    return dict(ms=ms, launches=launches, clocks=clocks, err=err, prof=prof, state=state)
 
 
-def e2e_form(w, precision, args, torch):
+def e2e_form(job, precision, args, torch):
     """Same metric through the public API with host buffers: every step copies
-    the state in from pinned host memory, advances one step and reads the
-    state back."""
+    every case's state in from pinned host memory, advances one step and
+    reads the states back."""
     import ctypes as C
     from paper_2304_00140_gb300 import fv
-    s = fv.Solver(w, precision=precision)
-    W = w.primitives()
-    s.set_state(W, kind=fv.FV_PRIMITIVE)
-    q = s.get_state()
-    h_in = torch.from_numpy(q.copy()).pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
+    s = _solver(job, precision)
+    nc = len(job.cases)
+    h_in = [torch.from_numpy(s.get_state(case=i).copy()).pin_memory() for i in range(nc)]
+    h_out = [torch.empty_like(h).pin_memory() for h in h_in]
     L = s.L
     nsteps = max(3, min(args.steps, 30))
-    L.fv_set_state(s.ctx, 0, fv.FV_CONSERVED, C.c_void_p(h_in.data_ptr()))
-    L.fv_step(s.ctx, 1, w.cfl, None)
+    for i in range(nc):
+        L.fv_set_state(s.ctx, i, fv.FV_CONSERVED, C.c_void_p(h_in[i].data_ptr()))
+    L.fv_step(s.ctx, 1, job.cfl, None)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(nsteps):
-        st = L.fv_set_state(s.ctx, 0, fv.FV_CONSERVED, C.c_void_p(h_in.data_ptr()))
-        st = st or L.fv_step_async(s.ctx, 1, w.cfl)
-        st = st or L.fv_get_state(s.ctx, 0, fv.FV_CONSERVED, C.c_void_p(h_out.data_ptr()))
+        st = 0
+        for i in range(nc):
+            st = st or L.fv_set_state(s.ctx, i, fv.FV_CONSERVED, C.c_void_p(h_in[i].data_ptr()))
+        st = st or L.fv_step_async(s.ctx, 1, job.cfl)
+        for i in range(nc):
+            st = st or L.fv_get_state(s.ctx, i, fv.FV_CONSERVED, C.c_void_p(h_out[i].data_ptr()))
         if st:
             raise fv.FVError(st, L.fv_last_error(s.ctx).decode())
     t1 = time.perf_counter()
-    nbytes = int(h_in.numel() * 8)
+    nbytes = int(sum(h.numel() for h in h_in) * 8)
     s.close()
-    return dict(value=w.cells * nsteps / (t1 - t0), unit=UNIT, h2d_bytes_per_step=nbytes,
+    return dict(value=job.cells * nsteps / (t1 - t0), unit=UNIT, h2d_bytes_per_step=nbytes,
                 d2h_bytes_per_step=nbytes, steps=nsteps)
 
 
@@ -181,21 +228,26 @@ def oracle_window_step(o, q, dt, lo, hi):
     return prev
 
 
-def cpu_oracle_rate(w, rows, reps=1):
+def cpu_oracle_rate(job, rows, reps=1):
     """The FP64 oracle, as it stands, single-threaded on the host: one LSRK
-    step on a band of ``rows`` full-width rows through the bubble."""
+    step on a band of ``rows`` full-width rows (2D) or planes (3D) through
+    the middle of the first case."""
     import oracle
-    o = oracle.Oracle(w)
+    w = job.w
+    o = oracle.Oracle(w, inflow_u=job.inflow[0] if job.inflow else None)
     q = o.prim_to_cons(w.primitives())
-    ny = w.n[1]
-    y0 = max(0, ny // 2 - rows // 2)
-    lo, hi = (0, y0, 0), (w.n[0], y0 + rows, 1)
-    dt = 1e-12
+    ax = w.ndim - 1
+    n = w.n[ax]
+    rows = min(rows, n)
+    a0 = max(0, n // 2 - rows // 2)
+    lo, hi = [0, 0, 0], [w.n[0], w.n[1], w.n[2]]
+    lo[ax], hi[ax] = a0, a0 + rows
+    dt = 0.1 * o.dt(q, w.cfl) if w.cells <= 4_000_000 else 1e-12
     t0 = time.perf_counter()
     for _ in range(reps):
         oracle_window_step(o, q, dt, lo, hi)
     t1 = time.perf_counter()
-    cells = w.n[0] * rows * reps
+    cells = w.cells // n * rows * reps
     return cells / (t1 - t0), cells, t1 - t0
 
 
@@ -205,9 +257,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = _workload(args)
+    job = _workload(args)
+    w = job.w
     import oracle
-    o = oracle.Oracle(w)
+    o = oracle.Oracle(w, inflow_u=job.inflow[0] if job.inflow else None)
     q = o.prim_to_cons(w.primitives())
     # band height sized so the whole run stays near two minutes of host time
     rows = args.ref_rows or int(min(64, max(2, 120.0 / ((args.steps + args.warmup) * 0.04))))
@@ -245,6 +298,9 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=192)
     ap.add_argument("--ref-rows", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=0, help="steps for the FP64 form (default: --steps)")
+    ap.add_argument("--workload", default="shock_bubble", choices=WORKLOADS)
+    ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--ncases", type=int, default=1024)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -267,65 +323,78 @@ def main():
 
     from paper_2304_00140_gb300 import fv
     fv.load()
-    w = _workload(args)
-    W = w.primitives()
+    job = _workload(args)
+    job.prims = [c.primitives() for c in job.cases]
+    w = job.w
     peaks = _peaks()
 
-    mixed = run_form(w, W, fv.FV_MIXED, args, torch, dist, rank, world)
+    forms = {"both": ("mixed", "fp64"), "mixed": ("mixed",), "fp64": ("fp64",)}[args.precision]
+    res = {}
     fargs = argparse.Namespace(**vars(args))
     if args.fp64_steps:
         fargs.steps = args.fp64_steps
-    f64 = run_form(w, W, fv.FV_FP64, fargs, torch, dist, rank, world)
+    if "mixed" in forms:
+        res["mixed"] = run_form(job, fv.FV_MIXED, args, torch, dist, rank, world)
+    if "fp64" in forms:
+        res["fp64"] = run_form(job, fv.FV_FP64, fargs, torch, dist, rank, world)
 
     # accuracy of the mixed form against the FP64 form after the same steps
-    # (both advanced warmup + steps + profiled steps from the same state)
+    # (both advanced warmup + steps + profiled steps from the same state):
     # relative L1 per conserved field; the momentum components are measured
     # against the L1 norm of the momentum vector (a component can be ~0)
     l1 = None
-    if fargs.steps == args.steps:
-        a, b = mixed["state"], f64["state"]
+    if len(res) == 2 and fargs.steps == args.steps:
+        a, b = res["mixed"]["state"], res["fp64"]["state"]
         nv = a.shape[0]
         den = np.abs(b).reshape(nv, -1).sum(1)
         den[1:1 + w.ndim] = np.sqrt((b[1:1 + w.ndim] ** 2).sum(0)).sum()
         l1 = (np.abs(a - b).reshape(nv, -1).sum(1) / den).tolist()
 
-    def roof(res, precision):
-        st = res["prof"]["stage"]
+    def roof(r, precision):
+        st = r["prof"]["stage"]
         avg_ms = st["ms"] / max(1, st["launches"])
-        byt = _algorithmic_stage_bytes(w, precision)
+        byt = _algorithmic_stage_bytes(job, precision)
         ach = byt / (avg_ms * 1e-3) / 1e9
         return dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
                     traffic=None, kernel="stage_kernel", avg_launch_ms=avg_ms,
                     algorithmic_bytes_per_launch=byt, peak_source=peaks["src"],
-                    kernel_share={k: v["ms"] for k, v in res["prof"].items()})
+                    kernel_share={k: v["ms"] for k, v in r["prof"].items()})
 
-    cells_all = w.cells * world
-    val = cells_all * args.steps / (mixed["ms"] * 1e-3)
-    v64 = cells_all * fargs.steps / (f64["ms"] * 1e-3)
-    e2e = e2e_form(w, fv.FV_MIXED, args, torch) if rank == 0 else None
+    head = forms[0]
+    hprec = fv.FV_MIXED if head == "mixed" else fv.FV_FP64
+    hsteps = args.steps if head == "mixed" else fargs.steps
+    cells_all = job.cells * world
+    val = cells_all * hsteps / (res[head]["ms"] * 1e-3)
+    e2e = e2e_form(job, hprec, args, torch) if rank == 0 else None
     if e2e is not None:
         e2e["value"] *= world
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cells, secs = cpu_oracle_rate(w, args.cpu_rows)
+        rate, cells, secs = cpu_oracle_rate(job, args.cpu_rows)
         cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
-                   sample=f"one LSRK step of a {w.n[0]}x{args.cpu_rows} row band of the same grid "
+                   sample=f"one LSRK step of a {args.cpu_rows}-row band of {job.w.name} "
                           f"({cells} cell-updates, {secs:.1f} s, single thread)")
 
     if rank == 0:
+        regbytes = job.nvar * job.cells * 8
         line = dict(
-            metric=METRIC, value=val, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-            ms_per_step=mixed["ms"] / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-            dtype="f32+f64", data="synthetic",
-            config=dict(workload=w.name, grid=w.n[:2], cells=w.cells, cfl=w.cfl, precision="mixed",
-                        parallelism=f"replicas{world}", l2="inputs larger than L2 (3 FP64 registers of "
-                        f"{w.nvar * w.cells * 8 / 1e6:.0f} MB each plus primitives)"),
-            roofline=roof(mixed, fv.FV_MIXED), cpu_baseline=cpu, e2e=e2e,
-            gpu_launches=mixed["launches"], clocks=mixed["clocks"],
-            fp64=dict(value=v64, unit=UNIT, dtype="f64", steps=fargs.steps, ms_per_step=f64["ms"] / fargs.steps,
-                      roofline=roof(f64, fv.FV_FP64), gpu_launches=f64["launches"], clocks=f64["clocks"]),
-            l1_mixed_vs_fp64=l1, device_errors=[mixed["err"], f64["err"]])
+            metric=METRIC, value=val, unit=UNIT, n_gpus=world, steps=hsteps, warmup=args.warmup,
+            ms_per_step=res[head]["ms"] / hsteps, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f32+f64" if head == "mixed" else "f64", data="synthetic",
+            config=dict(workload=job.name, cases=len(job.cases), grid=w.n[:w.ndim], cells=job.cells, cfl=job.cfl,
+                        precision=head, parallelism=f"replicas{world}",
+                        l2=("inputs larger than L2" if regbytes > 129e6 else "inputs smaller than L2") +
+                        f" (3 FP64 registers of {regbytes / 1e6:.0f} MB each plus primitives)"),
+            roofline=roof(res[head], hprec), cpu_baseline=cpu, e2e=e2e,
+            gpu_launches=res[head]["launches"], clocks=res[head]["clocks"],
+            l1_mixed_vs_fp64=l1, device_errors={k: v["err"] for k, v in res.items()})
+        if head == "mixed" and "fp64" in res:
+            f64 = res["fp64"]
+            line["fp64"] = dict(value=cells_all * fargs.steps / (f64["ms"] * 1e-3), unit=UNIT, dtype="f64",
+                                steps=fargs.steps, ms_per_step=f64["ms"] / fargs.steps,
+                                roofline=roof(f64, fv.FV_FP64), gpu_launches=f64["launches"],
+                                clocks=f64["clocks"])
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -76,6 +76,7 @@ def lib():
             L.or_totals.argtypes = [P, dp, dp]
             L.or_csf_source.argtypes = [P, dp, dp]
             L.or_sensor.argtypes = [P, dp, dp]
+            L.or_pr_state.argtypes = [P, C.c_double, C.c_double, dp, dp]
             _lib = L
     return _lib
 
@@ -205,6 +206,12 @@ class Oracle:
         p, T = C.c_double(), C.c_double()
         _check(self.L.or_closure_inverse(C.byref(self.P), rho, e, _ptr(Y), C.byref(p), C.byref(T)), "inverse")
         return p.value, T.value
+
+    def pr_state(self, T, v, Yt):
+        Y = np.ascontiguousarray(Yt, dtype=np.float64)
+        out = np.zeros(8)
+        _check(self.L.or_pr_state(C.byref(self.P), T, v, _ptr(Y), _ptr(out)), "pr_state")
+        return dict(p=out[0], e=out[1], c=out[2], cv=out[3], a=out[4], b=out[5], M=out[6], da=out[7])
 
     def face_flux(self, d, W4, rho4=None, c4=None, f=1):
         W = np.zeros((4, MAXV))

@@ -150,23 +150,247 @@ static int sg_inverse(const or_params* P, double rho, double e, const double* Y,
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------------
+ * App. A.2.1: Peng-Robinson closure.  p = R T/(v - b) - a/(v^2 + 2 b v - b^2)
+ * with v the molar volume M/rho, a = sum sum X_a X_b a_ab, b = sum X_a b_a,
+ * a_ab = 0.457236 (R Tc_ab)^2/pc_ab (1 + c_ab (1 - sqrt(T/Tc_ab)))^2,
+ * b_a = 0.077796 R Tc_a/pc_a, pc_ab = Zc_ab R Tc_ab/vc_ab,
+ * c_ab = 0.37464 + 1.5422 w_ab - 0.26992 w_ab^2, Tc_ab = sqrt(Tc_a Tc_b) (k = 0),
+ * vc_ab = (vc_a^(1/3) + vc_b^(1/3))^3 / 8, Zc_ab = (Zc_a + Zc_b)/2,
+ * w_ab = (w_a + w_b)/2.
+ * READING: the components' vc and Zc are not given; Zc = 0.3074 (the PR
+ * value) and vc = Zc R Tc/pc, which makes pc_aa = pc.
+ * READING: the caloric part uses the constant ideal-gas cv of each species
+ * (the NASA polynomials the paper cites are not available):
+ *   e = sum Y_k cv_k T + (a - T a')/(2 sqrt2 b M) ln((v + (1-sqrt2) b)/(v + (1+sqrt2) b))
+ * (the PR departure function per unit mass).
+ * --------------------------------------------------------------------- */
+#define PR_RU 8.314462618
+#define PR_ZC 0.3074
+
+typedef struct {
+    double X[OR_MAXC];
+    double M;          /* mixture molar mass */
+    double a, da, d2a; /* a(T) and its T derivatives */
+    double b;
+    double cvig;       /* sum Y_k cv_k */
+} pr_mix;
+
+static void pr_mixture(const or_params* P, const double* Y, double T, pr_mix* m)
+{
+    const int N = P->ncomp;
+    double s = 0.0;
+    m->cvig = 0.0;
+    for (int k = 0; k < N; ++k) {
+        s += Y[k] / P->comp[k].M;
+        m->cvig += Y[k] * P->comp[k].cv;
+    }
+    m->M = 1.0 / s;
+    m->b = 0.0;
+    for (int k = 0; k < N; ++k) {
+        m->X[k] = (Y[k] / P->comp[k].M) * m->M;
+        m->b += m->X[k] * 0.077796 * PR_RU * P->comp[k].Tc / P->comp[k].pc;
+    }
+    m->a = m->da = m->d2a = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            const or_comp* ci = &P->comp[i];
+            const or_comp* cj = &P->comp[j];
+            double Tc = sqrt(ci->Tc * cj->Tc);
+            double vci = PR_ZC * PR_RU * ci->Tc / ci->pc, vcj = PR_ZC * PR_RU * cj->Tc / cj->pc;
+            double vc = pow(cbrt(vci) + cbrt(vcj), 3.0) / 8.0;
+            double Zc = 0.5 * (PR_ZC + PR_ZC);
+            double pc = Zc * PR_RU * Tc / vc;
+            double w = 0.5 * (ci->omega + cj->omega);
+            double cc = 0.37464 + 1.5422 * w - 0.26992 * w * w;
+            double A = 0.457236 * (PR_RU * Tc) * (PR_RU * Tc) / pc;
+            double sq = sqrt(T / Tc);
+            double g = 1.0 + cc * (1.0 - sq);
+            double xx = m->X[i] * m->X[j];
+            m->a += xx * A * g * g;
+            m->da += xx * (-A * cc * g / sqrt(T * Tc));
+            m->d2a += xx * (A * cc * cc / (2.0 * T * Tc) + A * cc * g / (2.0 * T * sqrt(T * Tc)));
+        }
+}
+
+static double pr_p(const pr_mix* m, double T, double v)
+{
+    return PR_RU * T / (v - m->b) - m->a / (v * v + 2.0 * m->b * v - m->b * m->b);
+}
+
+static double pr_logterm(const pr_mix* m, double v)
+{
+    const double s2 = sqrt(2.0);
+    return log((v + (1.0 - s2) * m->b) / (v + (1.0 + s2) * m->b));
+}
+
+static double pr_e(const pr_mix* m, double T, double v)
+{
+    return m->cvig * T + (m->a - T * m->da) / (2.0 * sqrt(2.0) * m->b * m->M) * pr_logterm(m, v);
+}
+
+/* isochoric heat capacity per unit mass (d e / d T at fixed v) */
+static double pr_cv(const pr_mix* m, double T, double v)
+{
+    return m->cvig - T * m->d2a / (2.0 * sqrt(2.0) * m->b * m->M) * pr_logterm(m, v);
+}
+
+/* sound speed: c^2 = (dp/drho)_T + T (dp/dT)_rho^2 / (rho^2 cv) */
+static double pr_c(const pr_mix* m, double T, double v)
+{
+    const double d = v * v + 2.0 * m->b * v - m->b * m->b;
+    const double dpdT = PR_RU / (v - m->b) - m->da / d;
+    const double dpdv = -PR_RU * T / ((v - m->b) * (v - m->b)) + m->a * (2.0 * v + 2.0 * m->b) / (d * d);
+    const double rho = m->M / v;
+    const double dpdrho = -(v * v / m->M) * dpdv;
+    const double c2 = dpdrho + T * dpdT * dpdT / (rho * rho * pr_cv(m, T, v));
+    return sqrt(c2);
+}
+
+/* departure Gibbs energy / (R T) of a compressibility root Z */
+static double pr_gdep(double Z, double A, double B)
+{
+    const double s2 = sqrt(2.0);
+    return Z - 1.0 - log(Z - B) - A / (2.0 * s2 * B) * log((Z + (1.0 + s2) * B) / (Z + (1.0 - s2) * B));
+}
+
+/* forward (TDU): (p, T, Y) -> rho, e, c.  Z solves
+ * Z^3 - (1-B) Z^2 + (A - 3B^2 - 2B) Z - (AB - B^2 - B^3) = 0, A = a p/(R T)^2,
+ * B = b p/(R T).  Every real root above B is found by bisection on the
+ * monotone pieces of the cubic; READING (the paper is silent): with three
+ * roots the one of lowest Gibbs energy is taken. */
+static double cubic(double c2, double c1, double c0, double Z) { return ((Z + c2) * Z + c1) * Z + c0; }
+
+static double bisect_cubic(double c2, double c1, double c0, double lo, double hi)
+{
+    double flo = cubic(c2, c1, c0, lo);
+    for (int it = 0; it < 400; ++it) {
+        double mid = lo + 0.5 * (hi - lo);
+        if (mid <= lo || mid >= hi) break;
+        double fm = cubic(c2, c1, c0, mid);
+        if ((fm > 0.0) == (flo > 0.0)) { lo = mid; flo = fm; } else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static int pr_forward(const or_params* P, double p, double T, const double* Y, double* rho, double* e, double* cs)
+{
+    if (!(T > 0.0) || !(p > 0.0)) return OR_ERR_NONPHYS;
+    pr_mix m;
+    pr_mixture(P, Y, T, &m);
+    const double RT = PR_RU * T;
+    const double A = m.a * p / (RT * RT), B = m.b * p / RT;
+    const double c2 = -(1.0 - B), c1 = A - 3.0 * B * B - 2.0 * B, c0 = -(A * B - B * B - B * B * B);
+    /* stationary points split the real line into monotone pieces */
+    double pts[4];
+    int np = 0;
+    pts[np++] = B;
+    double disc = 4.0 * c2 * c2 - 12.0 * c1;
+    if (disc > 0.0) {
+        double s = sqrt(disc);
+        double z1 = (-2.0 * c2 - s) / 6.0, z2 = (-2.0 * c2 + s) / 6.0;
+        if (z1 > B) pts[np++] = z1;
+        if (z2 > B) pts[np++] = z2;
+    }
+    double hi = 1.0;
+    while (cubic(c2, c1, c0, hi) <= 0.0 || hi < pts[np - 1]) hi *= 2.0;
+    pts[np++] = hi;
+    double best = -1.0, gbest = INFINITY;
+    for (int i = 0; i + 1 < np; ++i) {
+        double fa = cubic(c2, c1, c0, pts[i]), fb = cubic(c2, c1, c0, pts[i + 1]);
+        if (fa == 0.0 && pts[i] > B) { double g = pr_gdep(pts[i], A, B); if (g < gbest) { gbest = g; best = pts[i]; } }
+        if ((fa > 0.0) != (fb > 0.0) && fb != 0.0) {
+            double Z = bisect_cubic(c2, c1, c0, pts[i], pts[i + 1]);
+            if (Z > B) {
+                double g = pr_gdep(Z, A, B);
+                if (g < gbest) { gbest = g; best = Z; }
+            }
+        }
+    }
+    if (!(best > B)) return OR_ERR_NONCONV;
+    const double v = best * RT / p;
+    if (rho) *rho = m.M / v;
+    if (e) *e = pr_e(&m, T, v);
+    if (cs) *cs = pr_c(&m, T, v);
+    return OR_OK;
+}
+
+/* inverse (App. B): T from e at fixed rho by bisection (e increases with T
+ * at fixed v), then p explicit from Eq. A.2.1 */
+static int pr_inverse(const or_params* P, double rho, double e, const double* Y, double* p, double* T)
+{
+    if (!(rho > 0.0) || !isfinite(e)) return OR_ERR_NONPHYS;
+    pr_mix m;
+    pr_mixture(P, Y, 300.0, &m);
+    const double v = m.M / rho;
+    if (!(v > m.b)) return OR_ERR_NONPHYS;
+    double lo = 1.0, hi = 2.0;
+    for (int it = 0;; ++it) {
+        pr_mixture(P, Y, hi, &m);
+        if (pr_e(&m, hi, v) > e) break;
+        lo = hi;
+        hi *= 2.0;
+        if (it > 60) return OR_ERR_NONCONV;
+    }
+    for (int it = 0; it < 400; ++it) {
+        double mid = lo + 0.5 * (hi - lo);
+        if (mid <= lo || mid >= hi) break;
+        pr_mixture(P, Y, mid, &m);
+        if (pr_e(&m, mid, v) > e) hi = mid; else lo = mid;
+    }
+    *T = 0.5 * (lo + hi);
+    pr_mixture(P, Y, *T, &m);
+    *p = pr_p(&m, *T, v);
+    if (!isfinite(*p)) return OR_ERR_NONPHYS;
+    return OR_OK;
+}
+
+static int all_kind(const or_params* P, int kind)
+{
+    for (int k = 0; k < P->ncomp; ++k)
+        if (P->comp[k].kind != kind) return 0;
+    return 1;
+}
+
 int or_closure_forward(const or_params* P, double p, double T, const double* Yt,
                        double* rho, double* e, double* c, double* alpha)
 {
     double Y[OR_MAXC];
     full_Y(P, Yt, Y);
-    for (int k = 0; k < P->ncomp; ++k)
-        if (P->comp[k].kind != OR_SG) return OR_ERR_ARG;
-    return sg_forward(P, p, T, Y, rho, e, c, alpha);
+    if (all_kind(P, OR_SG)) return sg_forward(P, p, T, Y, rho, e, c, alpha);
+    if (all_kind(P, OR_PR)) {
+        if (alpha)
+            for (int k = 0; k < P->ncomp; ++k) alpha[k] = 0.0;   /* no volume fractions for a real-fluid mixture */
+        return pr_forward(P, p, T, Y, rho, e, c);
+    }
+    return OR_ERR_ARG;
 }
 
 int or_closure_inverse(const or_params* P, double rho, double e, const double* Yt, double* p, double* T)
 {
     double Y[OR_MAXC];
     full_Y(P, Yt, Y);
-    for (int k = 0; k < P->ncomp; ++k)
-        if (P->comp[k].kind != OR_SG) return OR_ERR_ARG;
-    return sg_inverse(P, rho, e, Y, p, T);
+    if (all_kind(P, OR_SG)) return sg_inverse(P, rho, e, Y, p, T);
+    if (all_kind(P, OR_PR)) return pr_inverse(P, rho, e, Y, p, T);
+    return OR_ERR_ARG;
+}
+
+/* pointwise PR pieces for the pins: out = (Z roots count, chosen Z, a, b, M) */
+int or_pr_state(const or_params* P, double T, double v, const double* Yt, double* out)
+{
+    double Y[OR_MAXC];
+    full_Y(P, Yt, Y);
+    pr_mix m;
+    pr_mixture(P, Y, T, &m);
+    out[0] = pr_p(&m, T, v);
+    out[1] = pr_e(&m, T, v);
+    out[2] = pr_c(&m, T, v);
+    out[3] = pr_cv(&m, T, v);
+    out[4] = m.a;
+    out[5] = m.b;
+    out[6] = m.M;
+    out[7] = m.da;
+    return OR_OK;
 }
 
 /* ------------------------------------------------------------------------

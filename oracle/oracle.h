@@ -71,6 +71,9 @@ int or_closure_forward(const or_params* P, double p, double T, const double* Yt,
 int or_closure_inverse(const or_params* P, double rho, double e, const double* Yt,
                        double* p, double* T);
 
+/* Peng-Robinson pieces at (T, molar volume v): out = p, e, c, cv, a, b, M, da/dT */
+int or_pr_state(const or_params* P, double T, double v, const double* Yt, double* out);
+
 /* reconstruction pieces */
 double or_limiter(int id, double r);
 void or_muscl(int id, double x1, double x2, double x3, double x4, double* L, double* R);

@@ -127,9 +127,28 @@ static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm,
     }
     if (cm->ncomp < 2 || cm->ncomp > 3) { why = "ncomp must be 2 or 3"; return FV_ERR_ARG; }
     if (cm->liquid < 0 || cm->liquid >= cm->ncomp) { why = "bad liquid index"; return FV_ERR_ARG; }
+    int npr = 0;
+    for (int k = 0; k < cm->ncomp; ++k) npr += cm->comp[k].kind == FV_PR;
+    if (npr == cm->ncomp) {
+        // Peng-Robinson mixture (Eq. A.2.1)
+        for (int k = 0; k < cm->ncomp; ++k) {
+            const fv_component& c = cm->comp[k];
+            if (!(c.Tc > 0.0) || !(c.pc > 0.0) || !(c.M > 0.0) || !(c.cv > 0.0)) {
+                why = "bad Peng-Robinson constants";
+                return FV_ERR_ARG;
+            }
+        }
+        if (eos->sigma > 0.0 || eos->iles) {
+            why = "CSF and the App. D switch need stiffened-gas / ideal-gas components";
+            return FV_ERR_ARG;
+        }
+    } else if (npr > 0) {
+        why = "components must be all stiffened-gas / ideal-gas or all Peng-Robinson";
+        return FV_ERR_ARG;
+    }
     double pis[FV_MAX_COMP];
     int npi = 0;
-    for (int k = 0; k < cm->ncomp; ++k) {
+    for (int k = 0; k < cm->ncomp && npr == 0; ++k) {
         const fv_component& c = cm->comp[k];
         if (c.kind != FV_SG) { why = "only stiffened-gas / ideal-gas components are supported"; return FV_ERR_ARG; }
         if (!(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) { why = "bad component constants"; return FV_ERR_ARG; }
@@ -201,6 +220,33 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
         d.classA = (c.pinf == piA && !P.single_class) ? 1 : 0;
         d.pother = P.single_class ? 0.0 : (d.classA ? piB : piA);
         P.Pk[k] = P.p_ref + c.pinf;
+    }
+    // Peng-Robinson constants (Eq. A.2.1).  The components' critical volume
+    // and compressibility are not given: Zc = 0.3074 (the PR value) and
+    // vc = Zc R Tc / pc, so pc_aa = pc.
+    int npr = 0;
+    for (int k = 0; k < cm->ncomp; ++k) npr += cm->comp[k].kind == FV_PR;
+    P.pr = npr == cm->ncomp;
+    if (P.pr) {
+        const double RU = 8.314462618, ZC = 0.3074;
+        for (int i = 0; i < cm->ncomp; ++i) {
+            const fv_component& ci = cm->comp[i];
+            P.prc.b[i] = 0.077796 * RU * ci.Tc / ci.pc;
+            P.prc.iM[i] = 1.0 / ci.M;
+            P.prc.cv[i] = ci.cv;
+            for (int j = 0; j < cm->ncomp; ++j) {
+                const fv_component& cj = cm->comp[j];
+                const double Tc = std::sqrt(ci.Tc * cj.Tc);
+                const double vci = ZC * RU * ci.Tc / ci.pc, vcj = ZC * RU * cj.Tc / cj.pc;
+                const double vc = std::pow(std::cbrt(vci) + std::cbrt(vcj), 3.0) / 8.0;
+                const double pc = 0.5 * (ZC + ZC) * RU * Tc / vc;
+                const double w = 0.5 * (ci.omega + cj.omega);
+                P.prc.A[i][j] = 0.457236 * (RU * Tc) * (RU * Tc) / pc;
+                P.prc.cc[i][j] = 0.37464 + 1.5422 * w - 0.26992 * w * w;
+                P.prc.isqTc[i][j] = 1.0 / std::sqrt(Tc);
+            }
+        }
+        P.single_class = 1;
     }
     // working-precision copies of the constants
     auto fill = [&](auto& Kt) {
@@ -393,6 +439,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     CK(x, cudaMemset(x->t, 0, sizeof(double) * ncases));
     CK(x, cudaMemset(x->err, 0, sizeof(int)));
     CK(x, cudaMemset(x->Q0, 0, sizeof(double) * x->nv * L.ntot_q));
+    CK(x, cudaMemset(x->prim, 0, (x->mixed ? sizeof(float) : sizeof(double)) * (size_t)x->nprim * L.ntot_p));
     for (int c = 0; c < ncases; ++c)
         if (x->cases[c].in_uoff >= 0)
             CK(x, cudaMemcpy(x->in_u + x->cases[c].in_uoff, grids[c].in_u,

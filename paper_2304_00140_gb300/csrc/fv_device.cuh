@@ -50,6 +50,14 @@ struct CompDev {
     int classA;          // 1 if pinf == the larger class pressure
 };
 
+// Peng-Robinson constants (Eq. A.2.1): per species b_k, 1/M_k, cv_k; per
+// species pair A_ab = 0.457236 (R Tc_ab)^2 / pc_ab, c_ab (acentric term) and
+// 1/sqrt(Tc_ab).  Always used in FP64.
+struct PRConst {
+    double b[MAXC], iM[MAXC], cv[MAXC];
+    double A[MAXC][MAXC], cc[MAXC][MAXC], isqTc[MAXC][MAXC];
+};
+
 // Scheme constants, passed by value to every kernel (kernel-parameter bank).
 struct DevParams {
     int ndim, ncomp, nv, nprim, liquid;
@@ -66,6 +74,8 @@ struct DevParams {
     long long ntot_p;    // ghosted cells of all cases (field stride of primitives)
     ConstT<double> kd;
     ConstT<float> kf;
+    int pr;              // every component is Peng-Robinson
+    PRConst prc;
 };
 
 template <typename R> __device__ __forceinline__ const ConstT<R>& K(const DevParams& P);
@@ -106,6 +116,150 @@ __device__ __forceinline__ void recips(const R* P, R* iP)
     for (int k = N - 1; k >= 0; --k) { iP[k] = pre[k] * suf * inv; suf *= P[k]; }
 }
 
+
+// ------------------------------------------------------- Peng-Robinson
+constexpr double PR_RU = 8.314462618;
+constexpr double SQRT2 = 1.4142135623730951;
+
+template <int NC>
+struct PRMix {
+    double X[NC], M, b, cvig;
+};
+
+template <int NC>
+__device__ __forceinline__ void pr_mix(const DevParams& P, const double* Y, PRMix<NC>& m)
+{
+    double s = 0.0, cv = 0.0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) { s += Y[k] * P.prc.iM[k]; cv += Y[k] * P.prc.cv[k]; }
+    m.M = 1.0 / s;
+    m.cvig = cv;
+    m.b = 0.0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) { m.X[k] = Y[k] * P.prc.iM[k] * m.M; m.b += m.X[k] * P.prc.b[k]; }
+}
+
+// a(T) = sum_ab X_a X_b A_ab (1 + c_ab (1 - sqrt(T/Tc_ab)))^2 and its first two T derivatives
+template <int NC>
+__device__ __forceinline__ void pr_a(const DevParams& P, const PRMix<NC>& m, double T, double& a, double& da,
+                                     double& d2a)
+{
+    const double sT = sqrt(T), iT = 1.0 / T, isT = 1.0 / sT;
+    a = da = d2a = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC; ++i)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            const double xx = m.X[i] * m.X[j], A = P.prc.A[i][j], c = P.prc.cc[i][j], iq = P.prc.isqTc[i][j];
+            const double g = 1.0 + c * (1.0 - sT * iq);
+            a += xx * A * g * g;
+            da -= xx * A * c * g * iq * isT;
+            d2a += xx * 0.5 * A * c * iT * iq * (c * iq + g * isT);
+        }
+}
+
+__device__ __forceinline__ double pr_cubic(double c2, double c1, double c0, double Z) { return ((Z + c2) * Z + c1) * Z + c0; }
+
+__device__ __forceinline__ double pr_gdep(double Z, double A, double B)
+{
+    return Z - 1.0 - log(Z - B) - A / (2.0 * SQRT2 * B) * log((Z + (1.0 + SQRT2) * B) / (Z + (1.0 - SQRT2) * B));
+}
+
+// TDU with the PR closure: (p, T, Y) -> rho, e, c.  Roots of the cubic in Z
+// in closed form (Cardano / trigonometric), polished by Newton; of several
+// roots above B the one of lowest Gibbs energy is taken.
+template <int NC>
+__device__ __forceinline__ bool pr_tdu(const DevParams& P, double p, double T, const double* Y, double& rho,
+                                       double& e, double& c)
+{
+    if (!(T > 0.0) || !(p > 0.0)) return false;
+    PRMix<NC> m;
+    pr_mix<NC>(P, Y, m);
+    double a, da, d2a;
+    pr_a<NC>(P, m, T, a, da, d2a);
+    const double RT = PR_RU * T;
+    const double A = a * p / (RT * RT), B = m.b * p / RT;
+    const double c2 = -(1.0 - B), c1 = A - 3.0 * B * B - 2.0 * B, c0 = -(A * B - B * B - B * B * B);
+    const double sh = c2 / 3.0;
+    const double pp = c1 - c2 * sh;
+    const double qq = (2.0 / 27.0) * c2 * c2 * c2 - c2 * c1 / 3.0 + c0;
+    const double D = 0.25 * qq * qq + pp * pp * pp / 27.0;
+    double Z[3];
+    int nr;
+    if (D > 0.0) {
+        const double sD = sqrt(D);
+        Z[0] = cbrt(-0.5 * qq + sD) + cbrt(-0.5 * qq - sD) - sh;
+        nr = 1;
+    } else {
+        const double r = sqrt(fmax(-pp / 3.0, 0.0));
+        const double cosphi = (r > 0.0) ? fmin(1.0, fmax(-1.0, -0.5 * qq / (r * r * r))) : 1.0;
+        const double phi = acos(cosphi);
+        Z[0] = 2.0 * r * cos(phi / 3.0) - sh;
+        Z[1] = 2.0 * r * cos((phi - 2.0 * 3.141592653589793) / 3.0) - sh;
+        Z[2] = 2.0 * r * cos((phi + 2.0 * 3.141592653589793) / 3.0) - sh;
+        nr = 3;
+    }
+    double best = -1.0, gbest = 1e300;
+    for (int i = 0; i < nr; ++i) {
+        double z = Z[i];
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const double f = pr_cubic(c2, c1, c0, z), df = (3.0 * z + 2.0 * c2) * z + c1;
+            if (df != 0.0) z -= f / df;
+        }
+        if (!(z > B)) continue;
+        const double g = (nr == 1) ? 0.0 : pr_gdep(z, A, B);
+        if (g < gbest) { gbest = g; best = z; }
+    }
+    if (!(best > B)) return false;
+    const double v = best * RT / p;
+    const double L = log((v + (1.0 - SQRT2) * m.b) / (v + (1.0 + SQRT2) * m.b));
+    const double k2 = L / (2.0 * SQRT2 * m.b * m.M);
+    rho = m.M / v;
+    e = m.cvig * T + (a - T * da) * k2;
+    const double cv = m.cvig - T * d2a * k2;
+    const double dd = v * v + 2.0 * m.b * v - m.b * m.b;
+    const double dpdT = PR_RU / (v - m.b) - da / dd;
+    const double dpdv = -RT / ((v - m.b) * (v - m.b)) + a * (2.0 * v + 2.0 * m.b) / (dd * dd);
+    const double c2s = -(v * v / m.M) * dpdv + T * dpdT * dpdT / (rho * rho * cv);
+    c = sqrt(c2s);
+    return c2s > 0.0 && cv > 0.0;
+}
+
+// Primitive recovery with the PR closure (App. B): Newton on T for
+// e(T, v) = e at fixed molar volume v = M/rho, started from the previous T
+// (T0; an ideal-gas estimate when T0 is not usable), steps limited to a
+// factor 5, at most 50 iterations; then p explicit from Eq. A.2.1.
+template <int NC>
+__device__ __forceinline__ int pr_invert(const DevParams& P, double rho, double e, const double* Y, double T0,
+                                         double& p, double& T)
+{
+    PRMix<NC> m;
+    pr_mix<NC>(P, Y, m);
+    const double v = m.M / rho;
+    if (!(v > m.b) || !isfinite(e)) return ERR_NONPHYS;
+    const double L = log((v + (1.0 - SQRT2) * m.b) / (v + (1.0 + SQRT2) * m.b));
+    const double k2 = L / (2.0 * SQRT2 * m.b * m.M);
+    double t = (T0 > 1.0 && T0 < 1e5) ? T0 : (e > 0.0 ? e / m.cvig : 300.0);
+    double a, da, d2a;
+    bool conv = false;
+    for (int it = 0; it < 50; ++it) {
+        pr_a<NC>(P, m, t, a, da, d2a);
+        const double f = m.cvig * t + (a - t * da) * k2 - e;
+        const double df = m.cvig - t * d2a * k2;
+        double tn = t - f / df;
+        tn = fmin(fmax(tn, 0.2 * t), 5.0 * t);
+        const double dt = tn - t;
+        t = tn;
+        if (fabs(dt) <= 1e-13 * t) { conv = true; break; }
+    }
+    T = t;
+    pr_a<NC>(P, m, t, a, da, d2a);
+    p = PR_RU * t / (v - m.b) - a / (v * v + 2.0 * m.b * v - m.b * m.b);
+    if (!conv) return ERR_NONCONV;
+    return isfinite(p) ? 0 : ERR_NONPHYS;
+}
+
 // ------------------------------------------------------------ closure
 // Thermodynamic-dependent update (Eq. 3-5/3-6, App. B): from the face
 // pressure offset pp = p - p_ref, temperature T and the NC-1 tracked mass
@@ -124,6 +278,16 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
     for (int k = 0; k < NC - 1; ++k) { Y[k] = clip01(Yt[k]); s += Y[k]; }
     Y[NC - 1] = clip01(R(1) - s);
     const ConstT<R>& Kc = K<R>(P);
+    if (P.pr) {
+        double Yd[NC], rd, ed, cd;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) Yd[k] = double(Y[k]);
+        const bool ok = pr_tdu<NC>(P, P.p_ref + double(pp), double(T), Yd, rd, ed, cd);
+        rho = R(rd);
+        e = R(ed);
+        c = R(cd);
+        return ok;
+    }
     R Pk[NC], iP[NC];
     bool ok = T > R(0);
 #pragma unroll
@@ -160,8 +324,8 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
 // carry the p + pinf cancellation and are always formed in FP64.
 // Outputs w = (u_0..u_{ND-1}, p - p_ref, T, Y_0..Y_{NC-2}).
 template <int ND, int NC, typename R>
-__device__ __forceinline__ bool prim_recover(const DevParams& P, const double* qc, R* w, double& rho_d,
-                                             R& T_out, R& p_abs)
+__device__ __forceinline__ int prim_recover(const DevParams& P, const double* qc, R* w, double& rho_d,
+                                            R& T_out, R& p_abs, double T0)
 {
     constexpr int NV = ND + NC + 1;
     (void)NV;
@@ -184,6 +348,22 @@ __device__ __forceinline__ bool prim_recover(const DevParams& P, const double* q
         w[ND + 2 + k] = Y[k];
     }
     Y[NC - 1] = clip01(R(1) - s);
+    if (P.pr) {
+        // Peng-Robinson: FP64 Newton in both forms
+        double ked = 0.0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) ked += 0.5 * qc[1 + d] * qc[1 + d];
+        const double e = (qc[ND + 1] - ked / rho) / rho;
+        double Yd[NC], pd = 0.0, Td = 0.0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) Yd[k] = double(Y[k]);
+        const int st = (rho > 0.0) ? pr_invert<NC>(P, rho, e, Yd, T0, pd, Td) : ERR_NONPHYS;
+        w[ND] = R(pd - P.p_ref);
+        w[ND + 1] = R(Td);
+        T_out = R(Td);
+        p_abs = R(pd);
+        return st;
+    }
     const ConstT<R>& Kc = K<R>(P);
     R cv = R(0), cp = R(0), b = R(0), cc = R(0), se = R(0), eq = R(0);
     R sA = R(0), sB = R(0);
@@ -221,7 +401,7 @@ __device__ __forceinline__ bool prim_recover(const DevParams& P, const double* q
 #pragma unroll
     for (int k = 0; k < NC; ++k)
         if (Y[k] > R(0)) ok = ok && (p + Kc.pinf[k] > R(0));
-    return ok;
+    return ok ? 0 : ERR_NONPHYS;
 }
 
 // ---------------------------------------------------------- reconstruction

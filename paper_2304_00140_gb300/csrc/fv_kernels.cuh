@@ -115,7 +115,12 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             for (int v = 0; v < NV; ++v) qc[v] = A.q[v * P.ntot_q + sc];
             R w[NV], T, pabs;
             double rho;
-            bool ok = prim_recover<ND, NC, R>(P, qc, w, rho, T, pabs);
+            const long long pc = C.poff + ((long long)gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0];
+            // Peng-Robinson Newton starts from this cell's previous temperature
+            const double T0 = P.pr ? double(prim[(ND + 1) * P.ntot_p + pc]) : 0.0;
+            const int rst = prim_recover<ND, NC, R>(P, qc, w, rho, T, pabs, T0);
+            bool ok = rst == 0;
+            if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
 #pragma unroll
             for (int d = 0; d < ND; ++d) if (flip[d]) w[d] = -w[d];
             if (in_disc) {
@@ -134,8 +139,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 ok = tdu<NC, R>(P, w[ND], w[ND + 1], w + ND + 2, rr, e, cs) && ok;
                 if (!in_disc) rr = R(rho);
             }
-            if (!ok) set_err(A.err, ERR_NONPHYS);
-            const long long pc = C.poff + ((long long)gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0];
+            if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
 #pragma unroll
             for (int v = 0; v < NV; ++v) prim[v * P.ntot_p + pc] = w[v];
             if (P.aux_rc) {

@@ -107,8 +107,8 @@ __global__ void cons_to_prim_kernel(IoArgs A)
         const long long o = C.qoff + i;
 #pragma unroll
         for (int v = 0; v < NV; ++v) qc[v] = A.in[v * A.P.ntot_q + o];
-        const bool ok = prim_recover<ND, NC, double>(A.P, qc, w, rho, T, p);
-        if (!ok) set_err(A.err, ERR_NONPHYS);
+        const int st = prim_recover<ND, NC, double>(A.P, qc, w, rho, T, p, 0.0);
+        if (st) set_err(A.err, st);
         w[ND] = p;
 #pragma unroll
         for (int v = 0; v < NV; ++v) A.out[v * A.ncell + i] = w[v];

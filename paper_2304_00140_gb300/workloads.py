@@ -248,11 +248,14 @@ def _init_random(w: Workload):
         W[d] = P.get("u0", [0.0, 0.0, 0.0])[d] + field(P.get("du", 30.0))
     W[w.ndim] = P["p"] * (1.0 + field(P.get("dp_rel", 0.2)))
     W[w.ndim + 1] = P["T"] * (1.0 + field(P.get("dT_rel", 0.1)))
+    Tl = P.get("T_liquid")
     xc = [w.lo[d] + 0.5 * L[d] for d in range(3)]
     r2 = (X - xc[0]) ** 2 + (Y - xc[1]) ** 2
     if w.ndim == 3:
         r2 = r2 + (Z - xc[2]) ** 2
     h = tanh_indicator(np.sqrt(r2) - P["R"] * (1.0 + field(0.3)), P["width"] * w.dx[0])
+    if Tl is not None:        # liquid colder than the gas (temperature blended by the indicator)
+        W[w.ndim + 1] = (Tl * h + W[w.ndim + 1] * (1.0 - h))
     nc = w.ncomp
     if nc == 2:
         W[w.ndim + 2] = 1.0 - h
@@ -276,7 +279,40 @@ def _init_jet(w: Workload):
     return W
 
 
-_INIT = {"column": _init_column, "shock_bubble": _init_shock_bubble,
+def rh_post_shock_ig(p1, T1, Ms, gamma, Rs):
+    """Ideal-gas normal-shock state behind a shock of Mach number Ms moving
+    into gas at rest (p1, T1): pressure and density ratios and u2."""
+    g = gamma
+    pr_ = (2.0 * g * Ms * Ms - (g - 1.0)) / (g + 1.0)
+    rr_ = (g + 1.0) * Ms * Ms / ((g - 1.0) * Ms * Ms + 2.0)
+    c1 = math.sqrt(g * Rs * T1)
+    u2 = Ms * c1 * (1.0 - 1.0 / rr_)
+    return p1 * pr_, T1 * pr_ / rr_, u2
+
+
+def _init_pr_drop(w: Workload):
+    """configs[2]: n-dodecane droplet (radius R) at T_l in N2 at (p, T), Mach
+    Ms shock in the N2 at x_s moving +x.  READING: the post-shock state is
+    the ideal-gas Rankine-Hugoniot state of N2 (gamma = 1 + R/(M cv)); with
+    the PR closure the jump sheds a weak wave."""
+    P = w.params
+    X, Y, _ = _grid(w)
+    n2 = w.comps[0]
+    Rs = 8.314462618 / n2["M"]
+    p2, T2, u2 = rh_post_shock_ig(P["p"], P["T"], P["Ms"], 1.0 + Rs / n2["cv"], Rs)
+    xc, yc = 0.5 * (w.lo[0] + w.hi[0]), 0.5 * (w.lo[1] + w.hi[1])
+    r = np.sqrt((X - xc) ** 2 + (Y - yc) ** 2)
+    h = tanh_indicator(r - P["R"], P["width"] * w.dx[0])   # liquid indicator
+    post = X < P["xs"]
+    W = _alloc(w)
+    W[0] = np.where(post, u2, 0.0)
+    W[w.ndim] = np.where(post, p2, P["p"])
+    W[w.ndim + 1] = np.where(post, T2, P["T_l"] * h + P["T"] * (1.0 - h))
+    W[w.ndim + 2] = 1.0 - h                                 # N2 tracked, dodecane implied
+    return W
+
+
+_INIT = {"pr_drop": _init_pr_drop, "column": _init_column, "shock_bubble": _init_shock_bubble,
          "droplet": _init_droplet, "random": _init_random, "jet": _init_jet}
 
 
@@ -341,19 +377,26 @@ def droplet_ensemble(ncases=1024, seed=SEED, steps=500, **scheme):
     return cases
 
 
-def random_state(n=(24, 20), ncomp=2, seed=SEED, bc=None, ndim=2, **scheme):
+def random_state(n=(24, 20), ncomp=2, seed=SEED, bc=None, ndim=2, pr=False, **scheme):
     """Seeded smooth random state with a material interface for stage-level
-    parity (every branch of the stage is exercised)."""
+    parity (every branch of the stage is exercised).  pr=True: N2 / n-dodecane
+    on Peng-Robinson at 6 MPa, gas near 900 K around a 363 K liquid."""
     nx, ny = n[0], n[1]
     nz = n[2] if ndim == 3 else 1
     L = 1e-3
-    comps = [AIR, WATER] if ncomp == 2 else [N2_IG, CH4_IG, DODECANE_SG]
+    if pr:
+        comps = [N2_PR, DODECANE_PR]
+        params = dict(seed=seed, p=6e6, T=900.0, T_liquid=363.0, dT_rel=0.05, dp_rel=0.1, R=0.3e-3,
+                      width=1.5, du=40.0)
+        scheme = dict(dict(p_ref=6e6, T_ref=900.0), **scheme)
+    else:
+        comps = [AIR, WATER] if ncomp == 2 else [N2_IG, CH4_IG, DODECANE_SG]
+        params = dict(seed=seed, p=2e6, T=320.0, R=0.3e-3, width=1.5, du=40.0)
     bc = bc or [[BC_PERIODIC] * 2, [BC_PERIODIC] * 2, [BC_PERIODIC] * 2]
     return Workload(
         name=f"random_{nx}x{ny}x{nz}", ndim=ndim, n=[nx, ny, nz], lo=[0.0, 0.0, 0.0],
-        hi=[L, L * ny / nx, L * nz / nx], bc=bc, comps=comps, liquid=ncomp - 1,
-        scheme=default_scheme(**scheme), steps=1, cfl=0.4, init="random",
-        params=dict(seed=seed, p=2e6, T=320.0, R=0.3e-3, width=1.5, du=40.0))
+        hi=[L, L * ny / nx, L * nz / nx], bc=bc, comps=comps, liquid=len(comps) - 1,
+        scheme=default_scheme(**scheme), steps=1, cfl=0.4, init="random", params=params)
 
 
 def jet3d(n=(512, 256, 256), steps=1000, seed=SEED, **scheme):
@@ -394,3 +437,19 @@ def jet_inflow_velocity(w: Workload) -> np.ndarray:
     u = np.zeros((3, nz, ny))
     u[0] = P["U"] * (1.0 + P["amp"] * (0.5 * np.sin(4.0 * phi) + 0.5 * rnd))
     return u
+
+
+def pr_shock_droplet(n=1024, steps=2000, **scheme):
+    """2D near-critical shock/droplet on Peng-Robinson: n x n cells of
+    0.115 mm (READING of the unstated spacing), an n-dodecane droplet of
+    radius n/8 cells at 363 K in N2 at 6 MPa and 900 K, a Mach 2 shock in the
+    N2 at x = L/4 moving +x, outflow on every side, FP32-mixed with the FP64
+    Newton inversion.  CFL 0.4."""
+    dx = 0.115e-3
+    L = n * dx
+    sch = default_scheme(**dict(dict(precision=1, p_ref=6e6, T_ref=900.0), **scheme))
+    return Workload(
+        name=f"pr_shock_droplet_{n}x{n}", ndim=2, n=[n, n, 1], lo=[0.0, 0.0, 0.0], hi=[L, L, 1.0],
+        bc=[[BC_OUTFLOW] * 2, [BC_OUTFLOW] * 2, [BC_PERIODIC] * 2], comps=[N2_PR, DODECANE_PR], liquid=1,
+        scheme=sch, steps=steps, cfl=0.4, init="pr_drop",
+        params=dict(p=6e6, T=900.0, T_l=363.0, Ms=2.0, xs=0.25 * L, R=n / 8 * dx, width=1.5))

@@ -45,3 +45,12 @@ def oracle_step_window(o, q, dt, lo, hi):
         o.stage(k, dt, q0, prev, window=(wl_, wh_), out=out)
         prev = out
     return prev
+
+
+def rel_l1_vec(a, b, ndim):
+    """relative L1 per conserved field; the momentum components are measured
+    against the L1 norm of the momentum vector (a component can be ~0)"""
+    nv = a.shape[0]
+    den = np.abs(b).reshape(nv, -1).sum(1)
+    den[1:1 + ndim] = np.sqrt((b[1:1 + ndim] ** 2).sum(0)).sum()
+    return np.abs(a - b).reshape(nv, -1).sum(1) / np.maximum(den, 1e-300)

@@ -54,3 +54,17 @@ def test_workspace_size_and_argument_checks():
     cm3.comp[2] = fv.fv_component(0, 2.0, 5e8, 1000.0, 0, 0, 0, 0, 0)
     assert L.fv_workspace_size(1, g, C.byref(cm3), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
     assert L.fv_status_string(fv.FV_ERR_NONPHYSICAL) == b"FV_ERR_NONPHYSICAL"
+
+
+def test_peng_robinson_argument_checks():
+    L = fv.load()
+    w = wl.pr_shock_droplet(n=32)
+    g = (fv.fv_grid * 1)(fv.make_grid(w))
+    cm, e = fv.make_components(w), fv.make_eos(w.scheme)
+    n = C.c_size_t()
+    assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_OK
+    e2 = fv.make_eos(dict(w.scheme, sigma=0.07))          # CSF needs volume fractions: SG/IG only
+    assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e2), C.byref(n)) == fv.FV_ERR_ARG
+    cm2 = fv.make_components(w)
+    cm2.comp[0] = fv.fv_component(0, 1.4, 0.0, 718.0, 0, 0, 0, 0, 0)   # SG mixed with PR
+    assert L.fv_workspace_size(1, g, C.byref(cm2), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
