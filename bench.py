@@ -148,6 +148,7 @@ def run_form(job, precision, args, torch, dist, rank, world):
     stream = torch.cuda.current_stream()
     s.step_async(args.warmup, w.cfl)
     torch.cuda.synchronize()
+    tile = s.tile()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -176,7 +177,7 @@ def run_form(job, precision, args, torch, dist, rank, world):
     s.profile(False)
     state = np.concatenate([s.get_state(case=i).reshape(job.nvar, -1) for i in range(len(job.cases))], axis=1)
     s.close()
-    return dict(ms=ms, launches=launches, clocks=clocks, err=err, prof=prof, state=state)
+    return dict(ms=ms, launches=launches, clocks=clocks, err=err, prof=prof, state=state, tile=tile)
 
 
 def e2e_form(job, precision, args, torch):
@@ -358,7 +359,7 @@ def main():
         return dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
                     traffic=None, kernel="stage_kernel", avg_launch_ms=avg_ms,
                     algorithmic_bytes_per_launch=byt, peak_source=peaks["src"],
-                    kernel_share={k: v["ms"] for k, v in r["prof"].items()})
+                    kernel_share={k: v["ms"] for k, v in r["prof"].items()}, tile=r["tile"])
 
     head = forms[0]
     hprec = fv.FV_MIXED if head == "mixed" else fv.FV_FP64

@@ -59,7 +59,10 @@ enum { FV_CONSERVED = 0, FV_PRIMITIVE = 1 };
 enum { FV_DIAG_TOTALS = 0,   /* double[nv]: compensated sums of q over the case */
        FV_DIAG_DT = 1,       /* double: last step's dt of the case */
        FV_DIAG_TIME = 2,     /* double: accumulated time of the case */
-       FV_DIAG_ERROR = 3 };  /* int: device error word (bit set of FV_ERRBIT_*) */
+       FV_DIAG_ERROR = 3,    /* int: device error word (bit set of FV_ERRBIT_*) */
+       FV_DIAG_TILE = 4 };   /* double[8]: stage-kernel tile x, y, z, threads chosen by the
+                                autotuner (runs it if not yet run), then the tuner's
+                                per-candidate milliseconds (0 if not timed) */
 enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2 };
 
 /* Grid of one case.  lo/hi are the box corners (m); bc[d][0] is the low
@@ -144,6 +147,12 @@ fv_status fv_get_state_device(fv_ctx* ctx, int icase, int kind, double* dev);
  * (q^k = q^0 + a_k dt R(q^{k-1}); stage 1 starts from the current state,
  * stage 4 writes the new state).  Stages must be called in order. */
 fv_status fv_rk_stage(fv_ctx* ctx, int k, double dt);
+
+/* The first fv_rk_stage / fv_step of a context autotunes the stage kernel's
+ * tile shape on the current state (a few timed launches per candidate that
+ * write only a scratch register; cached per workload class for the process;
+ * FV_TILE=<index> in the environment forces a candidate).  Set the state
+ * first. */
 
 /* nsteps full steps: per step dt = cfl / max(sum_d (|u_d| + c)/dx_d) of each
  * case (computed on the device from the step's initial state), then the four

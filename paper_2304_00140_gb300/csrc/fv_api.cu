@@ -7,6 +7,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -67,7 +69,11 @@ struct fv_ctx {
     cudaStream_t stream = nullptr;          // user stream (0 = legacy default)
     cudaStream_t cap = nullptr;             // private stream used for graph capture
     size_t smem = 0;
-    int stage_grid = 0, prim_grid = 0;
+    int stage_grid = 0, prim_grid = 0, n_items_cur = 0;
+    float tune_ms[NTILES] = {0.f, 0.f, 0.f, 0.f};
+    int tile = 0;                           // stage-kernel tile (TILES2 / TILES3 index)
+    bool tuned = false;
+    int nsm = 0;
     std::vector<std::pair<double, cudaGraphExec_t>> graphs;
     long long launches = 0;
     std::string msg;
@@ -319,7 +325,12 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
         poff += (long long)C.g[0] * C.g[1] * C.g[2];
         L.max_cells = std::max(L.max_cells, ncell);
         if (cases) cases->push_back(C);
-        long long nst = ntiles(C.n, nd), npr = ntiles(gx, nd);
+        long long nst = 0, npr = ntiles(gx, nd);
+        for (int t = 0; t < NTILES; ++t) {
+            const TileDef td = tile_def(nd, t);
+            nst = std::max(nst, (long long)((C.n[0] + td.x - 1) / td.x) * ((C.n[1] + td.y - 1) / td.y) *
+                                    ((C.n[2] + td.z - 1) / td.z));
+        }
         L.n_items_stage += (int)nst;
         L.n_items_prim += (int)npr;
         if (items_stage)
@@ -373,6 +384,111 @@ extern "C" fv_status fv_workspace_size(int ncases, const fv_grid* grids, const f
     plan(ncases, grids, nd, nv, count_nprim(eos, nv), eos->precision == FV_MIXED, L, nullptr, nullptr, nullptr);
     if (bytes) *bytes = L.total;
     return FV_OK;
+}
+
+
+// work list of the stage kernel for one candidate tile
+static void stage_items(const std::vector<CaseDesc>& cases, int nd, int tile, std::vector<int4>& out)
+{
+    const TileDef td = tile_def(nd, tile < NTILES ? tile : 0);
+    out.clear();
+    for (size_t c = 0; c < cases.size(); ++c) {
+        const CaseDesc& C = cases[c];
+        for (int z = 0; z < C.n[2]; z += td.z)
+            for (int y = 0; y < C.n[1]; y += td.y)
+                for (int x = 0; x < C.n[0]; x += td.x) out.push_back(make_int4((int)c, x, y, z));
+    }
+}
+
+static fv_status apply_tile(fv_ctx* x, int tile)
+{
+    if (x->P.pr) tile = NTILES;   // the Peng-Robinson kernel has the default tile only
+    std::vector<int4> it;
+    stage_items(x->cases, x->nd, tile, it);
+    if ((long long)it.size() > x->L.n_items_stage) return fail(x, FV_ERR_STATE, "work list overflow%s");
+    CK(x, cudaMemcpy(x->d_items_stage, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
+    const size_t smem = stage_smem(x->nd, x->nc, x->mixed, tile, x->nprim);
+    CK(x, stage_set_smem(x->nd, x->nc, x->mixed, tile, smem));
+    const int occ = stage_occupancy(x->nd, x->nc, x->mixed, tile, smem);
+    if (occ < 1) return fail(x, FV_ERR_CUDA, "stage kernel tile cannot be resident%s");
+    x->tile = tile;
+    x->smem = smem;
+    x->n_items_cur = (int)it.size();
+    x->stage_grid = (int)std::min<long long>((long long)it.size(), (long long)x->nsm * occ);
+    return FV_OK;
+}
+
+// Tile autotuner: time every candidate tile of the stage kernel on this
+// context's cases (current state, one primitive pass, 1 warm-up and 3 timed
+// launches each, writing only the scratch register q^B) and keep the
+// fastest.  Results are cached per workload class for the process; the
+// environment variable FV_TILE=<index> forces a tile.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+}
+
+static std::string tune_key(const fv_ctx* x)
+{
+    long long cells = x->L.ntot_q;
+    int lg = 0;
+    while ((1LL << (lg + 1)) <= cells) ++lg;
+    char buf[160];
+    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%d/%d", x->nd, x->nc, x->mixed, x->P.iles, x->P.csf, x->P.pr,
+             x->ncases > 64 ? 2 : (x->ncases > 1 ? 1 : 0), lg);
+    return buf;
+}
+
+static fv_status tune(fv_ctx* x)
+{
+    if (x->tuned) return FV_OK;
+    x->tuned = true;
+    if (x->P.pr) return apply_tile(x, NTILES);
+    if (const char* f = getenv("FV_TILE")) {
+        const int t = atoi(f);
+        if (t >= 0 && t < NTILES) return apply_tile(x, t);
+    }
+    const std::string key = tune_key(x);
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) return apply_tile(x, it->second);
+    }
+    int err0 = 0;
+    CK(x, cudaStreamSynchronize(x->stream));
+    CK(x, cudaMemcpy(&err0, x->err, sizeof(int), cudaMemcpyDeviceToHost));
+    PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, x->Q0, x->prim, x->in_u, nullptr, x->err};
+    CK(x, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, x->stream));
+    cudaEvent_t e0, e1;
+    CK(x, cudaEventCreate(&e0));
+    CK(x, cudaEventCreate(&e1));
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int t = 0; t < NTILES; ++t) {
+        fv_status s = apply_tile(x, t);
+        if (s) { x->msg.clear(); continue; }
+        StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, x->Q0, x->QB, x->dt, 0.0, x->err};
+        float tmin = 1e30f;
+        for (int r = 0; r < 4; ++r) {
+            CK(x, cudaEventRecord(e0, x->stream));
+            CK(x, launch_stage(x->nd, x->nc, x->mixed, t, sa, x->stage_grid, x->smem, x->stream));
+            CK(x, cudaEventRecord(e1, x->stream));
+            CK(x, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(x, cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) tmin = std::min(tmin, ms);
+        }
+        x->tune_ms[t] = tmin;
+        if (tmin < best_ms) { best_ms = tmin; best = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(x, cudaMemcpy(x->err, &err0, sizeof(int), cudaMemcpyHostToDevice));
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    return apply_tile(x, best);
 }
 
 static fv_status init_common(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
@@ -432,7 +548,6 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     x->partial = reinterpret_cast<double*>(b + L.partial);
     CK(x, cudaStreamCreateWithFlags(&x->cap, cudaStreamNonBlocking));
     CK(x, cudaMemcpy(x->d_cases, x->cases.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice));
-    CK(x, cudaMemcpy(x->d_items_stage, ist.data(), sizeof(int4) * ist.size(), cudaMemcpyHostToDevice));
     CK(x, cudaMemcpy(x->d_items_prim, ipr.data(), sizeof(int4) * ipr.size(), cudaMemcpyHostToDevice));
     CK(x, cudaMemset(x->smax, 0, sizeof(unsigned long long) * ncases));
     CK(x, cudaMemset(x->dt, 0, sizeof(double) * ncases));
@@ -448,12 +563,13 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     int dev = 0, nsm = 0;
     CK(x, cudaGetDevice(&dev));
     CK(x, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    x->smem = stage_smem(x->nd, x->nc, x->mixed, x->nprim);
-    CK(x, stage_set_smem(x->nd, x->nc, x->mixed, x->smem));
-    const int occ_s = stage_occupancy(x->nd, x->nc, x->mixed, x->smem);
+    x->nsm = nsm;
     const int occ_p = prim_occupancy(x->nd, x->nc, x->mixed);
-    x->stage_grid = std::min(L.n_items_stage, std::max(1, nsm * occ_s));
     x->prim_grid = std::min(L.n_items_prim, std::max(1, nsm * occ_p));
+    {
+        fv_status s = apply_tile(x, 0);
+        if (s) return s;
+    }
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }
@@ -628,9 +744,9 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
         PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
         x->launches++;
     }
-    StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->L.n_items_stage, x->prim, x->Q0, out, x->dt,
+    StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, x->Q0, out, x->dt,
                  LSRK_A[k - 1], x->err};
-    PROF(FV_KERNEL_STAGE, launch_stage(x->nd, x->nc, x->mixed, sa, x->stage_grid, x->smem, s));
+    PROF(FV_KERNEL_STAGE, launch_stage(x->nd, x->nc, x->mixed, x->tile, sa, x->stage_grid, x->smem, s));
     x->launches++;
     return FV_OK;
 }
@@ -640,6 +756,8 @@ extern "C" fv_status fv_rk_stage(fv_ctx* x, int k, double dt)
     fv_status s = case_ok(x, 0);
     if (s) return s;
     if (k < 1 || k > 4) return fail(x, FV_ERR_ARG, "stage index must be 1..4%s");
+    s = tune(x);
+    if (s) return s;
     if (k == 1) {
         if (!(dt > 0.0)) return fail(x, FV_ERR_ARG, "dt must be positive%s");
         CK(x, launch_fill(x->dt, x->ncases, dt, x->stream));
@@ -689,6 +807,8 @@ extern "C" fv_status fv_step_async(fv_ctx* x, int nsteps, double cfl)
     fv_status s = case_ok(x, 0);
     if (s) return s;
     if (nsteps < 0 || !(cfl > 0.0)) return fail(x, FV_ERR_ARG, "need nsteps >= 0 and cfl > 0%s");
+    s = tune(x);
+    if (s) return s;
     if (x->profiling) {
         for (int i = 0; i < nsteps; ++i)
             for (int k = 1; k <= 4; ++k) {
@@ -743,6 +863,15 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
     if (what == FV_DIAG_DT || what == FV_DIAG_TIME) {
         CK(x, cudaStreamSynchronize(x->stream));
         CK(x, cudaMemcpy(out, (what == FV_DIAG_DT ? x->dt : x->t) + icase, sizeof(double), cudaMemcpyDeviceToHost));
+        return FV_OK;
+    }
+    if (what == FV_DIAG_TILE) {
+        s = tune(x);
+        if (s) return s;
+        const TileDef td = tile_def(x->nd, x->tile < NTILES ? x->tile : 0);
+        double* o = static_cast<double*>(out);
+        o[0] = td.x; o[1] = td.y; o[2] = td.z; o[3] = td.nt;
+        for (int t = 0; t < NTILES; ++t) o[4 + t] = x->tune_ms[t];
         return FV_OK;
     }
     if (what == FV_DIAG_ERROR) {
@@ -939,9 +1068,9 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
 
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FV_ERR_CUDA;
-    const size_t smem = stage_smem(x.nd, x.nc, x.mixed, x.nprim);
-    if (stage_set_smem(x.nd, x.nc, x.mixed, smem) != cudaSuccess) return FV_ERR_CUDA;
-    const int gs = (int)std::min<long long>(n_st, (long long)nsm * stage_occupancy(x.nd, x.nc, x.mixed, smem));
+    const size_t smem = stage_smem(x.nd, x.nc, x.mixed, 0, x.nprim);
+    if (stage_set_smem(x.nd, x.nc, x.mixed, 0, smem) != cudaSuccess) return FV_ERR_CUDA;
+    const int gs = (int)std::min<long long>(n_st, (long long)nsm * stage_occupancy(x.nd, x.nc, x.mixed, 0, smem));
     const int gp = (int)std::min<long long>(n_pr, (long long)nsm * prim_occupancy(x.nd, x.nc, x.mixed));
     const int nsetup = (int)std::min<long long>(1024, (std::max(n_st, n_pr) + 255) / 256);
 
@@ -951,7 +1080,7 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
     PrimArgs pa{x.P, dcase, ipr, (int)n_pr, qprev, prim, nullptr, nullptr, derr};
     if (launch_prim(x.nd, x.nc, x.mixed, pa, gp, s) != cudaSuccess) return FV_ERR_CUDA;
     StageArgs sa{x.P, dcase, ist, (int)n_st, prim, q0, qout, ddt, LSRK_A[k - 1], derr};
-    if (launch_stage(x.nd, x.nc, x.mixed, sa, gs, smem, s) != cudaSuccess) return FV_ERR_CUDA;
+    if (launch_stage(x.nd, x.nc, x.mixed, 0, sa, gs, smem, s) != cudaSuccess) return FV_ERR_CUDA;
     int e = 0;
     if (cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FV_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return FV_ERR_CUDA;

@@ -270,7 +270,7 @@ __device__ __forceinline__ int pr_invert(const DevParams& P, double rho, double 
 //   1/(rho c^2) = sum_k alpha_k / (gamma_k (p + pinf_k))   (Wood)
 // Returns false for a non-physical input (T <= 0, p + pinf_k <= 0 for a
 // present component, NaN).
-template <int NC, typename R>
+template <int NC, typename R, bool PRC>
 __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, R& rho, R& e, R& c)
 {
     R Y[NC], s = R(0);
@@ -278,7 +278,7 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
     for (int k = 0; k < NC - 1; ++k) { Y[k] = clip01(Yt[k]); s += Y[k]; }
     Y[NC - 1] = clip01(R(1) - s);
     const ConstT<R>& Kc = K<R>(P);
-    if (P.pr) {
+    if constexpr (PRC) {
         double Yd[NC], rd, ed, cd;
 #pragma unroll
         for (int k = 0; k < NC; ++k) Yd[k] = double(Y[k]);
@@ -323,7 +323,7 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
 // p = -sum_k Y_k cv_k E_k / cv.  Then T = (rho e' + p) / (rho cp).  The E_k
 // carry the p + pinf cancellation and are always formed in FP64.
 // Outputs w = (u_0..u_{ND-1}, p - p_ref, T, Y_0..Y_{NC-2}).
-template <int ND, int NC, typename R>
+template <int ND, int NC, typename R, bool PRC>
 __device__ __forceinline__ int prim_recover(const DevParams& P, const double* qc, R* w, double& rho_d,
                                             R& T_out, R& p_abs, double T0)
 {
@@ -348,7 +348,7 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const double* qc
         w[ND + 2 + k] = Y[k];
     }
     Y[NC - 1] = clip01(R(1) - s);
-    if (P.pr) {
+    if constexpr (PRC) {
         // Peng-Robinson: FP64 Newton in both forms
         double ked = 0.0;
 #pragma unroll
@@ -476,7 +476,7 @@ __device__ __forceinline__ R thinc_side(const DevParams& P, R xa, R xc, R xb, bo
 // F receives (rho, rho u_0.., rho E, rho Y..) fluxes.  In the mixed form the
 // constant p_ref is left out of the normal-momentum flux (it cancels in every
 // cell's flux difference).
-template <int ND, int NC, typename R>
+template <int ND, int NC, typename R, bool PRC>
 __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*ws)[ND + NC + 1], const R* rho4,
                                           const R* c4, int f, R* F)
 {
@@ -504,8 +504,8 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
         }
     }
     R rL, eL, cL, rR, eR, cR;
-    bool ok = tdu<NC, R>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
-    ok = tdu<NC, R>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
+    bool ok = tdu<NC, R, PRC>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
+    ok = tdu<NC, R, PRC>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
     const R pL = WL[IP], pR = WR[IP], uL = WL[d], uR = WR[d];
     R us, ps;
     if (P.iles) {

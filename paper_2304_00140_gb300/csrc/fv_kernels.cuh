@@ -41,12 +41,19 @@ struct StageArgs {
     int* err;
 };
 
-// Tile of the stage kernel and its thread count: NT covers the tile's
-// faces ((TX+1)TY + TX(TY+1) in 2D) in two nearly full rounds.
+// Tile of the prim kernel (one thread per ghosted cell, 256 threads).
 template <int ND> struct TileShape;
-template <> struct TileShape<2> { static constexpr int X = 32, Y = 8, Z = 1, NT = 288; };
+template <> struct TileShape<2> { static constexpr int X = 32, Y = 8, Z = 1, NT = 256; };
 template <> struct TileShape<3> { static constexpr int X = 32, Y = 4, Z = 2, NT = 256; };
-constexpr int PRIM_THREADS = 256;   // prim kernel: one thread per ghosted cell of a 32x8 / 32x4x2 tile
+
+// Candidate tiles of the stage kernel, chosen per workload by the autotuner.
+// NT (threads) is sized so the tile's faces take about two or three full
+// rounds; tile 0 is the default.
+struct TileDef { int x, y, z, nt; };
+constexpr int NTILES = 4;
+constexpr TileDef TILES2[NTILES] = {{32, 8, 1, 288}, {32, 16, 1, 544}, {64, 8, 1, 576}, {16, 16, 1, 288}};
+constexpr TileDef TILES3[NTILES] = {{32, 4, 2, 256}, {16, 4, 4, 320}, {16, 8, 2, 320}, {32, 4, 4, 608}};
+constexpr TileDef tile_def(int nd, int i) { return nd == 2 ? TILES2[i] : TILES3[i]; }
 
 __device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& flip, int& inflow)
 {
@@ -74,7 +81,7 @@ __device__ __forceinline__ void set_err(int* err, int bit)
 }
 
 // ----------------------------------------------------------------- prims
-template <int ND, int NC, typename R>
+template <int ND, int NC, typename R, bool PRC>
 __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 {
     constexpr int NV = ND + NC + 1;
@@ -117,8 +124,8 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             double rho;
             const long long pc = C.poff + ((long long)gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0];
             // Peng-Robinson Newton starts from this cell's previous temperature
-            const double T0 = P.pr ? double(prim[(ND + 1) * P.ntot_p + pc]) : 0.0;
-            const int rst = prim_recover<ND, NC, R>(P, qc, w, rho, T, pabs, T0);
+            const double T0 = PRC ? double(prim[(ND + 1) * P.ntot_p + pc]) : 0.0;
+            const int rst = prim_recover<ND, NC, R, PRC>(P, qc, w, rho, T, pabs, T0);
             bool ok = rst == 0;
             if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
 #pragma unroll
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             const bool need_c = P.aux_rc || A.smax || in_disc;
             if (need_c) {
                 R e;
-                ok = tdu<NC, R>(P, w[ND], w[ND + 1], w + ND + 2, rr, e, cs) && ok;
+                ok = tdu<NC, R, PRC>(P, w[ND], w[ND + 1], w + ND + 2, rr, e, cs) && ok;
                 if (!in_disc) rr = R(rho);
             }
             if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
@@ -181,13 +188,10 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 }
 
 // ------------------------------------------------------------------ stage
-template <int ND, int NC, typename R>
-__global__ void __launch_bounds__(TileShape<ND>::NT, 2) stage_kernel(StageArgs A)
+template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, bool PRC>
+__global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArgs A)
 {
     constexpr int NV = ND + NC + 1;
-    using TS = TileShape<ND>;
-    constexpr int TX = TS::X, TY = TS::Y, TZ = TS::Z;
-    constexpr int NT = TS::NT;
     constexpr int NCELL = TX * TY * TZ;
     constexpr int HX = TX + 4, HY = TY + 4, HZ = (ND == 3) ? TZ + 4 : 1;
     constexpr int HC = HX * HY * HZ;
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(TileShape<ND>::NT, 2) stage_kernel(StageArgs A
                 fl = (sflag[h0 + st] | sflag[h0 + 2 * st]) ? 1 : 0;
             }
             R F[NV];
-            const bool ok = face_flux<ND, NC, R>(P, d, ws, r4, c4, fl, F);
+            const bool ok = face_flux<ND, NC, R, PRC>(P, d, ws, r4, c4, fl, F);
             if (!ok) set_err(A.err, ERR_NONPHYS);
             // store at face index (fx, fy, fz) of the full tile face array
             int fi;
@@ -438,12 +442,10 @@ __global__ void __launch_bounds__(TileShape<ND>::NT, 2) stage_kernel(StageArgs A
 }
 
 // dynamic shared memory of stage_kernel
-template <int ND, int NC, typename R>
+template <int ND, int NC, typename R, int TX, int TY, int TZ>
 inline size_t stage_smem_bytes(int nprim)
 {
     constexpr int NV = ND + NC + 1;
-    using TS = TileShape<ND>;
-    constexpr int TX = TS::X, TY = TS::Y, TZ = TS::Z;
     constexpr int HC = (TX + 4) * (TY + 4) * ((ND == 3) ? TZ + 4 : 1);
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
     constexpr int AC = (TX + 2) * (TY + 2) * ((ND == 3) ? TZ + 2 : 1);

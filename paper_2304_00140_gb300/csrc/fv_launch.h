@@ -10,10 +10,12 @@ namespace tfv {
 
 // prim kernel and stage kernel, dispatched on (ndim, ncomp, mixed)
 cudaError_t launch_prim(int nd, int nc, int mixed, const PrimArgs& A, int grid, cudaStream_t s);
-cudaError_t launch_stage(int nd, int nc, int mixed, const StageArgs& A, int grid, size_t smem, cudaStream_t s);
-size_t stage_smem(int nd, int nc, int mixed, int nprim);
-cudaError_t stage_set_smem(int nd, int nc, int mixed, size_t smem);
-int stage_occupancy(int nd, int nc, int mixed, size_t smem);   // resident blocks per SM
+// `tile` indexes the candidate tiles (TILES2 / TILES3)
+cudaError_t launch_stage(int nd, int nc, int mixed, int tile, const StageArgs& A, int grid, size_t smem,
+                         cudaStream_t s);
+size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim);
+cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem);
+int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem);   // resident blocks per SM (0: cannot run)
 int prim_occupancy(int nd, int nc, int mixed);
 
 // state I/O and diagnostics (FP64)

@@ -4,18 +4,34 @@
 
 namespace tfv {
 
-cudaError_t launch_stage2(int nc, int mixed, const StageArgs& A, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_stage3(int nc, int mixed, const StageArgs& A, int grid, size_t smem, cudaStream_t s);
-cudaError_t set_smem2(int nc, int mixed, size_t smem);
-cudaError_t set_smem3(int nc, int mixed, size_t smem);
-size_t smem2(int nc, int mixed, int nprim);
-size_t smem3(int nc, int mixed, int nprim);
-int occupancy2(int nc, int mixed, size_t smem);
-int occupancy3(int nc, int mixed, size_t smem);
+#define FV_DECL(sfx)                                                                                  \
+    cudaError_t launch_stage_##sfx(int nc, int tile, const StageArgs& A, int grid, size_t smem, cudaStream_t s); \
+    cudaError_t set_smem_##sfx(int nc, int tile, size_t smem);                                                \
+    int occupancy_##sfx(int nc, int tile, size_t smem);                                                       \
+    size_t smem_##sfx(int nc, int tile, int nprim);
+FV_DECL(2d)
+FV_DECL(2f)
+FV_DECL(3d)
+FV_DECL(3f)
+#undef FV_DECL
 
-int stage_occupancy(int nd, int nc, int mixed, size_t smem)
+#define FV_PICK(fn, ...)                                                                 \
+    (nd == 2 ? (mixed ? fn##_2f(__VA_ARGS__) : fn##_2d(__VA_ARGS__))                    \
+             : (mixed ? fn##_3f(__VA_ARGS__) : fn##_3d(__VA_ARGS__)))
+
+cudaError_t launch_stage(int nd, int nc, int mixed, int tile, const StageArgs& A, int grid, size_t smem,
+                         cudaStream_t s)
 {
-    return nd == 2 ? occupancy2(nc, mixed, smem) : occupancy3(nc, mixed, smem);
+    return FV_PICK(launch_stage, nc, tile, A, grid, smem, s);
+}
+size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim) { return FV_PICK(smem, nc, tile, nprim); }
+cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem)
+{
+    return FV_PICK(set_smem, nc, tile, smem);
+}
+int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem)
+{
+    return FV_PICK(occupancy, nc, tile, smem);
 }
 
 int prim_occupancy(int nd, int nc, int mixed);
@@ -23,7 +39,8 @@ int prim_occupancy(int nd, int nc, int mixed);
 template <int ND, int NC, typename R>
 static cudaError_t gop(const PrimArgs& A, int grid, cudaStream_t s)
 {
-    prim_kernel<ND, NC, R><<<grid, 256, 0, s>>>(A);
+    if (A.P.pr) prim_kernel<ND, NC, R, true><<<grid, 256, 0, s>>>(A);
+    else prim_kernel<ND, NC, R, false><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -40,7 +57,8 @@ template <int ND, int NC, typename R>
 static int pocc()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prim_kernel<ND, NC, R>, 256, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prim_kernel<ND, NC, R, false>, 256, 0) != cudaSuccess)
+        return 1;
     return n < 1 ? 1 : n;
 }
 
@@ -50,21 +68,6 @@ int prim_occupancy(int nd, int nc, int mixed)
     if (nd == 2 && nc == 3) return mixed ? pocc<2, 3, float>() : pocc<2, 3, double>();
     if (nd == 3 && nc == 2) return mixed ? pocc<3, 2, float>() : pocc<3, 2, double>();
     return mixed ? pocc<3, 3, float>() : pocc<3, 3, double>();
-}
-
-cudaError_t launch_stage(int nd, int nc, int mixed, const StageArgs& A, int grid, size_t smem, cudaStream_t s)
-{
-    return nd == 2 ? launch_stage2(nc, mixed, A, grid, smem, s) : launch_stage3(nc, mixed, A, grid, smem, s);
-}
-
-size_t stage_smem(int nd, int nc, int mixed, int nprim)
-{
-    return nd == 2 ? smem2(nc, mixed, nprim) : smem3(nc, mixed, nprim);
-}
-
-cudaError_t stage_set_smem(int nd, int nc, int mixed, size_t smem)
-{
-    return nd == 2 ? set_smem2(nc, mixed, smem) : set_smem3(nc, mixed, smem);
 }
 
 // ----------------------------------------------------------- state I/O
@@ -80,7 +83,8 @@ __global__ void prim_to_cons_kernel(IoArgs A)
 #pragma unroll
         for (int v = 0; v < NV; ++v) w[v] = A.in[v * A.ncell + i];
         double rho, e, c;
-        const bool ok = tdu<NC, double>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c);
+        const bool ok = A.P.pr ? tdu<NC, double, true>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c)
+                               : tdu<NC, double, false>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c);
         if (!ok) set_err(A.err, ERR_NONPHYS);
         double ke = 0.0;
 #pragma unroll
@@ -107,7 +111,8 @@ __global__ void cons_to_prim_kernel(IoArgs A)
         const long long o = C.qoff + i;
 #pragma unroll
         for (int v = 0; v < NV; ++v) qc[v] = A.in[v * A.P.ntot_q + o];
-        const int st = prim_recover<ND, NC, double>(A.P, qc, w, rho, T, p, 0.0);
+        const int st = A.P.pr ? prim_recover<ND, NC, double, true>(A.P, qc, w, rho, T, p, 0.0)
+                              : prim_recover<ND, NC, double, false>(A.P, qc, w, rho, T, p, 0.0);
         if (st) set_err(A.err, st);
         w[ND] = p;
 #pragma unroll

@@ -22,7 +22,7 @@ MAX_COMP = 3
 FV_OK, FV_ERR_ARG, FV_ERR_ALLOC, FV_ERR_CUDA, FV_ERR_EOS_NONCONV, FV_ERR_NONPHYSICAL, FV_ERR_STATE = range(7)
 FV_FP64, FV_MIXED = 0, 1
 FV_CONSERVED, FV_PRIMITIVE = 0, 1
-FV_DIAG_TOTALS, FV_DIAG_DT, FV_DIAG_TIME, FV_DIAG_ERROR = range(4)
+FV_DIAG_TOTALS, FV_DIAG_DT, FV_DIAG_TIME, FV_DIAG_ERROR, FV_DIAG_TILE = range(5)
 
 # every exported function of the ABI (checked against include/thinc_fv.h by the tests)
 EXPORTS = ["fv_workspace_size", "fv_init", "fv_init_ws", "fv_destroy", "fv_set_stream", "fv_set_state",
@@ -268,6 +268,11 @@ class Solver:
         out = np.zeros(1)
         self._check(self.L.fv_get_diag(self.ctx, case, what, _dptr(out)))
         return float(out[0])
+
+    def tile(self) -> dict:
+        out = np.zeros(8)
+        self._check(self.L.fv_get_diag(self.ctx, 0, FV_DIAG_TILE, _dptr(out)))
+        return dict(tile=[int(v) for v in out[:3]], threads=int(out[3]), tune_ms=out[4:].tolist())
 
     def error_word(self) -> int:
         out = C.c_int()
