@@ -55,6 +55,10 @@ class Job:
         self.ndim = cases[0].ndim
 
 
+def _workload_cases(args):
+    return [None] * (args.ncases if args.workload == "droplet_ensemble" else 1)
+
+
 def _workload(args):
     from paper_2304_00140_gb300 import workloads as wl
     k = args.workload
@@ -164,9 +168,8 @@ def run_form(job, precision, args, torch, dist, rank, world):
     launches = s.launch_count() - l0
     ms = e0.elapsed_time(e1)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        from paper_2304_00140_gb300 import replicas
+        ms = replicas.max_over_ranks(ms, dist, device="cuda")
         dist.barrier()
     err = s.error_word()
     # per-kernel times with event pairs on the launching stream (no graph)
@@ -325,6 +328,11 @@ def main():
     from paper_2304_00140_gb300 import fv
     fv.load()
     job = _workload(args)
+    if dist and len(job.cases) > 1:
+        # a batch is split across ranks (longest-processing-time on cells)
+        from paper_2304_00140_gb300 import replicas
+        mine = replicas.lpt_partition([c.cells for c in job.cases], world)[rank]
+        job = Job(job.name, [job.cases[i] for i in mine])
     job.prims = [c.primitives() for c in job.cases]
     w = job.w
     peaks = _peaks()
@@ -364,11 +372,15 @@ def main():
     head = forms[0]
     hprec = fv.FV_MIXED if head == "mixed" else fv.FV_FP64
     hsteps = args.steps if head == "mixed" else fargs.steps
-    cells_all = job.cells * world
+    if dist:
+        from paper_2304_00140_gb300 import replicas
+        cells_all = replicas.sum_over_ranks(job.cells, dist, device="cuda")
+    else:
+        cells_all = job.cells
     val = cells_all * hsteps / (res[head]["ms"] * 1e-3)
     e2e = e2e_form(job, hprec, args, torch) if rank == 0 else None
     if e2e is not None:
-        e2e["value"] *= world
+        e2e["value"] *= cells_all / job.cells
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -384,7 +396,9 @@ def main():
             ms_per_step=res[head]["ms"] / hsteps, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f32+f64" if head == "mixed" else "f64", data="synthetic",
             config=dict(workload=job.name, cases=len(job.cases), grid=w.n[:w.ndim], cells=job.cells, cfl=job.cfl,
-                        precision=head, parallelism=f"replicas{world}",
+                        precision=head,
+                        parallelism=(f"batch split over {world} ranks" if len(_workload_cases(args)) > 1 else
+                                     f"replicas{world}") if world > 1 else "single GPU",
                         l2=("inputs larger than L2" if regbytes > 129e6 else "inputs smaller than L2") +
                         f" (3 FP64 registers of {regbytes / 1e6:.0f} MB each plus primitives)"),
             roofline=roof(res[head], hprec), cpu_baseline=cpu, e2e=e2e,

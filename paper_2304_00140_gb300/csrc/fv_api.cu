@@ -48,6 +48,7 @@ long long ntiles(const int* ext, int nd)
 
 struct fv_ctx {
     int ncases = 0, nd = 0, nc = 0, nv = 0, nprim = 0, mixed = 0;
+    int ff = 0;                             // float-float LSRK registers (the mixed form of a context)
     DevParams P{};
     std::vector<fv_grid> grids;
     std::vector<CaseDesc> cases;
@@ -72,6 +73,7 @@ struct fv_ctx {
     int stage_grid = 0, prim_grid = 0, n_items_cur = 0;
     float tune_ms[NTILES] = {0.f, 0.f, 0.f, 0.f};
     int tile = 0;                           // stage-kernel tile (TILES2 / TILES3 index)
+    size_t smem_max = 0;                    // opt-in shared memory per block of the device
     bool tuned = false;
     int nsm = 0;
     std::vector<std::pair<double, cudaGraphExec_t>> graphs;
@@ -267,6 +269,13 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
             Kt.q[k] = T(d.q);
             Kt.pinf[k] = T(d.pinf);
             Kt.pother[k] = T(d.pother);
+            // gamma - 1 and gamma pinf split into a float-float pair
+            const double gm1 = d.gamma - 1.0, gpi = d.gamma * d.pinf + P.p_ref;
+            Kt.Po[k] = T(d.pother + P.p_ref);
+            Kt.gm1_hi[k] = T(gm1);
+            Kt.gm1_lo[k] = T(gm1 - double(T(gm1)));
+            Kt.gpi_hi[k] = T(gpi);
+            Kt.gpi_lo[k] = T(gpi - double(T(gpi)));
         }
         Kt.p_ref = T(P.p_ref);
         Kt.beta = T(P.beta);
@@ -407,9 +416,10 @@ static fv_status apply_tile(fv_ctx* x, int tile)
     stage_items(x->cases, x->nd, tile, it);
     if ((long long)it.size() > x->L.n_items_stage) return fail(x, FV_ERR_STATE, "work list overflow%s");
     CK(x, cudaMemcpy(x->d_items_stage, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
-    const size_t smem = stage_smem(x->nd, x->nc, x->mixed, tile, x->nprim);
-    CK(x, stage_set_smem(x->nd, x->nc, x->mixed, tile, smem));
-    const int occ = stage_occupancy(x->nd, x->nc, x->mixed, tile, smem);
+    const size_t smem = stage_smem(x->nd, x->nc, x->mixed, tile, x->nprim, x->ff);
+    if (smem > x->smem_max) return fail(x, FV_ERR_ARG, "stage kernel tile does not fit in shared memory%s");
+    CK(x, stage_set_smem(x->nd, x->nc, x->mixed, tile, smem, x->ff));
+    const int occ = stage_occupancy(x->nd, x->nc, x->mixed, tile, smem, x->ff);
     if (occ < 1) return fail(x, FV_ERR_CUDA, "stage kernel tile cannot be resident%s");
     x->tile = tile;
     x->smem = smem;
@@ -458,7 +468,7 @@ static fv_status tune(fv_ctx* x)
     CK(x, cudaStreamSynchronize(x->stream));
     CK(x, cudaMemcpy(&err0, x->err, sizeof(int), cudaMemcpyDeviceToHost));
     PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, x->Q0, x->prim, x->in_u, nullptr, x->err};
-    CK(x, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, x->stream));
+    CK(x, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, x->stream, x->ff));
     cudaEvent_t e0, e1;
     CK(x, cudaEventCreate(&e0));
     CK(x, cudaEventCreate(&e1));
@@ -471,7 +481,7 @@ static fv_status tune(fv_ctx* x)
         float tmin = 1e30f;
         for (int r = 0; r < 4; ++r) {
             CK(x, cudaEventRecord(e0, x->stream));
-            CK(x, launch_stage(x->nd, x->nc, x->mixed, t, sa, x->stage_grid, x->smem, x->stream));
+            CK(x, launch_stage(x->nd, x->nc, x->mixed, t, sa, x->stage_grid, x->smem, x->stream, x->ff));
             CK(x, cudaEventRecord(e1, x->stream));
             CK(x, cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -510,6 +520,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     x->nc = comps->ncomp;
     x->nv = x->nd + x->nc + 1;
     x->mixed = eos->precision == FV_MIXED;
+    x->ff = x->mixed;
     x->grids.assign(grids, grids + ncases);
     build_params(x, comps, eos);
     std::vector<int4> ist, ipr;
@@ -564,10 +575,15 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     CK(x, cudaGetDevice(&dev));
     CK(x, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     x->nsm = nsm;
+    int smax = 0;
+    CK(x, cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    x->smem_max = (size_t)smax;
     const int occ_p = prim_occupancy(x->nd, x->nc, x->mixed);
     x->prim_grid = std::min(L.n_items_prim, std::max(1, nsm * occ_p));
     {
-        fv_status s = apply_tile(x, 0);
+        // the first candidate tile that fits is the default until the tuner runs
+        fv_status s = FV_ERR_ARG;
+        for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
     CK(x, cudaDeviceSynchronize());
@@ -635,13 +651,17 @@ static fv_status set_state_impl(fv_ctx* x, int c, int kind, const double* src, c
     if (!src) return fail(x, FV_ERR_ARG, "null state pointer%s");
     const long long n = case_cells(x, c);
     const CaseDesc& C = x->cases[c];
-    if (kind == FV_CONSERVED) {
+    if (kind == FV_CONSERVED && !x->ff) {
         CK(x, cudaMemcpy2DAsync(x->Q0 + C.qoff, sizeof(double) * x->L.ntot_q, src, sizeof(double) * n,
                                 sizeof(double) * n, x->nv, mk, x->stream));
+    } else if (kind == FV_CONSERVED) {
+        CK(x, cudaMemcpyAsync(x->io, src, sizeof(double) * x->nv * n, mk, x->stream));
+        CK(x, launch_split(x->nv, x->io, n, x->Q0, x->L.ntot_q, C.qoff, x->stream));
+        x->launches++;
     } else if (kind == FV_PRIMITIVE) {
         CK(x, cudaMemcpyAsync(x->io, src, sizeof(double) * x->nv * n, mk, x->stream));
         IoArgs A{x->P, x->d_cases, c, n, x->io, x->Q0, x->err};
-        CK(x, launch_prim_to_cons(x->nd, x->nc, A, x->stream));
+        CK(x, launch_prim_to_cons(x->nd, x->nc, A, x->stream, x->ff));
         x->launches++;
     } else {
         return fail(x, FV_ERR_ARG, "bad state kind%s");
@@ -661,12 +681,16 @@ static fv_status get_state_impl(fv_ctx* x, int c, int kind, double* dst, cudaMem
     if (!dst) return fail(x, FV_ERR_ARG, "null state pointer%s");
     const long long n = case_cells(x, c);
     const CaseDesc& C = x->cases[c];
-    if (kind == FV_CONSERVED) {
+    if (kind == FV_CONSERVED && !x->ff) {
         CK(x, cudaMemcpy2DAsync(dst, sizeof(double) * n, x->Q0 + C.qoff, sizeof(double) * x->L.ntot_q,
                                 sizeof(double) * n, x->nv, mk, x->stream));
+    } else if (kind == FV_CONSERVED) {
+        CK(x, launch_join(x->nv, x->Q0, x->L.ntot_q, C.qoff, n, x->io, x->stream));
+        x->launches++;
+        CK(x, cudaMemcpyAsync(dst, x->io, sizeof(double) * x->nv * n, mk, x->stream));
     } else if (kind == FV_PRIMITIVE) {
         IoArgs A{x->P, x->d_cases, c, n, x->Q0, x->io, x->err};
-        CK(x, launch_cons_to_prim(x->nd, x->nc, A, x->stream));
+        CK(x, launch_cons_to_prim(x->nd, x->nc, A, x->stream, x->ff));
         x->launches++;
         CK(x, cudaMemcpyAsync(dst, x->io, sizeof(double) * x->nv * n, mk, x->stream));
     } else {
@@ -738,7 +762,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
     const bool cfl_here = (k == 1 && cfl > 0.0);
     PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, in, x->prim, x->in_u,
                 cfl_here ? x->smax : nullptr, x->err};
-    PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s));
+    PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
     x->launches++;
     if (cfl_here) {
         PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
@@ -746,7 +770,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
     }
     StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, x->Q0, out, x->dt,
                  LSRK_A[k - 1], x->err};
-    PROF(FV_KERNEL_STAGE, launch_stage(x->nd, x->nc, x->mixed, x->tile, sa, x->stage_grid, x->smem, s));
+    PROF(FV_KERNEL_STAGE, launch_stage(x->nd, x->nc, x->mixed, x->tile, sa, x->stage_grid, x->smem, s, x->ff));
     x->launches++;
     return FV_OK;
 }
@@ -842,7 +866,7 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
     if (what == FV_DIAG_TOTALS) {
         const int nblk = 1024;
         CK(x, launch_totals(x->nv, x->Q0, x->L.ntot_q, x->cases[icase].qoff, case_cells(x, icase), x->partial,
-                            nblk, x->stream));
+                            nblk, x->stream, x->ff));
         x->launches++;
         std::vector<double> part((size_t)x->nv * nblk);
         CK(x, cudaMemcpyAsync(part.data(), x->partial, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,

@@ -39,6 +39,9 @@ struct ConstT {
     R gm1cv[MAXC], igamma[MAXC], gcv[MAXC], cv[MAXC], q[MAXC], pinf[MAXC], pother[MAXC];
     R p_ref, beta, thinc_eps, thinc_gamma, tb, icb, itb;
     R thr_ducros, thr_gas, eps_ducros, d3p_coef, sigma, grad_eps;
+    R gm1_lo[MAXC], gpi_hi[MAXC], gpi_lo[MAXC];   // gamma-1 (lo part) and gamma pinf + p_ref as float-float
+    R gm1_hi[MAXC];
+    R Po[MAXC];          // pinf of the other pressure class + p_ref
 };
 
 struct CompDev {
@@ -101,6 +104,53 @@ __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double frcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ float frcp(float a) { return __fdividef(1.0f, a); }
+
+// ------------------------------------------------ compensated FP32 registers
+// The mixed form keeps the conserved LSRK registers as float-float pairs
+// (float2: hi + lo, about 48 significant bits, 8 bytes like FP64), so that
+// its arithmetic never touches the FP64 pipe.  Error-free transformations
+// (Knuth two-sum, Dekker/FMA two-product).
+__device__ __forceinline__ float2 ff_two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 ff_fast(float a, float b)
+{
+    const float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 ff_add_f(float2 a, float b)
+{
+    const float2 s = ff_two_sum(a.x, b);
+    return ff_fast(s.x, s.y + a.y);
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b)
+{
+    const float2 s = ff_two_sum(a.x, b.x);
+    return ff_fast(s.x, s.y + (a.y + b.y));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b)
+{
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    return ff_fast(p, e);
+}
+__host__ __device__ inline float2 ff_from_double(double x)
+{
+    const float hi = float(x);
+    return make_float2(hi, float(x - double(hi)));
+}
+
+template <typename T> struct IsFF { static constexpr bool value = false; };
+template <> struct IsFF<float2> { static constexpr bool value = true; };
+
+// conserved register value in the working precision R
+__device__ __forceinline__ double qv_d(double x) { return x; }
+__device__ __forceinline__ double qv_d(float2 x) { return double(x.x) + double(x.y); }
+template <typename R> __device__ __forceinline__ R qv(double x) { return R(x); }
+template <typename R> __device__ __forceinline__ R qv(float2 x) { return R(x.x + x.y); }
 
 // Reciprocals of N (<= 3) pressures with one division:
 // 1/P_k = prod_{j != k} P_j / prod_j P_j (products stay far from overflow).
@@ -321,39 +371,38 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
 //   E_k = gamma_k pinf_k - (gamma_k - 1) rho e
 // whose larger root is the physical one; with one class present the root is
 // p = -sum_k Y_k cv_k E_k / cv.  Then T = (rho e' + p) / (rho cp).  The E_k
-// carry the p + pinf cancellation and are always formed in FP64.
+// carry the p + pinf cancellation and are formed in FP64 (or compensated
+// FP32 in the mixed form).
 // Outputs w = (u_0..u_{ND-1}, p - p_ref, T, Y_0..Y_{NC-2}).
-template <int ND, int NC, typename R, bool PRC>
-__device__ __forceinline__ int prim_recover(const DevParams& P, const double* qc, R* w, double& rho_d,
-                                            R& T_out, R& p_abs, double T0)
+template <int ND, int NC, typename R, bool PRC, typename Q>
+__device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* w, R& rho_out, R& T_out,
+                                            R& p_abs, double T0)
 {
-    constexpr int NV = ND + NC + 1;
-    (void)NV;
-    const double rho = qc[0];
-    rho_d = rho;
-    const R rr = R(rho);
+    const R rr = qv<R>(qc[0]);
+    rho_out = rr;
     const R irho = frcp(rr);
     R ke = R(0);
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-        R m = R(qc[1 + d]);
+        const R m = qv<R>(qc[1 + d]);
         w[d] = m * irho;
         ke += R(0.5) * m * w[d];
     }
     R Y[NC], s = R(0);
 #pragma unroll
     for (int k = 0; k < NC - 1; ++k) {
-        Y[k] = clip01(R(qc[ND + 2 + k]) * irho);
+        Y[k] = clip01(qv<R>(qc[ND + 2 + k]) * irho);
         s += Y[k];
         w[ND + 2 + k] = Y[k];
     }
     Y[NC - 1] = clip01(R(1) - s);
     if constexpr (PRC) {
         // Peng-Robinson: FP64 Newton in both forms
+        const double rho = qv_d(qc[0]);
         double ked = 0.0;
 #pragma unroll
-        for (int d = 0; d < ND; ++d) ked += 0.5 * qc[1 + d] * qc[1 + d];
-        const double e = (qc[ND + 1] - ked / rho) / rho;
+        for (int d = 0; d < ND; ++d) { const double m = qv_d(qc[1 + d]); ked += 0.5 * m * m; }
+        const double e = (qv_d(qc[ND + 1]) - ked / rho) / rho;
         double Yd[NC], pd = 0.0, Td = 0.0;
 #pragma unroll
         for (int k = 0; k < NC; ++k) Yd[k] = double(Y[k]);
@@ -367,40 +416,61 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const double* qc
     const ConstT<R>& Kc = K<R>(P);
     R cv = R(0), cp = R(0), b = R(0), cc = R(0), se = R(0), eq = R(0);
     R sA = R(0), sB = R(0);
-    const double rhoe = qc[ND + 1] - double(ke);
 #pragma unroll
     for (int k = 0; k < NC; ++k) eq += Y[k] * Kc.q[k];
-    const double rhoe_q = rhoe - rho * double(eq);
+    // The quadratic is solved directly for the offset p' = p - p_ref (so the
+    // FP32 form keeps p' to its own relative precision): with
+    //   E'_k = gamma_k pinf_k + p_ref - (gamma_k - 1) rho e'   (cancellation-prone)
+    // and Po_k = pinf_other(k) + p_ref,
+    //   cv p'^2 + b' p' + c' = 0,  b' = sum Y_k cv_k (E'_k + Po_k),  c' = sum Y_k cv_k Po_k E'_k.
+    R rhoe_r;     // rho e' in the working precision (for T)
+    R Ek[NC];
+    if constexpr (IsFF<Q>::value) {
+        // float-float registers: E'_k in compensated FP32, no FP64 instruction
+        float2 rhoe = ff_add_f(qc[ND + 1], -(ke + rr * eq));
+        rhoe_r = rhoe.x + rhoe.y;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const float2 t = ff_mul(rhoe, make_float2(-Kc.gm1_hi[k], -Kc.gm1_lo[k]));
+            const float2 E = ff_add(t, make_float2(Kc.gpi_hi[k], Kc.gpi_lo[k]));
+            Ek[k] = E.x + E.y;
+        }
+    } else {
+        // FP64 registers: the one FP64 operation per component
+        const double rhoe = qv_d(qc[ND + 1]) - double(ke) - double(rr) * double(eq);
+        rhoe_r = R(rhoe);
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+            Ek[k] = R(fma(-(P.c[k].gamma - 1.0), rhoe, P.c[k].gamma * P.c[k].pinf + P.p_ref));
+    }
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-        const CompDev& C = P.c[k];
-        // the one FP64 operation per component: E_k = gamma pinf - (gamma-1) rho e
-        const R Ek = R(fma(-(C.gamma - 1.0), rhoe_q, C.gamma * C.pinf));
         const R Yc = Y[k] * Kc.cv[k];
         cv += Yc;
         cp += Y[k] * Kc.gcv[k];
-        b += Yc * (Ek + Kc.pother[k]);
-        cc += Yc * (Kc.pother[k] * Ek);
-        se += Yc * Ek;
-        if (Y[k] > R(0)) { if (C.classA) sA += Y[k]; else sB += Y[k]; }
+        b += Yc * (Ek[k] + Kc.Po[k]);
+        cc += Yc * (Kc.Po[k] * Ek[k]);
+        se += Yc * Ek[k];
+        if (Y[k] > R(0)) { if (P.c[k].classA) sA += Y[k]; else sB += Y[k]; }
     }
-    R p;
+    R pp;     // p - p_ref
     if (P.single_class || sA == R(0) || sB == R(0)) {
-        p = fdiv(-se, cv);
+        pp = fdiv(-se, cv);
     } else {
         const R disc = b * b - R(4) * cv * cc;
         const R sq = sq_rt(disc > R(0) ? disc : R(0));
-        p = (b >= R(0)) ? fdiv(R(-2) * cc, b + sq) : fdiv(sq - b, R(2) * cv);
+        pp = (b >= R(0)) ? fdiv(R(-2) * cc, b + sq) : fdiv(sq - b, R(2) * cv);
     }
-    const R T = fdiv(R(rhoe_q) + p, rr * cp);
-    w[ND] = p - Kc.p_ref;
+    const R p = Kc.p_ref + pp;
+    const R T = fdiv(rhoe_r + p, rr * cp);
+    w[ND] = pp;
     w[ND + 1] = T;
     T_out = T;
     p_abs = p;
-    bool ok = (rho > 0.0) && (T > R(0)) && (cv > R(0));
+    bool ok = (rr > R(0)) && (T > R(0)) && (cv > R(0));
 #pragma unroll
     for (int k = 0; k < NC; ++k)
-        if (Y[k] > R(0)) ok = ok && (p + Kc.pinf[k] > R(0));
+        if (Y[k] > R(0)) ok = ok && (Kc.Pk[k] + pp > R(0));
     return ok ? 0 : ERR_NONPHYS;
 }
 

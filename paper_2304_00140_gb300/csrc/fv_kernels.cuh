@@ -21,7 +21,7 @@ struct PrimArgs {
     const CaseDesc* cases;
     const int4* items;
     int nitems;
-    const double* q;          // conserved register read (field stride P.ntot_q)
+    const void* q;            // conserved register read (double or float2; field stride P.ntot_q)
     void* prim;               // R[nprim][ntot_p]
     const double* in_u;       // inflow velocities (device) or null
     unsigned long long* smax; // per-case max wave speed bits, or null
@@ -34,8 +34,8 @@ struct StageArgs {
     const int4* items;
     int nitems;
     const void* prim;
-    const double* q0;
-    double* qout;
+    const void* q0;           // registers: double (FP64 form) or float2 (float-float, mixed form)
+    void* qout;
     const double* dt;         // per-case dt
     double a;                 // LSRK coefficient a_k
     int* err;
@@ -75,26 +75,52 @@ __device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& 
     return n - 1;
 }
 
+// Asynchronous global->shared copies (cp.async, zero-filled when invalid) so
+// the next work item's halo tile loads while the current one computes.
+__device__ __forceinline__ void cp_async_elem(float* dst, const float* src, bool valid)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src), "r"(valid ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async_elem(double* dst, const double* src, bool valid)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// halo-tile buffers of the stage kernel: two (prefetch the next item) in the
+// FP32 form, one in the FP64 form (FP64-pipe bound; keeps 3D tiles in shared memory)
+template <typename R> constexpr int tile_buffers() { return sizeof(R) == 4 ? 2 : 1; }
+
+// LSRK register update q^k = q^0 + a dt R (FP64, or compensated FP32)
+__device__ __forceinline__ double lsrk_update(double q0, double adt, float, double Rv) { return q0 + adt * Rv; }
+__device__ __forceinline__ double lsrk_update(double q0, double adt, float, float Rv) { return q0 + adt * double(Rv); }
+__device__ __forceinline__ float2 lsrk_update(float2 q0, double, float adtf, float Rv) { return ff_add_f(q0, adtf * Rv); }
+
 __device__ __forceinline__ void set_err(int* err, int bit)
 {
     if (err) atomicOr(err, bit);
 }
 
 // ----------------------------------------------------------------- prims
-template <int ND, int NC, typename R, bool PRC>
+template <int ND, int NC, typename R, bool PRC, typename Q>
 __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 {
+    const Q* const qreg = static_cast<const Q*>(A.q);
     constexpr int NV = ND + NC + 1;
     using TS = TileShape<ND>;
     const DevParams& P = A.P;
     R* prim = static_cast<R*>(A.prim);
     const int tx = threadIdx.x % TS::X, ty = (threadIdx.x / TS::X) % TS::Y, tz = threadIdx.x / (TS::X * TS::Y);
-    __shared__ double wmax[8];
+    __shared__ R wmax[8];
     for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
         const int4 wi = A.items[it];
         const CaseDesc& C = A.cases[wi.x];
         const int gc[3] = {wi.y + tx, wi.z + ty, wi.w + tz};   // ghosted coordinates
-        double speed = 0.0;
+        R speed = R(0);
         const bool valid = gc[0] < C.g[0] && gc[1] < C.g[1] && gc[2] < C.g[2];
         if (valid) {
             int src[3], flip[3], infl[3];
@@ -117,15 +143,14 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 else flip[0] = 1;
             }
             const long long sc = C.qoff + ((long long)src[2] * C.n[1] + src[1]) * C.n[0] + src[0];
-            double qc[NV];
+            Q qc[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) qc[v] = A.q[v * P.ntot_q + sc];
-            R w[NV], T, pabs;
-            double rho;
+            for (int v = 0; v < NV; ++v) qc[v] = qreg[v * P.ntot_q + sc];
+            R w[NV], T, pabs, rho;
             const long long pc = C.poff + ((long long)gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0];
             // Peng-Robinson Newton starts from this cell's previous temperature
             const double T0 = PRC ? double(prim[(ND + 1) * P.ntot_p + pc]) : 0.0;
-            const int rst = prim_recover<ND, NC, R, PRC>(P, qc, w, rho, T, pabs, T0);
+            const int rst = prim_recover<ND, NC, R, PRC, Q>(P, qc, w, rho, T, pabs, T0);
             bool ok = rst == 0;
             if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
 #pragma unroll
@@ -139,12 +164,12 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 #pragma unroll
                 for (int k = 0; k < NC - 1; ++k) w[ND + 2 + k] = R(C.in_Y[k]);
             }
-            R rr = R(rho), cs = R(0);
+            R rr = rho, cs = R(0);
             const bool need_c = P.aux_rc || A.smax || in_disc;
             if (need_c) {
                 R e;
                 ok = tdu<NC, R, PRC>(P, w[ND], w[ND + 1], w + ND + 2, rr, e, cs) && ok;
-                if (!in_disc) rr = R(rho);
+                if (!in_disc) rr = rho;
             }
             if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
 #pragma unroll
@@ -167,7 +192,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 R s = R(0);
 #pragma unroll
                 for (int d = 0; d < ND; ++d) s += (fabs(w[d]) + cs) * pick<R>(C.idx[d], C.fidx[d]);
-                speed = double(s);
+                speed = s;
             }
         }
         if (A.smax) {
@@ -177,10 +202,10 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = speed;
             __syncthreads();
             if (threadIdx.x == 0) {
-                double m = 0.0;
+                R m = R(0);
                 for (int i = 0; i < 8; ++i) m = fmax(m, wmax[i]);
                 // positive doubles order like their bit patterns
-                atomicMax(A.smax + wi.x, (unsigned long long)__double_as_longlong(m));
+                atomicMax(A.smax + wi.x, (unsigned long long)__double_as_longlong(double(m)));
             }
             __syncthreads();
         }
@@ -188,9 +213,11 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 }
 
 // ------------------------------------------------------------------ stage
-template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, bool PRC>
+template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, bool PRC, typename Q>
 __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArgs A)
 {
+    const Q* const q0reg = static_cast<const Q*>(A.q0);
+    Q* const qoreg = static_cast<Q*>(A.qout);
     constexpr int NV = ND + NC + 1;
     constexpr int NCELL = TX * TY * TZ;
     constexpr int HX = TX + 4, HY = TY + 4, HZ = (ND == 3) ? TZ + 4 : 1;
@@ -200,9 +227,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
     const R* prim = static_cast<const R*>(A.prim);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sp = reinterpret_cast<R*>(smem_raw);                 // [nprim][HC]
+    R* const spbuf = reinterpret_cast<R*>(smem_raw);        // two halo tiles [2][nprim][HC]
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
-    R* const sfx = sp + P.nprim * HC;                       // fluxes per direction [NV][faces]
+    R* const sfx = spbuf + tile_buffers<R>() * P.nprim * HC; // fluxes per direction [NV][faces]
     R* const sfy = sfx + NV * NFX;
     R* const sfz = sfy + NV * NFY;
     R* extra = (ND == 2) ? sfz : sfz + NV * NFZ;
@@ -215,10 +242,35 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
 
     const ConstT<R>& Kc = K<R>(P);
     const int tid = threadIdx.x;
+    // halo tile of primitives of item `item` (ghosted coordinates x0 .. x0+HX-1)
+    auto issue_tile = [&](int item, R* buf) {
+        if (item < A.nitems) {
+            const int4 wn = A.items[item];
+            const CaseDesc& Cn = A.cases[wn.x];
+            for (int h = tid; h < HC; h += NT) {
+                const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+                const int gx = wn.y + hx, gy = wn.z + hy, gz = wn.w + hz;
+                const bool ok = gx < Cn.g[0] && gy < Cn.g[1] && gz < Cn.g[2];
+                const long long pc = ok ? Cn.poff + ((long long)gz * Cn.g[1] + gy) * Cn.g[0] + gx : 0;
+                for (int v = 0; v < P.nprim; ++v) cp_async_elem(buf + v * HC + h, prim + v * P.ntot_p + pc, ok);
+            }
+        }
+        cp_async_commit();
+    };
+    constexpr int NBUF = tile_buffers<R>();
+    int cur = 0;
+    if (NBUF == 2) issue_tile(blockIdx.x, spbuf);
     for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
         const int4 wi = A.items[it];
         const CaseDesc& C = A.cases[wi.x];
         const int x0 = wi.y, y0 = wi.z, z0 = wi.w;
+        R* const sp = spbuf + cur * P.nprim * HC;
+        if (NBUF == 2) {
+            // the next item's tile goes to the other buffer while this one computes
+            issue_tile(it + gridDim.x, spbuf + (cur ^ 1) * P.nprim * HC);
+        } else {
+            issue_tile(it, sp);
+        }
         const int vx = min(TX, C.n[0] - x0), vy = min(TY, C.n[1] - y0), vz = (ND == 3) ? min(TZ, C.n[2] - z0) : 1;
         R ci[3], cdx[3];
 #pragma unroll
@@ -227,17 +279,10 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
         const int cx = tid % TX, cy = (tid / TX) % TY, cz = tid / (TX * TY);
         const bool own = tid < NCELL && cx < vx && cy < vy && cz < vz;
         const long long gcell = C.qoff + ((long long)(z0 + cz) * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx);
-        double q0r[NV];
+        Q q0r[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) q0r[v] = own ? A.q0[v * P.ntot_q + gcell] : 0.0;
-        // ---- halo tile of primitives (ghosted coordinates x0 .. x0+HX-1)
-        for (int h = tid; h < HC; h += NT) {
-            const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-            const int gx = x0 + hx, gy = y0 + hy, gz = z0 + hz;
-            const bool ok = gx < C.g[0] && gy < C.g[1] && gz < C.g[2];
-            const long long pc = C.poff + ((long long)gz * C.g[1] + gy) * C.g[0] + gx;
-            for (int v = 0; v < P.nprim; ++v) sp[v * HC + h] = ok ? prim[v * P.ntot_p + pc] : R(0);
-        }
+        for (int v = 0; v < NV; ++v) q0r[v] = own ? q0reg[v * P.ntot_q + gcell] : Q{};
+        if (NBUF == 2) cp_async_wait_prev(); else cp_async_wait_all();
         __syncthreads();
         // ---- App. D cell sensor on the tile + 1 halo
         if (P.iles) {
@@ -308,14 +353,26 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
             }
         }
         __syncthreads();
-        // ---- faces of all directions
-        const int nfx = (vx + 1) * vy * vz, nfy = vx * (vy + 1) * vz, nfz = (ND == 3) ? vx * vy * (vz + 1) : 0;
-        const int nf_total = nfx + nfy + nfz;
-        for (int f = tid; f < nf_total; f += NT) {
-            int d, fx, fy, fz, lx, ly;
-            if (f < nfx) { d = 0; lx = vx + 1; ly = vy; fx = f % lx; fy = (f / lx) % ly; fz = f / (lx * ly); }
-            else if (f < nfx + nfy) { const int g = f - nfx; d = 1; lx = vx; ly = vy + 1; fx = g % lx; fy = (g / lx) % ly; fz = g / (lx * ly); }
-            else { const int g = f - nfx - nfy; d = 2; lx = vx; ly = vy; fx = g % lx; fy = (g / lx) % ly; fz = g / (lx * ly); }
+        // ---- faces of all directions, in the full tile's layout (compile-time
+        // index decode); faces outside a ragged tile's valid part are skipped
+        constexpr int NFACE = NFX + NFY + (ND == 3 ? NFZ : 0);
+        for (int f = tid; f < NFACE; f += NT) {
+            int d, fx, fy, fz, fi;
+            bool valid;
+            if (f < NFX) {
+                d = 0; fi = f;
+                fx = f % (TX + 1); fy = (f / (TX + 1)) % TY; fz = f / ((TX + 1) * TY);
+                valid = fx <= vx && fy < vy && fz < vz;
+            } else if (f < NFX + NFY) {
+                d = 1; fi = f - NFX;
+                fx = fi % TX; fy = (fi / TX) % (TY + 1); fz = fi / (TX * (TY + 1));
+                valid = fx < vx && fy <= vy && fz < vz;
+            } else {
+                d = 2; fi = f - NFX - NFY;
+                fx = fi % TX; fy = (fi / TX) % TY; fz = fi / (TX * TY);
+                valid = fx < vx && fy < vy && fz <= vz;
+            }
+            if (!valid) continue;
             // cell i-1 of the stencil in halo coordinates
             int hx = fx + 2, hy = fy + 2, hz = (ND == 3) ? fz + 2 : 0;
             int st;
@@ -340,11 +397,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
             R F[NV];
             const bool ok = face_flux<ND, NC, R, PRC>(P, d, ws, r4, c4, fl, F);
             if (!ok) set_err(A.err, ERR_NONPHYS);
-            // store at face index (fx, fy, fz) of the full tile face array
-            int fi;
-            if (d == 0) fi = (fz * TY + fy) * (TX + 1) + fx;
-            else if (d == 1) fi = (fz * (TY + 1) + fy) * TX + fx;
-            else fi = (fz * TY + fy) * TX + fx;
+            // store at face index fi (= (fx, fy, fz)) of the full tile face array
             const int nfd = d == 0 ? NFX : (d == 1 ? NFY : NFZ);
             R* const dst = d == 0 ? sfx : (d == 1 ? sfy : sfz);
 #pragma unroll
@@ -424,6 +477,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                     S[1 + ND] = Kc.sigma * kappa * udg;
                 }
                 const double adt = A.a * A.dt[wi.x];
+                const float adtf = float(adt);
                 const int fxl = (cz * TY + cy) * (TX + 1) + cx;
                 const int fyl = (cz * (TY + 1) + cy) * TX + cx;
                 const int fzl = (cz * TY + cy) * TX + cx;
@@ -433,11 +487,12 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                     div += (sfy[v * NFY + fyl + TX] - sfy[v * NFY + fyl]) * ci[1];
                     if (ND == 3) div += (sfz[v * NFZ + fzl + TX * TY] - sfz[v * NFZ + fzl]) * ci[2];
                     const R Rv = S[v] - div;
-                    A.qout[v * P.ntot_q + gcell] = q0r[v] + adt * double(Rv);
+                    qoreg[v * P.ntot_q + gcell] = lsrk_update(q0r[v], adt, adtf, Rv);
                 }
             }
         }
         __syncthreads();
+        if (NBUF == 2) cur ^= 1;
     }
 }
 
@@ -450,7 +505,8 @@ inline size_t stage_smem_bytes(int nprim)
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
     constexpr int AC = (TX + 2) * (TY + 2) * ((ND == 3) ? TZ + 2 : 1);
     constexpr int VC = (TX + 1) * (TY + 1) * ((ND == 3) ? TZ + 1 : 1);
-    size_t n = (size_t)nprim * HC + (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC + ND * VC;
+    size_t n = tile_buffers<R>() * (size_t)nprim * HC + (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC +
+               ND * VC;
     return n * sizeof(R) + HC + 16;
 }
 

@@ -9,13 +9,14 @@
 namespace tfv {
 
 // prim kernel and stage kernel, dispatched on (ndim, ncomp, mixed)
-cudaError_t launch_prim(int nd, int nc, int mixed, const PrimArgs& A, int grid, cudaStream_t s);
+// ff = 1: float-float (float2) registers of the mixed form; ff = 0: double registers
+cudaError_t launch_prim(int nd, int nc, int mixed, const PrimArgs& A, int grid, cudaStream_t s, int ff = 0);
 // `tile` indexes the candidate tiles (TILES2 / TILES3)
 cudaError_t launch_stage(int nd, int nc, int mixed, int tile, const StageArgs& A, int grid, size_t smem,
-                         cudaStream_t s);
-size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim);
-cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem);
-int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem);   // resident blocks per SM (0: cannot run)
+                         cudaStream_t s, int ff = 0);
+size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim, int ff = 0);
+cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem, int ff = 0);
+int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem, int ff = 0);   // blocks per SM (0: cannot run)
 int prim_occupancy(int nd, int nc, int mixed);
 
 // state I/O and diagnostics (FP64)
@@ -24,15 +25,20 @@ struct IoArgs {
     const CaseDesc* cases;
     int icase;
     long long ncell;            // interior cells of the case
-    const double* in;           // [nv][ncell] (primitive or conserved), case-local
-    double* out;                // [nv][ntot_q] register or [nv][ncell] case-local
+    const void* in;             // [nv][ncell] doubles (case-local) or a register
+    void* out;                  // a register or [nv][ncell] doubles (case-local)
     int* err;
 };
-cudaError_t launch_prim_to_cons(int nd, int nc, const IoArgs& A, cudaStream_t s);
-cudaError_t launch_cons_to_prim(int nd, int nc, const IoArgs& A, cudaStream_t s);
+cudaError_t launch_prim_to_cons(int nd, int nc, const IoArgs& A, cudaStream_t s, int ff);
+cudaError_t launch_cons_to_prim(int nd, int nc, const IoArgs& A, cudaStream_t s, int ff);
+// case-local conserved doubles <-> float-float registers
+cudaError_t launch_split(int nv, const double* in, long long ncell, void* reg, long long ntot_q, long long off,
+                         cudaStream_t s);
+cudaError_t launch_join(int nv, const void* reg, long long ntot_q, long long off, long long ncell, double* out,
+                        cudaStream_t s);
 // per-block Kahan partial sums of each field of one case: partial[nv][nblk]
-cudaError_t launch_totals(int nv, const double* q, long long ntot_q, long long off, long long ncell,
-                          double* partial, int nblk, cudaStream_t s);
+cudaError_t launch_totals(int nv, const void* q, long long ntot_q, long long off, long long ncell,
+                          double* partial, int nblk, cudaStream_t s, int ff);
 // dt[c] = cfl / smax[c]; t[c] += dt[c]; smax[c] = 0   (per case)
 cudaError_t launch_dt(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err,
                       cudaStream_t s);

@@ -5,10 +5,11 @@
 namespace tfv {
 
 #define FV_DECL(sfx)                                                                                  \
-    cudaError_t launch_stage_##sfx(int nc, int tile, const StageArgs& A, int grid, size_t smem, cudaStream_t s); \
-    cudaError_t set_smem_##sfx(int nc, int tile, size_t smem);                                                \
-    int occupancy_##sfx(int nc, int tile, size_t smem);                                                       \
-    size_t smem_##sfx(int nc, int tile, int nprim);
+    cudaError_t launch_stage_##sfx(int nc, int tile, int ff, const StageArgs& A, int grid, size_t smem,       \
+                                   cudaStream_t s);                                                           \
+    cudaError_t set_smem_##sfx(int nc, int tile, int ff, size_t smem);                                        \
+    int occupancy_##sfx(int nc, int tile, int ff, size_t smem);                                               \
+    size_t smem_##sfx(int nc, int tile, int ff, int nprim);
 FV_DECL(2d)
 FV_DECL(2f)
 FV_DECL(3d)
@@ -20,36 +21,46 @@ FV_DECL(3f)
              : (mixed ? fn##_3f(__VA_ARGS__) : fn##_3d(__VA_ARGS__)))
 
 cudaError_t launch_stage(int nd, int nc, int mixed, int tile, const StageArgs& A, int grid, size_t smem,
-                         cudaStream_t s)
+                         cudaStream_t s, int ff)
 {
-    return FV_PICK(launch_stage, nc, tile, A, grid, smem, s);
+    return FV_PICK(launch_stage, nc, tile, ff, A, grid, smem, s);
 }
-size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim) { return FV_PICK(smem, nc, tile, nprim); }
-cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem)
+size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim, int ff)
 {
-    return FV_PICK(set_smem, nc, tile, smem);
+    return FV_PICK(smem, nc, tile, ff, nprim);
 }
-int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem)
+cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem, int ff)
 {
-    return FV_PICK(occupancy, nc, tile, smem);
+    return FV_PICK(set_smem, nc, tile, ff, smem);
+}
+int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem, int ff)
+{
+    return FV_PICK(occupancy, nc, tile, ff, smem);
 }
 
 int prim_occupancy(int nd, int nc, int mixed);
 
-template <int ND, int NC, typename R>
+template <int ND, int NC, typename R, typename Q>
 static cudaError_t gop(const PrimArgs& A, int grid, cudaStream_t s)
 {
-    if (A.P.pr) prim_kernel<ND, NC, R, true><<<grid, 256, 0, s>>>(A);
-    else prim_kernel<ND, NC, R, false><<<grid, 256, 0, s>>>(A);
+    if (A.P.pr) prim_kernel<ND, NC, R, true, Q><<<grid, 256, 0, s>>>(A);
+    else prim_kernel<ND, NC, R, false, Q><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prim(int nd, int nc, int mixed, const PrimArgs& A, int grid, cudaStream_t s)
+template <int ND, int NC>
+static cudaError_t gop2(int mixed, int ff, const PrimArgs& A, int grid, cudaStream_t s)
 {
-    if (nd == 2 && nc == 2) return mixed ? gop<2, 2, float>(A, grid, s) : gop<2, 2, double>(A, grid, s);
-    if (nd == 2 && nc == 3) return mixed ? gop<2, 3, float>(A, grid, s) : gop<2, 3, double>(A, grid, s);
-    if (nd == 3 && nc == 2) return mixed ? gop<3, 2, float>(A, grid, s) : gop<3, 2, double>(A, grid, s);
-    if (nd == 3 && nc == 3) return mixed ? gop<3, 3, float>(A, grid, s) : gop<3, 3, double>(A, grid, s);
+    if (!mixed) return gop<ND, NC, double, double>(A, grid, s);
+    return ff ? gop<ND, NC, float, float2>(A, grid, s) : gop<ND, NC, float, double>(A, grid, s);
+}
+
+cudaError_t launch_prim(int nd, int nc, int mixed, const PrimArgs& A, int grid, cudaStream_t s, int ff)
+{
+    if (nd == 2 && nc == 2) return gop2<2, 2>(mixed, ff, A, grid, s);
+    if (nd == 2 && nc == 3) return gop2<2, 3>(mixed, ff, A, grid, s);
+    if (nd == 3 && nc == 2) return gop2<3, 2>(mixed, ff, A, grid, s);
+    if (nd == 3 && nc == 3) return gop2<3, 3>(mixed, ff, A, grid, s);
     return cudaErrorInvalidValue;
 }
 
@@ -57,7 +68,8 @@ template <int ND, int NC, typename R>
 static int pocc()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prim_kernel<ND, NC, R, false>, 256, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prim_kernel<ND, NC, R, false, double>, 256, 0) !=
+        cudaSuccess)
         return 1;
     return n < 1 ? 1 : n;
 }
@@ -71,17 +83,23 @@ int prim_occupancy(int nd, int nc, int mixed)
 }
 
 // ----------------------------------------------------------- state I/O
+// register store / load of one conserved value (FP64 or float-float)
+__device__ __forceinline__ void reg_put(double* r, long long i, double x) { r[i] = x; }
+__device__ __forceinline__ void reg_put(float2* r, long long i, double x) { r[i] = ff_from_double(x); }
+
 // primitive (u, p, T, Y) -> conserved through the FP64 closure (Eq. 3-5)
-template <int ND, int NC>
+template <int ND, int NC, typename Q>
 __global__ void prim_to_cons_kernel(IoArgs A)
 {
     constexpr int NV = ND + NC + 1;
     const CaseDesc& C = A.cases[A.icase];
+    const double* in = static_cast<const double*>(A.in);
+    Q* out = static_cast<Q*>(A.out);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.ncell;
          i += (long long)gridDim.x * blockDim.x) {
         double w[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) w[v] = A.in[v * A.ncell + i];
+        for (int v = 0; v < NV; ++v) w[v] = in[v * A.ncell + i];
         double rho, e, c;
         const bool ok = A.P.pr ? tdu<NC, double, true>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c)
                                : tdu<NC, double, false>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c);
@@ -90,63 +108,108 @@ __global__ void prim_to_cons_kernel(IoArgs A)
 #pragma unroll
         for (int d = 0; d < ND; ++d) ke += 0.5 * w[d] * w[d];
         const long long o = C.qoff + i;
-        A.out[o] = rho;
+        reg_put(out, o, rho);
 #pragma unroll
-        for (int d = 0; d < ND; ++d) A.out[(1 + d) * A.P.ntot_q + o] = rho * w[d];
-        A.out[(1 + ND) * A.P.ntot_q + o] = rho * (e + ke);
+        for (int d = 0; d < ND; ++d) reg_put(out, (1 + d) * A.P.ntot_q + o, rho * w[d]);
+        reg_put(out, (1 + ND) * A.P.ntot_q + o, rho * (e + ke));
 #pragma unroll
-        for (int k = 0; k < NC - 1; ++k) A.out[(2 + ND + k) * A.P.ntot_q + o] = rho * w[ND + 2 + k];
+        for (int k = 0; k < NC - 1; ++k) reg_put(out, (2 + ND + k) * A.P.ntot_q + o, rho * w[ND + 2 + k]);
     }
 }
 
 // conserved register -> primitive (u, p, T, Y) through the FP64 recovery
-template <int ND, int NC>
+template <int ND, int NC, typename Q>
 __global__ void cons_to_prim_kernel(IoArgs A)
 {
     constexpr int NV = ND + NC + 1;
     const CaseDesc& C = A.cases[A.icase];
+    const Q* in = static_cast<const Q*>(A.in);
+    double* out = static_cast<double*>(A.out);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.ncell;
          i += (long long)gridDim.x * blockDim.x) {
         double qc[NV], w[NV], rho, T, p;
         const long long o = C.qoff + i;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) qc[v] = A.in[v * A.P.ntot_q + o];
-        const int st = A.P.pr ? prim_recover<ND, NC, double, true>(A.P, qc, w, rho, T, p, 0.0)
-                              : prim_recover<ND, NC, double, false>(A.P, qc, w, rho, T, p, 0.0);
+        for (int v = 0; v < NV; ++v) qc[v] = qv_d(in[v * A.P.ntot_q + o]);
+        const int st = A.P.pr ? prim_recover<ND, NC, double, true, double>(A.P, qc, w, rho, T, p, 0.0)
+                              : prim_recover<ND, NC, double, false, double>(A.P, qc, w, rho, T, p, 0.0);
         if (st) set_err(A.err, st);
         w[ND] = p;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) A.out[v * A.ncell + i] = w[v];
+        for (int v = 0; v < NV; ++v) out[v * A.ncell + i] = w[v];
+    }
+}
+
+// conserved case-local doubles <-> float-float registers
+__global__ void split_kernel(int nv, const double* in, long long ncell, float2* reg, long long ntot_q, long long off)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell * nv;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / ncell, c = i - v * ncell;
+        reg[v * ntot_q + off + c] = ff_from_double(in[i]);
+    }
+}
+__global__ void join_kernel(int nv, const float2* reg, long long ntot_q, long long off, long long ncell, double* out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell * nv;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / ncell, c = i - v * ncell;
+        out[i] = qv_d(reg[v * ntot_q + off + c]);
     }
 }
 
 static int io_grid(long long n) { long long g = (n + 255) / 256; return (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g)); }
 
-cudaError_t launch_prim_to_cons(int nd, int nc, const IoArgs& A, cudaStream_t s)
+cudaError_t launch_split(int nv, const double* in, long long ncell, void* reg, long long ntot_q, long long off,
+                         cudaStream_t s)
+{
+    split_kernel<<<io_grid(ncell * nv), 256, 0, s>>>(nv, in, ncell, static_cast<float2*>(reg), ntot_q, off);
+    return cudaGetLastError();
+}
+cudaError_t launch_join(int nv, const void* reg, long long ntot_q, long long off, long long ncell, double* out,
+                        cudaStream_t s)
+{
+    join_kernel<<<io_grid(ncell * nv), 256, 0, s>>>(nv, static_cast<const float2*>(reg), ntot_q, off, ncell, out);
+    return cudaGetLastError();
+}
+
+template <typename Q>
+static cudaError_t p2c(int nd, int nc, const IoArgs& A, cudaStream_t s)
 {
     const int g = io_grid(A.ncell);
-    if (nd == 2 && nc == 2) prim_to_cons_kernel<2, 2><<<g, 256, 0, s>>>(A);
-    else if (nd == 2 && nc == 3) prim_to_cons_kernel<2, 3><<<g, 256, 0, s>>>(A);
-    else if (nd == 3 && nc == 2) prim_to_cons_kernel<3, 2><<<g, 256, 0, s>>>(A);
-    else if (nd == 3 && nc == 3) prim_to_cons_kernel<3, 3><<<g, 256, 0, s>>>(A);
+    if (nd == 2 && nc == 2) prim_to_cons_kernel<2, 2, Q><<<g, 256, 0, s>>>(A);
+    else if (nd == 2 && nc == 3) prim_to_cons_kernel<2, 3, Q><<<g, 256, 0, s>>>(A);
+    else if (nd == 3 && nc == 2) prim_to_cons_kernel<3, 2, Q><<<g, 256, 0, s>>>(A);
+    else if (nd == 3 && nc == 3) prim_to_cons_kernel<3, 3, Q><<<g, 256, 0, s>>>(A);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+template <typename Q>
+static cudaError_t c2p(int nd, int nc, const IoArgs& A, cudaStream_t s)
+{
+    const int g = io_grid(A.ncell);
+    if (nd == 2 && nc == 2) cons_to_prim_kernel<2, 2, Q><<<g, 256, 0, s>>>(A);
+    else if (nd == 2 && nc == 3) cons_to_prim_kernel<2, 3, Q><<<g, 256, 0, s>>>(A);
+    else if (nd == 3 && nc == 2) cons_to_prim_kernel<3, 2, Q><<<g, 256, 0, s>>>(A);
+    else if (nd == 3 && nc == 3) cons_to_prim_kernel<3, 3, Q><<<g, 256, 0, s>>>(A);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t launch_cons_to_prim(int nd, int nc, const IoArgs& A, cudaStream_t s)
+cudaError_t launch_prim_to_cons(int nd, int nc, const IoArgs& A, cudaStream_t s, int ff)
 {
-    const int g = io_grid(A.ncell);
-    if (nd == 2 && nc == 2) cons_to_prim_kernel<2, 2><<<g, 256, 0, s>>>(A);
-    else if (nd == 2 && nc == 3) cons_to_prim_kernel<2, 3><<<g, 256, 0, s>>>(A);
-    else if (nd == 3 && nc == 2) cons_to_prim_kernel<3, 2><<<g, 256, 0, s>>>(A);
-    else if (nd == 3 && nc == 3) cons_to_prim_kernel<3, 3><<<g, 256, 0, s>>>(A);
-    else return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    return ff ? p2c<float2>(nd, nc, A, s) : p2c<double>(nd, nc, A, s);
+}
+
+cudaError_t launch_cons_to_prim(int nd, int nc, const IoArgs& A, cudaStream_t s, int ff)
+{
+    return ff ? c2p<float2>(nd, nc, A, s) : c2p<double>(nd, nc, A, s);
 }
 
 // ---------------------------------------------------------- diagnostics
 // per-block Kahan partial sums of every field of one case
-__global__ void totals_kernel(int nv, const double* q, long long ntot_q, long long off, long long ncell,
+template <typename Q>
+__global__ void totals_kernel(int nv, const Q* q, long long ntot_q, long long off, long long ncell,
                               double* partial)
 {
     __shared__ double ss[256], sc[256];
@@ -154,7 +217,7 @@ __global__ void totals_kernel(int nv, const double* q, long long ntot_q, long lo
         double s = 0.0, c = 0.0;
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
              i += (long long)gridDim.x * blockDim.x) {
-            const double y = q[v * ntot_q + off + i] - c;
+            const double y = qv_d(q[v * ntot_q + off + i]) - c;
             const double t = s + y;
             c = (t - s) - y;
             s = t;
@@ -176,10 +239,11 @@ __global__ void totals_kernel(int nv, const double* q, long long ntot_q, long lo
     }
 }
 
-cudaError_t launch_totals(int nv, const double* q, long long ntot_q, long long off, long long ncell,
-                          double* partial, int nblk, cudaStream_t s)
+cudaError_t launch_totals(int nv, const void* q, long long ntot_q, long long off, long long ncell,
+                          double* partial, int nblk, cudaStream_t s, int ff)
 {
-    totals_kernel<<<nblk, 256, 0, s>>>(nv, q, ntot_q, off, ncell, partial);
+    if (ff) totals_kernel<float2><<<nblk, 256, 0, s>>>(nv, static_cast<const float2*>(q), ntot_q, off, ncell, partial);
+    else totals_kernel<double><<<nblk, 256, 0, s>>>(nv, static_cast<const double*>(q), ntot_q, off, ncell, partial);
     return cudaGetLastError();
 }
 

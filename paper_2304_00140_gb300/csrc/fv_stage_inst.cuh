@@ -1,7 +1,9 @@
 // fv_stage_inst.cuh -- instantiations of the stage kernel for one
 // (dimension, precision) pair over every candidate tile and 2 or 3
 // components; included by the fv_stage_*.cu translation units, which define
-// FV_ND, FV_REAL and FV_SUFFIX.
+// FV_ND, FV_REAL and FV_SUFFIX.  Register types: double for the FP64 form;
+// float2 (float-float) for the mixed form of a context, plus double on the
+// default tile for the mixed no-alloc entry point.
 #include "fv_launch.h"
 
 namespace tfv {
@@ -14,32 +16,35 @@ namespace {
 // I == NTILES: Peng-Robinson closure on tile 0
 template <int I> constexpr int tile_of() { return I < NTILES ? I : 0; }
 template <int I> constexpr bool pr_of() { return I >= NTILES; }
+template <int FF> struct RegOf { using type = double; };
+template <> struct RegOf<1> { using type = float2; };
 
-template <int NC, int I>
+#define FV_KERNEL(NC, I, FF)                                                                  \
+    stage_kernel<FV_ND, NC, FV_REAL, tile_def(FV_ND, tile_of<I>()).x, tile_def(FV_ND, tile_of<I>()).y, \
+                 tile_def(FV_ND, tile_of<I>()).z, tile_def(FV_ND, tile_of<I>()).nt, pr_of<I>(),        \
+                 typename RegOf<FF>::type>
+
+template <int NC, int I, int FF>
 cudaError_t go(const StageArgs& A, int grid, size_t smem, cudaStream_t s)
 {
-    constexpr TileDef t = tile_def(FV_ND, tile_of<I>());
-    stage_kernel<FV_ND, NC, FV_REAL, t.x, t.y, t.z, t.nt, pr_of<I>()><<<grid, t.nt, smem, s>>>(A);
+    FV_KERNEL(NC, I, FF)<<<grid, tile_def(FV_ND, tile_of<I>()).nt, smem, s>>>(A);
     return cudaGetLastError();
 }
-template <int NC, int I>
+template <int NC, int I, int FF>
 cudaError_t attr(size_t smem)
 {
-    constexpr TileDef t = tile_def(FV_ND, tile_of<I>());
-    return cudaFuncSetAttribute(stage_kernel<FV_ND, NC, FV_REAL, t.x, t.y, t.z, t.nt, pr_of<I>()>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(FV_KERNEL(NC, I, FF), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
-template <int NC, int I>
+template <int NC, int I, int FF>
 int occ(size_t smem)
 {
-    constexpr TileDef t = tile_def(FV_ND, tile_of<I>());
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, stage_kernel<FV_ND, NC, FV_REAL, t.x, t.y, t.z, t.nt, pr_of<I>()>, t.nt, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FV_KERNEL(NC, I, FF), tile_def(FV_ND, tile_of<I>()).nt,
+                                                      smem) != cudaSuccess)
         return 0;
     return n;
 }
-template <int NC, int I>
+template <int NC, int I, int FF>
 size_t bytes(int nprim)
 {
     constexpr TileDef t = tile_def(FV_ND, tile_of<I>());
@@ -47,23 +52,31 @@ size_t bytes(int nprim)
 }
 }  // namespace
 
-// `tile` is the candidate index, NTILES selects the Peng-Robinson kernel
-#define FV_TILE_SWITCH(fn, ...)                                                    \
-    switch (tile) {                                                                \
-    case 0: return nc == 2 ? fn<2, 0>(__VA_ARGS__) : fn<3, 0>(__VA_ARGS__);        \
-    case 1: return nc == 2 ? fn<2, 1>(__VA_ARGS__) : fn<3, 1>(__VA_ARGS__);        \
-    case 2: return nc == 2 ? fn<2, 2>(__VA_ARGS__) : fn<3, 2>(__VA_ARGS__);        \
-    case 3: return nc == 2 ? fn<2, 3>(__VA_ARGS__) : fn<3, 3>(__VA_ARGS__);        \
-    default: return nc == 2 ? fn<2, NTILES>(__VA_ARGS__) : fn<3, NTILES>(__VA_ARGS__); \
+// FP64 form: double registers on every tile (FF = 0).  Mixed form: float2
+// registers on every tile (ff = 1) or double registers on tile 0 (ff = 0).
+#define FV_NC(fn, I, FF, ...) (nc == 2 ? fn<2, I, FF>(__VA_ARGS__) : fn<3, I, FF>(__VA_ARGS__))
+#if FV_IS_FLOAT
+#define FV_FF 1
+#else
+#define FV_FF 0
+#endif
+#define FV_TILE_SWITCH(fn, ...)                                                   \
+    if (FV_IS_FLOAT && !ff) return FV_NC(fn, 0, 0, __VA_ARGS__);                  \
+    switch (tile) {                                                               \
+    case 0: return FV_NC(fn, 0, FV_FF, __VA_ARGS__);                              \
+    case 1: return FV_NC(fn, 1, FV_FF, __VA_ARGS__);                              \
+    case 2: return FV_NC(fn, 2, FV_FF, __VA_ARGS__);                              \
+    case 3: return FV_NC(fn, 3, FV_FF, __VA_ARGS__);                              \
+    default: return FV_NC(fn, NTILES, FV_FF, __VA_ARGS__);                        \
     }
 
-cudaError_t FV_CAT(launch_stage_, FV_SUFFIX)(int nc, int tile, const StageArgs& A, int grid, size_t smem,
+cudaError_t FV_CAT(launch_stage_, FV_SUFFIX)(int nc, int tile, int ff, const StageArgs& A, int grid, size_t smem,
                                              cudaStream_t s)
 {
     FV_TILE_SWITCH(go, A, grid, smem, s)
 }
-cudaError_t FV_CAT(set_smem_, FV_SUFFIX)(int nc, int tile, size_t smem) { FV_TILE_SWITCH(attr, smem) }
-int FV_CAT(occupancy_, FV_SUFFIX)(int nc, int tile, size_t smem) { FV_TILE_SWITCH(occ, smem) }
-size_t FV_CAT(smem_, FV_SUFFIX)(int nc, int tile, int nprim) { FV_TILE_SWITCH(bytes, nprim) }
+cudaError_t FV_CAT(set_smem_, FV_SUFFIX)(int nc, int tile, int ff, size_t smem) { FV_TILE_SWITCH(attr, smem) }
+int FV_CAT(occupancy_, FV_SUFFIX)(int nc, int tile, int ff, size_t smem) { FV_TILE_SWITCH(occ, smem) }
+size_t FV_CAT(smem_, FV_SUFFIX)(int nc, int tile, int ff, int nprim) { FV_TILE_SWITCH(bytes, nprim) }
 
 }  // namespace tfv

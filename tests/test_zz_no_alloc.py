@@ -33,6 +33,13 @@ def _noalloc_step(L, args, dt, q0, qa, qb, stream):
         assert st == fv.FV_OK, fv.status_string(st)
 
 
+# max relative difference per field: the FP64 form's parity tolerance; in the
+# FP32-mixed form the context keeps float-float registers while the no-alloc
+# call works on the caller's FP64 arrays, so the two agree to the mixed
+# form's tolerance
+TOL = {fv.FV_FP64: 1e-12, fv.FV_MIXED: 1e-6}
+
+
 @pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
 def test_noalloc_matches_fv_rk_stage_twice(precision):
     import torch
@@ -54,7 +61,7 @@ def test_noalloc_matches_fv_rk_stage_twice(precision):
         _noalloc_step(L, args, dt, q0, qa, qb, stream)
         got = q0.cpu().numpy()
         d = rel_field_diff(got, refs[call])
-        assert np.all(d <= 1e-12), (call, d)
+        assert np.all(d <= TOL[precision]), (call, d)
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
