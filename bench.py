@@ -124,6 +124,44 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- one form
+def _alg_flops_per_cell(job):
+    """Algorithmic FP64 flops of one stage_kernel launch per interior cell,
+    counted from the formulas (+, -, *, /, sqrt, min, max, compare = 1, fused
+    multiply-add = 2) for the 2D two-component stiffened-gas / ideal-gas
+    plain scheme: 2 faces x 227 (MUSCL/THINC test 107, TDU of both sides 94,
+    Riemann 12, flux 14) + divergence and LSRK update 41.  None for other
+    schemes (only the HBM roofline is reported for them)."""
+    w = job.w
+    s = w.scheme
+    if w.ndim == 2 and len(w.comps) == 2 and not s["iles"] and s["sigma"] == 0 and w.comps[0]["kind"] == 0:
+        return 495
+    return None
+
+
+def _source_hash():
+    """sha1 of the CUDA sources: an ncu traffic figure is only quoted for the
+    kernel version it was taken on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2304_00140_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(job, form):
+    """DRAM bytes (read + write) of one stage_kernel launch from the ncu
+    capture recorded in profiles/stage_traffic.json for this source version,
+    or None."""
+    p = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(_source_hash(), {})
+    return d.get(f"{job.name}/{form}")
+
+
 def _nprim(w):
     s = w.scheme
     return w.nvar + (2 if s["iles"] else 0) + (1 if (s["iles"] or s["sigma"] > 0) else 0)
@@ -364,10 +402,25 @@ def main():
         avg_ms = st["ms"] / max(1, st["launches"])
         byt = _algorithmic_stage_bytes(job, precision)
         ach = byt / (avg_ms * 1e-3) / 1e9
-        return dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
-                    traffic=None, kernel="stage_kernel", avg_launch_ms=avg_ms,
-                    algorithmic_bytes_per_launch=byt, peak_source=peaks["src"],
-                    kernel_share={k: v["ms"] for k, v in r["prof"].items()}, tile=r["tile"])
+        form = "mixed" if precision == fv.FV_MIXED else "fp64"
+        out = dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
+                   traffic=_ncu_traffic(job, form), kernel="stage_kernel", avg_launch_ms=avg_ms,
+                   algorithmic_bytes_per_launch=byt, peak_source=peaks["src"],
+                   kernel_share={k: v["ms"] for k, v in r["prof"].items()}, tile=r["tile"])
+        fl = _alg_flops_per_cell(job)
+        if precision == fv.FV_FP64 and fl:
+            # the FP64 form is bound by the FP64 pipe: 152 SMs x 2 DFMA/clock x
+            # 2 flops at the 2070 MHz maximum SM clock
+            peak = 152 * 2 * 2 * 2.070e9 / 1e12
+            tf = fl * job.cells / (avg_ms * 1e-3) / 1e12
+            out = dict(bound="alu", achieved=tf, peak=peak, unit="TFLOP/s", frac=tf / peak,
+                       traffic=out["traffic"], kernel="stage_kernel", avg_launch_ms=avg_ms,
+                       algorithmic_flops_per_launch=fl * job.cells,
+                       peak_source="derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz",
+                       hbm=dict(achieved=ach, peak=peaks["hbm"], frac=ach / peaks["hbm"],
+                                algorithmic_bytes_per_launch=byt),
+                       kernel_share=out["kernel_share"], tile=r["tile"])
+        return out
 
     head = forms[0]
     hprec = fv.FV_MIXED if head == "mixed" else fv.FV_FP64
@@ -391,6 +444,7 @@ def main():
 
     if rank == 0:
         regbytes = job.nvar * job.cells * 8
+        footprint = 3 * regbytes + _nprim(job.w) * job.cells * (4 if head == "mixed" else 8)
         line = dict(
             metric=METRIC, value=val, unit=UNIT, n_gpus=world, steps=hsteps, warmup=args.warmup,
             ms_per_step=res[head]["ms"] / hsteps, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -399,7 +453,7 @@ def main():
                         precision=head,
                         parallelism=(f"batch split over {world} ranks" if len(_workload_cases(args)) > 1 else
                                      f"replicas{world}") if world > 1 else "single GPU",
-                        l2=("inputs larger than L2" if regbytes > 129e6 else "inputs smaller than L2") +
+                        l2=("inputs larger than L2" if footprint > 129e6 else "inputs smaller than L2") +
                         f" (3 FP64 registers of {regbytes / 1e6:.0f} MB each plus primitives)"),
             roofline=roof(res[head], hprec), cpu_baseline=cpu, e2e=e2e,
             gpu_launches=res[head]["launches"], clocks=res[head]["clocks"],

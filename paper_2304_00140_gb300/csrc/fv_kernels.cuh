@@ -95,6 +95,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // FP32 form, one in the FP64 form (FP64-pipe bound; keeps 3D tiles in shared memory)
 template <typename R> constexpr int tile_buffers() { return sizeof(R) == 4 ? 2 : 1; }
 
+// Encoded liquid volume fraction (see the prim kernel): 1 when e is the
+// negated gas fraction (sign bit set, including -0 for pure liquid), else 0.
+__device__ __forceinline__ float liq_side(float e) { return signbit(e) ? 1.f : 0.f; }
+__device__ __forceinline__ double liq_side(double e) { return signbit(e) ? 1.0 : 0.0; }
+
 // LSRK register update q^k = q^0 + a dt R (FP64, or compensated FP32)
 __device__ __forceinline__ double lsrk_update(double q0, double adt, float, double Rv) { return q0 + adt * Rv; }
 __device__ __forceinline__ double lsrk_update(double q0, double adt, float, float Rv) { return q0 + adt * double(Rv); }
@@ -142,14 +147,15 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 if (y * y + z * z <= C.in_r2) { in_disc = true; src[0] = 0; flip[0] = 0; }
                 else flip[0] = 1;
             }
-            const long long sc = C.qoff + ((long long)src[2] * C.n[1] + src[1]) * C.n[0] + src[0];
+            // case-local indices fit 32 bits; field strides advance a pointer
+            const Q* qp = qreg + C.qoff + ((src[2] * C.n[1] + src[1]) * C.n[0] + src[0]);
             Q qc[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) qc[v] = qreg[v * P.ntot_q + sc];
+            for (int v = 0; v < NV; ++v) { qc[v] = *qp; qp += P.ntot_q; }
             R w[NV], T, pabs, rho;
-            const long long pc = C.poff + ((long long)gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0];
+            R* const pp0 = prim + C.poff + ((gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0]);
             // Peng-Robinson Newton starts from this cell's previous temperature
-            const double T0 = PRC ? double(prim[(ND + 1) * P.ntot_p + pc]) : 0.0;
+            const double T0 = PRC ? double(pp0[(ND + 1) * P.ntot_p]) : 0.0;
             const int rst = prim_recover<ND, NC, R, PRC, Q>(P, qc, w, rho, T, pabs, T0);
             bool ok = rst == 0;
             if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
@@ -172,21 +178,31 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 if (!in_disc) rr = rho;
             }
             if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
+            {
+                R* o = pp0;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) prim[v * P.ntot_p + pc] = w[v];
+                for (int v = 0; v < NV; ++v) { *o = w[v]; o += P.ntot_p; }
+            }
             if (P.aux_rc) {
-                prim[P.i_rho * P.ntot_p + pc] = rr;
-                prim[P.i_c * P.ntot_p + pc] = cs;
+                pp0[P.i_rho * P.ntot_p] = rr;
+                pp0[P.i_c * P.ntot_p] = cs;
             }
             if (P.aux_al) {
-                // liquid volume fraction alpha_l = rho Y_l (gamma_l - 1) cv_l T / (p + pinf_l)  (Eq. A.1.4)
-                R s = R(0);
+                // liquid volume fraction (Eq. A.1.4/A.1.5) stored as the smaller
+                // side: e = alpha_l if alpha_l <= alpha_g, else -alpha_g
+                // (alpha_g = 1 - alpha_l from the gas terms), so differences of
+                // near-1 liquid fractions keep full precision:
+                //   alpha_l = e + [e < 0]
+                R s = R(0), al = R(0), ag = R(0);
 #pragma unroll
                 for (int k = 0; k < NC - 1; ++k) s += clip01(w[ND + 2 + k]);
-                const int L = P.liquid;
-                const R Yl = (L == NC - 1) ? clip01(R(1) - s) : clip01(w[ND + 2 + L]);
-                const R al = fdiv(rr * Yl * K<R>(P).gm1cv[L] * w[ND + 1], K<R>(P).Pk[L] + w[ND]);
-                prim[P.i_al * P.ntot_p + pc] = al;
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    const R Yk = (k == NC - 1) ? clip01(R(1) - s) : clip01(w[ND + 2 + k]);
+                    const R a = fdiv(rr * Yk * K<R>(P).gm1cv[k] * w[ND + 1], K<R>(P).Pk[k] + w[ND]);
+                    if (k == P.liquid) al = a; else ag += a;
+                }
+                pp0[P.i_al * P.ntot_p] = (al <= ag) ? al : -ag;
             }
             if (A.smax && interior) {
                 R s = R(0);
@@ -247,12 +263,19 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
         if (item < A.nitems) {
             const int4 wn = A.items[item];
             const CaseDesc& Cn = A.cases[wn.x];
+            const int g0 = Cn.g[0], g1 = Cn.g[1], g2 = Cn.g[2];
+            const R* const base = prim + Cn.poff;
             for (int h = tid; h < HC; h += NT) {
                 const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
                 const int gx = wn.y + hx, gy = wn.z + hy, gz = wn.w + hz;
-                const bool ok = gx < Cn.g[0] && gy < Cn.g[1] && gz < Cn.g[2];
-                const long long pc = ok ? Cn.poff + ((long long)gz * Cn.g[1] + gy) * Cn.g[0] + gx : 0;
-                for (int v = 0; v < P.nprim; ++v) cp_async_elem(buf + v * HC + h, prim + v * P.ntot_p + pc, ok);
+                const bool ok = gx < g0 && gy < g1 && gz < g2;
+                const R* src = ok ? base + ((gz * g1 + gy) * g0 + gx) : prim;
+                R* dst = buf + h;
+                for (int v = 0; v < P.nprim; ++v) {
+                    cp_async_elem(dst, src, ok);
+                    dst += HC;
+                    src += ok ? P.ntot_p : 0;
+                }
             }
         }
         cp_async_commit();
@@ -278,10 +301,13 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
         // this thread's cell: prefetch q0 so its latency hides behind the face work
         const int cx = tid % TX, cy = (tid / TX) % TY, cz = tid / (TX * TY);
         const bool own = tid < NCELL && cx < vx && cy < vy && cz < vz;
-        const long long gcell = C.qoff + ((long long)(z0 + cz) * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx);
+        const long long gcell = C.qoff + (((z0 + cz) * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx));
         Q q0r[NV];
+        {
+            const Q* qp = q0reg + gcell;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) q0r[v] = own ? q0reg[v * P.ntot_q + gcell] : Q{};
+            for (int v = 0; v < NV; ++v) { q0r[v] = own ? *qp : Q{}; qp += P.ntot_q; }
+        }
         if (NBUF == 2) cp_async_wait_prev(); else cp_async_wait_all();
         __syncthreads();
         // ---- App. D cell sensor on the tile + 1 halo
@@ -294,7 +320,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                 if (in) {
                     R g[3][3];
                     R tg = R(0);
-                    const R ag0 = R(1) - sp[P.i_al * HC + h];
+                    const R* ea = sp + P.i_al * HC;
+                    const R e0 = ea[h];
+                    const R o0 = liq_side(e0);
                     const int st[3] = {SX, SY, SZ};
 #pragma unroll
                     for (int bd = 0; bd < ND; ++bd) {
@@ -302,7 +330,9 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                         const R inv2dx = R(0.5) * ci[bd];
 #pragma unroll
                         for (int a = 0; a < ND; ++a) g[a][bd] = (sp[a * HC + hp] - sp[a * HC + hm]) * inv2dx;
-                        tg += fabs(ag0 - (R(1) - sp[P.i_al * HC + hm])) + fabs((R(1) - sp[P.i_al * HC + hp]) - ag0);
+                        // |delta alpha_gas| = |delta alpha_l| from the encoded fractions
+                        const R em = ea[hm], ep = ea[hp];
+                        tg += fabs((e0 - em) + (o0 - liq_side(em))) + fabs((ep - e0) + (liq_side(ep) - o0));
                     }
                     R div = R(0);
 #pragma unroll
@@ -328,27 +358,36 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                 const int ax = h % AX, ay = (h / AX) % AY, az = h / (AX * AY);
                 const int hc = (ax + 1) * SX + (ay + 1) * SY + (ND == 3 ? (az + 1) * SZ : 0);
                 const R* al = sp + P.i_al * HC;
-                R s = R(0);
+                // weighted sum of the encoded fractions plus the exact integer
+                // weight W1 of the liquid-side cells; encoded result
+                R s = R(0), W1 = R(0);
                 if (ND == 2) {
 #pragma unroll
                     for (int b = -1; b <= 1; ++b) {
-                        const R wb = (b == 0) ? R(2) : R(1);
-                        s += wb * (al[hc + b * SY - 1] + R(2) * al[hc + b * SY] + al[hc + b * SY + 1]);
-                    }
-                    s *= R(1.0 / 16.0);
-                } else {
 #pragma unroll
-                    for (int c = -1; c <= 1; ++c) {
-                        const R wc = (c == 0) ? R(2) : R(1);
-#pragma unroll
-                        for (int b = -1; b <= 1; ++b) {
-                            const R wb = (b == 0) ? R(2) : R(1);
-                            const int o = hc + c * SZ + b * SY;
-                            s += wc * wb * (al[o - 1] + R(2) * al[o] + al[o + 1]);
+                        for (int a = -1; a <= 1; ++a) {
+                            const R wt = R((b == 0 ? 2 : 1) * (a == 0 ? 2 : 1));
+                            const R e = al[hc + b * SY + a];
+                            s += wt * e;
+                            W1 += wt * liq_side(e);
                         }
                     }
-                    s *= R(1.0 / 64.0);
+                } else {
+#pragma unroll
+                    for (int c = -1; c <= 1; ++c)
+#pragma unroll
+                        for (int b = -1; b <= 1; ++b)
+#pragma unroll
+                            for (int a = -1; a <= 1; ++a) {
+                                const R wt = R((c == 0 ? 2 : 1) * (b == 0 ? 2 : 1) * (a == 0 ? 2 : 1));
+                                const R e = al[hc + c * SZ + b * SY + a];
+                                s += wt * e;
+                                W1 += wt * liq_side(e);
+                            }
                 }
+                const R norm = R(ND == 2 ? 16 : 64);
+                // liquid side stored as -(alpha_g~), a signed zero for pure liquid
+                s = (s + W1 > R(0.5) * norm) ? -(((norm - W1) - s) / norm) : (s + W1) / norm;
                 sa[h] = s;
             }
         }
@@ -412,19 +451,21 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
             for (int h = tid; h < VX * VY * VZ; h += NT) {
                 const int ix = h % VX, iy = (h / VX) % VY, iz = h / (VX * VY);
                 // vertex between smoothed cells (ix-1+1 .. ix+1) in sa coordinates: cells ix, ix+1
-                R g[3] = {R(0), R(0), R(0)};
+                R g[3] = {R(0), R(0), R(0)}, go[3] = {R(0), R(0), R(0)};
                 const int nc = 1 << ND;
 #pragma unroll
                 for (int cc = 0; cc < (1 << ND); ++cc) {
                     const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
-                    const R a = sa[((ND == 3 ? iz + bz : 0) * AY + iy + by) * AX + ix + bx];
-                    g[0] += bx ? a : -a;
-                    g[1] += by ? a : -a;
-                    if (ND == 3) g[2] += bz ? a : -a;
+                    // alpha~ = e + [e on the liquid side]; the offsets sum exactly
+                    const R e = sa[((ND == 3 ? iz + bz : 0) * AY + iy + by) * AX + ix + bx];
+                    const R oc = liq_side(e);
+                    g[0] += bx ? e : -e; go[0] += bx ? oc : -oc;
+                    g[1] += by ? e : -e; go[1] += by ? oc : -oc;
+                    if (ND == 3) { g[2] += bz ? e : -e; go[2] += bz ? oc : -oc; }
                 }
                 R mag2 = R(0);
 #pragma unroll
-                for (int d = 0; d < ND; ++d) { g[d] *= ci[d] * R(2.0 / nc); mag2 += g[d] * g[d]; }
+                for (int d = 0; d < ND; ++d) { g[d] = (g[d] + go[d]) * ci[d] * R(2.0 / nc); mag2 += g[d] * g[d]; }
                 const R mag = sq_rt(mag2);
                 const R inv = (mag > gthr) ? frcp(mag) : R(0);
 #pragma unroll
@@ -448,16 +489,18 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                     for (int vtx = 0; vtx < (1 << ND); ++vtx) {
                         const int ox = vtx & 1, oy = (vtx >> 1) & 1, oz = (vtx >> 2) & 1;
                         const int vi = ((ND == 3 ? cz + oz : 0) * VY + cy + oy) * VX + cx + ox;
-                        R gu[3] = {R(0), R(0), R(0)};
+                        R gu[3] = {R(0), R(0), R(0)}, gou[3] = {R(0), R(0), R(0)};
 #pragma unroll
                         for (int cc = 0; cc < (1 << ND); ++cc) {
                             const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
                             const int o = hc + (ox - 1 + bx) * SX + (oy - 1 + by) * SY + (ND == 3 ? (oz - 1 + bz) * SZ : 0);
-                            const R a = al[o];
-                            gu[0] += bx ? a : -a;
-                            gu[1] += by ? a : -a;
-                            if (ND == 3) gu[2] += bz ? a : -a;
+                            const R e = al[o], oc = liq_side(e);
+                            gu[0] += bx ? e : -e; gou[0] += bx ? oc : -oc;
+                            gu[1] += by ? e : -e; gou[1] += by ? oc : -oc;
+                            if (ND == 3) { gu[2] += bz ? e : -e; gou[2] += bz ? oc : -oc; }
                         }
+#pragma unroll
+                        for (int d = 0; d < ND; ++d) gu[d] += gou[d];
 #pragma unroll
                         for (int d = 0; d < ND; ++d) {
                             const R nd_ = sn[(d * VZ + (ND == 3 ? cz + oz : 0)) * VY * VX + (cy + oy) * VX + cx + ox];
@@ -481,13 +524,15 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                 const int fxl = (cz * TY + cy) * (TX + 1) + cx;
                 const int fyl = (cz * (TY + 1) + cy) * TX + cx;
                 const int fzl = (cz * TY + cy) * TX + cx;
+                Q* qo = qoreg + gcell;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     R div = (sfx[v * NFX + fxl + 1] - sfx[v * NFX + fxl]) * ci[0];
                     div += (sfy[v * NFY + fyl + TX] - sfy[v * NFY + fyl]) * ci[1];
                     if (ND == 3) div += (sfz[v * NFZ + fzl + TX * TY] - sfz[v * NFZ + fzl]) * ci[2];
                     const R Rv = S[v] - div;
-                    qoreg[v * P.ntot_q + gcell] = lsrk_update(q0r[v], adt, adtf, Rv);
+                    *qo = lsrk_update(q0r[v], adt, adtf, Rv);
+                    qo += P.ntot_q;
                 }
             }
         }

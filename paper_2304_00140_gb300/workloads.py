@@ -218,6 +218,7 @@ def _init_droplet(w: Workload):
     ri = P["R"] + P.get("A", 0.0) * np.cos(2.0 * th)
     h = tanh_indicator(r - ri, P["width"] * w.dx[0])
     W = _alloc(w)
+    W[0] = P.get("u", 0.0)
     W[w.ndim] = P["p"] + P.get("dp", 0.0) * h
     W[w.ndim + 1] = P["T"]
     W[w.ndim + 2] = 1.0 - h           # air tracked, water implied
