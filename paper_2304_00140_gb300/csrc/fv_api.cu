@@ -399,7 +399,7 @@ extern "C" fv_status fv_workspace_size(int ncases, const fv_grid* grids, const f
 // work list of the stage kernel for one candidate tile
 static void stage_items(const std::vector<CaseDesc>& cases, int nd, int tile, std::vector<int4>& out)
 {
-    const TileDef td = tile_def(nd, tile < NTILES ? tile : 0);
+    const TileDef td = tile_def(nd, variant_tile(tile));
     out.clear();
     for (size_t c = 0; c < cases.size(); ++c) {
         const CaseDesc& C = cases[c];
@@ -409,9 +409,22 @@ static void stage_items(const std::vector<CaseDesc>& cases, int nd, int tile, st
     }
 }
 
+// Stage-kernel variant for candidate tile `tile`: the autotuned tiles serve the
+// stiffened/ideal-gas closure with the Table 4.2 limiter pair; Peng-Robinson
+// and any other limiter pair run on tile 0.
+static int kernel_variant(const DevParams& P, int tile)
+{
+    const bool t42 = P.lim_vel == FV_KOREN && P.lim_scalar == FV_MINMOD;
+    if (t42 && !P.pr) return tile < NTILES ? tile : 0;
+    if (t42) return NTILES;
+    return P.pr ? NTILES + 2 : NTILES + 1;
+}
+
+static bool tunable(const DevParams& P) { return kernel_variant(P, 1) == 1; }
+
 static fv_status apply_tile(fv_ctx* x, int tile)
 {
-    if (x->P.pr) tile = NTILES;   // the Peng-Robinson kernel has the default tile only
+    tile = kernel_variant(x->P, tile);
     std::vector<int4> it;
     stage_items(x->cases, x->nd, tile, it);
     if ((long long)it.size() > x->L.n_items_stage) return fail(x, FV_ERR_STATE, "work list overflow%s");
@@ -453,7 +466,7 @@ static fv_status tune(fv_ctx* x)
 {
     if (x->tuned) return FV_OK;
     x->tuned = true;
-    if (x->P.pr) return apply_tile(x, NTILES);
+    if (!tunable(x->P)) return apply_tile(x, 0);
     if (const char* f = getenv("FV_TILE")) {
         const int t = atoi(f);
         if (t >= 0 && t < NTILES) return apply_tile(x, t);
@@ -892,7 +905,7 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
     if (what == FV_DIAG_TILE) {
         s = tune(x);
         if (s) return s;
-        const TileDef td = tile_def(x->nd, x->tile < NTILES ? x->tile : 0);
+        const TileDef td = tile_def(x->nd, variant_tile(x->tile));
         double* o = static_cast<double*>(out);
         o[0] = td.x; o[1] = td.y; o[2] = td.z; o[3] = td.nt;
         for (int t = 0; t < NTILES; ++t) o[4 + t] = x->tune_ms[t];
@@ -1092,9 +1105,10 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
 
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FV_ERR_CUDA;
-    const size_t smem = stage_smem(x.nd, x.nc, x.mixed, 0, x.nprim);
-    if (stage_set_smem(x.nd, x.nc, x.mixed, 0, smem) != cudaSuccess) return FV_ERR_CUDA;
-    const int gs = (int)std::min<long long>(n_st, (long long)nsm * stage_occupancy(x.nd, x.nc, x.mixed, 0, smem));
+    const int var = kernel_variant(x.P, 0);
+    const size_t smem = stage_smem(x.nd, x.nc, x.mixed, var, x.nprim);
+    if (stage_set_smem(x.nd, x.nc, x.mixed, var, smem) != cudaSuccess) return FV_ERR_CUDA;
+    const int gs = (int)std::min<long long>(n_st, (long long)nsm * stage_occupancy(x.nd, x.nc, x.mixed, var, smem));
     const int gp = (int)std::min<long long>(n_pr, (long long)nsm * prim_occupancy(x.nd, x.nc, x.mixed));
     const int nsetup = (int)std::min<long long>(1024, (std::max(n_st, n_pr) + 255) / 256);
 
@@ -1104,7 +1118,7 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
     PrimArgs pa{x.P, dcase, ipr, (int)n_pr, qprev, prim, nullptr, nullptr, derr};
     if (launch_prim(x.nd, x.nc, x.mixed, pa, gp, s) != cudaSuccess) return FV_ERR_CUDA;
     StageArgs sa{x.P, dcase, ist, (int)n_st, prim, q0, qout, ddt, LSRK_A[k - 1], derr};
-    if (launch_stage(x.nd, x.nc, x.mixed, 0, sa, gs, smem, s) != cudaSuccess) return FV_ERR_CUDA;
+    if (launch_stage(x.nd, x.nc, x.mixed, var, sa, gs, smem, s) != cudaSuccess) return FV_ERR_CUDA;
     int e = 0;
     if (cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FV_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return FV_ERR_CUDA;

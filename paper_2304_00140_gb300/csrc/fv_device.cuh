@@ -546,7 +546,12 @@ __device__ __forceinline__ R thinc_side(const DevParams& P, R xa, R xc, R xb, bo
 // F receives (rho, rho u_0.., rho E, rho Y..) fluxes.  In the mixed form the
 // constant p_ref is left out of the normal-momentum flux (it cancels in every
 // cell's flux difference).
-template <int ND, int NC, typename R, bool PRC>
+// LIM: limiter pair fixed at compile time ((velocity id << 4) | scalar id), or
+// LIM_RUNTIME to read it from the parameters.
+constexpr int LIM_RUNTIME = -1;
+constexpr int LIM_TABLE42 = (1 << 4) | 0;   // Koren for velocities, Minmod for p, T, Y (Table 4.2)
+
+template <int ND, int NC, typename R, bool PRC, int LIM>
 __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*ws)[ND + NC + 1], const R* rho4,
                                           const R* c4, int f, R* F)
 {
@@ -564,7 +569,7 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     } else {
 #pragma unroll
         for (int v = 0; v < NW; ++v) {
-            const int lim = (v < ND) ? P.lim_vel : P.lim_scalar;
+            const int lim = LIM >= 0 ? ((v < ND) ? (LIM >> 4) : (LIM & 15)) : ((v < ND) ? P.lim_vel : P.lim_scalar);
             muscl(lim, ws[0][v], ws[1][v], ws[2][v], ws[3][v], WL[v], WR[v]);
             if (v >= IY && P.thinc) {
                 const R eps = K<R>(P).thinc_eps;
@@ -576,7 +581,12 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     R rL, eL, cL, rR, eR, cR;
     bool ok = tdu<NC, R, PRC>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
     ok = tdu<NC, R, PRC>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
-    const R pL = WL[IP], pR = WR[IP], uL = WL[d], uR = WR[d];
+    // normal velocities by select: indexing with the run-time d would put WL
+    // and WR in local memory
+    R uL = WL[0], uR = WR[0];
+    if (ND > 1 && d == 1) { uL = WL[1]; uR = WR[1]; }
+    if (ND > 2 && d == 2) { uL = WL[ND > 2 ? 2 : 0]; uR = WR[ND > 2 ? 2 : 0]; }
+    const R pL = WL[IP], pR = WR[IP];
     R us, ps;
     if (P.iles) {
         const R cm = fmax(c4[1], c4[2]);
@@ -596,7 +606,9 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
         us = fdiv(zL * uL + zR * uR + pL - pR, zL + zR);
     }
     const bool up = us >= R(0);
-    const R* Ws = up ? WL : WR;
+    R Ws[NW];   // element-wise select keeps both sides in registers
+#pragma unroll
+    for (int v = 0; v < NW; ++v) Ws[v] = up ? WL[v] : WR[v];
     const R rs = up ? rL : rR;
     const R es = up ? eL : eR;
     R ke = R(0);

@@ -49,11 +49,20 @@ template <> struct TileShape<3> { static constexpr int X = 32, Y = 4, Z = 2, NT 
 // Candidate tiles of the stage kernel, chosen per workload by the autotuner.
 // NT (threads) is sized so the tile's faces take about two or three full
 // rounds; tile 0 is the default.
-struct TileDef { int x, y, z, nt; };
+// mb: resident blocks per SM the register allocation is sized for
+// (__launch_bounds__), trading registers for latency hiding.
+struct TileDef { int x, y, z, nt, mb; };
 constexpr int NTILES = 4;
-constexpr TileDef TILES2[NTILES] = {{32, 8, 1, 288}, {32, 16, 1, 544}, {64, 8, 1, 576}, {16, 16, 1, 288}};
-constexpr TileDef TILES3[NTILES] = {{32, 4, 2, 256}, {16, 4, 4, 320}, {16, 8, 2, 320}, {32, 4, 4, 608}};
+constexpr TileDef TILES2[NTILES] = {{32, 8, 1, 288, 2}, {32, 8, 1, 288, 3}, {16, 16, 1, 288, 3}, {16, 16, 1, 288, 2}};
+constexpr TileDef TILES3[NTILES] = {{32, 4, 2, 256, 2}, {32, 4, 2, 256, 3}, {16, 8, 2, 320, 2}, {16, 4, 4, 320, 2}};
 constexpr TileDef tile_def(int nd, int i) { return nd == 2 ? TILES2[i] : TILES3[i]; }
+
+// Kernel variants of the stage kernel: 0 .. NTILES-1 stiffened/ideal-gas
+// closure with the Table 4.2 limiter pair on tile i; NTILES Peng-Robinson with
+// that pair on tile 0; NTILES+1 / NTILES+2 stiffened-gas / Peng-Robinson with
+// any limiter pair (read at run time) on tile 0.
+constexpr int NVARIANTS = NTILES + 3;
+constexpr int variant_tile(int v) { return v < NTILES ? v : 0; }
 
 __device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& flip, int& inflow)
 {
@@ -229,8 +238,8 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 }
 
 // ------------------------------------------------------------------ stage
-template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, bool PRC, typename Q>
-__global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArgs A)
+template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, int MB, bool PRC, int LIM, typename Q>
+__global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 {
     const Q* const q0reg = static_cast<const Q*>(A.q0);
     Q* const qoreg = static_cast<Q*>(A.qout);
@@ -434,7 +443,7 @@ __global__ void __launch_bounds__(NT, (NT <= 320 ? 2 : 1)) stage_kernel(StageArg
                 fl = (sflag[h0 + st] | sflag[h0 + 2 * st]) ? 1 : 0;
             }
             R F[NV];
-            const bool ok = face_flux<ND, NC, R, PRC>(P, d, ws, r4, c4, fl, F);
+            const bool ok = face_flux<ND, NC, R, PRC, LIM>(P, d, ws, r4, c4, fl, F);
             if (!ok) set_err(A.err, ERR_NONPHYS);
             // store at face index fi (= (fx, fy, fz)) of the full tile face array
             const int nfd = d == 0 ? NFX : (d == 1 ? NFY : NFZ);

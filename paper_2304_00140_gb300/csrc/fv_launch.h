@@ -11,7 +11,8 @@ namespace tfv {
 // prim kernel and stage kernel, dispatched on (ndim, ncomp, mixed)
 // ff = 1: float-float (float2) registers of the mixed form; ff = 0: double registers
 cudaError_t launch_prim(int nd, int nc, int mixed, const PrimArgs& A, int grid, cudaStream_t s, int ff = 0);
-// `tile` indexes the candidate tiles (TILES2 / TILES3)
+// `tile` is a stage-kernel variant (NVARIANTS): a candidate tile of TILES2 /
+// TILES3, or one of the tile-0 variants for Peng-Robinson or a run-time limiter pair
 cudaError_t launch_stage(int nd, int nc, int mixed, int tile, const StageArgs& A, int grid, size_t smem,
                          cudaStream_t s, int ff = 0);
 size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim, int ff = 0);

@@ -40,6 +40,24 @@ def test_step_parity_random_state(n, bc):
     assert np.all(rel_field_diff(got, ref) < 1e-12), rel_field_diff(got, ref)
 
 
+@pytest.mark.parametrize("lims", [
+    (wl.LIM_VANLEER, wl.LIM_VANALBADA),
+    (wl.LIM_MC, wl.LIM_SUPERBEE),
+    (wl.LIM_CHAKRAVARTHY, wl.LIM_KOREN),
+    (wl.LIM_MINMOD, wl.LIM_MINMOD),
+])
+def test_step_parity_other_limiter_pairs(lims):
+    """Table 4.2's other limiters (the stage kernel's run-time limiter
+    variant; Koren/Minmod has compile-time kernels of its own)."""
+    w = wl.random_state(n=(37, 23), lim_vel=lims[0], lim_scalar=lims[1])
+    o, q, s = _pair(w)
+    dt = 0.3 * o.dt(q, 1.0)
+    s.step_dt(dt)
+    ref = oracle_step_dt(o, q, dt)
+    d = rel_field_diff(s.get_state(), ref)
+    assert np.all(d < 1e-12), d
+
+
 def test_cfl_dt_matches_oracle():
     w = wl.random_state(n=(50, 31))
     o, q, s = _pair(w)

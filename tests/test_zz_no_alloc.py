@@ -41,9 +41,11 @@ TOL = {fv.FV_FP64: 1e-12, fv.FV_MIXED: 1e-6}
 
 
 @pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
-def test_noalloc_matches_fv_rk_stage_twice(precision):
+@pytest.mark.parametrize("lims", [(wl.LIM_KOREN, wl.LIM_MINMOD), (wl.LIM_VANLEER, wl.LIM_MC)])
+def test_noalloc_matches_fv_rk_stage_twice(precision, lims):
     import torch
-    w = wl.random_state(n=(37, 23), bc=[[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2, [0, 0]])
+    w = wl.random_state(n=(37, 23), bc=[[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2, [0, 0]],
+                        lim_vel=lims[0], lim_scalar=lims[1])
     s = fv.Solver(w, precision=precision)
     s.set_state(w.primitives(), kind=fv.FV_PRIMITIVE)
     q = s.get_state()
