@@ -124,17 +124,18 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------- one form
-def _alg_flops_per_cell(job):
-    """Algorithmic FP64 flops of one stage_kernel launch per interior cell,
+def _alg_flops_per_cell(job, fused=False):
+    """Algorithmic FP64 flops of one stage-kernel launch per interior cell,
     counted from the formulas (+, -, *, /, sqrt, min, max, compare = 1, fused
     multiply-add = 2) for the 2D two-component stiffened-gas / ideal-gas
     plain scheme: 2 faces x 227 (MUSCL/THINC test 107, TDU of both sides 94,
-    Riemann 12, flux 14) + divergence and LSRK update 41.  None for other
-    schemes (only the HBM roofline is reported for them)."""
+    Riemann 12, flux 14) + divergence and LSRK update 41; the fused kernel
+    also recovers every cell's primitives once (App. B quadratic: 74).  None
+    for other schemes (only the HBM roofline is reported for them)."""
     w = job.w
     s = w.scheme
     if w.ndim == 2 and len(w.comps) == 2 and not s["iles"] and s["sigma"] == 0 and w.comps[0]["kind"] == 0:
-        return 495
+        return 495 + (74 if fused else 0)
     return None
 
 
@@ -162,15 +163,45 @@ def _ncu_traffic(job, form):
     return d.get(f"{job.name}/{form}")
 
 
+def record_traffic(args):
+    """--record-traffic CSV: average DRAM bytes (read + write) per stage_kernel
+    launch from an ncu ``--csv --log-file`` capture of this bench's own command
+    (metrics dram__bytes_read.sum, dram__bytes_write.sum), stored in
+    profiles/stage_traffic.json under the current CUDA source hash and the
+    workload/form the capture ran."""
+    import csv
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
+    per = {}
+    rows = [r for r in csv.reader(open(args.record_traffic)) if len(r) > 5]
+    hdr = rows[0]
+    ki, ii, mi, vi, ui = (hdr.index(k) for k in ("Kernel Name", "ID", "Metric Name", "Metric Value", "Metric Unit"))
+    for r in rows[1:]:
+        if ("stage_kernel" in r[ki] or "march2d_kernel" in r[ki]) and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            per[r[ii]] = per.get(r[ii], 0.0) + float(r[vi].replace(",", "")) * scale[r[ui]]
+    if not per or args.precision == "both":
+        raise SystemExit("need stage_kernel DRAM metrics in the CSV and --precision mixed|fp64")
+    job = _workload(args)
+    p = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    d = json.load(open(p)) if os.path.exists(p) else {}
+    d = {k: v for k, v in d.items() if k == _source_hash()}   # drop figures of older kernels
+    d.setdefault(_source_hash(), {})[f"{job.name}/{args.precision}"] = sum(per.values()) / len(per)
+    json.dump(d, open(p, "w"), indent=1, sort_keys=True)
+    print(json.dumps(dict(launches=len(per), bytes_per_launch=sum(per.values()) / len(per))))
+
+
 def _nprim(w):
     s = w.scheme
     return w.nvar + (2 if s["iles"] else 0) + (1 if (s["iles"] or s["sigma"] > 0) else 0)
 
 
-def _algorithmic_stage_bytes(job, precision):
-    """Compulsory HBM bytes of one stage_kernel launch: every interior cell's
-    primitives read once (fp32 in the mixed form, fp64 otherwise), q^0 read
-    and q^k written in FP64."""
+def _algorithmic_stage_bytes(job, precision, fused=False):
+    """Compulsory HBM bytes of one stage-kernel launch per the kernel's inputs
+    and outputs.  Tiled kernel: every interior cell's primitives read once
+    (fp32 in the mixed form, fp64 otherwise), q^0 read and q^k written (8
+    bytes a value: FP64 or float-float).  Fused kernel: q^{k-1} and q^0 read,
+    q^k written."""
+    if fused:
+        return job.cells * 3 * job.nvar * 8
     rs = 4 if precision == 1 else 8
     return job.cells * (_nprim(job.w) * rs + 2 * job.nvar * 8)
 
@@ -339,17 +370,23 @@ def main():
     ap.add_argument("--nx", type=int, default=2048)
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=192)
+    ap.add_argument("--cpu-rows", type=int, default=0,
+                    help="rows (2D) or planes (3D) of the CPU-baseline band (default: about 1e6 cells, 10-20 s)")
     ap.add_argument("--ref-rows", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=0, help="steps for the FP64 form (default: --steps)")
     ap.add_argument("--workload", default="shock_bubble", choices=WORKLOADS)
     ap.add_argument("--precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--ncases", type=int, default=1024)
+    ap.add_argument("--record-traffic", default="", help="ncu CSV of this command: store its stage_kernel DRAM "
+                    "bytes per launch in profiles/stage_traffic.json and exit")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 100 if args.workload == "jet3d" else 400
     if args.warmup < 3:
         args.warmup = 3
+    if args.record_traffic:
+        record_traffic(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -404,21 +441,23 @@ def main():
     def roof(r, precision):
         st = r["prof"]["stage"]
         avg_ms = st["ms"] / max(1, st["launches"])
-        byt = _algorithmic_stage_bytes(job, precision)
+        fused = bool(r["tile"].get("fused"))
+        byt = _algorithmic_stage_bytes(job, precision, fused)
         ach = byt / (avg_ms * 1e-3) / 1e9
         form = "mixed" if precision == fv.FV_MIXED else "fp64"
         out = dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
-                   traffic=_ncu_traffic(job, form), kernel="stage_kernel", avg_launch_ms=avg_ms,
+                   traffic=_ncu_traffic(job, form), kernel="march2d_kernel" if fused else "stage_kernel",
+                   avg_launch_ms=avg_ms,
                    algorithmic_bytes_per_launch=byt, peak_source=peaks["src"],
                    kernel_share={k: v["ms"] for k, v in r["prof"].items()}, tile=r["tile"])
-        fl = _alg_flops_per_cell(job)
+        fl = _alg_flops_per_cell(job, fused)
         if precision == fv.FV_FP64 and fl:
             # the FP64 form is bound by the FP64 pipe: 152 SMs x 2 DFMA/clock x
             # 2 flops at the 2070 MHz maximum SM clock
             peak = 152 * 2 * 2 * 2.070e9 / 1e12
             tf = fl * job.cells / (avg_ms * 1e-3) / 1e12
             out = dict(bound="alu", achieved=tf, peak=peak, unit="TFLOP/s", frac=tf / peak,
-                       traffic=out["traffic"], kernel="stage_kernel", avg_launch_ms=avg_ms,
+                       traffic=out["traffic"], kernel=out["kernel"], avg_launch_ms=avg_ms,
                        algorithmic_flops_per_launch=fl * job.cells,
                        peak_source="derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz",
                        hbm=dict(achieved=ach, peak=peaks["hbm"], frac=ach / peaks["hbm"],
@@ -441,9 +480,11 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cells, secs = cpu_oracle_rate(job, args.cpu_rows)
+        per_row = job.w.cells // job.w.n[job.w.ndim - 1]
+        rows = args.cpu_rows or max(1, min(job.w.n[job.w.ndim - 1], int(1.0e6 / per_row)))
+        rate, cells, secs = cpu_oracle_rate(job, rows)
         cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
-                   sample=f"one LSRK step of a {args.cpu_rows}-row band of {job.w.name} "
+                   sample=f"one LSRK step of a {rows}-{'plane' if job.w.ndim == 3 else 'row'} band of {job.w.name} "
                           f"({cells} cell-updates, {secs:.1f} s, single thread)")
 
     if rank == 0:

@@ -60,9 +60,13 @@ enum { FV_DIAG_TOTALS = 0,   /* double[nv]: compensated sums of q over the case 
        FV_DIAG_DT = 1,       /* double: last step's dt of the case */
        FV_DIAG_TIME = 2,     /* double: accumulated time of the case */
        FV_DIAG_ERROR = 3,    /* int: device error word (bit set of FV_ERRBIT_*) */
-       FV_DIAG_TILE = 4 };   /* double[8]: stage-kernel tile x, y, z, threads chosen by the
-                                autotuner (runs it if not yet run), then the tuner's
-                                per-candidate milliseconds (0 if not timed) */
+       FV_DIAG_TILE = 4 };   /* double[12]: stage-kernel tile x, y, z, threads chosen by the
+                                autotuner (runs it if not yet run; for the fused 2D
+                                kernel: strip width, rows per work item, 1, threads),
+                                [4..7] the tuner's milliseconds per tile (0 if not
+                                timed), [8] 1 if the fused kernel was chosen, [9] its
+                                best tuned milliseconds, [10] the primitive pass's,
+                                [11] the fused kernel variant (-1: tiled) */
 enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2 };
 
 /* Grid of one case.  lo/hi are the box corners (m); bc[d][0] is the low
@@ -148,10 +152,14 @@ fv_status fv_get_state_device(fv_ctx* ctx, int icase, int kind, double* dev);
  * stage 4 writes the new state).  Stages must be called in order. */
 fv_status fv_rk_stage(fv_ctx* ctx, int k, double dt);
 
-/* The first fv_rk_stage / fv_step of a context autotunes the stage kernel's
- * tile shape on the current state (a few timed launches per candidate that
- * write only a scratch register; cached per workload class for the process;
- * FV_TILE=<index> in the environment forces a candidate).  Set the state
+/* The first fv_rk_stage / fv_step of a context autotunes the stage kernel on
+ * the current state (a few timed launches per candidate that write only a
+ * scratch register; cached per workload class for the process).  Candidates:
+ * the tiled kernel's tile shapes (each after a primitive pass) and, for 2D
+ * grids in plain mode with the stiffened/ideal-gas closure, a fused kernel
+ * that recovers the primitives itself (one pass per stage, no primitive
+ * pass).  FV_TILE=<index> in the environment forces a tile of the tiled
+ * kernel, FV_FUSED=0/1 excludes or forces the fused kernel.  Set the state
  * first. */
 
 /* nsteps full steps: per step dt = cfl / max(sum_d (|u_d| + c)/dx_d) of each

@@ -1,6 +1,6 @@
 """Build the CUDA library libthinc_fv.so in-tree (nvcc, sm_103a only).
 
-The four translation units compile in parallel; nothing here needs a GPU.
+The translation units compile in parallel; nothing here needs a GPU.
 """
 from __future__ import annotations
 
@@ -14,8 +14,9 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libthinc_fv.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["fv_api.cu", "fv_prim.cu", "fv_stage2d.cu", "fv_stage2f.cu", "fv_stage3d.cu", "fv_stage3f.cu"]
-HEADERS = ["fv_device.cuh", "fv_kernels.cuh", "fv_launch.h", "fv_stage_inst.cuh"]
+SOURCES = ["fv_api.cu", "fv_prim.cu", "fv_march.cu", "fv_stage2d.cu", "fv_stage2f.cu", "fv_stage3d.cu",
+           "fv_stage3f.cu"]
+HEADERS = ["fv_device.cuh", "fv_kernels.cuh", "fv_launch.h", "fv_stage_inst.cuh", "fv_march.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "--expt-relaxed-constexpr",

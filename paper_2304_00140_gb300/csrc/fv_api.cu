@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/thinc_fv.h"
+#include "fv_march.cuh"
 #include "fv_launch.h"
 
 using namespace tfv;
@@ -27,10 +28,13 @@ const double LSRK_A[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t cases, items_stage, items_prim, q0, qa, qb, prim, io, smax, dt, t, err, in_u, partial, total;
-    int n_items_stage, n_items_prim;
+    size_t cases, items_stage, items_prim, items_march, q0, qa, qb, prim, io, smax, dt, t, err, in_u, partial, total;
+    int n_items_stage, n_items_prim, n_items_march;
     long long ntot_q, ntot_p, max_cells, n_in_u;
 };
+
+constexpr int MARCH_CHUNK_MIN = 16;                  // shortest row chunk of a fused-kernel work item
+constexpr int MARCH_CHUNKS[3] = {16, 32, 64};        // row chunks the tuner tries
 
 int tile_x(int nd) { return nd == 2 ? TileShape<2>::X : TileShape<3>::X; }
 int tile_y(int nd) { return nd == 2 ? TileShape<2>::Y : TileShape<3>::Y; }
@@ -73,6 +77,12 @@ struct fv_ctx {
     int stage_grid = 0, prim_grid = 0, n_items_cur = 0;
     float tune_ms[NTILES] = {0.f, 0.f, 0.f, 0.f};
     int tile = 0;                           // stage-kernel tile (TILES2 / TILES3 index)
+    // fused stage kernel (2D plain mode): one pass per stage, no primitive pass
+    bool fused_ok = false;                  // the context's scheme has a fused kernel
+    bool fused = false;                     // the fused kernel is in use
+    int mvar = 0, chunk = 0, march_grid = 0, n_items_march = 0;
+    int4* d_items_march = nullptr;
+    float march_ms = 0.f, prim_ms = 0.f;
     size_t smem_max = 0;                    // opt-in shared memory per block of the device
     bool tuned = false;
     int nsm = 0;
@@ -342,6 +352,8 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
         }
         L.n_items_stage += (int)nst;
         L.n_items_prim += (int)npr;
+        if (nd == 2)
+            L.n_items_march += ((C.n[0] + MARCH_COLS - 1) / MARCH_COLS) * ((C.n[1] + MARCH_CHUNK_MIN - 1) / MARCH_CHUNK_MIN);
         if (items_stage)
             for (int z = 0; z < C.n[2]; z += ts[2])
                 for (int y = 0; y < C.n[1]; y += ts[1])
@@ -360,6 +372,7 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
     L.cases = take(sizeof(CaseDesc) * ncases);
     L.items_stage = take(sizeof(int4) * L.n_items_stage);
     L.items_prim = take(sizeof(int4) * L.n_items_prim);
+    L.items_march = take(sizeof(int4) * std::max(1, L.n_items_march));
     L.q0 = take(sizeof(double) * nv * qoff);
     L.qa = take(sizeof(double) * nv * qoff);
     L.qb = take(sizeof(double) * nv * qoff);
@@ -435,9 +448,35 @@ static fv_status apply_tile(fv_ctx* x, int tile)
     const int occ = stage_occupancy(x->nd, x->nc, x->mixed, tile, smem, x->ff);
     if (occ < 1) return fail(x, FV_ERR_CUDA, "stage kernel tile cannot be resident%s");
     x->tile = tile;
+    x->fused = false;
     x->smem = smem;
     x->n_items_cur = (int)it.size();
     x->stage_grid = (int)std::min<long long>((long long)it.size(), (long long)x->nsm * occ);
+    return FV_OK;
+}
+
+// Fused kernel with row chunk `chunk` and variant `var`: work list of
+// (case, strip column, first row, rows) items.
+static fv_status apply_march(fv_ctx* x, int chunk, int var)
+{
+    const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
+    if (!t42) var = 2;
+    std::vector<int4> it;
+    for (size_t c = 0; c < x->cases.size(); ++c) {
+        const CaseDesc& C = x->cases[c];
+        for (int x0 = 0; x0 < C.n[0]; x0 += MARCH_COLS)
+            for (int y0 = 0; y0 < C.n[1]; y0 += chunk) it.push_back(make_int4((int)c, x0, y0, chunk));
+    }
+    if ((int)it.size() > x->L.n_items_march) return fail(x, FV_ERR_STATE, "fused work list overflow%s");
+    CK(x, cudaMemcpy(x->d_items_march, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
+    const int occ = march_occupancy(x->nc, x->mixed, var);
+    if (occ < 1) return fail(x, FV_ERR_CUDA, "fused stage kernel cannot be resident%s");
+    x->fused = true;
+    x->mvar = var;
+    x->chunk = chunk;
+    x->n_items_march = (int)it.size();
+    const long long warps = (long long)x->nsm * occ * MARCH_WARPS;
+    x->march_grid = (int)((std::min<long long>(warps, it.size()) + MARCH_WARPS - 1) / MARCH_WARPS);
     return FV_OK;
 }
 
@@ -457,7 +496,8 @@ static std::string tune_key(const fv_ctx* x)
     int lg = 0;
     while ((1LL << (lg + 1)) <= cells) ++lg;
     char buf[160];
-    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%d/%d", x->nd, x->nc, x->mixed, x->P.iles, x->P.csf, x->P.pr,
+    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%d%d/%d/%d", x->nd, x->nc, x->mixed, x->P.iles, x->P.csf, x->P.pr,
+             x->P.lim_vel, x->P.lim_scalar,
              x->ncases > 64 ? 2 : (x->ncases > 1 ? 1 : 0), lg);
     return buf;
 }
@@ -466,52 +506,93 @@ static fv_status tune(fv_ctx* x)
 {
     if (x->tuned) return FV_OK;
     x->tuned = true;
-    if (!tunable(x->P)) return apply_tile(x, 0);
+    int want_fused = -1;   // -1: the tuner decides; FV_FUSED=0/1 in the environment forces it
+    if (const char* f = getenv("FV_FUSED")) want_fused = atoi(f) ? 1 : 0;
+    if (!x->fused_ok) want_fused = 0;
     if (const char* f = getenv("FV_TILE")) {
         const int t = atoi(f);
         if (t >= 0 && t < NTILES) return apply_tile(x, t);
     }
-    const std::string key = tune_key(x);
+    const bool tiles = tunable(x->P);
+    if (!tiles && want_fused == 0) return apply_tile(x, 0);   // a single candidate
+    const std::string key = tune_key(x) + "/" + std::to_string(want_fused);
+    auto apply = [&](int code) {
+        return code < 100 ? apply_tile(x, code) : apply_march(x, MARCH_CHUNKS[(code - 100) / 10], (code - 100) % 10);
+    };
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) return apply_tile(x, it->second);
+        if (it != g_tune_cache.end()) return apply(it->second);
     }
     int err0 = 0;
     CK(x, cudaStreamSynchronize(x->stream));
     CK(x, cudaMemcpy(&err0, x->err, sizeof(int), cudaMemcpyDeviceToHost));
-    PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, x->Q0, x->prim, x->in_u, nullptr, x->err};
-    CK(x, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, x->stream, x->ff));
     cudaEvent_t e0, e1;
     CK(x, cudaEventCreate(&e0));
     CK(x, cudaEventCreate(&e1));
-    int best = 0;
-    float best_ms = 1e30f;
-    for (int t = 0; t < NTILES; ++t) {
-        fv_status s = apply_tile(x, t);
-        if (s) { x->msg.clear(); continue; }
-        StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, x->Q0, x->QB, x->dt, 0.0, x->err};
-        float tmin = 1e30f;
+    // one warm-up and three timed launches; the minimum of the timed ones
+    auto timed = [&](auto&& launch, float& tmin) -> fv_status {
+        tmin = 1e30f;
         for (int r = 0; r < 4; ++r) {
             CK(x, cudaEventRecord(e0, x->stream));
-            CK(x, launch_stage(x->nd, x->nc, x->mixed, t, sa, x->stage_grid, x->smem, x->stream, x->ff));
+            CK(x, launch());
             CK(x, cudaEventRecord(e1, x->stream));
             CK(x, cudaEventSynchronize(e1));
             float ms = 0.f;
             CK(x, cudaEventElapsedTime(&ms, e0, e1));
             if (r > 0) tmin = std::min(tmin, ms);
         }
-        x->tune_ms[t] = tmin;
-        if (tmin < best_ms) { best_ms = tmin; best = t; }
+        return FV_OK;
+    };
+    // the primitive pass: input of the tiled kernel, and part of its cost
+    // when the fused kernel (which needs none) competes
+    PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, x->Q0, x->prim, x->in_u, nullptr, x->err};
+    float prim_ms = 0.f;
+    fv_status st = timed([&] { return launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, x->stream, x->ff); },
+                         prim_ms);
+    if (st) return st;
+    int best = -1;
+    float best_ms = 1e30f;
+    if (want_fused != 1) {
+        for (int t = 0; t < (tiles ? NTILES : 1); ++t) {
+            if (apply_tile(x, t)) { x->msg.clear(); continue; }
+            StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, x->Q0, x->QB, x->dt, 0.0,
+                         x->err};
+            float ms = 0.f;
+            st = timed([&] { return launch_stage(x->nd, x->nc, x->mixed, x->tile, sa, x->stage_grid, x->smem,
+                                                 x->stream, x->ff); }, ms);
+            if (st) return st;
+            x->tune_ms[t] = ms;
+            const float cost = ms + (want_fused != 0 ? prim_ms : 0.f);
+            if (cost < best_ms) { best_ms = cost; best = t; }
+        }
     }
+    if (want_fused != 0) {
+        const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
+        float fbest = 1e30f;
+        for (int ci = 0; ci < 3; ++ci)
+            for (int var = (t42 ? 0 : 2); var < (t42 ? 2 : 3); ++var) {
+                if (apply_march(x, MARCH_CHUNKS[ci], var)) { x->msg.clear(); continue; }
+                MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, x->Q0, x->Q0, x->QB, x->in_u,
+                             x->dt, 0.0, x->err};
+                float ms = 0.f;
+                st = timed([&] { return launch_march(x->nc, x->mixed, x->mvar, ma, x->march_grid, x->stream); }, ms);
+                if (st) return st;
+                fbest = std::min(fbest, ms);
+                if (ms < best_ms) { best_ms = ms; best = 100 + 10 * ci + var; }
+            }
+        x->march_ms = fbest;
+    }
+    x->prim_ms = prim_ms;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(x, cudaMemcpy(x->err, &err0, sizeof(int), cudaMemcpyHostToDevice));
+    if (best < 0) return fail(x, FV_ERR_CUDA, "no stage kernel candidate can run%s");
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    return apply_tile(x, best);
+    return apply(best);
 }
 
 static fv_status init_common(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
@@ -559,6 +640,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     x->d_cases = reinterpret_cast<CaseDesc*>(b + L.cases);
     x->d_items_stage = reinterpret_cast<int4*>(b + L.items_stage);
     x->d_items_prim = reinterpret_cast<int4*>(b + L.items_prim);
+    x->d_items_march = reinterpret_cast<int4*>(b + L.items_march);
     x->Q0 = reinterpret_cast<double*>(b + L.q0);
     x->QA = reinterpret_cast<double*>(b + L.qa);
     x->QB = reinterpret_cast<double*>(b + L.qb);
@@ -599,6 +681,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
+    x->fused_ok = x->nd == 2 && !x->P.iles && !x->P.csf && !x->P.pr;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }
@@ -773,6 +856,22 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
     const double* in = k == 1 ? x->Q0 : (k == 2 ? x->QA : (k == 3 ? x->QB : x->QA));
     double* out = k == 1 ? x->QA : (k == 2 ? x->QB : (k == 3 ? x->QA : x->Q0));
     const bool cfl_here = (k == 1 && cfl > 0.0);
+    if (x->fused) {
+        // the CFL pass (primitive recovery without writing primitives), then
+        // one fused pass that recovers the primitives it needs itself
+        if (cfl_here) {
+            PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, in, nullptr, x->in_u, x->smax, x->err};
+            PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
+            x->launches++;
+            PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
+            x->launches++;
+        }
+        MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, in, x->Q0, out, x->in_u, x->dt,
+                     LSRK_A[k - 1], x->err};
+        PROF(FV_KERNEL_STAGE, launch_march(x->nc, x->mixed, x->mvar, ma, x->march_grid, s));
+        x->launches++;
+        return FV_OK;
+    }
     PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, in, x->prim, x->in_u,
                 cfl_here ? x->smax : nullptr, x->err};
     PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
@@ -836,8 +935,9 @@ static fv_status step_graph(fv_ctx* x, double cfl, cudaGraphExec_t* exec)
     return FV_OK;
 }
 
-// kernels per step: 4 prim + 1 dt + 4 stage
-static const int LAUNCHES_PER_STEP = 9;
+// kernels per step: 4 prim + 1 dt + 4 stage, or with the fused kernel
+// 1 CFL pass + 1 dt + 4 fused stages
+static int launches_per_step(const fv_ctx* x) { return x->fused ? 6 : 9; }
 
 extern "C" fv_status fv_step_async(fv_ctx* x, int nsteps, double cfl)
 {
@@ -858,7 +958,7 @@ extern "C" fv_status fv_step_async(fv_ctx* x, int nsteps, double cfl)
     s = step_graph(x, cfl, &ge);
     if (s) return s;
     for (int i = 0; i < nsteps; ++i) CK(x, cudaGraphLaunch(ge, x->stream));
-    x->launches += (long long)LAUNCHES_PER_STEP * nsteps;
+    x->launches += (long long)launches_per_step(x) * nsteps;
     return FV_OK;
 }
 
@@ -907,8 +1007,16 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
         if (s) return s;
         const TileDef td = tile_def(x->nd, variant_tile(x->tile));
         double* o = static_cast<double*>(out);
-        o[0] = td.x; o[1] = td.y; o[2] = td.z; o[3] = td.nt;
+        if (x->fused) {
+            o[0] = MARCH_COLS; o[1] = x->chunk; o[2] = 1; o[3] = 32 * MARCH_WARPS;
+        } else {
+            o[0] = td.x; o[1] = td.y; o[2] = td.z; o[3] = td.nt;
+        }
         for (int t = 0; t < NTILES; ++t) o[4 + t] = x->tune_ms[t];
+        o[8] = x->fused ? 1.0 : 0.0;
+        o[9] = x->march_ms;
+        o[10] = x->prim_ms;
+        o[11] = x->fused ? x->mvar : -1;
         return FV_OK;
     }
     if (what == FV_DIAG_ERROR) {

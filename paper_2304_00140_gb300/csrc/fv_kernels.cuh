@@ -50,11 +50,15 @@ template <> struct TileShape<3> { static constexpr int X = 32, Y = 4, Z = 2, NT 
 // NT (threads) is sized so the tile's faces take about two or three full
 // rounds; tile 0 is the default.
 // mb: resident blocks per SM the register allocation is sized for
-// (__launch_bounds__), trading registers for latency hiding.
-struct TileDef { int x, y, z, nt, mb; };
+// (__launch_bounds__), trading registers for latency hiding; nb: halo tile
+// buffers of the FP32 form (2: the next item's tile loads while this one
+// computes; 1: half the shared memory, more resident blocks).
+struct TileDef { int x, y, z, nt, mb, nb; };
 constexpr int NTILES = 4;
-constexpr TileDef TILES2[NTILES] = {{32, 8, 1, 288, 2}, {32, 8, 1, 288, 3}, {16, 16, 1, 288, 3}, {16, 16, 1, 288, 2}};
-constexpr TileDef TILES3[NTILES] = {{32, 4, 2, 256, 2}, {32, 4, 2, 256, 3}, {16, 8, 2, 320, 2}, {16, 4, 4, 320, 2}};
+constexpr TileDef TILES2[NTILES] = {{32, 8, 1, 288, 2, 2}, {32, 8, 1, 288, 3, 2}, {16, 16, 1, 288, 3, 2},
+                                    {16, 16, 1, 288, 2, 2}};
+constexpr TileDef TILES3[NTILES] = {{32, 4, 2, 256, 2, 1}, {16, 4, 4, 320, 2, 1}, {16, 8, 2, 320, 2, 1},
+                                    {16, 4, 4, 320, 2, 2}};
 constexpr TileDef tile_def(int nd, int i) { return nd == 2 ? TILES2[i] : TILES3[i]; }
 
 // Kernel variants of the stage kernel: 0 .. NTILES-1 stiffened/ideal-gas
@@ -102,7 +106,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // halo-tile buffers of the stage kernel: two (prefetch the next item) in the
 // FP32 form, one in the FP64 form (FP64-pipe bound; keeps 3D tiles in shared memory)
-template <typename R> constexpr int tile_buffers() { return sizeof(R) == 4 ? 2 : 1; }
+template <typename R, int NB> constexpr int tile_buffers() { return sizeof(R) == 4 ? NB : 1; }
 
 // Encoded liquid volume fraction (see the prim kernel): 1 when e is the
 // negated gas fraction (sign bit set, including -0 for pure liquid), else 0.
@@ -162,9 +166,10 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 #pragma unroll
             for (int v = 0; v < NV; ++v) { qc[v] = *qp; qp += P.ntot_q; }
             R w[NV], T, pabs, rho;
-            R* const pp0 = prim + C.poff + ((gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0]);
+            // prim == null: CFL pass only (the fused stage kernel recovers its own primitives)
+            R* const pp0 = prim ? prim + C.poff + ((gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0]) : nullptr;
             // Peng-Robinson Newton starts from this cell's previous temperature
-            const double T0 = PRC ? double(pp0[(ND + 1) * P.ntot_p]) : 0.0;
+            const double T0 = (PRC && pp0) ? double(pp0[(ND + 1) * P.ntot_p]) : 0.0;
             const int rst = prim_recover<ND, NC, R, PRC, Q>(P, qc, w, rho, T, pabs, T0);
             bool ok = rst == 0;
             if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
@@ -187,16 +192,16 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 if (!in_disc) rr = rho;
             }
             if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
-            {
+            if (pp0) {
                 R* o = pp0;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) { *o = w[v]; o += P.ntot_p; }
             }
-            if (P.aux_rc) {
+            if (pp0 && P.aux_rc) {
                 pp0[P.i_rho * P.ntot_p] = rr;
                 pp0[P.i_c * P.ntot_p] = cs;
             }
-            if (P.aux_al) {
+            if (pp0 && P.aux_al) {
                 // liquid volume fraction (Eq. A.1.4/A.1.5) stored as the smaller
                 // side: e = alpha_l if alpha_l <= alpha_g, else -alpha_g
                 // (alpha_g = 1 - alpha_l from the gas terms), so differences of
@@ -238,7 +243,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 }
 
 // ------------------------------------------------------------------ stage
-template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, int MB, bool PRC, int LIM, typename Q>
+template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, int MB, int NB, bool PRC, int LIM, typename Q>
 __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 {
     const Q* const q0reg = static_cast<const Q*>(A.q0);
@@ -254,7 +259,7 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* const spbuf = reinterpret_cast<R*>(smem_raw);        // two halo tiles [2][nprim][HC]
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
-    R* const sfx = spbuf + tile_buffers<R>() * P.nprim * HC; // fluxes per direction [NV][faces]
+    R* const sfx = spbuf + tile_buffers<R, NB>() * P.nprim * HC; // fluxes per direction [NV][faces]
     R* const sfy = sfx + NV * NFX;
     R* const sfz = sfy + NV * NFY;
     R* extra = (ND == 2) ? sfz : sfz + NV * NFZ;
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
         }
         cp_async_commit();
     };
-    constexpr int NBUF = tile_buffers<R>();
+    constexpr int NBUF = tile_buffers<R, NB>();
     int cur = 0;
     if (NBUF == 2) issue_tile(blockIdx.x, spbuf);
     for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
@@ -551,7 +556,7 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 }
 
 // dynamic shared memory of stage_kernel
-template <int ND, int NC, typename R, int TX, int TY, int TZ>
+template <int ND, int NC, typename R, int TX, int TY, int TZ, int NB>
 inline size_t stage_smem_bytes(int nprim)
 {
     constexpr int NV = ND + NC + 1;
@@ -559,7 +564,7 @@ inline size_t stage_smem_bytes(int nprim)
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
     constexpr int AC = (TX + 2) * (TY + 2) * ((ND == 3) ? TZ + 2 : 1);
     constexpr int VC = (TX + 1) * (TY + 1) * ((ND == 3) ? TZ + 1 : 1);
-    size_t n = tile_buffers<R>() * (size_t)nprim * HC + (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC +
+    size_t n = tile_buffers<R, NB>() * (size_t)nprim * HC + (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC +
                ND * VC;
     return n * sizeof(R) + HC + 16;
 }

@@ -22,7 +22,7 @@ template <> struct RegOf<1> { using type = float2; };
 #define FV_KERNEL(NC, I, FF)                                                                  \
     stage_kernel<FV_ND, NC, FV_REAL, tile_def(FV_ND, tile_of<I>()).x, tile_def(FV_ND, tile_of<I>()).y, \
                  tile_def(FV_ND, tile_of<I>()).z, tile_def(FV_ND, tile_of<I>()).nt,                    \
-                 tile_def(FV_ND, tile_of<I>()).mb, pr_of<I>(),                                         \
+                 tile_def(FV_ND, tile_of<I>()).mb, tile_def(FV_ND, tile_of<I>()).nb, pr_of<I>(),       \
                  lim_of<I>(), typename RegOf<FF>::type>
 
 template <int NC, int I, int FF>
@@ -49,7 +49,7 @@ template <int NC, int I, int FF>
 size_t bytes(int nprim)
 {
     constexpr TileDef t = tile_def(FV_ND, tile_of<I>());
-    return stage_smem_bytes<FV_ND, NC, FV_REAL, t.x, t.y, t.z>(nprim);
+    return stage_smem_bytes<FV_ND, NC, FV_REAL, t.x, t.y, t.z, t.nb>(nprim);
 }
 }  // namespace
 

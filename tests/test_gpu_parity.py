@@ -14,12 +14,21 @@ from tests.helpers import oracle_step_dt, oracle_step_window, rel_field_diff
 pytestmark = pytest.mark.gpu
 
 
-def _pair(w, precision=fv.FV_FP64):
-    o = oracle.Oracle(w)
+def _pair(w, precision=fv.FV_FP64, inflow_u=None):
+    o = oracle.Oracle(w, inflow_u=inflow_u)
     q = o.prim_to_cons(w.primitives())
-    s = fv.Solver(w, precision=precision)
+    s = fv.Solver(w, precision=precision, inflow_u=[inflow_u] if inflow_u is not None else None)
     s.set_state(q)
     return o, q, s
+
+
+# 2D plain-mode parity runs both stage kernels: the tiled one after a
+# primitive pass (FV_FUSED=0) and the fused one (FV_FUSED=1)
+FUSED = pytest.mark.parametrize("fused", ["0", "1"])
+
+
+def _check_kernel(s, fused):
+    assert s.tile()["fused"] == (fused == "1")
 
 
 @pytest.mark.parametrize("n,bc", [
@@ -30,13 +39,37 @@ def _pair(w, precision=fv.FV_FP64):
     ((33, 17), [[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_OUTFLOW, wl.BC_REFLECT], [0, 0]]),
     ((40, 1), None),                                             # one cell wide (1D through the 2D path)
 ])
-def test_step_parity_random_state(n, bc):
+@FUSED
+def test_step_parity_random_state(n, bc, fused, monkeypatch):
+    monkeypatch.setenv("FV_FUSED", fused)
     w = wl.random_state(n=n, bc=bc)
     o, q, s = _pair(w)
     dt = 0.3 * o.dt(q, 1.0)
     s.step_dt(dt)
     ref = oracle_step_dt(o, q, dt)
     got = s.get_state()
+    _check_kernel(s, fused)
+    assert np.all(rel_field_diff(got, ref) < 1e-12), rel_field_diff(got, ref)
+
+
+@FUSED
+def test_step_parity_inflow_disc_2d(fused, monkeypatch):
+    """x-low inflow boundary in 2D (Dirichlet u, T, Y inside the disc, a slip
+    wall outside it), with a per-cell inflow velocity profile."""
+    monkeypatch.setenv("FV_FUSED", fused)
+    w = wl.random_state(n=(41, 30), bc=[[wl.BC_INFLOW, wl.BC_OUTFLOW], [wl.BC_REFLECT, wl.BC_REFLECT], [0, 0]])
+    ly = w.n[1] * w.dx[1]
+    w.inflow = dict(yc=w.lo[1] + 0.4 * ly, zc=0.0, radius=0.3 * ly, T=310.0, Y=[0.7], u0=(40.0, 0.0, 0.0))
+    u = np.zeros((3, 1, w.n[1]))
+    u[0, 0] = 40.0 + 5.0 * np.sin(np.arange(w.n[1]))
+    u[1, 0] = 3.0 * np.cos(np.arange(w.n[1]))
+    o, q, s = _pair(w, inflow_u=u)
+    dt = 0.3 * o.dt(q, 1.0)
+    for _ in range(2):
+        s.step_dt(dt)
+    ref = oracle_step_dt(o, oracle_step_dt(o, q, dt), dt)
+    got = s.get_state()
+    _check_kernel(s, fused)
     assert np.all(rel_field_diff(got, ref) < 1e-12), rel_field_diff(got, ref)
 
 
@@ -46,15 +79,18 @@ def test_step_parity_random_state(n, bc):
     (wl.LIM_CHAKRAVARTHY, wl.LIM_KOREN),
     (wl.LIM_MINMOD, wl.LIM_MINMOD),
 ])
-def test_step_parity_other_limiter_pairs(lims):
-    """Table 4.2's other limiters (the stage kernel's run-time limiter
-    variant; Koren/Minmod has compile-time kernels of its own)."""
+@FUSED
+def test_step_parity_other_limiter_pairs(lims, fused, monkeypatch):
+    """Table 4.2's other limiters (the stage kernels' run-time limiter
+    variants; Koren/Minmod has compile-time kernels of its own)."""
+    monkeypatch.setenv("FV_FUSED", fused)
     w = wl.random_state(n=(37, 23), lim_vel=lims[0], lim_scalar=lims[1])
     o, q, s = _pair(w)
     dt = 0.3 * o.dt(q, 1.0)
     s.step_dt(dt)
     ref = oracle_step_dt(o, q, dt)
     d = rel_field_diff(s.get_state(), ref)
+    _check_kernel(s, fused)
     assert np.all(d < 1e-12), d
 
 
@@ -67,13 +103,16 @@ def test_cfl_dt_matches_oracle():
     assert np.all(rel_field_diff(s.get_state(), ref) < 1e-12)
 
 
-def test_advection_128_full_run_fp64():
+@FUSED
+def test_advection_128_full_run_fp64(fused, monkeypatch):
     """128^2 water column in air, 200 steps at CFL 0.4 (the full run)."""
+    monkeypatch.setenv("FV_FUSED", fused)
     w = wl.advection(n=128, steps=200)
     o, q, s = _pair(w)
     t_gpu = s.step(w.steps, w.cfl)
     ref, t_ref = o.step(q, w.steps, w.cfl)
     got = s.get_state()
+    _check_kernel(s, fused)
     d = rel_field_diff(got, ref)
     assert np.all(d < 1e-10), d
     assert t_gpu == pytest.approx(t_ref, rel=1e-12)
