@@ -455,6 +455,9 @@ static fv_status apply_tile(fv_ctx* x, int tile)
     return FV_OK;
 }
 
+// scheme features of the fused kernel (App. D switch, CSF)
+static int march_mode(const fv_ctx* x) { return (x->P.iles ? MARCH_ILES : 0) | (x->P.csf ? MARCH_CSF : 0); }
+
 // Fused kernel with row chunk `chunk` and variant `var`: work list of
 // (case, strip column, first row, rows) items.
 static fv_status apply_march(fv_ctx* x, int chunk, int var)
@@ -469,7 +472,7 @@ static fv_status apply_march(fv_ctx* x, int chunk, int var)
     }
     if ((int)it.size() > x->L.n_items_march) return fail(x, FV_ERR_STATE, "fused work list overflow%s");
     CK(x, cudaMemcpy(x->d_items_march, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
-    const int occ = march_occupancy(x->nc, x->mixed, var);
+    const int occ = march_occupancy(x->nc, x->mixed, march_mode(x), var);
     if (occ < 1) return fail(x, FV_ERR_CUDA, "fused stage kernel cannot be resident%s");
     x->fused = true;
     x->mvar = var;
@@ -571,12 +574,13 @@ static fv_status tune(fv_ctx* x)
         const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
         float fbest = 1e30f;
         for (int ci = 0; ci < 3; ++ci)
-            for (int var = (t42 ? 0 : 2); var < (t42 ? 2 : 3); ++var) {
+            for (int var = (t42 ? 0 : 2); var < (t42 ? 1 : 3); ++var) {
                 if (apply_march(x, MARCH_CHUNKS[ci], var)) { x->msg.clear(); continue; }
                 MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, x->Q0, x->Q0, x->QB, x->in_u,
                              x->dt, 0.0, x->err};
                 float ms = 0.f;
-                st = timed([&] { return launch_march(x->nc, x->mixed, x->mvar, ma, x->march_grid, x->stream); }, ms);
+                st = timed([&] { return launch_march(x->nc, x->mixed, march_mode(x), x->mvar, ma, x->march_grid,
+                                                     x->stream); }, ms);
                 if (st) return st;
                 fbest = std::min(fbest, ms);
                 if (ms < best_ms) { best_ms = ms; best = 100 + 10 * ci + var; }
@@ -681,7 +685,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
-    x->fused_ok = x->nd == 2 && !x->P.iles && !x->P.csf && !x->P.pr;
+    x->fused_ok = x->nd == 2 && !x->P.pr;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }
@@ -868,7 +872,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
         }
         MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, in, x->Q0, out, x->in_u, x->dt,
                      LSRK_A[k - 1], x->err};
-        PROF(FV_KERNEL_STAGE, launch_march(x->nc, x->mixed, x->mvar, ma, x->march_grid, s));
+        PROF(FV_KERNEL_STAGE, launch_march(x->nc, x->mixed, march_mode(x), x->mvar, ma, x->march_grid, s));
         x->launches++;
         return FV_OK;
     }

@@ -20,14 +20,13 @@ cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem, int
 int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem, int ff = 0);   // blocks per SM (0: cannot run)
 int prim_occupancy(int nd, int nc, int mixed);
 
-// fused 2D stage kernel (fv_march.cuh), plain mode, stiffened/ideal-gas closure.
-// var: 0 / 1 Table 4.2 limiter pair sized for 4 / 5 (FP32) or 2 / 3 (FP64)
-// resident blocks per SM, 2 limiter pair read at run time.  mixed = 1: float-float registers.
+// fused 2D stage kernel (fv_march.cuh), stiffened/ideal-gas closure.
+// mode: MARCH_ILES | MARCH_CSF bits of the scheme.  var: 0 Table 4.2 limiter
+// pair, 2 limiter pair read at run time.  mixed = 1: float-float registers.
 struct MarchArgs;
 constexpr int MARCH_WARPS = 4;
-constexpr int MARCH_VARIANTS = 3;
-cudaError_t launch_march(int nc, int mixed, int var, const MarchArgs& A, int grid, cudaStream_t s);
-int march_occupancy(int nc, int mixed, int var);   // blocks per SM
+cudaError_t launch_march(int nc, int mixed, int mode, int var, const MarchArgs& A, int grid, cudaStream_t s);
+int march_occupancy(int nc, int mixed, int mode, int var);   // blocks per SM
 
 // state I/O and diagnostics (FP64)
 struct IoArgs {

@@ -1,15 +1,19 @@
-// fv_march.cuh -- fused stage kernel for 2D grids in plain mode (no App. D
-// switch, no CSF, stiffened/ideal-gas closure): one pass per LSRK stage that
-// reads the stage's input register q^{k-1}, recovers the primitives (App. B)
-// with the boundary update, reconstructs, does the TDU and the all-Mach flux
-// on every face and writes q^k = q^0 + a_k dt R (Algorithm 1, Sec. 3.1).
+// fv_march.cuh -- fused stage kernel for 2D grids with the stiffened/ideal-gas
+// closure: one pass per LSRK stage that reads the stage's input register
+// q^{k-1}, recovers the primitives (App. B) with the boundary update,
+// evaluates the App. D sensor (Eq. D.4) and the CSF source (Sec. 3.5,
+// Eq. 3-9/3-10), reconstructs, does the TDU and the all-Mach flux on every
+// face and writes q^k = q^0 + a_k dt R (Algorithm 1, Sec. 3.1).
 //
 // Layout of the work: each warp owns a strip of 32 columns -- lanes 2..29 are
 // the strip's cells, lanes 0, 1, 30, 31 its halo -- and marches along y over
-// a chunk of rows, keeping the four rows of the y-face stencil in registers.
-// The x-face stencil comes from neighbouring lanes (warp shuffles), the y-face
-// flux of the previous row is carried in registers, so the kernel uses no
-// shared memory and no block barrier, and no primitive field goes through HBM.
+// a chunk of rows, keeping the four rows y-1 .. y+2 in registers.  Neighbours
+// in x come from other lanes (warp shuffles); per-row quantities that the
+// next row needs (the y-flux, the sensor flag, the smoothed fraction and the
+// vertex normals of the row's upper edge) are carried in registers.  The
+// kernel uses no shared memory and no block barrier, and no primitive field
+// goes through HBM.  Every formula follows the tiled kernel's operation
+// order, so both give the same sensor decisions and the same rounding.
 #pragma once
 
 #include "fv_kernels.cuh"
@@ -31,6 +35,8 @@ struct MarchArgs {
 };
 
 constexpr int MARCH_COLS = 28;   // cells per strip (32 lanes minus 2 + 2 halo)
+// scheme features of a fused-kernel instantiation
+constexpr int MARCH_ILES = 1, MARCH_CSF = 2;
 
 // Inflow-disc test of an x-low ghost cell in source row iy (FP64, the same
 // expression as the primitive pass).  Not inlined: only lanes on an inflow
@@ -41,11 +47,21 @@ static __device__ __noinline__ bool march_in_disc(const CaseDesc& C, int iy)
     return yy * yy <= C.in_r2;
 }
 
-template <int NC, typename R, int NWARP, int MB, int LIM, typename Q>
+// one row of the window: primitives, and for App. D / CSF the cell density,
+// sound speed and encoded liquid fraction (e = alpha_l, or -alpha_g when the
+// gas is the smaller side; see the primitive pass)
+template <int NV, typename R> struct MRow {
+    R w[NV];
+    R rho, c, e;
+};
+
+template <int NC, typename R, int NWARP, int MB, int LIM, int MODE, typename Q>
 __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 {
     constexpr int ND = 2, NV = ND + NC + 1;
+    constexpr bool ILES = (MODE & MARCH_ILES) != 0, CSF = (MODE & MARCH_CSF) != 0, AUX = ILES || CSF;
     const DevParams& P = A.P;
+    const ConstT<R>& Kc = K<R>(P);
     const Q* const qin = static_cast<const Q*>(A.qin);
     const Q* const q0reg = static_cast<const Q*>(A.q0);
     Q* const qoreg = static_cast<Q*>(A.qout);
@@ -64,10 +80,10 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
         const R ci0 = pick<R>(C.idx[0], C.fidx[0]), ci1 = pick<R>(C.idx[1], C.fidx[1]);
         const Q* const qcase = qin + C.qoff;
 
-        // primitives (u, v, p', T, Y) of this lane's cell in row y, ghosts
-        // through the boundary update exactly as the primitive pass does it;
-        // the row's conserved values are fetched one row ahead (fetch_row)
-        // and recovered when the row enters the window (recover_row)
+        // a row enters the window in two parts: its conserved values are
+        // fetched one row ahead (fetch_row) and recovered when it enters
+        // (recover_row), ghosts through the boundary update exactly as the
+        // primitive pass does it
         struct RowRef { int iy, fy, disc; };
         auto fetch_row = [&](int y, Q* qc, RowRef& rr) {
             int iny;
@@ -77,10 +93,12 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 #pragma unroll
             for (int v = 0; v < NV; ++v) { qc[v] = *qp; qp += P.ntot_q; }
         };
-        auto recover_row = [&](const Q* qc, const RowRef& rr, R* w) {
+        auto recover_row = [&](const Q* qc, const RowRef& rr, MRow<NV, R>& row) {
+            R* const w = row.w;
             R rho, T, pabs;
             const int rst = prim_recover<ND, NC, R, false, Q>(P, qc, w, rho, T, pabs, 0.0);
-            if (rst) set_err(A.err, rst == ERR_NONCONV ? ERR_NONCONV : ERR_NONPHYS);
+            bool ok = rst == 0;
+            if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
             if (inx ? !rr.disc : fx) w[0] = -w[0];
             if (rr.fy) w[1] = -w[1];
             if (rr.disc) {
@@ -90,27 +108,143 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                 w[ND + 1] = R(C.in_T);
 #pragma unroll
                 for (int k = 0; k < NC - 1; ++k) w[ND + 2 + k] = R(C.in_Y[k]);
-                R r_, e_, c_;
-                if (!tdu<NC, R, false>(P, w[ND], w[ND + 1], w + ND + 2, r_, e_, c_)) set_err(A.err, ERR_NONPHYS);
+            }
+            R rr_ = rho, cs = R(0);
+            if (ILES || rr.disc) {
+                R e_;
+                ok = tdu<NC, R, false>(P, w[ND], w[ND + 1], w + ND + 2, rr_, e_, cs) && ok;
+                if (!rr.disc) rr_ = rho;
+            }
+            if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
+            row.rho = rr_;
+            row.c = cs;
+            if (AUX) {
+                R s = R(0), al = R(0), ag = R(0);
+#pragma unroll
+                for (int k = 0; k < NC - 1; ++k) s += clip01(w[ND + 2 + k]);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    const R Yk = (k == NC - 1) ? clip01(R(1) - s) : clip01(w[ND + 2 + k]);
+                    const R a = fdiv(rr_ * Yk * Kc.gm1cv[k] * w[ND + 1], Kc.Pk[k] + w[ND]);
+                    if (k == P.liquid) al = a; else ag += a;
+                }
+                row.e = (al <= ag) ? al : -ag;
+            } else {
+                row.e = R(0);
             }
         };
-        auto load_row = [&](int y, R* w) {
-            Q qc[NV];
-            RowRef rr;
-            fetch_row(y, qc, rr);
-            recover_row(qc, rr, w);
+        auto shl = [&](R v) { return __shfl_up_sync(FULL, v, 1); };     // value of lane - 1
+        auto shr = [&](R v) { return __shfl_down_sync(FULL, v, 1); };   // value of lane + 1
+
+        // App. D cell sensor f (Eq. D.4) of window row m (rows m-1 .. m+1)
+        auto sensor = [&](const MRow<NV, R>* Wr, int m) -> int {
+            R g[2][2];
+            R tg = R(0);
+            const R e0 = Wr[m].e;
+            const R o0 = liq_side(e0);
+            {
+                const R inv2dx = R(0.5) * ci0;
+#pragma unroll
+                for (int a = 0; a < ND; ++a) g[a][0] = (shr(Wr[m].w[a]) - shl(Wr[m].w[a])) * inv2dx;
+                const R em = shl(e0), ep = shr(e0);
+                tg += fabs((e0 - em) + (o0 - liq_side(em))) + fabs((ep - e0) + (liq_side(ep) - o0));
+            }
+            {
+                const R inv2dx = R(0.5) * ci1;
+#pragma unroll
+                for (int a = 0; a < ND; ++a) g[a][1] = (Wr[m + 1].w[a] - Wr[m - 1].w[a]) * inv2dx;
+                const R em = Wr[m - 1].e, ep = Wr[m + 1].e;
+                tg += fabs((e0 - em) + (o0 - liq_side(em))) + fabs((ep - e0) + (liq_side(ep) - o0));
+            }
+            R div = R(0);
+#pragma unroll
+            for (int a = 0; a < ND; ++a) div += g[a][a];
+            const R wz = g[1][0] - g[0][1];
+            const R curl2 = wz * wz;
+            const R d2 = div * div;
+            const R thD = fdiv(d2, d2 + curl2 + Kc.eps_ducros);
+            return (thD > Kc.thr_ducros || tg > Kc.thr_gas) ? 1 : 0;
+        };
+        // CSF smoothed fraction (Eq. 3-9) of window row m, encoded like e
+        auto smooth = [&](const MRow<NV, R>* Wr, int m) -> R {
+            R s = R(0), W1 = R(0);
+#pragma unroll
+            for (int b = -1; b <= 1; ++b) {
+                const R ec = Wr[m + b].e;
+                const R el = shl(ec), er = shr(ec);
+                const R wb = R(b == 0 ? 2 : 1);
+                s += wb * el;
+                W1 += wb * liq_side(el);
+                s += (R(2) * wb) * ec;
+                W1 += (R(2) * wb) * liq_side(ec);
+                s += wb * er;
+                W1 += wb * liq_side(er);
+            }
+            const R norm = R(16);
+            return (s + W1 > R(0.5) * norm) ? -(((norm - W1) - s) / norm) : (s + W1) / norm;
+        };
+        const R cdx0 = pick<R>(C.dx[0], C.fdx[0]), cdx1 = pick<R>(C.dx[1], C.fdx[1]);
+        const R gthr = Kc.grad_eps / fmin(cdx0, cdx1);
+        // vertex between this lane's and the next lane's cells of two rows,
+        // values (lo row: a0, a1 = lane+1; hi row: b0, b1): gradient sums of
+        // the encoded fraction with the liquid-side offsets summed apart
+        auto vgrad = [&](R a0, R a1, R b0, R b1, R* gu) {
+            R g0 = R(0), g1 = R(0), o0 = R(0), o1 = R(0);
+            const R ev[4] = {a0, a1, b0, b1};
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int bx = cc & 1, by = (cc >> 1) & 1;
+                const R e = ev[cc], oc = liq_side(e);
+                g0 += bx ? e : -e; o0 += bx ? oc : -oc;
+                g1 += by ? e : -e; o1 += by ? oc : -oc;
+            }
+            gu[0] = g0 + o0;
+            gu[1] = g1 + o1;
+        };
+        // unit normal at that vertex from the smoothed fractions of two rows
+        auto vnormal = [&](R alo, R ahi, R* n) {
+            R g[2];
+            vgrad(alo, shr(alo), ahi, shr(ahi), g);
+            g[0] = g[0] * ci0 * R(0.5);
+            g[1] = g[1] * ci1 * R(0.5);
+            R mag2 = R(0);
+            mag2 += g[0] * g[0];
+            mag2 += g[1] * g[1];
+            const R mag = sq_rt(mag2);
+            const R inv = (mag > gthr) ? frcp(mag) : R(0);
+            n[0] = g[0] * inv;
+            n[1] = g[1] * inv;
         };
 
         const int y0 = wi.z, y1 = min(wi.z + wi.w, n1);
-        R W[4][NV];
-        load_row(y0 - 2, W[0]);
-        load_row(y0 - 1, W[1]);
-        load_row(y0, W[2]);
-        load_row(y0 + 1, W[3]);
-        R r4[4], c4[4];   // App. D impedance inputs (unused in plain mode)
+        MRow<NV, R> W[4];
+        {
+            Q qc[NV];
+            RowRef rr;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) { fetch_row(y0 - 2 + m, qc, rr); recover_row(qc, rr, W[m]); }
+        }
+        // carried per-row quantities of row y
+        int flag_y = 1;          // App. D sensor
+        R at_y = R(0);           // smoothed fraction
+        R nlo[2] = {R(0), R(0)}; // unit normal at the vertex (lane + 1/2, y - 1/2)
+        R r4[4] = {R(0), R(0), R(0), R(0)}, c4[4] = {R(0), R(0), R(0), R(0)};
         R Fy[NV];
         {
-            const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, W, r4, c4, 1, Fy);
+            int flag_lo = 1;
+            if (ILES) { flag_lo = sensor(W, 1); flag_y = sensor(W, 2); }
+            if (CSF) {
+                const R at_lo = smooth(W, 1);
+                at_y = smooth(W, 2);
+                vnormal(at_lo, at_y, nlo);
+            }
+            R ws[4][NV];
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) ws[s][v] = W[s].w[v];
+            if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
+            const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, ws, r4, c4, flag_lo | flag_y, Fy);
             if (!ok && own_col) set_err(A.err, ERR_NONPHYS);
         }
         const double adt = A.a * A.dt[wi.x];
@@ -128,41 +262,100 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                 for (int v = 0; v < NV; ++v) { q0r[v] = own_col ? *qp : Q{}; qp += P.ntot_q; }
             }
             // advance the window: rows y-1 .. y+2; fetch row y+3 for the next round
-#pragma unroll
-            for (int v = 0; v < NV; ++v) { W[0][v] = W[1][v]; W[1][v] = W[2][v]; W[2][v] = W[3][v]; }
+            W[0] = W[1];
+            W[1] = W[2];
+            W[2] = W[3];
             recover_row(qn, rn, W[3]);
             if (y + 1 < y1) fetch_row(y + 3, qn, rn);
+            // sensor of row y+1 (the y face needs rows y and y+1)
+            int flag_up = 1;
+            if (ILES) flag_up = sensor(W, 2);
             // y face y+1/2
             R Fyn[NV];
             {
-                const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, W, r4, c4, 1, Fyn);
+                R ws[4][NV];
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) ws[s][v] = W[s].w[v];
+                if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
+                const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, ws, r4, c4, flag_y | flag_up, Fyn);
                 if (!ok && own_col) set_err(A.err, ERR_NONPHYS);
             }
             // x face between this lane's cell and the next, row y
-            R ws[4][NV], Fx[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                ws[1][v] = W[1][v];
-                ws[0][v] = __shfl_up_sync(FULL, W[1][v], 1);
-                ws[2][v] = __shfl_down_sync(FULL, W[1][v], 1);
-                ws[3][v] = __shfl_down_sync(FULL, W[1][v], 2);
-            }
+            R Fx[NV];
             {
-                const bool ok = face_flux<ND, NC, R, false, LIM>(P, 0, ws, r4, c4, 1, Fx);
+                R ws[4][NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    ws[1][v] = W[1].w[v];
+                    ws[0][v] = shl(W[1].w[v]);
+                    ws[2][v] = shr(W[1].w[v]);
+                    ws[3][v] = __shfl_down_sync(FULL, W[1].w[v], 2);
+                }
+                int fl = 1;
+                if (ILES) {
+                    r4[1] = W[1].rho; r4[2] = shr(W[1].rho);
+                    c4[1] = W[1].c; c4[2] = shr(W[1].c);
+                    fl = flag_y | __shfl_down_sync(FULL, flag_y, 1);
+                }
+                const bool ok = face_flux<ND, NC, R, false, LIM>(P, 0, ws, r4, c4, fl, Fx);
                 if (!ok && (own_col || own_right)) set_err(A.err, ERR_NONPHYS);
+            }
+            // CSF source of this lane's cell (momentum, energy)
+            R S[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) S[v] = R(0);
+            if (CSF) {
+                const R at_up = smooth(W, 2);
+                R nhi[2];
+                vnormal(at_y, at_up, nhi);
+                // unsmoothed-fraction gradients at the two right-hand vertices
+                R glo[2], ghi[2];
+                vgrad(W[0].e, shr(W[0].e), W[1].e, shr(W[1].e), glo);
+                vgrad(W[1].e, shr(W[1].e), W[2].e, shr(W[2].e), ghi);
+                // the cell's vertices in the tiled kernel's order: (-,-), (+,-), (-,+), (+,+)
+                const R nv[4][2] = {{shl(nlo[0]), shl(nlo[1])}, {nlo[0], nlo[1]},
+                                    {shl(nhi[0]), shl(nhi[1])}, {nhi[0], nhi[1]}};
+                const R gv[4][2] = {{shl(glo[0]), shl(glo[1])}, {glo[0], glo[1]},
+                                    {shl(ghi[0]), shl(ghi[1])}, {ghi[0], ghi[1]}};
+                R kappa = R(0), ga[2] = {R(0), R(0)};
+                const R cis[2] = {ci0, ci1};
+#pragma unroll
+                for (int vtx = 0; vtx < 4; ++vtx) {
+                    const int ox = vtx & 1, oy = (vtx >> 1) & 1;
+#pragma unroll
+                    for (int d = 0; d < 2; ++d) {
+                        const int od = d == 0 ? ox : oy;
+                        kappa -= (od ? nv[vtx][d] : -nv[vtx][d]) * cis[d] * R(0.5);
+                        ga[d] += gv[vtx][d] * cis[d] * R(0.5);
+                    }
+                }
+                R udg = R(0);
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    ga[d] *= R(0.25);
+                    S[1 + d] = Kc.sigma * kappa * ga[d];
+                    udg += W[1].w[d] * ga[d];
+                }
+                S[1 + ND] = Kc.sigma * kappa * udg;
+                at_y = at_up;
+                nlo[0] = nhi[0];
+                nlo[1] = nhi[1];
             }
             // divergence and LSRK update of this lane's cell
             Q* qo = qoreg + gcell;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const R Fxm = __shfl_up_sync(FULL, Fx[v], 1);
+                const R Fxm = shl(Fx[v]);
                 R div = (Fx[v] - Fxm) * ci0;
                 div += (Fyn[v] - Fy[v]) * ci1;
-                const R Rv = R(0) - div;
+                const R Rv = S[v] - div;
                 if (own_col) *qo = lsrk_update(q0r[v], adt, adtf, Rv);
                 qo += P.ntot_q;
                 Fy[v] = Fyn[v];
             }
+            flag_y = flag_up;
         }
     }
 }

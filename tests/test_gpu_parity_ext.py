@@ -33,7 +33,14 @@ def _scale_momentum(d, w, got, ref):
     return d
 
 
-def test_csf_droplet_parity():
+# 2D cases run both stage kernels: tiled after a primitive pass (FV_FUSED=0)
+# and fused (FV_FUSED=1)
+FUSED = pytest.mark.parametrize("fused", ["0", "1"])
+
+
+@FUSED
+def test_csf_droplet_parity(fused, monkeypatch):
+    monkeypatch.setenv("FV_FUSED", fused)
     w = wl.droplet(n=(40, 36), A=0.15, sigma=30.0)
     o, q, got, ref = _run_pair(w, steps_dt=3)
     S = o.csf_source(q)
@@ -42,13 +49,28 @@ def test_csf_droplet_parity():
     assert np.all(d < 1e-11), d
 
 
-def test_iles_switch_parity_2d():
+@FUSED
+def test_iles_switch_parity_2d(fused, monkeypatch):
+    monkeypatch.setenv("FV_FUSED", fused)
     w = wl.random_state(n=(40, 33), iles=1)
     o = oracle.Oracle(w)
     f = o.sensor(o.prim_to_cons(w.primitives()))
     assert 0.05 < f.mean() < 0.95          # both branches of Eq. D.3 are exercised
     o, q, got, ref = _run_pair(w, steps_dt=2)
     d = rel_field_diff(got, ref)
+    assert np.all(d < 1e-11), d
+
+
+@FUSED
+@pytest.mark.parametrize("ncomp", [2, 3])
+def test_iles_csf_2d_parity(ncomp, fused, monkeypatch):
+    """App. D switch and CSF together in 2D, two or three components, mixed
+    boundary kinds."""
+    monkeypatch.setenv("FV_FUSED", fused)
+    w = wl.random_state(n=(45, 31), ncomp=ncomp, iles=1, sigma=5.0,
+                        bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_PERIODIC] * 2, [0, 0]])
+    o, q, got, ref = _run_pair(w, steps_dt=2)
+    d = _scale_momentum(rel_field_diff(got, ref), w, got, ref)
     assert np.all(d < 1e-11), d
 
 
@@ -85,7 +107,9 @@ def test_jet_inflow_parity():
     assert np.all(d < 1e-11), d
 
 
-def test_droplet_batch_matches_single_and_oracle():
+@FUSED
+def test_droplet_batch_matches_single_and_oracle(fused, monkeypatch):
+    monkeypatch.setenv("FV_FUSED", fused)
     cases = [wl.droplet(n=n, A=a, sigma=20.0) for n, a in ((24, 0.1), (40, 0.2), (33, 0.05), (16, 0.15))]
     qs = [oracle.Oracle(c).prim_to_cons(c.primitives()) for c in cases]
     b = fv.Solver(cases)
