@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
     constexpr bool ILES = (MODE & MARCH_ILES) != 0, CSF = (MODE & MARCH_CSF) != 0, AUX = ILES || CSF;
     const DevParams& P = A.P;
     const ConstT<R>& Kc = K<R>(P);
-    const Q* const qin = static_cast<const Q*>(A.qin);
+    // q^{k-1} never aliases q^k (the stages go q0 -> qA -> qB -> qA -> q0)
+    const Q* __restrict__ const qin = static_cast<const Q*>(A.qin);
     const Q* const q0reg = static_cast<const Q*>(A.q0);
     Q* const qoreg = static_cast<Q*>(A.qout);
     const unsigned FULL = 0xffffffffu;
@@ -70,7 +71,11 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
     for (int it = blockIdx.x * NWARP + (threadIdx.x >> 5); it < A.nitems; it += gridDim.x * NWARP) {
         const int4 wi = A.items[it];
         const CaseDesc& C = A.cases[wi.x];
+        // the case's fields in registers (the row loop stores to q^k, which the
+        // compiler cannot tell apart from the case table)
         const int n0 = C.n[0], n1 = C.n[1];
+        const int bcy0 = C.bc[1][0], bcy1 = C.bc[1][1];
+        const long long qoff = C.qoff;
         // this lane's column and its boundary mapping (fixed along the strip)
         const int col = wi.y - 2 + lane;
         int fx, inx;
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
         const bool own_col = lane >= 2 && lane < 30 && col < n0;
         const bool own_right = lane >= 1 && lane < 29 && col + 1 < n0;   // lane + 1 owns a cell
         const R ci0 = pick<R>(C.idx[0], C.fidx[0]), ci1 = pick<R>(C.idx[1], C.fidx[1]);
-        const Q* const qcase = qin + C.qoff;
+        const Q* __restrict__ const qcase = qin + qoff;
 
         // a row enters the window in two parts: its conserved values are
         // fetched one row ahead (fetch_row) and recovered when it enters
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
         struct RowRef { int iy, fy, disc; };
         auto fetch_row = [&](int y, Q* qc, RowRef& rr) {
             int iny;
-            rr.iy = map_index(n1, y, C.bc[1][0], C.bc[1][1], rr.fy, iny);
+            rr.iy = map_index(n1, y, bcy0, bcy1, rr.fy, iny);
             rr.disc = inx ? (march_in_disc(C, rr.iy) ? 1 : 0) : 0;
             const Q* qp = qcase + (rr.iy * n0 + (rr.disc ? 0 : ix));
 #pragma unroll
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
         for (int y = y0; y < y1; ++y) {
             // q^0 of this lane's cell, loaded early so its latency hides
             Q q0r[NV];
-            const long long gcell = C.qoff + ((long long)y * n0 + (own_col ? col : 0));
+            const long long gcell = qoff + ((long long)y * n0 + (own_col ? col : 0));
             {
                 const Q* qp = q0reg + gcell;
 #pragma unroll
