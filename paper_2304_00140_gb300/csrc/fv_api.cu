@@ -264,6 +264,16 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
                 P.prc.isqTc[i][j] = 1.0 / std::sqrt(Tc);
             }
         }
+        for (int i = 0; i < MAXC; ++i) {
+            P.prcf.b[i] = float(P.prc.b[i]);
+            P.prcf.iM[i] = float(P.prc.iM[i]);
+            P.prcf.cv[i] = float(P.prc.cv[i]);
+            for (int j = 0; j < MAXC; ++j) {
+                P.prcf.A[i][j] = float(P.prc.A[i][j]);
+                P.prcf.cc[i][j] = float(P.prc.cc[i][j]);
+                P.prcf.isqTc[i][j] = float(P.prc.isqTc[i][j]);
+            }
+        }
         P.single_class = 1;
     }
     // working-precision copies of the constants

@@ -56,10 +56,12 @@ struct CompDev {
 // Peng-Robinson constants (Eq. A.2.1): per species b_k, 1/M_k, cv_k; per
 // species pair A_ab = 0.457236 (R Tc_ab)^2 / pc_ab, c_ab (acentric term) and
 // 1/sqrt(Tc_ab).  Always used in FP64.
-struct PRConst {
-    double b[MAXC], iM[MAXC], cv[MAXC];
-    double A[MAXC][MAXC], cc[MAXC][MAXC], isqTc[MAXC][MAXC];
+template <typename F>
+struct PRConstT {
+    F b[MAXC], iM[MAXC], cv[MAXC];
+    F A[MAXC][MAXC], cc[MAXC][MAXC], isqTc[MAXC][MAXC];
 };
+using PRConst = PRConstT<double>;
 
 // Scheme constants, passed by value to every kernel (kernel-parameter bank).
 struct DevParams {
@@ -79,6 +81,7 @@ struct DevParams {
     ConstT<float> kf;
     int pr;              // every component is Peng-Robinson
     PRConst prc;
+    PRConstT<float> prcf;  // FP32 copy (the mixed form's face TDU)
 };
 
 template <typename R> __device__ __forceinline__ const ConstT<R>& K(const DevParams& P);
@@ -171,115 +174,154 @@ __device__ __forceinline__ void recips(const R* P, R* iP)
 constexpr double PR_RU = 8.314462618;
 constexpr double SQRT2 = 1.4142135623730951;
 
-template <int NC>
+template <int NC, typename F = double>
 struct PRMix {
-    double X[NC], M, b, cvig;
+    F X[NC], M, b, cvig;
 };
 
-template <int NC>
-__device__ __forceinline__ void pr_mix(const DevParams& P, const double* Y, PRMix<NC>& m)
+// PR constants in the working precision
+template <typename F> __device__ __forceinline__ const PRConstT<F>& prk(const DevParams& P);
+template <> __device__ __forceinline__ const PRConstT<double>& prk<double>(const DevParams& P) { return P.prc; }
+template <> __device__ __forceinline__ const PRConstT<float>& prk<float>(const DevParams& P) { return P.prcf; }
+
+// math of the working precision (the CUDA library functions of each type)
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_cbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float m_cbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double m_acos(double x) { return acos(x); }
+__device__ __forceinline__ float m_acos(float x) { return acosf(x); }
+__device__ __forceinline__ double m_cos(double x) { return cos(x); }
+__device__ __forceinline__ float m_cos(float x) { return cosf(x); }
+
+template <int NC, typename F = double>
+__device__ __forceinline__ void pr_mix(const DevParams& P, const F* Y, PRMix<NC, F>& m)
 {
-    double s = 0.0, cv = 0.0;
+    const PRConstT<F>& K = prk<F>(P);
+    F s = F(0), cv = F(0);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) { s += Y[k] * P.prc.iM[k]; cv += Y[k] * P.prc.cv[k]; }
-    m.M = 1.0 / s;
+    for (int k = 0; k < NC; ++k) { s += Y[k] * K.iM[k]; cv += Y[k] * K.cv[k]; }
+    m.M = F(1) / s;
     m.cvig = cv;
-    m.b = 0.0;
+    m.b = F(0);
 #pragma unroll
-    for (int k = 0; k < NC; ++k) { m.X[k] = Y[k] * P.prc.iM[k] * m.M; m.b += m.X[k] * P.prc.b[k]; }
+    for (int k = 0; k < NC; ++k) { m.X[k] = Y[k] * K.iM[k] * m.M; m.b += m.X[k] * K.b[k]; }
 }
 
 // a(T) = sum_ab X_a X_b A_ab (1 + c_ab (1 - sqrt(T/Tc_ab)))^2 and its first two T derivatives
-template <int NC>
-__device__ __forceinline__ void pr_a(const DevParams& P, const PRMix<NC>& m, double T, double& a, double& da,
-                                     double& d2a)
+template <int NC, typename F = double>
+__device__ __forceinline__ void pr_a(const DevParams& P, const PRMix<NC, F>& m, F T, F& a, F& da, F& d2a)
 {
-    const double sT = sqrt(T), iT = 1.0 / T, isT = 1.0 / sT;
-    a = da = d2a = 0.0;
+    const PRConstT<F>& K = prk<F>(P);
+    const F isT = rsq(T), sT = T * isT, iT = isT * isT;
+    a = da = d2a = F(0);
 #pragma unroll
     for (int i = 0; i < NC; ++i)
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
-            const double xx = m.X[i] * m.X[j], A = P.prc.A[i][j], c = P.prc.cc[i][j], iq = P.prc.isqTc[i][j];
-            const double g = 1.0 + c * (1.0 - sT * iq);
+            const F xx = m.X[i] * m.X[j], A = K.A[i][j], c = K.cc[i][j], iq = K.isqTc[i][j];
+            const F g = F(1) + c * (F(1) - sT * iq);
             a += xx * A * g * g;
             da -= xx * A * c * g * iq * isT;
-            d2a += xx * 0.5 * A * c * iT * iq * (c * iq + g * isT);
+            d2a += xx * F(0.5) * A * c * iT * iq * (c * iq + g * isT);
         }
 }
 
-__device__ __forceinline__ double pr_cubic(double c2, double c1, double c0, double Z) { return ((Z + c2) * Z + c1) * Z + c0; }
+template <typename F> __device__ __forceinline__ F pr_cubic(F c2, F c1, F c0, F Z) { return ((Z + c2) * Z + c1) * Z + c0; }
 
+// log((v + (1 - sqrt2) b) / (v + (1 + sqrt2) b)): as written in FP64; in FP32
+// as log1p(-2 sqrt2 b / (v + (1 + sqrt2) b)), the same value without the
+// cancellation of a ratio near 1 (gas-like states, v >> b)
+__device__ __forceinline__ double pr_logratio(double v, double b)
+{
+    return log((v + (1.0 - SQRT2) * b) / (v + (1.0 + SQRT2) * b));
+}
+__device__ __forceinline__ float pr_logratio(float v, float b)
+{
+    return log1pf(-2.0f * float(SQRT2) * b / (v + (1.0f + float(SQRT2)) * b));
+}
+
+// Gibbs-energy departure of root Z (up to terms common to all roots)
 __device__ __forceinline__ double pr_gdep(double Z, double A, double B)
 {
     return Z - 1.0 - log(Z - B) - A / (2.0 * SQRT2 * B) * log((Z + (1.0 + SQRT2) * B) / (Z + (1.0 - SQRT2) * B));
 }
+__device__ __forceinline__ float pr_gdep(float Z, float A, float B)
+{
+    const float s2 = float(SQRT2);
+    return Z - 1.0f - logf(Z - B) - A / (2.0f * s2 * B) * log1pf(2.0f * s2 * B / (Z + (1.0f - s2) * B));
+}
 
 // TDU with the PR closure: (p, T, Y) -> rho, e, c.  Roots of the cubic in Z
 // in closed form (Cardano / trigonometric), polished by Newton; of several
-// roots above B the one of lowest Gibbs energy is taken.
-template <int NC>
-__device__ __forceinline__ bool pr_tdu(const DevParams& P, double p, double T, const double* Y, double& rho,
-                                       double& e, double& c)
+// roots above B the one of lowest Gibbs energy is taken.  FP64, or FP32 for
+// the mixed form's face states (the App. B Newton inversion stays FP64).
+template <int NC, typename F = double>
+__device__ __forceinline__ bool pr_tdu(const DevParams& P, F p, F T, const F* Y, F& rho, F& e, F& c)
 {
-    if (!(T > 0.0) || !(p > 0.0)) return false;
-    PRMix<NC> m;
-    pr_mix<NC>(P, Y, m);
-    double a, da, d2a;
-    pr_a<NC>(P, m, T, a, da, d2a);
-    const double RT = PR_RU * T;
-    const double A = a * p / (RT * RT), B = m.b * p / RT;
-    const double c2 = -(1.0 - B), c1 = A - 3.0 * B * B - 2.0 * B, c0 = -(A * B - B * B - B * B * B);
-    const double sh = c2 / 3.0;
-    const double pp = c1 - c2 * sh;
-    const double qq = (2.0 / 27.0) * c2 * c2 * c2 - c2 * c1 / 3.0 + c0;
-    const double D = 0.25 * qq * qq + pp * pp * pp / 27.0;
-    double Z[3];
+    if (!(T > F(0)) || !(p > F(0))) return false;
+    PRMix<NC, F> m;
+    pr_mix<NC, F>(P, Y, m);
+    F a, da, d2a;
+    pr_a<NC, F>(P, m, T, a, da, d2a);
+    const F RU = F(PR_RU);
+    const F RT = RU * T;
+    const F A = a * p / (RT * RT), B = m.b * p / RT;
+    const F c2 = -(F(1) - B), c1 = A - F(3) * B * B - F(2) * B, c0 = -(A * B - B * B - B * B * B);
+    const F sh = c2 / F(3);
+    const F pp = c1 - c2 * sh;
+    const F qq = (F(2) / F(27)) * c2 * c2 * c2 - c2 * c1 / F(3) + c0;
+    const F D = F(0.25) * qq * qq + pp * pp * pp / F(27);
+    F Z[3];
     int nr;
-    if (D > 0.0) {
-        const double sD = sqrt(D);
-        Z[0] = cbrt(-0.5 * qq + sD) + cbrt(-0.5 * qq - sD) - sh;
+    if (D > F(0)) {
+        const F sD = sq_rt(D);
+        Z[0] = m_cbrt(F(-0.5) * qq + sD) + m_cbrt(F(-0.5) * qq - sD) - sh;
         nr = 1;
     } else {
-        const double r = sqrt(fmax(-pp / 3.0, 0.0));
-        const double cosphi = (r > 0.0) ? fmin(1.0, fmax(-1.0, -0.5 * qq / (r * r * r))) : 1.0;
-        const double phi = acos(cosphi);
-        Z[0] = 2.0 * r * cos(phi / 3.0) - sh;
-        Z[1] = 2.0 * r * cos((phi - 2.0 * 3.141592653589793) / 3.0) - sh;
-        Z[2] = 2.0 * r * cos((phi + 2.0 * 3.141592653589793) / 3.0) - sh;
+        const F r = sq_rt(fmax(-pp / F(3), F(0)));
+        const F cosphi = (r > F(0)) ? fmin(F(1), fmax(F(-1), F(-0.5) * qq / (r * r * r))) : F(1);
+        const F phi = m_acos(cosphi);
+        const F tpi = F(2) * F(3.141592653589793);
+        Z[0] = F(2) * r * m_cos(phi / F(3)) - sh;
+        Z[1] = F(2) * r * m_cos((phi - tpi) / F(3)) - sh;
+        Z[2] = F(2) * r * m_cos((phi + tpi) / F(3)) - sh;
         nr = 3;
     }
-    double best = -1.0, gbest = 1e300;
+    F best = F(-1), gbest = F(sizeof(F) == 8 ? 1e300 : 1e30);
     for (int i = 0; i < nr; ++i) {
-        double z = Z[i];
+        F z = Z[i];
 #pragma unroll
         for (int it = 0; it < 2; ++it) {
-            const double f = pr_cubic(c2, c1, c0, z), df = (3.0 * z + 2.0 * c2) * z + c1;
-            if (df != 0.0) z -= f / df;
+            const F f = pr_cubic(c2, c1, c0, z), df = (F(3) * z + F(2) * c2) * z + c1;
+            if (df != F(0)) z -= f / df;
         }
         if (!(z > B)) continue;
-        const double g = (nr == 1) ? 0.0 : pr_gdep(z, A, B);
+        const F g = (nr == 1) ? F(0) : pr_gdep(z, A, B);
         if (g < gbest) { gbest = g; best = z; }
     }
     if (!(best > B)) return false;
-    const double v = best * RT / p;
-    const double L = log((v + (1.0 - SQRT2) * m.b) / (v + (1.0 + SQRT2) * m.b));
-    const double k2 = L / (2.0 * SQRT2 * m.b * m.M);
+    const F v = best * RT / p;
+    const F L = pr_logratio(v, m.b);
+    const F k2 = L / (F(2) * F(SQRT2) * m.b * m.M);
     rho = m.M / v;
     e = m.cvig * T + (a - T * da) * k2;
-    const double cv = m.cvig - T * d2a * k2;
-    const double dd = v * v + 2.0 * m.b * v - m.b * m.b;
-    const double dpdT = PR_RU / (v - m.b) - da / dd;
-    const double dpdv = -RT / ((v - m.b) * (v - m.b)) + a * (2.0 * v + 2.0 * m.b) / (dd * dd);
-    const double c2s = -(v * v / m.M) * dpdv + T * dpdT * dpdT / (rho * rho * cv);
-    c = sqrt(c2s);
-    return c2s > 0.0 && cv > 0.0;
+    const F cv = m.cvig - T * d2a * k2;
+    const F dd = v * v + F(2) * m.b * v - m.b * m.b;
+    const F dpdT = RU / (v - m.b) - da / dd;
+    const F dpdv = -RT / ((v - m.b) * (v - m.b)) + a * (F(2) * v + F(2) * m.b) / (dd * dd);
+    const F c2s = -(v * v / m.M) * dpdv + T * dpdT * dpdT / (rho * rho * cv);
+    c = sq_rt(c2s);
+    return c2s > F(0) && cv > F(0);
 }
 
 // Primitive recovery with the PR closure (App. B): Newton on T for
 // e(T, v) = e at fixed molar volume v = M/rho, started from the previous T
 // (T0; an ideal-gas estimate when T0 is not usable), steps limited to a
-// factor 5, at most 50 iterations; then p explicit from Eq. A.2.1.
+// factor 5, at most 50 iterations; then p explicit from Eq. A.2.1.  Newton
+// converges quadratically, so once a step is below 3e-7 T the next one would
+// be below ~1e-13 T: the iteration stops there, and a(T) at the new T is the
+// first-order Taylor value a + a' dT (second-order term ~(dT/T)^2 ~ 1e-13).
 template <int NC>
 __device__ __forceinline__ int pr_invert(const DevParams& P, double rho, double e, const double* Y, double T0,
                                          double& p, double& T)
@@ -300,11 +342,16 @@ __device__ __forceinline__ int pr_invert(const DevParams& P, double rho, double 
         double tn = t - f / df;
         tn = fmin(fmax(tn, 0.2 * t), 5.0 * t);
         const double dt = tn - t;
+        if (fabs(dt) <= 3e-7 * t) {
+            a += da * dt;
+            t = tn;
+            conv = true;
+            break;
+        }
         t = tn;
-        if (fabs(dt) <= 1e-13 * t) { conv = true; break; }
     }
     T = t;
-    pr_a<NC>(P, m, t, a, da, d2a);
+    if (!conv) pr_a<NC>(P, m, t, a, da, d2a);
     p = PR_RU * t / (v - m.b) - a / (v * v + 2.0 * m.b * v - m.b * m.b);
     if (!conv) return ERR_NONCONV;
     return isfinite(p) ? 0 : ERR_NONPHYS;
@@ -329,14 +376,8 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
     Y[NC - 1] = clip01(R(1) - s);
     const ConstT<R>& Kc = K<R>(P);
     if constexpr (PRC) {
-        double Yd[NC], rd, ed, cd;
-#pragma unroll
-        for (int k = 0; k < NC; ++k) Yd[k] = double(Y[k]);
-        const bool ok = pr_tdu<NC>(P, P.p_ref + double(pp), double(T), Yd, rd, ed, cd);
-        rho = R(rd);
-        e = R(ed);
-        c = R(cd);
-        return ok;
+        // the face state's PR closure in the working precision
+        return pr_tdu<NC, R>(P, Kc.p_ref + pp, T, Y, rho, e, c);
     }
     R Pk[NC], iP[NC];
     bool ok = T > R(0);
