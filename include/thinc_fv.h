@@ -138,9 +138,12 @@ fv_status fv_set_stream(fv_ctx* ctx, void* stream);
 
 /* Copy a case's state from/to host memory (kind FV_CONSERVED or
  * FV_PRIMITIVE; nv * n[0]*n[1]*n[2] doubles).  Primitive input is turned
- * into conserved variables by the closure on the device.  Synchronous:
- * returns once the copy is complete.  get_state also reports a pending
- * device error word as FV_ERR_NONPHYSICAL / FV_ERR_EOS_NONCONV. */
+ * into conserved variables by the closure on the device.  Page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister) is read or written by the
+ * device's conversion kernel directly over the host link; other host memory
+ * is staged through a device buffer.  Synchronous: returns once the copy is
+ * complete.  get_state also reports a pending device error word as
+ * FV_ERR_NONPHYSICAL / FV_ERR_EOS_NONCONV. */
 fv_status fv_set_state(fv_ctx* ctx, int icase, int kind, const double* host);
 fv_status fv_get_state(fv_ctx* ctx, int icase, int kind, double* host);
 /* Same with device pointers; asynchronous on the context's stream. */

@@ -754,6 +754,22 @@ static fv_status read_err(fv_ctx* x)
     return FV_OK;
 }
 
+// Device-accessible address of caller memory: the pointer itself for device
+// memory, the mapped alias of page-locked host memory (the conversion kernels
+// then read or write it over the host link, with no staging copy), or null
+// for other host memory (staged through the context's I/O buffer).
+static const void* device_alias(const void* p, cudaMemcpyKind mk)
+{
+    if (mk == cudaMemcpyDeviceToDevice) return p;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
+}
+
 static fv_status set_state_impl(fv_ctx* x, int c, int kind, const double* src, cudaMemcpyKind mk, bool sync)
 {
     fv_status s = case_ok(x, c);
@@ -761,21 +777,22 @@ static fv_status set_state_impl(fv_ctx* x, int c, int kind, const double* src, c
     if (!src) return fail(x, FV_ERR_ARG, "null state pointer%s");
     const long long n = case_cells(x, c);
     const CaseDesc& C = x->cases[c];
+    const double* in = static_cast<const double*>(device_alias(src, mk));
+    if (!in) {
+        CK(x, cudaMemcpyAsync(x->io, src, sizeof(double) * x->nv * n, mk, x->stream));
+        in = x->io;
+    }
     if (kind == FV_CONSERVED && !x->ff) {
-        CK(x, cudaMemcpy2DAsync(x->Q0 + C.qoff, sizeof(double) * x->L.ntot_q, src, sizeof(double) * n,
-                                sizeof(double) * n, x->nv, mk, x->stream));
+        CK(x, launch_copy_fields(x->nv, in, n, x->Q0 + C.qoff, x->L.ntot_q, n, x->stream));
     } else if (kind == FV_CONSERVED) {
-        CK(x, cudaMemcpyAsync(x->io, src, sizeof(double) * x->nv * n, mk, x->stream));
-        CK(x, launch_split(x->nv, x->io, n, x->Q0, x->L.ntot_q, C.qoff, x->stream));
-        x->launches++;
+        CK(x, launch_split(x->nv, in, n, x->Q0, x->L.ntot_q, C.qoff, x->stream));
     } else if (kind == FV_PRIMITIVE) {
-        CK(x, cudaMemcpyAsync(x->io, src, sizeof(double) * x->nv * n, mk, x->stream));
-        IoArgs A{x->P, x->d_cases, c, n, x->io, x->Q0, x->err};
+        IoArgs A{x->P, x->d_cases, c, n, in, x->Q0, x->err};
         CK(x, launch_prim_to_cons(x->nd, x->nc, A, x->stream, x->ff));
-        x->launches++;
     } else {
         return fail(x, FV_ERR_ARG, "bad state kind%s");
     }
+    x->launches++;
     CK(x, cudaMemsetAsync(x->t + c, 0, sizeof(double), x->stream));
     if (sync) {
         CK(x, cudaStreamSynchronize(x->stream));
@@ -791,21 +808,20 @@ static fv_status get_state_impl(fv_ctx* x, int c, int kind, double* dst, cudaMem
     if (!dst) return fail(x, FV_ERR_ARG, "null state pointer%s");
     const long long n = case_cells(x, c);
     const CaseDesc& C = x->cases[c];
+    double* const direct = static_cast<double*>(const_cast<void*>(device_alias(dst, mk)));
+    double* out = direct ? direct : x->io;
     if (kind == FV_CONSERVED && !x->ff) {
-        CK(x, cudaMemcpy2DAsync(dst, sizeof(double) * n, x->Q0 + C.qoff, sizeof(double) * x->L.ntot_q,
-                                sizeof(double) * n, x->nv, mk, x->stream));
+        CK(x, launch_copy_fields(x->nv, x->Q0 + C.qoff, x->L.ntot_q, out, n, n, x->stream));
     } else if (kind == FV_CONSERVED) {
-        CK(x, launch_join(x->nv, x->Q0, x->L.ntot_q, C.qoff, n, x->io, x->stream));
-        x->launches++;
-        CK(x, cudaMemcpyAsync(dst, x->io, sizeof(double) * x->nv * n, mk, x->stream));
+        CK(x, launch_join(x->nv, x->Q0, x->L.ntot_q, C.qoff, n, out, x->stream));
     } else if (kind == FV_PRIMITIVE) {
-        IoArgs A{x->P, x->d_cases, c, n, x->Q0, x->io, x->err};
+        IoArgs A{x->P, x->d_cases, c, n, x->Q0, out, x->err};
         CK(x, launch_cons_to_prim(x->nd, x->nc, A, x->stream, x->ff));
-        x->launches++;
-        CK(x, cudaMemcpyAsync(dst, x->io, sizeof(double) * x->nv * n, mk, x->stream));
     } else {
         return fail(x, FV_ERR_ARG, "bad state kind%s");
     }
+    x->launches++;
+    if (!direct) CK(x, cudaMemcpyAsync(dst, x->io, sizeof(double) * x->nv * n, mk, x->stream));
     if (sync) {
         CK(x, cudaStreamSynchronize(x->stream));
         return read_err(x);

@@ -40,11 +40,15 @@ struct IoArgs {
 };
 cudaError_t launch_prim_to_cons(int nd, int nc, const IoArgs& A, cudaStream_t s, int ff);
 cudaError_t launch_cons_to_prim(int nd, int nc, const IoArgs& A, cudaStream_t s, int ff);
-// case-local conserved doubles <-> float-float registers
+// case-local conserved doubles <-> float-float registers; in / out may be
+// device memory or mapped page-locked host memory
 cudaError_t launch_split(int nv, const double* in, long long ncell, void* reg, long long ntot_q, long long off,
                          cudaStream_t s);
 cudaError_t launch_join(int nv, const void* reg, long long ntot_q, long long off, long long ncell, double* out,
                         cudaStream_t s);
+// nv fields of ncell doubles between two field strides (FP64 registers)
+cudaError_t launch_copy_fields(int nv, const double* in, long long in_stride, double* out, long long out_stride,
+                               long long ncell, cudaStream_t s);
 // per-block Kahan partial sums of each field of one case: partial[nv][nblk]
 cudaError_t launch_totals(int nv, const void* q, long long ntot_q, long long off, long long ncell,
                           double* partial, int nblk, cudaStream_t s, int ff);

@@ -141,35 +141,61 @@ __global__ void cons_to_prim_kernel(IoArgs A)
 }
 
 // conserved case-local doubles <-> float-float registers
-__global__ void split_kernel(int nv, const double* in, long long ncell, float2* reg, long long ntot_q, long long off)
+// Case-local conserved doubles [nv][ncell] <-> the registers (field stride
+// ntot_q, case offset off).  One grid row (blockIdx.y) per field.  `in` /
+// `out` may be device memory or page-locked host memory mapped into the
+// device's address space (read and written over the host link directly).
+__global__ void split_kernel(const double* in, long long ncell, float2* reg, long long ntot_q, long long off)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell * nv;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long v = i / ncell, c = i - v * ncell;
-        reg[v * ntot_q + off + c] = ff_from_double(in[i]);
-    }
+    const int v = blockIdx.y;
+    const double* src = in + v * ncell;
+    float2* dst = reg + v * ntot_q + off;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+        dst[c] = ff_from_double(src[c]);
 }
-__global__ void join_kernel(int nv, const float2* reg, long long ntot_q, long long off, long long ncell, double* out)
+__global__ void join_kernel(const float2* reg, long long ntot_q, long long off, long long ncell, double* out)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell * nv;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long v = i / ncell, c = i - v * ncell;
-        out[i] = qv_d(reg[v * ntot_q + off + c]);
-    }
+    const int v = blockIdx.y;
+    const float2* src = reg + v * ntot_q + off;
+    double* dst = out + v * ncell;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+        dst[c] = qv_d(src[c]);
+}
+// FP64 registers: plain field copies in (to_reg = 1) or out
+__global__ void copy_fields_kernel(const double* in, long long in_stride, double* out, long long out_stride,
+                                   long long ncell)
+{
+    const int v = blockIdx.y;
+    const double* src = in + v * in_stride;
+    double* dst = out + v * out_stride;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
+        dst[c] = src[c];
 }
 
 static int io_grid(long long n) { long long g = (n + 255) / 256; return (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g)); }
+static dim3 field_grid(long long ncell, int nv)
+{
+    long long g = (ncell + 255) / 256;
+    g = g > 2048 ? 2048 : (g < 1 ? 1 : g);
+    return dim3((unsigned)g, (unsigned)nv);
+}
 
 cudaError_t launch_split(int nv, const double* in, long long ncell, void* reg, long long ntot_q, long long off,
                          cudaStream_t s)
 {
-    split_kernel<<<io_grid(ncell * nv), 256, 0, s>>>(nv, in, ncell, static_cast<float2*>(reg), ntot_q, off);
+    split_kernel<<<field_grid(ncell, nv), 256, 0, s>>>(in, ncell, static_cast<float2*>(reg), ntot_q, off);
     return cudaGetLastError();
 }
 cudaError_t launch_join(int nv, const void* reg, long long ntot_q, long long off, long long ncell, double* out,
                         cudaStream_t s)
 {
-    join_kernel<<<io_grid(ncell * nv), 256, 0, s>>>(nv, static_cast<const float2*>(reg), ntot_q, off, ncell, out);
+    join_kernel<<<field_grid(ncell, nv), 256, 0, s>>>(static_cast<const float2*>(reg), ntot_q, off, ncell, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_copy_fields(int nv, const double* in, long long in_stride, double* out, long long out_stride,
+                               long long ncell, cudaStream_t s)
+{
+    copy_fields_kernel<<<field_grid(ncell, nv), 256, 0, s>>>(in, in_stride, out, out_stride, ncell);
     return cudaGetLastError();
 }
 
