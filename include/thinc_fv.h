@@ -67,7 +67,8 @@ enum { FV_DIAG_TOTALS = 0,   /* double[nv]: compensated sums of q over the case 
                                 timed), [8] 1 if the fused kernel was chosen, [9] its
                                 best tuned milliseconds, [10] the primitive pass's,
                                 [11] the fused kernel variant (-1: tiled) */
-enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2 };
+enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2,
+       FV_ERRBIT_TIMEOUT = 4 };   /* a bounded wait in a kernel gave up (reported as FV_ERR_CUDA) */
 
 /* Grid of one case.  lo/hi are the box corners (m); bc[d][0] is the low
  * side of dimension d.  FV_BC_INFLOW is accepted on the x-low side only:

@@ -1,5 +1,6 @@
 // fv_api.cu -- the C ABI (include/thinc_fv.h): context set-up, device memory
 // layout, work lists, the stage sequence and its CUDA-graph replay.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,7 +29,8 @@ const double LSRK_A[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t cases, items_stage, items_prim, items_march, q0, qa, qb, prim, io, smax, dt, t, err, in_u, partial, total;
+    size_t cases, items_stage, items_prim, items_march, q0, qa, qb, prim, io, smax, dt, t, err, in_u, partial, tmaps,
+        total;
     int n_items_stage, n_items_prim, n_items_march;
     long long ntot_q, ntot_p, max_cells, n_in_u;
 };
@@ -82,6 +84,9 @@ struct fv_ctx {
     bool fused = false;                     // the fused kernel is in use
     int mvar = 0, chunk = 0, march_grid = 0, n_items_march = 0;
     int4* d_items_march = nullptr;
+    // TMA halo-tile loads of the tiled kernel: one descriptor per case for the current tile
+    unsigned char* d_tmaps = nullptr;
+    bool tma = false;
     float march_ms = 0.f, prim_ms = 0.f;
     size_t smem_max = 0;                    // opt-in shared memory per block of the device
     bool tuned = false;
@@ -335,6 +340,7 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
             C.bc[d][0] = d < nd ? g[c].bc[d][0] : 0;
             C.bc[d][1] = d < nd ? g[c].bc[d][1] : 0;
         }
+        C.gp = (C.g[0] + 3) & ~3;
         C.qoff = qoff;
         C.poff = poff;
         C.inflow = g[c].bc[0][0] == FV_BC_INFLOW;
@@ -351,7 +357,7 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
         }
         const long long ncell = (long long)C.n[0] * C.n[1] * C.n[2];
         qoff += ncell;
-        poff += (long long)C.g[0] * C.g[1] * C.g[2];
+        poff += (long long)C.gp * C.g[1] * C.g[2];
         L.max_cells = std::max(L.max_cells, ncell);
         if (cases) cases->push_back(C);
         long long nst = 0, npr = ntiles(gx, nd);
@@ -394,6 +400,7 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
     L.err = take(sizeof(int));
     L.in_u = take(sizeof(double) * std::max(1LL, nin));
     L.partial = take(sizeof(double) * nv * 1024);
+    L.tmaps = take(TMAP_BYTES * (size_t)ncases);
     L.total = o;
 }
 
@@ -418,6 +425,69 @@ extern "C" fv_status fv_workspace_size(int ncases, const fv_grid* grids, const f
     return FV_OK;
 }
 
+
+// ------------------------------------------------------------------ TMA
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+static const void* stage_tmaps(const fv_ctx* x) { return x->tma ? x->d_tmaps : nullptr; }
+
+// One 4D descriptor [x, y, z, field] of each case's primitive arrays with the
+// halo box of `variant`'s tile; zero fill outside the ghosted box.  Every TMA
+// alignment rule is checked here; if one fails (or FV_TMA=0 in the
+// environment, or no encoder) the tiled kernel keeps its cp.async loads.
+static fv_status encode_tmaps(fv_ctx* x, int variant)
+{
+    x->tma = false;
+    if (const char* f = getenv("FV_TMA"))
+        if (atoi(f) == 0) return FV_OK;
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return FV_OK;
+    const TileDef td = tile_def(x->nd, variant_tile(variant));
+    const cuuint64_t es = x->mixed ? sizeof(float) : sizeof(double);
+    const cuuint32_t box[4] = {cuuint32_t(td.x + 4), cuuint32_t(td.y + 4), cuuint32_t(x->nd == 3 ? td.z + 4 : 1),
+                               cuuint32_t(x->nprim)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    // tile origins are multiples of td.x cells: x * element size on 16 bytes
+    if ((td.x * es) % 16 || (box[0] * es) % 16 || box[0] > 256 || box[1] > 256 || box[2] > 256 || box[3] > 256)
+        return FV_OK;
+    std::vector<CUtensorMap> maps(x->ncases);
+    for (int c = 0; c < x->ncases; ++c) {
+        const CaseDesc& C = x->cases[c];
+        unsigned char* base = static_cast<unsigned char*>(x->prim) + C.poff * es;
+        const cuuint64_t dims[4] = {cuuint64_t(C.g[0]), cuuint64_t(C.g[1]), cuuint64_t(C.g[2]), cuuint64_t(x->nprim)};
+        const cuuint64_t strides[3] = {C.gp * es, C.gp * es * C.g[1], cuuint64_t(x->L.ntot_p) * es};
+        if (reinterpret_cast<uintptr_t>(base) % 16 || strides[0] % 16 || strides[1] % 16 || strides[2] % 16)
+            return FV_OK;
+        if (fn(&maps[c], es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return FV_OK;
+    }
+    static_assert(sizeof(CUtensorMap) == TMAP_BYTES, "descriptor size");
+    CK(x, cudaMemcpy(x->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
+    x->tma = true;
+    return FV_OK;
+}
 
 // work list of the stage kernel for one candidate tile
 static void stage_items(const std::vector<CaseDesc>& cases, int nd, int tile, std::vector<int4>& out)
@@ -460,6 +530,10 @@ static fv_status apply_tile(fv_ctx* x, int tile)
     x->tile = tile;
     x->fused = false;
     x->smem = smem;
+    {
+        const fv_status st = encode_tmaps(x, tile);
+        if (st) return st;
+    }
     x->n_items_cur = (int)it.size();
     x->stage_grid = (int)std::min<long long>((long long)it.size(), (long long)x->nsm * occ);
     return FV_OK;
@@ -569,7 +643,8 @@ static fv_status tune(fv_ctx* x)
     if (want_fused != 1) {
         for (int t = 0; t < (tiles ? NTILES : 1); ++t) {
             if (apply_tile(x, t)) { x->msg.clear(); continue; }
-            StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, x->Q0, x->QB, x->dt, 0.0,
+            StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, stage_tmaps(x), x->Q0, x->QB,
+                         x->dt, 0.0,
                          x->err};
             float ms = 0.f;
             st = timed([&] { return launch_stage(x->nd, x->nc, x->mixed, x->tile, sa, x->stage_grid, x->smem,
@@ -666,6 +741,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     x->err = reinterpret_cast<int*>(b + L.err);
     x->in_u = reinterpret_cast<double*>(b + L.in_u);
     x->partial = reinterpret_cast<double*>(b + L.partial);
+    x->d_tmaps = b + L.tmaps;
     CK(x, cudaStreamCreateWithFlags(&x->cap, cudaStreamNonBlocking));
     CK(x, cudaMemcpy(x->d_cases, x->cases.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice));
     CK(x, cudaMemcpy(x->d_items_prim, ipr.data(), sizeof(int4) * ipr.size(), cudaMemcpyHostToDevice));
@@ -749,6 +825,7 @@ static fv_status read_err(fv_ctx* x)
 {
     int e = 0;
     CK(x, cudaMemcpy(&e, x->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e & ERR_TIMEOUT) return fail(x, FV_ERR_CUDA, "a bounded wait in a kernel gave up%s");
     if (e & ERR_NONCONV) return fail(x, FV_ERR_EOS_NONCONV, "closure iteration did not converge%s");
     if (e & ERR_NONPHYS) return fail(x, FV_ERR_NONPHYSICAL, "non-physical state met in a kernel%s");
     return FV_OK;
@@ -910,7 +987,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
         PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
         x->launches++;
     }
-    StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, x->Q0, out, x->dt,
+    StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, stage_tmaps(x), x->Q0, out, x->dt,
                  LSRK_A[k - 1], x->err};
     PROF(FV_KERNEL_STAGE, launch_stage(x->nd, x->nc, x->mixed, x->tile, sa, x->stage_grid, x->smem, s, x->ff));
     x->launches++;
@@ -1221,7 +1298,8 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
     for (int c = 0; c < FV_MAX_COMP && c < MAXC; ++c) C.in_Y[c] = grid->in_Y[c];
     C.in_uoff = -1;
     const long long ncell = (long long)C.n[0] * C.n[1] * C.n[2];
-    const long long nghost = (long long)C.g[0] * C.g[1] * C.g[2];
+    C.gp = (C.g[0] + 3) & ~3;
+    const long long nghost = (long long)C.gp * C.g[1] * C.g[2];
     x.P.ntot_q = ncell;
     x.P.ntot_p = nghost;
     const int tx = tile_x(x.nd), ty = tile_y(x.nd), tz = tile_z(x.nd);
@@ -1255,7 +1333,7 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
     if (cudaGetLastError() != cudaSuccess) return FV_ERR_CUDA;
     PrimArgs pa{x.P, dcase, ipr, (int)n_pr, qprev, prim, nullptr, nullptr, derr};
     if (launch_prim(x.nd, x.nc, x.mixed, pa, gp, s) != cudaSuccess) return FV_ERR_CUDA;
-    StageArgs sa{x.P, dcase, ist, (int)n_st, prim, q0, qout, ddt, LSRK_A[k - 1], derr};
+    StageArgs sa{x.P, dcase, ist, (int)n_st, prim, nullptr, q0, qout, ddt, LSRK_A[k - 1], derr};
     if (launch_stage(x.nd, x.nc, x.mixed, var, sa, gs, smem, s) != cudaSuccess) return FV_ERR_CUDA;
     int e = 0;
     if (cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FV_ERR_CUDA;

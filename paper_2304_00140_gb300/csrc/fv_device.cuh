@@ -14,11 +14,13 @@ namespace tfv {
 constexpr int MAXC = 4;
 constexpr int ERR_NONPHYS = 1;
 constexpr int ERR_NONCONV = 2;
+constexpr int ERR_TIMEOUT = 4;   // a bounded wait in a kernel gave up
 
 // Per-case geometry, copied to the device once at init.
 struct CaseDesc {
     int n[3];            // interior cells (1 in unused dims)
     int g[3];            // ghosted extents: n + 4 in active dims, 1 otherwise
+    int gp;              // row pitch of the primitive arrays: g[0] rounded up to 4 (16-byte rows for TMA)
     long long qoff;      // first cell of this case in the conserved arrays
     long long poff;      // first cell of this case in the primitive arrays
     double dx[3], idx[3];

@@ -34,6 +34,7 @@ struct StageArgs {
     const int4* items;
     int nitems;
     const void* prim;
+    const void* tmaps;        // per-case TMA descriptors of the primitive arrays for this tile, or null (cp.async)
     const void* q0;           // registers: double (FP64 form) or float2 (float-float, mixed form)
     void* qout;
     const double* dt;         // per-case dt
@@ -104,9 +105,63 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
+// Tensor memory access (TMA): one bulk tensor copy brings a whole halo tile
+// (all primitive fields) into shared memory and signals an mbarrier with the
+// byte count.  Waits are bounded (see tma_wait).
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned a, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned a, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned a, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// the descriptor (global memory, written by the host) as seen by the tensormap proxy
+__device__ __forceinline__ void tmap_acquire(const void* tmap)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(tmap) : "memory");
+}
+// generic-proxy accesses of shared memory before async-proxy (TMA) writes
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// 4D tile load [x, y, z, field] at the given coordinates; x * element size is
+// a multiple of 16 bytes (tile origins are multiples of 16 cells)
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const void* tmap, int x, int y, int z, int f, unsigned mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(f), "r"(mbar)
+        : "memory");
+}
+// bounded wait for phase `parity` of an mbarrier: false after ~2^22 polls
+// (each poll may suspend the thread for a while), far beyond any copy time
+__device__ __forceinline__ bool tma_wait(unsigned a, unsigned parity)
+{
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(a, parity)) return true;
+    return false;
+}
+constexpr int TMAP_BYTES = 128;   // one CUtensorMap
+
 // halo-tile buffers of the stage kernel: two (prefetch the next item) in the
 // FP32 form, one in the FP64 form (FP64-pipe bound; keeps 3D tiles in shared memory)
 template <typename R, int NB> constexpr int tile_buffers() { return sizeof(R) == 4 ? NB : 1; }
+// elements between two halo-tile buffers: nprim x HC rounded up to 128 bytes
+template <typename R, int HC> __host__ __device__ inline int tile_buffer_stride(int nprim)
+{
+    const int bytes = (nprim * HC * int(sizeof(R)) + 127) & ~127;
+    return bytes / int(sizeof(R));
+}
 
 // Encoded liquid volume fraction (see the prim kernel): 1 when e is the
 // negated gas fraction (sign bit set, including -0 for pure liquid), else 0.
@@ -167,7 +222,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             for (int v = 0; v < NV; ++v) { qc[v] = *qp; qp += P.ntot_q; }
             R w[NV], T, pabs, rho;
             // prim == null: CFL pass only (the fused stage kernel recovers its own primitives)
-            R* const pp0 = prim ? prim + C.poff + ((gc[2] * C.g[1] + gc[1]) * C.g[0] + gc[0]) : nullptr;
+            R* const pp0 = prim ? prim + C.poff + ((gc[2] * C.g[1] + gc[1]) * C.gp + gc[0]) : nullptr;
             // Peng-Robinson Newton starts from this cell's previous temperature
             const double T0 = (PRC && pp0) ? double(pp0[(ND + 1) * P.ntot_p]) : 0.0;
             const int rst = prim_recover<ND, NC, R, PRC, Q>(P, qc, w, rho, T, pabs, T0);
@@ -256,10 +311,12 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
     const DevParams& P = A.P;
     const R* prim = static_cast<const R*>(A.prim);
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* const spbuf = reinterpret_cast<R*>(smem_raw);        // two halo tiles [2][nprim][HC]
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // halo tiles [NBUF][nprim][HC], each buffer on a 128-byte boundary (TMA destination)
+    R* const spbuf = reinterpret_cast<R*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int bstride = tile_buffer_stride<R, HC>(P.nprim);
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
-    R* const sfx = spbuf + tile_buffers<R, NB>() * P.nprim * HC; // fluxes per direction [NV][faces]
+    R* const sfx = spbuf + tile_buffers<R, NB>() * bstride;   // fluxes per direction [NV][faces]
     R* const sfy = sfx + NV * NFX;
     R* const sfz = sfy + NV * NFY;
     R* extra = (ND == 2) ? sfz : sfz + NV * NFZ;
@@ -272,18 +329,44 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 
     const ConstT<R>& Kc = K<R>(P);
     const int tid = threadIdx.x;
+    // TMA mode: one bulk tensor copy per tile, completion on an mbarrier per buffer
+    const bool tma = A.tmaps != nullptr;
+    __shared__ __align__(8) unsigned long long mbar[2];
+    const unsigned mb[2] = {smem_addr(&mbar[0]), smem_addr(&mbar[1])};
+    const unsigned tile_bytes = unsigned(HC * P.nprim * sizeof(R));
+    unsigned phase = 0;   // bit b: parity of buffer b's next completion
+    if (tma) {
+        if (tid == 0) {
+            mbar_init(mb[0], 1);
+            mbar_init(mb[1], 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
     // halo tile of primitives of item `item` (ghosted coordinates x0 .. x0+HX-1)
-    auto issue_tile = [&](int item, R* buf) {
+    auto issue_tile = [&](int item, int b) {
+        R* const buf = spbuf + b * bstride;
+        if (tma) {
+            if (tid == 0 && item < A.nitems) {
+                const int4 wn = A.items[item];
+                const void* tm = static_cast<const unsigned char*>(A.tmaps) + size_t(wn.x) * TMAP_BYTES;
+                tmap_acquire(tm);
+                fence_async_smem();
+                mbar_expect_tx(mb[b], tile_bytes);
+                tma_load_4d(smem_addr(buf), tm, wn.y, wn.z, wn.w, 0, mb[b]);
+            }
+            return;
+        }
         if (item < A.nitems) {
             const int4 wn = A.items[item];
             const CaseDesc& Cn = A.cases[wn.x];
-            const int g0 = Cn.g[0], g1 = Cn.g[1], g2 = Cn.g[2];
+            const int g0 = Cn.g[0], g1 = Cn.g[1], g2 = Cn.g[2], gp = Cn.gp;
             const R* const base = prim + Cn.poff;
             for (int h = tid; h < HC; h += NT) {
                 const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
                 const int gx = wn.y + hx, gy = wn.z + hy, gz = wn.w + hz;
                 const bool ok = gx < g0 && gy < g1 && gz < g2;
-                const R* src = ok ? base + ((gz * g1 + gy) * g0 + gx) : prim;
+                const R* src = ok ? base + ((gz * g1 + gy) * gp + gx) : prim;
                 R* dst = buf + h;
                 for (int v = 0; v < P.nprim; ++v) {
                     cp_async_elem(dst, src, ok);
@@ -296,17 +379,17 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
     };
     constexpr int NBUF = tile_buffers<R, NB>();
     int cur = 0;
-    if (NBUF == 2) issue_tile(blockIdx.x, spbuf);
+    if (NBUF == 2) issue_tile(blockIdx.x, 0);
     for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
         const int4 wi = A.items[it];
         const CaseDesc& C = A.cases[wi.x];
         const int x0 = wi.y, y0 = wi.z, z0 = wi.w;
-        R* const sp = spbuf + cur * P.nprim * HC;
+        R* const sp = spbuf + cur * bstride;
         if (NBUF == 2) {
             // the next item's tile goes to the other buffer while this one computes
-            issue_tile(it + gridDim.x, spbuf + (cur ^ 1) * P.nprim * HC);
+            issue_tile(it + gridDim.x, cur ^ 1);
         } else {
-            issue_tile(it, sp);
+            issue_tile(it, 0);
         }
         const int vx = min(TX, C.n[0] - x0), vy = min(TY, C.n[1] - y0), vz = (ND == 3) ? min(TZ, C.n[2] - z0) : 1;
         R ci[3], cdx[3];
@@ -322,8 +405,22 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 #pragma unroll
             for (int v = 0; v < NV; ++v) { q0r[v] = own ? *qp : Q{}; qp += P.ntot_q; }
         }
-        if (NBUF == 2) cp_async_wait_prev(); else cp_async_wait_all();
-        __syncthreads();
+        if (tma) {
+            const bool ok = tma_wait(mb[cur], (phase >> cur) & 1u);
+            phase ^= 1u << cur;
+            if (__syncthreads_or(!ok)) {
+                // a copy did not complete: report, let the other buffer's copy
+                // (if one was issued) finish within the same bound, and stop
+                if (tid == 0) {
+                    set_err(A.err, ERR_TIMEOUT);
+                    if (NBUF == 2 && it + gridDim.x < A.nitems) tma_wait(mb[cur ^ 1], (phase >> (cur ^ 1)) & 1u);
+                }
+                return;
+            }
+        } else {
+            if (NBUF == 2) cp_async_wait_prev(); else cp_async_wait_all();
+            __syncthreads();
+        }
         // ---- App. D cell sensor on the tile + 1 halo
         if (P.iles) {
             for (int h = tid; h < HC; h += NT) {
@@ -564,9 +661,9 @@ inline size_t stage_smem_bytes(int nprim)
     constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
     constexpr int AC = (TX + 2) * (TY + 2) * ((ND == 3) ? TZ + 2 : 1);
     constexpr int VC = (TX + 1) * (TY + 1) * ((ND == 3) ? TZ + 1 : 1);
-    size_t n = tile_buffers<R, NB>() * (size_t)nprim * HC + (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC +
-               ND * VC;
-    return n * sizeof(R) + HC + 16;
+    size_t n = tile_buffers<R, NB>() * (size_t)tile_buffer_stride<R, HC>(nprim) +
+               (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC + ND * VC;
+    return n * sizeof(R) + HC + 16 + 128;   // + alignment of the buffers to 128 bytes
 }
 
 }  // namespace tfv
