@@ -74,15 +74,24 @@ def test_iles_csf_2d_parity(ncomp, fused, monkeypatch):
     assert np.all(d < 1e-11), d
 
 
+# the tiled kernel's halo tiles: TMA bulk tensor copies (FV_TMA=1) or
+# per-element cp.async (FV_TMA=0)
+TMA = pytest.mark.parametrize("tma", ["1", "0"])
+
+
+@TMA
 @pytest.mark.parametrize("ncomp", [2, 3])
-def test_plain_3d_parity(ncomp):
+def test_plain_3d_parity(ncomp, tma, monkeypatch):
+    monkeypatch.setenv("FV_TMA", tma)
     w = wl.random_state(n=(20, 14, 11), ndim=3, ncomp=ncomp)
     o, q, got, ref = _run_pair(w)
     d = rel_field_diff(got, ref)
     assert np.all(d < 1e-12), d
 
 
-def test_iles_csf_3d_three_components_parity():
+@TMA
+def test_iles_csf_3d_three_components_parity(tma, monkeypatch):
+    monkeypatch.setenv("FV_TMA", tma)
     w = wl.random_state(n=(18, 12, 10), ndim=3, ncomp=3, iles=1, sigma=5.0,
                         bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_PERIODIC] * 2, [wl.BC_REFLECT, wl.BC_OUTFLOW]])
     o, q, got, ref = _run_pair(w, steps_dt=2)
