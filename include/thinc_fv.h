@@ -147,6 +147,14 @@ fv_status fv_set_stream(fv_ctx* ctx, void* stream);
  * FV_ERR_NONPHYSICAL / FV_ERR_EOS_NONCONV. */
 fv_status fv_set_state(fv_ctx* ctx, int icase, int kind, const double* host);
 fv_status fv_get_state(fv_ctx* ctx, int icase, int kind, double* host);
+/* Every case in one call, for batches of many small cases: `host` holds
+ * each case's block of the layout above (nv * cells doubles) concatenated in
+ * case order.  Conserved state in page-locked host memory is moved by one
+ * kernel over all cases; other memory, and primitive input, goes case by
+ * case.  One synchronisation per call; errors as for fv_set_state /
+ * fv_get_state. */
+fv_status fv_set_state_all(fv_ctx* ctx, int kind, const double* host);
+fv_status fv_get_state_all(fv_ctx* ctx, int kind, double* host);
 /* Same with device pointers; asynchronous on the context's stream. */
 fv_status fv_set_state_device(fv_ctx* ctx, int icase, int kind, const double* dev);
 fv_status fv_get_state_device(fv_ctx* ctx, int icase, int kind, double* dev);

@@ -917,6 +917,44 @@ extern "C" fv_status fv_get_state(fv_ctx* x, int icase, int kind, double* host)
     return get_state_impl(x, icase, kind, host, cudaMemcpyDeviceToHost, true);
 }
 
+// All cases in one call (concatenated per-case blocks): conserved state in
+// device or page-locked host memory takes one kernel over every case; any
+// other case goes case by case, with one synchronisation at the end.
+static fv_status state_all(fv_ctx* x, int kind, double* buf, bool set)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (!buf) return fail(x, FV_ERR_ARG, "null state pointer%s");
+    const cudaMemcpyKind mk = set ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    if (set) CK(x, cudaMemsetAsync(x->err, 0, sizeof(int), x->stream));
+    const double* direct = static_cast<const double*>(device_alias(buf, mk));
+    if (direct && kind == FV_CONSERVED) {
+        CK(x, launch_all_cases(x->nv, x->ncases, x->d_cases, x->L.max_cells, direct, x->Q0, x->L.ntot_q, x->ff,
+                               set ? 1 : 0, x->stream));
+        x->launches++;
+        if (set) CK(x, cudaMemsetAsync(x->t, 0, sizeof(double) * x->ncases, x->stream));
+    } else {
+        long long off = 0;
+        for (int c = 0; c < x->ncases; ++c) {
+            s = set ? set_state_impl(x, c, kind, buf + off, mk, false) : get_state_impl(x, c, kind, buf + off, mk, false);
+            if (s) return s;
+            off += (long long)x->nv * case_cells(x, c);
+        }
+    }
+    CK(x, cudaStreamSynchronize(x->stream));
+    return read_err(x);
+}
+
+extern "C" fv_status fv_set_state_all(fv_ctx* x, int kind, const double* host)
+{
+    return state_all(x, kind, const_cast<double*>(host), true);
+}
+
+extern "C" fv_status fv_get_state_all(fv_ctx* x, int kind, double* host)
+{
+    return state_all(x, kind, host, false);
+}
+
 extern "C" fv_status fv_set_state_device(fv_ctx* x, int icase, int kind, const double* dev)
 {
     return set_state_impl(x, icase, kind, dev, cudaMemcpyDeviceToDevice, false);

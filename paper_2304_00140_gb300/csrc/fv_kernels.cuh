@@ -58,8 +58,10 @@ struct TileDef { int x, y, z, nt, mb, nb; };
 constexpr int NTILES = 4;
 constexpr TileDef TILES2[NTILES] = {{32, 8, 1, 288, 2, 2}, {32, 8, 1, 288, 3, 2}, {16, 16, 1, 288, 3, 2},
                                     {16, 16, 1, 288, 2, 2}};
+// 3D: 16x8x4 recomputes fewer faces at tile edges (3.44 a cell against 3.56
+// for 16x4x4) with a smaller halo, at one block per SM
 constexpr TileDef TILES3[NTILES] = {{32, 4, 2, 256, 2, 1}, {16, 4, 4, 320, 2, 1}, {16, 8, 2, 320, 2, 1},
-                                    {16, 4, 4, 320, 2, 2}};
+                                    {16, 8, 4, 544, 1, 1}};
 constexpr TileDef tile_def(int nd, int i) { return nd == 2 ? TILES2[i] : TILES3[i]; }
 
 // Kernel variants of the stage kernel: 0 .. NTILES-1 stiffened/ideal-gas

@@ -46,6 +46,10 @@ cudaError_t launch_split(int nv, const double* in, long long ncell, void* reg, l
                          cudaStream_t s);
 cudaError_t launch_join(int nv, const void* reg, long long ntot_q, long long off, long long ncell, double* out,
                         cudaStream_t s);
+// every case's conserved doubles (concatenated [case][nv][ncell], device or
+// mapped host memory) <-> the registers; to_reg = 1 writes the registers
+cudaError_t launch_all_cases(int nv, int ncases, const CaseDesc* cases, long long max_cells, const double* host,
+                             void* reg, long long ntot_q, int ff, int to_reg, cudaStream_t s);
 // nv fields of ncell doubles between two field strides (FP64 registers)
 cudaError_t launch_copy_fields(int nv, const double* in, long long in_stride, double* out, long long out_stride,
                                long long ncell, cudaStream_t s);

@@ -28,7 +28,7 @@ FV_DIAG_TOTALS, FV_DIAG_DT, FV_DIAG_TIME, FV_DIAG_ERROR, FV_DIAG_TILE = range(5)
 EXPORTS = ["fv_workspace_size", "fv_init", "fv_init_ws", "fv_destroy", "fv_set_stream", "fv_set_state",
            "fv_get_state", "fv_set_state_device", "fv_get_state_device", "fv_rk_stage", "fv_step",
            "fv_step_async", "fv_get_diag", "fv_launch_count", "fv_last_error", "fv_status_string",
-           "fv_profile", "fv_profile_read", "fv_rk_stage_noalloc"]
+           "fv_profile", "fv_profile_read", "fv_rk_stage_noalloc", "fv_set_state_all", "fv_get_state_all"]
 FV_KERNEL_PRIM, FV_KERNEL_DT, FV_KERNEL_STAGE = range(3)
 
 
@@ -89,6 +89,8 @@ def load(build_if_missing: bool = True):
         L.fv_set_stream.argtypes = [vp, vp]
         for f in ("fv_set_state", "fv_get_state", "fv_set_state_device", "fv_get_state_device"):
             getattr(L, f).argtypes = [vp, C.c_int, C.c_int, vp]
+        for f in ("fv_set_state_all", "fv_get_state_all"):
+            getattr(L, f).argtypes = [vp, C.c_int, vp]
         L.fv_rk_stage.argtypes = [vp, C.c_int, C.c_double]
         L.fv_step.argtypes = [vp, C.c_int, C.c_double, dp]
         L.fv_step_async.argtypes = [vp, C.c_int, C.c_double]
@@ -241,6 +243,17 @@ class Solver:
 
     def get_state_device(self, t, kind=FV_CONSERVED, case: int = 0):
         self._check(self.L.fv_get_state_device(self.ctx, case, kind, C.c_void_p(t.data_ptr())))
+
+    def set_state_all(self, arr: np.ndarray, kind=FV_CONSERVED):
+        """every case at once: each case's state flattened, concatenated in case order"""
+        a = np.ascontiguousarray(arr, dtype=np.float64)
+        assert a.size == sum(int(np.prod(self.shape(c))) for c in range(len(self.cases)))
+        self._check(self.L.fv_set_state_all(self.ctx, kind, _dptr(a)))
+
+    def get_state_all(self, kind=FV_CONSERVED) -> np.ndarray:
+        a = np.zeros(sum(int(np.prod(self.shape(c))) for c in range(len(self.cases))), dtype=np.float64)
+        self._check(self.L.fv_get_state_all(self.ctx, kind, _dptr(a)))
+        return a
 
     # -- time stepping
     def rk_stage(self, k: int, dt: float):

@@ -48,3 +48,34 @@ def test_state_io_paths_agree(precision, kind):
     assert L.fv_set_state(s.ctx, 0, kind, C.c_void_p(pin.data_ptr())) == fv.FV_OK
     s.step(2, w.cfl)
     assert np.array_equal(s.get_state(), a)
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_all_cases_io_matches_per_case(precision):
+    """fv_set_state_all / fv_get_state_all on a batch of uneven cases: the
+    concatenated blocks equal the per-case calls, from page-locked memory
+    (one kernel over all cases) and from pageable memory (case by case)."""
+    import torch
+    cases = [wl.droplet(n=n, A=a, sigma=20.0) for n, a in ((24, 0.1), (40, 0.2), (33, 0.05), (16, 0.15))]
+    s = fv.Solver(cases, precision=precision)
+    for i, c in enumerate(cases):
+        s.set_state(c.primitives(), kind=fv.FV_PRIMITIVE, case=i)
+    s.step(2, 0.4)
+    per_case = np.concatenate([s.get_state(case=i).ravel() for i in range(len(cases))])
+    assert np.array_equal(s.get_state_all(), per_case)                  # pageable
+    L = s.L
+    out = torch.zeros(per_case.size, dtype=torch.float64).pin_memory()
+    assert L.fv_get_state_all(s.ctx, fv.FV_CONSERVED, C.c_void_p(out.data_ptr())) == fv.FV_OK
+    assert np.array_equal(out.numpy(), per_case)                       # page-locked
+    # set from page-locked memory, step, compare with the per-case set
+    pin = torch.from_numpy(per_case.copy()).pin_memory()
+    assert L.fv_set_state_all(s.ctx, fv.FV_CONSERVED, C.c_void_p(pin.data_ptr())) == fv.FV_OK
+    s.step(2, 0.4)
+    a = s.get_state_all()
+    off = 0
+    for i, c in enumerate(cases):
+        n = c.nvar * c.cells
+        s.set_state(per_case[off:off + n].reshape(s.shape(i)), case=i)
+        off += n
+    s.step(2, 0.4)
+    assert np.array_equal(s.get_state_all(), a)
