@@ -176,7 +176,7 @@ def record_traffic(args):
     hdr = rows[0]
     ki, ii, mi, vi, ui = (hdr.index(k) for k in ("Kernel Name", "ID", "Metric Name", "Metric Value", "Metric Unit"))
     for r in rows[1:]:
-        if ("stage_kernel" in r[ki] or "march2d_kernel" in r[ki]) and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        if ("stage_kernel" in r[ki] or "march2d_kernel" in r[ki] or "zmarch_kernel" in r[ki]) and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             per[r[ii]] = per.get(r[ii], 0.0) + float(r[vi].replace(",", "")) * scale[r[ui]]
     if not per or args.precision == "both":
         raise SystemExit("need stage_kernel DRAM metrics in the CSV and --precision mixed|fp64")
@@ -449,7 +449,8 @@ def main():
         ach = byt / (avg_ms * 1e-3) / 1e9
         form = "mixed" if precision == fv.FV_MIXED else "fp64"
         out = dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
-                   traffic=_ncu_traffic(job, form), kernel="march2d_kernel" if fused else "stage_kernel",
+                   traffic=_ncu_traffic(job, form),
+                   kernel="march2d_kernel" if fused else ("zmarch_kernel" if r["tile"].get("zmarch") else "stage_kernel"),
                    avg_launch_ms=avg_ms,
                    algorithmic_bytes_per_launch=byt, peak_source=peaks["src"],
                    kernel_share={k: v["ms"] for k, v in r["prof"].items()}, tile=r["tile"])

@@ -64,9 +64,10 @@ enum { FV_DIAG_TOTALS = 0,   /* double[nv]: compensated sums of q over the case 
                                 autotuner (runs it if not yet run; for the fused 2D
                                 kernel: strip width, rows per work item, 1, threads),
                                 [4..7] the tuner's milliseconds per tile (0 if not
-                                timed), [8] 1 if the fused kernel was chosen, [9] its
-                                best tuned milliseconds, [10] the primitive pass's,
-                                [11] the fused kernel variant (-1: tiled) */
+                                timed), [8] 1 if the fused 2D kernel was chosen, 2 for
+                                the z-marching 3D kernel (tile x, y, planes per item,
+                                threads in [0..3]), [9] its best tuned milliseconds,
+                                [10] the primitive pass's, [11] its variant (-1: tiled) */
 enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2,
        FV_ERRBIT_TIMEOUT = 4 };   /* a bounded wait in a kernel gave up (reported as FV_ERR_CUDA) */
 
@@ -170,9 +171,11 @@ fv_status fv_rk_stage(fv_ctx* ctx, int k, double dt);
  * the tiled kernel's tile shapes (each after a primitive pass) and, for 2D
  * grids in plain mode with the stiffened/ideal-gas closure, a fused kernel
  * that recovers the primitives itself (one pass per stage, no primitive
- * pass).  FV_TILE=<index> in the environment forces a tile of the tiled
- * kernel, FV_FUSED=0/1 excludes or forces the fused kernel.  Set the state
- * first. */
+ * pass), and for 3D grids in the FP32-mixed form with the stiffened/ideal-gas
+ * closure a kernel that marches along z with TMA plane loads.
+ * FV_TILE=<index> in the environment forces a tile of the tiled kernel,
+ * FV_FUSED=0/1 and FV_ZMARCH=0/1 exclude or force the fused and the
+ * z-marching kernel.  Set the state first. */
 
 /* nsteps full steps: per step dt = cfl / max(sum_d (|u_d| + c)/dx_d) of each
  * case (computed on the device from the step's initial state), then the four

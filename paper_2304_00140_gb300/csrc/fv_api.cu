@@ -16,6 +16,7 @@
 
 #include "../../include/thinc_fv.h"
 #include "fv_march.cuh"
+#include "fv_zmarch.cuh"
 #include "fv_launch.h"
 
 using namespace tfv;
@@ -30,13 +31,14 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
     size_t cases, items_stage, items_prim, items_march, q0, qa, qb, prim, io, smax, dt, t, err, in_u, partial, tmaps,
-        total;
-    int n_items_stage, n_items_prim, n_items_march;
+        items_z, tmaps_z, total;
+    int n_items_stage, n_items_prim, n_items_march, n_items_z;
     long long ntot_q, ntot_p, max_cells, n_in_u;
 };
 
 constexpr int MARCH_CHUNK_MIN = 16;                  // shortest row chunk of a fused-kernel work item
 constexpr int MARCH_CHUNKS[3] = {16, 32, 64};        // row chunks the tuner tries
+constexpr int ZM_CHUNKS[3] = {16, 32, 64};           // z-plane chunks of the z-marching kernel
 
 int tile_x(int nd) { return nd == 2 ? TileShape<2>::X : TileShape<3>::X; }
 int tile_y(int nd) { return nd == 2 ? TileShape<2>::Y : TileShape<3>::Y; }
@@ -87,6 +89,13 @@ struct fv_ctx {
     // TMA halo-tile loads of the tiled kernel: one descriptor per case for the current tile
     unsigned char* d_tmaps = nullptr;
     bool tma = false;
+    // z-marching 3D stage kernel (FP32-mixed, stiffened/ideal gas, TMA planes)
+    bool zm_ok = false, zm = false;
+    int zvar = 0, zchunk = 0, zm_grid = 0, n_items_z = 0;
+    size_t zm_smem = 0;
+    int4* d_items_z = nullptr;
+    unsigned char* d_tmaps_z = nullptr;
+    float zm_ms = 0.f;
     float march_ms = 0.f, prim_ms = 0.f;
     size_t smem_max = 0;                    // opt-in shared memory per block of the device
     bool tuned = false;
@@ -370,6 +379,9 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
         L.n_items_prim += (int)npr;
         if (nd == 2)
             L.n_items_march += ((C.n[0] + MARCH_COLS - 1) / MARCH_COLS) * ((C.n[1] + MARCH_CHUNK_MIN - 1) / MARCH_CHUNK_MIN);
+        if (nd == 3)
+            L.n_items_z += ((C.n[0] + ZM_TX - 1) / ZM_TX) * ((C.n[1] + ZM_TY - 1) / ZM_TY) *
+                           ((C.n[2] + ZM_CHUNKS[0] - 1) / ZM_CHUNKS[0]);
         if (items_stage)
             for (int z = 0; z < C.n[2]; z += ts[2])
                 for (int y = 0; y < C.n[1]; y += ts[1])
@@ -401,6 +413,8 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
     L.in_u = take(sizeof(double) * std::max(1LL, nin));
     L.partial = take(sizeof(double) * nv * 1024);
     L.tmaps = take(TMAP_BYTES * (size_t)ncases);
+    L.items_z = take(sizeof(int4) * std::max(1, L.n_items_z));
+    L.tmaps_z = take(TMAP_BYTES * (size_t)ncases);
     L.total = o;
 }
 
@@ -455,21 +469,20 @@ static const void* stage_tmaps(const fv_ctx* x) { return x->tma ? x->d_tmaps : n
 // halo box of `variant`'s tile; zero fill outside the ghosted box.  Every TMA
 // alignment rule is checked here; if one fails (or FV_TMA=0 in the
 // environment, or no encoder) the tiled kernel keeps its cp.async loads.
-static fv_status encode_tmaps(fv_ctx* x, int variant)
+// Descriptors [x, y, z, field] of every case's primitive arrays with box
+// `box` (zero fill outside the ghosted box) into `dst`.  Every TMA alignment
+// rule is checked here (x0 = tile origins in x, multiples of `xalign` cells);
+// false if one fails, if FV_TMA=0 is set or if there is no encoder.
+static bool encode_maps(fv_ctx* x, const cuuint32_t* box, int xalign, unsigned char* dst)
 {
-    x->tma = false;
     if (const char* f = getenv("FV_TMA"))
-        if (atoi(f) == 0) return FV_OK;
+        if (atoi(f) == 0) return false;
     EncodeTiledFn fn = encode_tiled();
-    if (!fn) return FV_OK;
-    const TileDef td = tile_def(x->nd, variant_tile(variant));
+    if (!fn) return false;
     const cuuint64_t es = x->mixed ? sizeof(float) : sizeof(double);
-    const cuuint32_t box[4] = {cuuint32_t(td.x + 4), cuuint32_t(td.y + 4), cuuint32_t(x->nd == 3 ? td.z + 4 : 1),
-                               cuuint32_t(x->nprim)};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    // tile origins are multiples of td.x cells: x * element size on 16 bytes
-    if ((td.x * es) % 16 || (box[0] * es) % 16 || box[0] > 256 || box[1] > 256 || box[2] > 256 || box[3] > 256)
-        return FV_OK;
+    if ((xalign * es) % 16 || (box[0] * es) % 16 || box[0] > 256 || box[1] > 256 || box[2] > 256 || box[3] > 256)
+        return false;
     std::vector<CUtensorMap> maps(x->ncases);
     for (int c = 0; c < x->ncases; ++c) {
         const CaseDesc& C = x->cases[c];
@@ -477,15 +490,55 @@ static fv_status encode_tmaps(fv_ctx* x, int variant)
         const cuuint64_t dims[4] = {cuuint64_t(C.g[0]), cuuint64_t(C.g[1]), cuuint64_t(C.g[2]), cuuint64_t(x->nprim)};
         const cuuint64_t strides[3] = {C.gp * es, C.gp * es * C.g[1], cuuint64_t(x->L.ntot_p) * es};
         if (reinterpret_cast<uintptr_t>(base) % 16 || strides[0] % 16 || strides[1] % 16 || strides[2] % 16)
-            return FV_OK;
+            return false;
         if (fn(&maps[c], es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base, dims,
                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return FV_OK;
+            return false;
     }
     static_assert(sizeof(CUtensorMap) == TMAP_BYTES, "descriptor size");
-    CK(x, cudaMemcpy(x->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice));
-    x->tma = true;
+    return cudaMemcpy(dst, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// the tiled kernel's descriptors for `variant`'s halo box; without them it
+// keeps its cp.async loads
+static fv_status encode_tmaps(fv_ctx* x, int variant)
+{
+    const TileDef td = tile_def(x->nd, variant_tile(variant));
+    const cuuint32_t box[4] = {cuuint32_t(td.x + 4), cuuint32_t(td.y + 4), cuuint32_t(x->nd == 3 ? td.z + 4 : 1),
+                               cuuint32_t(x->nprim)};
+    x->tma = encode_maps(x, box, td.x, x->d_tmaps);
+    return FV_OK;
+}
+
+// z-marching kernel with z-chunk `chunk` and variant `var` (needs TMA)
+static fv_status apply_zmarch(fv_ctx* x, int chunk, int var)
+{
+    const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
+    if (!t42) var = 2;
+    const cuuint32_t box[4] = {cuuint32_t(ZM_TX + 4), cuuint32_t(ZM_TY + 4), 1, cuuint32_t(x->nprim)};
+    if (!encode_maps(x, box, ZM_TX, x->d_tmaps_z)) return fail(x, FV_ERR_ARG, "z-marching kernel needs TMA%s");
+    std::vector<int4> it;
+    for (size_t c = 0; c < x->cases.size(); ++c) {
+        const CaseDesc& C = x->cases[c];
+        for (int z = 0; z < C.n[2]; z += chunk)
+            for (int y = 0; y < C.n[1]; y += ZM_TY)
+                for (int xx = 0; xx < C.n[0]; xx += ZM_TX) it.push_back(make_int4((int)c, xx, y, z));
+    }
+    if ((int)it.size() > x->L.n_items_z) return fail(x, FV_ERR_STATE, "z-march work list overflow%s");
+    CK(x, cudaMemcpy(x->d_items_z, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
+    const size_t smem = zmarch_smem(x->nc, x->nprim);
+    if (smem > x->smem_max) return fail(x, FV_ERR_ARG, "z-marching kernel does not fit in shared memory%s");
+    CK(x, zmarch_set_smem(x->nc, var, smem));
+    const int occ = zmarch_occupancy(x->nc, var, smem);
+    if (occ < 1) return fail(x, FV_ERR_CUDA, "z-marching kernel cannot be resident%s");
+    x->zm = true;
+    x->fused = false;
+    x->zvar = var;
+    x->zchunk = chunk;
+    x->zm_smem = smem;
+    x->n_items_z = (int)it.size();
+    x->zm_grid = (int)std::min<long long>((long long)it.size(), (long long)x->nsm * occ);
     return FV_OK;
 }
 
@@ -529,6 +582,7 @@ static fv_status apply_tile(fv_ctx* x, int tile)
     if (occ < 1) return fail(x, FV_ERR_CUDA, "stage kernel tile cannot be resident%s");
     x->tile = tile;
     x->fused = false;
+    x->zm = false;
     x->smem = smem;
     {
         const fv_status st = encode_tmaps(x, tile);
@@ -559,6 +613,7 @@ static fv_status apply_march(fv_ctx* x, int chunk, int var)
     const int occ = march_occupancy(x->nc, x->mixed, march_mode(x), var);
     if (occ < 1) return fail(x, FV_ERR_CUDA, "fused stage kernel cannot be resident%s");
     x->fused = true;
+    x->zm = false;
     x->mvar = var;
     x->chunk = chunk;
     x->n_items_march = (int)it.size();
@@ -600,10 +655,14 @@ static fv_status tune(fv_ctx* x)
         const int t = atoi(f);
         if (t >= 0 && t < NTILES) return apply_tile(x, t);
     }
+    int want_zm = -1;      // FV_ZMARCH=0/1 excludes or forces the z-marching kernel
+    if (const char* f = getenv("FV_ZMARCH")) want_zm = atoi(f) ? 1 : 0;
+    if (!x->zm_ok) want_zm = 0;
     const bool tiles = tunable(x->P);
-    if (!tiles && want_fused == 0) return apply_tile(x, 0);   // a single candidate
-    const std::string key = tune_key(x) + "/" + std::to_string(want_fused);
+    if (!tiles && want_fused == 0 && want_zm == 0) return apply_tile(x, 0);   // a single candidate
+    const std::string key = tune_key(x) + "/" + std::to_string(want_fused) + "/" + std::to_string(want_zm);
     auto apply = [&](int code) {
+        if (code >= 200) return apply_zmarch(x, ZM_CHUNKS[(code - 200) / 10], (code - 200) % 10);
         return code < 100 ? apply_tile(x, code) : apply_march(x, MARCH_CHUNKS[(code - 100) / 10], (code - 100) % 10);
     };
     {
@@ -640,7 +699,7 @@ static fv_status tune(fv_ctx* x)
     if (st) return st;
     int best = -1;
     float best_ms = 1e30f;
-    if (want_fused != 1) {
+    if (want_fused != 1 && want_zm != 1) {
         for (int t = 0; t < (tiles ? NTILES : 1); ++t) {
             if (apply_tile(x, t)) { x->msg.clear(); continue; }
             StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, stage_tmaps(x), x->Q0, x->QB,
@@ -671,6 +730,23 @@ static fv_status tune(fv_ctx* x)
                 if (ms < best_ms) { best_ms = ms; best = 100 + 10 * ci + var; }
             }
         x->march_ms = fbest;
+    }
+    if (want_zm != 0) {
+        // after the primitive pass above, like the tiled kernel
+        const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
+        float zbest = 1e30f;
+        for (int ci = 0; ci < 3; ++ci)
+            for (int var = (t42 ? 0 : 2); var < (t42 ? 2 : 3); ++var) {
+                if (apply_zmarch(x, ZM_CHUNKS[ci], var)) { x->msg.clear(); continue; }
+                ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, x->QB,
+                         x->dt, 0.0, x->err};
+                float ms = 0.f;
+                st = timed([&] { return launch_zmarch(x->nc, x->zvar, za, x->zm_grid, x->zm_smem, x->stream); }, ms);
+                if (st) return st;
+                zbest = std::min(zbest, ms);
+                if (ms < best_ms) { best_ms = ms; best = 200 + 10 * ci + var; }
+            }
+        x->zm_ms = zbest;
     }
     x->prim_ms = prim_ms;
     cudaEventDestroy(e0);
@@ -742,6 +818,8 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     x->in_u = reinterpret_cast<double*>(b + L.in_u);
     x->partial = reinterpret_cast<double*>(b + L.partial);
     x->d_tmaps = b + L.tmaps;
+    x->d_items_z = reinterpret_cast<int4*>(b + L.items_z);
+    x->d_tmaps_z = b + L.tmaps_z;
     CK(x, cudaStreamCreateWithFlags(&x->cap, cudaStreamNonBlocking));
     CK(x, cudaMemcpy(x->d_cases, x->cases.data(), sizeof(CaseDesc) * ncases, cudaMemcpyHostToDevice));
     CK(x, cudaMemcpy(x->d_items_prim, ipr.data(), sizeof(int4) * ipr.size(), cudaMemcpyHostToDevice));
@@ -772,6 +850,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         if (s) return s;
     }
     x->fused_ok = x->nd == 2 && !x->P.pr;
+    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }
@@ -1025,6 +1104,13 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
         PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
         x->launches++;
     }
+    if (x->zm) {
+        ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, out, x->dt,
+                 LSRK_A[k - 1], x->err};
+        PROF(FV_KERNEL_STAGE, launch_zmarch(x->nc, x->zvar, za, x->zm_grid, x->zm_smem, s));
+        x->launches++;
+        return FV_OK;
+    }
     StageArgs sa{x->P, x->d_cases, x->d_items_stage, x->n_items_cur, x->prim, stage_tmaps(x), x->Q0, out, x->dt,
                  LSRK_A[k - 1], x->err};
     PROF(FV_KERNEL_STAGE, launch_stage(x->nd, x->nc, x->mixed, x->tile, sa, x->stage_grid, x->smem, s, x->ff));
@@ -1154,14 +1240,16 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
         double* o = static_cast<double*>(out);
         if (x->fused) {
             o[0] = MARCH_COLS; o[1] = x->chunk; o[2] = 1; o[3] = 32 * MARCH_WARPS;
+        } else if (x->zm) {
+            o[0] = ZM_TX; o[1] = ZM_TY; o[2] = x->zchunk; o[3] = zmarch_threads(x->zvar);
         } else {
             o[0] = td.x; o[1] = td.y; o[2] = td.z; o[3] = td.nt;
         }
         for (int t = 0; t < NTILES; ++t) o[4 + t] = x->tune_ms[t];
-        o[8] = x->fused ? 1.0 : 0.0;
-        o[9] = x->march_ms;
+        o[8] = x->fused ? 1.0 : (x->zm ? 2.0 : 0.0);
+        o[9] = x->zm ? x->zm_ms : x->march_ms;
         o[10] = x->prim_ms;
-        o[11] = x->fused ? x->mvar : -1;
+        o[11] = x->fused ? x->mvar : (x->zm ? x->zvar : -1);
         return FV_OK;
     }
     if (what == FV_DIAG_ERROR) {

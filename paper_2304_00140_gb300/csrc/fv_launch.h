@@ -28,6 +28,16 @@ constexpr int MARCH_WARPS = 4;
 cudaError_t launch_march(int nc, int mixed, int mode, int var, const MarchArgs& A, int grid, cudaStream_t s);
 int march_occupancy(int nc, int mixed, int mode, int var);   // blocks per SM
 
+// z-marching 3D stage kernel (fv_zmarch.cuh), FP32-mixed, stiffened/ideal gas,
+// TMA plane loads.  var: 0 / 1 Table 4.2 limiter pair with 320 / 256
+// threads, 2 limiter pair read at run time.
+struct ZArgs;
+cudaError_t launch_zmarch(int nc, int var, const ZArgs& A, int grid, size_t smem, cudaStream_t s);
+cudaError_t zmarch_set_smem(int nc, int var, size_t smem);
+int zmarch_occupancy(int nc, int var, size_t smem);   // blocks per SM
+int zmarch_threads(int var);
+size_t zmarch_smem(int nc, int nprim);
+
 // state I/O and diagnostics (FP64)
 struct IoArgs {
     DevParams P;

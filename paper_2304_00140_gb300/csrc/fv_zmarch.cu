@@ -1,0 +1,53 @@
+// fv_zmarch.cu -- instantiations and launchers of the z-marching 3D stage
+// kernel (fv_zmarch.cuh): FP32-mixed form, 2 or 3 components.
+// Variants: 0 Table 4.2 limiter pair, 320 threads; 1 the same with 256
+// threads; 2 a limiter pair read at run time, 320 threads.  Two resident
+// blocks per SM (the plane ring takes about 100 KB of shared memory).
+#include "fv_launch.h"
+#include "fv_zmarch.cuh"
+
+namespace tfv {
+
+namespace {
+template <int V> constexpr int nt_of() { return V == 1 ? 256 : 320; }
+template <int V> constexpr int lim_of() { return V == 2 ? LIM_RUNTIME : LIM_TABLE42; }
+#define FV_ZK(NC, V) zmarch_kernel<NC, nt_of<V>(), 2, lim_of<V>(), float2>
+
+template <int NC, int V>
+cudaError_t go(const ZArgs& A, int grid, size_t smem, cudaStream_t s)
+{
+    FV_ZK(NC, V)<<<grid, nt_of<V>(), smem, s>>>(A);
+    return cudaGetLastError();
+}
+template <int NC, int V>
+cudaError_t attr(size_t smem)
+{
+    return cudaFuncSetAttribute(FV_ZK(NC, V), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+template <int NC, int V>
+int occ(size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FV_ZK(NC, V), nt_of<V>(), smem) != cudaSuccess) return 0;
+    return n;
+}
+#undef FV_ZK
+}  // namespace
+
+#define FV_ZSWITCH(fn, ...)                                                                 \
+    switch (var) {                                                                          \
+    case 1: return nc == 2 ? fn<2, 1>(__VA_ARGS__) : fn<3, 1>(__VA_ARGS__);                  \
+    case 2: return nc == 2 ? fn<2, 2>(__VA_ARGS__) : fn<3, 2>(__VA_ARGS__);                  \
+    default: return nc == 2 ? fn<2, 0>(__VA_ARGS__) : fn<3, 0>(__VA_ARGS__);                 \
+    }
+
+cudaError_t launch_zmarch(int nc, int var, const ZArgs& A, int grid, size_t smem, cudaStream_t s)
+{
+    FV_ZSWITCH(go, A, grid, smem, s)
+}
+cudaError_t zmarch_set_smem(int nc, int var, size_t smem) { FV_ZSWITCH(attr, smem) }
+int zmarch_occupancy(int nc, int var, size_t smem) { FV_ZSWITCH(occ, smem) }
+int zmarch_threads(int var) { return var == 1 ? 256 : 320; }
+size_t zmarch_smem(int nc, int nprim) { return nc == 2 ? zm_smem_bytes<2>(nprim) : zm_smem_bytes<3>(nprim); }
+
+}  // namespace tfv

@@ -286,7 +286,8 @@ class Solver:
         out = np.zeros(12)
         self._check(self.L.fv_get_diag(self.ctx, 0, FV_DIAG_TILE, _dptr(out)))
         return dict(tile=[int(v) for v in out[:3]], threads=int(out[3]), tune_ms=out[4:8].tolist(),
-                    fused=bool(out[8]), fused_ms=float(out[9]), prim_ms=float(out[10]), fused_variant=int(out[11]))
+                    fused=bool(out[8] == 1), zmarch=bool(out[8] == 2), fused_ms=float(out[9]),
+                    prim_ms=float(out[10]), fused_variant=int(out[11]))
 
     def error_word(self) -> int:
         out = C.c_int()
