@@ -735,8 +735,10 @@ static fv_status tune(fv_ctx* x)
         // after the primitive pass above, like the tiled kernel
         const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
         float zbest = 1e30f;
+        const int zvars_t42[3] = {0, 1, 3}, zvars_rt[1] = {2};
         for (int ci = 0; ci < 3; ++ci)
-            for (int var = (t42 ? 0 : 2); var < (t42 ? 2 : 3); ++var) {
+            for (int vi = 0; vi < (t42 ? 3 : 1); ++vi) {
+                const int var = t42 ? zvars_t42[vi] : zvars_rt[vi];
                 if (apply_zmarch(x, ZM_CHUNKS[ci], var)) { x->msg.clear(); continue; }
                 ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, x->QB,
                          x->dt, 0.0, x->err};

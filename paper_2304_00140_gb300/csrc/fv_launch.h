@@ -29,8 +29,8 @@ cudaError_t launch_march(int nc, int mixed, int mode, int var, const MarchArgs& 
 int march_occupancy(int nc, int mixed, int mode, int var);   // blocks per SM
 
 // z-marching 3D stage kernel (fv_zmarch.cuh), FP32-mixed, stiffened/ideal gas,
-// TMA plane loads.  var: 0 / 1 Table 4.2 limiter pair with 320 / 256
-// threads, 2 limiter pair read at run time.
+// TMA plane loads.  var: 0 / 1 / 3 Table 4.2 limiter pair with 320 / 256 /
+// 352 threads, 2 limiter pair read at run time (320 threads).
 struct ZArgs;
 cudaError_t launch_zmarch(int nc, int var, const ZArgs& A, int grid, size_t smem, cudaStream_t s);
 cudaError_t zmarch_set_smem(int nc, int var, size_t smem);

@@ -1,7 +1,8 @@
 // fv_zmarch.cu -- instantiations and launchers of the z-marching 3D stage
 // kernel (fv_zmarch.cuh): FP32-mixed form, 2 or 3 components.
-// Variants: 0 Table 4.2 limiter pair, 320 threads; 1 the same with 256
-// threads; 2 a limiter pair read at run time, 320 threads.  Two resident
+// Variants: 0 / 1 / 3 Table 4.2 limiter pair with 320 / 256 / 352 threads
+// (352 covers a plane's 18 x 18 sensor and smoothing cells in one round);
+// 2 a limiter pair read at run time, 320 threads.  Two resident
 // blocks per SM (the plane ring takes about 100 KB of shared memory).
 #include "fv_launch.h"
 #include "fv_zmarch.cuh"
@@ -9,7 +10,7 @@
 namespace tfv {
 
 namespace {
-template <int V> constexpr int nt_of() { return V == 1 ? 256 : 320; }
+template <int V> constexpr int nt_of() { return V == 1 ? 256 : (V == 3 ? 352 : 320); }
 template <int V> constexpr int lim_of() { return V == 2 ? LIM_RUNTIME : LIM_TABLE42; }
 #define FV_ZK(NC, V) zmarch_kernel<NC, nt_of<V>(), 2, lim_of<V>(), float2>
 
@@ -38,6 +39,7 @@ int occ(size_t smem)
     switch (var) {                                                                          \
     case 1: return nc == 2 ? fn<2, 1>(__VA_ARGS__) : fn<3, 1>(__VA_ARGS__);                  \
     case 2: return nc == 2 ? fn<2, 2>(__VA_ARGS__) : fn<3, 2>(__VA_ARGS__);                  \
+    case 3: return nc == 2 ? fn<2, 3>(__VA_ARGS__) : fn<3, 3>(__VA_ARGS__);                  \
     default: return nc == 2 ? fn<2, 0>(__VA_ARGS__) : fn<3, 0>(__VA_ARGS__);                 \
     }
 
@@ -47,7 +49,7 @@ cudaError_t launch_zmarch(int nc, int var, const ZArgs& A, int grid, size_t smem
 }
 cudaError_t zmarch_set_smem(int nc, int var, size_t smem) { FV_ZSWITCH(attr, smem) }
 int zmarch_occupancy(int nc, int var, size_t smem) { FV_ZSWITCH(occ, smem) }
-int zmarch_threads(int var) { return var == 1 ? 256 : 320; }
+int zmarch_threads(int var) { return var == 1 ? 256 : (var == 3 ? 352 : 320); }
 size_t zmarch_smem(int nc, int nprim) { return nc == 2 ? zm_smem_bytes<2>(nprim) : zm_smem_bytes<3>(nprim); }
 
 }  // namespace tfv

@@ -384,8 +384,11 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                     qo += P.ntot_q;
                 }
             }
-            __syncthreads();
+            // no barrier here: the update writes only global memory, and what it
+            // reads (fluxes, normals, gradients, plane z) is overwritten only
+            // after the next plane's wait, which is a block barrier
         }
+        __syncthreads();   // the next item's prologue rewrites every ring
     }
 }
 
