@@ -7,11 +7,12 @@
 // A block owns a TX x TY column of cells and walks up a chunk of z-planes.
 // The primitives of planes z-1 .. z+2 (with a 2-cell halo in x and y) sit in
 // a ring of four shared-memory slots; each step brings in one new plane with
-// one TMA copy.  Per plane the block computes the sensor flags and smoothed
-// fractions of plane z+1, the vertex normals and z-face fluxes between z and
-// z+1, the x- and y-faces of plane z and the update of plane z; the flags,
-// smoothed fractions, normals and z-fluxes of the plane below are kept from
-// the previous step.  Every face is computed once (the tiled kernel computes
+// one TMA copy.  A step has two phases, each closed by a block barrier:
+// (1) the vertex normals and z-face fluxes between z and z+1 and the x- and
+// y-faces of plane z; (2) the update of plane z, then (once plane z+3 has
+// arrived) the sensor flags and smoothed fractions of plane z+2 for the next
+// step.  The flags, smoothed fractions, normals and z-fluxes of the planes
+// below are kept in two-slot rings.  Every face is computed once (the tiled kernel computes
 // a tile's edge faces twice), and the +1 halo work of the sensor and the
 // smoothing is in x and y only.
 #pragma once
@@ -283,6 +284,10 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
         for (int f = tid; f < TXY; f += NT) zfaces(z0 - 1, f);
         __syncthreads();
         issue(z0 + 2);   // into the slot of plane z0-2, read for the last time above
+        if (!wait(z0 + 2)) { timeout(); return; }
+        if (P.iles) sensor_plane(z0 + 1);
+        if (P.csf) smooth_plane(z0 + 1);
+        __syncthreads();
 
         const double adt = A.a * A.dt[wi.x];
         const float adtf = float(adt);
@@ -296,11 +301,8 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) { q0r[v] = own ? *qp : Q{}; qp += P.ntot_q; }
             }
-            if (!wait(z + 2)) { timeout(); return; }
-            // sensor and smoothed fractions of plane z+1
-            if (P.iles) sensor_plane(z + 1);
-            if (P.csf) smooth_plane(z + 1);
-            __syncthreads();
+            // planes z-1 .. z+2 and the flags and smoothed fractions of planes z
+            // and z+1 are in place (previous step or prologue).
             // normals between z and z+1; x- and y-faces of plane z; z-faces between z and z+1
             if (P.csf) normals(z);
             {
@@ -335,7 +337,8 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
             }
             __syncthreads();
             // plane z-1 is no longer read: its slot takes plane z+3 while the update runs
-            if (z + 1 < z1) issue(z + 3);
+            const bool more = z + 1 < z1;
+            if (more) issue(z + 3);
             // divergence, CSF source and LSRK update of plane z
             if (own) {
                 R S[NV];
@@ -384,9 +387,20 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                     qo += P.ntot_q;
                 }
             }
-            // no barrier here: the update writes only global memory, and what it
-            // reads (fluxes, normals, gradients, plane z) is overwritten only
-            // after the next plane's wait, which is a block barrier
+            // then, for the next step, plane z+3 and the flags and smoothed
+            // fractions of plane z+2 (they overwrite plane z's, read last in
+            // this step's faces); one barrier closes the step
+            bool ok_next = true;
+            if (more) {
+                const int sl = slot4(z + 3);
+                ok_next = tma_wait(mb(sl), (phase >> sl) & 1u);
+                phase ^= 1u << sl;
+                if (ok_next) {
+                    if (P.iles) sensor_plane(z + 2);
+                    if (P.csf) smooth_plane(z + 2);
+                }
+            }
+            if (__syncthreads_or(!ok_next)) { timeout(); return; }
         }
         __syncthreads();   // the next item's prologue rewrites every ring
     }
