@@ -206,6 +206,14 @@ fv_status fv_profile_read(fv_ctx* ctx, double* out);
 const char* fv_last_error(const fv_ctx* ctx);
 const char* fv_status_string(int status);
 
+/* Self-test of the kernels' bounded waits (the TMA tile and plane copies
+ * wait on an mbarrier with a poll limit): one block waits `polls` polls on an
+ * mbarrier that nothing completes and takes the give-up path.  *err_word
+ * receives the device error word (FV_ERRBIT_TIMEOUT expected); the device
+ * stays usable.  Synchronous, on the legacy default stream; not a paper
+ * operation. */
+fv_status fv_wait_selftest(int polls, int* err_word);
+
 /* One Runge-Kutta stage of one grid that allocates no device memory, for
  * callers that cannot call cudaMalloc: code that runs inside a host
  * application owning the whole device through its own memory pool, code

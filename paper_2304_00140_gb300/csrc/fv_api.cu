@@ -1301,6 +1301,38 @@ extern "C" fv_status fv_profile_read(fv_ctx* x, double* out)
 
 extern "C" const char* fv_last_error(const fv_ctx* x) { return x ? x->msg.c_str() : "null context"; }
 
+namespace {
+__device__ int g_probe_err;   // error word of the wait self-test (not reentrant)
+
+// Self-test of the bounded wait: one block waits on an mbarrier that nothing
+// ever completes, with `polls` polls; the give-up path sets ERR_TIMEOUT in
+// *err exactly as the stage kernels' waits do.
+__global__ void wait_probe_kernel(int polls, int* err)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned a = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(a, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = tma_wait(a, 0u, polls);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+}
+}  // namespace
+
+extern "C" fv_status fv_wait_selftest(int polls, int* err_word)
+{
+    if (polls < 1 || !err_word) return FV_ERR_ARG;
+    int* d = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&d), g_probe_err) != cudaSuccess) return FV_ERR_CUDA;
+    if (cudaMemset(d, 0, sizeof(int)) != cudaSuccess) return FV_ERR_CUDA;
+    wait_probe_kernel<<<1, 64>>>(polls, d);
+    if (cudaGetLastError() != cudaSuccess) return FV_ERR_CUDA;
+    if (cudaMemcpy(err_word, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FV_ERR_CUDA;
+    return FV_OK;
+}
+
 extern "C" const char* fv_status_string(int s)
 {
     switch (s) {

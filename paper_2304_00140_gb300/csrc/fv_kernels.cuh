@@ -147,12 +147,14 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const void* tmap, int 
 }
 // bounded wait for phase `parity` of an mbarrier: false after ~2^22 polls
 // (each poll may suspend the thread for a while), far beyond any copy time
-__device__ __forceinline__ bool tma_wait(unsigned a, unsigned parity)
+constexpr int TMA_WAIT_POLLS = 1 << 22;
+__device__ __forceinline__ bool tma_wait(unsigned a, unsigned parity, int polls = TMA_WAIT_POLLS)
 {
-    for (int i = 0; i < (1 << 22); ++i)
+    for (int i = 0; i < polls; ++i)
         if (mbar_try_wait(a, parity)) return true;
     return false;
 }
+
 constexpr int TMAP_BYTES = 128;   // one CUtensorMap
 
 // halo-tile buffers of the stage kernel: two (prefetch the next item) in the

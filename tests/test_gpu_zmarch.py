@@ -28,6 +28,8 @@ CASES = {
     "plain_3comp_bc": lambda: wl.random_state(
         n=(20, 33, 11), ndim=3, ncomp=3,
         bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2]),
+    "other_limiters": lambda: wl.random_state(n=(21, 18, 13), ndim=3, ncomp=2, iles=1,
+                                              lim_vel=wl.LIM_VANLEER, lim_scalar=wl.LIM_MC),
     "iles_csf_3comp": lambda: wl.random_state(
         n=(18, 17, 40), ndim=3, ncomp=3, iles=1, sigma=5.0,
         bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_PERIODIC] * 2, [wl.BC_REFLECT, wl.BC_OUTFLOW]]),
