@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
 class Comp(C.Structure):
     _fields_ = [("kind", C.c_int), ("gamma", C.c_double), ("pinf", C.c_double), ("cv", C.c_double),
                 ("q", C.c_double), ("Tc", C.c_double), ("pc", C.c_double), ("omega", C.c_double),
-                ("M", C.c_double)]
+                ("M", C.c_double), ("mu", C.c_double), ("kc", C.c_double)]
 
 
 class Params(C.Structure):
@@ -49,7 +49,7 @@ class Params(C.Structure):
                 ("d3p_coef", C.c_double), ("sigma", C.c_double), ("grad_eps", C.c_double),
                 ("in_yc", C.c_double), ("in_zc", C.c_double), ("in_radius", C.c_double),
                 ("in_T", C.c_double), ("in_Y", C.c_double * MAXC), ("in_u", C.POINTER(C.c_double)),
-                ("in_u0", C.c_double * 3)]
+                ("in_u0", C.c_double * 3), ("grav", C.c_double * 3)]
 
 
 def lib():
@@ -76,6 +76,7 @@ def lib():
             L.or_totals.argtypes = [P, dp, dp]
             L.or_csf_source.argtypes = [P, dp, dp]
             L.or_sensor.argtypes = [P, dp, dp]
+            L.or_transport.argtypes = [P, dp, dp]
             L.or_pr_state.argtypes = [P, C.c_double, C.c_double, dp, dp]
             _lib = L
     return _lib
@@ -106,13 +107,16 @@ def make_params(w, inflow_u: np.ndarray | None = None) -> Params:
     P.ncomp = len(w.comps)
     P.liquid = w.liquid
     for k, c in enumerate(w.comps):
-        P.comp[k] = Comp(c["kind"], c["gamma"], c["pinf"], c["cv"], c["q"], c["Tc"], c["pc"], c["omega"], c["M"])
+        P.comp[k] = Comp(c["kind"], c["gamma"], c["pinf"], c["cv"], c["q"], c["Tc"], c["pc"], c["omega"], c["M"],
+                         c.get("mu", 0.0), c.get("kc", 0.0))
     s = w.scheme
     P.iles, P.thinc = int(s["iles"]), int(s["thinc"])
     P.beta, P.thinc_eps, P.thinc_gamma = s["beta"], s["thinc_eps"], s["thinc_gamma"]
     P.lim_vel, P.lim_scalar = s["lim_vel"], s["lim_scalar"]
     P.thr_ducros, P.thr_gas, P.eps_ducros, P.d3p_coef = s["thr_ducros"], s["thr_gas"], s["eps_ducros"], s["d3p_coef"]
     P.sigma, P.grad_eps = s["sigma"], s["grad_eps"]
+    for d, g in enumerate(s.get("gravity", (0.0, 0.0, 0.0))):
+        P.grav[d] = g
     if w.inflow:
         f = w.inflow
         P.in_yc, P.in_zc, P.in_radius, P.in_T = f["yc"] - w.lo[1], f["zc"] - w.lo[2], f["radius"], f["T"]
@@ -185,6 +189,13 @@ class Oracle:
         S = np.zeros((self.w.ndim + 1,) + self.shape[1:])
         _check(self.L.or_csf_source(C.byref(self.P), _ptr(q), _ptr(S)), "csf_source")
         return S
+
+    def transport(self, q):
+        """mixture viscosity and conductivity per interior cell, [2, nz, ny, nx]"""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros((2,) + self.shape[1:])
+        _check(self.L.or_transport(C.byref(self.P), _ptr(q), _ptr(out)), "transport")
+        return out
 
     def sensor(self, q):
         q = np.ascontiguousarray(q, dtype=np.float64)

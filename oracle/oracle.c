@@ -543,7 +543,7 @@ int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4
  * and thermodynamic parameters according to EOS")
  * --------------------------------------------------------------------- */
 static int cell_prim(const or_params* P, const double* qc, double* w, double* rho_out, double* c_out,
-                     double* aliq)
+                     double* al_out /* N volume fractions, or NULL */)
 {
     const int nd = P->ndim, N = P->ncomp;
     double rho = qc[0];
@@ -568,8 +568,40 @@ static int cell_prim(const or_params* P, const double* qc, double* w, double* rh
     if (st) return st;
     if (rho_out) *rho_out = rho;
     if (c_out) *c_out = c;
-    if (aliq) *aliq = al[P->liquid];
+    if (al_out)
+        for (int k = 0; k < N; ++k) al_out[k] = al[k];
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------
+ * Transport properties (Eq. 2-2, Eq. 2-8).  With no vapour in the mixture
+ * (alpha_v = 0) Eq. 2-8 weights each component's viscosity by its volume
+ * fraction.  READING: the paper gives no mixing rule for the thermal
+ * conductivity k_c; it is weighted the same way.  Peng-Robinson mixtures
+ * have no volume fractions, so viscous terms need stiffened-gas / ideal-gas
+ * components.
+ * --------------------------------------------------------------------- */
+static int has_visc(const or_params* P)
+{
+    for (int k = 0; k < P->ncomp; ++k)
+        if (P->comp[k].mu != 0.0 || P->comp[k].kc != 0.0) return 1;
+    return 0;
+}
+
+static int has_grav(const or_params* P)
+{
+    return P->grav[0] != 0.0 || P->grav[1] != 0.0 || P->grav[2] != 0.0;
+}
+
+static void mix_transport(const or_params* P, const double* al, double* mu, double* kc)
+{
+    double m = 0.0, k = 0.0;
+    for (int c = 0; c < P->ncomp; ++c) {
+        m += al[c] * P->comp[c].mu;
+        k += al[c] * P->comp[c].kc;
+    }
+    *mu = m;
+    *kc = k;
 }
 
 static void gather_q(const or_params* P, const double* q, size_t c, double* qc)
@@ -617,6 +649,8 @@ typedef struct {
     double* c;
     double* al;
     double* flag;  /* App. D cell sensor */
+    double* mu;    /* mixture viscosity and conductivity */
+    double* kc;
 } box_t;
 
 static size_t bidx(const box_t* B, int i, int j, int k)
@@ -626,7 +660,7 @@ static size_t bidx(const box_t* B, int i, int j, int k)
 
 static void box_free(box_t* B)
 {
-    free(B->W); free(B->rho); free(B->c); free(B->al); free(B->flag);
+    free(B->W); free(B->rho); free(B->c); free(B->al); free(B->flag); free(B->mu); free(B->kc);
 }
 
 static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo, const int* hi)
@@ -643,7 +677,9 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
     B->c = calloc(B->cnt, sizeof(double));
     B->al = calloc(B->cnt, sizeof(double));
     B->flag = calloc(B->cnt, sizeof(double));
-    if (!B->W || !B->rho || !B->c || !B->al || !B->flag) return OR_ERR_ARG;
+    B->mu = calloc(B->cnt, sizeof(double));
+    B->kc = calloc(B->cnt, sizeof(double));
+    if (!B->W || !B->rho || !B->c || !B->al || !B->flag || !B->mu || !B->kc) return OR_ERR_ARG;
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
             for (int i = lo[0]; i < hi[0]; ++i) {
@@ -664,9 +700,9 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
                         flip[0] = 1;   /* slip wall */
                     }
                 }
-                double qc[OR_MAXV], w[OR_MAXV], r, c, al;
+                double qc[OR_MAXV], w[OR_MAXV], r, c, alk[OR_MAXC];
                 gather_q(P, q, cidx(P, src[0], src[1], src[2]), qc);
-                int st = cell_prim(P, qc, w, &r, &c, &al);
+                int st = cell_prim(P, qc, w, &r, &c, alk);
                 if (st) return st;
                 for (int d = 0; d < nd; ++d)
                     if (flip[d]) w[d] = -w[d];
@@ -678,16 +714,15 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
                     for (int kk = 0; kk < P->ncomp - 1; ++kk) w[nd + 2 + kk] = P->in_Y[kk];
                     double Y[OR_MAXC], e2;
                     full_Y(P, w + nd + 2, Y);
-                    double alk[OR_MAXC];
                     st = sg_forward(P, w[nd], w[nd + 1], Y, &r, &e2, &c, alk);
                     if (st) return st;
-                    al = alk[P->liquid];
                 }
                 size_t b = bidx(B, i, j, k);
                 for (int v = 0; v < nv; ++v) B->W[(size_t)v * B->cnt + b] = w[v];
                 B->rho[b] = r;
                 B->c[b] = c;
-                B->al[b] = al;
+                B->al[b] = alk[P->liquid];
+                mix_transport(P, alk, &B->mu[b], &B->kc[b]);
             }
     return OR_OK;
 }
@@ -802,6 +837,53 @@ static void csf_cell(const or_params* P, const box_t* B, int i, int j, int k, do
     S[nd] = P->sigma * kappa * udg;
 }
 
+/* Eq. 2-2: the stress term S adds to the flux of direction d
+ *   momentum  -tau_{d a},   tau = mu (grad u + grad u^T - 2/3 (div u) I),
+ *   energy    -(u . tau)_d - k_c dT/dx_d.
+ * READING (the paper gives no discretisation of these terms beyond its
+ * compact four-cell stencil): at the face between cells L and R = L + e_d,
+ * a derivative along d is (phi_R - phi_L) / dx_d; a derivative along
+ * another direction b is the mean of the two cells' central differences,
+ * (phi(L+e_b) - phi(L-e_b) + phi(R+e_b) - phi(R-e_b)) / (4 dx_b); u, mu
+ * and k_c at the face are the means of the two cells' values. */
+static double bW(const box_t* B, int v, const int* c)
+{
+    return B->W[(size_t)v * B->cnt + bidx(B, c[0], c[1], c[2])];
+}
+
+static void visc_face(const or_params* P, const box_t* B, int d, const int* cl, double* F)
+{
+    const int nd = P->ndim;
+    int cr[3] = {cl[0], cl[1], cl[2]};
+    cr[d] += 1;
+    double g[3][3] = {{0.0}};   /* g[a][b] = d u_a / d x_b at the face */
+    for (int b = 0; b < nd; ++b)
+        for (int a = 0; a < nd; ++a) {
+            if (b == d) {
+                g[a][b] = (bW(B, a, cr) - bW(B, a, cl)) / P->dx[d];
+            } else {
+                int lp[3] = {cl[0], cl[1], cl[2]}, lm[3] = {cl[0], cl[1], cl[2]};
+                int rp[3] = {cr[0], cr[1], cr[2]}, rm[3] = {cr[0], cr[1], cr[2]};
+                lp[b] += 1; lm[b] -= 1; rp[b] += 1; rm[b] -= 1;
+                g[a][b] = (bW(B, a, lp) - bW(B, a, lm) + bW(B, a, rp) - bW(B, a, rm)) / (4.0 * P->dx[b]);
+            }
+        }
+    double div = 0.0;
+    for (int a = 0; a < nd; ++a) div += g[a][a];
+    const size_t bl = bidx(B, cl[0], cl[1], cl[2]), br = bidx(B, cr[0], cr[1], cr[2]);
+    const double mu = 0.5 * (B->mu[bl] + B->mu[br]);
+    const double kc = 0.5 * (B->kc[bl] + B->kc[br]);
+    double utau = 0.0;
+    for (int a = 0; a < nd; ++a) {
+        double tau = mu * (g[a][d] + g[d][a]);
+        if (a == d) tau -= 2.0 / 3.0 * mu * div;
+        F[1 + a] -= tau;
+        utau += 0.5 * (bW(B, a, cl) + bW(B, a, cr)) * tau;
+    }
+    const double dTdx = (bW(B, nd + 1, cr) - bW(B, nd + 1, cl)) / P->dx[d];
+    F[1 + nd] -= utau + kc * dTdx;
+}
+
 /* ------------------------------------------------------------------------
  * One Runge-Kutta stage over the window [wlo, whi) (whole interior when
  * NULL): Algorithm 1 in order.
@@ -812,6 +894,8 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
     const int nd = P->ndim, nv = nvar(P);
     if (kst < 1 || kst > 4 || nd < 1 || nd > 3 || nv > OR_MAXV || P->ncomp < 2 || P->ncomp > OR_MAXC)
         return OR_ERR_ARG;
+    const int visc = has_visc(P), grav = has_grav(P);
+    if (visc && !all_kind(P, OR_SG)) return OR_ERR_ARG;
     int lo[3], hi[3], blo[3], bhi[3], slo[3], shi[3];
     for (int d = 0; d < 3; ++d) {
         lo[d] = wlo ? wlo[d] : 0;
@@ -862,6 +946,7 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                     double F[OR_MAXV];
                     st = or_face_flux(P, d, W4, r4, c4, f, F);
                     if (st) goto done;
+                    if (visc) visc_face(P, &B, d, c, F);
                     size_t fi = ((size_t)k * fext[d][1] + j) * fext[d][0] + i;
                     for (int v = 0; v < nv; ++v) Fd[d][(size_t)v * fc + fi] = F[v];
                 }
@@ -879,6 +964,14 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                         csf_cell(P, &B, i, j, k, s4);
                         for (int d = 0; d < nd; ++d) S[1 + d] = s4[d];
                         S[1 + nd] = s4[nd];
+                    }
+                    if (grav) {
+                        /* Eq. 2-2 Q: rho g (momentum) and rho u . g (energy) */
+                        const size_t b0 = bidx(&B, i, j, k);
+                        for (int d = 0; d < nd; ++d) {
+                            S[1 + d] += B.rho[b0] * P->grav[d];
+                            S[1 + nd] += B.rho[b0] * B.W[(size_t)d * B.cnt + b0] * P->grav[d];
+                        }
                     }
                     int wi = i - lo[0], wj = j - lo[1], wk = k - lo[2];
                     size_t c = cidx(P, i, j, k);
@@ -940,21 +1033,33 @@ int or_cons_to_prim(const or_params* P, const double* q, double* W)
     return OR_OK;
 }
 
-/* READING (no CFL definition in the paper): dt = CFL / max_i sum_d
- * (|u_d| + c) / dx_d over interior cells, from the state at the start of
- * the step. */
+/* READING (no CFL definition in the paper): dt = CFL / max_i [sum_d
+ * (|u_d| + c) / dx_d + 2 D sum_d 1 / dx_d^2] over interior cells, from the
+ * state at the start of the step, with the diffusivity
+ * D = max(4/3 mu, k_c / cv_min) / rho (cv_min: the smallest component cv)
+ * when viscous terms are on, else D = 0. */
 int or_dt(const or_params* P, const double* q, double cfl, double* dt)
 {
     const int nd = P->ndim;
     const size_t nc = ncells(P);
+    const int visc = has_visc(P);
+    if (visc && !all_kind(P, OR_SG)) return OR_ERR_ARG;
+    double cvmin = P->comp[0].cv, idx2 = 0.0;
+    for (int k = 1; k < P->ncomp; ++k) cvmin = fmin(cvmin, P->comp[k].cv);
+    for (int d = 0; d < nd; ++d) idx2 += 1.0 / (P->dx[d] * P->dx[d]);
     double smax = 0.0;
     for (size_t c = 0; c < nc; ++c) {
-        double qc[OR_MAXV], w[OR_MAXV], r, cs;
+        double qc[OR_MAXV], w[OR_MAXV], r, cs, al[OR_MAXC];
         gather_q(P, q, c, qc);
-        int st = cell_prim(P, qc, w, &r, &cs, NULL);
+        int st = cell_prim(P, qc, w, &r, &cs, al);
         if (st) return st;
         double s = 0.0;
         for (int d = 0; d < nd; ++d) s += (fabs(w[d]) + cs) / P->dx[d];
+        if (visc) {
+            double mu, kc;
+            mix_transport(P, al, &mu, &kc);
+            s += 2.0 * fmax(4.0 / 3.0 * mu, kc / cvmin) / r * idx2;
+        }
         if (s > smax) smax = s;
     }
     *dt = cfl / smax;
@@ -1046,4 +1151,18 @@ int or_sensor(const or_params* P, const double* q, double* f)
     }
     box_free(&B);
     return st;
+}
+
+int or_transport(const or_params* P, const double* q, double* out)
+{
+    const size_t nc = ncells(P);
+    if (!all_kind(P, OR_SG)) return OR_ERR_ARG;
+    for (size_t c = 0; c < nc; ++c) {
+        double qc[OR_MAXV], w[OR_MAXV], al[OR_MAXC];
+        gather_q(P, q, c, qc);
+        int st = cell_prim(P, qc, w, NULL, NULL, al);
+        if (st) return st;
+        mix_transport(P, al, &out[c], &out[nc + c]);
+    }
+    return OR_OK;
 }

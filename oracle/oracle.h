@@ -11,9 +11,10 @@
  * boundary update, primitive/thermodynamic update (App. A, App. B),
  * sensor (App. D, Eq. D.4), reconstruction (Sec. 3.3, Eq. 3-3/3-4,
  * Table 4.2; App. D Eq. D.1-D.3), thermodynamic-dependent update
- * (Eq. 3-5/3-6), all-Mach Riemann flux (Eq. 3-1/3-2; D.5/D.6), CSF source
- * (Sec. 2.3, Sec. 3.5, Eq. 3-9/3-10), flux divergence and the low-storage
- * Runge-Kutta update (Sec. 3.1).
+ * (Eq. 3-5/3-6), all-Mach Riemann flux (Eq. 3-1/3-2; D.5/D.6), viscous
+ * stress and heat conduction fluxes (Eq. 2-2, mixture viscosity Eq. 2-8),
+ * CSF and gravity sources (Sec. 2.3, Sec. 3.5, Eq. 3-9/3-10; Eq. 2-2 Q),
+ * flux divergence and the low-storage Runge-Kutta update (Sec. 3.1).
  *
  * Layouts: conserved state q and primitive state W are SoA float64 arrays
  * [nv][nz][ny][nx], x fastest, interior cells only.
@@ -41,6 +42,7 @@ typedef struct {
     int kind;                         /* OR_SG (ideal gas when pinf = 0) or OR_PR */
     double gamma, pinf, cv, q;        /* Eq. A.1.1 */
     double Tc, pc, omega, M;          /* Eq. A.2.1 (M in kg/mol) */
+    double mu, kc;                    /* viscosity (Pa s), conductivity (W/(m K)); Eq. 2-2, 2-8 */
 } or_comp;
 
 typedef struct {
@@ -63,6 +65,7 @@ typedef struct {
     double in_Y[OR_MAXC];             /* tracked mass fractions of the inflow */
     const double* in_u;               /* [3][nz][ny] inflow velocity, or NULL */
     double in_u0[3];                  /* uniform inflow velocity used when in_u is NULL */
+    double grav[3];                   /* body force per unit mass g (m/s^2), Eq. 2-2 Q */
 } or_params;
 
 /* closure, pointwise (Yt = the N-1 tracked mass fractions) */
@@ -97,6 +100,8 @@ void or_totals(const or_params* P, const double* q, double* out /* nv */);
 int or_csf_source(const or_params* P, const double* q, double* S);
 /* App. D cell sensor f (0/1) on the interior */
 int or_sensor(const or_params* P, const double* q, double* f);
+/* cell mixture viscosity and conductivity on the interior (out[2][cells]) */
+int or_transport(const or_params* P, const double* q, double* out);
 
 #ifdef __cplusplus
 }

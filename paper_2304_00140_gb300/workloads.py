@@ -69,14 +69,16 @@ class SplitMix64:
 # --------------------------------------------------------------------------
 # materials (parameters of Eq. A.1.1 / A.2.1)
 # --------------------------------------------------------------------------
-def comp_sg(gamma, pinf, cv, q=0.0, M=0.0):
+def comp_sg(gamma, pinf, cv, q=0.0, M=0.0, mu=0.0, kc=0.0):
+    """stiffened gas (ideal gas when pinf = 0); mu, kc: dynamic viscosity
+    (Pa s) and thermal conductivity (W/(m K)) of Eq. 2-2, 0 = inviscid"""
     return dict(kind=KIND_SG, gamma=float(gamma), pinf=float(pinf), cv=float(cv), q=float(q),
-                Tc=0.0, pc=0.0, omega=0.0, M=float(M))
+                Tc=0.0, pc=0.0, omega=0.0, M=float(M), mu=float(mu), kc=float(kc))
 
 
 def comp_pr(Tc, pc, omega, cv, M):
     return dict(kind=KIND_PR, gamma=0.0, pinf=0.0, cv=float(cv), q=0.0,
-                Tc=float(Tc), pc=float(pc), omega=float(omega), M=float(M))
+                Tc=float(Tc), pc=float(pc), omega=float(omega), M=float(M), mu=0.0, kc=0.0)
 
 
 WATER = comp_sg(6.12, 3.43e8, 1816.0)
@@ -92,9 +94,22 @@ def default_scheme(**kw) -> Dict:
     s = dict(iles=0, thinc=1, beta=1.6, thinc_eps=1e-4, thinc_gamma=1e-20,
              lim_vel=LIM_KOREN, lim_scalar=LIM_MINMOD,
              thr_ducros=0.95, thr_gas=0.4, eps_ducros=1e-20, d3p_coef=1.0,
-             sigma=0.0, grad_eps=1e-5, precision=0, p_ref=1e5, T_ref=300.0)
+             sigma=0.0, grad_eps=1e-5, precision=0, p_ref=1e5, T_ref=300.0,
+             gravity=(0.0, 0.0, 0.0))
     s.update(kw)
     return s
+
+
+def with_transport(w: "Workload", mu, kc=None, gravity=None) -> "Workload":
+    """Copy of a workload with per-component viscosities ``mu`` and
+    conductivities ``kc`` (Eq. 2-2; lists in component order) and, if given,
+    the body force per unit mass ``gravity`` (3 components, m/s^2)."""
+    kc = kc if kc is not None else [0.0] * len(w.comps)
+    comps = [dict(c, mu=float(m), kc=float(k)) for c, m, k in zip(w.comps, mu, kc)]
+    scheme = dict(w.scheme)
+    if gravity is not None:
+        scheme["gravity"] = tuple(float(g) for g in gravity)
+    return dataclasses.replace(w, comps=comps, scheme=scheme)
 
 
 @dataclasses.dataclass
@@ -313,7 +328,26 @@ def _init_pr_drop(w: Workload):
     return W
 
 
-_INIT = {"pr_drop": _init_pr_drop, "column": _init_column, "shock_bubble": _init_shock_bubble,
+def _init_bubble(w: Workload):
+    """Rising bubble: a gas bubble of radius R at (xb, yb) in liquid at rest,
+    hydrostatic pressure p_top + rho_l |g| (H - y) in the liquid, the liquid
+    pressure at the bubble centre plus the Laplace jump sigma / R inside,
+    uniform T; the gas fraction tanh-smoothed."""
+    P = w.params
+    X, Y, _ = _grid(w)
+    r = np.sqrt((X - P["xb"]) ** 2 + (Y - P["yb"]) ** 2)
+    gas = tanh_indicator(r - P["R"], P["width"] * w.dx[0])
+    g = abs(w.scheme["gravity"][1])
+    p_liq = P["p"] + P["rho_l"] * g * (w.hi[1] - Y)
+    p_in = P["p"] + P["rho_l"] * g * (w.hi[1] - P["yb"]) + w.scheme["sigma"] / P["R"]
+    W = _alloc(w)
+    W[w.ndim] = gas * p_in + (1.0 - gas) * p_liq
+    W[w.ndim + 1] = P["T"]
+    W[w.ndim + 2] = gas               # gas tracked, liquid implied
+    return W
+
+
+_INIT = {"bubble": _init_bubble, "pr_drop": _init_pr_drop, "column": _init_column, "shock_bubble": _init_shock_bubble,
          "droplet": _init_droplet, "random": _init_random, "jet": _init_jet}
 
 
@@ -454,3 +488,30 @@ def pr_shock_droplet(n=1024, steps=2000, **scheme):
         bc=[[BC_OUTFLOW] * 2, [BC_OUTFLOW] * 2, [BC_PERIODIC] * 2], comps=[N2_PR, DODECANE_PR], liquid=1,
         scheme=sch, steps=steps, cfl=0.4, init="pr_drop",
         params=dict(p=6e6, T=900.0, T_l=363.0, Ms=2.0, xs=0.25 * L, R=n / 8 * dx, width=1.5))
+
+
+# Table 4.4: liquid / gas densities, viscosities, gravity and surface tension
+RISING_BUBBLE_CASES = {1: dict(rho_l=1000.0, rho_g=100.0, mu_l=10.0, mu_g=1.0, g=0.98, sigma=24.5),
+                       2: dict(rho_l=1000.0, rho_g=1.0, mu_l=10.0, mu_g=0.1, g=0.98, sigma=1.96)}
+
+
+def rising_bubble(case=1, n=None, steps=1000, **scheme):
+    """Rising bubble (Sec. 4.3, Table 4.4): a 1 x 2 m box of n cells
+    (100 x 200 for case 1, 160 x 320 for case 2), a gas bubble of radius
+    0.25 m at (0.5, 0.5) m in liquid, gravity 0.98 m/s^2 along -y, walls on
+    every side, CSF and viscous stresses on.  The paper closes both fluids
+    with its barotropic relations; here the liquid is a stiffened gas
+    (gamma 6.12, pinf 3.43e8 Pa) and the gas an ideal gas (gamma 1.4), their
+    cv chosen so that the densities of Table 4.4 hold at 1e5 Pa and 300 K.
+    No heat conduction."""
+    c = RISING_BUBBLE_CASES[case]
+    nx, ny = n if n is not None else ((100, 200) if case == 1 else (160, 320))
+    p0, T0 = 1e5, 300.0
+    liquid = comp_sg(6.12, 3.43e8, (p0 + 3.43e8) / (5.12 * c["rho_l"] * T0), mu=c["mu_l"])
+    gas = comp_sg(1.4, 0.0, p0 / (0.4 * c["rho_g"] * T0), mu=c["mu_g"])
+    sch = default_scheme(**dict(dict(sigma=c["sigma"], gravity=(0.0, -c["g"], 0.0)), **scheme))
+    return Workload(
+        name=f"rising_bubble{case}_{nx}x{ny}", ndim=2, n=[nx, ny, 1], lo=[0.0, 0.0, 0.0], hi=[1.0, 1.0 * ny / nx, 1.0],
+        bc=[[BC_REFLECT] * 2, [BC_REFLECT] * 2, [BC_PERIODIC] * 2], comps=[gas, liquid], liquid=1,
+        scheme=sch, steps=steps, cfl=0.4, init="bubble",
+        params=dict(p=p0, T=T0, rho_l=c["rho_l"], xb=0.5, yb=0.5, R=0.25, width=1.5))
