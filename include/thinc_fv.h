@@ -9,9 +9,11 @@
  * reconstruction switching between limited MUSCL (Sec. 3.3, Table 4.2),
  * THINC (Eq. 3-3/3-4) and 4th-order central (Eq. D.1-D.3), the
  * thermodynamic-dependent update of rho and e (Eq. 3-5/3-6), the all-Mach
- * Riemann flux (Eq. 3-1/3-2; Eq. D.5/D.6), the CSF surface-tension source
- * with Gaussian-smoothed curvature (Sec. 3.5, Eq. 3-9/3-10) and the
- * flux-divergence / LSRK register update.  All arithmetic runs in CUDA
+ * Riemann flux (Eq. 3-1/3-2; Eq. D.5/D.6), the viscous stress and heat
+ * conduction fluxes (Eq. 2-2, mixture viscosity Eq. 2-8), the CSF
+ * surface-tension source with Gaussian-smoothed curvature (Sec. 3.5,
+ * Eq. 3-9/3-10), the gravity source (Eq. 2-2) and the flux-divergence /
+ * LSRK register update.  All arithmetic runs in CUDA
  * kernels for sm_103a; there is no CPU path.
  *
  * Conventions
@@ -89,11 +91,16 @@ typedef struct {
 
 /* One material.  FV_SG: stiffened gas p = (gamma-1) rho (e-q) - gamma pinf
  * (Eq. A.1.1; ideal gas when pinf = 0).  FV_PR: Peng-Robinson (Eq. A.2.1)
- * with constant ideal-gas cv; M is the molar mass in kg/mol. */
+ * with constant ideal-gas cv; M is the molar mass in kg/mol.  mu (Pa s) and
+ * kc (W/(m K)) are the dynamic viscosity and thermal conductivity of the
+ * stress and heat-flux terms of Eq. 2-2, mixed by volume fraction (Eq. 2-8,
+ * no vapour); 0 for every component = inviscid.  Viscous terms need
+ * stiffened-gas / ideal-gas components (FV_ERR_ARG otherwise). */
 typedef struct {
     int kind;
     double gamma, pinf, cv, q;
     double Tc, pc, omega, M;
+    double mu, kc;
 } fv_component;
 
 typedef struct {
@@ -113,6 +120,8 @@ typedef struct {
     double grad_eps;             /* |grad alpha~| * dx below this gives a zero normal */
     int precision;               /* FV_FP64 or FV_MIXED */
     double p_ref, T_ref;         /* offsets carried by the FP32 arithmetic of FV_MIXED */
+    double gravity[3];           /* body force per unit mass (m/s^2) of Eq. 2-2: source rho g
+                                    (momentum) and rho u . g (energy); zero = off */
 } fv_eos;
 
 typedef struct fv_ctx fv_ctx;

@@ -196,7 +196,31 @@ static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm,
     if (eos->precision != FV_FP64 && eos->precision != FV_MIXED) { why = "bad precision"; return FV_ERR_ARG; }
     if (eos->thinc && !(eos->beta > 0.0)) { why = "THINC beta must be positive"; return FV_ERR_ARG; }
     if (!(eos->sigma >= 0.0)) { why = "sigma must be >= 0"; return FV_ERR_ARG; }
+    bool visc = false;
+    for (int k = 0; k < cm->ncomp; ++k) {
+        const fv_component& c = cm->comp[k];
+        if (!(c.mu >= 0.0) || !(c.kc >= 0.0) || !std::isfinite(c.mu) || !std::isfinite(c.kc)) {
+            why = "viscosity and conductivity must be finite and >= 0";
+            return FV_ERR_ARG;
+        }
+        visc = visc || c.mu > 0.0 || c.kc > 0.0;
+    }
+    if (visc && npr > 0) { why = "viscous terms need stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
+    for (int d = 0; d < 3; ++d)
+        if (!std::isfinite(eos->gravity[d])) { why = "gravity must be finite"; return FV_ERR_ARG; }
     return FV_OK;
+}
+
+static bool has_visc(const fv_components* cm)
+{
+    for (int k = 0; k < cm->ncomp; ++k)
+        if (cm->comp[k].mu > 0.0 || cm->comp[k].kc > 0.0) return true;
+    return false;
+}
+
+static bool has_grav(const fv_eos* eos)
+{
+    return eos->gravity[0] != 0.0 || eos->gravity[1] != 0.0 || eos->gravity[2] != 0.0;
 }
 
 static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
@@ -212,12 +236,15 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
     P.lim_vel = eos->lim_vel;
     P.lim_scalar = eos->lim_scalar;
     P.csf = eos->sigma > 0.0 ? 1 : 0;
-    P.aux_rc = P.iles;
+    P.visc = has_visc(cm) ? 1 : 0;
+    P.grav = has_grav(eos) ? 1 : 0;
+    P.aux_rc = (P.iles || P.grav) ? 1 : 0;
     P.aux_al = (P.csf || P.iles) ? 1 : 0;
     int np = x->nv;
-    P.i_rho = P.i_c = P.i_al = -1;
+    P.i_rho = P.i_c = P.i_al = P.i_mu = P.i_kc = -1;
     if (P.aux_rc) { P.i_rho = np++; P.i_c = np++; }
     if (P.aux_al) P.i_al = np++;
+    if (P.visc) { P.i_mu = np++; P.i_kc = np++; }
     P.nprim = np;
     x->nprim = np;
     P.beta = eos->beta;
@@ -324,6 +351,15 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
         Kt.d3p_coef = T(P.d3p_coef);
         Kt.sigma = T(P.sigma);
         Kt.grad_eps = T(P.grad_eps);
+        double cvmin = cm->comp[0].cv;
+        for (int k = 0; k < MAXC; ++k) {
+            const bool on = k < cm->ncomp;
+            Kt.mu[k] = T(on ? cm->comp[k].mu : 0.0);
+            Kt.kc[k] = T(on ? cm->comp[k].kc : 0.0);
+            if (on) cvmin = std::min(cvmin, cm->comp[k].cv);
+        }
+        Kt.icvmin = T(1.0 / cvmin);
+        for (int d = 0; d < 3; ++d) Kt.grav[d] = T(eos->gravity[d]);
     };
     fill(P.kd);
     fill(P.kf);
@@ -418,11 +454,12 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
     L.total = o;
 }
 
-static int count_nprim(const fv_eos* eos, int nv)
+static int count_nprim(const fv_components* cm, const fv_eos* eos, int nv)
 {
     int np = nv;
-    if (eos->iles) np += 2;
+    if (eos->iles || has_grav(eos)) np += 2;
     if (eos->iles || eos->sigma > 0.0) np += 1;
+    if (has_visc(cm)) np += 2;
     return np;
 }
 
@@ -434,7 +471,7 @@ extern "C" fv_status fv_workspace_size(int ncases, const fv_grid* grids, const f
     if (s) return s;
     const int nd = grids[0].ndim, nv = nd + comps->ncomp + 1;
     Layout L;
-    plan(ncases, grids, nd, nv, count_nprim(eos, nv), eos->precision == FV_MIXED, L, nullptr, nullptr, nullptr);
+    plan(ncases, grids, nd, nv, count_nprim(comps, eos, nv), eos->precision == FV_MIXED, L, nullptr, nullptr, nullptr);
     if (bytes) *bytes = L.total;
     return FV_OK;
 }
@@ -504,7 +541,7 @@ static bool encode_maps(fv_ctx* x, const cuuint32_t* box, int xalign, unsigned c
 // keeps its cp.async loads
 static fv_status encode_tmaps(fv_ctx* x, int variant)
 {
-    const TileDef td = tile_def(x->nd, variant_tile(variant));
+    const TileDef td = tile_def(x->nd, variant_tile(x->nd, variant));
     const cuuint32_t box[4] = {cuuint32_t(td.x + 4), cuuint32_t(td.y + 4), cuuint32_t(x->nd == 3 ? td.z + 4 : 1),
                                cuuint32_t(x->nprim)};
     x->tma = encode_maps(x, box, td.x, x->d_tmaps);
@@ -545,7 +582,7 @@ static fv_status apply_zmarch(fv_ctx* x, int chunk, int var)
 // work list of the stage kernel for one candidate tile
 static void stage_items(const std::vector<CaseDesc>& cases, int nd, int tile, std::vector<int4>& out)
 {
-    const TileDef td = tile_def(nd, variant_tile(tile));
+    const TileDef td = tile_def(nd, variant_tile(nd, tile));
     out.clear();
     for (size_t c = 0; c < cases.size(); ++c) {
         const CaseDesc& C = cases[c];
@@ -560,6 +597,7 @@ static void stage_items(const std::vector<CaseDesc>& cases, int nd, int tile, st
 // and any other limiter pair run on tile 0.
 static int kernel_variant(const DevParams& P, int tile)
 {
+    if (P.visc || P.grav) return NTILES + 3;
     const bool t42 = P.lim_vel == FV_KOREN && P.lim_scalar == FV_MINMOD;
     if (t42 && !P.pr) return tile < NTILES ? tile : 0;
     if (t42) return NTILES;
@@ -851,8 +889,8 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
-    x->fused_ok = x->nd == 2 && !x->P.pr;
-    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr;
+    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.visc && !x->P.grav;
+    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.visc && !x->P.grav;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }
@@ -1238,7 +1276,7 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
     if (what == FV_DIAG_TILE) {
         s = tune(x);
         if (s) return s;
-        const TileDef td = tile_def(x->nd, variant_tile(x->tile));
+        const TileDef td = tile_def(x->nd, variant_tile(x->nd, x->tile));
         double* o = static_cast<double*>(out);
         if (x->fused) {
             o[0] = MARCH_COLS; o[1] = x->chunk; o[2] = 1; o[3] = 32 * MARCH_WARPS;
@@ -1364,7 +1402,7 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
 
 __global__ void noalloc_setup_kernel(CaseDesc C, CaseDesc* dcase, double* dt, double dtv, int* err, int4* ist,
-                                     int n_st, int4* ipr, int n_pr, int tx, int ty, int tz)
+                                     int n_st, int4* ipr, int n_pr, int tx, int ty, int tz, TileDef st)
 {
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (i0 == 0) {
@@ -1373,9 +1411,10 @@ __global__ void noalloc_setup_kernel(CaseDesc C, CaseDesc* dcase, double* dt, do
         *err = 0;
     }
     // tile origins in the same x-fastest order as the context work lists
-    const int sx = (C.n[0] + tx - 1) / tx, sy = (C.n[1] + ty - 1) / ty;
+    // (stage tile st, primitive-pass tile tx x ty x tz)
+    const int sx = (C.n[0] + st.x - 1) / st.x, sy = (C.n[1] + st.y - 1) / st.y;
     for (int i = i0; i < n_st; i += gridDim.x * blockDim.x)
-        ist[i] = make_int4(0, (i % sx) * tx, ((i / sx) % sy) * ty, (i / (sx * sy)) * tz);
+        ist[i] = make_int4(0, (i % sx) * st.x, ((i / sx) % sy) * st.y, (i / (sx * sy)) * st.z);
     const int px = (C.g[0] + tx - 1) / tx, py = (C.g[1] + ty - 1) / ty;
     for (int i = i0; i < n_pr; i += gridDim.x * blockDim.x)
         ipr[i] = make_int4(0, (i % px) * tx, ((i / px) % py) * ty, (i / (px * py)) * tz);
@@ -1403,6 +1442,7 @@ bool noalloc_args_ok(const fv_grid* g, const fv_components* cm, const fv_eos* e)
     for (int k = 0; k < cm->ncomp; ++k) {
         const fv_component& c = cm->comp[k];
         if (c.kind != FV_SG || !(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) return false;
+        if (!(c.mu >= 0.0) || !(c.kc >= 0.0) || !std::isfinite(c.mu) || !std::isfinite(c.kc)) return false;
         if (pa < 0.0 || c.pinf == pa) pa = c.pinf;
         else if (pb < 0.0 || c.pinf == pb) pb = c.pinf;
         else return false;
@@ -1463,7 +1503,11 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
     x.P.ntot_q = ncell;
     x.P.ntot_p = nghost;
     const int tx = tile_x(x.nd), ty = tile_y(x.nd), tz = tile_z(x.nd);
-    const long long n_st = ntiles(C.n, x.nd), n_pr = ntiles(C.g, x.nd);
+    const int var = kernel_variant(x.P, 0);
+    const TileDef stile = tile_def(x.nd, variant_tile(x.nd, var));
+    const long long n_pr = ntiles(C.g, x.nd);
+    const long long n_st = (long long)((C.n[0] + stile.x - 1) / stile.x) * ((C.n[1] + stile.y - 1) / stile.y) *
+                           ((C.n[2] + stile.z - 1) / stile.z);
     // scratch layout
     const size_t o_case = 0, o_dt = align256(sizeof(CaseDesc)), o_err = o_dt + 256, o_ist = o_err + 256;
     const size_t o_ipr = o_ist + align256(sizeof(int4) * n_st);
@@ -1481,7 +1525,6 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
 
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FV_ERR_CUDA;
-    const int var = kernel_variant(x.P, 0);
     const size_t smem = stage_smem(x.nd, x.nc, x.mixed, var, x.nprim);
     if (stage_set_smem(x.nd, x.nc, x.mixed, var, smem) != cudaSuccess) return FV_ERR_CUDA;
     const int gs = (int)std::min<long long>(n_st, (long long)nsm * stage_occupancy(x.nd, x.nc, x.mixed, var, smem));
@@ -1489,7 +1532,7 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
     const int nsetup = (int)std::min<long long>(1024, (std::max(n_st, n_pr) + 255) / 256);
 
     noalloc_setup_kernel<<<std::max(1, nsetup), 256, 0, s>>>(C, dcase, ddt, dt, derr, ist, (int)n_st, ipr,
-                                                            (int)n_pr, tx, ty, tz);
+                                                            (int)n_pr, tx, ty, tz, stile);
     if (cudaGetLastError() != cudaSuccess) return FV_ERR_CUDA;
     PrimArgs pa{x.P, dcase, ipr, (int)n_pr, qprev, prim, nullptr, nullptr, derr};
     if (launch_prim(x.nd, x.nc, x.mixed, pa, gp, s) != cudaSuccess) return FV_ERR_CUDA;

@@ -44,6 +44,9 @@ struct ConstT {
     R gm1_lo[MAXC], gpi_hi[MAXC], gpi_lo[MAXC];   // gamma-1 (lo part) and gamma pinf + p_ref as float-float
     R gm1_hi[MAXC];
     R Po[MAXC];          // pinf of the other pressure class + p_ref
+    R mu[MAXC], kc[MAXC];   // viscosity and conductivity per component (Eq. 2-2)
+    R grav[3];              // body force per unit mass (Eq. 2-2 Q)
+    R icvmin;               // 1 / smallest component cv (diffusive step limit)
 };
 
 struct CompDev {
@@ -70,6 +73,8 @@ struct DevParams {
     int ndim, ncomp, nv, nprim, liquid;
     int iles, thinc, lim_vel, lim_scalar;
     int csf, aux_rc, aux_al, i_rho, i_c, i_al;
+    int visc, grav;      // viscous / heat-flux terms on; gravity source on
+    int i_mu, i_kc;      // primitive-array fields of the mixture viscosity and conductivity
     double beta, thinc_eps, thinc_gamma, tb, icb, itb;
     double thr_ducros, thr_gas, eps_ducros, d3p_coef;
     double sigma, grad_eps;

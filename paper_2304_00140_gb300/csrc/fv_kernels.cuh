@@ -67,9 +67,12 @@ constexpr TileDef tile_def(int nd, int i) { return nd == 2 ? TILES2[i] : TILES3[
 // Kernel variants of the stage kernel: 0 .. NTILES-1 stiffened/ideal-gas
 // closure with the Table 4.2 limiter pair on tile i; NTILES Peng-Robinson with
 // that pair on tile 0; NTILES+1 / NTILES+2 stiffened-gas / Peng-Robinson with
-// any limiter pair (read at run time) on tile 0.
-constexpr int NVARIANTS = NTILES + 3;
-constexpr int variant_tile(int v) { return v < NTILES ? v : 0; }
+// any limiter pair (read at run time) on tile 0; NTILES+3 stiffened-gas with
+// any limiter pair plus the viscous, heat-flux and gravity terms, tile 0.
+constexpr int NVARIANTS = NTILES + 4;
+// tile of variant v: the viscous 3D variant (twelve primitive fields with the
+// App. D and CSF fields) takes the 16x4x4 tile, whose halo fits in shared memory
+constexpr int variant_tile(int nd, int v) { return v < NTILES ? v : (v == NTILES + 3 && nd == 3 ? 1 : 0); }
 
 __device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& flip, int& inflow)
 {
@@ -251,6 +254,25 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 if (!in_disc) rr = rho;
             }
             if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
+            R mu_c = R(0), kc_c = R(0);
+            if (!PRC && P.visc) {
+                // Eq. 2-8 with no vapour: mixture viscosity = sum_k alpha_k mu_k with
+                // alpha_k = rho Y_k / rho_k (Eq. A.1.4); the conductivity mixed alike
+                R s = R(0);
+#pragma unroll
+                for (int k = 0; k < NC - 1; ++k) s += clip01(w[ND + 2 + k]);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    const R Yk = (k == NC - 1) ? clip01(R(1) - s) : clip01(w[ND + 2 + k]);
+                    const R a = fdiv(rr * Yk * K<R>(P).gm1cv[k] * w[ND + 1], K<R>(P).Pk[k] + w[ND]);
+                    mu_c += a * K<R>(P).mu[k];
+                    kc_c += a * K<R>(P).kc[k];
+                }
+                if (pp0) {
+                    pp0[P.i_mu * P.ntot_p] = mu_c;
+                    pp0[P.i_kc * P.ntot_p] = kc_c;
+                }
+            }
             if (pp0) {
                 R* o = pp0;
 #pragma unroll
@@ -281,6 +303,13 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 R s = R(0);
 #pragma unroll
                 for (int d = 0; d < ND; ++d) s += (fabs(w[d]) + cs) * pick<R>(C.idx[d], C.fidx[d]);
+                if (!PRC && P.visc) {
+                    // diffusive limit: 2 D sum_d 1/dx_d^2, D = max(4/3 mu, k_c / cv_min) / rho
+                    R i2 = R(0);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) i2 += pick<R>(C.idx[d], C.fidx[d]) * pick<R>(C.idx[d], C.fidx[d]);
+                    s += R(2) * fdiv(fmax(R(4.0 / 3.0) * mu_c, kc_c * K<R>(P).icvmin), rr) * i2;
+                }
                 speed = s;
             }
         }
@@ -301,8 +330,46 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
     }
 }
 
+// Eq. 2-2 stress and heat-flux terms, added to the flux F of the face between
+// halo cells hl and hl + e_D (st: halo strides): momentum -tau_{D a} with
+// tau = mu (grad u + grad u^T - 2/3 (div u) I), energy -(u . tau)_D - k_c dT/dx_D.
+// A derivative along D is the two cells' difference; along another direction
+// the mean of the two cells' central differences; u, mu and k_c at the face
+// are the two cells' means.
+template <int ND, int D, typename R>
+__device__ __forceinline__ void visc_face(const DevParams& P, const R* sp, int HC, int hl, const int* st,
+                                          const R* ci, R* F)
+{
+    const int hr = hl + st[D];
+    R g[ND][ND];   // g[a][b] = d u_a / d x_b at the face
+#pragma unroll
+    for (int b = 0; b < ND; ++b)
+#pragma unroll
+        for (int a = 0; a < ND; ++a) {
+            const R* u = sp + a * HC;
+            if (b == D) g[a][b] = (u[hr] - u[hl]) * ci[D];
+            else g[a][b] = ((u[hl + st[b]] - u[hl - st[b]]) + (u[hr + st[b]] - u[hr - st[b]])) * (R(0.25) * ci[b]);
+        }
+    R div = R(0);
+#pragma unroll
+    for (int a = 0; a < ND; ++a) div += g[a][a];
+    const R mu = R(0.5) * (sp[P.i_mu * HC + hl] + sp[P.i_mu * HC + hr]);
+    const R kc = R(0.5) * (sp[P.i_kc * HC + hl] + sp[P.i_kc * HC + hr]);
+    R utau = R(0);
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+        R tau = mu * (g[a][D] + g[D][a]);
+        if (a == D) tau -= R(2.0 / 3.0) * mu * div;
+        F[1 + a] -= tau;
+        utau += R(0.5) * (sp[a * HC + hl] + sp[a * HC + hr]) * tau;
+    }
+    const R* T = sp + (ND + 1) * HC;
+    F[1 + ND] -= utau + kc * ((T[hr] - T[hl]) * ci[D]);
+}
+
 // ------------------------------------------------------------------ stage
-template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, int MB, int NB, bool PRC, int LIM, typename Q>
+template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, int MB, int NB, bool PRC, int LIM, bool VISC,
+          typename Q>
 __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 {
     const Q* const q0reg = static_cast<const Q*>(A.q0);
@@ -551,6 +618,12 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
             R F[NV];
             const bool ok = face_flux<ND, NC, R, PRC, LIM>(P, d, ws, r4, c4, fl, F);
             if (!ok) set_err(A.err, ERR_NONPHYS);
+            if (VISC && P.visc) {
+                const int sts[3] = {SX, SY, SZ};
+                if (d == 0) visc_face<ND, 0>(P, sp, HC, h0 + st, sts, ci, F);
+                else if (d == 1) visc_face<ND, 1>(P, sp, HC, h0 + st, sts, ci, F);
+                else visc_face<ND, ND - 1>(P, sp, HC, h0 + st, sts, ci, F);   // d == 2 (3D only)
+            }
             // store at face index fi (= (fx, fy, fz)) of the full tile face array
             const int nfd = d == 0 ? NFX : (d == 1 ? NFY : NFZ);
             R* const dst = d == 0 ? sfx : (d == 1 ? sfy : sfz);
@@ -633,6 +706,18 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
                         udg += sp[d * HC + hc] * ga[d];
                     }
                     S[1 + ND] = Kc.sigma * kappa * udg;
+                }
+                if (VISC && P.grav) {
+                    // Eq. 2-2 Q: rho g (momentum), rho u . g (energy)
+                    const int hc = (cx + 2) * SX + (cy + 2) * SY + (ND == 3 ? (cz + 2) * SZ : 0);
+                    const R rho = sp[P.i_rho * HC + hc];
+                    R ug = R(0);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        S[1 + d] += rho * Kc.grav[d];
+                        ug += sp[d * HC + hc] * Kc.grav[d];
+                    }
+                    S[1 + ND] += rho * ug;
                 }
                 const double adt = A.a * A.dt[wi.x];
                 const float adtf = float(adt);

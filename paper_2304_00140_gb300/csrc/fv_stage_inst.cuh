@@ -13,9 +13,10 @@ namespace tfv {
 
 namespace {
 // kernel variant I (see NVARIANTS): tile, closure and limiter pair
-template <int I> constexpr int tile_of() { return variant_tile(I); }
+template <int I> constexpr int tile_of() { return variant_tile(FV_ND, I); }
 template <int I> constexpr bool pr_of() { return I == NTILES || I == NTILES + 2; }
 template <int I> constexpr int lim_of() { return I <= NTILES ? LIM_TABLE42 : LIM_RUNTIME; }
+template <int I> constexpr bool visc_of() { return I == NTILES + 3; }
 template <int FF> struct RegOf { using type = double; };
 template <> struct RegOf<1> { using type = float2; };
 
@@ -23,7 +24,7 @@ template <> struct RegOf<1> { using type = float2; };
     stage_kernel<FV_ND, NC, FV_REAL, tile_def(FV_ND, tile_of<I>()).x, tile_def(FV_ND, tile_of<I>()).y, \
                  tile_def(FV_ND, tile_of<I>()).z, tile_def(FV_ND, tile_of<I>()).nt,                    \
                  tile_def(FV_ND, tile_of<I>()).mb, tile_def(FV_ND, tile_of<I>()).nb, pr_of<I>(),       \
-                 lim_of<I>(), typename RegOf<FF>::type>
+                 lim_of<I>(), visc_of<I>(), typename RegOf<FF>::type>
 
 template <int NC, int I, int FF>
 cudaError_t go(const StageArgs& A, int grid, size_t smem, cudaStream_t s)
@@ -54,7 +55,7 @@ size_t bytes(int nprim)
 }  // namespace
 
 // FP64 form: double registers on every variant (FF = 0).  Mixed form: float2
-// registers on every variant (ff = 1) or double registers on the two
+// registers on every variant (ff = 1) or double registers on the three
 // stiffened-gas tile-0 variants (ff = 0, the no-alloc entry point).
 #define FV_NC(fn, I, FF, ...) (nc == 2 ? fn<2, I, FF>(__VA_ARGS__) : fn<3, I, FF>(__VA_ARGS__))
 #if FV_IS_FLOAT
@@ -63,10 +64,11 @@ size_t bytes(int nprim)
 #define FV_FF 0
 #endif
 #define FV_TILE_SWITCH(fn, ...)                                                   \
-    static_assert(NTILES == 4, "variant switch below lists four tiles");          \
+    static_assert(NTILES == 4 && NVARIANTS == 8, "variant switch below lists eight variants");          \
     if (FV_IS_FLOAT && !ff)                                                       \
-        return tile == NTILES + 1 ? FV_NC(fn, NTILES + 1, 0, __VA_ARGS__)          \
-                                  : FV_NC(fn, 0, 0, __VA_ARGS__);                  \
+        return tile == NTILES + 1   ? FV_NC(fn, NTILES + 1, 0, __VA_ARGS__)        \
+               : tile == NTILES + 3 ? FV_NC(fn, NTILES + 3, 0, __VA_ARGS__)        \
+                                    : FV_NC(fn, 0, 0, __VA_ARGS__);                \
     switch (tile) {                                                               \
     case 0: return FV_NC(fn, 0, FV_FF, __VA_ARGS__);                              \
     case 1: return FV_NC(fn, 1, FV_FF, __VA_ARGS__);                              \
@@ -74,7 +76,8 @@ size_t bytes(int nprim)
     case 3: return FV_NC(fn, 3, FV_FF, __VA_ARGS__);                              \
     case NTILES: return FV_NC(fn, NTILES, FV_FF, __VA_ARGS__);                    \
     case NTILES + 1: return FV_NC(fn, NTILES + 1, FV_FF, __VA_ARGS__);            \
-    default: return FV_NC(fn, NTILES + 2, FV_FF, __VA_ARGS__);                    \
+    case NTILES + 2: return FV_NC(fn, NTILES + 2, FV_FF, __VA_ARGS__);            \
+    default: return FV_NC(fn, NTILES + 3, FV_FF, __VA_ARGS__);                    \
     }
 
 cudaError_t FV_CAT(launch_stage_, FV_SUFFIX)(int nc, int tile, int ff, const StageArgs& A, int grid, size_t smem,

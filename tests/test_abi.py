@@ -68,3 +68,54 @@ def test_peng_robinson_argument_checks():
     cm2 = fv.make_components(w)
     cm2.comp[0] = fv.fv_component(0, 1.4, 0.0, 718.0, 0, 0, 0, 0, 0)   # SG mixed with PR
     assert L.fv_workspace_size(1, g, C.byref(cm2), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
+
+
+def test_viscous_and_gravity_argument_checks():
+    L = fv.load()
+    n = C.c_size_t()
+    w = wl.rising_bubble(1, n=(20, 40))
+    g = (fv.fv_grid * 1)(fv.make_grid(w))
+    cm, e = fv.make_components(w), fv.make_eos(w.scheme)
+    assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_OK
+    w0 = wl.with_transport(w, mu=[0.0, 0.0], gravity=(0.0, 0.0, 0.0))
+    n0 = C.c_size_t()
+    assert L.fv_workspace_size(1, g, C.byref(fv.make_components(w0)), C.byref(fv.make_eos(w0.scheme)),
+                               C.byref(n0)) == fv.FV_OK
+    assert n.value > n0.value          # rho, c (gravity) and mu, k_c (viscosity) primitive fields
+    bad = fv.make_components(w)
+    bad.comp[0].mu = -1.0
+    assert L.fv_workspace_size(1, g, C.byref(bad), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
+    bad = fv.make_components(w)
+    bad.comp[1].kc = float("nan")
+    assert L.fv_workspace_size(1, g, C.byref(bad), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
+    e2 = fv.make_eos(w.scheme)
+    e2.gravity[1] = float("inf")
+    assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e2), C.byref(n)) == fv.FV_ERR_ARG
+    # Peng-Robinson mixtures have no volume fractions for Eq. 2-8
+    wp = wl.pr_shock_droplet(n=32)
+    gp = (fv.fv_grid * 1)(fv.make_grid(wp))
+    cmp_ = fv.make_components(wl.with_transport(wp, mu=[1e-5, 1e-3]))
+    assert L.fv_workspace_size(1, gp, C.byref(cmp_), C.byref(fv.make_eos(wp.scheme)), C.byref(n)) == fv.FV_ERR_ARG
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """offsets and sizes of the ABI structs as the C compiler lays them out
+    from include/thinc_fv.h equal the ctypes mirrors of the binding"""
+    structs = {"fv_grid": fv.fv_grid, "fv_component": fv.fv_component, "fv_components": fv.fv_components,
+               "fv_eos": fv.fv_eos}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "thinc_fv.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).split("\n") if l)
+    for name, cls in structs.items():
+        assert int(out[name]) == C.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(out[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])

@@ -1,0 +1,147 @@
+"""GPU parity with the FP64 oracle for the viscous stress, heat conduction
+and gravity terms (Eq. 2-2; mixture viscosity Eq. 2-8), alone and together
+with the App. D switch, CSF, three components and every boundary kind; the
+rising-bubble workload (Sec. 4.3, Table 4.4) with the step size from the
+diffusive limit; the FP32-mixed form's accuracy on it.
+
+Tolerance as for the inviscid parity tests: 1e-11 relative per conserved
+field (momentum against the momentum vector's scale) after two steps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2304_00140_gb300 import fv, workloads as wl
+from tests.helpers import oracle_step_dt, rel_field_diff, rel_l1_vec
+
+pytestmark = pytest.mark.gpu
+
+MIXED_BC = [[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_PERIODIC] * 2]
+
+
+def _transport(w, mu=(2e-3, 5e-3, 1e-3), kc=(0.4, 0.6, 0.1), g=(0.3, -9.8, 0.2)):
+    n = w.ncomp
+    return wl.with_transport(w, mu=list(mu[:n]), kc=list(kc[:n]), gravity=g)
+
+
+def _run_pair(w, steps=2, dt_frac=0.3, precision=fv.FV_FP64):
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=precision)
+    s.set_state(q)
+    dt = dt_frac * o.dt(q, 1.0)
+    ref = q
+    for _ in range(steps):
+        s.step_dt(dt)
+        ref = oracle_step_dt(o, ref, dt)
+    assert not s.tile()["fused"] and not s.tile()["zmarch"]
+    return q, s.get_state(), ref
+
+
+def _rel(w, got, ref):
+    d = rel_field_diff(got, ref)
+    mag = np.sqrt((ref[1:1 + w.ndim] ** 2).sum(0)).max()
+    for a in range(w.ndim):
+        d[1 + a] = np.abs(got[1 + a] - ref[1 + a]).max() / mag
+    return d
+
+
+CASES = {
+    "2d_2comp": lambda: _transport(wl.random_state(n=(37, 23))),
+    "2d_ragged_small": lambda: _transport(wl.random_state(n=(5, 3), bc=MIXED_BC)),
+    "2d_3comp_iles_csf_bc": lambda: _transport(wl.random_state(n=(41, 30), ncomp=3, bc=MIXED_BC, iles=1,
+                                                               sigma=5.0)),
+    "2d_other_limiters": lambda: _transport(wl.random_state(n=(33, 18), lim_vel=wl.LIM_VANLEER,
+                                                            lim_scalar=wl.LIM_MC)),
+    "2d_gravity_only": lambda: _transport(wl.random_state(n=(30, 21)), mu=(0, 0, 0), kc=(0, 0, 0)),
+    "2d_heat_only": lambda: _transport(wl.random_state(n=(30, 21)), mu=(0, 0, 0), g=(0, 0, 0)),
+    "3d_2comp_bc": lambda: _transport(wl.random_state(n=(20, 17, 13), ndim=3, bc=MIXED_BC)),
+    "3d_3comp_iles_csf": lambda: _transport(wl.random_state(n=(18, 17, 21), ndim=3, ncomp=3, iles=1, sigma=5.0,
+                                                            bc=[[wl.BC_OUTFLOW] * 2, [wl.BC_PERIODIC] * 2,
+                                                                [wl.BC_REFLECT, wl.BC_OUTFLOW]])),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_viscous_parity_fp64(name):
+    w = CASES[name]()
+    q, got, ref = _run_pair(w)
+    # the terms are active: the same run without them differs clearly
+    w0 = wl.with_transport(w, mu=[0.0] * w.ncomp, kc=[0.0] * w.ncomp, gravity=(0.0, 0.0, 0.0))
+    _, got0, _ = _run_pair(w0)
+    assert np.abs(got0 - got).max() > 0.0
+    d = _rel(w, got, ref)
+    assert np.all(d < 1e-11), d
+
+
+def test_rising_bubble_parity_with_cfl_steps():
+    """Table 4.4 case 1 on a coarse 40 x 80 grid: five CFL steps (the step
+    size includes the diffusive limit) against the oracle, and the step
+    size itself.  The momentum is the small residual of the hydrostatic
+    pressure gradient against rho g (and of the Laplace jump against the
+    CSF force), so it is ill-conditioned: a 1e-16 relative perturbation of
+    the oracle's own input moves it by about 1e-8.  Its bound is that
+    spread; the other fields keep the 1e-11 bound."""
+    w = wl.rising_bubble(1, n=(40, 80))
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=fv.FV_FP64)
+    s.set_state(q)
+    s.step(1, w.cfl)
+    assert abs(s.diag_scalar(fv.FV_DIAG_DT) / o.dt(q, w.cfl) - 1.0) < 1e-12
+    s.step(4, w.cfl)
+    ref, t = o.step(q, 5, w.cfl)
+    assert abs(s.diag_scalar(fv.FV_DIAG_TIME) / t - 1.0) < 1e-12
+    d = _rel(w, s.get_state(), ref)
+    rng = np.random.default_rng(20230401)
+    spread = _rel(w, o.step(q * (1 + 1e-16 * rng.standard_normal(q.shape)), 5, w.cfl)[0], ref)
+    mom = slice(1, 1 + w.ndim)
+    assert np.all(np.r_[d[:1], d[1 + w.ndim:]] < 1e-11), d
+    assert np.all(d[mom] < 3 * spread[mom]), (d, spread)
+    assert np.all(spread[mom] < 1e-6), spread
+
+
+def test_diffusive_step_limit_matches_oracle():
+    """a viscosity large enough for the diffusive limit to set the step"""
+    w = _transport(wl.random_state(n=(24, 20)), mu=(40.0, 80.0), kc=(0.0, 0.0))
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    w_inv = wl.with_transport(w, mu=[0.0, 0.0], kc=[0.0, 0.0])
+    assert o.dt(q, 0.4) < 0.5 * oracle.Oracle(w_inv).dt(q, 0.4)
+    for precision, tol in ((fv.FV_FP64, 1e-12), (fv.FV_MIXED, 1e-5)):
+        s = fv.Solver(w, precision=precision)
+        s.set_state(q)
+        s.step(1, 0.4)
+        assert abs(s.diag_scalar(fv.FV_DIAG_DT) / o.dt(q, 0.4) - 1.0) < tol
+
+
+def test_rising_bubble_mixed_accuracy():
+    """FP32-mixed rising bubble (CSF, viscosity, gravity) against the FP64
+    oracle after 20 steps: relative L1 per conserved field.  Density,
+    energy and mass fraction below 1e-6.  The momentum of the liquid at rest
+    is the residual of the hydrostatic and Laplace balances; a relative
+    perturbation of 1e-10 of the oracle's own input (a pressure noise of
+    c^2 rho 1e-10 in the stiff liquid) moves it by about 1e-3 in L1.  Its
+    bound is that spread."""
+    w = wl.rising_bubble(2, n=(48, 96))
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=fv.FV_MIXED)
+    s.set_state(q)
+    s.step(20, w.cfl)
+    ref, _ = o.step(q, 20, w.cfl)
+    rng = np.random.default_rng(20230401)
+    spread = rel_l1_vec(o.step(q * (1 + 1e-10 * rng.standard_normal(q.shape)), 20, w.cfl)[0], ref, w.ndim)
+    e = rel_l1_vec(s.get_state(), ref, w.ndim)
+    mom = slice(1, 1 + w.ndim)
+    print("mixed rising bubble L1", e, "spread(1e-10)", spread)
+    assert np.all(np.r_[e[:1], e[1 + w.ndim:]] < 1e-6), e
+    assert np.all(e[mom] < spread[mom]), (e, spread)
+    assert np.all(spread[mom] < 1e-2), spread
+
+
+def test_viscous_rejected_for_peng_robinson():
+    w = wl.random_state(n=(16, 16), pr=True)
+    w = wl.with_transport(w, mu=[1e-5, 1e-3])
+    with pytest.raises(fv.FVError) as ei:
+        fv.Solver(w, precision=fv.FV_FP64)
+    assert ei.value.status == fv.FV_ERR_ARG

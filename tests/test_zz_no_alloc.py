@@ -41,11 +41,14 @@ TOL = {fv.FV_FP64: 1e-12, fv.FV_MIXED: 1e-6}
 
 
 @pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
-@pytest.mark.parametrize("lims", [(wl.LIM_KOREN, wl.LIM_MINMOD), (wl.LIM_VANLEER, wl.LIM_MC)])
-def test_noalloc_matches_fv_rk_stage_twice(precision, lims):
+@pytest.mark.parametrize("lims,viscous", [((wl.LIM_KOREN, wl.LIM_MINMOD), False), ((wl.LIM_VANLEER, wl.LIM_MC), False),
+                                          ((wl.LIM_KOREN, wl.LIM_MINMOD), True)])
+def test_noalloc_matches_fv_rk_stage_twice(precision, lims, viscous):
     import torch
     w = wl.random_state(n=(37, 23), bc=[[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2, [0, 0]],
                         lim_vel=lims[0], lim_scalar=lims[1])
+    if viscous:   # stress, heat flux and gravity terms (Eq. 2-2)
+        w = wl.with_transport(w, mu=[2e-3, 5e-3], kc=[0.4, 0.6], gravity=(0.3, -9.8, 0.0))
     s = fv.Solver(w, precision=precision)
     s.set_state(w.primitives(), kind=fv.FV_PRIMITIVE)
     q = s.get_state()
