@@ -40,7 +40,7 @@ def _peaks():
     return dict(hbm=6800.0, src="fallback")
 
 
-WORKLOADS = ("shock_bubble", "advection", "pr_shock_droplet", "droplet_ensemble", "jet3d")
+WORKLOADS = ("shock_bubble", "advection", "pr_shock_droplet", "droplet_ensemble", "jet3d", "rising_bubble")
 
 
 class Job:
@@ -78,6 +78,11 @@ def _workload(args):
         n = (512, 256, 256) if args.nx == 2048 else (args.nx, args.nx // 2, args.nx // 2)
         w = wl.jet3d(n=n)
         return Job(w.name, [w], inflow=[wl.jet_inflow_velocity(w)])
+    if k == "rising_bubble":
+        # Table 4.4 case 2 (viscous stresses, gravity, CSF); --nx N: an N x 2N grid
+        n = (160, 320) if args.nx == 2048 else (args.nx, 2 * args.nx)
+        w = wl.rising_bubble(2, n=n)
+        return Job(w.name, [w])
     raise SystemExit(f"unknown workload {k}")
 
 
@@ -190,8 +195,13 @@ def record_traffic(args):
 
 
 def _nprim(w):
+    """primitive-array fields: W, then rho and c (App. D switch or gravity),
+    the encoded liquid fraction (App. D or CSF), mu and k_c (viscous terms)"""
     s = w.scheme
-    return w.nvar + (2 if s["iles"] else 0) + (1 if (s["iles"] or s["sigma"] > 0) else 0)
+    grav = any(g != 0.0 for g in s.get("gravity", (0.0, 0.0, 0.0)))
+    visc = any(c.get("mu", 0.0) > 0.0 or c.get("kc", 0.0) > 0.0 for c in w.comps)
+    return (w.nvar + (2 if (s["iles"] or grav) else 0) + (1 if (s["iles"] or s["sigma"] > 0) else 0)
+            + (2 if visc else 0))
 
 
 def _algorithmic_stage_bytes(job, precision, fused=False):
@@ -351,7 +361,7 @@ def run_reference(args):
     t1 = time.perf_counter()
     cells = w.n[0] * rows
     val = cells * args.steps / (t1 - t0)
-    sample = f"one LSRK step per bench step on a {w.n[0]}x{rows} band of the {w.n[0]}x{ny} shock-bubble grid"
+    sample = f"one LSRK step per bench step on a {w.n[0]}x{rows} band of the {w.n[0]}x{ny} grid of {w.name}"
     line = dict(impl="reference", metric=METRIC, value=val, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * (t1 - t0) / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
