@@ -37,7 +37,8 @@ def build(force: bool = False) -> str:
 class Comp(C.Structure):
     _fields_ = [("kind", C.c_int), ("gamma", C.c_double), ("pinf", C.c_double), ("cv", C.c_double),
                 ("q", C.c_double), ("Tc", C.c_double), ("pc", C.c_double), ("omega", C.c_double),
-                ("M", C.c_double), ("mu", C.c_double), ("kc", C.c_double)]
+                ("M", C.c_double), ("mu", C.c_double), ("kc", C.c_double), ("psat", C.c_double),
+                ("rho_sl", C.c_double), ("rho_sv", C.c_double), ("cl", C.c_double), ("rt", C.c_double)]
 
 
 class Params(C.Structure):
@@ -49,7 +50,7 @@ class Params(C.Structure):
                 ("d3p_coef", C.c_double), ("sigma", C.c_double), ("grad_eps", C.c_double),
                 ("in_yc", C.c_double), ("in_zc", C.c_double), ("in_radius", C.c_double),
                 ("in_T", C.c_double), ("in_Y", C.c_double * MAXC), ("in_u", C.POINTER(C.c_double)),
-                ("in_u0", C.c_double * 3), ("grav", C.c_double * 3)]
+                ("in_u0", C.c_double * 3), ("grav", C.c_double * 3), ("thr_vap", C.c_double)]
 
 
 def lib():
@@ -77,6 +78,9 @@ def lib():
             L.or_csf_source.argtypes = [P, dp, dp]
             L.or_sensor.argtypes = [P, dp, dp]
             L.or_transport.argtypes = [P, dp, dp]
+            L.or_baro_vapour.argtypes = [P, C.c_double, dp]
+            L.or_baro_vapour.restype = C.c_double
+            L.or_face_flux_av.argtypes = [P, C.c_int, dp, dp, dp, dp, C.c_int, dp]
             L.or_pr_state.argtypes = [P, C.c_double, C.c_double, dp, dp]
             _lib = L
     return _lib
@@ -108,7 +112,8 @@ def make_params(w, inflow_u: np.ndarray | None = None) -> Params:
     P.liquid = w.liquid
     for k, c in enumerate(w.comps):
         P.comp[k] = Comp(c["kind"], c["gamma"], c["pinf"], c["cv"], c["q"], c["Tc"], c["pc"], c["omega"], c["M"],
-                         c.get("mu", 0.0), c.get("kc", 0.0))
+                         c.get("mu", 0.0), c.get("kc", 0.0), c.get("psat", 0.0), c.get("rho_sl", 0.0),
+                         c.get("rho_sv", 0.0), c.get("cl", 0.0), c.get("rt", 0.0))
     s = w.scheme
     P.iles, P.thinc = int(s["iles"]), int(s["thinc"])
     P.beta, P.thinc_eps, P.thinc_gamma = s["beta"], s["thinc_eps"], s["thinc_gamma"]
@@ -117,6 +122,7 @@ def make_params(w, inflow_u: np.ndarray | None = None) -> Params:
     P.sigma, P.grad_eps = s["sigma"], s["grad_eps"]
     for d, g in enumerate(s.get("gravity", (0.0, 0.0, 0.0))):
         P.grav[d] = g
+    P.thr_vap = s.get("thr_vap", 0.4)
     if w.inflow:
         f = w.inflow
         P.in_yc, P.in_zc, P.in_radius, P.in_T = f["yc"] - w.lo[1], f["zc"] - w.lo[2], f["radius"], f["T"]
@@ -224,7 +230,24 @@ class Oracle:
         _check(self.L.or_pr_state(C.byref(self.P), T, v, _ptr(Y), _ptr(out)), "pr_state")
         return dict(p=out[0], e=out[1], c=out[2], cv=out[3], a=out[4], b=out[5], M=out[6], da=out[7])
 
-    def face_flux(self, d, W4, rho4=None, c4=None, f=1):
+    def vapour(self, p, alpha):
+        """Eq. 2-7 vapour volume fraction at p given the phase fractions"""
+        a = np.zeros(MAXC)
+        a[:len(alpha)] = alpha
+        return self.L.or_baro_vapour(C.byref(self.P), p, _ptr(a))
+
+    def face_flux(self, d, W4, rho4=None, c4=None, f=1, av4=None):
+        if av4 is not None:
+            W = np.zeros((4, MAXV))
+            W4 = np.asarray(W4, dtype=np.float64)
+            W[:, :W4.shape[1]] = W4
+            r4 = np.ascontiguousarray(rho4, dtype=np.float64)
+            c4 = np.ascontiguousarray(c4 if c4 is not None else np.ones(4), dtype=np.float64)
+            a4 = np.ascontiguousarray(av4, dtype=np.float64)
+            F = np.zeros(MAXV)
+            _check(self.L.or_face_flux_av(C.byref(self.P), d, _ptr(W), _ptr(r4), _ptr(c4), _ptr(a4), int(f),
+                                          _ptr(F)), "face_flux_av")
+            return F[:self.w.nvar].copy()
         W = np.zeros((4, MAXV))
         W4 = np.asarray(W4, dtype=np.float64)
         W[:, :W4.shape[1]] = W4

@@ -345,6 +345,128 @@ static int pr_inverse(const or_params* P, double rho, double e, const double* Y,
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------------
+ * Sec. 2.2: barotropic equilibrium model.  The liquid component (OR_BARO,
+ * rho_sl > 0) is pure liquid at p >= p_sat (Eq. 2-3, sound speed c_L) and a
+ * liquid-vapour mixture below (Eq. 2-4, c_M^2 = p_sat / rho_sat,liq); every
+ * other component is a non-condensable ideal gas at its fixed temperature
+ * (Eq. 2-5: rho_i = p / (R_i T_ref,i)).  With alpha_k = xi_k rho / rho_k
+ * (Eq. 2-6) the mixture density obeys 1/rho = sum_k xi_k / rho_k(p), which
+ * is the coupled relation the paper writes after Eq. 2-6; p = f(rho, xi).
+ * READING: the energy equation is carried but does not enter p; the T slot
+ * of W holds the specific internal energy e.
+ * READING: the sound speed is Wood's, 1/(rho c^2) = sum alpha_k /
+ * (rho_k c_k^2), with c_k^2 = c_L^2 or c_M^2 for the liquid-vapour phase and
+ * R_i T_ref,i for a gas (isothermal); it equals dp/drho at fixed xi.
+ * --------------------------------------------------------------------- */
+static double bar_c2_k(const or_comp* c, double p)
+{
+    if (c->rho_sl > 0.0) return p >= c->psat ? c->cl * c->cl : c->psat / c->rho_sl;
+    return c->rt;
+}
+
+static double bar_rho_k(const or_comp* c, double p)
+{
+    if (c->rho_sl > 0.0) return c->rho_sl + (p - c->psat) / bar_c2_k(c, p);   /* Eq. 2-3 / 2-4 */
+    return p / c->rt;                                                          /* Eq. 2-5 */
+}
+
+static int bar_forward(const or_params* P, double p, const double* Y, double* rho, double* cs, double* alpha)
+{
+    const int N = P->ncomp;
+    if (!(p > 0.0) || !isfinite(p)) return OR_ERR_NONPHYS;
+    double v = 0.0, rk[OR_MAXC];
+    for (int k = 0; k < N; ++k) {
+        rk[k] = bar_rho_k(&P->comp[k], p);
+        if (Y[k] <= 0.0) continue;
+        if (!(rk[k] > 0.0)) return OR_ERR_NONPHYS;
+        v += Y[k] / rk[k];
+    }
+    const double r = 1.0 / v;
+    double inv = 0.0;
+    for (int k = 0; k < N; ++k) {
+        double a = (Y[k] > 0.0) ? r * Y[k] / rk[k] : 0.0;
+        if (alpha) alpha[k] = a;
+        if (a > 0.0) inv += a / (rk[k] * bar_c2_k(&P->comp[k], p));
+    }
+    if (rho) *rho = r;
+    if (cs) *cs = sqrt(1.0 / (r * inv));
+    return OR_OK;
+}
+
+/* p from (rho, xi): the specific-volume residual sum xi_k / rho_k(p) - 1/rho
+ * decreases in p and changes sign on (0, inf); bisection to adjacent doubles */
+static double bar_G(const or_params* P, const double* Y, double v, double p)
+{
+    double s = 0.0;
+    for (int k = 0; k < P->ncomp; ++k)
+        if (Y[k] > 0.0) s += Y[k] / bar_rho_k(&P->comp[k], p);
+    return s - v;
+}
+
+static int bar_inverse(const or_params* P, double rho, const double* Y, double* p)
+{
+    if (!(rho > 0.0) || !isfinite(rho)) return OR_ERR_NONPHYS;
+    const double v = 1.0 / rho;
+    double lo = 0.0, hi = 1.0;
+    int it = 0;
+    while (bar_G(P, Y, v, hi) > 0.0) {
+        hi *= 2.0;
+        if (++it > 4000) return OR_ERR_NONCONV;
+    }
+    for (it = 0; it < 4000; ++it) {
+        double mid = lo + 0.5 * (hi - lo);
+        if (mid <= lo || mid >= hi) break;
+        if (bar_G(P, Y, v, mid) > 0.0) lo = mid; else hi = mid;
+    }
+    *p = (0.5 * (lo + hi) > lo) ? 0.5 * (lo + hi) : hi;
+    return OR_OK;
+}
+
+/* Eq. 2-7: vapour volume fraction alpha_v = alpha_LM (rho_sat,liq - rho_M) /
+ * (rho_sat,liq - rho_sat,vap) where the liquid-vapour phase is below the
+ * saturated-liquid density, alpha_LM its volume fraction.  READING ("no pure
+ * vapour", at most 99.5% vapour): the vapour share of that phase is capped at
+ * 0.995. */
+double or_baro_vapour(const or_params* P, double p, const double* alpha)
+{
+    const or_comp* c = &P->comp[P->liquid];
+    const double rlm = bar_rho_k(c, p);
+    if (rlm >= c->rho_sl) return 0.0;
+    double s = (c->rho_sl - rlm) / (c->rho_sl - c->rho_sv);
+    if (s > 0.995) s = 0.995;
+    return alpha[P->liquid] * s;
+}
+
+/* Sound speed of a face state whose density rho came from the THINC
+ * reconstruction (Sec. 3.4 Remark 2, last step): the gas fractions follow
+ * from (p, rho, xi), the liquid-vapour phase takes the rest; Wood's formula
+ * with that phase's branch.  Returns 0 when (p, rho, xi) leave it no
+ * positive volume or density. */
+static int bar_sound_rho(const or_params* P, double p, double rho, const double* Y, double* cs)
+{
+    const int N = P->ncomp, L = P->liquid;
+    const or_comp* cl = &P->comp[L];
+    double aG = 0.0, inv = 0.0;
+    for (int k = 0; k < N; ++k) {
+        if (k == L || Y[k] <= 0.0) continue;
+        double a = Y[k] * rho * P->comp[k].rt / p;
+        aG += a;
+        inv += a / p;                          /* rho_i c_i^2 = p for an isothermal gas */
+    }
+    const double aLM = 1.0 - aG;
+    if (Y[L] > 0.0) {
+        if (!(aLM > 0.0)) return 0;
+        const double rlm = Y[L] * rho / aLM;
+        if (!(rlm > 0.0)) return 0;
+        const double c2 = rlm >= cl->rho_sl ? cl->cl * cl->cl : cl->psat / cl->rho_sl;
+        inv += aLM / (rlm * c2);
+    }
+    if (!(inv > 0.0)) return 0;
+    *cs = sqrt(1.0 / (rho * inv));
+    return 1;
+}
+
 static int all_kind(const or_params* P, int kind)
 {
     for (int k = 0; k < P->ncomp; ++k)
@@ -358,6 +480,10 @@ int or_closure_forward(const or_params* P, double p, double T, const double* Yt,
     double Y[OR_MAXC];
     full_Y(P, Yt, Y);
     if (all_kind(P, OR_SG)) return sg_forward(P, p, T, Y, rho, e, c, alpha);
+    if (all_kind(P, OR_BARO)) {
+        if (e) *e = T;                        /* the T slot holds e */
+        return bar_forward(P, p, Y, rho, c, alpha);
+    }
     if (all_kind(P, OR_PR)) {
         if (alpha)
             for (int k = 0; k < P->ncomp; ++k) alpha[k] = 0.0;   /* no volume fractions for a real-fluid mixture */
@@ -371,6 +497,11 @@ int or_closure_inverse(const or_params* P, double rho, double e, const double* Y
     double Y[OR_MAXC];
     full_Y(P, Yt, Y);
     if (all_kind(P, OR_SG)) return sg_inverse(P, rho, e, Y, p, T);
+    if (all_kind(P, OR_BARO)) {
+        if (!isfinite(e)) return OR_ERR_NONPHYS;
+        *T = e;
+        return bar_inverse(P, rho, Y, p);
+    }
     if (all_kind(P, OR_PR)) return pr_inverse(P, rho, e, Y, p, T);
     return OR_ERR_ARG;
 }
@@ -466,6 +597,18 @@ static int thinc_eligible(double eps, double xm, double x, double xp)
 int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
                  int f, double* F)
 {
+    return or_face_flux_av(P, d, W4, rho4, c4, NULL, f, F);
+}
+
+/* Sec. 3.4 Remarks 1-2 (barotropic closure): where the cells' vapour
+ * fraction is eligible (eps < alpha_v < 1 - eps and monotone, as for the mass
+ * fractions) the face density is the THINC profile of the cell densities
+ * (Eq. 3-7 / 3-8, the same formula as Eq. 3-3 / 3-4) in place of the TDU
+ * density; the face sound speed then follows from (p*, rho*, xi*).  It acts
+ * where the upwind-biased reconstruction does (plain mode, or f = 1). */
+int or_face_flux_av(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
+                    const double* av4, int f, double* F)
+{
     const int nd = P->ndim, N = P->ncomp, nv = nvar(P);
     const int ip = nd, iT = nd + 1, iY = nd + 2;
     const double* w1 = W4;
@@ -474,13 +617,16 @@ int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4
     const double* w4 = W4 + 3 * OR_MAXV;
     double WL[OR_MAXV], WR[OR_MAXV];
     const int smooth = P->iles && !f;
+    const int baro = all_kind(P, OR_BARO);
 
     for (int v = 0; v < nv; ++v) {
         if (smooth) {
             /* Eq. D.1 for u, p, T; READING: 2nd-order central for the mass
-             * fractions, as the text after Eq. D.4 says */
-            double c = (v < iY) ? (7.0 * (w2[v] + w3[v]) - w1[v] - w4[v]) / 12.0
-                                : 0.5 * (w2[v] + w3[v]);
+             * fractions, as the text after Eq. D.4 says, and for the internal
+             * energy of the barotropic closure (same text) */
+            const int fourth = (v < iY) && !(baro && v == iT);
+            double c = fourth ? (7.0 * (w2[v] + w3[v]) - w1[v] - w4[v]) / 12.0
+                              : 0.5 * (w2[v] + w3[v]);
             WL[v] = WR[v] = c;
             continue;
         }
@@ -500,6 +646,20 @@ int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4
     if (st) return st;
     st = or_closure_forward(P, WR[ip], WR[iT], WR + iY, &rR, &eR, &cR, NULL);
     if (st) return st;
+    if (baro && av4 && P->thinc && !smooth) {
+        double tl, tr, YL[OR_MAXC], YR[OR_MAXC], cs;
+        or_thinc(P->beta, P->thinc_gamma, rho4[0], rho4[1], rho4[2], rho4[3], &tl, &tr);
+        full_Y(P, WL + iY, YL);
+        full_Y(P, WR + iY, YR);
+        if (thinc_eligible(P->thinc_eps, av4[0], av4[1], av4[2]) && bar_sound_rho(P, WL[ip], tl, YL, &cs)) {
+            rL = tl;
+            cL = cs;
+        }
+        if (thinc_eligible(P->thinc_eps, av4[1], av4[2], av4[3]) && bar_sound_rho(P, WR[ip], tr, YR, &cs)) {
+            rR = tr;
+            cR = cs;
+        }
+    }
 
     double pL = WL[ip], pR = WR[ip], uL = WL[d], uR = WR[d];
     double us, ps;
@@ -651,6 +811,7 @@ typedef struct {
     double* flag;  /* App. D cell sensor */
     double* mu;    /* mixture viscosity and conductivity */
     double* kc;
+    double* av;    /* vapour volume fraction (barotropic closure) */
 } box_t;
 
 static size_t bidx(const box_t* B, int i, int j, int k)
@@ -660,7 +821,7 @@ static size_t bidx(const box_t* B, int i, int j, int k)
 
 static void box_free(box_t* B)
 {
-    free(B->W); free(B->rho); free(B->c); free(B->al); free(B->flag); free(B->mu); free(B->kc);
+    free(B->W); free(B->rho); free(B->c); free(B->al); free(B->flag); free(B->mu); free(B->kc); free(B->av);
 }
 
 static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo, const int* hi)
@@ -679,7 +840,8 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
     B->flag = calloc(B->cnt, sizeof(double));
     B->mu = calloc(B->cnt, sizeof(double));
     B->kc = calloc(B->cnt, sizeof(double));
-    if (!B->W || !B->rho || !B->c || !B->al || !B->flag || !B->mu || !B->kc) return OR_ERR_ARG;
+    B->av = calloc(B->cnt, sizeof(double));
+    if (!B->W || !B->rho || !B->c || !B->al || !B->flag || !B->mu || !B->kc || !B->av) return OR_ERR_ARG;
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
             for (int i = lo[0]; i < hi[0]; ++i) {
@@ -723,6 +885,7 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
                 B->c[b] = c;
                 B->al[b] = alk[P->liquid];
                 mix_transport(P, alk, &B->mu[b], &B->kc[b]);
+                if (all_kind(P, OR_BARO)) B->av[b] = or_baro_vapour(P, w[nd], alk);
             }
     return OR_OK;
 }
@@ -738,7 +901,7 @@ static void box_sensor(const or_params* P, box_t* B, const int* lo, const int* h
             for (int i = lo[0]; i < hi[0]; ++i) {
                 int ijk[3] = {i, j, k};
                 double g[3][3] = {{0}};  /* g[a][b] = d u_a / d x_b */
-                double tg = 0.0;
+                double tg = 0.0, tv = 0.0;
                 size_t b0 = bidx(B, i, j, k);
                 double ag0 = 1.0 - B->al[b0];
                 for (int bd = 0; bd < nd; ++bd) {
@@ -749,6 +912,7 @@ static void box_sensor(const or_params* P, box_t* B, const int* lo, const int* h
                     for (int a = 0; a < nd; ++a)
                         g[a][bd] = (B->W[(size_t)a * B->cnt + bp] - B->W[(size_t)a * B->cnt + bm]) / (2.0 * P->dx[bd]);
                     tg += fabs(ag0 - (1.0 - B->al[bm])) + fabs((1.0 - B->al[bp]) - ag0);
+                    tv += fabs(B->av[b0] - B->av[bm]) + fabs(B->av[bp] - B->av[b0]);
                 }
                 double div = 0.0;
                 for (int a = 0; a < nd; ++a) div += g[a][a];
@@ -763,7 +927,9 @@ static void box_sensor(const or_params* P, box_t* B, const int* lo, const int* h
                     curl2 = 0.0;
                 }
                 double thD = div * div / (div * div + curl2 + P->eps_ducros);
-                B->flag[b0] = (thD > P->thr_ducros || tg > P->thr_gas) ? 1.0 : 0.0;
+                /* theta^alpha: the same variation of the vapour fraction (zero
+                 * without the barotropic closure) */
+                B->flag[b0] = (thD > P->thr_ducros || tg > P->thr_gas || tv > P->thr_vap) ? 1.0 : 0.0;
             }
 }
 
@@ -894,8 +1060,9 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
     const int nd = P->ndim, nv = nvar(P);
     if (kst < 1 || kst > 4 || nd < 1 || nd > 3 || nv > OR_MAXV || P->ncomp < 2 || P->ncomp > OR_MAXC)
         return OR_ERR_ARG;
-    const int visc = has_visc(P), grav = has_grav(P);
+    const int visc = has_visc(P), grav = has_grav(P), baro = all_kind(P, OR_BARO);
     if (visc && !all_kind(P, OR_SG)) return OR_ERR_ARG;
+    if (baro && (P->sigma != 0.0 || P->bc[0][0] == OR_BC_INFLOW)) return OR_ERR_ARG;
     int lo[3], hi[3], blo[3], bhi[3], slo[3], shi[3];
     for (int d = 0; d < 3; ++d) {
         lo[d] = wlo ? wlo[d] : 0;
@@ -927,7 +1094,7 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                 for (int i = 0; i < fext[d][0]; ++i) {
                     int c[3] = {lo[0] + i, lo[1] + j, lo[2] + k};
                     c[d] -= 1;   /* left cell of the face */
-                    double W4[4 * OR_MAXV], r4[4], c4[4];
+                    double W4[4 * OR_MAXV], r4[4], c4[4], a4[4];
                     for (int s = 0; s < 4; ++s) {
                         int cc[3] = {c[0], c[1], c[2]};
                         cc[d] += s - 1;
@@ -935,6 +1102,7 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                         for (int v = 0; v < nv; ++v) W4[s * OR_MAXV + v] = B.W[(size_t)v * B.cnt + b];
                         r4[s] = B.rho[b];
                         c4[s] = B.c[b];
+                        a4[s] = B.av[b];
                     }
                     int f = 1;
                     if (P->iles) {
@@ -944,7 +1112,7 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                              B.flag[bidx(&B, cp[0], cp[1], cp[2])] > 0.5) ? 1 : 0;
                     }
                     double F[OR_MAXV];
-                    st = or_face_flux(P, d, W4, r4, c4, f, F);
+                    st = or_face_flux_av(P, d, W4, r4, c4, baro ? a4 : NULL, f, F);
                     if (st) goto done;
                     if (visc) visc_face(P, &B, d, c, F);
                     size_t fi = ((size_t)k * fext[d][1] + j) * fext[d][0] + i;

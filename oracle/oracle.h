@@ -20,6 +20,8 @@
  * [nv][nz][ny][nx], x fastest, interior cells only.
  *   q = (rho, rho u_0..rho u_{d-1}, rho E, rho Y_0..rho Y_{N-2})   (Eq. 2-1)
  *   W = (u_0..u_{d-1}, p, T, Y_0..Y_{N-2})
+ * With the barotropic closure (Sec. 2.2) p does not depend on the energy:
+ * the slot of T holds the specific internal energy e.
  * The mass fraction of the last component is 1 - sum of the others.
  */
 #ifndef THINC_ORACLE_H
@@ -34,7 +36,7 @@ extern "C" {
 
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_NONPHYS = 2, OR_ERR_NONCONV = 3 };
 enum { OR_BC_PERIODIC = 0, OR_BC_REFLECT = 1, OR_BC_OUTFLOW = 2, OR_BC_INFLOW = 3 };
-enum { OR_SG = 0, OR_PR = 1 };
+enum { OR_SG = 0, OR_PR = 1, OR_BARO = 2 };
 enum { OR_MINMOD = 0, OR_KOREN = 1, OR_VANLEER = 2, OR_VANALBADA = 3,
        OR_CHAKRAVARTHY = 4, OR_MC = 5, OR_SUPERBEE = 6 };
 
@@ -43,6 +45,10 @@ typedef struct {
     double gamma, pinf, cv, q;        /* Eq. A.1.1 */
     double Tc, pc, omega, M;          /* Eq. A.2.1 (M in kg/mol) */
     double mu, kc;                    /* viscosity (Pa s), conductivity (W/(m K)); Eq. 2-2, 2-8 */
+    /* OR_BARO (Sec. 2.2): the liquid (rho_sl > 0) has saturation pressure
+     * psat, saturated liquid / vapour densities rho_sl, rho_sv and liquid
+     * sound speed cl (Eq. 2-3, 2-4, 2-7); a gas has rt = R T_ref (Eq. 2-5) */
+    double psat, rho_sl, rho_sv, cl, rt;
 } or_comp;
 
 typedef struct {
@@ -66,6 +72,7 @@ typedef struct {
     const double* in_u;               /* [3][nz][ny] inflow velocity, or NULL */
     double in_u0[3];                  /* uniform inflow velocity used when in_u is NULL */
     double grav[3];                   /* body force per unit mass g (m/s^2), Eq. 2-2 Q */
+    double thr_vap;                   /* App. D vapour-fraction threshold (barotropic closure) */
 } or_params;
 
 /* closure, pointwise (Yt = the N-1 tracked mass fractions) */
@@ -102,6 +109,13 @@ int or_csf_source(const or_params* P, const double* q, double* S);
 int or_sensor(const or_params* P, const double* q, double* f);
 /* cell mixture viscosity and conductivity on the interior (out[2][cells]) */
 int or_transport(const or_params* P, const double* q, double* out);
+/* barotropic closure (Sec. 2.2): vapour volume fraction (Eq. 2-7) at p with
+ * the phase fractions alpha of or_closure_forward */
+double or_baro_vapour(const or_params* P, double p, const double* alpha);
+/* one face with the cells' vapour fractions av4 for the liquid-vapour
+ * density THINC (Sec. 3.4 Remarks 1-2; av4 NULL: none) */
+int or_face_flux_av(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
+                    const double* av4, int f, double* F);
 
 #ifdef __cplusplus
 }

@@ -38,7 +38,7 @@ BC_PERIODIC, BC_REFLECT, BC_OUTFLOW, BC_INFLOW = 0, 1, 2, 3
 # limiter ids (Table 4.2 plus the Superbee form printed in Sec. 3.3)
 LIM_MINMOD, LIM_KOREN, LIM_VANLEER, LIM_VANALBADA, LIM_CHAKRAVARTHY, LIM_MC, LIM_SUPERBEE = range(7)
 # component kinds
-KIND_SG, KIND_PR = 0, 1
+KIND_SG, KIND_PR, KIND_BARO = 0, 1, 2
 
 
 # --------------------------------------------------------------------------
@@ -76,6 +76,20 @@ def comp_sg(gamma, pinf, cv, q=0.0, M=0.0, mu=0.0, kc=0.0):
                 Tc=0.0, pc=0.0, omega=0.0, M=float(M), mu=float(mu), kc=float(kc))
 
 
+def comp_baro_liquid(psat, rho_sl, rho_sv, cl):
+    """barotropic liquid / liquid-vapour mixture (Sec. 2.2, Eq. 2-3, 2-4,
+    2-7): saturation pressure, saturated liquid and vapour densities, liquid
+    sound speed"""
+    return dict(kind=KIND_BARO, gamma=0.0, pinf=0.0, cv=1.0, q=0.0, Tc=0.0, pc=0.0, omega=0.0, M=0.0,
+                mu=0.0, kc=0.0, psat=float(psat), rho_sl=float(rho_sl), rho_sv=float(rho_sv), cl=float(cl), rt=0.0)
+
+
+def comp_baro_gas(R, T_ref):
+    """non-condensable ideal gas at the fixed temperature T_ref (Eq. 2-5)"""
+    return dict(kind=KIND_BARO, gamma=0.0, pinf=0.0, cv=1.0, q=0.0, Tc=0.0, pc=0.0, omega=0.0, M=0.0,
+                mu=0.0, kc=0.0, psat=0.0, rho_sl=0.0, rho_sv=0.0, cl=0.0, rt=float(R) * float(T_ref))
+
+
 def comp_pr(Tc, pc, omega, cv, M):
     return dict(kind=KIND_PR, gamma=0.0, pinf=0.0, cv=float(cv), q=0.0,
                 Tc=float(Tc), pc=float(pc), omega=float(omega), M=float(M), mu=0.0, kc=0.0)
@@ -95,7 +109,7 @@ def default_scheme(**kw) -> Dict:
              lim_vel=LIM_KOREN, lim_scalar=LIM_MINMOD,
              thr_ducros=0.95, thr_gas=0.4, eps_ducros=1e-20, d3p_coef=1.0,
              sigma=0.0, grad_eps=1e-5, precision=0, p_ref=1e5, T_ref=300.0,
-             gravity=(0.0, 0.0, 0.0))
+             gravity=(0.0, 0.0, 0.0), thr_vap=0.4)
     s.update(kw)
     return s
 
@@ -347,7 +361,27 @@ def _init_bubble(w: Workload):
     return W
 
 
-_INIT = {"bubble": _init_bubble, "pr_drop": _init_pr_drop, "column": _init_column, "shock_bubble": _init_shock_bubble,
+def _init_collapse(w: Workload):
+    """Bubble collapse near a wall: bubble of radius R centred at (0, H),
+    liquid at rest with the pressure p_inf + (R / r)(p_b - p_inf) outside
+    the bubble (r from the bubble centre), p_b inside; tanh-smoothed.  Gas
+    bubble: non-condensable gas (Y = 1) at p_b.  Vapour bubble: no gas, the
+    liquid-vapour mixture at the pressure p_b that the barotropic law gives
+    for the capped vapour fraction."""
+    P = w.params
+    X, Y, _ = _grid(w)
+    r = np.sqrt(X ** 2 + (Y - P["H"]) ** 2)
+    h = tanh_indicator(r - P["R"], P["width"] * w.dx[0])      # bubble indicator
+    pb, pinf = P["p_b"], P["p_inf"]
+    ramp = pinf + (P["R"] / np.maximum(r, P["R"])) * (pb - pinf)
+    W = _alloc(w)
+    W[w.ndim] = h * pb + (1.0 - h) * ramp
+    W[w.ndim + 1] = P["e"]
+    W[w.ndim + 2] = h if P["gas"] else 0.0
+    return W
+
+
+_INIT = {"collapse": _init_collapse, "bubble": _init_bubble, "pr_drop": _init_pr_drop, "column": _init_column, "shock_bubble": _init_shock_bubble,
          "droplet": _init_droplet, "random": _init_random, "jet": _init_jet}
 
 
@@ -515,3 +549,31 @@ def rising_bubble(case=1, n=None, steps=1000, **scheme):
         bc=[[BC_REFLECT] * 2, [BC_REFLECT] * 2, [BC_PERIODIC] * 2], comps=[gas, liquid], liquid=1,
         scheme=sch, steps=steps, cfl=0.4, init="bubble",
         params=dict(p=p0, T=T0, rho_l=c["rho_l"], xb=0.5, yb=0.5, R=0.25, width=1.5))
+
+
+# water near 11 C: saturation pressure 1342 Pa (Sec. 4.9), saturated liquid
+# and vapour densities, liquid sound speed; air as the non-condensable gas
+WATER_BARO = comp_baro_liquid(1342.0, 999.7, 0.0100, 1450.0)
+AIR_BARO = comp_baro_gas(287.05, 293.15)
+
+
+def bubble_collapse(kind="vapour", n=(1000, 1000), p_inf=1e7, steps=2000, **scheme):
+    """Gas / vapour bubble collapse near a wall (Sec. 4.9): bubble radius
+    R = 400 um centred H = 440 um above a wall at y = 0, on a 4 x 4 mm box
+    ([-2, 2] x [0, 4] mm; n = 1000 gives the paper's finest 4 um cells
+    everywhere), barotropic closure (Sec. 2.2).  Gas bubble: air at
+    3000 Pa.  Vapour bubble: the liquid-vapour mixture at the capped vapour
+    fraction (0.995), whose barotropic pressure is 6.7 Pa (p_sat = 1342 Pa).
+    Ambient liquid p_inf = 10 MPa with the 1/r pressure ramp, at rest; wall
+    below, outflow elsewhere; App. D switch off, THINC on.  CFL 0.4."""
+    nx, ny = n
+    L = 4e-3
+    liq = WATER_BARO
+    rho_m = liq["rho_sl"] - 0.995 * (liq["rho_sl"] - liq["rho_sv"])
+    p_b = 3000.0 if kind == "gas" else liq["psat"] * rho_m / liq["rho_sl"]
+    sch = default_scheme(**dict(dict(p_ref=p_inf), **scheme))
+    return Workload(
+        name=f"{kind}_bubble_collapse_{nx}x{ny}", ndim=2, n=[nx, ny, 1], lo=[-0.5 * L, 0.0, 0.0],
+        hi=[0.5 * L, L * ny / nx, 1.0], bc=[[BC_OUTFLOW] * 2, [BC_REFLECT, BC_OUTFLOW], [BC_PERIODIC] * 2],
+        comps=[AIR_BARO, liq], liquid=1, scheme=sch, steps=steps, cfl=0.4, init="collapse",
+        params=dict(R=400e-6, H=440e-6, p_b=p_b, p_inf=p_inf, e=0.0, gas=(kind == "gas"), width=1.5))
