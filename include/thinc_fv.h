@@ -53,7 +53,7 @@ typedef enum {
 } fv_status;
 
 enum { FV_BC_PERIODIC = 0, FV_BC_REFLECT = 1, FV_BC_OUTFLOW = 2, FV_BC_INFLOW = 3 };
-enum { FV_SG = 0, FV_PR = 1 };
+enum { FV_SG = 0, FV_PR = 1, FV_BARO = 2 };
 enum { FV_MINMOD = 0, FV_KOREN = 1, FV_VANLEER = 2, FV_VANALBADA = 3,
        FV_CHAKRAVARTHY = 4, FV_MC = 5, FV_SUPERBEE = 6 };
 enum { FV_FP64 = 0, FV_MIXED = 1 };
@@ -91,7 +91,14 @@ typedef struct {
 
 /* One material.  FV_SG: stiffened gas p = (gamma-1) rho (e-q) - gamma pinf
  * (Eq. A.1.1; ideal gas when pinf = 0).  FV_PR: Peng-Robinson (Eq. A.2.1)
- * with constant ideal-gas cv; M is the molar mass in kg/mol.  mu (Pa s) and
+ * with constant ideal-gas cv; M is the molar mass in kg/mol.  FV_BARO: the
+ * barotropic model of Sec. 2.2 -- the component at fv_components.liquid is
+ * the liquid / liquid-vapour mixture with saturation pressure psat,
+ * saturated liquid and vapour densities rho_sl, rho_sv and liquid sound
+ * speed cl (Eq. 2-3, 2-4, 2-7), every other one an ideal gas at a fixed
+ * temperature with rt = R T_ref (Eq. 2-5).  Then p = f(rho, Y) and the energy
+ * is carried passively: the T slot of primitive states holds the specific
+ * internal energy e.  All components share one kind.  mu (Pa s) and
  * kc (W/(m K)) are the dynamic viscosity and thermal conductivity of the
  * stress and heat-flux terms of Eq. 2-2, mixed by volume fraction (Eq. 2-8,
  * no vapour); 0 for every component = inviscid.  Viscous terms need
@@ -101,6 +108,7 @@ typedef struct {
     double gamma, pinf, cv, q;
     double Tc, pc, omega, M;
     double mu, kc;
+    double psat, rho_sl, rho_sv, cl, rt;
 } fv_component;
 
 typedef struct {
@@ -122,6 +130,7 @@ typedef struct {
     double p_ref, T_ref;         /* offsets carried by the FP32 arithmetic of FV_MIXED */
     double gravity[3];           /* body force per unit mass (m/s^2) of Eq. 2-2: source rho g
                                     (momentum) and rho u . g (energy); zero = off */
+    double thr_vap;              /* App. D vapour-fraction sensor threshold (FV_BARO) */
 } fv_eos;
 
 typedef struct fv_ctx fv_ctx;

@@ -159,9 +159,34 @@ static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm,
     }
     if (cm->ncomp < 2 || cm->ncomp > 3) { why = "ncomp must be 2 or 3"; return FV_ERR_ARG; }
     if (cm->liquid < 0 || cm->liquid >= cm->ncomp) { why = "bad liquid index"; return FV_ERR_ARG; }
-    int npr = 0;
-    for (int k = 0; k < cm->ncomp; ++k) npr += cm->comp[k].kind == FV_PR;
-    if (npr == cm->ncomp) {
+    int npr = 0, nbaro = 0;
+    for (int k = 0; k < cm->ncomp; ++k) {
+        npr += cm->comp[k].kind == FV_PR;
+        nbaro += cm->comp[k].kind == FV_BARO;
+    }
+    if (nbaro > 0) {
+        // barotropic closure (Sec. 2.2): the liquid-vapour component at
+        // `liquid`, isothermal ideal gases elsewhere
+        if (nbaro != cm->ncomp) { why = "barotropic components cannot mix with other closures"; return FV_ERR_ARG; }
+        for (int k = 0; k < cm->ncomp; ++k) {
+            const fv_component& c = cm->comp[k];
+            if (k == cm->liquid) {
+                if (!(c.psat > 0.0) || !(c.rho_sl > 0.0) || !(c.rho_sv > 0.0) || !(c.rho_sv < c.rho_sl) ||
+                    !(c.cl > 0.0) || !std::isfinite(c.psat * c.rho_sl * c.cl)) {
+                    why = "bad barotropic liquid constants";
+                    return FV_ERR_ARG;
+                }
+            } else if (!(c.rt > 0.0) || !std::isfinite(c.rt)) {
+                why = "bad barotropic gas constant R T_ref";
+                return FV_ERR_ARG;
+            }
+            if (c.mu != 0.0 || c.kc != 0.0) { why = "viscous terms need stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
+        }
+        if (eos->sigma > 0.0) { why = "CSF needs stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
+        for (int c = 0; c < ncases; ++c)
+            if (g[c].bc[0][0] == FV_BC_INFLOW) { why = "the inflow disc needs stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
+        if (!std::isfinite(eos->thr_vap)) { why = "bad vapour sensor threshold"; return FV_ERR_ARG; }
+    } else if (npr == cm->ncomp) {
         // Peng-Robinson mixture (Eq. A.2.1)
         for (int k = 0; k < cm->ncomp; ++k) {
             const fv_component& c = cm->comp[k];
@@ -180,7 +205,7 @@ static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm,
     }
     double pis[FV_MAX_COMP];
     int npi = 0;
-    for (int k = 0; k < cm->ncomp && npr == 0; ++k) {
+    for (int k = 0; k < cm->ncomp && npr == 0 && nbaro == 0; ++k) {
         const fv_component& c = cm->comp[k];
         if (c.kind != FV_SG) { why = "only stiffened-gas / ideal-gas components are supported"; return FV_ERR_ARG; }
         if (!(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) { why = "bad component constants"; return FV_ERR_ARG; }
@@ -218,6 +243,11 @@ static bool has_visc(const fv_components* cm)
     return false;
 }
 
+static bool is_baro(const fv_components* cm)
+{
+    return cm->ncomp > 0 && cm->comp[0].kind == FV_BARO;
+}
+
 static bool has_grav(const fv_eos* eos)
 {
     return eos->gravity[0] != 0.0 || eos->gravity[1] != 0.0 || eos->gravity[2] != 0.0;
@@ -238,13 +268,15 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
     P.csf = eos->sigma > 0.0 ? 1 : 0;
     P.visc = has_visc(cm) ? 1 : 0;
     P.grav = has_grav(eos) ? 1 : 0;
-    P.aux_rc = (P.iles || P.grav) ? 1 : 0;
+    P.baro = is_baro(cm) ? 1 : 0;
+    P.aux_rc = (P.iles || P.grav || P.baro) ? 1 : 0;
     P.aux_al = (P.csf || P.iles) ? 1 : 0;
     int np = x->nv;
-    P.i_rho = P.i_c = P.i_al = P.i_mu = P.i_kc = -1;
+    P.i_rho = P.i_c = P.i_al = P.i_mu = P.i_kc = P.i_av = -1;
     if (P.aux_rc) { P.i_rho = np++; P.i_c = np++; }
     if (P.aux_al) P.i_al = np++;
     if (P.visc) { P.i_mu = np++; P.i_kc = np++; }
+    if (P.baro) P.i_av = np++;
     P.nprim = np;
     x->nprim = np;
     P.beta = eos->beta;
@@ -360,6 +392,16 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
         }
         Kt.icvmin = T(1.0 / cvmin);
         for (int d = 0; d < 3; ++d) Kt.grav[d] = T(eos->gravity[d]);
+        if (P.baro) {
+            const fv_component& lq = cm->comp[cm->liquid];
+            for (int k = 0; k < MAXC; ++k) Kt.brt[k] = T(k < cm->ncomp && k != cm->liquid ? cm->comp[k].rt : 0.0);
+            Kt.b_rsl = T(lq.rho_sl);
+            Kt.b_rsv = T(lq.rho_sv);
+            Kt.b_pso = T(lq.psat - P.p_ref);
+            Kt.b_icl2 = T(1.0 / (lq.cl * lq.cl));
+            Kt.b_icm2 = T(lq.rho_sl / lq.psat);   // 1/c_M^2, c_M^2 = p_sat / rho_sat,liq
+        }
+        Kt.thr_vap = T(eos->thr_vap);
     };
     fill(P.kd);
     fill(P.kf);
@@ -457,9 +499,10 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
 static int count_nprim(const fv_components* cm, const fv_eos* eos, int nv)
 {
     int np = nv;
-    if (eos->iles || has_grav(eos)) np += 2;
+    if (eos->iles || has_grav(eos) || is_baro(cm)) np += 2;
     if (eos->iles || eos->sigma > 0.0) np += 1;
     if (has_visc(cm)) np += 2;
+    if (is_baro(cm)) np += 1;
     return np;
 }
 
@@ -597,6 +640,7 @@ static void stage_items(const std::vector<CaseDesc>& cases, int nd, int tile, st
 // and any other limiter pair run on tile 0.
 static int kernel_variant(const DevParams& P, int tile)
 {
+    if (P.baro) return NTILES + 4;
     if (P.visc || P.grav) return NTILES + 3;
     const bool t42 = P.lim_vel == FV_KOREN && P.lim_scalar == FV_MINMOD;
     if (t42 && !P.pr) return tile < NTILES ? tile : 0;
@@ -889,8 +933,8 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
-    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.visc && !x->P.grav;
-    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.visc && !x->P.grav;
+    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav;
+    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }

@@ -12,6 +12,9 @@
 namespace tfv {
 
 constexpr int MAXC = 4;
+// closures (compile-time kernel parameter): stiffened / ideal gas (App. A.1),
+// Peng-Robinson (App. A.2.1), barotropic liquid-vapour + gases (Sec. 2.2)
+constexpr int CL_SG = 0, CL_PR = 1, CL_BARO = 2;
 constexpr int ERR_NONPHYS = 1;
 constexpr int ERR_NONCONV = 2;
 constexpr int ERR_TIMEOUT = 4;   // a bounded wait in a kernel gave up
@@ -47,6 +50,10 @@ struct ConstT {
     R mu[MAXC], kc[MAXC];   // viscosity and conductivity per component (Eq. 2-2)
     R grav[3];              // body force per unit mass (Eq. 2-2 Q)
     R icvmin;               // 1 / smallest component cv (diffusive step limit)
+    // barotropic closure (Sec. 2.2): R T_ref per gas (0 for the liquid);
+    // saturated liquid / vapour densities, p_sat - p_ref, 1/c_L^2, 1/c_M^2
+    R brt[MAXC];
+    R b_rsl, b_rsv, b_pso, b_icl2, b_icm2, thr_vap;
 };
 
 struct CompDev {
@@ -87,6 +94,8 @@ struct DevParams {
     ConstT<double> kd;
     ConstT<float> kf;
     int pr;              // every component is Peng-Robinson
+    int baro;            // barotropic closure (Sec. 2.2)
+    int i_av;            // primitive-array field of the vapour volume fraction (barotropic)
     PRConst prc;
     PRConstT<float> prcf;  // FP32 copy (the mixed form's face TDU)
 };
@@ -374,7 +383,10 @@ __device__ __forceinline__ int pr_invert(const DevParams& P, double rho, double 
 //   1/(rho c^2) = sum_k alpha_k / (gamma_k (p + pinf_k))   (Wood)
 // Returns false for a non-physical input (T <= 0, p + pinf_k <= 0 for a
 // present component, NaN).
-template <int NC, typename R, bool PRC>
+template <int NC, typename R>
+__device__ __forceinline__ bool baro_tdu(const DevParams& P, R pp, const R* Y, R& rho, R& c);
+
+template <int NC, typename R, int CL>
 __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, R& rho, R& e, R& c)
 {
     R Y[NC], s = R(0);
@@ -382,9 +394,13 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
     for (int k = 0; k < NC - 1; ++k) { Y[k] = clip01(Yt[k]); s += Y[k]; }
     Y[NC - 1] = clip01(R(1) - s);
     const ConstT<R>& Kc = K<R>(P);
-    if constexpr (PRC) {
+    if constexpr (CL == CL_PR) {
         // the face state's PR closure in the working precision
         return pr_tdu<NC, R>(P, Kc.p_ref + pp, T, Y, rho, e, c);
+    }
+    if constexpr (CL == CL_BARO) {
+        e = T;   // the energy is passive: the T slot carries e
+        return baro_tdu<NC, R>(P, pp, Y, rho, c);
     }
     R Pk[NC], iP[NC];
     bool ok = T > R(0);
@@ -411,6 +427,106 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
     return ok && (v > R(0)) && (w > R(0));
 }
 
+// Barotropic closure (Sec. 2.2) at the offset pressure pp = p - p_ref: the
+// liquid-vapour phase density rho_LM = rho_sat,liq + (p - p_sat)/c^2 with
+// c = c_L above p_sat (Eq. 2-3) and c_M^2 = p_sat/rho_sat,liq below (Eq. 2-4),
+// gas densities p/(R T_ref) (Eq. 2-5); 1/rho = sum_k Y_k/rho_k and Wood's
+// 1/(rho c^2) = rho sum_k Y_k/(rho_k^2 c_k^2), i.e. c = (1/rho)/sqrt(W) with
+// W = Y_LM/(rho_LM^2 c_LM^2) + sum_gas Y_g R T_ref,g / p^2.
+template <int NC, typename R>
+__device__ __forceinline__ bool baro_tdu(const DevParams& P, R pp, const R* Y, R& rho, R& c)
+{
+    const ConstT<R>& Kc = K<R>(P);
+    const R p = Kc.p_ref + pp;
+    const R ic2 = (pp >= Kc.b_pso) ? Kc.b_icl2 : Kc.b_icm2;
+    const R rlm = Kc.b_rsl + (pp - Kc.b_pso) * ic2;
+    const R ip = frcp(p);
+    R v = R(0), w = R(0);
+    bool ok = p > R(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        if (k == P.liquid) {
+            if (Y[k] > R(0)) {
+                ok = ok && rlm > R(0);
+                const R ir = frcp(rlm);
+                v += Y[k] * ir;
+                w += Y[k] * ir * ir * ic2;
+            }
+        } else {
+            const R a = Y[k] * Kc.brt[k] * ip;
+            v += a;
+            w += a * ip;
+        }
+    }
+    rho = frcp(v);
+    c = v * rsq(w);
+    return ok && (v > R(0)) && (w > R(0));
+}
+
+// Vapour volume fraction of Eq. 2-7 (vapour share of the liquid-vapour phase
+// capped at 0.995), that phase's volume fraction alpha_LM = rho Y_LM / rho_LM
+// and the gas volume fraction sum_g Y_g rho R T_g / p (Eq. 2-6), from rho, Y, pp
+template <int NC, typename R>
+__device__ __forceinline__ R baro_vapour(const DevParams& P, R pp, R rho, const R* Yt, R* alm_out = nullptr,
+                                         R* ag_out = nullptr)
+{
+    const ConstT<R>& Kc = K<R>(P);
+    R Y[NC], s = R(0);
+#pragma unroll
+    for (int k = 0; k < NC - 1; ++k) { Y[k] = clip01(Yt[k]); s += Y[k]; }
+    Y[NC - 1] = clip01(R(1) - s);
+    const R ic2 = (pp >= Kc.b_pso) ? Kc.b_icl2 : Kc.b_icm2;
+    const R rlm = Kc.b_rsl + (pp - Kc.b_pso) * ic2;
+    R YL = R(0), ag = R(0);
+    const R ip = frcp(Kc.p_ref + pp);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        if (k == P.liquid) YL = Y[k];
+        else ag += Y[k] * rho * Kc.brt[k] * ip;
+    }
+    const R alm = fdiv(rho * YL, rlm);
+    if (alm_out) *alm_out = alm;
+    if (ag_out) *ag_out = ag;
+    if (rlm >= Kc.b_rsl) return R(0);
+    const R sh = fmin(R(0.995), fdiv(Kc.b_rsl - rlm, Kc.b_rsl - Kc.b_rsv));
+    return alm * sh;
+}
+
+// Sound speed of a face state whose density came from the liquid-vapour
+// THINC (Sec. 3.4 Remark 2): gas fractions from (p, rho, Y), the liquid-vapour
+// phase takes the rest; false when that leaves no positive volume or density.
+template <int NC, typename R>
+__device__ __forceinline__ bool baro_sound_rho(const DevParams& P, R pp, R rho, const R* Yt, R& c)
+{
+    const ConstT<R>& Kc = K<R>(P);
+    R Y[NC], s = R(0);
+#pragma unroll
+    for (int k = 0; k < NC - 1; ++k) { Y[k] = clip01(Yt[k]); s += Y[k]; }
+    Y[NC - 1] = clip01(R(1) - s);
+    const R p = Kc.p_ref + pp;
+    const R ip = frcp(p);
+    R ag = R(0), inv = R(0);
+#pragma unroll
+    for (int k = 0; k < NC; ++k)
+        if (k != P.liquid && Y[k] > R(0)) {
+            const R a = Y[k] * rho * Kc.brt[k] * ip;
+            ag += a;
+            inv += a * ip;
+        }
+    const R alm = R(1) - ag;
+    const R YL = Y[P.liquid];
+    if (YL > R(0)) {
+        if (!(alm > R(0))) return false;
+        const R rlm = fdiv(YL * rho, alm);
+        if (!(rlm > R(0))) return false;
+        const R ic2 = (rlm >= Kc.b_rsl) ? Kc.b_icl2 : Kc.b_icm2;
+        inv += fdiv(alm * ic2, rlm);
+    }
+    if (!(inv > R(0))) return false;
+    c = rsq(rho * inv);
+    return true;
+}
+
 // Primitive recovery (App. B "T = f(e, rho, xi), then p"): for the SG/IG
 // mixture with at most two distinct pinf (classes A and B) the p-T
 // equilibrium is the quadratic
@@ -422,7 +538,7 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
 // carry the p + pinf cancellation and are formed in FP64 (or compensated
 // FP32 in the mixed form).
 // Outputs w = (u_0..u_{ND-1}, p - p_ref, T, Y_0..Y_{NC-2}).
-template <int ND, int NC, typename R, bool PRC, typename Q>
+template <int ND, int NC, typename R, int CL, typename Q>
 __device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* w, R& rho_out, R& T_out,
                                             R& p_abs, double T0)
 {
@@ -444,7 +560,40 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* 
         w[ND + 2 + k] = Y[k];
     }
     Y[NC - 1] = clip01(R(1) - s);
-    if constexpr (PRC) {
+    if constexpr (CL == CL_BARO) {
+        // barotropic (Sec. 2.2), FP64 in both forms: with A = rho sum_g Y_g R T_ref,g
+        // and B = Y_LM rho, 1/rho = Y_LM/rho_LM(p) + sum Y_g R T_g / p becomes
+        // (p - A)(d + k p) = B p, k = 1/c^2, d = rho_sat,liq - p_sat k: the liquid
+        // branch's positive root if it is >= p_sat, else (d = 0 below p_sat)
+        // p = A + B p_sat / rho_sat,liq.  The energy is passive (T slot = e).
+        const ConstT<double>& Kd = P.kd;
+        const double rho = qv_d(qc[0]);
+        double ked = 0.0;
+#pragma unroll
+        for (int d = 0; d < ND; ++d) { const double m = qv_d(qc[1 + d]); ked += 0.5 * m * m; }
+        const double e = (qv_d(qc[ND + 1]) - ked / rho) / rho;
+        double A = 0.0, B = 0.0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (k == P.liquid) B = double(Y[k]) * rho;
+            else A += double(Y[k]) * rho * Kd.brt[k];
+        }
+        const double psat = Kd.b_pso + P.p_ref;
+        double pd = A;
+        if (B > 0.0) {
+            const double kk = Kd.b_icl2, dd = Kd.b_rsl - psat * kk;
+            const double b = dd - A * kk - B;
+            const double disc = sqrt(b * b + 4.0 * kk * A * dd);
+            pd = (b < 0.0) ? (disc - b) / (2.0 * kk) : ((A > 0.0) ? 2.0 * A * dd / (b + disc) : 0.0);
+            if (!(pd >= psat)) pd = A + B * psat / Kd.b_rsl;
+        }
+        w[ND] = R(pd - P.p_ref);
+        w[ND + 1] = R(e);
+        T_out = R(e);
+        p_abs = R(pd);
+        return (rho > 0.0 && pd > 0.0 && isfinite(pd) && isfinite(e)) ? 0 : ERR_NONPHYS;
+    }
+    if constexpr (CL == CL_PR) {
         // Peng-Robinson: FP64 Newton in both forms
         const double rho = qv_d(qc[0]);
         double ked = 0.0;
@@ -599,9 +748,10 @@ __device__ __forceinline__ R thinc_side(const DevParams& P, R xa, R xc, R xb, bo
 constexpr int LIM_RUNTIME = -1;
 constexpr int LIM_TABLE42 = (1 << 4) | 0;   // Koren for velocities, Minmod for p, T, Y (Table 4.2)
 
-template <int ND, int NC, typename R, bool PRC, int LIM>
+// av4: vapour fractions of the four cells (barotropic closure), else unused
+template <int ND, int NC, typename R, int CL, int LIM>
 __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*ws)[ND + NC + 1], const R* rho4,
-                                          const R* c4, int f, R* F)
+                                          const R* c4, int f, R* F, const R* av4 = nullptr)
 {
     constexpr int NW = ND + NC + 1;
     constexpr int IP = ND, IT = ND + 1, IY = ND + 2;
@@ -610,8 +760,11 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     if (smooth) {
 #pragma unroll
         for (int v = 0; v < NW; ++v) {
-            const R cval = (v < IY) ? (R(7) * (ws[1][v] + ws[2][v]) - ws[0][v] - ws[3][v]) * R(1.0 / 12.0)
-                                    : R(0.5) * (ws[1][v] + ws[2][v]);
+            // Eq. D.1 for u, p, T; the 2nd-order mean for Y and for the
+            // barotropic closure's internal energy
+            const bool fourth = (v < IY) && !(CL == CL_BARO && v == IT);
+            const R cval = fourth ? (R(7) * (ws[1][v] + ws[2][v]) - ws[0][v] - ws[3][v]) * R(1.0 / 12.0)
+                                  : R(0.5) * (ws[1][v] + ws[2][v]);
             WL[v] = WR[v] = cval;
         }
     } else {
@@ -627,8 +780,24 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
         }
     }
     R rL, eL, cL, rR, eR, cR;
-    bool ok = tdu<NC, R, PRC>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
-    ok = tdu<NC, R, PRC>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
+    bool ok = tdu<NC, R, CL>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
+    ok = tdu<NC, R, CL>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
+    if constexpr (CL == CL_BARO) {
+        // Sec. 3.4 Remarks 1-2: THINC of the cell densities where the vapour
+        // fraction is eligible, then the sound speed from (p*, rho*, Y*)
+        if (P.thinc && !smooth) {
+            const R eps = K<R>(P).thinc_eps;
+            R cs;
+            if (eligible(eps, av4[0], av4[1], av4[2])) {
+                const R t = thinc_side(P, rho4[0], rho4[1], rho4[2], true);
+                if (baro_sound_rho<NC, R>(P, WL[IP], t, WL + IY, cs)) { rL = t; cL = cs; }
+            }
+            if (eligible(eps, av4[1], av4[2], av4[3])) {
+                const R t = thinc_side(P, rho4[1], rho4[2], rho4[3], false);
+                if (baro_sound_rho<NC, R>(P, WR[IP], t, WR + IY, cs)) { rR = t; cR = cs; }
+            }
+        }
+    }
     // normal velocities by select: indexing with the run-time d would put WL
     // and WR in local memory
     R uL = WL[0], uR = WR[0];

@@ -68,8 +68,9 @@ constexpr TileDef tile_def(int nd, int i) { return nd == 2 ? TILES2[i] : TILES3[
 // closure with the Table 4.2 limiter pair on tile i; NTILES Peng-Robinson with
 // that pair on tile 0; NTILES+1 / NTILES+2 stiffened-gas / Peng-Robinson with
 // any limiter pair (read at run time) on tile 0; NTILES+3 stiffened-gas with
-// any limiter pair plus the viscous, heat-flux and gravity terms, tile 0.
-constexpr int NVARIANTS = NTILES + 4;
+// any limiter pair plus the viscous, heat-flux and gravity terms, tile 0;
+// NTILES+4 the barotropic closure with any limiter pair, tile 0.
+constexpr int NVARIANTS = NTILES + 5;
 // tile of variant v: the viscous 3D variant (twelve primitive fields with the
 // App. D and CSF fields) takes the 16x4x4 tile, whose halo fits in shared memory
 constexpr int variant_tile(int nd, int v) { return v < NTILES ? v : (v == NTILES + 3 && nd == 3 ? 1 : 0); }
@@ -186,7 +187,7 @@ __device__ __forceinline__ void set_err(int* err, int bit)
 }
 
 // ----------------------------------------------------------------- prims
-template <int ND, int NC, typename R, bool PRC, typename Q>
+template <int ND, int NC, typename R, int CL, typename Q>
 __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
 {
     const Q* const qreg = static_cast<const Q*>(A.q);
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             // prim == null: CFL pass only (the fused stage kernel recovers its own primitives)
             R* const pp0 = prim ? prim + C.poff + ((gc[2] * C.g[1] + gc[1]) * C.gp + gc[0]) : nullptr;
             // Peng-Robinson Newton starts from this cell's previous temperature
-            const double T0 = (PRC && pp0) ? double(pp0[(ND + 1) * P.ntot_p]) : 0.0;
-            const int rst = prim_recover<ND, NC, R, PRC, Q>(P, qc, w, rho, T, pabs, T0);
+            const double T0 = (CL == CL_PR && pp0) ? double(pp0[(ND + 1) * P.ntot_p]) : 0.0;
+            const int rst = prim_recover<ND, NC, R, CL, Q>(P, qc, w, rho, T, pabs, T0);
             bool ok = rst == 0;
             if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
 #pragma unroll
@@ -250,12 +251,12 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             const bool need_c = P.aux_rc || A.smax || in_disc;
             if (need_c) {
                 R e;
-                ok = tdu<NC, R, PRC>(P, w[ND], w[ND + 1], w + ND + 2, rr, e, cs) && ok;
+                ok = tdu<NC, R, CL>(P, w[ND], w[ND + 1], w + ND + 2, rr, e, cs) && ok;
                 if (!in_disc) rr = rho;
             }
             if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
             R mu_c = R(0), kc_c = R(0);
-            if (!PRC && P.visc) {
+            if (CL == CL_SG && P.visc) {
                 // Eq. 2-8 with no vapour: mixture viscosity = sum_k alpha_k mu_k with
                 // alpha_k = rho Y_k / rho_k (Eq. A.1.4); the conductivity mixed alike
                 R s = R(0);
@@ -282,7 +283,14 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 pp0[P.i_rho * P.ntot_p] = rr;
                 pp0[P.i_c * P.ntot_p] = cs;
             }
-            if (pp0 && P.aux_al) {
+            if constexpr (CL == CL_BARO) {
+                // liquid-vapour phase fraction (encoded as below, for the gas
+                // sensor) and the vapour fraction of Eq. 2-7
+                R alm, ag;
+                const R av = baro_vapour<NC, R>(P, w[ND], rr, w + ND + 2, &alm, &ag);
+                if (pp0 && P.aux_al) pp0[P.i_al * P.ntot_p] = (alm <= ag) ? alm : -ag;
+                if (pp0) pp0[P.i_av * P.ntot_p] = av;
+            } else if (pp0 && P.aux_al) {
                 // liquid volume fraction (Eq. A.1.4/A.1.5) stored as the smaller
                 // side: e = alpha_l if alpha_l <= alpha_g, else -alpha_g
                 // (alpha_g = 1 - alpha_l from the gas terms), so differences of
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
                 R s = R(0);
 #pragma unroll
                 for (int d = 0; d < ND; ++d) s += (fabs(w[d]) + cs) * pick<R>(C.idx[d], C.fidx[d]);
-                if (!PRC && P.visc) {
+                if (CL == CL_SG && P.visc) {
                     // diffusive limit: 2 D sum_d 1/dx_d^2, D = max(4/3 mu, k_c / cv_min) / rho
                     R i2 = R(0);
 #pragma unroll
@@ -368,7 +376,7 @@ __device__ __forceinline__ void visc_face(const DevParams& P, const R* sp, int H
 }
 
 // ------------------------------------------------------------------ stage
-template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, int MB, int NB, bool PRC, int LIM, bool VISC,
+template <int ND, int NC, typename R, int TX, int TY, int TZ, int NT, int MB, int NB, int CL, int LIM, bool VISC,
           typename Q>
 __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 {
@@ -501,7 +509,7 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
                                 (ND == 2 || (hz >= 1 && hz <= vz + 2));
                 if (in) {
                     R g[3][3];
-                    R tg = R(0);
+                    R tg = R(0), tv = R(0);
                     const R* ea = sp + P.i_al * HC;
                     const R e0 = ea[h];
                     const R o0 = liq_side(e0);
@@ -515,6 +523,11 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
                         // |delta alpha_gas| = |delta alpha_l| from the encoded fractions
                         const R em = ea[hm], ep = ea[hp];
                         tg += fabs((e0 - em) + (o0 - liq_side(em))) + fabs((ep - e0) + (liq_side(ep) - o0));
+                        if (CL == CL_BARO) {
+                            // theta^alpha: the same variation of the vapour fraction
+                            const R* va = sp + P.i_av * HC;
+                            tv += fabs(va[h] - va[hm]) + fabs(va[hp] - va[h]);
+                        }
                     }
                     R div = R(0);
 #pragma unroll
@@ -529,7 +542,7 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
                     }
                     const R d2 = div * div;
                     const R thD = fdiv(d2, d2 + curl2 + Kc.eps_ducros);
-                    fl = (thD > Kc.thr_ducros || tg > Kc.thr_gas) ? 1 : 0;
+                    fl = (thD > Kc.thr_ducros || tg > Kc.thr_gas || (CL == CL_BARO && tv > Kc.thr_vap)) ? 1 : 0;
                 }
                 sflag[h] = fl;
             }
@@ -607,16 +620,25 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
                 for (int v = 0; v < NV; ++v) ws[s][v] = sp[v * HC + h0 + s * st];
             }
             int fl = 1;
-            if (P.iles) {
+            R a4[4];
+            if constexpr (CL == CL_BARO) {
+                // cell densities and vapour fractions of the liquid-vapour THINC
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    r4[s] = sp[P.i_rho * HC + h0 + s * st];
+                    c4[s] = sp[P.i_c * HC + h0 + s * st];
+                    a4[s] = sp[P.i_av * HC + h0 + s * st];
+                }
+            } else if (P.iles) {
 #pragma unroll
                 for (int s = 1; s <= 2; ++s) {
                     r4[s] = sp[P.i_rho * HC + h0 + s * st];
                     c4[s] = sp[P.i_c * HC + h0 + s * st];
                 }
-                fl = (sflag[h0 + st] | sflag[h0 + 2 * st]) ? 1 : 0;
             }
+            if (P.iles) fl = (sflag[h0 + st] | sflag[h0 + 2 * st]) ? 1 : 0;
             R F[NV];
-            const bool ok = face_flux<ND, NC, R, PRC, LIM>(P, d, ws, r4, c4, fl, F);
+            const bool ok = face_flux<ND, NC, R, CL, LIM>(P, d, ws, r4, c4, fl, F, a4);
             if (!ok) set_err(A.err, ERR_NONPHYS);
             if (VISC && P.visc) {
                 const int sts[3] = {SX, SY, SZ};

@@ -43,8 +43,9 @@ int prim_occupancy(int nd, int nc, int mixed);
 template <int ND, int NC, typename R, typename Q>
 static cudaError_t gop(const PrimArgs& A, int grid, cudaStream_t s)
 {
-    if (A.P.pr) prim_kernel<ND, NC, R, true, Q><<<grid, 256, 0, s>>>(A);
-    else prim_kernel<ND, NC, R, false, Q><<<grid, 256, 0, s>>>(A);
+    if (A.P.pr) prim_kernel<ND, NC, R, CL_PR, Q><<<grid, 256, 0, s>>>(A);
+    else if (A.P.baro) prim_kernel<ND, NC, R, CL_BARO, Q><<<grid, 256, 0, s>>>(A);
+    else prim_kernel<ND, NC, R, CL_SG, Q><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -101,8 +102,10 @@ __global__ void prim_to_cons_kernel(IoArgs A)
 #pragma unroll
         for (int v = 0; v < NV; ++v) w[v] = in[v * A.ncell + i];
         double rho, e, c;
-        const bool ok = A.P.pr ? tdu<NC, double, true>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c)
-                               : tdu<NC, double, false>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c);
+        const bool ok =
+            A.P.pr     ? tdu<NC, double, CL_PR>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c)
+            : A.P.baro ? tdu<NC, double, CL_BARO>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c)
+                       : tdu<NC, double, CL_SG>(A.P, w[ND] - A.P.p_ref, w[ND + 1], w + ND + 2, rho, e, c);
         if (!ok) set_err(A.err, ERR_NONPHYS);
         double ke = 0.0;
 #pragma unroll
@@ -131,8 +134,9 @@ __global__ void cons_to_prim_kernel(IoArgs A)
         const long long o = C.qoff + i;
 #pragma unroll
         for (int v = 0; v < NV; ++v) qc[v] = qv_d(in[v * A.P.ntot_q + o]);
-        const int st = A.P.pr ? prim_recover<ND, NC, double, true, double>(A.P, qc, w, rho, T, p, 0.0)
-                              : prim_recover<ND, NC, double, false, double>(A.P, qc, w, rho, T, p, 0.0);
+        const int st = A.P.pr     ? prim_recover<ND, NC, double, CL_PR, double>(A.P, qc, w, rho, T, p, 0.0)
+                       : A.P.baro ? prim_recover<ND, NC, double, CL_BARO, double>(A.P, qc, w, rho, T, p, 0.0)
+                                  : prim_recover<ND, NC, double, CL_SG, double>(A.P, qc, w, rho, T, p, 0.0);
         if (st) set_err(A.err, st);
         w[ND] = p;
 #pragma unroll

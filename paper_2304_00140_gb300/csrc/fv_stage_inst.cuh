@@ -14,7 +14,10 @@ namespace tfv {
 namespace {
 // kernel variant I (see NVARIANTS): tile, closure and limiter pair
 template <int I> constexpr int tile_of() { return variant_tile(FV_ND, I); }
-template <int I> constexpr bool pr_of() { return I == NTILES || I == NTILES + 2; }
+template <int I> constexpr int cl_of()
+{
+    return (I == NTILES || I == NTILES + 2) ? CL_PR : (I == NTILES + 4 ? CL_BARO : CL_SG);
+}
 template <int I> constexpr int lim_of() { return I <= NTILES ? LIM_TABLE42 : LIM_RUNTIME; }
 template <int I> constexpr bool visc_of() { return I == NTILES + 3; }
 template <int FF> struct RegOf { using type = double; };
@@ -23,7 +26,7 @@ template <> struct RegOf<1> { using type = float2; };
 #define FV_KERNEL(NC, I, FF)                                                                  \
     stage_kernel<FV_ND, NC, FV_REAL, tile_def(FV_ND, tile_of<I>()).x, tile_def(FV_ND, tile_of<I>()).y, \
                  tile_def(FV_ND, tile_of<I>()).z, tile_def(FV_ND, tile_of<I>()).nt,                    \
-                 tile_def(FV_ND, tile_of<I>()).mb, tile_def(FV_ND, tile_of<I>()).nb, pr_of<I>(),       \
+                 tile_def(FV_ND, tile_of<I>()).mb, tile_def(FV_ND, tile_of<I>()).nb, cl_of<I>(),       \
                  lim_of<I>(), visc_of<I>(), typename RegOf<FF>::type>
 
 template <int NC, int I, int FF>
@@ -64,7 +67,7 @@ size_t bytes(int nprim)
 #define FV_FF 0
 #endif
 #define FV_TILE_SWITCH(fn, ...)                                                   \
-    static_assert(NTILES == 4 && NVARIANTS == 8, "variant switch below lists eight variants");          \
+    static_assert(NTILES == 4 && NVARIANTS == 9, "variant switch below lists nine variants");            \
     if (FV_IS_FLOAT && !ff)                                                       \
         return tile == NTILES + 1   ? FV_NC(fn, NTILES + 1, 0, __VA_ARGS__)        \
                : tile == NTILES + 3 ? FV_NC(fn, NTILES + 3, 0, __VA_ARGS__)        \
@@ -77,7 +80,8 @@ size_t bytes(int nprim)
     case NTILES: return FV_NC(fn, NTILES, FV_FF, __VA_ARGS__);                    \
     case NTILES + 1: return FV_NC(fn, NTILES + 1, FV_FF, __VA_ARGS__);            \
     case NTILES + 2: return FV_NC(fn, NTILES + 2, FV_FF, __VA_ARGS__);            \
-    default: return FV_NC(fn, NTILES + 3, FV_FF, __VA_ARGS__);                    \
+    case NTILES + 3: return FV_NC(fn, NTILES + 3, FV_FF, __VA_ARGS__);            \
+    default: return FV_NC(fn, NTILES + 4, FV_FF, __VA_ARGS__);                    \
     }
 
 cudaError_t FV_CAT(launch_stage_, FV_SUFFIX)(int nc, int tile, int ff, const StageArgs& A, int grid, size_t smem,

@@ -43,7 +43,8 @@ class fv_grid(C.Structure):
 class fv_component(C.Structure):
     _fields_ = [("kind", C.c_int), ("gamma", C.c_double), ("pinf", C.c_double), ("cv", C.c_double),
                 ("q", C.c_double), ("Tc", C.c_double), ("pc", C.c_double), ("omega", C.c_double),
-                ("M", C.c_double), ("mu", C.c_double), ("kc", C.c_double)]
+                ("M", C.c_double), ("mu", C.c_double), ("kc", C.c_double), ("psat", C.c_double),
+                ("rho_sl", C.c_double), ("rho_sv", C.c_double), ("cl", C.c_double), ("rt", C.c_double)]
 
 
 class fv_components(C.Structure):
@@ -56,7 +57,7 @@ class fv_eos(C.Structure):
                 ("thr_ducros", C.c_double), ("thr_gas", C.c_double), ("eps_ducros", C.c_double),
                 ("d3p_coef", C.c_double), ("sigma", C.c_double), ("grad_eps", C.c_double),
                 ("precision", C.c_int), ("p_ref", C.c_double), ("T_ref", C.c_double),
-                ("gravity", C.c_double * 3)]
+                ("gravity", C.c_double * 3), ("thr_vap", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -143,7 +144,8 @@ def make_components(w: "wl.Workload") -> fv_components:
     c.liquid = w.liquid
     for k, m in enumerate(w.comps):
         c.comp[k] = fv_component(m["kind"], m["gamma"], m["pinf"], m["cv"], m["q"], m["Tc"], m["pc"], m["omega"], m["M"],
-                                 m.get("mu", 0.0), m.get("kc", 0.0))
+                                 m.get("mu", 0.0), m.get("kc", 0.0), m.get("psat", 0.0), m.get("rho_sl", 0.0),
+                                 m.get("rho_sv", 0.0), m.get("cl", 0.0), m.get("rt", 0.0))
     return c
 
 
@@ -158,6 +160,7 @@ def make_eos(s: dict) -> fv_eos:
     e.p_ref, e.T_ref = s["p_ref"], s["T_ref"]
     for d, g in enumerate(s.get("gravity", (0.0, 0.0, 0.0))):
         e.gravity[d] = g
+    e.thr_vap = s.get("thr_vap", 0.4)
     return e
 
 

@@ -119,3 +119,22 @@ def test_struct_layout_matches_header(tmp_path):
         assert int(out[name]) == C.sizeof(cls), name
         for f in cls._fields_:
             assert int(out[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_barotropic_argument_checks():
+    L = fv.load()
+    n = C.c_size_t()
+    w = wl.bubble_collapse("vapour", n=(20, 20))
+    g = (fv.fv_grid * 1)(fv.make_grid(w))
+    e = fv.make_eos(w.scheme)
+    assert L.fv_workspace_size(1, g, C.byref(fv.make_components(w)), C.byref(e), C.byref(n)) == fv.FV_OK
+    for field, val in (("rho_sv", 2000.0), ("cl", 0.0), ("psat", -1.0)):
+        cm = fv.make_components(w)
+        setattr(cm.comp[w.liquid], field, val)
+        assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG, field
+    cm = fv.make_components(w)
+    cm.comp[0].rt = 0.0                                   # a gas without R T_ref
+    assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
+    cm = fv.make_components(w)
+    cm.comp[0] = fv.make_components(wl.advection(n=8)).comp[0]   # a stiffened gas among barotropic ones
+    assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
