@@ -605,7 +605,13 @@ int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4
  * fractions) the face density is the THINC profile of the cell densities
  * (Eq. 3-7 / 3-8, the same formula as Eq. 3-3 / 3-4) in place of the TDU
  * density; the face sound speed then follows from (p*, rho*, xi*).  It acts
- * where the upwind-biased reconstruction does (plain mode, or f = 1). */
+ * where the upwind-biased reconstruction does (plain mode, or f = 1).
+ * READING: the densities must be monotone across the three cells as well
+ * (the THINC profile needs the centre value between its neighbours; where
+ * alpha_v sits at its cap or varies at rounding level it can be monotone
+ * while rho is not, and the profile's F then leaves [0, 1]). */
+static int rho_monotone(double xm, double x, double xp) { return (x - xm) * (xp - x) > 0.0; }
+
 int or_face_flux_av(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
                     const double* av4, int f, double* F)
 {
@@ -651,11 +657,13 @@ int or_face_flux_av(const or_params* P, int d, const double* W4, const double* r
         or_thinc(P->beta, P->thinc_gamma, rho4[0], rho4[1], rho4[2], rho4[3], &tl, &tr);
         full_Y(P, WL + iY, YL);
         full_Y(P, WR + iY, YR);
-        if (thinc_eligible(P->thinc_eps, av4[0], av4[1], av4[2]) && bar_sound_rho(P, WL[ip], tl, YL, &cs)) {
+        if (thinc_eligible(P->thinc_eps, av4[0], av4[1], av4[2]) && rho_monotone(rho4[0], rho4[1], rho4[2]) &&
+            bar_sound_rho(P, WL[ip], tl, YL, &cs)) {
             rL = tl;
             cL = cs;
         }
-        if (thinc_eligible(P->thinc_eps, av4[1], av4[2], av4[3]) && bar_sound_rho(P, WR[ip], tr, YR, &cs)) {
+        if (thinc_eligible(P->thinc_eps, av4[1], av4[2], av4[3]) && rho_monotone(rho4[1], rho4[2], rho4[3]) &&
+            bar_sound_rho(P, WR[ip], tr, YR, &cs)) {
             rR = tr;
             cR = cs;
         }

@@ -1482,6 +1482,20 @@ bool noalloc_args_ok(const fv_grid* g, const fv_components* cm, const fv_eos* e)
     }
     if (g->in_u) return false;   // per-cell inflow velocities would need device memory
     if (cm->ncomp < 2 || cm->ncomp > 3 || cm->liquid < 0 || cm->liquid >= cm->ncomp) return false;
+    if (cm->comp[0].kind == FV_BARO) {
+        // barotropic closure: FP64 form only (the mixed no-alloc variants are
+        // instantiated for the stiffened-gas closure)
+        if (e->precision != FV_FP64 || e->sigma != 0.0 || g->bc[0][0] == FV_BC_INFLOW) return false;
+        for (int k = 0; k < cm->ncomp; ++k) {
+            const fv_component& c = cm->comp[k];
+            if (c.kind != FV_BARO || c.mu != 0.0 || c.kc != 0.0) return false;
+            if (k == cm->liquid ? !(c.psat > 0.0 && c.rho_sl > 0.0 && c.rho_sv > 0.0 && c.rho_sv < c.rho_sl && c.cl > 0.0)
+                                : !(c.rt > 0.0))
+                return false;
+        }
+        if (e->lim_vel < 0 || e->lim_vel > 6 || e->lim_scalar < 0 || e->lim_scalar > 6) return false;
+        return !e->thinc || e->beta > 0.0;
+    }
     double pa = -1.0, pb = -1.0;
     for (int k = 0; k < cm->ncomp; ++k) {
         const fv_component& c = cm->comp[k];

@@ -784,15 +784,17 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     ok = tdu<NC, R, CL>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
     if constexpr (CL == CL_BARO) {
         // Sec. 3.4 Remarks 1-2: THINC of the cell densities where the vapour
-        // fraction is eligible, then the sound speed from (p*, rho*, Y*)
+        // fraction is eligible and the densities are monotone (the profile
+        // needs the centre value between its neighbours), then the sound
+        // speed from (p*, rho*, Y*)
         if (P.thinc && !smooth) {
             const R eps = K<R>(P).thinc_eps;
             R cs;
-            if (eligible(eps, av4[0], av4[1], av4[2])) {
+            if (eligible(eps, av4[0], av4[1], av4[2]) && (rho4[1] - rho4[0]) * (rho4[2] - rho4[1]) > R(0)) {
                 const R t = thinc_side(P, rho4[0], rho4[1], rho4[2], true);
                 if (baro_sound_rho<NC, R>(P, WL[IP], t, WL + IY, cs)) { rL = t; cL = cs; }
             }
-            if (eligible(eps, av4[1], av4[2], av4[3])) {
+            if (eligible(eps, av4[1], av4[2], av4[3]) && (rho4[2] - rho4[1]) * (rho4[3] - rho4[2]) > R(0)) {
                 const R t = thinc_side(P, rho4[1], rho4[2], rho4[3], false);
                 if (baro_sound_rho<NC, R>(P, WR[IP], t, WR + IY, cs)) { rR = t; cR = cs; }
             }

@@ -205,3 +205,20 @@ def test_smooth_branch_internal_energy_is_second_order_central():
     F = o.face_flux(0, W4, np.full(4, rho), np.full(4, c), f=0)
     es = (F[3] - 2e6 * 2.0) / F[0] - 0.5 * 2.0 ** 2
     assert abs(es - 2.5e3) < 1e-9 * 2.5e3
+
+
+def test_density_thinc_needs_monotone_density():
+    """vapour fraction monotone at rounding level near its cap while the
+    density is not: no THINC (its profile would leave [0, 1] and overflow);
+    the face keeps the TDU state"""
+    o, _ = _o()
+    ps, rl = LIQ["psat"], LIQ["rho_sl"]
+    rho4 = np.array([5.0084500000021928, 5.0084500000025729, 5.008450000002199, 5.0084500000023])
+    p4 = ps * rho4 / rl
+    W4 = np.zeros((4, 5))
+    W4[:, 2] = p4
+    c4 = np.array([o.forward(p, 0.0, np.array([0.0]))[2] for p in p4])
+    av4 = np.array([0.99500000000001865, 0.99499999999999278, 0.99499999999998612, 0.9949999999999])
+    F_plain = o.face_flux(0, W4, rho4, c4, f=1)
+    F = o.face_flux(0, W4, rho4, c4, f=1, av4=av4)
+    assert np.all(np.isfinite(F)) and np.array_equal(F, F_plain)
