@@ -70,6 +70,9 @@ enum { FV_DIAG_TOTALS = 0,   /* double[nv]: compensated sums of q over the case 
                                 the z-marching 3D kernel (tile x, y, planes per item,
                                 threads in [0..3]), [9] its best tuned milliseconds,
                                 [10] the primitive pass's, [11] its variant (-1: tiled) */
+enum { FV_DIAG_FLAGS = 5 };  /* unsigned char[n cells]: App. D sensor flag f (Eq. D.4) of each
+                                interior cell for the current state (x fastest); needs the
+                                App. D switch (FV_ERR_ARG otherwise); synchronous */
 enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2,
        FV_ERRBIT_TIMEOUT = 4 };   /* a bounded wait in a kernel gave up (reported as FV_ERR_CUDA) */
 

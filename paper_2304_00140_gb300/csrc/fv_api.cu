@@ -1312,6 +1312,22 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
         }
         return FV_OK;
     }
+    if (what == FV_DIAG_FLAGS) {
+        // App. D sensor of the current state: a primitive pass, then the
+        // stage kernel's sensor function per interior cell (scratch: the QB
+        // register, free between steps)
+        if (!x->P.iles) return fail(x, FV_ERR_ARG, "the sensor flags need the App. D switch%s");
+        PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, x->Q0, x->prim, x->in_u, nullptr, x->err};
+        CK(x, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, x->stream, x->ff));
+        x->launches++;
+        const long long nc = case_cells(x, icase);
+        unsigned char* dflags = reinterpret_cast<unsigned char*>(x->QB);
+        CK(x, launch_sensor_dump(x->nd, x->mixed, x->P, x->d_cases, icase, x->prim, nc, dflags, x->stream));
+        x->launches++;
+        CK(x, cudaMemcpyAsync(out, dflags, (size_t)nc, cudaMemcpyDeviceToHost, x->stream));
+        CK(x, cudaStreamSynchronize(x->stream));
+        return FV_OK;
+    }
     if (what == FV_DIAG_DT || what == FV_DIAG_TIME) {
         CK(x, cudaStreamSynchronize(x->stream));
         CK(x, cudaMemcpy(out, (what == FV_DIAG_DT ? x->dt : x->t) + icase, sizeof(double), cudaMemcpyDeviceToHost));

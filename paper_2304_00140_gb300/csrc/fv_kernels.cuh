@@ -338,6 +338,53 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
     }
 }
 
+// App. D cell sensor (Eq. D.4) of cell h of a block of primitives (field
+// stride fs, neighbour strides st): the Ducros ratio from central
+// differences, the variation of the gas volume fraction (from the encoded
+// liquid fraction) and, for the barotropic closure, of the vapour fraction;
+// 1 if one of them exceeds its threshold.  Used by the stage kernel on its
+// halo tile and by the flags diagnostic on the primitive arrays.
+template <int ND, typename R, int CL, typename I>
+__device__ __forceinline__ unsigned char sensor_flag(const DevParams& P, const R* sp, I fs, I h, const I* st,
+                                                     const R* ci)
+{
+    const ConstT<R>& Kc = K<R>(P);
+    R g[3][3];
+    R tg = R(0), tv = R(0);
+    const R* ea = sp + P.i_al * fs;
+    const R e0 = ea[h];
+    const R o0 = liq_side(e0);
+#pragma unroll
+    for (int bd = 0; bd < ND; ++bd) {
+        const I hp = h + st[bd], hm = h - st[bd];
+        const R inv2dx = R(0.5) * ci[bd];
+#pragma unroll
+        for (int a = 0; a < ND; ++a) g[a][bd] = (sp[a * fs + hp] - sp[a * fs + hm]) * inv2dx;
+        // |delta alpha_gas| = |delta alpha_l| from the encoded fractions
+        const R em = ea[hm], ep = ea[hp];
+        tg += fabs((e0 - em) + (o0 - liq_side(em))) + fabs((ep - e0) + (liq_side(ep) - o0));
+        if (CL == CL_BARO) {
+            // theta^alpha: the same variation of the vapour fraction
+            const R* va = sp + P.i_av * fs;
+            tv += fabs(va[h] - va[hm]) + fabs(va[hp] - va[h]);
+        }
+    }
+    R div = R(0);
+#pragma unroll
+    for (int a = 0; a < ND; ++a) div += g[a][a];
+    R curl2;
+    if (ND == 3) {
+        const R wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
+        curl2 = wx * wx + wy * wy + wz * wz;
+    } else {
+        const R wz = g[1][0] - g[0][1];
+        curl2 = wz * wz;
+    }
+    const R d2 = div * div;
+    const R thD = fdiv(d2, d2 + curl2 + Kc.eps_ducros);
+    return (thD > Kc.thr_ducros || tg > Kc.thr_gas || (CL == CL_BARO && tv > Kc.thr_vap)) ? 1 : 0;
+}
+
 // Eq. 2-2 stress and heat-flux terms, added to the flux F of the face between
 // halo cells hl and hl + e_D (st: halo strides): momentum -tau_{D a} with
 // tau = mu (grad u + grad u^T - 2/3 (div u) I), energy -(u . tau)_D - k_c dT/dx_D.
@@ -502,48 +549,13 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
         }
         // ---- App. D cell sensor on the tile + 1 halo
         if (P.iles) {
+            const int st3[3] = {SX, SY, SZ};
             for (int h = tid; h < HC; h += NT) {
                 const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
                 unsigned char fl = 0;
                 const bool in = hx >= 1 && hx <= vx + 2 && hy >= 1 && hy <= vy + 2 &&
                                 (ND == 2 || (hz >= 1 && hz <= vz + 2));
-                if (in) {
-                    R g[3][3];
-                    R tg = R(0), tv = R(0);
-                    const R* ea = sp + P.i_al * HC;
-                    const R e0 = ea[h];
-                    const R o0 = liq_side(e0);
-                    const int st[3] = {SX, SY, SZ};
-#pragma unroll
-                    for (int bd = 0; bd < ND; ++bd) {
-                        const int hp = h + st[bd], hm = h - st[bd];
-                        const R inv2dx = R(0.5) * ci[bd];
-#pragma unroll
-                        for (int a = 0; a < ND; ++a) g[a][bd] = (sp[a * HC + hp] - sp[a * HC + hm]) * inv2dx;
-                        // |delta alpha_gas| = |delta alpha_l| from the encoded fractions
-                        const R em = ea[hm], ep = ea[hp];
-                        tg += fabs((e0 - em) + (o0 - liq_side(em))) + fabs((ep - e0) + (liq_side(ep) - o0));
-                        if (CL == CL_BARO) {
-                            // theta^alpha: the same variation of the vapour fraction
-                            const R* va = sp + P.i_av * HC;
-                            tv += fabs(va[h] - va[hm]) + fabs(va[hp] - va[h]);
-                        }
-                    }
-                    R div = R(0);
-#pragma unroll
-                    for (int a = 0; a < ND; ++a) div += g[a][a];
-                    R curl2;
-                    if (ND == 3) {
-                        const R wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
-                        curl2 = wx * wx + wy * wy + wz * wz;
-                    } else {
-                        const R wz = g[1][0] - g[0][1];
-                        curl2 = wz * wz;
-                    }
-                    const R d2 = div * div;
-                    const R thD = fdiv(d2, d2 + curl2 + Kc.eps_ducros);
-                    fl = (thD > Kc.thr_ducros || tg > Kc.thr_gas || (CL == CL_BARO && tv > Kc.thr_vap)) ? 1 : 0;
-                }
+                if (in) fl = sensor_flag<ND, R, CL, int>(P, sp, HC, h, st3, ci);
                 sflag[h] = fl;
             }
         }

@@ -70,5 +70,9 @@ cudaError_t launch_totals(int nv, const void* q, long long ntot_q, long long off
 cudaError_t launch_dt(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err,
                       cudaStream_t s);
 cudaError_t launch_fill(double* x, int n, double v, cudaStream_t s);
+// App. D flag (0/1) of every interior cell of case icase from the primitive
+// arrays into out[ncell] (device)
+cudaError_t launch_sensor_dump(int nd, int mixed, const DevParams& P, const CaseDesc* cases, int icase,
+                               const void* prim, long long ncell, unsigned char* out, cudaStream_t s);
 
 }  // namespace tfv

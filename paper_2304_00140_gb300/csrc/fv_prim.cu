@@ -1,5 +1,7 @@
 // fv_prim.cu -- primitive-update kernel instantiations, state I/O and
 // diagnostics kernels, and the (ndim, ncomp, precision) dispatch.
+#include <algorithm>
+
 #include "fv_launch.h"
 
 namespace tfv {
@@ -81,6 +83,43 @@ int prim_occupancy(int nd, int nc, int mixed)
     if (nd == 2 && nc == 3) return mixed ? pocc<2, 3, float>() : pocc<2, 3, double>();
     if (nd == 3 && nc == 2) return mixed ? pocc<3, 2, float>() : pocc<3, 2, double>();
     return mixed ? pocc<3, 3, float>() : pocc<3, 3, double>();
+}
+
+// ------------------------------------------------------ sensor flags dump
+// App. D flag of every interior cell of one case from the primitive arrays
+// (written by a primitive pass), through the stage kernel's sensor function
+template <int ND, typename R, int CL>
+__global__ void sensor_dump_kernel(DevParams P, const CaseDesc* cases, int icase, const R* prim, long long ncell,
+                                   unsigned char* out)
+{
+    const CaseDesc& C = cases[icase];
+    const long long st[3] = {1, C.gp, (long long)C.gp * C.g[1]};
+    R ci[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ci[d] = pick<R>(C.idx[d], C.fidx[d]);
+    const R* base = prim + C.poff;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long x = i % C.n[0], y = (i / C.n[0]) % C.n[1], z = i / ((long long)C.n[0] * C.n[1]);
+        const long long h = (ND == 3 ? (z + 2) * st[2] : 0) + (y + 2) * st[1] + (x + 2);
+        out[i] = sensor_flag<ND, R, CL, long long>(P, base, P.ntot_p, h, st, ci);
+    }
+}
+
+cudaError_t launch_sensor_dump(int nd, int mixed, const DevParams& P, const CaseDesc* cases, int icase,
+                               const void* prim, long long ncell, unsigned char* out, cudaStream_t s)
+{
+    const int g = (int)std::min<long long>(4096, (ncell + 255) / 256);
+    const bool b = P.baro != 0;
+#define FV_DUMP(ND_, R_)                                                                                      \
+    (b ? sensor_dump_kernel<ND_, R_, CL_BARO><<<g, 256, 0, s>>>(P, cases, icase, static_cast<const R_*>(prim),  \
+                                                                ncell, out)                                    \
+       : sensor_dump_kernel<ND_, R_, CL_SG><<<g, 256, 0, s>>>(P, cases, icase, static_cast<const R_*>(prim),    \
+                                                              ncell, out))
+    if (nd == 2) { if (mixed) FV_DUMP(2, float); else FV_DUMP(2, double); }
+    else { if (mixed) FV_DUMP(3, float); else FV_DUMP(3, double); }
+#undef FV_DUMP
+    return cudaGetLastError();
 }
 
 // ----------------------------------------------------------- state I/O

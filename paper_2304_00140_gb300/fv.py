@@ -22,7 +22,7 @@ MAX_COMP = 3
 FV_OK, FV_ERR_ARG, FV_ERR_ALLOC, FV_ERR_CUDA, FV_ERR_EOS_NONCONV, FV_ERR_NONPHYSICAL, FV_ERR_STATE = range(7)
 FV_FP64, FV_MIXED = 0, 1
 FV_CONSERVED, FV_PRIMITIVE = 0, 1
-FV_DIAG_TOTALS, FV_DIAG_DT, FV_DIAG_TIME, FV_DIAG_ERROR, FV_DIAG_TILE = range(5)
+FV_DIAG_TOTALS, FV_DIAG_DT, FV_DIAG_TIME, FV_DIAG_ERROR, FV_DIAG_TILE, FV_DIAG_FLAGS = range(6)
 
 # every exported function of the ABI (checked against include/thinc_fv.h by the tests)
 EXPORTS = ["fv_workspace_size", "fv_init", "fv_init_ws", "fv_destroy", "fv_set_stream", "fv_set_state",
@@ -297,6 +297,13 @@ class Solver:
         return dict(tile=[int(v) for v in out[:3]], threads=int(out[3]), tune_ms=out[4:8].tolist(),
                     fused=bool(out[8] == 1), zmarch=bool(out[8] == 2), fused_ms=float(out[9]),
                     prim_ms=float(out[10]), fused_variant=int(out[11]))
+
+    def sensor_flags(self, case: int = 0) -> np.ndarray:
+        """App. D sensor flag (0/1) of every interior cell, [nz, ny, nx] uint8"""
+        w = self.cases[case]
+        out = np.zeros((w.n[2], w.n[1], w.n[0]), dtype=np.uint8)
+        self._check(self.L.fv_get_diag(self.ctx, case, FV_DIAG_FLAGS, C.c_void_p(out.ctypes.data)))
+        return out
 
     def error_word(self) -> int:
         out = C.c_int()
