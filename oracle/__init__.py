@@ -50,7 +50,8 @@ class Params(C.Structure):
                 ("d3p_coef", C.c_double), ("sigma", C.c_double), ("grad_eps", C.c_double),
                 ("in_yc", C.c_double), ("in_zc", C.c_double), ("in_radius", C.c_double),
                 ("in_T", C.c_double), ("in_Y", C.c_double * MAXC), ("in_u", C.POINTER(C.c_double)),
-                ("in_u0", C.c_double * 3), ("grav", C.c_double * 3), ("thr_vap", C.c_double)]
+                ("in_u0", C.c_double * 3), ("grav", C.c_double * 3), ("thr_vap", C.c_double),
+                ("curv", C.c_int)]
 
 
 def lib():
@@ -78,6 +79,7 @@ def lib():
             L.or_csf_source.argtypes = [P, dp, dp]
             L.or_sensor.argtypes = [P, dp, dp]
             L.or_transport.argtypes = [P, dp, dp]
+            L.or_curvature.argtypes = [P, dp, dp]
             L.or_baro_vapour.argtypes = [P, C.c_double, dp]
             L.or_baro_vapour.restype = C.c_double
             L.or_face_flux_av.argtypes = [P, C.c_int, dp, dp, dp, dp, C.c_int, dp]
@@ -123,6 +125,7 @@ def make_params(w, inflow_u: np.ndarray | None = None) -> Params:
     for d, g in enumerate(s.get("gravity", (0.0, 0.0, 0.0))):
         P.grav[d] = g
     P.thr_vap = s.get("thr_vap", 0.4)
+    P.curv = int(s.get("curvature", 0))
     if w.inflow:
         f = w.inflow
         P.in_yc, P.in_zc, P.in_radius, P.in_T = f["yc"] - w.lo[1], f["zc"] - w.lo[2], f["radius"], f["T"]
@@ -202,6 +205,13 @@ class Oracle:
         out = np.zeros((2,) + self.shape[1:])
         _check(self.L.or_transport(C.byref(self.P), _ptr(q), _ptr(out)), "transport")
         return out
+
+    def curvature(self, q):
+        """curvature the CSF source uses, per interior cell [nz, ny, nx]"""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        k = np.zeros(self.shape[1:])
+        _check(self.L.or_curvature(C.byref(self.P), _ptr(q), _ptr(k)), "curvature")
+        return k
 
     def sensor(self, q):
         q = np.ascontiguousarray(q, dtype=np.float64)

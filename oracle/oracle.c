@@ -965,14 +965,69 @@ static double smooth_at(const or_params* P, const box_t* B, int i, int j, int k)
     return s / norm;   /* norm = 16 in 2D, 64 in 3D */
 }
 
-static void csf_cell(const or_params* P, const box_t* B, int i, int j, int k, double* S)
+/* Sec. 3.5, the height-function option: columns of liquid fraction summed
+ * along the axis where alpha varies most give heights H; with H' and H'' the
+ * central differences of H across the neighbouring columns,
+ * kappa = -H'' / (1 + H'^2)^{3/2} in 2D (H counts liquid, so the sign does
+ * not depend on which side the liquid lies) and, in 3D,
+ * kappa = -(H_xx (1 + H_y^2) + H_yy (1 + H_x^2) - 2 H_xy H_x H_y)
+ *         / (1 + H_x^2 + H_y^2)^{3/2}.
+ * READING: the paper lists 3x3, 3x5, 3x7 windows (3x3x3 ... 3x3x7 in 3D); the
+ * columns here have 5 cells (3x5, 3x3x5), the two-cell halo of the stage;
+ * the axis is the one with the largest central difference of the
+ * unsmoothed alpha; alpha is the liquid volume fraction, not smoothed. */
+static double hf_curvature(const or_params* P, const box_t* B, int i, int j, int k)
+{
+    const int nd = P->ndim;
+    int c[3] = {i, j, k}, dir = 0;
+    double gmax = -1.0;
+    for (int d = 0; d < nd; ++d) {
+        int p[3] = {i, j, k}, m[3] = {i, j, k};
+        p[d] += 1;
+        m[d] -= 1;
+        double g = fabs(B->al[bidx(B, p[0], p[1], p[2])] - B->al[bidx(B, m[0], m[1], m[2])]) / (2.0 * P->dx[d]);
+        if (g > gmax) { gmax = g; dir = d; }
+    }
+    int t[2] = {0, 0}, nt = 0;
+    for (int d = 0; d < nd; ++d)
+        if (d != dir) t[nt++] = d;
+    double H[3][3] = {{0}};
+    for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b) {
+            if (nt < 2 && b != 0) continue;
+            double h = 0.0;
+            for (int m = -2; m <= 2; ++m) {
+                int q[3] = {c[0], c[1], c[2]};
+                q[dir] += m;
+                q[t[0]] += a;
+                if (nt == 2) q[t[1]] += b;
+                h += B->al[bidx(B, q[0], q[1], q[2])] * P->dx[dir];
+            }
+            H[a + 1][b + 1] = h;
+        }
+    const double d1 = P->dx[t[0]];
+    const double Hx = (H[2][1] - H[0][1]) / (2.0 * d1);
+    const double Hxx = (H[2][1] + H[0][1] - 2.0 * H[1][1]) / (d1 * d1);
+    if (nt < 2) return -Hxx / pow(1.0 + Hx * Hx, 1.5);
+    const double d2 = P->dx[t[1]];
+    const double Hy = (H[1][2] - H[1][0]) / (2.0 * d2);
+    const double Hyy = (H[1][2] + H[1][0] - 2.0 * H[1][1]) / (d2 * d2);
+    const double Hxy = (H[2][2] - H[2][0] - H[0][2] + H[0][0]) / (4.0 * d1 * d2);
+    return -(Hxx * (1.0 + Hy * Hy) + Hyy * (1.0 + Hx * Hx) - 2.0 * Hxy * Hx * Hy) /
+           pow(1.0 + Hx * Hx + Hy * Hy, 1.5);
+}
+
+/* one CSF cell: kappa (vertex normals of the smoothed fraction, or the
+ * height function) and the mean vertex gradient of the unsmoothed fraction */
+static void csf_parts(const or_params* P, const box_t* B, int i, int j, int k, double* kappa_out, double* galpha)
 {
     const int nd = P->ndim;
     const int nvtx = 1 << nd;
     const double scale = (double)(1 << (nd - 1));
-    double kappa = 0.0, galpha[3] = {0.0, 0.0, 0.0};
+    double kappa = 0.0;
     double dxmin = P->dx[0];
     for (int d = 1; d < nd; ++d) dxmin = fmin(dxmin, P->dx[d]);
+    for (int d = 0; d < 3; ++d) galpha[d] = 0.0;
     int ijk[3] = {i, j, k};
     for (int vtx = 0; vtx < nvtx; ++vtx) {
         int voff[3] = {vtx & 1, (vtx >> 1) & 1, (vtx >> 2) & 1};
@@ -1002,6 +1057,14 @@ static void csf_cell(const or_params* P, const box_t* B, int i, int j, int k, do
             galpha[d] += gu[d] / nvtx;
         }
     }
+    *kappa_out = (P->curv == 1) ? hf_curvature(P, B, i, j, k) : kappa;
+}
+
+static void csf_cell(const or_params* P, const box_t* B, int i, int j, int k, double* S)
+{
+    const int nd = P->ndim;
+    double kappa, galpha[3];
+    csf_parts(P, B, i, j, k, &kappa, galpha);
     size_t b0 = bidx(B, i, j, k);
     double udg = 0.0;
     for (int d = 0; d < nd; ++d) {
@@ -1341,4 +1404,26 @@ int or_transport(const or_params* P, const double* q, double* out)
         mix_transport(P, al, &out[c], &out[nc + c]);
     }
     return OR_OK;
+}
+
+int or_curvature(const or_params* P, const double* q, double* kappa)
+{
+    const int nd = P->ndim;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    int st = box_fill(P, q, &B, blo, bhi);
+    if (!st)
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) {
+                    double g[3];
+                    csf_parts(P, &B, i, j, k, &kappa[cidx(P, i, j, k)], g);
+                }
+    box_free(&B);
+    return st;
 }

@@ -73,6 +73,8 @@ typedef struct {
     double in_u0[3];                  /* uniform inflow velocity used when in_u is NULL */
     double grav[3];                   /* body force per unit mass g (m/s^2), Eq. 2-2 Q */
     double thr_vap;                   /* App. D vapour-fraction threshold (barotropic closure) */
+    int curv;                         /* CSF curvature: 0 Gaussian-smoothed vertex normals,
+                                         1 height function (Sec. 3.5) */
 } or_params;
 
 /* closure, pointwise (Yt = the N-1 tracked mass fractions) */
@@ -104,6 +106,8 @@ int or_dt(const or_params* P, const double* q, double cfl, double* dt);
 int or_step(const or_params* P, double* q, int nsteps, double cfl, double* t);
 void or_totals(const or_params* P, const double* q, double* out /* nv */);
 /* CSF source on the interior (S[d+1][cells]: momentum then energy) */
+/* curvature used by the CSF source on the interior (kappa[cells]) */
+int or_curvature(const or_params* P, const double* q, double* kappa);
 int or_csf_source(const or_params* P, const double* q, double* S);
 /* App. D cell sensor f (0/1) on the interior */
 int or_sensor(const or_params* P, const double* q, double* f);

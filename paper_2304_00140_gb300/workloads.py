@@ -109,7 +109,7 @@ def default_scheme(**kw) -> Dict:
              lim_vel=LIM_KOREN, lim_scalar=LIM_MINMOD,
              thr_ducros=0.95, thr_gas=0.4, eps_ducros=1e-20, d3p_coef=1.0,
              sigma=0.0, grad_eps=1e-5, precision=0, p_ref=1e5, T_ref=300.0,
-             gravity=(0.0, 0.0, 0.0), thr_vap=0.4)
+             gravity=(0.0, 0.0, 0.0), thr_vap=0.4, curvature=0)
     s.update(kw)
     return s
 
