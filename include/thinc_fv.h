@@ -134,6 +134,9 @@ typedef struct {
     double gravity[3];           /* body force per unit mass (m/s^2) of Eq. 2-2: source rho g
                                     (momentum) and rho u . g (energy); zero = off */
     double thr_vap;              /* App. D vapour-fraction sensor threshold (FV_BARO) */
+    int curvature;               /* CSF curvature: 0 vertex normals of the Gaussian-smoothed
+                                    fraction (Sec. 3.5, Eq. 3-9/3-10), 1 the height function
+                                    of 5-cell columns (the Sec. 3.5 option) */
 } fv_eos;
 
 typedef struct fv_ctx fv_ctx;

@@ -975,7 +975,9 @@ static double smooth_at(const or_params* P, const box_t* B, int i, int j, int k)
  * READING: the paper lists 3x3, 3x5, 3x7 windows (3x3x3 ... 3x3x7 in 3D); the
  * columns here have 5 cells (3x5, 3x3x5), the two-cell halo of the stage;
  * the axis is the one with the largest central difference of the
- * unsmoothed alpha; alpha is the liquid volume fraction, not smoothed. */
+ * unsmoothed alpha (within a relative 1e-12 the lower axis, so that a
+ * symmetric tie does not depend on rounding); alpha is the liquid volume
+ * fraction, not smoothed. */
 static double hf_curvature(const or_params* P, const box_t* B, int i, int j, int k)
 {
     const int nd = P->ndim;
@@ -986,7 +988,7 @@ static double hf_curvature(const or_params* P, const box_t* B, int i, int j, int
         p[d] += 1;
         m[d] -= 1;
         double g = fabs(B->al[bidx(B, p[0], p[1], p[2])] - B->al[bidx(B, m[0], m[1], m[2])]) / (2.0 * P->dx[d]);
-        if (g > gmax) { gmax = g; dir = d; }
+        if (g > gmax * (1.0 + 1e-12)) { gmax = g; dir = d; }   /* near-ties go to the lower axis */
     }
     int t[2] = {0, 0}, nt = 0;
     for (int d = 0; d < nd; ++d)

@@ -221,6 +221,7 @@ static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm,
     if (eos->precision != FV_FP64 && eos->precision != FV_MIXED) { why = "bad precision"; return FV_ERR_ARG; }
     if (eos->thinc && !(eos->beta > 0.0)) { why = "THINC beta must be positive"; return FV_ERR_ARG; }
     if (!(eos->sigma >= 0.0)) { why = "sigma must be >= 0"; return FV_ERR_ARG; }
+    if (eos->curvature != 0 && eos->curvature != 1) { why = "curvature must be 0 or 1"; return FV_ERR_ARG; }
     bool visc = false;
     for (int k = 0; k < cm->ncomp; ++k) {
         const fv_component& c = cm->comp[k];
@@ -266,6 +267,7 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
     P.lim_vel = eos->lim_vel;
     P.lim_scalar = eos->lim_scalar;
     P.csf = eos->sigma > 0.0 ? 1 : 0;
+    P.hf = eos->curvature == 1 ? 1 : 0;
     P.visc = has_visc(cm) ? 1 : 0;
     P.grav = has_grav(eos) ? 1 : 0;
     P.baro = is_baro(cm) ? 1 : 0;
@@ -933,8 +935,8 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
-    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav;
-    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav;
+    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav && !x->P.hf;
+    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav && !x->P.hf;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }

@@ -81,6 +81,7 @@ struct DevParams {
     int iles, thinc, lim_vel, lim_scalar;
     int csf, aux_rc, aux_al, i_rho, i_c, i_al;
     int visc, grav;      // viscous / heat-flux terms on; gravity source on
+    int hf;              // CSF curvature from the height function (Sec. 3.5 option)
     int i_mu, i_kc;      // primitive-array fields of the mixture viscosity and conductivity
     double beta, thinc_eps, thinc_gamma, tb, icb, itb;
     double thr_ducros, thr_gas, eps_ducros, d3p_coef;

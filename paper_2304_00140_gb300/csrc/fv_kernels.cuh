@@ -385,6 +385,53 @@ __device__ __forceinline__ unsigned char sensor_flag(const DevParams& P, const R
     return (thD > Kc.thr_ducros || tg > Kc.thr_gas || (CL == CL_BARO && tv > Kc.thr_vap)) ? 1 : 0;
 }
 
+// Height-function curvature (Sec. 3.5 option) of cell hc from the encoded
+// liquid fraction ea (strides st): 5-cell columns along the axis where the
+// fraction varies most (a near-tie within 1e-12 goes to the lower axis), heights
+// H over the 3 (3x3) neighbouring columns, kappa = -H''/(1+H'^2)^{3/2} in 2D and
+// -(H_xx (1+H_y^2) + H_yy (1+H_x^2) - 2 H_xy H_x H_y)/(1+H_x^2+H_y^2)^{3/2} in 3D.
+template <int ND, typename R>
+__device__ __forceinline__ R hf_kappa(const R* ea, int hc, const int* st, const R* cdx)
+{
+    auto A = [&](int h) { const R e = ea[h]; return e + liq_side(e); };
+    int dir = 0;
+    R gmax = R(-1);
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        const R g = fdiv(fabs(A(hc + st[d]) - A(hc - st[d])), R(2) * cdx[d]);
+        if (g > gmax * R(1.0 + 1e-12)) { gmax = g; dir = d; }
+    }
+    // transverse axes t0 (and t1 in 3D)
+    const int t0 = dir == 0 ? 1 : 0;
+    const int t1 = dir == 2 ? 1 : 2;
+    const int sd = st[dir], s0 = st[t0], s1 = ND == 3 ? st[t1] : 0;
+    R H[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (ND == 2 && b != 1) { H[a][b] = R(0); continue; }
+            const int c = hc + (a - 1) * s0 + (b - 1) * s1;
+            R h = R(0);
+#pragma unroll
+            for (int m = -2; m <= 2; ++m) h += A(c + m * sd) * cdx[dir];
+            H[a][b] = h;
+        }
+    const R d1 = cdx[t0];
+    const R Hx = fdiv(H[2][1] - H[0][1], R(2) * d1);
+    const R Hxx = fdiv(H[2][1] + H[0][1] - R(2) * H[1][1], d1 * d1);
+    if (ND == 2) {
+        const R q = R(1) + Hx * Hx;
+        return -fdiv(Hxx, q * sq_rt(q));
+    }
+    const R d2 = cdx[t1];
+    const R Hy = fdiv(H[1][2] - H[1][0], R(2) * d2);
+    const R Hyy = fdiv(H[1][2] + H[1][0] - R(2) * H[1][1], d2 * d2);
+    const R Hxy = fdiv(H[2][2] - H[2][0] - H[0][2] + H[0][0], R(4) * d1 * d2);
+    const R q = R(1) + Hx * Hx + Hy * Hy;
+    return -fdiv(Hxx * (R(1) + Hy * Hy) + Hyy * (R(1) + Hx * Hx) - R(2) * Hxy * Hx * Hy, q * sq_rt(q));
+}
+
 // Eq. 2-2 stress and heat-flux terms, added to the flux F of the face between
 // halo cells hl and hl + e_D (st: halo strides): momentum -tau_{D a} with
 // tau = mu (grad u + grad u^T - 2/3 (div u) I), energy -(u . tau)_D - k_c dT/dx_D.
@@ -731,6 +778,10 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
                             ga[d] += gu[d] * ci[d] * R(2.0 / nc);
                         }
                         (void)vi;
+                    }
+                    if (P.hf) {
+                        const int st3[3] = {SX, SY, SZ};
+                        kappa = hf_kappa<ND, R>(al, hc, st3, cdx);
                     }
                     R udg = R(0);
 #pragma unroll
