@@ -1,6 +1,7 @@
 // fv_prim.cu -- primitive-update kernel instantiations, state I/O and
 // diagnostics kernels, and the (ndim, ncomp, precision) dispatch.
 #include <algorithm>
+#include <cstdint>
 
 #include "fv_launch.h"
 
@@ -188,31 +189,102 @@ __global__ void cons_to_prim_kernel(IoArgs A)
 // ntot_q, case offset off).  One grid row (blockIdx.y) per field.  `in` /
 // `out` may be device memory or page-locked host memory mapped into the
 // device's address space (read and written over the host link directly).
-__global__ void split_kernel(const double* in, long long ncell, float2* reg, long long ntot_q, long long off)
+// Over the host link a thread keeps several independent 16-byte accesses in
+// flight (IO_UNROLL pairs of values per iteration) when every field starts on
+// a 16-byte boundary (even cell counts and offsets); otherwise one value at a
+// time.
+constexpr int IO_UNROLL = 4;
+__device__ __forceinline__ float4 ff_pair(double2 x)
+{
+    const float2 a = ff_from_double(x.x), b = ff_from_double(x.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ double2 dd_pair(float4 x) { return make_double2(qv_d(make_float2(x.x, x.y)), qv_d(make_float2(x.z, x.w))); }
+
+__global__ void split_kernel(const double* __restrict__ in, long long ncell, float2* __restrict__ reg, long long ntot_q,
+                             long long off, int vec)
 {
     const int v = blockIdx.y;
     const double* src = in + v * ncell;
     float2* dst = reg + v * ntot_q + off;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
-        dst[c] = ff_from_double(src[c]);
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    if (!vec) {
+        for (long long c = t0; c < ncell; c += nt) dst[c] = ff_from_double(src[c]);
+        return;
+    }
+    const long long np = ncell / 2;
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    float4* d2 = reinterpret_cast<float4*>(dst);
+    for (long long c = t0; c < np; c += nt * IO_UNROLL) {
+        double2 x[IO_UNROLL];
+#pragma unroll
+        for (int u = 0; u < IO_UNROLL; ++u) {
+            const long long i = c + u * nt;
+            x[u] = i < np ? s2[i] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < IO_UNROLL; ++u) {
+            const long long i = c + u * nt;
+            if (i < np) d2[i] = ff_pair(x[u]);
+        }
+    }
 }
-__global__ void join_kernel(const float2* reg, long long ntot_q, long long off, long long ncell, double* out)
+__global__ void join_kernel(const float2* __restrict__ reg, long long ntot_q, long long off, long long ncell,
+                            double* __restrict__ out, int vec)
 {
     const int v = blockIdx.y;
     const float2* src = reg + v * ntot_q + off;
     double* dst = out + v * ncell;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
-        dst[c] = qv_d(src[c]);
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    if (!vec) {
+        for (long long c = t0; c < ncell; c += nt) dst[c] = qv_d(src[c]);
+        return;
+    }
+    const long long np = ncell / 2;
+    const float4* s2 = reinterpret_cast<const float4*>(src);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    for (long long c = t0; c < np; c += nt * IO_UNROLL) {
+        float4 x[IO_UNROLL];
+#pragma unroll
+        for (int u = 0; u < IO_UNROLL; ++u) {
+            const long long i = c + u * nt;
+            x[u] = i < np ? s2[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < IO_UNROLL; ++u) {
+            const long long i = c + u * nt;
+            if (i < np) d2[i] = dd_pair(x[u]);
+        }
+    }
 }
 // FP64 registers: plain field copies in (to_reg = 1) or out
-__global__ void copy_fields_kernel(const double* in, long long in_stride, double* out, long long out_stride,
-                                   long long ncell)
+__global__ void copy_fields_kernel(const double* __restrict__ in, long long in_stride, double* __restrict__ out,
+                                   long long out_stride, long long ncell, int vec)
 {
     const int v = blockIdx.y;
     const double* src = in + v * in_stride;
     double* dst = out + v * out_stride;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x)
-        dst[c] = src[c];
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, nt = (long long)gridDim.x * blockDim.x;
+    if (!vec) {
+        for (long long c = t0; c < ncell; c += nt) dst[c] = src[c];
+        return;
+    }
+    const long long np = ncell / 2;
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    for (long long c = t0; c < np; c += nt * IO_UNROLL) {
+        double2 x[IO_UNROLL];
+#pragma unroll
+        for (int u = 0; u < IO_UNROLL; ++u) {
+            const long long i = c + u * nt;
+            x[u] = i < np ? s2[i] : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int u = 0; u < IO_UNROLL; ++u) {
+            const long long i = c + u * nt;
+            if (i < np) d2[i] = x[u];
+        }
+    }
 }
 
 // All cases at once: `in` / `out` hold each case's [nv][ncell] block in case
@@ -261,22 +333,39 @@ static dim3 field_grid(long long ncell, int nv)
     return dim3((unsigned)g, (unsigned)nv);
 }
 
+// the 16-byte path: both arrays' field starts on 16-byte boundaries
+static int io_vec(const void* a, const void* b, long long sa, long long sb, long long esize)
+{
+    const uintptr_t m = reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b);
+    return ((m & 15) == 0 && ((sa * esize) & 15) == 0 && ((sb * esize) & 15) == 0) ? 1 : 0;
+}
+static dim3 io_field_grid(long long ncell, int nv, int vec)
+{
+    const long long n = vec ? (ncell / 2 + IO_UNROLL - 1) / IO_UNROLL : ncell;
+    return field_grid(n, nv);
+}
 cudaError_t launch_split(int nv, const double* in, long long ncell, void* reg, long long ntot_q, long long off,
                          cudaStream_t s)
 {
-    split_kernel<<<field_grid(ncell, nv), 256, 0, s>>>(in, ncell, static_cast<float2*>(reg), ntot_q, off);
+    float2* r = static_cast<float2*>(reg) + off;
+    const int vec = io_vec(in, r, ncell, ntot_q, 8) && (ncell % 2 == 0);
+    split_kernel<<<io_field_grid(ncell, nv, vec), 256, 0, s>>>(in, ncell, static_cast<float2*>(reg), ntot_q, off, vec);
     return cudaGetLastError();
 }
 cudaError_t launch_join(int nv, const void* reg, long long ntot_q, long long off, long long ncell, double* out,
                         cudaStream_t s)
 {
-    join_kernel<<<field_grid(ncell, nv), 256, 0, s>>>(static_cast<const float2*>(reg), ntot_q, off, ncell, out);
+    const float2* r = static_cast<const float2*>(reg) + off;
+    const int vec = io_vec(r, out, ntot_q, ncell, 8) && (ncell % 2 == 0);
+    join_kernel<<<io_field_grid(ncell, nv, vec), 256, 0, s>>>(static_cast<const float2*>(reg), ntot_q, off, ncell, out,
+                                                               vec);
     return cudaGetLastError();
 }
 cudaError_t launch_copy_fields(int nv, const double* in, long long in_stride, double* out, long long out_stride,
                                long long ncell, cudaStream_t s)
 {
-    copy_fields_kernel<<<field_grid(ncell, nv), 256, 0, s>>>(in, in_stride, out, out_stride, ncell);
+    const int vec = io_vec(in, out, in_stride, out_stride, 8) && (ncell % 2 == 0);
+    copy_fields_kernel<<<io_field_grid(ncell, nv, vec), 256, 0, s>>>(in, in_stride, out, out_stride, ncell, vec);
     return cudaGetLastError();
 }
 

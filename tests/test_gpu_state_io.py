@@ -14,9 +14,10 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
 @pytest.mark.parametrize("kind", [fv.FV_CONSERVED, fv.FV_PRIMITIVE])
-def test_state_io_paths_agree(precision, kind):
+@pytest.mark.parametrize("n", [(37, 23), (36, 22)])   # odd cell count: one value a time; even: 16-byte accesses
+def test_state_io_paths_agree(precision, kind, n):
     import torch
-    w = wl.random_state(n=(37, 23), bc=[[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2, [0, 0]])
+    w = wl.random_state(n=n, bc=[[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2, [0, 0]])
     s = fv.Solver(w, precision=precision)
     s.set_state(w.primitives(), kind=fv.FV_PRIMITIVE)
     x = s.get_state(kind)
