@@ -13,8 +13,11 @@
  * Table 4.2; App. D Eq. D.1-D.3), thermodynamic-dependent update
  * (Eq. 3-5/3-6), all-Mach Riemann flux (Eq. 3-1/3-2; D.5/D.6), viscous
  * stress and heat conduction fluxes (Eq. 2-2, mixture viscosity Eq. 2-8),
- * CSF and gravity sources (Sec. 2.3, Sec. 3.5, Eq. 3-9/3-10; Eq. 2-2 Q),
- * flux divergence and the low-storage Runge-Kutta update (Sec. 3.1).
+ * CSF and gravity sources (Sec. 2.3, Sec. 3.5, Eq. 3-9/3-10, the
+ * height-function option; Eq. 2-2 Q), flux divergence and the low-storage
+ * Runge-Kutta update (Sec. 3.1).  Closures: stiffened / ideal gas
+ * (App. A.1), Peng-Robinson (App. A.2.1), the barotropic model of Sec. 2.2
+ * with the liquid-vapour density THINC of Sec. 3.4.
  *
  * Layouts: conserved state q and primitive state W are SoA float64 arrays
  * [nv][nz][ny][nx], x fastest, interior cells only.
