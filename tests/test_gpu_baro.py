@@ -142,3 +142,33 @@ def test_vapour_collapse_long_run(precision):
     s.step(500, w.cfl)
     q = s.get_state()
     assert np.all(np.isfinite(q)) and q[0].min() > 0
+
+
+def test_vapour_collapse_full_size_windows():
+    """the 1000 x 1000 vapour collapse in the configuration the benchmark
+    times: one GPU step (FP64) against the oracle on windows at the top and
+    the bottom of the bubble, at the wall and at an outflow corner"""
+    from tests.helpers import oracle_step_window
+    w = wl.bubble_collapse("vapour", n=(1000, 1000))
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=fv.FV_FP64)
+    s.set_state(q)
+    dt = 0.4 * 4e-6 / (2 * 1460.0)
+    s.step_dt(dt)
+    got = s.get_state()
+    nx, ny = w.n[0], w.n[1]
+    jt = int((440e-6 + 400e-6) / w.dx[1])           # top of the bubble
+    jb = int((440e-6 - 400e-6) / w.dx[1])           # bottom, 10 cells above the wall
+    wins = [((nx // 2 - 8, jt - 8, 0), (nx // 2 + 8, jt + 8, 1)),
+            ((nx // 2 - 8, max(jb - 6, 0), 0), (nx // 2 + 8, jb + 8, 1)),
+            ((nx // 2 + 60, 0, 0), (nx // 2 + 76, 6, 1)),
+            ((nx - 7, ny - 9, 0), (nx, ny, 1))]
+    scale = np.abs(got).reshape(q.shape[0], -1).max(axis=1)
+    scale[1:3] = np.sqrt(got[1] ** 2 + got[2] ** 2).max()
+    scale[4] = 1.0                                   # no gas anywhere
+    for lo, hi in wins:
+        ref = oracle_step_window(o, q, dt, lo, hi)
+        sl = (slice(None), 0, slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / scale
+        assert np.all(d < 1e-11), (lo, d)

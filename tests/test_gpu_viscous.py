@@ -145,3 +145,36 @@ def test_viscous_rejected_for_peng_robinson():
     with pytest.raises(fv.FVError) as ei:
         fv.Solver(w, precision=fv.FV_FP64)
     assert ei.value.status == fv.FV_ERR_ARG
+
+
+def test_rising_bubble_full_size_windows():
+    """the rising bubble (case 2) at 1024 x 2048, the size the benchmark
+    times: one GPU step (FP64) against the oracle on windows at the
+    bubble's top and side, at a wall and at a corner.  Density, energy and
+    mass fraction to 1e-12 of their scale; the momentum, one step's residual
+    of the hydrostatic and Laplace balances, to 1e-7 of its scale (reading
+    26: a 1e-16 input perturbation moves it by about that)"""
+    from tests.helpers import oracle_step_window
+    w = wl.rising_bubble(2, n=(1024, 2048))
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=fv.FV_FP64)
+    s.set_state(q)
+    dt = 0.4 * w.dx[0] / (2 * 1460.0)
+    s.step_dt(dt)
+    got = s.get_state()
+    nx, ny = w.n[0], w.n[1]
+    jt = int(0.75 / w.dx[1])
+    ib = int(0.25 / w.dx[0])
+    wins = [((nx // 2 - 8, jt - 8, 0), (nx // 2 + 8, jt + 8, 1)),
+            ((ib - 8, ny // 4 - 8, 0), (ib + 8, ny // 4 + 8, 1)),
+            ((0, ny // 2, 0), (6, ny // 2 + 10, 1)),
+            ((nx - 7, ny - 9, 0), (nx, ny, 1))]
+    scale = np.abs(got).reshape(q.shape[0], -1).max(axis=1)
+    scale[1:3] = np.sqrt(got[1] ** 2 + got[2] ** 2).max()
+    tol = np.array([1e-12, 1e-7, 1e-7, 1e-12, 1e-12])
+    for lo, hi in wins:
+        ref = oracle_step_window(o, q, dt, lo, hi)
+        sl = (slice(None), 0, slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / scale
+        assert np.all(d < tol), (lo, d)
