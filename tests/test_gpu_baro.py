@@ -167,8 +167,12 @@ def test_vapour_collapse_full_size_windows():
     scale = np.abs(got).reshape(q.shape[0], -1).max(axis=1)
     scale[1:3] = np.sqrt(got[1] ** 2 + got[2] ** 2).max()
     scale[4] = 1.0                                   # no gas anywhere
+    # the passive energy starts at zero (e = 0, at rest): after one step it is
+    # the divergence of p* u* with p ~ 1e7 Pa, a cancellation that the
+    # relative bound allows for with 1e-10
+    tol = np.array([1e-11, 1e-11, 1e-11, 1e-10, 1e-11])
     for lo, hi in wins:
         ref = oracle_step_window(o, q, dt, lo, hi)
         sl = (slice(None), 0, slice(lo[1], hi[1]), slice(lo[0], hi[0]))
         d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / scale
-        assert np.all(d < 1e-11), (lo, d)
+        assert np.all(d < tol), (lo, d)
