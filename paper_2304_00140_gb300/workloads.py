@@ -369,8 +369,11 @@ def _init_collapse(w: Workload):
     liquid-vapour mixture at the pressure p_b that the barotropic law gives
     for the capped vapour fraction."""
     P = w.params
-    X, Y, _ = _grid(w)
-    r = np.sqrt(X ** 2 + (Y - P["H"]) ** 2)
+    X, Y, Z = _grid(w)
+    r2 = X ** 2 + (Y - P["H"]) ** 2
+    if w.ndim == 3:
+        r2 = r2 + Z ** 2
+    r = np.sqrt(r2)
     h = tanh_indicator(r - P["R"], P["width"] * w.dx[0])      # bubble indicator
     pb, pinf = P["p_b"], P["p_inf"]
     ramp = pinf + (P["R"] / np.maximum(r, P["R"])) * (pb - pinf)
@@ -378,7 +381,7 @@ def _init_collapse(w: Workload):
     W[w.ndim] = h * pb + (1.0 - h) * ramp
     W[w.ndim + 1] = P["e"]
     W[w.ndim + 2] = h if P["gas"] else 0.0
-    return W
+    return _split_gas(W, w)
 
 
 _INIT = {"collapse": _init_collapse, "bubble": _init_bubble, "pr_drop": _init_pr_drop, "column": _init_column, "shock_bubble": _init_shock_bubble,
@@ -555,6 +558,35 @@ def rising_bubble(case=1, n=None, steps=1000, **scheme):
 # and vapour densities, liquid sound speed; air as the non-condensable gas
 WATER_BARO = comp_baro_liquid(1342.0, 999.7, 0.0100, 1450.0)
 AIR_BARO = comp_baro_gas(287.05, 293.15)
+
+
+def bubble_collapse3d(kind="gas", n=(48, 48, 48), p_inf=1e7, gases=1, steps=200, **scheme):
+    """3D form of the bubble collapse near a wall: the 4 x 4 x 4 mm box
+    [-2, 2] x [0, 4] x [-2, 2] mm, bubble centred at (0, H, 0), wall at
+    y = 0, outflow elsewhere.  gases = 2 splits the non-condensable gas
+    into air and a second ideal gas (R T_ref = 189 * 293.15, CO2-like) in
+    equal mass shares."""
+    w = bubble_collapse(kind, n=(n[0], n[1]), p_inf=p_inf, steps=steps, **scheme)
+    L = 4e-3
+    w.name = f"{kind}_bubble_collapse3d_{n[0]}x{n[1]}x{n[2]}"
+    w.ndim = 3
+    w.n = [n[0], n[1], n[2]]
+    w.lo = [-0.5 * L, 0.0, -0.5 * L]
+    w.hi = [0.5 * L, L * n[1] / n[0], 0.5 * L * n[2] / n[0]]
+    w.bc = [[BC_OUTFLOW] * 2, [BC_REFLECT, BC_OUTFLOW], [BC_OUTFLOW] * 2]
+    if gases == 2:
+        w.comps = [AIR_BARO, comp_baro_gas(188.9, 293.15), w.comps[1]]
+        w.liquid = 2
+    return w
+
+
+def _split_gas(W, w):
+    """equal mass shares of the two gases (3D, gases = 2)"""
+    if w.ncomp == 3:
+        g = W[w.ndim + 2].copy()
+        W[w.ndim + 2] = 0.5 * g
+        W[w.ndim + 3] = 0.5 * g
+    return W
 
 
 def bubble_collapse(kind="vapour", n=(1000, 1000), p_inf=1e7, steps=2000, **scheme):

@@ -53,6 +53,11 @@ CASES = {
     "vapour_sheared_iles": lambda: _sheared("vapour", 1),
     "vapour_other_limiters": lambda: (lambda w: (w, w.primitives()))(
         wl.bubble_collapse("vapour", n=(33, 29), lim_vel=wl.LIM_VANLEER, lim_scalar=wl.LIM_MC)),
+    "gas_collapse_3d": lambda: (lambda w: (w, w.primitives()))(wl.bubble_collapse3d("gas", n=(20, 18, 16))),
+    "two_gases_collapse_3d": lambda: (lambda w: (w, w.primitives()))(
+        wl.bubble_collapse3d("gas", n=(21, 17, 18), gases=2)),
+    "vapour_collapse_3d_iles": lambda: (lambda w: (w, w.primitives()))(
+        wl.bubble_collapse3d("vapour", n=(20, 18, 16), p_inf=2e5, iles=1)),
 }
 
 
