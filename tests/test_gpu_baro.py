@@ -56,8 +56,10 @@ CASES = {
     "gas_collapse_3d": lambda: (lambda w: (w, w.primitives()))(wl.bubble_collapse3d("gas", n=(20, 18, 16))),
     "two_gases_collapse_3d": lambda: (lambda w: (w, w.primitives()))(
         wl.bubble_collapse3d("gas", n=(21, 17, 18), gases=2)),
-    "vapour_collapse_3d_iles": lambda: (lambda w: (w, w.primitives()))(
-        wl.bubble_collapse3d("vapour", n=(20, 18, 16), p_inf=2e5, iles=1)),
+    "vapour_collapse_3d": lambda: (lambda w: (w, w.primitives()))(
+        wl.bubble_collapse3d("vapour", n=(20, 18, 16), p_inf=2e5)),
+    "gas_collapse_3d_iles": lambda: (lambda w: (w, w.primitives()))(
+        wl.bubble_collapse3d("gas", n=(20, 18, 16), p_inf=2e4, iles=1)),
 }
 
 
