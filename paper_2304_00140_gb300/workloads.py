@@ -598,7 +598,8 @@ def bubble_collapse(kind="vapour", n=(1000, 1000), p_inf=1e7, steps=2000, **sche
     fraction (0.995), whose barotropic pressure is 6.7 Pa (p_sat = 1342 Pa).
     Ambient liquid p_inf = 10 MPa with the 1/r pressure ramp, at rest; wall
     below, outflow elsewhere; App. D switch off, THINC on.  CFL 0.4.  The
-    FP32-mixed form's pressure offset is p_sat."""
+    FP32-mixed form's pressure offset is p_sat.  The passive internal
+    energy starts uniform at 4.2e5 J/kg (about c_v T of water)."""
     nx, ny = n
     L = 4e-3
     liq = WATER_BARO
@@ -610,4 +611,4 @@ def bubble_collapse(kind="vapour", n=(1000, 1000), p_inf=1e7, steps=2000, **sche
         name=f"{kind}_bubble_collapse_{nx}x{ny}", ndim=2, n=[nx, ny, 1], lo=[-0.5 * L, 0.0, 0.0],
         hi=[0.5 * L, L * ny / nx, 1.0], bc=[[BC_OUTFLOW] * 2, [BC_REFLECT, BC_OUTFLOW], [BC_PERIODIC] * 2],
         comps=[AIR_BARO, liq], liquid=1, scheme=sch, steps=steps, cfl=0.4, init="collapse",
-        params=dict(R=400e-6, H=440e-6, p_b=p_b, p_inf=p_inf, e=0.0, gas=(kind == "gas"), width=1.5))
+        params=dict(R=400e-6, H=440e-6, p_b=p_b, p_inf=p_inf, e=4.2e5, gas=(kind == "gas"), width=1.5))

@@ -65,6 +65,10 @@ CASES = {
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_baro_parity_fp64(name):
+    """bound 1e-11, or three times the oracle's own spread under a 1e-16
+    relative perturbation of its input where that is larger (the momentum of
+    a collapse that starts at rest is the small residual of large pressure
+    forces)"""
     w, W = CASES[name]()
     o = oracle.Oracle(w)
     q = o.prim_to_cons(W)
@@ -72,13 +76,17 @@ def test_baro_parity_fp64(name):
     s.set_state(q)
     dt = 0.3 * o.dt(q, 1.0)
     ref = q
+    pert = q * (1 + 1e-16 * np.random.default_rng(20230401).standard_normal(q.shape))
     for _ in range(3):
         s.step_dt(dt)
         ref = oracle_step_dt(o, ref, dt)
+        pert = oracle_step_dt(o, pert, dt)
     got = s.get_state()
     assert not s.tile()["fused"]
     d = _rel(w, got, ref)
-    assert np.all(d < 1e-11), d
+    spread = _rel(w, pert, ref)
+    assert np.all(spread < 1e-8), spread
+    assert np.all(d < np.maximum(1e-11, 3 * spread)), (d, spread)
 
 
 def test_baro_cfl_steps_and_time():
@@ -174,10 +182,7 @@ def test_vapour_collapse_full_size_windows():
     scale = np.abs(got).reshape(q.shape[0], -1).max(axis=1)
     scale[1:3] = np.sqrt(got[1] ** 2 + got[2] ** 2).max()
     scale[4] = 1.0                                   # no gas anywhere
-    # the passive energy starts at zero (e = 0, at rest): after one step it is
-    # the divergence of p* u* with p ~ 1e7 Pa, a cancellation that the
-    # relative bound allows for with 1e-10
-    tol = np.array([1e-11, 1e-11, 1e-11, 1e-10, 1e-11])
+    tol = np.full(q.shape[0], 1e-11)
     for lo, hi in wins:
         ref = oracle_step_window(o, q, dt, lo, hi)
         sl = (slice(None), 0, slice(lo[1], hi[1]), slice(lo[0], hi[0]))
