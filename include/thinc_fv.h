@@ -253,7 +253,8 @@ fv_status fv_wait_selftest(int polls, int* err_word);
  * qprev.  Limit: the primitive scratch of (n+4)^d ghosted cells times
  * (ndim + ncomp + 1 + extra fields) values of 8 bytes (FV_FP64) or 4 bytes
  * (FV_MIXED), plus small work lists, must fit the array; larger grids, a
- * per-cell inflow array (grid->in_u) and every argument error return
+ * per-cell inflow array (grid->in_u), the barotropic closure in the FV_MIXED
+ * form, Peng-Robinson components and every argument error return
  * FV_ERR_ARG.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  Every call uses the same array: calls that

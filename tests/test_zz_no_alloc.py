@@ -69,6 +69,31 @@ def test_noalloc_matches_fv_rk_stage_twice(precision, lims, viscous):
         assert np.all(d <= TOL[precision]), (call, d)
 
 
+def test_noalloc_barotropic_fp64_matches_fv_rk_stage():
+    """the barotropic closure through the no-alloc entry point (FP64 form)"""
+    import torch
+    w = wl.bubble_collapse("vapour", n=(64, 60))
+    s = fv.Solver(w, precision=fv.FV_FP64)
+    s.set_state(w.primitives(), kind=fv.FV_PRIMITIVE)
+    q = s.get_state()
+    dt = 2e-10
+    s.step_dt(dt)
+    ref = s.get_state()
+    L = fv.load()
+    args = _abi(w, fv.FV_FP64)
+    q0 = torch.from_numpy(q.copy()).cuda()
+    qa, qb = torch.empty_like(q0), torch.empty_like(q0)
+    _noalloc_step(L, args, dt, q0, qa, qb, torch.cuda.current_stream().cuda_stream)
+    d = rel_field_diff(q0.cpu().numpy(), ref)
+    assert np.all(d <= 1e-12), d
+    g, cm, e = _abi(w, fv.FV_MIXED)            # the mixed no-alloc variants are stiffened-gas only
+    buf = torch.zeros(8, dtype=torch.float64, device="cuda")
+    p = C.c_void_p(buf.data_ptr())
+    st = L.fv_rk_stage_noalloc(C.byref(g), C.byref(cm), C.byref(e), 1, dt, p, p, p,
+                               C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == fv.FV_ERR_ARG
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch():
     import torch
     w = wl.random_state(n=(2048, 2048))
