@@ -678,7 +678,10 @@ static fv_status apply_tile(fv_ctx* x, int tile)
 }
 
 // scheme features of the fused kernel (App. D switch, CSF)
-static int march_mode(const fv_ctx* x) { return (x->P.iles ? MARCH_ILES : 0) | (x->P.csf ? MARCH_CSF : 0); }
+static int march_mode(const fv_ctx* x)
+{
+    return (x->P.iles ? MARCH_ILES : 0) | (x->P.csf ? MARCH_CSF : 0) | ((x->P.visc || x->P.grav) ? MARCH_VISC : 0);
+}
 
 // Fused kernel with row chunk `chunk` and variant `var`: work list of
 // (case, strip column, first row, rows) items.
@@ -722,9 +725,10 @@ static std::string tune_key(const fv_ctx* x)
     int lg = 0;
     while ((1LL << (lg + 1)) <= cells) ++lg;
     char buf[160];
-    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%d%d/%d/%d", x->nd, x->nc, x->mixed, x->P.iles, x->P.csf, x->P.pr,
-             x->P.lim_vel, x->P.lim_scalar,
-             x->ncases > 64 ? 2 : (x->ncases > 1 ? 1 : 0), lg);
+    // every scheme switch that selects a different kernel instantiation
+    snprintf(buf, sizeof buf, "%d/%d/%d/%d/%d/%d/%d%d/%d/%d/%d%d%d", x->nd, x->nc, x->mixed, x->P.iles, x->P.csf,
+             x->P.pr, x->P.lim_vel, x->P.lim_scalar, x->ncases > 64 ? 2 : (x->ncases > 1 ? 1 : 0), lg,
+             (x->P.visc || x->P.grav) ? 1 : 0, x->P.baro, x->P.hf);
     return buf;
 }
 
@@ -935,7 +939,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
-    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav && !x->P.hf;
+    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.hf;
     x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav && !x->P.hf;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;

@@ -433,11 +433,33 @@ __device__ __forceinline__ R hf_kappa(const R* ea, int hc, const int* st, const 
 }
 
 // Eq. 2-2 stress and heat-flux terms, added to the flux F of the face between
-// halo cells hl and hl + e_D (st: halo strides): momentum -tau_{D a} with
+// cells L and R = L + e_D (visc_core: from the face's velocity gradient g,
+// the two cells' u, mu, k_c, T; visc_face: from halo cells hl and hl + e_D
+// with halo strides st): momentum -tau_{D a} with
 // tau = mu (grad u + grad u^T - 2/3 (div u) I), energy -(u . tau)_D - k_c dT/dx_D.
 // A derivative along D is the two cells' difference; along another direction
 // the mean of the two cells' central differences; u, mu and k_c at the face
 // are the two cells' means.
+template <int ND, int D, typename R>
+__device__ __forceinline__ void visc_core(const R (&g)[ND][ND], const R* uL, const R* uR, R muL, R muR, R kcL,
+                                          R kcR, R TL, R TR, R ciD, R* F)
+{
+    R div = R(0);
+#pragma unroll
+    for (int a = 0; a < ND; ++a) div += g[a][a];
+    const R mu = R(0.5) * (muL + muR);
+    const R kc = R(0.5) * (kcL + kcR);
+    R utau = R(0);
+#pragma unroll
+    for (int a = 0; a < ND; ++a) {
+        R tau = mu * (g[a][D] + g[D][a]);
+        if (a == D) tau -= R(2.0 / 3.0) * mu * div;
+        F[1 + a] -= tau;
+        utau += R(0.5) * (uL[a] + uR[a]) * tau;
+    }
+    F[1 + ND] -= utau + kc * ((TR - TL) * ciD);
+}
+
 template <int ND, int D, typename R>
 __device__ __forceinline__ void visc_face(const DevParams& P, const R* sp, int HC, int hl, const int* st,
                                           const R* ci, R* F)
@@ -452,21 +474,12 @@ __device__ __forceinline__ void visc_face(const DevParams& P, const R* sp, int H
             if (b == D) g[a][b] = (u[hr] - u[hl]) * ci[D];
             else g[a][b] = ((u[hl + st[b]] - u[hl - st[b]]) + (u[hr + st[b]] - u[hr - st[b]])) * (R(0.25) * ci[b]);
         }
-    R div = R(0);
+    R uL[ND], uR[ND];
 #pragma unroll
-    for (int a = 0; a < ND; ++a) div += g[a][a];
-    const R mu = R(0.5) * (sp[P.i_mu * HC + hl] + sp[P.i_mu * HC + hr]);
-    const R kc = R(0.5) * (sp[P.i_kc * HC + hl] + sp[P.i_kc * HC + hr]);
-    R utau = R(0);
-#pragma unroll
-    for (int a = 0; a < ND; ++a) {
-        R tau = mu * (g[a][D] + g[D][a]);
-        if (a == D) tau -= R(2.0 / 3.0) * mu * div;
-        F[1 + a] -= tau;
-        utau += R(0.5) * (sp[a * HC + hl] + sp[a * HC + hr]) * tau;
-    }
+    for (int a = 0; a < ND; ++a) { uL[a] = sp[a * HC + hl]; uR[a] = sp[a * HC + hr]; }
     const R* T = sp + (ND + 1) * HC;
-    F[1 + ND] -= utau + kc * ((T[hr] - T[hl]) * ci[D]);
+    visc_core<ND, D, R>(g, uL, uR, sp[P.i_mu * HC + hl], sp[P.i_mu * HC + hr], sp[P.i_kc * HC + hl],
+                        sp[P.i_kc * HC + hr], T[hl], T[hr], ci[D], F);
 }
 
 // ------------------------------------------------------------------ stage

@@ -35,8 +35,9 @@ struct MarchArgs {
 };
 
 constexpr int MARCH_COLS = 28;   // cells per strip (32 lanes minus 2 + 2 halo)
-// scheme features of a fused-kernel instantiation
-constexpr int MARCH_ILES = 1, MARCH_CSF = 2;
+// scheme features of a fused-kernel instantiation (MARCH_VISC: the Eq. 2-2
+// stress, heat-flux and gravity terms)
+constexpr int MARCH_ILES = 1, MARCH_CSF = 2, MARCH_VISC = 4;
 
 // Inflow-disc test of an x-low ghost cell in source row iy (FP64, the same
 // expression as the primitive pass).  Not inlined: only lanes on an inflow
@@ -53,6 +54,7 @@ static __device__ __noinline__ bool march_in_disc(const CaseDesc& C, int iy)
 template <int NV, typename R> struct MRow {
     R w[NV];
     R rho, c, e;
+    R mu, kc;    // mixture viscosity and conductivity (viscous mode)
 };
 
 template <int NC, typename R, int NWARP, int MB, int LIM, int MODE, typename Q>
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 {
     constexpr int ND = 2, NV = ND + NC + 1;
     constexpr bool ILES = (MODE & MARCH_ILES) != 0, CSF = (MODE & MARCH_CSF) != 0, AUX = ILES || CSF;
+    constexpr bool VISC = (MODE & MARCH_VISC) != 0;
     const DevParams& P = A.P;
     const ConstT<R>& Kc = K<R>(P);
     // q^{k-1} never aliases q^k (the stages go q0 -> qA -> qB -> qA -> q0)
@@ -137,9 +140,49 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
             } else {
                 row.e = R(0);
             }
+            if (VISC) {
+                // Eq. 2-8 with no vapour, as the primitive pass computes it
+                R s = R(0), mu = R(0), kc = R(0);
+#pragma unroll
+                for (int k = 0; k < NC - 1; ++k) s += clip01(w[ND + 2 + k]);
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    const R Yk = (k == NC - 1) ? clip01(R(1) - s) : clip01(w[ND + 2 + k]);
+                    const R a = fdiv(rr_ * Yk * Kc.gm1cv[k] * w[ND + 1], Kc.Pk[k] + w[ND]);
+                    mu += a * Kc.mu[k];
+                    kc += a * Kc.kc[k];
+                }
+                row.mu = mu;
+                row.kc = kc;
+            }
         };
         auto shl = [&](R v) { return __shfl_up_sync(FULL, v, 1); };     // value of lane - 1
         auto shr = [&](R v) { return __shfl_down_sync(FULL, v, 1); };   // value of lane + 1
+        // Eq. 2-2 stress and heat flux of the y face between window rows 1 and 2
+        // and of the x face between this lane's and the next lane's cell of row
+        // 1, with the tiled kernel's face gradients and operation order
+        auto visc_y = [&](const MRow<NV, R>* Wr, R* F) {
+            R g[2][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                g[a][1] = (Wr[2].w[a] - Wr[1].w[a]) * ci1;
+                g[a][0] = ((shr(Wr[1].w[a]) - shl(Wr[1].w[a])) + (shr(Wr[2].w[a]) - shl(Wr[2].w[a]))) * (R(0.25) * ci0);
+            }
+            visc_core<2, 1, R>(g, Wr[1].w, Wr[2].w, Wr[1].mu, Wr[2].mu, Wr[1].kc, Wr[2].kc, Wr[1].w[ND + 1],
+                               Wr[2].w[ND + 1], ci1, F);
+        };
+        auto visc_x = [&](const MRow<NV, R>* Wr, R* F) {
+            R g[2][2], uR[2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                uR[a] = shr(Wr[1].w[a]);
+                g[a][0] = (uR[a] - Wr[1].w[a]) * ci0;
+                const R dL = Wr[2].w[a] - Wr[0].w[a];
+                g[a][1] = (dL + shr(dL)) * (R(0.25) * ci1);
+            }
+            visc_core<2, 0, R>(g, Wr[1].w, uR, Wr[1].mu, shr(Wr[1].mu), Wr[1].kc, shr(Wr[1].kc), Wr[1].w[ND + 1],
+                               shr(Wr[1].w[ND + 1]), ci0, F);
+        };
 
         // App. D cell sensor f (Eq. D.4) of window row m (rows m-1 .. m+1)
         auto sensor = [&](const MRow<NV, R>* Wr, int m) -> int {
@@ -251,6 +294,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
             if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
             const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, ws, r4, c4, flag_lo | flag_y, Fy);
             if (!ok && own_col) set_err(A.err, ERR_NONPHYS);
+            if (VISC && P.visc) visc_y(W, Fy);
         }
         const double adt = A.a * A.dt[wi.x];
         const float adtf = float(adt);
@@ -286,6 +330,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                 if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
                 const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, ws, r4, c4, flag_y | flag_up, Fyn);
                 if (!ok && own_col) set_err(A.err, ERR_NONPHYS);
+                if (VISC && P.visc) visc_y(W, Fyn);
             }
             // x face between this lane's cell and the next, row y
             R Fx[NV];
@@ -306,6 +351,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                 }
                 const bool ok = face_flux<ND, NC, R, false, LIM>(P, 0, ws, r4, c4, fl, Fx);
                 if (!ok && (own_col || own_right)) set_err(A.err, ERR_NONPHYS);
+                if (VISC && P.visc) visc_x(W, Fx);
             }
             // CSF source of this lane's cell (momentum, energy)
             R S[NV];
@@ -347,6 +393,17 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                 at_y = at_up;
                 nlo[0] = nhi[0];
                 nlo[1] = nhi[1];
+            }
+            if (VISC && P.grav) {
+                // Eq. 2-2 Q: rho g (momentum), rho u . g (energy), the stage's input rho
+                const R rho = W[1].rho;
+                R ug = R(0);
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    S[1 + d] += rho * Kc.grav[d];
+                    ug += W[1].w[d] * Kc.grav[d];
+                }
+                S[1 + ND] += rho * ug;
             }
             // divergence and LSRK update of this lane's cell
             Q* qo = qoreg + gcell;

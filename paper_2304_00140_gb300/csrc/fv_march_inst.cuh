@@ -13,11 +13,15 @@ namespace tfv {
 namespace {
 // variant v: 0 Table 4.2 limiter pair, 2 limiter pair read at run time; both
 // sized for 4 (FP32) or 2 (FP64) resident blocks of 4 warps per SM (a fifth
-// FP32 block needs <= 96 registers and spills)
-template <int V, typename R> constexpr int mb_of() { return sizeof(R) == 4 ? 4 : 2; }
+// FP32 block needs <= 96 registers and spills); the viscous modes, which keep
+// two more values per window row, for 3 FP32 blocks
+template <int V, typename R, int M> constexpr int mb_of()
+{
+    return sizeof(R) == 4 ? ((M & MARCH_VISC) ? 3 : 4) : 2;
+}
 template <int V> constexpr int lim_of() { return V == 2 ? LIM_RUNTIME : LIM_TABLE42; }
 
-#define FV_MARCH(NC, V, M) march2d_kernel<NC, FV_MR, MARCH_WARPS, mb_of<V, FV_MR>(), lim_of<V>(), M, FV_MQ>
+#define FV_MARCH(NC, V, M) march2d_kernel<NC, FV_MR, MARCH_WARPS, mb_of<V, FV_MR, M>(), lim_of<V>(), M, FV_MQ>
 
 template <int NC, int V, int M>
 cudaError_t go(const MarchArgs& A, int grid, cudaStream_t s)
@@ -54,7 +58,11 @@ int occ_v(int var)
     case 0: return nc == 2 ? fn<2, 0>(__VA_ARGS__) : fn<3, 0>(__VA_ARGS__);        \
     case 1: return nc == 2 ? fn<2, 1>(__VA_ARGS__) : fn<3, 1>(__VA_ARGS__);        \
     case 2: return nc == 2 ? fn<2, 2>(__VA_ARGS__) : fn<3, 2>(__VA_ARGS__);        \
-    default: return nc == 2 ? fn<2, 3>(__VA_ARGS__) : fn<3, 3>(__VA_ARGS__);       \
+    case 3: return nc == 2 ? fn<2, 3>(__VA_ARGS__) : fn<3, 3>(__VA_ARGS__);        \
+    case 4: return nc == 2 ? fn<2, 4>(__VA_ARGS__) : fn<3, 4>(__VA_ARGS__);        \
+    case 5: return nc == 2 ? fn<2, 5>(__VA_ARGS__) : fn<3, 5>(__VA_ARGS__);        \
+    case 6: return nc == 2 ? fn<2, 6>(__VA_ARGS__) : fn<3, 6>(__VA_ARGS__);        \
+    default: return nc == 2 ? fn<2, 7>(__VA_ARGS__) : fn<3, 7>(__VA_ARGS__);       \
     }
 
 cudaError_t FV_MCAT(launch_march_, FV_MSUFFIX)(int nc, int mode, int var, const MarchArgs& A, int grid,

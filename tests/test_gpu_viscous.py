@@ -23,7 +23,7 @@ def _transport(w, mu=(2e-3, 5e-3, 1e-3), kc=(0.4, 0.6, 0.1), g=(0.3, -9.8, 0.2))
     return wl.with_transport(w, mu=list(mu[:n]), kc=list(kc[:n]), gravity=g)
 
 
-def _run_pair(w, steps=2, dt_frac=0.3, precision=fv.FV_FP64):
+def _run_pair(w, steps=2, dt_frac=0.3, precision=fv.FV_FP64, fused=None):
     o = oracle.Oracle(w)
     q = o.prim_to_cons(w.primitives())
     s = fv.Solver(w, precision=precision)
@@ -33,7 +33,9 @@ def _run_pair(w, steps=2, dt_frac=0.3, precision=fv.FV_FP64):
     for _ in range(steps):
         s.step_dt(dt)
         ref = oracle_step_dt(o, ref, dt)
-    assert not s.tile()["fused"] and not s.tile()["zmarch"]
+    assert not s.tile()["zmarch"]
+    if fused is not None:
+        assert s.tile()["fused"] == fused
     return q, s.get_state(), ref
 
 
@@ -61,10 +63,16 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(CASES))
-def test_viscous_parity_fp64(name):
+# 2D cases run both kernels that carry the viscous terms: the tiled stage
+# kernel after a primitive pass (FV_FUSED=0) and the fused 2D kernel (FV_FUSED=1)
+PARITY = [(n, f) for n in sorted(CASES) for f in (("0", "1") if n.startswith("2d") else ("0",))]
+
+
+@pytest.mark.parametrize("name,fused", PARITY)
+def test_viscous_parity_fp64(name, fused, monkeypatch):
+    monkeypatch.setenv("FV_FUSED", fused)
     w = CASES[name]()
-    q, got, ref = _run_pair(w)
+    q, got, ref = _run_pair(w, fused=(fused == "1"))
     # the terms are active: the same run without them differs clearly
     w0 = wl.with_transport(w, mu=[0.0] * w.ncomp, kc=[0.0] * w.ncomp, gravity=(0.0, 0.0, 0.0))
     _, got0, _ = _run_pair(w0)
