@@ -150,17 +150,17 @@ def test_viscous_residual_converges_3d():
     assert np.all(e12 / e24 > 3.5), (e12, e24)
 
 
-def _shear(mu, n=32, U=1e-3):
+def _shear(mu, n=32, U=1e-3, waves=1):
     w = wl.Workload(name="shear", ndim=2, n=[4, n, 1], lo=[0, 0, 0], hi=[L / 8, L, 1.0],
                     bc=[[0, 0]] * 3, comps=[wl.AIR, wl.WATER], liquid=1, scheme=wl.default_scheme(),
                     steps=1, cfl=0.4, init="random")
     w = wl.with_transport(w, mu=[mu, 1e-3])
     y = (np.arange(n) + 0.5) * (L / n)
     W = np.zeros((w.nvar, 1, n, 4))
-    W[0] = (U * np.sin(K * y))[None, :, None]
+    W[0] = (U * np.sin(waves * K * y))[None, :, None]
     W[2], W[3], W[4] = P0, T0, 1.0
     o = oracle.Oracle(w)
-    return o, o.prim_to_cons(W), np.sin(K * y)
+    return o, o.prim_to_cons(W), np.sin(waves * K * y)
 
 
 def test_shear_wave_decay():
@@ -238,3 +238,25 @@ def test_mixture_transport_pure_components():
     np.testing.assert_allclose(tr[0][pure_water], 1e-3, rtol=1e-12)
     np.testing.assert_allclose(tr[1][pure_water], 0.6, rtol=1e-12)
     assert tr[0].min() >= 1.8e-5 * (1 - 1e-12) and tr[0].max() <= 1e-3 * (1 + 1e-12)
+
+
+def test_lsrk_amplifies_a_linear_mode_by_the_degree_4_taylor_polynomial():
+    """Sec. 3.1's explicit four-stage low-storage scheme (coefficients
+    1/4, 1/3, 1/2, 1): on a linear mode with R = lambda q one step multiplies
+    the mode by 1 + z + z^2/2 + z^3/6 + z^4/24, z = lambda dt (a different
+    order of the coefficients gives another polynomial).  The mode is a small
+    shear wave, for which the residual is linear (no convective flux, heating
+    of order U^2), four cells per wavelength, so that no other mode of the
+    grid has more than twice its decay rate and rounding noise in them stays
+    damped at these step sizes."""
+    o, q, s = _shear(0.5, U=1e-7, waves=8)
+    ku = 2                                            # a row where sin(k y) is near its peak
+    R = o.stage(4, 1.0, q, q) - q
+    lam = R[1][0, ku, 0] / q[1][0, ku, 0]
+    assert lam < 0
+    for z in (-0.4, -0.9, -1.3):
+        dt = z / lam
+        from tests.helpers import oracle_step_dt
+        q1 = oracle_step_dt(o, q, dt)
+        G = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+        assert abs(q1[1][0, ku, 0] / q[1][0, ku, 0] - G) < 1e-9, (z, q1[1][0, ku, 0] / q[1][0, ku, 0], G)
