@@ -200,7 +200,7 @@ def _grid(w: Workload):
 
 
 def _init_column(w: Workload):
-    """configs[0]: a water column of radius R (centred) in air, uniform p, T
+    """Advection: a water column of radius R (centred) in air, uniform p, T
     and velocity; Y_water tanh-smoothed over ``width`` cells."""
     P = w.params
     X, Y, _ = _grid(w)
@@ -216,7 +216,7 @@ def _init_column(w: Workload):
 
 
 def _init_shock_bubble(w: Workload):
-    """configs[1]: planar shock in water (post-shock p2, RH states) at x_s
+    """Shock-bubble: planar shock in water (post-shock p2, RH states) at x_s
     moving +x, air bubble (radius R at (xb, yb)) tanh-smoothed."""
     P = w.params
     X, Y, _ = _grid(w)
@@ -235,7 +235,7 @@ def _init_shock_bubble(w: Workload):
 
 
 def _init_droplet(w: Workload):
-    """configs[3] case: a water droplet with an elliptical (mode-2) radius
+    """Oscillating droplet: a water droplet with an elliptical (mode-2) radius
     perturbation r_i(theta) = R + A cos(2 theta), at rest, uniform p and T.
     ``dp`` optionally presets a pressure jump inside (static-drop tests)."""
     P = w.params
@@ -298,7 +298,7 @@ def _init_random(w: Workload):
 
 
 def _init_jet(w: Workload):
-    """configs[4]: ambient N2/CH4 gas at rest filling the box; the liquid
+    """3D jet: ambient N2/CH4 gas at rest filling the box; the liquid
     enters through the inflow disc on the x-low face (boundary data)."""
     P = w.params
     W = _alloc(w)
@@ -321,7 +321,7 @@ def rh_post_shock_ig(p1, T1, Ms, gamma, Rs):
 
 
 def _init_pr_drop(w: Workload):
-    """configs[2]: n-dodecane droplet (radius R) at T_l in N2 at (p, T), Mach
+    """Near-critical shock/droplet: n-dodecane droplet (radius R) at T_l in N2 at (p, T), Mach
     Ms shock in the N2 at x_s moving +x.  READING: the post-shock state is
     the ideal-gas Rankine-Hugoniot state of N2 (gamma = 1 + R/(M cv)); with
     the PR closure the jump sheds a weak wave."""
