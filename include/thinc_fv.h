@@ -72,7 +72,9 @@ enum { FV_DIAG_TOTALS = 0,   /* double[nv]: compensated sums of q over the case 
                                 [10] the primitive pass's, [11] its variant (-1: tiled) */
 enum { FV_DIAG_FLAGS = 5 };  /* unsigned char[n cells]: App. D sensor flag f (Eq. D.4) of each
                                 interior cell for the current state (x fastest); needs the
-                                App. D switch (FV_ERR_ARG otherwise); synchronous */
+                                App. D switch (FV_ERR_ARG otherwise); synchronous; call it
+                                between steps, not between the stages of a step (it uses a
+                                stage register as scratch) */
 enum { FV_ERRBIT_NONPHYS = 1, FV_ERRBIT_NONCONV = 2,
        FV_ERRBIT_TIMEOUT = 4 };   /* a bounded wait in a kernel gave up (reported as FV_ERR_CUDA) */
 
