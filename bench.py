@@ -212,16 +212,49 @@ def _nprim(w):
             + (2 if visc else 0) + (1 if baro else 0))
 
 
-def _algorithmic_stage_bytes(job, precision, fused=False):
-    """Compulsory HBM bytes of one stage-kernel launch per the kernel's inputs
-    and outputs.  Tiled kernel: every interior cell's primitives read once
-    (fp32 in the mixed form, fp64 otherwise), q^0 read and q^k written (8
-    bytes a value: FP64 or float-float).  Fused kernel: q^{k-1} and q^0 read,
-    q^k written."""
+def _design_stage_bytes(job, precision, fused=False):
+    """HBM bytes one stage-kernel launch of this design must move per its
+    inputs and outputs.  Tiled kernel: every interior cell's primitives read
+    once (fp32 in the mixed form, fp64 otherwise), q^0 read and q^k written
+    (8 bytes a value: FP64 or float-float).  Fused kernel: q^{k-1} and q^0
+    read, q^k written."""
     if fused:
         return job.cells * 3 * job.nvar * 8
     rs = 4 if precision == 1 else 8
     return job.cells * (_nprim(job.w) * rs + 2 * job.nvar * 8)
+
+
+def _compulsory_stage_bytes(job, precision):
+    """Compulsory HBM bytes of one stage (average over the four) of an ideal
+    single-pass design: per cell-update, FP64 reads q^0 once, every stage
+    reads q^{k-1} (and q^0 for stages 2-4) and writes q^k, all 8 bytes a
+    value: (2 + 3 + 3 + 3) x 8 = 88 bytes per conserved field; the mixed
+    form keeps q^A, q^B in FP32 (4 bytes) and q^0, q^{n+1} in 8 bytes:
+    (8 + 4) + 2 x (4 + 8 + 4) + (4 + 8 + 8) = 64 bytes per field."""
+    per_field = 64 if precision == 1 else 88
+    return job.cells * job.nvar * per_field / 4.0
+
+
+def fp64_peak(torch):
+    """Measured FP64 FMA rate of this GPU (TFLOP/s): the best of five
+    launches of the library's FMA-chain probe over 8 blocks per SM."""
+    import ctypes as C
+    from paper_2304_00140_gb300 import fv
+    L = fv.load()
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clk = ClockSampler(torch.cuda.current_device())
+    time.sleep(0.2)
+    best = 0.0
+    for _ in range(5):
+        ms, fl = C.c_double(), C.c_double()
+        st = L.fv_probe_fp64(8 * nsm, 256, 4096, C.byref(ms), C.byref(fl))
+        if st != fv.FV_OK:
+            raise fv.FVError(st, "fp64 probe")
+        best = max(best, fl.value / (ms.value * 1e-3) / 1e12)
+    clocks = clk.stop()
+    return dict(tflops=best, sms=nsm, clocks=clocks,
+                how=f"FMA chains, 8 independent per thread, {8 * nsm} blocks x 256 threads x 4096 rounds, "
+                    "best of 5 launches, CUDA events")
 
 
 def _solver(job, precision):
@@ -267,7 +300,8 @@ def run_form(job, precision, args, torch, dist, rank, world):
     s.profile(False)
     state = np.concatenate([s.get_state(case=i).reshape(job.nvar, -1) for i in range(len(job.cases))], axis=1)
     s.close()
-    return dict(ms=ms, launches=launches, clocks=clocks, err=err, prof=prof, state=state, tile=tile)
+    return dict(ms=ms, launches=launches, clocks=clocks, err=err, prof=prof, state=state, tile=tile,
+                steps=args.steps)
 
 
 def e2e_form(job, precision, args, torch):
@@ -461,31 +495,41 @@ def main():
         # a field that is zero in both forms (no gas in the vapour collapse) has error 0
         l1 = np.where(num == 0.0, 0.0, num / np.maximum(den, 1e-300)).tolist()
 
+    f64peak = fp64_peak(torch) if (rank == 0 and "fp64" in forms) else None
+
     def roof(r, precision):
         st = r["prof"]["stage"]
         avg_ms = st["ms"] / max(1, st["launches"])
         fused = bool(r["tile"].get("fused"))
-        byt = _algorithmic_stage_bytes(job, precision, fused)
+        design = _design_stage_bytes(job, precision, fused)
+        byt = _compulsory_stage_bytes(job, precision)
         ach = byt / (avg_ms * 1e-3) / 1e9
         form = "mixed" if precision == fv.FV_MIXED else "fp64"
+        step_ms = r["ms"] / r["steps"]
+        step = dict(compulsory_bytes_per_step=4 * byt, ms_per_step=step_ms,
+                    achieved=4 * byt / (step_ms * 1e-3) / 1e9, frac=4 * byt / (step_ms * 1e-3) / 1e9 / peaks["hbm"])
         out = dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
                    traffic=_ncu_traffic(job, form),
                    kernel="march2d_kernel" if fused else ("zmarch_kernel" if r["tile"].get("zmarch") else "stage_kernel"),
-                   avg_launch_ms=avg_ms,
-                   algorithmic_bytes_per_launch=byt, peak_source=peaks["src"],
+                   avg_launch_ms=avg_ms, algorithmic_bytes_per_launch=byt,
+                   algorithmic_basis=("compulsory bytes of one stage, the four stages' average: "
+                                      + ("64" if precision == fv.FV_MIXED else "88") + " B per conserved field "
+                                      "per cell-update / 4"),
+                   design_bytes_per_launch=design, design_frac=design / (avg_ms * 1e-3) / 1e9 / peaks["hbm"],
+                   peak_source=peaks["src"], step_level=step,
                    kernel_share={k: v["ms"] for k, v in r["prof"].items()}, tile=r["tile"])
         fl = _alg_flops_per_cell(job, fused)
-        if precision == fv.FV_FP64 and fl:
-            # the FP64 form is bound by the FP64 pipe: 152 SMs x 2 DFMA/clock x
-            # 2 flops at the 2070 MHz maximum SM clock
-            peak = 152 * 2 * 2 * 2.070e9 / 1e12
+        if precision == fv.FV_FP64 and fl and f64peak:
+            # the FP64 form is bound by the FP64 pipe (measured FMA rate)
+            peak = f64peak["tflops"]
             tf = fl * job.cells / (avg_ms * 1e-3) / 1e12
             out = dict(bound="alu", achieved=tf, peak=peak, unit="TFLOP/s", frac=tf / peak,
                        traffic=out["traffic"], kernel=out["kernel"], avg_launch_ms=avg_ms,
                        algorithmic_flops_per_launch=fl * job.cells,
-                       peak_source="derived: 152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz",
+                       peak_source="measured: " + f64peak["how"], peak_clocks=f64peak["clocks"],
                        hbm=dict(achieved=ach, peak=peaks["hbm"], frac=ach / peaks["hbm"],
-                                algorithmic_bytes_per_launch=byt),
+                                algorithmic_bytes_per_launch=byt, design_bytes_per_launch=design,
+                                step_level=step),
                        kernel_share=out["kernel_share"], tile=r["tile"])
         return out
 

@@ -240,6 +240,13 @@ const char* fv_status_string(int status);
  * operation. */
 fv_status fv_wait_selftest(int polls, int* err_word);
 
+/* FP64 arithmetic-rate probe for the FP64 form's roofline (not a paper
+ * operation): blocks x threads threads each run `iters` rounds of eight
+ * independent FP64 fused multiply-adds; *ms receives the CUDA-event time of
+ * one launch (after a warm-up launch) and *flops the flops it performed
+ * (2 per FMA).  Synchronous, on the legacy default stream. */
+fv_status fv_probe_fp64(int blocks, int threads, int iters, double* ms, double* flops);
+
 /* One Runge-Kutta stage of one grid that allocates no device memory, for
  * callers that cannot call cudaMalloc: code that runs inside a host
  * application owning the whole device through its own memory pool, code
@@ -251,18 +258,20 @@ fv_status fv_wait_selftest(int polls, int* err_word);
  *
  * q0 (the step's initial state), qprev (stage k-1's output; q0 for k = 1) and
  * qout are caller-owned device arrays in the conserved layout above; qout
- * receives q0 + a_k dt R(qprev).  qout may alias q0 (as stage 4 does) but not
- * qprev.  Limit: the primitive scratch of (n+4)^d ghosted cells times
- * (ndim + ncomp + 1 + extra fields) values of 8 bytes (FV_FP64) or 4 bytes
- * (FV_MIXED), plus small work lists, must fit the array; larger grids, a
- * per-cell inflow array (grid->in_u), the barotropic closure in the FV_MIXED
- * form, Peng-Robinson components and every argument error return
- * FV_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call uses the same array: calls that
- * overlap on the GPU (other streams, other threads) race.  The call runs on
- * `stream` and returns once the stage has finished, reporting a non-physical
- * state met by the kernels as FV_ERR_NONPHYSICAL. */
+ * receives q0 + a_k dt R(qprev).  qout may be q0 itself (as stage 4 does) but
+ * may not overlap qprev or part of q0 (FV_ERR_ARG).  Limit: the primitive
+ * scratch of (n+4)^d ghosted cells times (ndim + ncomp + 1 + extra fields)
+ * values of 8 bytes (FV_FP64) or 4 bytes (FV_MIXED), plus small work lists,
+ * must fit the array; larger grids, a per-cell inflow array (grid->in_u), the
+ * barotropic closure in the FV_MIXED form, Peng-Robinson components and every
+ * argument fv_init would reject return FV_ERR_ARG.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current and keeps it for the process; make that first call before any
+ * stream capture, and do not reset the device (cudaDeviceReset) after it.
+ * Every call uses the same array: calls that overlap on the GPU (other
+ * streams, other threads) race.  The call runs on `stream` and returns once
+ * the stage has finished, reporting a non-physical state met by the kernels
+ * as FV_ERR_NONPHYSICAL and a kernel wait that gave up as FV_ERR_CUDA. */
 #define FV_NOALLOC_SCRATCH_BYTES (48u << 20)
 fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_components* comps, const fv_eos* eos,
                               int k, double dt, const double* q0, const double* qprev, double* qout,

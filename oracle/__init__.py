@@ -80,6 +80,8 @@ def lib():
             L.or_sensor.argtypes = [P, dp, dp]
             L.or_transport.argtypes = [P, dp, dp]
             L.or_curvature.argtypes = [P, dp, dp]
+            L.or_sensor_args.argtypes = [P, dp, dp]
+            L.or_hf_axis.argtypes = [P, dp, dp, dp]
             L.or_baro_vapour.argtypes = [P, C.c_double, dp]
             L.or_baro_vapour.restype = C.c_double
             L.or_face_flux_av.argtypes = [P, C.c_int, dp, dp, dp, dp, C.c_int, dp]
@@ -212,6 +214,23 @@ class Oracle:
         k = np.zeros(self.shape[1:])
         _check(self.L.or_curvature(C.byref(self.P), _ptr(q), _ptr(k)), "curvature")
         return k
+
+    def sensor_args(self, q):
+        """App. D switch arguments per interior cell (Eq. D.4):
+        [theta^D, theta^Gas, theta^alpha, |div u|, |curl u|] x [nz, ny, nx]"""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros((5,) + self.shape[1:])
+        _check(self.L.or_sensor_args(C.byref(self.P), _ptr(q), _ptr(out)), "sensor_args")
+        return out
+
+    def hf_axis(self, q):
+        """height-function column axis per interior cell and the relative gap
+        to the competing axis (Sec. 3.5 option)"""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        axis = np.zeros(self.shape[1:])
+        gap = np.zeros(self.shape[1:])
+        _check(self.L.or_hf_axis(C.byref(self.P), _ptr(q), _ptr(axis), _ptr(gap)), "hf_axis")
+        return axis.astype(int), gap
 
     def sensor(self, q):
         q = np.ascontiguousarray(q, dtype=np.float64)

@@ -900,44 +900,56 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
 
 /* App. D: vorticity-dilatation sensor (Ducros) and total-gas volume
  * fraction variation; f = 1 where either exceeds its threshold (Eq. D.4).
- * Derivatives by central differences. */
-static void box_sensor(const or_params* P, box_t* B, const int* lo, const int* hi)
+ * Derivatives by central differences.  sensor_args gives the switch
+ * arguments of one cell: a[0] = theta^D, a[1] = theta^Gas, a[2] = theta^alpha
+ * (the vapour-fraction variation, zero without the barotropic closure),
+ * a[3] = |div u|, a[4] = |curl u|. */
+static void sensor_args(const or_params* P, const box_t* B, int i, int j, int k, double* a5)
 {
     const int nd = P->ndim;
+    int ijk[3] = {i, j, k};
+    double g[3][3] = {{0}};  /* g[a][b] = d u_a / d x_b */
+    double tg = 0.0, tv = 0.0;
+    size_t b0 = bidx(B, i, j, k);
+    double ag0 = 1.0 - B->al[b0];
+    for (int bd = 0; bd < nd; ++bd) {
+        int pp[3] = {ijk[0], ijk[1], ijk[2]}, mm[3] = {ijk[0], ijk[1], ijk[2]};
+        pp[bd] += 1;
+        mm[bd] -= 1;
+        size_t bp = bidx(B, pp[0], pp[1], pp[2]), bm = bidx(B, mm[0], mm[1], mm[2]);
+        for (int a = 0; a < nd; ++a)
+            g[a][bd] = (B->W[(size_t)a * B->cnt + bp] - B->W[(size_t)a * B->cnt + bm]) / (2.0 * P->dx[bd]);
+        tg += fabs(ag0 - (1.0 - B->al[bm])) + fabs((1.0 - B->al[bp]) - ag0);
+        tv += fabs(B->av[b0] - B->av[bm]) + fabs(B->av[bp] - B->av[b0]);
+    }
+    double div = 0.0;
+    for (int a = 0; a < nd; ++a) div += g[a][a];
+    double curl2;
+    if (nd == 3) {
+        double wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
+        curl2 = wx * wx + wy * wy + wz * wz;
+    } else if (nd == 2) {
+        double wz = g[1][0] - g[0][1];
+        curl2 = wz * wz;
+    } else {
+        curl2 = 0.0;
+    }
+    a5[0] = div * div / (div * div + curl2 + P->eps_ducros);
+    a5[1] = tg;
+    /* theta^alpha: the same variation of the vapour fraction */
+    a5[2] = tv;
+    a5[3] = fabs(div);
+    a5[4] = sqrt(curl2);
+}
+
+static void box_sensor(const or_params* P, box_t* B, const int* lo, const int* hi)
+{
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
             for (int i = lo[0]; i < hi[0]; ++i) {
-                int ijk[3] = {i, j, k};
-                double g[3][3] = {{0}};  /* g[a][b] = d u_a / d x_b */
-                double tg = 0.0, tv = 0.0;
-                size_t b0 = bidx(B, i, j, k);
-                double ag0 = 1.0 - B->al[b0];
-                for (int bd = 0; bd < nd; ++bd) {
-                    int pp[3] = {ijk[0], ijk[1], ijk[2]}, mm[3] = {ijk[0], ijk[1], ijk[2]};
-                    pp[bd] += 1;
-                    mm[bd] -= 1;
-                    size_t bp = bidx(B, pp[0], pp[1], pp[2]), bm = bidx(B, mm[0], mm[1], mm[2]);
-                    for (int a = 0; a < nd; ++a)
-                        g[a][bd] = (B->W[(size_t)a * B->cnt + bp] - B->W[(size_t)a * B->cnt + bm]) / (2.0 * P->dx[bd]);
-                    tg += fabs(ag0 - (1.0 - B->al[bm])) + fabs((1.0 - B->al[bp]) - ag0);
-                    tv += fabs(B->av[b0] - B->av[bm]) + fabs(B->av[bp] - B->av[b0]);
-                }
-                double div = 0.0;
-                for (int a = 0; a < nd; ++a) div += g[a][a];
-                double curl2;
-                if (nd == 3) {
-                    double wx = g[2][1] - g[1][2], wy = g[0][2] - g[2][0], wz = g[1][0] - g[0][1];
-                    curl2 = wx * wx + wy * wy + wz * wz;
-                } else if (nd == 2) {
-                    double wz = g[1][0] - g[0][1];
-                    curl2 = wz * wz;
-                } else {
-                    curl2 = 0.0;
-                }
-                double thD = div * div / (div * div + curl2 + P->eps_ducros);
-                /* theta^alpha: the same variation of the vapour fraction (zero
-                 * without the barotropic closure) */
-                B->flag[b0] = (thD > P->thr_ducros || tg > P->thr_gas || tv > P->thr_vap) ? 1.0 : 0.0;
+                double a5[5];
+                sensor_args(P, B, i, j, k, a5);
+                B->flag[bidx(B, i, j, k)] = (a5[0] > P->thr_ducros || a5[1] > P->thr_gas || a5[2] > P->thr_vap) ? 1.0 : 0.0;
             }
 }
 
@@ -975,21 +987,31 @@ static double smooth_at(const or_params* P, const box_t* B, int i, int j, int k)
  * READING: the paper lists 3x3, 3x5, 3x7 windows (3x3x3 ... 3x3x7 in 3D); the
  * columns here have 5 cells (3x5, 3x3x5), the two-cell halo of the stage;
  * the axis is the one with the largest central difference of the
- * unsmoothed alpha (within a relative 1e-12 the lower axis, so that a
- * symmetric tie does not depend on rounding); alpha is the liquid volume
- * fraction, not smoothed. */
-static double hf_curvature(const or_params* P, const box_t* B, int i, int j, int k)
+ * unsmoothed alpha, an exact tie going to the lower axis; alpha is the
+ * liquid volume fraction, not smoothed.  hf_axis also returns the relative
+ * gap between the largest and the second-largest difference (1 in 1D). */
+static int hf_axis(const or_params* P, const box_t* B, int i, int j, int k, double* gap)
 {
     const int nd = P->ndim;
-    int c[3] = {i, j, k}, dir = 0;
-    double gmax = -1.0;
+    int dir = 0;
+    double gmax = -1.0, gsec = -1.0;
     for (int d = 0; d < nd; ++d) {
         int p[3] = {i, j, k}, m[3] = {i, j, k};
         p[d] += 1;
         m[d] -= 1;
         double g = fabs(B->al[bidx(B, p[0], p[1], p[2])] - B->al[bidx(B, m[0], m[1], m[2])]) / (2.0 * P->dx[d]);
-        if (g > gmax * (1.0 + 1e-12)) { gmax = g; dir = d; }   /* near-ties go to the lower axis */
+        if (g > gmax) { gsec = gmax; gmax = g; dir = d; }
+        else if (g > gsec) gsec = g;
     }
+    if (gap) *gap = (nd < 2) ? 1.0 : (gmax > 0.0 ? (gmax - gsec) / gmax : 0.0);
+    return dir;
+}
+
+static double hf_curvature(const or_params* P, const box_t* B, int i, int j, int k)
+{
+    const int nd = P->ndim;
+    int c[3] = {i, j, k};
+    const int dir = hf_axis(P, B, i, j, k, NULL);
     int t[2] = {0, 0}, nt = 0;
     for (int d = 0; d < nd; ++d)
         if (d != dir) t[nt++] = d;
@@ -1425,6 +1447,60 @@ int or_curvature(const or_params* P, const double* q, double* kappa)
                 for (int i = 0; i < P->n[0]; ++i) {
                     double g[3];
                     csf_parts(P, &B, i, j, k, &kappa[cidx(P, i, j, k)], g);
+                }
+    box_free(&B);
+    return st;
+}
+
+/* App. D switch arguments of every interior cell (Eq. D.4):
+ * out[v][cells] with v = 0 theta^D, 1 theta^Gas, 2 theta^alpha, 3 |div u|,
+ * 4 |curl u|.  A diagnostic for locating cells whose switch decision lies
+ * at a threshold; the stage itself uses box_sensor. */
+int or_sensor_args(const or_params* P, const double* q, double* out)
+{
+    const int nd = P->ndim;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    int st = box_fill(P, q, &B, blo, bhi);
+    if (!st) {
+        const size_t nc = ncells(P);
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) {
+                    double a5[5];
+                    sensor_args(P, &B, i, j, k, a5);
+                    for (int v = 0; v < 5; ++v) out[(size_t)v * nc + cidx(P, i, j, k)] = a5[v];
+                }
+    }
+    box_free(&B);
+    return st;
+}
+
+/* Height-function column axis of every interior cell (Sec. 3.5 option):
+ * axis[cells] and gap[cells], the relative gap between the largest and the
+ * second-largest central difference of the liquid fraction. */
+int or_hf_axis(const or_params* P, const double* q, double* axis, double* gap)
+{
+    const int nd = P->ndim;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    int st = box_fill(P, q, &B, blo, bhi);
+    if (!st)
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) {
+                    size_t c = cidx(P, i, j, k);
+                    axis[c] = (double)hf_axis(P, &B, i, j, k, &gap[c]);
                 }
     box_free(&B);
     return st;

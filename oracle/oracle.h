@@ -114,6 +114,13 @@ int or_curvature(const or_params* P, const double* q, double* kappa);
 int or_csf_source(const or_params* P, const double* q, double* S);
 /* App. D cell sensor f (0/1) on the interior */
 int or_sensor(const or_params* P, const double* q, double* f);
+/* App. D switch arguments on the interior: out[5][cells] = theta^D,
+ * theta^Gas, theta^alpha, |div u|, |curl u| (Eq. D.4) */
+int or_sensor_args(const or_params* P, const double* q, double* out);
+/* height-function column axis (0..ndim-1) of each interior cell and the
+ * relative gap between the largest and second-largest central difference
+ * of the liquid fraction (Sec. 3.5 option) */
+int or_hf_axis(const or_params* P, const double* q, double* axis, double* gap);
 /* cell mixture viscosity and conductivity on the interior (out[2][cells]) */
 int or_transport(const or_params* P, const double* q, double* out);
 /* barotropic closure (Sec. 2.2): vapour volume fraction (Eq. 2-7) at p with

@@ -130,35 +130,38 @@ static fv_status cuda_fail(fv_ctx* c, cudaError_t e, const char* where)
     } while (0)
 
 // ------------------------------------------------------------------ checks
-static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm, const fv_eos* eos,
-                          std::string& why)
+// Argument checks shared by fv_init and fv_rk_stage_noalloc: nullptr when
+// the arguments are valid, else a static description (nothing allocated).
+static const char* check_args(int ncases, const fv_grid* g, const fv_components* cm, const fv_eos* eos)
 {
-    if (ncases < 1 || !g || !cm || !eos) { why = "null argument or ncases < 1"; return FV_ERR_ARG; }
+    if (ncases < 1 || !g || !cm || !eos) return "null argument or ncases < 1";
     const int nd = g[0].ndim;
-    if (nd != 2 && nd != 3) { why = "ndim must be 2 or 3"; return FV_ERR_ARG; }
+    if (nd != 2 && nd != 3) return "ndim must be 2 or 3";
     for (int c = 0; c < ncases; ++c) {
-        if (g[c].ndim != nd) { why = "all cases must share ndim"; return FV_ERR_ARG; }
+        if (g[c].ndim != nd) return "all cases must share ndim";
         for (int d = 0; d < 3; ++d) {
             const int want1 = d >= nd;
-            if (g[c].n[d] < 1 || (want1 && g[c].n[d] != 1)) { why = "bad cell counts"; return FV_ERR_ARG; }
-            if (d < nd && !(g[c].hi[d] > g[c].lo[d])) { why = "hi must exceed lo"; return FV_ERR_ARG; }
+            if (g[c].n[d] < 1 || (want1 && g[c].n[d] != 1)) return "bad cell counts";
+            if (d < nd && !(g[c].hi[d] > g[c].lo[d])) return "hi must exceed lo";
             if (d < nd) {
                 for (int s = 0; s < 2; ++s)
-                    if (g[c].bc[d][s] < 0 || g[c].bc[d][s] > 3) { why = "bad boundary kind"; return FV_ERR_ARG; }
-                if ((g[c].bc[d][0] == FV_BC_PERIODIC) != (g[c].bc[d][1] == FV_BC_PERIODIC)) {
-                    why = "periodic boundaries must pair";
-                    return FV_ERR_ARG;
-                }
-                if ((d > 0 && g[c].bc[d][0] == FV_BC_INFLOW) || g[c].bc[d][1] == FV_BC_INFLOW) {
-                    why = "inflow only on the x-low side";
-                    return FV_ERR_ARG;
-                }
+                    if (g[c].bc[d][s] < 0 || g[c].bc[d][s] > 3) return "bad boundary kind";
+                if ((g[c].bc[d][0] == FV_BC_PERIODIC) != (g[c].bc[d][1] == FV_BC_PERIODIC))
+                    return "periodic boundaries must pair";
+                if ((d > 0 && g[c].bc[d][0] == FV_BC_INFLOW) || g[c].bc[d][1] == FV_BC_INFLOW)
+                    return "inflow only on the x-low side";
             }
         }
-        if ((long long)g[c].n[0] * g[c].n[1] * g[c].n[2] > (1LL << 31)) { why = "case too large"; return FV_ERR_ARG; }
+        // each extent and the cell count within 2^31 (checked without overflow),
+        // so that every ghosted extent n + 4 and every cell index fits the
+        // kernels' int and 64-bit arithmetic
+        const long long lim = 1LL << 31;
+        if (g[c].n[0] > lim - 8 || g[c].n[1] > lim - 8 || g[c].n[2] > lim - 8) return "case too large";
+        const long long n01 = (long long)g[c].n[0] * g[c].n[1];
+        if (n01 > lim || n01 * g[c].n[2] > lim) return "case too large";
     }
-    if (cm->ncomp < 2 || cm->ncomp > 3) { why = "ncomp must be 2 or 3"; return FV_ERR_ARG; }
-    if (cm->liquid < 0 || cm->liquid >= cm->ncomp) { why = "bad liquid index"; return FV_ERR_ARG; }
+    if (cm->ncomp < 2 || cm->ncomp > 3) return "ncomp must be 2 or 3";
+    if (cm->liquid < 0 || cm->liquid >= cm->ncomp) return "bad liquid index";
     int npr = 0, nbaro = 0;
     for (int k = 0; k < cm->ncomp; ++k) {
         npr += cm->comp[k].kind == FV_PR;
@@ -167,74 +170,65 @@ static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm,
     if (nbaro > 0) {
         // barotropic closure (Sec. 2.2): the liquid-vapour component at
         // `liquid`, isothermal ideal gases elsewhere
-        if (nbaro != cm->ncomp) { why = "barotropic components cannot mix with other closures"; return FV_ERR_ARG; }
+        if (nbaro != cm->ncomp) return "barotropic components cannot mix with other closures";
         for (int k = 0; k < cm->ncomp; ++k) {
             const fv_component& c = cm->comp[k];
             if (k == cm->liquid) {
                 if (!(c.psat > 0.0) || !(c.rho_sl > 0.0) || !(c.rho_sv > 0.0) || !(c.rho_sv < c.rho_sl) ||
-                    !(c.cl > 0.0) || !std::isfinite(c.psat * c.rho_sl * c.cl)) {
-                    why = "bad barotropic liquid constants";
-                    return FV_ERR_ARG;
-                }
-            } else if (!(c.rt > 0.0) || !std::isfinite(c.rt)) {
-                why = "bad barotropic gas constant R T_ref";
-                return FV_ERR_ARG;
-            }
-            if (c.mu != 0.0 || c.kc != 0.0) { why = "viscous terms need stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
+                    !(c.cl > 0.0) || !std::isfinite(c.psat * c.rho_sl * c.cl))
+                    return "bad barotropic liquid constants";
+            } else if (!(c.rt > 0.0) || !std::isfinite(c.rt)) return "bad barotropic gas constant R T_ref";
+            if (c.mu != 0.0 || c.kc != 0.0) return "viscous terms need stiffened-gas / ideal-gas components";
         }
-        if (eos->sigma > 0.0) { why = "CSF needs stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
+        if (eos->sigma > 0.0) return "CSF needs stiffened-gas / ideal-gas components";
         for (int c = 0; c < ncases; ++c)
-            if (g[c].bc[0][0] == FV_BC_INFLOW) { why = "the inflow disc needs stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
-        if (!std::isfinite(eos->thr_vap)) { why = "bad vapour sensor threshold"; return FV_ERR_ARG; }
+            if (g[c].bc[0][0] == FV_BC_INFLOW) return "the inflow disc needs stiffened-gas / ideal-gas components";
+        if (!std::isfinite(eos->thr_vap)) return "bad vapour sensor threshold";
     } else if (npr == cm->ncomp) {
         // Peng-Robinson mixture (Eq. A.2.1)
         for (int k = 0; k < cm->ncomp; ++k) {
             const fv_component& c = cm->comp[k];
-            if (!(c.Tc > 0.0) || !(c.pc > 0.0) || !(c.M > 0.0) || !(c.cv > 0.0)) {
-                why = "bad Peng-Robinson constants";
-                return FV_ERR_ARG;
-            }
+            if (!(c.Tc > 0.0) || !(c.pc > 0.0) || !(c.M > 0.0) || !(c.cv > 0.0)) return "bad Peng-Robinson constants";
         }
-        if (eos->sigma > 0.0 || eos->iles) {
-            why = "CSF and the App. D switch need stiffened-gas / ideal-gas components";
-            return FV_ERR_ARG;
-        }
-    } else if (npr > 0) {
-        why = "components must be all stiffened-gas / ideal-gas or all Peng-Robinson";
-        return FV_ERR_ARG;
-    }
+        if (eos->sigma > 0.0 || eos->iles) return "CSF and the App. D switch need stiffened-gas / ideal-gas components";
+    } else if (npr > 0) return "components must be all stiffened-gas / ideal-gas or all Peng-Robinson";
     double pis[FV_MAX_COMP];
     int npi = 0;
     for (int k = 0; k < cm->ncomp && npr == 0 && nbaro == 0; ++k) {
         const fv_component& c = cm->comp[k];
-        if (c.kind != FV_SG) { why = "only stiffened-gas / ideal-gas components are supported"; return FV_ERR_ARG; }
-        if (!(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) { why = "bad component constants"; return FV_ERR_ARG; }
+        if (c.kind != FV_SG) return "only stiffened-gas / ideal-gas components are supported";
+        if (!(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) return "bad component constants";
         bool seen = false;
         for (int j = 0; j < npi; ++j) seen = seen || pis[j] == c.pinf;
         if (!seen) pis[npi++] = c.pinf;
     }
-    if (npi > 2) { why = "at most two distinct pinf values"; return FV_ERR_ARG; }
-    if (eos->lim_vel < 0 || eos->lim_vel > 6 || eos->lim_scalar < 0 || eos->lim_scalar > 6) {
-        why = "bad limiter id";
-        return FV_ERR_ARG;
-    }
-    if (eos->precision != FV_FP64 && eos->precision != FV_MIXED) { why = "bad precision"; return FV_ERR_ARG; }
-    if (eos->thinc && !(eos->beta > 0.0)) { why = "THINC beta must be positive"; return FV_ERR_ARG; }
-    if (!(eos->sigma >= 0.0)) { why = "sigma must be >= 0"; return FV_ERR_ARG; }
-    if (eos->curvature != 0 && eos->curvature != 1) { why = "curvature must be 0 or 1"; return FV_ERR_ARG; }
+    if (npi > 2) return "at most two distinct pinf values";
+    if (eos->lim_vel < 0 || eos->lim_vel > 6 || eos->lim_scalar < 0 || eos->lim_scalar > 6) return "bad limiter id";
+    if (eos->precision != FV_FP64 && eos->precision != FV_MIXED) return "bad precision";
+    if (eos->thinc && !(eos->beta > 0.0)) return "THINC beta must be positive";
+    if (!(eos->sigma >= 0.0)) return "sigma must be >= 0";
+    if (eos->curvature != 0 && eos->curvature != 1) return "curvature must be 0 or 1";
     bool visc = false;
     for (int k = 0; k < cm->ncomp; ++k) {
         const fv_component& c = cm->comp[k];
-        if (!(c.mu >= 0.0) || !(c.kc >= 0.0) || !std::isfinite(c.mu) || !std::isfinite(c.kc)) {
-            why = "viscosity and conductivity must be finite and >= 0";
-            return FV_ERR_ARG;
-        }
+        if (!(c.mu >= 0.0) || !(c.kc >= 0.0) || !std::isfinite(c.mu) || !std::isfinite(c.kc))
+            return "viscosity and conductivity must be finite and >= 0";
         visc = visc || c.mu > 0.0 || c.kc > 0.0;
     }
-    if (visc && npr > 0) { why = "viscous terms need stiffened-gas / ideal-gas components"; return FV_ERR_ARG; }
+    if (visc && npr > 0) return "viscous terms need stiffened-gas / ideal-gas components";
     for (int d = 0; d < 3; ++d)
-        if (!std::isfinite(eos->gravity[d])) { why = "gravity must be finite"; return FV_ERR_ARG; }
-    return FV_OK;
+        if (!std::isfinite(eos->gravity[d])) return "gravity must be finite";
+    if (!std::isfinite(eos->sigma)) return "sigma must be finite";
+    return nullptr;
+}
+
+static fv_status validate(int ncases, const fv_grid* g, const fv_components* cm, const fv_eos* eos,
+                          std::string& why)
+{
+    const char* w = check_args(ncases, g, cm, eos);
+    if (!w) return FV_OK;
+    why = w;
+    return FV_ERR_ARG;
 }
 
 static bool has_visc(const fv_components* cm)
@@ -1437,6 +1431,50 @@ extern "C" fv_status fv_wait_selftest(int polls, int* err_word)
     return FV_OK;
 }
 
+// FP64 arithmetic-rate probe: every thread runs eight independent chains of
+// dependent fused multiply-adds (enough independent work per warp to keep the
+// FP64 pipe fed); the result only reaches memory if it equals a value the
+// chains never produce, so the work cannot be dropped.
+namespace {
+__device__ double g_fma_sink;
+__global__ void fma64_probe_kernel(int iters, double b, double c)
+{
+    double a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = 1e-3 * (threadIdx.x + j);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == -1.0) g_fma_sink = s;
+}
+}  // namespace
+
+extern "C" fv_status fv_probe_fp64(int blocks, int threads, int iters, double* ms, double* flops)
+{
+    if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !ms || !flops) return FV_ERR_ARG;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FV_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return FV_ERR_CUDA; }
+    fv_status st = FV_OK;
+    fma64_probe_kernel<<<blocks, threads>>>(iters, 0.9999999, 1e-7);   // warm-up
+    cudaEventRecord(e0);
+    fma64_probe_kernel<<<blocks, threads>>>(iters, 0.9999999, 1e-7);
+    cudaEventRecord(e1);
+    float t = 0.0f;
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+        st = FV_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t;
+    *flops = 2.0 * 8.0 * (double)blocks * threads * iters;
+    return st;
+}
+
 extern "C" const char* fv_status_string(int s)
 {
     switch (s) {
@@ -1486,51 +1524,18 @@ __global__ void noalloc_setup_kernel(CaseDesc C, CaseDesc* dcase, double* dt, do
         ipr[i] = make_int4(0, (i % px) * tx, ((i / px) % py) * ty, (i / (px * py)) * tz);
 }
 
-// argument checks of the no-alloc path (no strings, nothing allocated)
+// argument checks of the no-alloc path: those of fv_init for one case
+// (nothing allocated) plus what this path leaves out
 bool noalloc_args_ok(const fv_grid* g, const fv_components* cm, const fv_eos* e)
 {
-    if (!g || !cm || !e) return false;
-    const int nd = g->ndim;
-    if (nd != 2 && nd != 3) return false;
-    for (int d = 0; d < 3; ++d) {
-        if (g->n[d] < 1 || (d >= nd && g->n[d] != 1)) return false;
-        if (d < nd) {
-            if (!(g->hi[d] > g->lo[d])) return false;
-            for (int s = 0; s < 2; ++s)
-                if (g->bc[d][s] < 0 || g->bc[d][s] > 3) return false;
-            if ((g->bc[d][0] == FV_BC_PERIODIC) != (g->bc[d][1] == FV_BC_PERIODIC)) return false;
-            if ((d > 0 && g->bc[d][0] == FV_BC_INFLOW) || g->bc[d][1] == FV_BC_INFLOW) return false;
-        }
-    }
+    if (check_args(1, g, cm, e)) return false;
     if (g->in_u) return false;   // per-cell inflow velocities would need device memory
-    if (cm->ncomp < 2 || cm->ncomp > 3 || cm->liquid < 0 || cm->liquid >= cm->ncomp) return false;
-    if (cm->comp[0].kind == FV_BARO) {
-        // barotropic closure: FP64 form only (the mixed no-alloc variants are
-        // instantiated for the stiffened-gas closure)
-        if (e->precision != FV_FP64 || e->sigma != 0.0 || g->bc[0][0] == FV_BC_INFLOW) return false;
-        for (int k = 0; k < cm->ncomp; ++k) {
-            const fv_component& c = cm->comp[k];
-            if (c.kind != FV_BARO || c.mu != 0.0 || c.kc != 0.0) return false;
-            if (k == cm->liquid ? !(c.psat > 0.0 && c.rho_sl > 0.0 && c.rho_sv > 0.0 && c.rho_sv < c.rho_sl && c.cl > 0.0)
-                                : !(c.rt > 0.0))
-                return false;
-        }
-        if (e->lim_vel < 0 || e->lim_vel > 6 || e->lim_scalar < 0 || e->lim_scalar > 6) return false;
-        return !e->thinc || e->beta > 0.0;
-    }
-    double pa = -1.0, pb = -1.0;
-    for (int k = 0; k < cm->ncomp; ++k) {
-        const fv_component& c = cm->comp[k];
-        if (c.kind != FV_SG || !(c.gamma > 1.0) || !(c.cv > 0.0) || !(c.pinf >= 0.0)) return false;
-        if (!(c.mu >= 0.0) || !(c.kc >= 0.0) || !std::isfinite(c.mu) || !std::isfinite(c.kc)) return false;
-        if (pa < 0.0 || c.pinf == pa) pa = c.pinf;
-        else if (pb < 0.0 || c.pinf == pb) pb = c.pinf;
-        else return false;
-    }
-    if (e->lim_vel < 0 || e->lim_vel > 6 || e->lim_scalar < 0 || e->lim_scalar > 6) return false;
-    if (e->precision != FV_FP64 && e->precision != FV_MIXED) return false;
-    if (e->thinc && !(e->beta > 0.0)) return false;
-    return e->sigma >= 0.0;
+    for (int k = 0; k < cm->ncomp; ++k)
+        if (cm->comp[k].kind == FV_PR) return false;   // Peng-Robinson variants are not instantiated here
+    // barotropic closure: FP64 form only (the mixed no-alloc variants are
+    // instantiated for the stiffened-gas closure)
+    if (cm->comp[0].kind == FV_BARO && e->precision != FV_FP64) return false;
+    return true;
 }
 
 }  // namespace
@@ -1539,8 +1544,19 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
                                          int k, double dt, const double* q0, const double* qprev, double* qout,
                                          void* stream)
 {
-    if (!noalloc_args_ok(grid, comps, eos) || k < 1 || k > 4 || !(dt > 0.0) || !q0 || !qprev || !qout)
+    if (!noalloc_args_ok(grid, comps, eos) || k < 1 || k > 4 || !(dt > 0.0) || !std::isfinite(dt) || !q0 ||
+        !qprev || !qout)
         return FV_ERR_ARG;
+    // qout may be q0 itself (the update is pointwise) but may not overlap
+    // qprev, whose halo cells other blocks still read, or part of q0
+    {
+        const size_t bytes = sizeof(double) * (size_t)(grid->ndim + comps->ncomp + 1) * (size_t)grid->n[0] *
+                             (size_t)grid->n[1] * (size_t)grid->n[2];
+        const uintptr_t o = reinterpret_cast<uintptr_t>(qout), pv = reinterpret_cast<uintptr_t>(qprev),
+                        z = reinterpret_cast<uintptr_t>(q0);
+        if (o < pv + bytes && pv < o + bytes) return FV_ERR_ARG;
+        if (qout != q0 && o < z + bytes && z < o + bytes) return FV_ERR_ARG;
+    }
     // per-device set-up: the device address of the scratch array
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return FV_ERR_CUDA;
@@ -1621,6 +1637,7 @@ extern "C" fv_status fv_rk_stage_noalloc(const fv_grid* grid, const fv_component
     int e = 0;
     if (cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return FV_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return FV_ERR_CUDA;
+    if (e & ERR_TIMEOUT) return FV_ERR_CUDA;
     if (e & ERR_NONCONV) return FV_ERR_EOS_NONCONV;
     if (e & ERR_NONPHYS) return FV_ERR_NONPHYSICAL;
     return FV_OK;

@@ -387,7 +387,7 @@ __device__ __forceinline__ unsigned char sensor_flag(const DevParams& P, const R
 
 // Height-function curvature (Sec. 3.5 option) of cell hc from the encoded
 // liquid fraction ea (strides st): 5-cell columns along the axis where the
-// fraction varies most (a near-tie within 1e-12 goes to the lower axis), heights
+// fraction varies most (an exact tie goes to the lower axis), heights
 // H over the 3 (3x3) neighbouring columns, kappa = -H''/(1+H'^2)^{3/2} in 2D and
 // -(H_xx (1+H_y^2) + H_yy (1+H_x^2) - 2 H_xy H_x H_y)/(1+H_x^2+H_y^2)^{3/2} in 3D.
 template <int ND, typename R>
@@ -399,7 +399,7 @@ __device__ __forceinline__ R hf_kappa(const R* ea, int hc, const int* st, const 
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
         const R g = fdiv(fabs(A(hc + st[d]) - A(hc - st[d])), R(2) * cdx[d]);
-        if (g > gmax * R(1.0 + 1e-12)) { gmax = g; dir = d; }
+        if (g > gmax) { gmax = g; dir = d; }
     }
     // transverse axes t0 (and t1 in 3D)
     const int t0 = dir == 0 ? 1 : 0;

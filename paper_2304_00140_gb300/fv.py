@@ -29,7 +29,7 @@ EXPORTS = ["fv_workspace_size", "fv_init", "fv_init_ws", "fv_destroy", "fv_set_s
            "fv_get_state", "fv_set_state_device", "fv_get_state_device", "fv_rk_stage", "fv_step",
            "fv_step_async", "fv_get_diag", "fv_launch_count", "fv_last_error", "fv_status_string",
            "fv_profile", "fv_profile_read", "fv_rk_stage_noalloc", "fv_set_state_all", "fv_get_state_all",
-           "fv_wait_selftest"]
+           "fv_wait_selftest", "fv_probe_fp64"]
 FV_KERNEL_PRIM, FV_KERNEL_DT, FV_KERNEL_STAGE = range(3)
 
 
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
         for f in ("fv_set_state_all", "fv_get_state_all"):
             getattr(L, f).argtypes = [vp, C.c_int, vp]
         L.fv_wait_selftest.argtypes = [C.c_int, C.POINTER(C.c_int)]
+        L.fv_probe_fp64.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
         L.fv_rk_stage.argtypes = [vp, C.c_int, C.c_double]
         L.fv_step.argtypes = [vp, C.c_int, C.c_double, dp]
         L.fv_step_async.argtypes = [vp, C.c_int, C.c_double]

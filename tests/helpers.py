@@ -54,3 +54,31 @@ def rel_l1_vec(a, b, ndim):
     den = np.abs(b).reshape(nv, -1).sum(1)
     den[1:1 + ndim] = np.sqrt((b[1:1 + ndim] ** 2).sum(0)).sum()
     return np.abs(a - b).reshape(nv, -1).sum(1) / np.maximum(den, 1e-300)
+
+
+def gpu_stage(w, precision, k, dt, q0, qprev):
+    """one stage q0 + a_k dt R(qprev) of workload w on the GPU through the
+    C ABI's fv_rk_stage_noalloc, from host arrays (the tiled stage kernel)"""
+    import ctypes as C
+
+    import torch
+
+    from paper_2304_00140_gb300 import fv
+    L = fv.load()
+    g, cm = fv.make_grid(w), fv.make_components(w)
+    e = fv.make_eos(dict(w.scheme, precision=precision))
+    d0 = torch.from_numpy(np.ascontiguousarray(q0)).cuda()
+    dp = torch.from_numpy(np.ascontiguousarray(qprev)).cuda()
+    out = torch.empty_like(d0)
+    st = L.fv_rk_stage_noalloc(C.byref(g), C.byref(cm), C.byref(e), k, dt, C.c_void_p(d0.data_ptr()),
+                               C.c_void_p(dp.data_ptr()), C.c_void_p(out.data_ptr()),
+                               C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == fv.FV_OK, fv.status_string(st)
+    return out.cpu().numpy()
+
+
+def cell_rel_diff(a, b):
+    """per cell, the largest over fields of |a - b| / max |b| of the field"""
+    nv = a.shape[0]
+    scale = np.maximum(np.abs(b).reshape(nv, -1).max(axis=1), 1e-300)
+    return (np.abs(a - b) / scale.reshape((nv,) + (1,) * (a.ndim - 1))).max(axis=0)

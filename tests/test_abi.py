@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "thinc_fv.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fv_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(fv_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():
@@ -138,3 +138,28 @@ def test_barotropic_argument_checks():
     cm = fv.make_components(w)
     cm.comp[0] = fv.make_components(wl.advection(n=8)).comp[0]   # a stiffened gas among barotropic ones
     assert L.fv_workspace_size(1, g, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG
+
+
+def test_noalloc_host_side_argument_checks():
+    """fv_rk_stage_noalloc rejects, before any device work, what fv_init
+    rejects, extents whose ghosted sizes would overflow, and output arrays
+    that overlap its inputs (the pointers here are never dereferenced)"""
+    L = fv.load()
+    w = wl.random_state(n=(16, 12))
+    g, cm, e = fv.make_grid(w), fv.make_components(w), fv.make_eos(w.scheme)
+    nbytes = w.nvar * w.cells * 8
+    base = 1 << 40
+
+    def call(grid, k, q0, qprev, qout, eos=e):
+        return L.fv_rk_stage_noalloc(C.byref(grid), C.byref(cm), C.byref(eos), k, 1e-12, C.c_void_p(q0),
+                                     C.c_void_p(qprev), C.c_void_p(qout), None)
+    assert call(g, 1, base, base, base) == fv.FV_ERR_ARG                         # qout == qprev
+    assert call(g, 2, base, base + nbytes, base + nbytes + 8) == fv.FV_ERR_ARG   # overlaps qprev
+    assert call(g, 2, base + 8, base + 2 * nbytes, base) == fv.FV_ERR_ARG       # overlaps part of q0
+    assert call(g, 0, base, base + nbytes, base + 2 * nbytes) == fv.FV_ERR_ARG   # stage index
+    for n in ((2 ** 31 - 2, 2), (2 ** 16, 2 ** 16), (70000, 70000)):
+        big = fv.make_grid(w)
+        big.n[0], big.n[1] = n
+        assert call(big, 1, base, base, base + nbytes) == fv.FV_ERR_ARG
+    e2 = fv.make_eos(dict(w.scheme, gravity=(float("nan"), 0.0, 0.0)))
+    assert call(g, 2, base, base + nbytes, base + 2 * nbytes, eos=e2) == fv.FV_ERR_ARG

