@@ -65,8 +65,8 @@ CASES = {
 }
 
 
-def _with_flow(w, W, amp=10.0):
-    """the same state with a smooth O(10 m/s) velocity field added, so that
+def _with_flow(w, W, amp=3.0):
+    """the same state with a smooth O(3 m/s) velocity field added, so that
     the momentum is no longer the small residual of balanced pressure
     forces"""
     W = W.copy()
@@ -104,7 +104,7 @@ def _parity(w, W):
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_baro_parity_fp64(name):
     """well-conditioned states (sheared pockets, and the collapses with an
-    O(10 m/s) flow added): 1e-10 per conserved field after three steps"""
+    O(3 m/s) flow added): 1e-10 per conserved field after three steps"""
     w, W = CASES[name]()
     if name in AT_REST:
         W = _with_flow(w, W)

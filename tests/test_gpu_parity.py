@@ -174,13 +174,15 @@ def test_shock_bubble_full_size_windows():
     # (momentum components share the scale of the momentum vector)
     scale = np.abs(q).reshape(q.shape[0], -1).max(axis=1)
     scale[1:3] = np.sqrt(q[1] ** 2 + q[2] ** 2).max()
+    moved = []
     for lo, hi in wins:
         ref = oracle_step_window(o, q, dt, lo, hi)
         sl = (slice(None), 0, slice(lo[1], hi[1]), slice(lo[0], hi[0]))
         d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / scale
         assert np.all(d < 1e-10), (lo, d)
-        # the step moved every window by far more than the tolerance
-        assert (np.abs(ref[sl] - q[sl]).reshape(q.shape[0], -1).max(axis=1) / scale).max() > 1e-4
+        moved.append((np.abs(ref[sl] - q[sl]).reshape(q.shape[0], -1).max(axis=1) / scale).max())
+    # the step moved the shock and interface windows by far more than the tolerance
+    assert min(moved[:2]) > 1e-4, moved
 
 
 def test_nonphysical_state_reported_not_trapped():
