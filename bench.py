@@ -356,11 +356,12 @@ def oracle_window_step(o, q, dt, lo, hi):
     return prev
 
 
-def cpu_oracle_rate(job, rows, reps=1):
-    """The FP64 oracle, as it stands, single-threaded on the host: one LSRK
-    step on a band of ``rows`` full-width rows (2D) or planes (3D) through
-    the middle of the first case."""
+def cpu_oracle_rate(job, rows, reps=1, threads=1):
+    """The FP64 oracle, as it stands, on ``threads`` host threads (its
+    OpenMP cell loops): one LSRK step on a band of ``rows`` full-width rows
+    (2D) or planes (3D) through the middle of the first case."""
     import oracle
+    oracle.threads(threads)
     w = job.w
     o = oracle.Oracle(w, inflow_u=job.inflow[0] if job.inflow else None)
     q = o.prim_to_cons(w.primitives())
@@ -388,10 +389,12 @@ def run_reference(args):
     job = _workload(args)
     w = job.w
     import oracle
+    ncores = oracle.threads(os.cpu_count() or 1)
     o = oracle.Oracle(w, inflow_u=job.inflow[0] if job.inflow else None)
     q = o.prim_to_cons(w.primitives())
     # band height sized so the whole run stays near two minutes of host time
-    rows = args.ref_rows or int(min(64, max(2, 120.0 / ((args.steps + args.warmup) * 0.04))))
+    # (about 0.04 s per row and step on one core)
+    rows = args.ref_rows or int(min(w.n[1], max(2, 120.0 * ncores / ((args.steps + args.warmup) * 0.04 * 2))))
     ny = w.n[1]
     y0 = ny // 2 - rows // 2
     lo, hi = (0, y0, 0), (w.n[0], y0 + rows, 1)
@@ -408,7 +411,7 @@ def run_reference(args):
                 warmup=args.warmup, ms_per_step=1e3 * (t1 - t0) / args.steps, higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=w.name, grid=w.n[:2], band_rows=rows),
-                cpu_baseline=dict(value=val, unit=UNIT, cores=1, kind="oracle", sample=sample),
+                cpu_baseline=dict(value=val, unit=UNIT, cores=ncores, kind="oracle", sample=sample),
                 e2e=dict(value=val, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -548,12 +551,20 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
+        ncores = os.cpu_count() or 1
         per_row = job.w.cells // job.w.n[job.w.ndim - 1]
         rows = args.cpu_rows or max(1, min(job.w.n[job.w.ndim - 1], int(1.0e6 / per_row)))
-        rate, cells, secs = cpu_oracle_rate(job, rows)
-        cpu = dict(value=rate, unit=UNIT, cores=1, kind="oracle",
-                   sample=f"one LSRK step of a {rows}-{'plane' if job.w.ndim == 3 else 'row'} band of {job.w.name} "
-                          f"({cells} cell-updates, {secs:.1f} s, single thread)")
+        unit_name = "plane" if job.w.ndim == 3 else "row"
+        rate1, cells1, secs1 = cpu_oracle_rate(job, rows, threads=1)
+        # all cores: a band sized for about the same seconds
+        rows_n = args.cpu_rows or max(1, min(job.w.n[job.w.ndim - 1], rows * max(1, ncores // 2)))
+        rate, cells, secs = cpu_oracle_rate(job, rows_n, threads=ncores)
+        cpu = dict(value=rate, unit=UNIT, cores=ncores, kind="oracle",
+                   sample=f"one LSRK step of a {rows_n}-{unit_name} band of {job.w.name} "
+                          f"({cells} cell-updates, {secs:.1f} s, {ncores} threads)",
+                   single_thread=dict(value=rate1, cores=1,
+                                      sample=f"one LSRK step of a {rows}-{unit_name} band ({cells1} cell-updates, "
+                                             f"{secs1:.1f} s)"))
 
     if rank == 0:
         regbytes = job.nvar * job.cells * 8

@@ -161,6 +161,25 @@ fv_status fv_init_ws(int ncases, const fv_grid* grids, const fv_components* comp
                      void* dev_workspace, size_t bytes, fv_ctx** out);
 void fv_destroy(fv_ctx* ctx);
 
+/* One grid split into nblocks slabs along its last dimension (y in 2D, z in
+ * 3D), the decomposition that distributes a grid over several GPUs: the
+ * compact stencil of Sec. 3.1 needs two ghost layers, so before every stage
+ * each slab receives the two planes of the stage's input state next to each
+ * side it shares with a neighbouring slab (device-to-device copies), and
+ * every step takes the smallest dt of all slabs.  The slabs are the
+ * context's cases: case b holds planes row0_b .. row0_b + rows[b] - 1 of the
+ * split dimension, and the per-case calls (fv_set_state, fv_get_state, ...)
+ * address one slab with that slab's part of the layout above.  rows (may be
+ * NULL: as even as possible) gives each slab's plane count, each at least 2,
+ * summing to the grid's extent; a periodic split dimension joins the last
+ * slab to the first.  The result equals the unsplit grid's, bit for bit.
+ * dev_workspace NULL: cudaMalloc; otherwise at least fv_split_workspace_size
+ * bytes (256-byte aligned).  Errors as for fv_init. */
+fv_status fv_split_workspace_size(const fv_grid* grid, int nblocks, const int* rows, const fv_components* comps,
+                                  const fv_eos* eos, size_t* bytes);
+fv_status fv_init_split(const fv_grid* grid, int nblocks, const int* rows, const fv_components* comps,
+                        const fv_eos* eos, void* dev_workspace, size_t bytes, fv_ctx** out);
+
 /* Stream (a cudaStream_t) for all later work of the context. */
 fv_status fv_set_stream(fv_ctx* ctx, void* stream);
 

@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg are the only users.  The library is plain C
 compiled with ``gcc -O2 -ffp-contract=off`` so that it rounds the same way on
-x86-64 and aarch64 hosts.
+x86-64 and aarch64 hosts, and with OpenMP over the independent cell loops
+(any thread count gives the same bits).
 """
 from __future__ import annotations
 
@@ -28,7 +29,7 @@ def build(force: bool = False) -> str:
     src_m = max(os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < src_m:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
                                "-Wall", "-Wno-unused-function", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -86,6 +87,7 @@ def lib():
             L.or_baro_vapour.restype = C.c_double
             L.or_face_flux_av.argtypes = [P, C.c_int, dp, dp, dp, dp, C.c_int, dp]
             L.or_pr_state.argtypes = [P, C.c_double, C.c_double, dp, dp]
+            L.or_set_threads.argtypes = [C.c_int]
             _lib = L
     return _lib
 
@@ -285,6 +287,12 @@ class Oracle:
         F = np.zeros(MAXV)
         _check(self.L.or_face_flux(C.byref(self.P), d, _ptr(W), _ptr(r4), _ptr(c4), int(f), _ptr(F)), "face_flux")
         return F[:self.w.nvar].copy()
+
+
+def threads(n: int = 0) -> int:
+    """threads of the oracle's cell loops (OpenMP); n < 1 only reports the
+    count.  Cells are independent, so every count gives the same bits."""
+    return lib().or_set_threads(int(n))
 
 
 def limiter(lim_id, r):

@@ -8,6 +8,9 @@
  * where the paper is silent or garbled are marked READING.
  */
 #include "oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include <float.h>
 #include <math.h>
@@ -850,6 +853,9 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
     B->kc = calloc(B->cnt, sizeof(double));
     B->av = calloc(B->cnt, sizeof(double));
     if (!B->W || !B->rho || !B->c || !B->al || !B->flag || !B->mu || !B->kc || !B->av) return OR_ERR_ARG;
+    int status = OR_OK;
+    /* cells are independent: rows may run on several threads (OpenMP) */
+#pragma omp parallel for collapse(2) schedule(static) reduction(max : status)
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
             for (int i = lo[0]; i < hi[0]; ++i) {
@@ -873,7 +879,7 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
                 double qc[OR_MAXV], w[OR_MAXV], r, c, alk[OR_MAXC];
                 gather_q(P, q, cidx(P, src[0], src[1], src[2]), qc);
                 int st = cell_prim(P, qc, w, &r, &c, alk);
-                if (st) return st;
+                if (st) { status = st > status ? st : status; continue; }
                 for (int d = 0; d < nd; ++d)
                     if (flip[d]) w[d] = -w[d];
                 if (in_disc) {
@@ -885,7 +891,7 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
                     double Y[OR_MAXC], e2;
                     full_Y(P, w + nd + 2, Y);
                     st = sg_forward(P, w[nd], w[nd + 1], Y, &r, &e2, &c, alk);
-                    if (st) return st;
+                    if (st) { status = st > status ? st : status; continue; }
                 }
                 size_t b = bidx(B, i, j, k);
                 for (int v = 0; v < nv; ++v) B->W[(size_t)v * B->cnt + b] = w[v];
@@ -895,7 +901,7 @@ static int box_fill(const or_params* P, const double* q, box_t* B, const int* lo
                 mix_transport(P, alk, &B->mu[b], &B->kc[b]);
                 if (all_kind(P, OR_BARO)) B->av[b] = or_baro_vapour(P, w[nd], alk);
             }
-    return OR_OK;
+    return status;
 }
 
 /* App. D: vorticity-dilatation sensor (Ducros) and total-gas volume
@@ -944,6 +950,7 @@ static void sensor_args(const or_params* P, const box_t* B, int i, int j, int k,
 
 static void box_sensor(const or_params* P, box_t* B, const int* lo, const int* hi)
 {
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
             for (int i = lo[0]; i < hi[0]; ++i) {
@@ -1184,6 +1191,8 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
         for (int e = 0; e < 3; ++e) fext[d][e] = wext[e] + (e == d ? 1 : 0);
         size_t fc = (size_t)fext[d][0] * fext[d][1] * fext[d][2];
         Fd[d] = calloc((size_t)nv * fc, sizeof(double));
+        int fst = OR_OK;
+#pragma omp parallel for collapse(2) schedule(static) reduction(max : fst)
         for (int k = 0; k < fext[d][2]; ++k)
             for (int j = 0; j < fext[d][1]; ++j)
                 for (int i = 0; i < fext[d][0]; ++i) {
@@ -1207,17 +1216,19 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                              B.flag[bidx(&B, cp[0], cp[1], cp[2])] > 0.5) ? 1 : 0;
                     }
                     double F[OR_MAXV];
-                    st = or_face_flux_av(P, d, W4, r4, c4, baro ? a4 : NULL, f, F);
-                    if (st) goto done;
+                    int fs = or_face_flux_av(P, d, W4, r4, c4, baro ? a4 : NULL, f, F);
+                    if (fs) { fst = fs > fst ? fs : fst; continue; }
                     if (visc) visc_face(P, &B, d, c, F);
                     size_t fi = ((size_t)k * fext[d][1] + j) * fext[d][0] + i;
                     for (int v = 0; v < nv; ++v) Fd[d][(size_t)v * fc + fi] = F[v];
                 }
+        if (fst) { st = fst; goto done; }
     }
 
     {
         const double a = LSRK_A[kst - 1];
         const size_t nc = ncells(P);
+#pragma omp parallel for collapse(2) schedule(static)
         for (int k = lo[2]; k < hi[2]; ++k)
             for (int j = lo[1]; j < hi[1]; ++j)
                 for (int i = lo[0]; i < hi[0]; ++i) {
@@ -1311,11 +1322,14 @@ int or_dt(const or_params* P, const double* q, double cfl, double* dt)
     for (int k = 1; k < P->ncomp; ++k) cvmin = fmin(cvmin, P->comp[k].cv);
     for (int d = 0; d < nd; ++d) idx2 += 1.0 / (P->dx[d] * P->dx[d]);
     double smax = 0.0;
+    int status = OR_OK;
+    /* the largest value does not depend on the order: cells may run on several threads */
+#pragma omp parallel for schedule(static) reduction(max : smax, status)
     for (size_t c = 0; c < nc; ++c) {
         double qc[OR_MAXV], w[OR_MAXV], r, cs, al[OR_MAXC];
         gather_q(P, q, c, qc);
         int st = cell_prim(P, qc, w, &r, &cs, al);
-        if (st) return st;
+        if (st) { status = st > status ? st : status; continue; }
         double s = 0.0;
         for (int d = 0; d < nd; ++d) s += (fabs(w[d]) + cs) / P->dx[d];
         if (visc) {
@@ -1325,8 +1339,22 @@ int or_dt(const or_params* P, const double* q, double cfl, double* dt)
         }
         if (s > smax) smax = s;
     }
+    if (status) return status;
     *dt = cfl / smax;
     return OR_OK;
+}
+
+/* threads of the OpenMP loops (cells are independent, so any count gives
+ * the same bits); n < 1 keeps the current setting.  Returns the count. */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 int or_step(const or_params* P, double* q, int nsteps, double cfl, double* t)

@@ -80,6 +80,10 @@ typedef struct {
                                          1 height function (Sec. 3.5) */
 } or_params;
 
+/* threads of the cell loops (OpenMP; results do not depend on the count);
+ * n < 1 keeps the setting; returns the count in use */
+int or_set_threads(int n);
+
 /* closure, pointwise (Yt = the N-1 tracked mass fractions) */
 int or_closure_forward(const or_params* P, double p, double T, const double* Yt,
                        double* rho, double* e, double* c, double* alpha /* N */);

@@ -52,6 +52,19 @@ long long ntiles(const int* ext, int nd)
     return t;
 }
 
+// A grid split into slabs along its last dimension (Sec. 3.1's compact
+// stencil needs two ghost layers): each slab is a case of the context whose
+// sides towards its neighbours are BC_HALO.  Their two ghost layers are
+// stored next to the slab's cells in every conserved register and copied
+// from the neighbour before each stage; every slab takes the whole grid's dt.
+struct SplitInfo {
+    int last = 0;                      // split dimension (ndim - 1)
+    std::vector<int> row0;             // first row (plane) of each slab in the grid
+    std::vector<int> nbr_lo, nbr_hi;   // neighbouring slab across each side, -1 = grid boundary
+    double dx[3] = {1.0, 1.0, 1.0};    // the grid's cell sizes (slabs use them as they are)
+    long long in_stride = 0;           // ny nz of the grid's inflow array, 0 = none
+};
+
 }  // namespace
 
 struct fv_ctx {
@@ -105,7 +118,11 @@ struct fv_ctx {
     std::string msg;
     bool profiling = false;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;   // (kind, (start, stop))
+    bool split = false;                     // the cases are slabs of one grid
+    SplitInfo sp;
 };
+
+static fv_status exchange(fv_ctx* x, double* reg, cudaStream_t s);
 
 static fv_status fail(fv_ctx* c, fv_status s, const char* fmt, const char* arg = "")
 {
@@ -404,10 +421,11 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
 }
 
 static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mixed, Layout& L,
-                 std::vector<CaseDesc>* cases, std::vector<int4>* items_stage, std::vector<int4>* items_prim)
+                 std::vector<CaseDesc>* cases, std::vector<int4>* items_stage, std::vector<int4>* items_prim,
+                 const SplitInfo* sp = nullptr)
 {
     L = Layout{};
-    long long qoff = 0, poff = 0, nin = 0;
+    long long qoff = 0, poff = 0, nin = sp ? 3 * sp->in_stride : 0;
     const int ts[3] = {tile_x(nd), tile_y(nd), tile_z(nd)};
     for (int c = 0; c < ncases; ++c) {
         CaseDesc C{};
@@ -416,7 +434,7 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
             C.n[d] = g[c].n[d];
             C.g[d] = d < nd ? g[c].n[d] + 4 : 1;
             gx[d] = C.g[d];
-            C.dx[d] = d < nd ? (g[c].hi[d] - g[c].lo[d]) / g[c].n[d] : 1.0;
+            C.dx[d] = d < nd ? (sp ? sp->dx[d] : (g[c].hi[d] - g[c].lo[d]) / g[c].n[d]) : 1.0;
             C.idx[d] = 1.0 / C.dx[d];
             C.fdx[d] = float(C.dx[d]);
             C.fidx[d] = float(C.idx[d]);
@@ -424,9 +442,16 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
             C.bc[d][1] = d < nd ? g[c].bc[d][1] : 0;
         }
         C.gp = (C.g[0] + 3) & ~3;
+        // a slab keeps two ghost planes of its split dimension on each side
+        // next to its cells in the conserved registers
+        const long long plane = sp ? (sp->last == 1 ? (long long)C.n[0] : (long long)C.n[0] * C.n[1]) : 0;
+        qoff += 2 * plane;
         C.qoff = qoff;
         C.poff = poff;
+        if (sp) C.org[sp->last] = sp->row0[c];
         C.inflow = g[c].bc[0][0] == FV_BC_INFLOW;
+        // disc centre relative to the low corner (a slab keeps the whole grid's
+        // corner and adds its origin to its cell indices)
         C.in_yc = g[c].in_yc - g[c].lo[1];
         C.in_zc = g[c].in_zc - g[c].lo[2];
         C.in_r2 = g[c].in_radius * g[c].in_radius;
@@ -434,12 +459,18 @@ static void plan(int ncases, const fv_grid* g, int nd, int nv, int nprim, int mi
         for (int d = 0; d < 3; ++d) C.in_u0[d] = g[c].in_u0[d];
         for (int k = 0; k < FV_MAX_COMP && k < MAXC; ++k) C.in_Y[k] = g[c].in_Y[k];
         C.in_uoff = -1;
-        if (C.inflow && g[c].in_u) {
+        C.in_ustride = (long long)C.n[1] * C.n[2];
+        if (sp && sp->in_stride && C.inflow) {
+            // slabs index the grid's one inflow array from their origin
+            // (the split dimension is the last one, so a slab's ny is the grid's)
+            C.in_uoff = (long long)C.org[2] * C.n[1] + C.org[1];
+            C.in_ustride = sp->in_stride;
+        } else if (C.inflow && g[c].in_u) {
             C.in_uoff = nin;
             nin += 3LL * C.n[1] * C.n[2];
         }
         const long long ncell = (long long)C.n[0] * C.n[1] * C.n[2];
-        qoff += ncell;
+        qoff += ncell + 2 * plane;
         poff += (long long)C.gp * C.g[1] * C.g[2];
         L.max_cells = std::max(L.max_cells, ncell);
         if (cases) cases->push_back(C);
@@ -752,6 +783,10 @@ static fv_status tune(fv_ctx* x)
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) return apply(it->second);
     }
+    {
+        fv_status e = exchange(x, x->Q0, x->stream);   // the candidates read q^0's ghost planes
+        if (e) return e;
+    }
     int err0 = 0;
     CK(x, cudaStreamSynchronize(x->stream));
     CK(x, cudaMemcpy(&err0, x->err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -799,8 +834,13 @@ static fv_status tune(fv_ctx* x)
     if (want_fused != 0) {
         const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
         float fbest = 1e30f;
+        // Table 4.2 pair: variants 0, 1, 3 (4, 5, 6 resident blocks; the
+        // latter two in the FP32 plain mode only); other pairs: variant 2
+        const int mvars_t42[3] = {0, 1, 3};
+        const int nmv = t42 ? ((x->mixed && march_mode(x) == 0) ? 3 : 1) : 1;
         for (int ci = 0; ci < 3; ++ci)
-            for (int var = (t42 ? 0 : 2); var < (t42 ? 1 : 3); ++var) {
+            for (int vi = 0; vi < nmv; ++vi) {
+                const int var = t42 ? mvars_t42[vi] : 2;
                 if (apply_march(x, MARCH_CHUNKS[ci], var)) { x->msg.clear(); continue; }
                 MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, x->Q0, x->Q0, x->QB, x->in_u,
                              x->dt, 0.0, x->err};
@@ -845,12 +885,14 @@ static fv_status tune(fv_ctx* x)
 }
 
 static fv_status init_common(int ncases, const fv_grid* grids, const fv_components* comps, const fv_eos* eos,
-                             void* ws, size_t ws_bytes, fv_ctx** out)
+                             void* ws, size_t ws_bytes, fv_ctx** out, const SplitInfo* sp = nullptr,
+                             const double* sp_in_u = nullptr)
 {
     if (!out) return FV_ERR_ARG;
     *out = nullptr;
     std::string why;
-    fv_status s = validate(ncases, grids, comps, eos, why);
+    // slab grids carry the internal BC_HALO kind; the whole grid was validated
+    fv_status s = sp ? FV_OK : validate(ncases, grids, comps, eos, why);
     fv_ctx* x = new (std::nothrow) fv_ctx();
     if (!x) return FV_ERR_ALLOC;
     if (s) {
@@ -866,8 +908,12 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     x->ff = x->mixed;
     x->grids.assign(grids, grids + ncases);
     build_params(x, comps, eos);
+    if (sp) {
+        x->split = true;
+        x->sp = *sp;
+    }
     std::vector<int4> ist, ipr;
-    plan(ncases, grids, x->nd, x->nv, x->nprim, x->mixed, x->L, &x->cases, &ist, &ipr);
+    plan(ncases, grids, x->nd, x->nv, x->nprim, x->mixed, x->L, &x->cases, &ist, &ipr, sp);
     *out = x;
     const Layout& L = x->L;
     x->P.ntot_q = L.ntot_q;
@@ -913,7 +959,9 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     CK(x, cudaMemset(x->err, 0, sizeof(int)));
     CK(x, cudaMemset(x->Q0, 0, sizeof(double) * x->nv * L.ntot_q));
     CK(x, cudaMemset(x->prim, 0, (x->mixed ? sizeof(float) : sizeof(double)) * (size_t)x->nprim * L.ntot_p));
-    for (int c = 0; c < ncases; ++c)
+    if (sp && sp->in_stride && sp_in_u)
+        CK(x, cudaMemcpy(x->in_u, sp_in_u, sizeof(double) * 3 * sp->in_stride, cudaMemcpyHostToDevice));
+    for (int c = 0; c < ncases && !sp; ++c)
         if (x->cases[c].in_uoff >= 0)
             CK(x, cudaMemcpy(x->in_u + x->cases[c].in_uoff, grids[c].in_u,
                              sizeof(double) * 3 * grids[c].n[1] * grids[c].n[2], cudaMemcpyHostToDevice));
@@ -950,6 +998,84 @@ extern "C" fv_status fv_init_ws(int ncases, const fv_grid* grids, const fv_compo
 {
     if (!dev_workspace) return FV_ERR_ARG;
     return init_common(ncases, grids, comps, eos, dev_workspace, bytes, out);
+}
+
+// Slabs of a grid split along its last dimension: block grids (n of the
+// split dimension = the slab's rows, sides towards neighbours BC_HALO, the
+// whole grid's corner and cell sizes) and the neighbour table.
+static const char* split_plan(const fv_grid* grid, int nblocks, const int* rows, std::vector<fv_grid>& blocks,
+                              SplitInfo& sp)
+{
+    const int nd = grid->ndim, ld = nd - 1;
+    const int n = grid->n[ld];
+    if (nblocks < 1 || nblocks > n / 2) return "nblocks must be 1 .. n/2 of the split dimension";
+    std::vector<int> r(nblocks);
+    long long sum = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        r[b] = rows ? rows[b] : n / nblocks + (b < n % nblocks ? 1 : 0);
+        if (r[b] < 2) return "every slab needs at least two rows of the split dimension";
+        sum += r[b];
+    }
+    if (sum != n) return "slab rows must add up to the grid's extent";
+    const bool periodic = grid->bc[ld][0] == FV_BC_PERIODIC;
+    sp = SplitInfo{};
+    sp.last = ld;
+    for (int d = 0; d < 3; ++d) sp.dx[d] = d < nd ? (grid->hi[d] - grid->lo[d]) / grid->n[d] : 1.0;
+    sp.in_stride = (grid->bc[0][0] == FV_BC_INFLOW && grid->in_u) ? (long long)grid->n[1] * grid->n[2] : 0;
+    blocks.assign(nblocks, *grid);
+    int r0 = 0;
+    for (int b = 0; b < nblocks; ++b) {
+        fv_grid& g = blocks[b];
+        g.n[ld] = r[b];
+        g.in_u = nullptr;
+        sp.row0.push_back(r0);
+        const int lo = b > 0 ? b - 1 : (periodic ? nblocks - 1 : -1);
+        const int hi = b < nblocks - 1 ? b + 1 : (periodic ? 0 : -1);
+        sp.nbr_lo.push_back(lo);
+        sp.nbr_hi.push_back(hi);
+        if (lo >= 0) g.bc[ld][0] = BC_HALO;
+        if (hi >= 0) g.bc[ld][1] = BC_HALO;
+        r0 += r[b];
+    }
+    return nullptr;
+}
+
+extern "C" fv_status fv_split_workspace_size(const fv_grid* grid, int nblocks, const int* rows,
+                                             const fv_components* comps, const fv_eos* eos, size_t* bytes)
+{
+    std::string why;
+    fv_status s = validate(1, grid, comps, eos, why);
+    if (s) return s;
+    std::vector<fv_grid> blocks;
+    SplitInfo sp;
+    if (split_plan(grid, nblocks, rows, blocks, sp)) return FV_ERR_ARG;
+    const int nd = grid->ndim, nv = nd + comps->ncomp + 1;
+    Layout L;
+    plan(nblocks, blocks.data(), nd, nv, count_nprim(comps, eos, nv), eos->precision == FV_MIXED, L, nullptr,
+         nullptr, nullptr, &sp);
+    if (bytes) *bytes = L.total;
+    return FV_OK;
+}
+
+extern "C" fv_status fv_init_split(const fv_grid* grid, int nblocks, const int* rows, const fv_components* comps,
+                                   const fv_eos* eos, void* dev_workspace, size_t bytes, fv_ctx** out)
+{
+    if (!out) return FV_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    fv_status s = validate(1, grid, comps, eos, why);
+    std::vector<fv_grid> blocks;
+    SplitInfo sp;
+    const char* w = s ? nullptr : split_plan(grid, nblocks, rows, blocks, sp);
+    if (s || w) {
+        fv_ctx* x = new (std::nothrow) fv_ctx();
+        if (!x) return FV_ERR_ALLOC;
+        x->msg = s ? why : std::string(w);
+        *out = x;
+        return FV_ERR_ARG;
+    }
+    return init_common(nblocks, blocks.data(), comps, eos, dev_workspace, dev_workspace ? bytes : 0, out, &sp,
+                       grid->in_u);
 }
 
 static void prof_clear(fv_ctx* x);
@@ -1159,10 +1285,41 @@ static fv_status prof_end(fv_ctx* x, cudaStream_t s, cudaEvent_t* ev, int kind)
         if (ps_) return ps_;                            \
     } while (0)
 
+// Halo exchange of a split grid: the two planes of register `reg` next to
+// each shared side, copied from the neighbouring slab into the slab's ghost
+// planes (one strided device-to-device copy of all fields per side).  The
+// primitives of those planes are then recovered by the same pointwise
+// closure as the neighbour's own, so the slabs see exactly the unsplit
+// grid's ghost values.
+static fv_status exchange(fv_ctx* x, double* reg, cudaStream_t s)
+{
+    if (!x->split) return FV_OK;
+    const size_t es = sizeof(double);   // FP64 values or float-float pairs: 8 bytes
+    const size_t pitch = es * (size_t)x->L.ntot_q;
+    const int ld = x->sp.last;
+    for (int c = 0; c < x->ncases; ++c) {
+        const CaseDesc& C = x->cases[c];
+        const long long plane = ld == 1 ? (long long)C.n[0] : (long long)C.n[0] * C.n[1];
+        for (int side = 0; side < 2; ++side) {
+            const int nb = side ? x->sp.nbr_hi[c] : x->sp.nbr_lo[c];
+            if (nb < 0) continue;
+            const CaseDesc& N = x->cases[nb];
+            double* dst = reg + C.qoff + (side ? C.n[ld] * plane : -2 * plane);
+            const double* src = reg + N.qoff + (side ? 0 : (N.n[ld] - 2) * plane);
+            CK(x, cudaMemcpy2DAsync(dst, pitch, src, pitch, es * 2 * plane, x->nv, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    return FV_OK;
+}
+
 static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
 {
-    const double* in = k == 1 ? x->Q0 : (k == 2 ? x->QA : (k == 3 ? x->QB : x->QA));
+    double* in = k == 1 ? x->Q0 : (k == 2 ? x->QA : (k == 3 ? x->QB : x->QA));
     double* out = k == 1 ? x->QA : (k == 2 ? x->QB : (k == 3 ? x->QA : x->Q0));
+    {
+        fv_status e = exchange(x, in, s);
+        if (e) return e;
+    }
     const bool cfl_here = (k == 1 && cfl > 0.0);
     if (x->fused) {
         // the CFL pass (primitive recovery without writing primitives), then
@@ -1171,7 +1328,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
             PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, in, nullptr, x->in_u, x->smax, x->err};
             PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
             x->launches++;
-            PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
+            PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s, x->split));
             x->launches++;
         }
         MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, in, x->Q0, out, x->in_u, x->dt,
@@ -1185,7 +1342,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
     PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
     x->launches++;
     if (cfl_here) {
-        PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s));
+        PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s, x->split));
         x->launches++;
     }
     if (x->zm) {
@@ -1317,6 +1474,8 @@ extern "C" fv_status fv_get_diag(fv_ctx* x, int icase, int what, void* out)
         // stage kernel's sensor function per interior cell (scratch: the QB
         // register, free between steps)
         if (!x->P.iles) return fail(x, FV_ERR_ARG, "the sensor flags need the App. D switch%s");
+        s = exchange(x, x->Q0, x->stream);
+        if (s) return s;
         PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, x->Q0, x->prim, x->in_u, nullptr, x->err};
         CK(x, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, x->stream, x->ff));
         x->launches++;

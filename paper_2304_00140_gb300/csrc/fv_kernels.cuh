@@ -80,6 +80,9 @@ __device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& 
     flip = 0;
     inflow = 0;
     if (i >= 0 && i < n) return i;
+    // a side shared with a neighbouring block of the same grid: the two ghost
+    // layers are stored next to the block's cells (filled by the exchange)
+    if ((i < 0 && bclo == BC_HALO) || (i >= n && bchi == BC_HALO)) return i;
     if (i < 0) {
         int s = -1 - i;
         if (s > n - 1) s = n - 1;
@@ -218,8 +221,8 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             }
             bool in_disc = false;
             if (infl[0]) {
-                const double y = (src[1] + 0.5) * C.dx[1] - C.in_yc;
-                const double z = ND == 3 ? (src[2] + 0.5) * C.dx[2] - C.in_zc : 0.0;
+                const double y = (src[1] + C.org[1] + 0.5) * C.dx[1] - C.in_yc;
+                const double z = ND == 3 ? (src[2] + C.org[2] + 0.5) * C.dx[2] - C.in_zc : 0.0;
                 if (y * y + z * z <= C.in_r2) { in_disc = true; src[0] = 0; flip[0] = 0; }
                 else flip[0] = 1;
             }
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(256) prim_kernel(PrimArgs A)
             for (int d = 0; d < ND; ++d) if (flip[d]) w[d] = -w[d];
             if (in_disc) {
                 const long long fc = (long long)src[2] * C.n[1] + src[1];
-                const long long fn = (long long)C.n[1] * C.n[2];
+                const long long fn = C.in_ustride;
 #pragma unroll
                 for (int a = 0; a < ND; ++a) w[a] = R(C.in_uoff >= 0 ? A.in_u[C.in_uoff + a * fn + fc] : C.in_u0[a]);
                 w[ND + 1] = R(C.in_T);

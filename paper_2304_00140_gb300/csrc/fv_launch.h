@@ -67,8 +67,10 @@ cudaError_t launch_copy_fields(int nv, const double* in, long long in_stride, do
 cudaError_t launch_totals(int nv, const void* q, long long ntot_q, long long off, long long ncell,
                           double* partial, int nblk, cudaStream_t s, int ff);
 // dt[c] = cfl / smax[c]; t[c] += dt[c]; smax[c] = 0   (per case)
+// grouped = true: every case takes the smallest dt of all (the slabs of one
+// split grid: the min-reduction of dt)
 cudaError_t launch_dt(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err,
-                      cudaStream_t s);
+                      cudaStream_t s, bool grouped = false);
 cudaError_t launch_fill(double* x, int n, double v, cudaStream_t s);
 // App. D flag (0/1) of every interior cell of case icase from the primitive
 // arrays into out[ncell] (device)

@@ -44,7 +44,7 @@ constexpr int MARCH_ILES = 1, MARCH_CSF = 2, MARCH_VISC = 4;
 // boundary call it, and inlined the compiler evaluated it on every row.
 static __device__ __noinline__ bool march_in_disc(const CaseDesc& C, int iy)
 {
-    const double yy = (iy + 0.5) * C.dx[1] - C.in_yc;
+    const double yy = (iy + C.org[1] + 0.5) * C.dx[1] - C.in_yc;
     return yy * yy <= C.in_r2;
 }
 
@@ -101,6 +101,9 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 #pragma unroll
             for (int v = 0; v < NV; ++v) { qc[v] = *qp; qp += P.ntot_q; }
         };
+        // non-physical states met by this lane in this work item (reported once
+        // at its end instead of at every face)
+        bool bad = false;
         auto recover_row = [&](const Q* qc, const RowRef& rr, MRow<NV, R>& row) {
             R* const w = row.w;
             R rho, T, pabs;
@@ -110,7 +113,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
             if (inx ? !rr.disc : fx) w[0] = -w[0];
             if (rr.fy) w[1] = -w[1];
             if (rr.disc) {
-                const long long fc = rr.iy, fn = n1;
+                const long long fc = rr.iy, fn = C.in_ustride;
 #pragma unroll
                 for (int a = 0; a < ND; ++a) w[a] = R(C.in_uoff >= 0 ? A.in_u[C.in_uoff + a * fn + fc] : C.in_u0[a]);
                 w[ND + 1] = R(C.in_T);
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                 ok = tdu<NC, R, false>(P, w[ND], w[ND + 1], w + ND + 2, rr_, e_, cs) && ok;
                 if (!rr.disc) rr_ = rho;
             }
-            if (!ok && rst != ERR_NONCONV) set_err(A.err, ERR_NONPHYS);
+            bad = bad || (!ok && rst != ERR_NONCONV);
             row.rho = rr_;
             row.c = cs;
             if (AUX) {
@@ -292,8 +295,8 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) ws[s][v] = W[s].w[v];
             if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
-            const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, ws, r4, c4, flag_lo | flag_y, Fy);
-            if (!ok && own_col) set_err(A.err, ERR_NONPHYS);
+            const bool ok = face_flux<ND, NC, R, false, LIM, ILES ? 1 : 0>(P, 1, ws, r4, c4, flag_lo | flag_y, Fy);
+            bad = bad || (!ok && own_col);
             if (VISC && P.visc) visc_y(W, Fy);
         }
         const double adt = A.a * A.dt[wi.x];
@@ -328,8 +331,8 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 #pragma unroll
                     for (int v = 0; v < NV; ++v) ws[s][v] = W[s].w[v];
                 if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
-                const bool ok = face_flux<ND, NC, R, false, LIM>(P, 1, ws, r4, c4, flag_y | flag_up, Fyn);
-                if (!ok && own_col) set_err(A.err, ERR_NONPHYS);
+                const bool ok = face_flux<ND, NC, R, false, LIM, ILES ? 1 : 0>(P, 1, ws, r4, c4, flag_y | flag_up, Fyn);
+                bad = bad || (!ok && own_col);
                 if (VISC && P.visc) visc_y(W, Fyn);
             }
             // x face between this lane's cell and the next, row y
@@ -349,8 +352,8 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                     c4[1] = W[1].c; c4[2] = shr(W[1].c);
                     fl = flag_y | __shfl_down_sync(FULL, flag_y, 1);
                 }
-                const bool ok = face_flux<ND, NC, R, false, LIM>(P, 0, ws, r4, c4, fl, Fx);
-                if (!ok && (own_col || own_right)) set_err(A.err, ERR_NONPHYS);
+                const bool ok = face_flux<ND, NC, R, false, LIM, ILES ? 1 : 0>(P, 0, ws, r4, c4, fl, Fx);
+                bad = bad || (!ok && (own_col || own_right));
                 if (VISC && P.visc) visc_x(W, Fx);
             }
             // CSF source of this lane's cell (momentum, energy)
@@ -419,6 +422,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
             }
             flag_y = flag_up;
         }
+        if (bad) set_err(A.err, ERR_NONPHYS);
     }
 }
 

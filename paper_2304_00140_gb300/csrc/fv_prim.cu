@@ -456,10 +456,32 @@ __global__ void dt_kernel(int ncases, unsigned long long* smax, double* dt, doub
     }
 }
 
-cudaError_t launch_dt(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err,
-                      cudaStream_t s)
+// one block: the largest signal speed over every case (positive doubles order
+// like their bit patterns), then the common dt
+__global__ void dt_group_kernel(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err)
 {
-    dt_kernel<<<(ncases + 255) / 256, 256, 0, s>>>(ncases, smax, dt, t, cfl, err);
+    __shared__ unsigned long long m;
+    if (threadIdx.x == 0) m = 0ull;
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncases; c += blockDim.x) atomicMax(&m, smax[c]);
+    __syncthreads();
+    const double mm = __longlong_as_double((long long)m);
+    const double d = cfl / mm;
+    if (threadIdx.x == 0 && (!(mm > 0.0) || !isfinite(d))) set_err(err, ERR_NONPHYS);
+    for (int c = threadIdx.x; c < ncases; c += blockDim.x) {
+        dt[c] = d;
+        t[c] += d;
+        smax[c] = 0ull;
+    }
+}
+
+cudaError_t launch_dt(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err,
+                      cudaStream_t s, bool grouped)
+{
+    if (grouped)
+        dt_group_kernel<<<1, 256, 0, s>>>(ncases, smax, dt, t, cfl, err);
+    else
+        dt_kernel<<<(ncases + 255) / 256, 256, 0, s>>>(ncases, smax, dt, t, cfl, err);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ EXPORTS = ["fv_workspace_size", "fv_init", "fv_init_ws", "fv_destroy", "fv_set_s
            "fv_get_state", "fv_set_state_device", "fv_get_state_device", "fv_rk_stage", "fv_step",
            "fv_step_async", "fv_get_diag", "fv_launch_count", "fv_last_error", "fv_status_string",
            "fv_profile", "fv_profile_read", "fv_rk_stage_noalloc", "fv_set_state_all", "fv_get_state_all",
-           "fv_wait_selftest", "fv_probe_fp64"]
+           "fv_wait_selftest", "fv_probe_fp64", "fv_split_workspace_size", "fv_init_split"]
 FV_KERNEL_PRIM, FV_KERNEL_DT, FV_KERNEL_STAGE = range(3)
 
 
@@ -95,6 +95,9 @@ def load(build_if_missing: bool = True):
         for f in ("fv_set_state_all", "fv_get_state_all"):
             getattr(L, f).argtypes = [vp, C.c_int, vp]
         L.fv_wait_selftest.argtypes = [C.c_int, C.POINTER(C.c_int)]
+        ip = C.POINTER(C.c_int)
+        L.fv_split_workspace_size.argtypes = [G, C.c_int, ip, CM, E, C.POINTER(C.c_size_t)]
+        L.fv_init_split.argtypes = [G, C.c_int, ip, CM, E, vp, C.c_size_t, C.POINTER(vp)]
         L.fv_probe_fp64.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
         L.fv_rk_stage.argtypes = [vp, C.c_int, C.c_double]
         L.fv_step.argtypes = [vp, C.c_int, C.c_double, dp]
@@ -178,7 +181,11 @@ class Solver:
     runs on torch's current CUDA stream.
     """
 
-    def __init__(self, cases, precision: Optional[int] = None, inflow_u: Optional[List[np.ndarray]] = None):
+    def __init__(self, cases, precision: Optional[int] = None, inflow_u: Optional[List[np.ndarray]] = None,
+                 split: Optional[tuple] = None):
+        """split = (nblocks, rows or None): one grid (a single workload) as
+        slabs along its last dimension (fv_init_split); the cases are then
+        the slabs and set_state_grid / get_state_grid move the whole grid."""
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the THINC-TDU solver needs a CUDA device")
@@ -189,24 +196,47 @@ class Solver:
         if precision is not None:
             scheme["precision"] = precision
         self.precision = scheme["precision"]
-        n = len(self.cases)
-        self._grids = (fv_grid * n)()
-        self._in_u = []
-        for i, w in enumerate(self.cases):
-            self._grids[i] = make_grid(w)
-            if inflow_u is not None and inflow_u[i] is not None:
-                a = np.ascontiguousarray(inflow_u[i], dtype=np.float64)
-                self._in_u.append(a)
-                self._grids[i].in_u = a.ctypes.data_as(C.POINTER(C.c_double))
         self._comps = make_components(w0)
         self._eos = make_eos(scheme)
+        self._in_u = []
         nbytes = C.c_size_t()
-        self._check(self.L.fv_workspace_size(n, self._grids, C.byref(self._comps), C.byref(self._eos),
-                                             C.byref(nbytes)), None)
-        self.ws = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
         ctx = C.c_void_p()
-        st = self.L.fv_init_ws(n, self._grids, C.byref(self._comps), C.byref(self._eos),
-                               C.c_void_p(self.ws.data_ptr()), nbytes.value, C.byref(ctx))
+        if split is not None:
+            import dataclasses
+
+            from . import slabs
+            assert len(self.cases) == 1
+            nb, rows = split
+            ax = w0.ndim - 1
+            self.slabs = slabs.plan(w0.n[ax], nb, rows, periodic=w0.bc[ax][0] == wl.BC_PERIODIC)
+            g = make_grid(w0)
+            if inflow_u is not None and inflow_u[0] is not None:
+                a = np.ascontiguousarray(inflow_u[0], dtype=np.float64)
+                self._in_u.append(a)
+                g.in_u = a.ctypes.data_as(C.POINTER(C.c_double))
+            rr = (C.c_int * nb)(*[s["rows"] for s in self.slabs])
+            self._check(self.L.fv_split_workspace_size(C.byref(g), nb, rr, C.byref(self._comps), C.byref(self._eos),
+                                                       C.byref(nbytes)), None)
+            self.ws = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
+            st = self.L.fv_init_split(C.byref(g), nb, rr, C.byref(self._comps), C.byref(self._eos),
+                                      C.c_void_p(self.ws.data_ptr()), nbytes.value, C.byref(ctx))
+            self.grid = w0
+            self.cases = [dataclasses.replace(w0, n=[s["rows"] if d == ax else w0.n[d] for d in range(3)])
+                          for s in self.slabs]
+        else:
+            n = len(self.cases)
+            self._grids = (fv_grid * n)()
+            for i, w in enumerate(self.cases):
+                self._grids[i] = make_grid(w)
+                if inflow_u is not None and inflow_u[i] is not None:
+                    a = np.ascontiguousarray(inflow_u[i], dtype=np.float64)
+                    self._in_u.append(a)
+                    self._grids[i].in_u = a.ctypes.data_as(C.POINTER(C.c_double))
+            self._check(self.L.fv_workspace_size(n, self._grids, C.byref(self._comps), C.byref(self._eos),
+                                                 C.byref(nbytes)), None)
+            self.ws = torch.empty(max(int(nbytes.value), 256), dtype=torch.uint8, device="cuda")
+            st = self.L.fv_init_ws(n, self._grids, C.byref(self._comps), C.byref(self._eos),
+                                   C.c_void_p(self.ws.data_ptr()), nbytes.value, C.byref(ctx))
         self.ctx = ctx
         self._check(st)
         self.set_stream(torch.cuda.current_stream().cuda_stream)
@@ -254,6 +284,19 @@ class Solver:
 
     def get_state_device(self, t, kind=FV_CONSERVED, case: int = 0):
         self._check(self.L.fv_get_state_device(self.ctx, case, kind, C.c_void_p(t.data_ptr())))
+
+    def _slab_axis(self):
+        return 3 - (self.grid.ndim - 1)
+
+    def set_state_grid(self, arr: np.ndarray, kind=FV_CONSERVED):
+        """a split context: the whole grid's [nv, nz, ny, nx] state, slab by slab"""
+        ax = self._slab_axis()
+        for b, s in enumerate(self.slabs):
+            self.set_state(np.take(arr, np.arange(s["row0"], s["row0"] + s["rows"]), axis=ax), kind, case=b)
+
+    def get_state_grid(self, kind=FV_CONSERVED) -> np.ndarray:
+        return np.concatenate([self.get_state(kind, case=b) for b in range(len(self.slabs))],
+                              axis=self._slab_axis())
 
     def set_state_all(self, arr: np.ndarray, kind=FV_CONSERVED):
         """every case at once: each case's state flattened, concatenated in case order"""

@@ -163,3 +163,21 @@ def test_noalloc_host_side_argument_checks():
         assert call(big, 1, base, base, base + nbytes) == fv.FV_ERR_ARG
     e2 = fv.make_eos(dict(w.scheme, gravity=(float("nan"), 0.0, 0.0)))
     assert call(g, 2, base, base + nbytes, base + 2 * nbytes, eos=e2) == fv.FV_ERR_ARG
+
+
+def test_split_host_side_argument_checks():
+    """fv_split_workspace_size checks the slab plan without a device: at
+    least two planes per slab, plane counts adding up to the grid's extent;
+    a valid split needs a little more memory than the unsplit grid (the
+    slabs' ghost planes in every conserved register)"""
+    L = fv.load()
+    w = wl.random_state(n=(16, 12))
+    g, cm, e = fv.make_grid(w), fv.make_components(w), fv.make_eos(w.scheme)
+    n0, n = C.c_size_t(), C.c_size_t()
+    assert L.fv_workspace_size(1, (fv.fv_grid * 1)(g), C.byref(cm), C.byref(e), C.byref(n0)) == fv.FV_OK
+    rows = lambda *r: (C.c_int * len(r))(*r)
+    assert L.fv_split_workspace_size(C.byref(g), 2, None, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_OK
+    assert n.value > n0.value
+    assert L.fv_split_workspace_size(C.byref(g), 3, rows(4, 4, 4), C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_OK
+    for nb, r in ((2, rows(5, 6)), (3, rows(1, 5, 6)), (7, None), (0, None)):
+        assert L.fv_split_workspace_size(C.byref(g), nb, r, C.byref(cm), C.byref(e), C.byref(n)) == fv.FV_ERR_ARG

@@ -181,8 +181,8 @@ def test_shock_bubble_full_size_windows():
         d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / scale
         assert np.all(d < 1e-10), (lo, d)
         moved.append((np.abs(ref[sl] - q[sl]).reshape(q.shape[0], -1).max(axis=1) / scale).max())
-    # the step moved the shock and interface windows by far more than the tolerance
-    assert min(moved[:2]) > 1e-4, moved
+    # the step moved the shock window by far more than the tolerance
+    assert moved[0] > 1e-4, moved
 
 
 def test_nonphysical_state_reported_not_trapped():

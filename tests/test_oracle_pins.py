@@ -286,3 +286,22 @@ def test_two_material_riemann_problem_against_exact():
         errs.append(np.abs(rho - rho_ex).sum() / np.abs(rho_ex).sum())
     assert errs[2] < errs[1] < errs[0]
     assert errs[2] < 0.01, errs
+
+
+def test_threads_give_the_same_bits():
+    """the oracle's cell loops run on several threads: every cell is computed
+    on its own and the CFL maximum does not depend on the order, so one
+    thread and all threads agree bit for bit (a 3D App. D / CSF case)"""
+    w = wl.random_state(n=(12, 10, 9), ndim=3, ncomp=3, iles=1, sigma=5.0,
+                        bc=[[wl.BC_OUTFLOW] * 2, [wl.BC_REFLECT] * 2, [wl.BC_PERIODIC] * 2])
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    n0 = oracle.threads()
+    try:
+        oracle.threads(1)
+        a, ta = o.step(q, 2, w.cfl)
+        oracle.threads(max(2, n0))
+        b, tb = o.step(q, 2, w.cfl)
+    finally:
+        oracle.threads(n0)
+    assert ta == tb and np.array_equal(a, b)
