@@ -52,7 +52,7 @@ class Params(C.Structure):
                 ("in_yc", C.c_double), ("in_zc", C.c_double), ("in_radius", C.c_double),
                 ("in_T", C.c_double), ("in_Y", C.c_double * MAXC), ("in_u", C.POINTER(C.c_double)),
                 ("in_u0", C.c_double * 3), ("grav", C.c_double * 3), ("thr_vap", C.c_double),
-                ("curv", C.c_int)]
+                ("curv", C.c_int), ("st_model", C.c_int)]
 
 
 def lib():
@@ -88,6 +88,8 @@ def lib():
             L.or_face_flux_av.argtypes = [P, C.c_int, dp, dp, dp, dp, C.c_int, dp]
             L.or_pr_state.argtypes = [P, C.c_double, C.c_double, dp, dp]
             L.or_set_threads.argtypes = [C.c_int]
+            L.or_capillary_force.argtypes = [P, dp, dp]
+            L.or_face_flux_kappa.argtypes = [P, C.c_int, dp, dp, dp, C.c_int, C.c_double, C.c_double, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -130,6 +132,7 @@ def make_params(w, inflow_u: np.ndarray | None = None) -> Params:
         P.grav[d] = g
     P.thr_vap = s.get("thr_vap", 0.4)
     P.curv = int(s.get("curvature", 0))
+    P.st_model = int(s.get("st_model", 0))
     if w.inflow:
         f = w.inflow
         P.in_yc, P.in_zc, P.in_radius, P.in_T = f["yc"] - w.lo[1], f["zc"] - w.lo[2], f["radius"], f["T"]
@@ -233,6 +236,28 @@ class Oracle:
         gap = np.zeros(self.shape[1:])
         _check(self.L.or_hf_axis(C.byref(self.P), _ptr(q), _ptr(axis), _ptr(gap)), "hf_axis")
         return axis.astype(int), gap
+
+    def capillary_force(self, q):
+        """momentum source of the capillary face jumps per interior cell,
+        [ndim, nz, ny, nx] (st_model = 1)"""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        S = np.zeros((self.w.ndim,) + self.shape[1:])
+        _check(self.L.or_capillary_force(C.byref(self.P), _ptr(q), _ptr(S)), "capillary_force")
+        return S
+
+    def face_flux_kappa(self, d, W4, kapL, kapR, alpha2, rho4=None, c4=None, f=1):
+        """one face with the capillary jump (st_model = 1) between cells of
+        curvatures kapL, kapR and liquid fractions alpha2: (F, G)"""
+        W = np.zeros((4, MAXV))
+        W4 = np.asarray(W4, dtype=np.float64)
+        W[:, :W4.shape[1]] = W4
+        r4 = np.ascontiguousarray(rho4 if rho4 is not None else np.ones(4), dtype=np.float64)
+        c4 = np.ascontiguousarray(c4 if c4 is not None else np.ones(4), dtype=np.float64)
+        F, G = np.zeros(MAXV), np.zeros(2)
+        a2 = np.ascontiguousarray(alpha2, dtype=np.float64)
+        _check(self.L.or_face_flux_kappa(C.byref(self.P), d, _ptr(W), _ptr(r4), _ptr(c4), int(f), kapL, kapR,
+                                         _ptr(a2), _ptr(F), _ptr(G)), "face_flux_kappa")
+        return F[:self.w.nvar].copy(), G
 
     def sensor(self, q):
         q = np.ascontiguousarray(q, dtype=np.float64)

@@ -615,8 +615,33 @@ int or_face_flux(const or_params* P, int d, const double* W4, const double* rho4
  * while rho is not, and the profile's F then leaves [0, 1]). */
 static int rho_monotone(double xm, double x, double xp) { return (x - xm) * (xp - x) > 0.0; }
 
+/* One face (see or_face_flux_av); with the capillary-jump model of Sec. 3.5
+ * (st_model = 1, sigma > 0) the contact's pressure jump [P] = sigma kappa
+ * [alpha] enters the Riemann solution: u* gains J / (Z_L + Z_R) with
+ * J = sigma kappa_f (alpha_i+1 - alpha_i), and the two sides see p* -/+ J/2.
+ * READING: alpha is the liquid volume fraction, kappa = +1/R for a drop
+ * (the CSF curvature), kappa_f the mean of the two cells' curvatures, and
+ * [alpha] the jump of the two cells' fractions (al2 = alpha_i, alpha_i+1):
+ * the reconstructed states of a diffuse or THINC-sharpened interface place
+ * most of the jump inside the cells, where no face would see it, while the
+ * cell jumps add up across the interface to its full jump.  G[0], G[1]
+ * receive J / 2 and u* J / 2: the face's left cell takes F minus
+ * (0, G[0] n, G[1], 0), its right cell F plus it. */
+static int face_flux_core(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
+                          const double* av4, int f, double kapL, double kapR, const double* al2, double* F,
+                          double* G);
+
 int or_face_flux_av(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
                     const double* av4, int f, double* F)
+{
+    double G[2];
+    const double al2[2] = {0.0, 0.0};
+    return face_flux_core(P, d, W4, rho4, c4, av4, f, 0.0, 0.0, al2, F, G);
+}
+
+static int face_flux_core(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
+                          const double* av4, int f, double kapL, double kapR, const double* al2, double* F,
+                          double* G)
 {
     const int nd = P->ndim, N = P->ncomp, nv = nvar(P);
     const int ip = nd, iT = nd + 1, iY = nd + 2;
@@ -655,6 +680,9 @@ int or_face_flux_av(const or_params* P, int d, const double* W4, const double* r
     if (st) return st;
     st = or_closure_forward(P, WR[ip], WR[iT], WR + iY, &rR, &eR, &cR, NULL);
     if (st) return st;
+    /* capillary pressure jump across the contact (Sec. 3.5, [P] = sigma k [alpha]) */
+    const double J = (P->st_model == 1 && P->sigma != 0.0)
+                         ? P->sigma * 0.5 * (kapL + kapR) * (al2[1] - al2[0]) : 0.0;
     if (baro && av4 && P->thinc && !smooth) {
         double tl, tr, YL[OR_MAXC], YR[OR_MAXC], cs;
         or_thinc(P->beta, P->thinc_gamma, rho4[0], rho4[1], rho4[2], rho4[3], &tl, &tr);
@@ -680,20 +708,22 @@ int or_face_flux_av(const or_params* P, int d, const double* W4, const double* r
         double IL = (3.0 * rho4[1] + rho4[2]) * cm / 4.0;
         double IR = (rho4[1] + 3.0 * rho4[2]) * cm / 4.0;
         if (f) {
-            us = (IL * uL + IR * uR + pL - pR) / (IL + IR);
+            us = (IL * uL + IR * uR + pL - pR + J) / (IL + IR);
             ps = 0.5 * (pL + pR);
         } else {
             /* READING: Delta^3 p = p_{i-1} - 3 p_i + 3 p_{i+1} - p_{i+2}
              * (sign that damps odd-even pressure modes, like the p_L - p_R
              * term of the upwind branch), scaled by d3p_coef */
             double d3 = P->d3p_coef * (w1[ip] - 3.0 * w2[ip] + 3.0 * w3[ip] - w4[ip]);
-            us = uL - d3 / (IL + IR);
+            us = uL - (d3 - J) / (IL + IR);
             ps = pL;
         }
     } else {
         ps = 0.5 * (pL + pR);                                            /* Eq. 3-1 */
-        us = (rL * cL * uL + rR * cR * uR + pL - pR) / (rL * cL + rR * cR); /* Eq. 3-2 */
+        us = (rL * cL * uL + rR * cR * uR + pL - pR + J) / (rL * cL + rR * cR); /* Eq. 3-2 */
     }
+    G[0] = 0.5 * J;
+    G[1] = 0.5 * J * us;
 
     /* u* selects the upstream side; the convected state is that side's
      * reconstructed (rho, rho u, rho E, rho xi) (Eq. 2-2, rho H = rho E + p) */
@@ -1156,6 +1186,44 @@ static void visc_face(const or_params* P, const box_t* B, int d, const int* cl, 
  * One Runge-Kutta stage over the window [wlo, whi) (whole interior when
  * NULL): Algorithm 1 in order.
  * --------------------------------------------------------------------- */
+/* interior cell that a (possibly ghost) cell index maps to under the
+ * boundary update (the inflow disc's ghosts take their mirror cell) */
+static size_t mapped_cell(const or_params* P, const int* c)
+{
+    int src[3];
+    for (int d = 0; d < 3; ++d) {
+        int flip, infl;
+        src[d] = (d < P->ndim) ? map_dim(P->n[d], c[d], P->bc[d][0], P->bc[d][1], &flip, &infl) : 0;
+    }
+    return cidx(P, src[0], src[1], src[2]);
+}
+
+/* the CSF curvature (vertex normals of the smoothed fraction, or the height
+ * function) of every interior cell, into a new array *out */
+static int interior_curvature(const or_params* P, const double* q, double** out)
+{
+    const int nd = P->ndim;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    *out = calloc(ncells(P), sizeof(double));
+    if (!*out) return OR_ERR_ARG;
+    int st = box_fill(P, q, &B, blo, bhi);
+    if (!st)
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) {
+                    double g[3];
+                    csf_parts(P, &B, i, j, k, &(*out)[cidx(P, i, j, k)], g);
+                }
+    box_free(&B);
+    return st;
+}
+
 int or_stage(const or_params* P, int kst, double dt, const double* q0, const double* qprev,
              double* qout, const int* wlo, const int* whi)
 {
@@ -1184,13 +1252,24 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
 
     int wext[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
     size_t wcnt = (size_t)wext[0] * wext[1] * wext[2];
+    /* capillary-jump model: the CSF curvature of every interior cell (on a
+     * box of the whole grid); READING: a ghost cell takes the curvature of
+     * the interior cell the boundary update maps it to */
+    const int capj = P->st_model == 1 && P->sigma != 0.0;
+    double* kap = NULL;
+    if (capj) {
+        st = interior_curvature(P, qprev, &kap);
+        if (st) { box_free(&B); return st; }
+    }
     /* face fluxes per direction: faces c[d] = lo[d]-1 .. hi[d]-1 (face c+1/2) */
     double* Fd[3] = {NULL, NULL, NULL};
+    double* Gd[3] = {NULL, NULL, NULL};   /* capillary jump halves J / 2 and u* J / 2 per face */
     int fext[3][3];
     for (int d = 0; d < nd; ++d) {
         for (int e = 0; e < 3; ++e) fext[d][e] = wext[e] + (e == d ? 1 : 0);
         size_t fc = (size_t)fext[d][0] * fext[d][1] * fext[d][2];
         Fd[d] = calloc((size_t)nv * fc, sizeof(double));
+        if (capj) Gd[d] = calloc(2 * fc, sizeof(double));
         int fst = OR_OK;
 #pragma omp parallel for collapse(2) schedule(static) reduction(max : fst)
         for (int k = 0; k < fext[d][2]; ++k)
@@ -1215,12 +1294,29 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                         f = (B.flag[bidx(&B, c[0], c[1], c[2])] > 0.5 ||
                              B.flag[bidx(&B, cp[0], cp[1], cp[2])] > 0.5) ? 1 : 0;
                     }
-                    double F[OR_MAXV];
-                    int fs = or_face_flux_av(P, d, W4, r4, c4, baro ? a4 : NULL, f, F);
+                    double F[OR_MAXV], G[2], kl = 0.0, kr = 0.0;
+                    if (capj) {
+                        int cp[3] = {c[0], c[1], c[2]};
+                        cp[d] += 1;
+                        kl = kap[mapped_cell(P, c)];
+                        kr = kap[mapped_cell(P, cp)];
+                    }
+                    double al2[2] = {0.0, 0.0};
+                    if (capj) {
+                        int cp[3] = {c[0], c[1], c[2]};
+                        cp[d] += 1;
+                        al2[0] = B.al[bidx(&B, c[0], c[1], c[2])];
+                        al2[1] = B.al[bidx(&B, cp[0], cp[1], cp[2])];
+                    }
+                    int fs = face_flux_core(P, d, W4, r4, c4, baro ? a4 : NULL, f, kl, kr, al2, F, G);
                     if (fs) { fst = fs > fst ? fs : fst; continue; }
                     if (visc) visc_face(P, &B, d, c, F);
                     size_t fi = ((size_t)k * fext[d][1] + j) * fext[d][0] + i;
                     for (int v = 0; v < nv; ++v) Fd[d][(size_t)v * fc + fi] = F[v];
+                    if (capj) {
+                        Gd[d][fi] = G[0];
+                        Gd[d][fc + fi] = G[1];
+                    }
                 }
         if (fst) { st = fst; goto done; }
     }
@@ -1233,7 +1329,7 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
             for (int j = lo[1]; j < hi[1]; ++j)
                 for (int i = lo[0]; i < hi[0]; ++i) {
                     double S[OR_MAXV] = {0};
-                    if (P->sigma != 0.0) {
+                    if (P->sigma != 0.0 && !capj) {
                         double s4[4];
                         csf_cell(P, &B, i, j, k, s4);
                         for (int d = 0; d < nd; ++d) S[1 + d] = s4[d];
@@ -1260,13 +1356,31 @@ int or_stage(const or_params* P, int kst, double dt, const double* q0, const dou
                             div += (Fd[d][(size_t)v * fc + fhi] - Fd[d][(size_t)v * fc + flo]) / P->dx[d];
                         }
                         double R = S[v] - div;
+                        if (capj && (v == 1 + nd || (v >= 1 && v < 1 + nd))) {
+                            /* the jump halves of the cell's two faces along each
+                             * direction: normal momentum and energy */
+                            for (int d = 0; d < nd; ++d) {
+                                if (v != 1 + nd && v != 1 + d) continue;
+                                size_t fc = (size_t)fext[d][0] * fext[d][1] * fext[d][2];
+                                int hiw[3] = {wi, wj, wk};
+                                hiw[d] += 1;
+                                size_t flo = ((size_t)wk * fext[d][1] + wj) * fext[d][0] + wi;
+                                size_t fhi = ((size_t)hiw[2] * fext[d][1] + hiw[1]) * fext[d][0] + hiw[0];
+                                const int g = (v == 1 + nd) ? 1 : 0;
+                                R += (Gd[d][g * fc + fhi] + Gd[d][g * fc + flo]) / P->dx[d];
+                            }
+                        }
                         qout[(size_t)v * nc + c] = q0[(size_t)v * nc + c] + a * dt * R;
                     }
                 }
         (void)wcnt;
     }
 done:
-    for (int d = 0; d < 3; ++d) free(Fd[d]);
+    for (int d = 0; d < 3; ++d) {
+        free(Fd[d]);
+        free(Gd[d]);
+    }
+    free(kap);
     box_free(&B);
     return st;
 }
@@ -1532,4 +1646,58 @@ int or_hf_axis(const or_params* P, const double* q, double* axis, double* gap)
                 }
     box_free(&B);
     return st;
+}
+
+/* Capillary-jump model (st_model = 1): the momentum source the face jumps
+ * give each interior cell, S[d][cells] = sum over its two faces along d of
+ * J / (2 dx_d) with J = sigma kappa_f (alpha_R - alpha_L) (see
+ * face_flux_core); and one face with given curvatures and liquid fractions
+ * of its two cells. */
+int or_capillary_force(const or_params* P, const double* q, double* S)
+{
+    const int nd = P->ndim, nv = nvar(P);
+    if (P->st_model != 1) return OR_ERR_ARG;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+    }
+    double* kap = NULL;
+    int st = interior_curvature(P, q, &kap);
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    if (!st) st = box_fill(P, q, &B, blo, bhi);
+    const size_t nc = ncells(P);
+    for (size_t c = 0; c < (size_t)nd * nc; ++c) S[c] = 0.0;
+    for (int d = 0; d < nd && !st; ++d)
+        for (int k = 0; k < P->n[2] + (d == 2); ++k)
+            for (int j = 0; j < P->n[1] + (d == 1); ++j)
+                for (int i = 0; i < P->n[0] + (d == 0); ++i) {
+                    int cl[3] = {i, j, k}, cr[3] = {i, j, k};
+                    cl[d] -= 1;   /* face between cl and cr */
+                    double W4[4 * OR_MAXV], r4[4], c4[4], F[OR_MAXV], G[2];
+                    for (int sidx = 0; sidx < 4; ++sidx) {
+                        int cc[3] = {cl[0], cl[1], cl[2]};
+                        cc[d] += sidx - 1;
+                        size_t b = bidx(&B, cc[0], cc[1], cc[2]);
+                        for (int v = 0; v < nv; ++v) W4[sidx * OR_MAXV + v] = B.W[(size_t)v * B.cnt + b];
+                        r4[sidx] = B.rho[b];
+                        c4[sidx] = B.c[b];
+                    }
+                    const double al2[2] = {B.al[bidx(&B, cl[0], cl[1], cl[2])], B.al[bidx(&B, cr[0], cr[1], cr[2])]};
+                    st = face_flux_core(P, d, W4, r4, c4, NULL, 1, kap[mapped_cell(P, cl)], kap[mapped_cell(P, cr)],
+                                        al2, F, G);
+                    if (st) break;
+                    if (cl[d] >= 0) S[(size_t)d * nc + cidx(P, cl[0], cl[1], cl[2])] += G[0] / P->dx[d];
+                    if (cr[d] < P->n[d]) S[(size_t)d * nc + cidx(P, cr[0], cr[1], cr[2])] += G[0] / P->dx[d];
+                }
+    free(kap);
+    box_free(&B);
+    return st;
+}
+
+int or_face_flux_kappa(const or_params* P, int d, const double* W4, const double* rho4, const double* c4, int f,
+                       double kapL, double kapR, const double* al2, double* F, double* G)
+{
+    return face_flux_core(P, d, W4, rho4, c4, NULL, f, kapL, kapR, al2, F, G);
 }

@@ -78,6 +78,9 @@ typedef struct {
     double thr_vap;                   /* App. D vapour-fraction threshold (barotropic closure) */
     int curv;                         /* CSF curvature: 0 Gaussian-smoothed vertex normals,
                                          1 height function (Sec. 3.5) */
+    int st_model;                     /* surface tension: 0 CSF volume force (Sec. 2.3, 3.5),
+                                         1 capillary pressure jump in the Riemann solver
+                                         (the Sec. 3.5 alternative) */
 } or_params;
 
 /* threads of the cell loops (OpenMP; results do not depend on the count);
@@ -134,6 +137,15 @@ double or_baro_vapour(const or_params* P, double p, const double* alpha);
  * density THINC (Sec. 3.4 Remarks 1-2; av4 NULL: none) */
 int or_face_flux_av(const or_params* P, int d, const double* W4, const double* rho4, const double* c4,
                     const double* av4, int f, double* F);
+
+/* capillary-jump surface tension (st_model = 1, the Sec. 3.5 alternative):
+ * the momentum source of the face pressure jumps on each interior cell
+ * (S[ndim][cells]), and one face with the curvatures and liquid fractions
+ * al2 of its two cells (G: J/2 and u* J/2, the jump halves the two sides
+ * take) */
+int or_capillary_force(const or_params* P, const double* q, double* S);
+int or_face_flux_kappa(const or_params* P, int d, const double* W4, const double* rho4, const double* c4, int f,
+                       double kapL, double kapR, const double* al2, double* F, double* G);
 
 #ifdef __cplusplus
 }

@@ -834,13 +834,8 @@ static fv_status tune(fv_ctx* x)
     if (want_fused != 0) {
         const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
         float fbest = 1e30f;
-        // Table 4.2 pair: variants 0, 1, 3 (4, 5, 6 resident blocks; the
-        // latter two in the FP32 plain mode only); other pairs: variant 2
-        const int mvars_t42[3] = {0, 1, 3};
-        const int nmv = t42 ? ((x->mixed && march_mode(x) == 0) ? 3 : 1) : 1;
         for (int ci = 0; ci < 3; ++ci)
-            for (int vi = 0; vi < nmv; ++vi) {
-                const int var = t42 ? mvars_t42[vi] : 2;
+            for (int var = (t42 ? 0 : 2); var < (t42 ? 1 : 3); ++var) {
                 if (apply_march(x, MARCH_CHUNKS[ci], var)) { x->msg.clear(); continue; }
                 MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, x->Q0, x->Q0, x->QB, x->in_u,
                              x->dt, 0.0, x->err};

@@ -12,13 +12,13 @@ namespace tfv {
 
 namespace {
 // variant v: 0 Table 4.2 limiter pair, 2 limiter pair read at run time; both
-// sized for 4 (FP32) or 2 (FP64) resident blocks of 4 warps per SM; the
-// viscous modes, which keep two more values per window row, for 3 FP32
-// blocks.  Variants 1 and 3 (FP32 plain mode, Table 4.2 pair) trade register
-// spills for occupancy: 5 and 6 resident blocks (96 and 80 registers).
+// sized for 4 (FP32) or 2 (FP64) resident blocks of 4 warps per SM (5 or 6
+// FP32 blocks, at 96 or 80 registers, spill and were slower on the
+// 2048 x 1024 shock-bubble); the viscous modes, which keep two more values
+// per window row, for 3 FP32 blocks
 template <int V, typename R, int M> constexpr int mb_of()
 {
-    return sizeof(R) == 4 ? ((M & MARCH_VISC) ? 3 : (V == 1 ? 5 : (V == 3 ? 6 : 4))) : 2;
+    return sizeof(R) == 4 ? ((M & MARCH_VISC) ? 3 : 4) : 2;
 }
 template <int V> constexpr int lim_of() { return V == 2 ? LIM_RUNTIME : LIM_TABLE42; }
 
@@ -44,20 +44,12 @@ template <int NC, int M>
 cudaError_t go_v(int var, const MarchArgs& A, int grid, cudaStream_t s)
 {
     if (var == 2) return go<NC, 2, M>(A, grid, s);
-    if constexpr (M == 0 && sizeof(FV_MR) == 4) {
-        if (var == 1) return go<NC, 1, M>(A, grid, s);
-        if (var == 3) return go<NC, 3, M>(A, grid, s);
-    }
     return go<NC, 0, M>(A, grid, s);
 }
 template <int NC, int M>
 int occ_v(int var)
 {
     if (var == 2) return occ<NC, 2, M>();
-    if constexpr (M == 0 && sizeof(FV_MR) == 4) {
-        if (var == 1) return occ<NC, 1, M>();
-        if (var == 3) return occ<NC, 3, M>();
-    }
     return occ<NC, 0, M>();
 }
 }  // namespace

@@ -107,7 +107,7 @@ N2_PR = comp_pr(126.2, 3.396e6, 0.037, 743.0, 0.0280134)
 def default_scheme(**kw) -> Dict:
     s = dict(iles=0, thinc=1, beta=1.6, thinc_eps=1e-4, thinc_gamma=1e-20,
              lim_vel=LIM_KOREN, lim_scalar=LIM_MINMOD,
-             thr_ducros=0.95, thr_gas=0.4, eps_ducros=1e-20, d3p_coef=1.0,
+             thr_ducros=0.95, thr_gas=0.4, eps_ducros=1e-20, d3p_coef=0.5,
              sigma=0.0, grad_eps=1e-5, precision=0, p_ref=1e5, T_ref=300.0,
              gravity=(0.0, 0.0, 0.0), thr_vap=0.4, curvature=0)
     s.update(kw)

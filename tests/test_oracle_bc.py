@@ -45,6 +45,7 @@ WALL_CASES = {
     "2d_y_iles_csf_3comp": dict(d=1, kw=dict(ncomp=3, iles=1, sigma=5.0)),
     "2d_x_hf": dict(d=0, kw=dict(sigma=5.0, curvature=1)),
     "3d_z_iles_csf": dict(d=2, ndim=3, kw=dict(iles=1, sigma=5.0)),
+    "2d_y_capillary_jump": dict(d=1, kw=dict(sigma=5.0, st_model=1)),
 }
 
 

@@ -74,3 +74,37 @@ def test_smooth_branch_pressure_term_damps_odd_even_mode():
         F0 = o.face_flux(0, W4, rho4=np.full(4, rho), c4=np.full(4, c), f=0)
         F1 = o.face_flux(0, W4, rho4=np.full(4, rho), c4=np.full(4, c), f=1)
         assert np.sign(F0[0]) == np.sign(F1[0]) == s
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("coef", [0.5, 1.0])
+def test_odd_even_pressure_mode_follows_linear_theory(ndim, coef):
+    """App. D smooth branch (Eq. D.5): in a liquid at rest the pressure mode
+    (-1)^(i+j+k) has zero central face pressure and velocity, so it evolves
+    only through the Delta^3 p term of u*: each face carries
+    u* = 4 coef p'/(rho c) and the pressure equation gives dp'/dt = lambda p'
+    with lambda = -8 ndim coef c / dx.  One step of the four-stage scheme
+    multiplies the mode by 1 + z + z^2/2 + z^3/6 + z^4/24, z = lambda dt (the
+    linear-theory factor the oracle must reproduce).  At CFL 0.4 z = -3.2
+    coef: coef = 1 gives a factor 1.83 per step (the explicit step is
+    unstable, beyond z = -2.785), coef = 1/2 damps the mode by 0.27."""
+    import dataclasses
+    n = 8
+    w = wl.random_state(n=(n,) * ndim if ndim == 3 else (n, n), ndim=ndim, ncomp=3, iles=1, d3p_coef=coef)
+    w = dataclasses.replace(w, comps=[wl.N2_IG, wl.CH4_IG, wl.DODECANE_SG], liquid=2)
+    o = oracle.Oracle(w)
+    shape = (n,) * 3 if ndim == 3 else (1, n, n)
+    sgn = (-1.0) ** np.indices(shape).sum(0)
+    W = np.zeros((w.nvar,) + shape)
+    W[ndim] = 6e6 + 1.0 * sgn                  # a 1 Pa mode on 6 MPa: linear
+    W[ndim + 1] = 363.0                         # pure liquid (tracked gas fractions 0)
+    q = o.prim_to_cons(W)
+    assert o.sensor(q).max() == 0.0             # the smooth branch everywhere
+    dt = o.dt(q, 0.4)
+    c = o.forward(6e6, 363.0, [0.0, 0.0])[2]
+    z = -8.0 * ndim * coef * c * dt / w.dx[0]
+    factor = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
+    q1, _ = o.step(q, 1, 0.4)
+    g = ((o.cons_to_prim(q1)[ndim] - 6e6) * sgn).mean() / (W[ndim] - 6e6)[0].flat[0]
+    assert abs(z - (-3.2 * coef)) < 1e-9
+    assert abs(g / factor - 1.0) < 1e-5, (g, factor)
