@@ -139,6 +139,16 @@ typedef struct {
     int curvature;               /* CSF curvature: 0 vertex normals of the Gaussian-smoothed
                                     fraction (Sec. 3.5, Eq. 3-9/3-10), 1 the height function
                                     of 5-cell columns (the Sec. 3.5 option) */
+    int st_model;                /* surface tension model: 0 the CSF volume force sigma kappa
+                                    grad(alpha) (Sec. 2.3, 3.5); 1 the capillary pressure jump
+                                    [P] = sigma kappa [alpha] inside the Riemann solver (the
+                                    Sec. 3.5 alternative): u* gains J / (Z_L + Z_R) and the two
+                                    sides of a face see p* -/+ J/2, J = sigma kappa_f
+                                    (alpha_i+1 - alpha_i) with kappa_f the mean of the cells'
+                                    curvatures (the curvature option above).  The jump model
+                                    runs the tiled stage kernel and is not combined with
+                                    viscous terms, slabs of a split grid or the no-alloc stage
+                                    (FV_ERR_ARG). */
 } fv_eos;
 
 typedef struct fv_ctx fv_ctx;

@@ -225,6 +225,7 @@ static const char* check_args(int ncases, const fv_grid* g, const fv_components*
     if (eos->thinc && !(eos->beta > 0.0)) return "THINC beta must be positive";
     if (!(eos->sigma >= 0.0)) return "sigma must be >= 0";
     if (eos->curvature != 0 && eos->curvature != 1) return "curvature must be 0 or 1";
+    if (eos->st_model != 0 && eos->st_model != 1) return "st_model must be 0 or 1";
     bool visc = false;
     for (int k = 0; k < cm->ncomp; ++k) {
         const fv_component& c = cm->comp[k];
@@ -233,6 +234,8 @@ static const char* check_args(int ncases, const fv_grid* g, const fv_components*
         visc = visc || c.mu > 0.0 || c.kc > 0.0;
     }
     if (visc && npr > 0) return "viscous terms need stiffened-gas / ideal-gas components";
+    if (visc && eos->st_model == 1 && eos->sigma > 0.0)
+        return "the capillary jump model is not combined with viscous terms";
     for (int d = 0; d < 3; ++d)
         if (!std::isfinite(eos->gravity[d])) return "gravity must be finite";
     if (!std::isfinite(eos->sigma)) return "sigma must be finite";
@@ -277,19 +280,21 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
     P.thinc = eos->thinc ? 1 : 0;
     P.lim_vel = eos->lim_vel;
     P.lim_scalar = eos->lim_scalar;
-    P.csf = eos->sigma > 0.0 ? 1 : 0;
+    P.capj = (eos->sigma > 0.0 && eos->st_model == 1) ? 1 : 0;
+    P.csf = (eos->sigma > 0.0 && !P.capj) ? 1 : 0;
     P.hf = eos->curvature == 1 ? 1 : 0;
     P.visc = has_visc(cm) ? 1 : 0;
     P.grav = has_grav(eos) ? 1 : 0;
     P.baro = is_baro(cm) ? 1 : 0;
     P.aux_rc = (P.iles || P.grav || P.baro) ? 1 : 0;
-    P.aux_al = (P.csf || P.iles) ? 1 : 0;
+    P.aux_al = (P.csf || P.iles || P.capj) ? 1 : 0;
     int np = x->nv;
-    P.i_rho = P.i_c = P.i_al = P.i_mu = P.i_kc = P.i_av = -1;
+    P.i_rho = P.i_c = P.i_al = P.i_mu = P.i_kc = P.i_av = P.i_kap = -1;
     if (P.aux_rc) { P.i_rho = np++; P.i_c = np++; }
     if (P.aux_al) P.i_al = np++;
     if (P.visc) { P.i_mu = np++; P.i_kc = np++; }
     if (P.baro) P.i_av = np++;
+    if (P.capj) P.i_kap = np++;
     P.nprim = np;
     x->nprim = np;
     P.beta = eos->beta;
@@ -530,6 +535,7 @@ static int count_nprim(const fv_components* cm, const fv_eos* eos, int nv)
     if (eos->iles || eos->sigma > 0.0) np += 1;
     if (has_visc(cm)) np += 2;
     if (is_baro(cm)) np += 1;
+    if (eos->sigma > 0.0 && eos->st_model == 1) np += 1;   // cell curvature of the jump model
     return np;
 }
 
@@ -669,6 +675,7 @@ static int kernel_variant(const DevParams& P, int tile)
 {
     if (P.baro) return NTILES + 4;
     if (P.visc || P.grav) return NTILES + 3;
+    if (P.capj) return NTILES + 1;   // the variant that carries the capillary jump model
     const bool t42 = P.lim_vel == FV_KOREN && P.lim_scalar == FV_MINMOD;
     if (t42 && !P.pr) return tile < NTILES ? tile : 0;
     if (t42) return NTILES;
@@ -976,8 +983,9 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         for (int t = 0; t < NTILES && s; ++t) s = apply_tile(x, t);
         if (s) return s;
     }
-    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.hf;
-    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav && !x->P.hf;
+    x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.hf && !x->P.capj;
+    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav && !x->P.hf &&
+               !x->P.capj;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
 }
@@ -1062,6 +1070,8 @@ extern "C" fv_status fv_init_split(const fv_grid* grid, int nblocks, const int* 
     std::vector<fv_grid> blocks;
     SplitInfo sp;
     const char* w = s ? nullptr : split_plan(grid, nblocks, rows, blocks, sp);
+    if (!s && !w && eos->st_model == 1 && eos->sigma > 0.0)
+        w = "the capillary jump model's curvature pass needs more ghost layers than slabs exchange";
     if (s || w) {
         fv_ctx* x = new (std::nothrow) fv_ctx();
         if (!x) return FV_ERR_ALLOC;
@@ -1336,6 +1346,11 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
                 cfl_here ? x->smax : nullptr, x->err};
     PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
     x->launches++;
+    if (x->P.capj) {
+        // cell curvatures of the capillary jump model, from the primitives
+        PROF(FV_KERNEL_PRIM, launch_kappa(x->nd, x->mixed, pa, x->prim_grid, s));
+        x->launches++;
+    }
     if (cfl_here) {
         PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s, x->split));
         x->launches++;
@@ -1684,6 +1699,7 @@ bool noalloc_args_ok(const fv_grid* g, const fv_components* cm, const fv_eos* e)
 {
     if (check_args(1, g, cm, e)) return false;
     if (g->in_u) return false;   // per-cell inflow velocities would need device memory
+    if (e->st_model == 1 && e->sigma > 0.0) return false;   // the curvature pass is not part of this path
     for (int k = 0; k < cm->ncomp; ++k)
         if (cm->comp[k].kind == FV_PR) return false;   // Peng-Robinson variants are not instantiated here
     // barotropic closure: FP64 form only (the mixed no-alloc variants are

@@ -87,6 +87,8 @@ struct DevParams {
     int csf, aux_rc, aux_al, i_rho, i_c, i_al;
     int visc, grav;      // viscous / heat-flux terms on; gravity source on
     int hf;              // CSF curvature from the height function (Sec. 3.5 option)
+    int capj;            // surface tension as a capillary pressure jump in the Riemann solver
+    int i_kap;           // primitive-array field of the cell curvature (capillary jump)
     int i_mu, i_kc;      // primitive-array fields of the mixture viscosity and conductivity
     double beta, thinc_eps, thinc_gamma, tb, icb, itb;
     double thr_ducros, thr_gas, eps_ducros, d3p_coef;
@@ -770,9 +772,13 @@ constexpr int LIM_TABLE42 = (1 << 4) | 0;   // Koren for velocities, Minmod for 
 // av4: vapour fractions of the four cells (barotropic closure), else unused.
 // SW: the App. D switch fixed at compile time (0 off, 1 on) or -1 to read it
 // from the parameters.
-template <int ND, int NC, typename R, int CL, int LIM, int SW = -1>
+// CJ = 1: capJ is the capillary pressure jump J = sigma kappa_f
+// (alpha_i+1 - alpha_i) of the Sec. 3.5 jump model, added to the pressure
+// difference of u*; the face's u* is returned in *us_out when given.
+template <int ND, int NC, typename R, int CL, int LIM, int SW = -1, int CJ = 0>
 __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*ws)[ND + NC + 1], const R* rho4,
-                                          const R* c4, int f, R* F, const R* av4 = nullptr)
+                                          const R* c4, int f, R* F, const R* av4 = nullptr, R capJ = R(0),
+                                          R* us_out = nullptr)
 {
     constexpr int NW = ND + NC + 1;
     constexpr int IP = ND, IT = ND + 1, IY = ND + 2;
@@ -834,18 +840,19 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
         const R IL = (R(3) * rho4[1] + rho4[2]) * cm * R(0.25);
         const R IR = (rho4[1] + R(3) * rho4[2]) * cm * R(0.25);
         if (f) {
-            us = fdiv(IL * uL + IR * uR + pL - pR, IL + IR);
+            us = fdiv(CJ ? IL * uL + IR * uR + pL - pR + capJ : IL * uL + IR * uR + pL - pR, IL + IR);
             ps = R(0.5) * (pL + pR);
         } else {
             const R d3 = K<R>(P).d3p_coef * (ws[0][IP] - R(3) * ws[1][IP] + R(3) * ws[2][IP] - ws[3][IP]);
-            us = uL - fdiv(d3, IL + IR);
+            us = uL - fdiv(CJ ? d3 - capJ : d3, IL + IR);
             ps = pL;
         }
     } else {
         ps = R(0.5) * (pL + pR);
         const R zL = rL * cL, zR = rR * cR;
-        us = fdiv(zL * uL + zR * uR + pL - pR, zL + zR);
+        us = fdiv(CJ ? zL * uL + zR * uR + pL - pR + capJ : zL * uL + zR * uR + pL - pR, zL + zR);
     }
+    if (us_out) *us_out = us;
     const bool up = us >= R(0);
     R Ws[NW];   // element-wise select keeps both sides in registers
 #pragma unroll

@@ -73,7 +73,13 @@ constexpr TileDef tile_def(int nd, int i) { return nd == 2 ? TILES2[i] : TILES3[
 constexpr int NVARIANTS = NTILES + 5;
 // tile of variant v: the viscous 3D variant (twelve primitive fields with the
 // App. D and CSF fields) takes the 16x4x4 tile, whose halo fits in shared memory
-constexpr int variant_tile(int nd, int v) { return v < NTILES ? v : (v == NTILES + 3 && nd == 3 ? 1 : 0); }
+// (3D viscous and run-time-limiter variants, which hold the most primitive
+// fields and, with the capillary jump model, the jump halves of every face,
+// take the 16 x 4 x 4 tile so that the FP64 halo tile fits shared memory)
+constexpr int variant_tile(int nd, int v)
+{
+    return v < NTILES ? v : ((v == NTILES + 3 || v == NTILES + 1) && nd == 3 ? 1 : 0);
+}
 
 __device__ __forceinline__ int map_index(int n, int i, int bclo, int bchi, int& flip, int& inflow)
 {
@@ -435,6 +441,132 @@ __device__ __forceinline__ R hf_kappa(const R* ea, int hc, const int* st, const 
     return -fdiv(Hxx * (R(1) + Hy * Hy) + Hyy * (R(1) + Hx * Hx) - R(2) * Hxy * Hx * Hy, q * sq_rt(q));
 }
 
+// Curvature of the CSF force (Sec. 3.5) at the cell hc of the encoded liquid
+// fraction ea (strides SY, SZ): one pass of the Gaussian kernel (Eq. 3-9) on
+// the cell and its neighbours, unit normals at the cell's vertices from the
+// smoothed fraction, kappa = -div n -- the stage kernel's formulas and
+// operation order, for the curvature pass of the capillary-jump model.
+template <int ND, typename R>
+__device__ __forceinline__ R smoothed_enc(const R* ea, int hc, int SY, int SZ)
+{
+    R s = R(0), W1 = R(0);
+    if (ND == 2) {
+#pragma unroll
+        for (int b = -1; b <= 1; ++b)
+#pragma unroll
+            for (int a = -1; a <= 1; ++a) {
+                const R wt = R((b == 0 ? 2 : 1) * (a == 0 ? 2 : 1));
+                const R e = ea[hc + b * SY + a];
+                s += wt * e;
+                W1 += wt * liq_side(e);
+            }
+    } else {
+#pragma unroll
+        for (int c = -1; c <= 1; ++c)
+#pragma unroll
+            for (int b = -1; b <= 1; ++b)
+#pragma unroll
+                for (int a = -1; a <= 1; ++a) {
+                    const R wt = R((c == 0 ? 2 : 1) * (b == 0 ? 2 : 1) * (a == 0 ? 2 : 1));
+                    const R e = ea[hc + c * SZ + b * SY + a];
+                    s += wt * e;
+                    W1 += wt * liq_side(e);
+                }
+    }
+    const R norm = R(ND == 2 ? 16 : 64);
+    return (s + W1 > R(0.5) * norm) ? -(((norm - W1) - s) / norm) : (s + W1) / norm;
+}
+
+template <int ND, typename R>
+__device__ __forceinline__ R kappa_smoothed(const DevParams& P, const R* ea, int hc, int SY, int SZ, const R* ci,
+                                            const R* cdx)
+{
+    constexpr int nc = 1 << ND;
+    const ConstT<R>& Kc = K<R>(P);
+    R dxmin = cdx[0];
+#pragma unroll
+    for (int d = 1; d < ND; ++d) dxmin = fmin(dxmin, cdx[d]);
+    const R gthr = Kc.grad_eps / dxmin;
+    // smoothed fractions of the cell's 3^ND block (offsets -1 .. 1)
+    R sa[ND == 3 ? 27 : 9];
+#pragma unroll
+    for (int c = 0; c < (ND == 3 ? 3 : 1); ++c)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                sa[(c * 3 + b) * 3 + a] =
+                    smoothed_enc<ND, R>(ea, hc + (ND == 3 ? (c - 1) * SZ : 0) + (b - 1) * SY + (a - 1), SY, SZ);
+    R kappa = R(0);
+#pragma unroll
+    for (int vtx = 0; vtx < nc; ++vtx) {
+        const int ox = vtx & 1, oy = (vtx >> 1) & 1, oz = (vtx >> 2) & 1;
+        R g[3] = {R(0), R(0), R(0)}, go[3] = {R(0), R(0), R(0)};
+#pragma unroll
+        for (int cc = 0; cc < nc; ++cc) {
+            const int bx = cc & 1, by = (cc >> 1) & 1, bz = (cc >> 2) & 1;
+            const R e = sa[((ND == 3 ? oz + bz : 0) * 3 + oy + by) * 3 + ox + bx];
+            const R oc = liq_side(e);
+            g[0] += bx ? e : -e; go[0] += bx ? oc : -oc;
+            g[1] += by ? e : -e; go[1] += by ? oc : -oc;
+            if (ND == 3) { g[2] += bz ? e : -e; go[2] += bz ? oc : -oc; }
+        }
+        R mag2 = R(0);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) { g[d] = (g[d] + go[d]) * ci[d] * R(2.0 / nc); mag2 += g[d] * g[d]; }
+        const R mag = sq_rt(mag2);
+        const R inv = (mag > gthr) ? frcp(mag) : R(0);
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            const R nd_ = g[d] * inv;
+            const int od = d == 0 ? ox : (d == 1 ? oy : oz);
+            kappa -= (od ? nd_ : -nd_) * ci[d] * R(2.0 / nc);
+        }
+    }
+    return kappa;
+}
+
+// Curvature pass of the capillary-jump surface tension (Sec. 3.5 jump
+// model): the CSF curvature (smoothed-fraction normals, or the height
+// function) of every ghosted cell into the primitive field i_kap; a ghost
+// cell takes the curvature of the interior cell the boundary update maps it
+// to.  Runs after the primitive pass, on its work list.
+template <int ND, typename R>
+__global__ void __launch_bounds__(256) kappa_kernel(PrimArgs A)
+{
+    using TS = TileShape<ND>;
+    const DevParams& P = A.P;
+    R* prim = static_cast<R*>(A.prim);
+    const int tx = threadIdx.x % TS::X, ty = (threadIdx.x / TS::X) % TS::Y, tz = threadIdx.x / (TS::X * TS::Y);
+    for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+        const int4 wi = A.items[it];
+        const CaseDesc& C = A.cases[wi.x];
+        const int gc[3] = {wi.y + tx, wi.z + ty, wi.w + tz};
+        if (!(gc[0] < C.g[0] && gc[1] < C.g[1] && gc[2] < C.g[2])) continue;
+        int src[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int flip, infl;
+            src[d] = d < ND ? map_index(C.n[d], gc[d] - 2, C.bc[d][0], C.bc[d][1], flip, infl) : 0;
+        }
+        const int SY = C.gp, SZ = C.gp * C.g[1];
+        R* const base = prim + C.poff;
+        const R* ea = base + (long long)P.i_al * P.ntot_p;
+        const int hm = (ND == 3 ? (src[2] + 2) * SZ : 0) + (src[1] + 2) * SY + src[0] + 2;
+        const R ci[3] = {pick<R>(C.idx[0], C.fidx[0]), pick<R>(C.idx[1], C.fidx[1]), pick<R>(C.idx[2], C.fidx[2])};
+        const R cdx[3] = {pick<R>(C.dx[0], C.fdx[0]), pick<R>(C.dx[1], C.fdx[1]), pick<R>(C.dx[2], C.fdx[2])};
+        R kap;
+        if (P.hf) {
+            const int st3[3] = {1, SY, SZ};
+            kap = hf_kappa<ND, R>(ea, hm, st3, cdx);
+        } else {
+            kap = kappa_smoothed<ND, R>(P, ea, hm, SY, SZ, ci, cdx);
+        }
+        const int h = (ND == 3 ? gc[2] * SZ : 0) + gc[1] * SY + gc[0];
+        base[(long long)P.i_kap * P.ntot_p + h] = kap;
+    }
+}
+
 // Eq. 2-2 stress and heat-flux terms, added to the flux F of the face between
 // cells L and R = L + e_D (visc_core: from the face's velocity gradient g,
 // the two cells' u, mu, k_c, T; visc_face: from halo cells hl and hl + e_D
@@ -515,6 +647,11 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
     R* sa = extra;                        // [AZ][AY][AX]
     R* sn = sa + AX * AY * AZ;            // [ND][VZ][VY][VX]
     unsigned char* sflag = reinterpret_cast<unsigned char*>(sn + ND * VX * VY * VZ);  // [HC]
+    // capillary-jump model (the stiffened-gas variant with run-time limiters
+    // carries it): the jump halves J/2 and u* J/2 of every face [2][faces]
+    constexpr bool CJK = LIM == LIM_RUNTIME && CL == CL_SG && !VISC;
+    constexpr int NFALL = NFX + NFY + (ND == 3 ? NFZ : 0);
+    R* const sg = reinterpret_cast<R*>((reinterpret_cast<uintptr_t>(sflag + HC) + 15) & ~uintptr_t(15));
 
     const ConstT<R>& Kc = K<R>(P);
     const int tid = threadIdx.x;
@@ -713,7 +850,27 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
             }
             if (P.iles) fl = (sflag[h0 + st] | sflag[h0 + 2 * st]) ? 1 : 0;
             R F[NV];
-            const bool ok = face_flux<ND, NC, R, CL, LIM>(P, d, ws, r4, c4, fl, F, a4);
+            bool ok;
+            if constexpr (CJK) {
+                if (P.capj) {
+                    // J = sigma kappa_f (alpha_i+1 - alpha_i): cell curvatures and
+                    // liquid fractions of the face's two cells
+                    const R* al = sp + P.i_al * HC;
+                    const R* kp = sp + P.i_kap * HC;
+                    const R eL = al[h0 + st], eR = al[h0 + 2 * st];
+                    const R J = Kc.sigma * R(0.5) * (kp[h0 + st] + kp[h0 + 2 * st]) *
+                                ((eR + liq_side(eR)) - (eL + liq_side(eL)));
+                    R us;
+                    ok = face_flux<ND, NC, R, CL, LIM, -1, 1>(P, d, ws, r4, c4, fl, F, a4, J, &us);
+                    const int fo = (d == 0 ? 0 : (d == 1 ? NFX : NFX + NFY)) + fi;
+                    sg[fo] = R(0.5) * J;
+                    sg[NFALL + fo] = R(0.5) * J * us;
+                } else {
+                    ok = face_flux<ND, NC, R, CL, LIM>(P, d, ws, r4, c4, fl, F, a4);
+                }
+            } else {
+                ok = face_flux<ND, NC, R, CL, LIM>(P, d, ws, r4, c4, fl, F, a4);
+            }
             if (!ok) set_err(A.err, ERR_NONPHYS);
             if (VISC && P.visc) {
                 const int sts[3] = {SX, SY, SZ};
@@ -831,7 +988,21 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
                     R div = (sfx[v * NFX + fxl + 1] - sfx[v * NFX + fxl]) * ci[0];
                     div += (sfy[v * NFY + fyl + TX] - sfy[v * NFY + fyl]) * ci[1];
                     if (ND == 3) div += (sfz[v * NFZ + fzl + TX * TY] - sfz[v * NFZ + fzl]) * ci[2];
-                    const R Rv = S[v] - div;
+                    R Rv = S[v] - div;
+                    if constexpr (CJK) {
+                        // the jump halves of the cell's two faces per direction:
+                        // normal momentum and energy
+                        if (P.capj && v >= 1 && v <= 1 + ND) {
+                            const int lo[3] = {fxl, NFX + fyl, NFX + NFY + fzl};
+                            const int step[3] = {1, TX, TX * TY};
+#pragma unroll
+                            for (int d = 0; d < ND; ++d) {
+                                if (v != 1 + ND && v != 1 + d) continue;
+                                const R* g = sg + (v == 1 + ND ? NFALL : 0);
+                                Rv += (g[lo[d] + step[d]] + g[lo[d]]) * ci[d];
+                            }
+                        }
+                    }
                     *qo = lsrk_update(q0r[v], adt, adtf, Rv);
                     qo += P.ntot_q;
                 }
@@ -844,7 +1015,7 @@ __global__ void __launch_bounds__(NT, MB) stage_kernel(StageArgs A)
 
 // dynamic shared memory of stage_kernel
 template <int ND, int NC, typename R, int TX, int TY, int TZ, int NB>
-inline size_t stage_smem_bytes(int nprim)
+inline size_t stage_smem_bytes(int nprim, bool capj_faces = false)
 {
     constexpr int NV = ND + NC + 1;
     constexpr int HC = (TX + 4) * (TY + 4) * ((ND == 3) ? TZ + 4 : 1);
@@ -853,7 +1024,9 @@ inline size_t stage_smem_bytes(int nprim)
     constexpr int VC = (TX + 1) * (TY + 1) * ((ND == 3) ? TZ + 1 : 1);
     size_t n = tile_buffers<R, NB>() * (size_t)tile_buffer_stride<R, HC>(nprim) +
                (size_t)NV * (NFX + NFY + (ND == 3 ? NFZ : 0)) + AC + ND * VC;
-    return n * sizeof(R) + HC + 16 + 128;   // + alignment of the buffers to 128 bytes
+    // + the capillary jump halves of every face (aligned after the flags)
+    const size_t cj = capj_faces ? 2 * (size_t)(NFX + NFY + (ND == 3 ? NFZ : 0)) * sizeof(R) + 16 : 0;
+    return n * sizeof(R) + HC + 16 + 128 + cj;   // + alignment of the buffers to 128 bytes
 }
 
 }  // namespace tfv

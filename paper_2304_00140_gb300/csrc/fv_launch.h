@@ -19,6 +19,8 @@ size_t stage_smem(int nd, int nc, int mixed, int tile, int nprim, int ff = 0);
 cudaError_t stage_set_smem(int nd, int nc, int mixed, int tile, size_t smem, int ff = 0);
 int stage_occupancy(int nd, int nc, int mixed, int tile, size_t smem, int ff = 0);   // blocks per SM (0: cannot run)
 int prim_occupancy(int nd, int nc, int mixed);
+// curvature pass of the capillary jump model (after the primitive pass, on its work list)
+cudaError_t launch_kappa(int nd, int mixed, const PrimArgs& A, int grid, cudaStream_t s);
 
 // fused 2D stage kernel (fv_march.cuh), stiffened/ideal-gas closure.
 // mode: MARCH_ILES | MARCH_CSF bits of the scheme.  var: 0 Table 4.2 limiter

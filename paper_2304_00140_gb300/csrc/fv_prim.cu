@@ -456,6 +456,18 @@ __global__ void dt_kernel(int ncases, unsigned long long* smax, double* dt, doub
     }
 }
 
+cudaError_t launch_kappa(int nd, int mixed, const PrimArgs& A, int grid, cudaStream_t s)
+{
+    if (nd == 2) {
+        if (mixed) kappa_kernel<2, float><<<grid, 256, 0, s>>>(A);
+        else kappa_kernel<2, double><<<grid, 256, 0, s>>>(A);
+    } else {
+        if (mixed) kappa_kernel<3, float><<<grid, 256, 0, s>>>(A);
+        else kappa_kernel<3, double><<<grid, 256, 0, s>>>(A);
+    }
+    return cudaGetLastError();
+}
+
 // one block: the largest signal speed over every case (positive doubles order
 // like their bit patterns), then the common dt
 __global__ void dt_group_kernel(int ncases, unsigned long long* smax, double* dt, double* t, double cfl, int* err)

@@ -53,7 +53,8 @@ template <int NC, int I, int FF>
 size_t bytes(int nprim)
 {
     constexpr TileDef t = tile_def(FV_ND, tile_of<I>());
-    return stage_smem_bytes<FV_ND, NC, FV_REAL, t.x, t.y, t.z, t.nb>(nprim);
+    // the stiffened-gas run-time-limiter variant carries the capillary jump model
+    return stage_smem_bytes<FV_ND, NC, FV_REAL, t.x, t.y, t.z, t.nb>(nprim, I == NTILES + 1);
 }
 }  // namespace
 

@@ -57,7 +57,8 @@ class fv_eos(C.Structure):
                 ("thr_ducros", C.c_double), ("thr_gas", C.c_double), ("eps_ducros", C.c_double),
                 ("d3p_coef", C.c_double), ("sigma", C.c_double), ("grad_eps", C.c_double),
                 ("precision", C.c_int), ("p_ref", C.c_double), ("T_ref", C.c_double),
-                ("gravity", C.c_double * 3), ("thr_vap", C.c_double), ("curvature", C.c_int)]
+                ("gravity", C.c_double * 3), ("thr_vap", C.c_double), ("curvature", C.c_int),
+                ("st_model", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -166,6 +167,7 @@ def make_eos(s: dict) -> fv_eos:
         e.gravity[d] = g
     e.thr_vap = s.get("thr_vap", 0.4)
     e.curvature = int(s.get("curvature", 0))
+    e.st_model = int(s.get("st_model", 0))
     return e
 
 
