@@ -136,18 +136,17 @@ class ClockSampler:
 
 # --------------------------------------------------------------- one form
 def _alg_flops_per_cell(job, fused=False):
-    """Algorithmic FP64 flops of one stage-kernel launch per interior cell,
-    counted from the formulas (+, -, *, /, sqrt, min, max, compare = 1, fused
-    multiply-add = 2) for the 2D two-component stiffened-gas / ideal-gas
-    plain scheme: 2 faces x 227 (MUSCL/THINC test 107, TDU of both sides 94,
-    Riemann 12, flux 14) + divergence and LSRK update 41; the fused kernel
-    also recovers every cell's primitives once (App. B quadratic: 74).  None
-    for other schemes (only the HBM roofline is reported for them)."""
-    w = job.w
-    s = w.scheme
-    if w.ndim == 2 and len(w.comps) == 2 and not s["iles"] and s["sigma"] == 0 and w.comps[0]["kind"] == 0:
-        return 495 + (74 if fused else 0)
-    return None
+    """Algorithmic FP64 flops of one stage-kernel launch per interior cell:
+    the op-counting build of the oracle (profiles/fp64_opcount.json, written
+    by oracle/opcount_table.py) counts the stage's faces, sources and update
+    (+, -, *, /, sqrt, min, max, compare = 1 each).  None for workloads it
+    has no entry for, and for the fused kernel (which also recovers the
+    primitives), where only the HBM roofline is reported."""
+    p = os.path.join(ROOT, "profiles", "fp64_opcount.json")
+    if fused or not os.path.exists(p):
+        return None
+    e = json.load(open(p))["workloads"].get(job.name)
+    return e["flops_per_cell"] if e else None
 
 
 def _source_hash():
@@ -306,39 +305,57 @@ def run_form(job, precision, args, torch, dist, rank, world):
 
 
 def e2e_form(job, precision, args, torch):
-    """Same metric through the public API with host buffers: every step copies
-    every case's state in from pinned host memory, advances one step and
-    reads the states back."""
+    """Same metric through the public API with host buffers: every step's
+    input state goes in from page-locked host memory and every step's result
+    comes back.  The pipelined calls (fv_upload_async / fv_commit_upload /
+    fv_download_async) move them on the copy engines while the previous step
+    runs; the blocking calls (fv_set_state / fv_get_state, one synchronisation
+    each) are timed too."""
     import ctypes as C
     from paper_2304_00140_gb300 import fv
     s = _solver(job, precision)
     nc = len(job.cases)
     L = s.L
     nsteps = max(3, min(args.steps, 30))
+    h_in = torch.from_numpy(s.get_state_all().copy()).pin_memory()
+    h_out = [torch.empty_like(h_in).pin_memory() for _ in range(2)]
+    pin = C.c_void_p(h_in.data_ptr())
+    pout = [C.c_void_p(h.data_ptr()) for h in h_out]
+
+    def check(st):
+        if st:
+            raise fv.FVError(st, L.fv_last_error(s.ctx).decode())
+    # warm-up of the pipeline (staging buffers, graph)
+    check(L.fv_upload_async(s.ctx, pin) or L.fv_commit_upload(s.ctx) or L.fv_step_async(s.ctx, 1, job.cfl)
+          or L.fv_download_async(s.ctx, pout[0]) or L.fv_io_wait(s.ctx))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    check(L.fv_upload_async(s.ctx, pin))
+    for i in range(nsteps):
+        check(L.fv_commit_upload(s.ctx))
+        if i + 1 < nsteps:
+            check(L.fv_upload_async(s.ctx, pin))
+        check(L.fv_step_async(s.ctx, 1, job.cfl) or L.fv_download_async(s.ctx, pout[i % 2]))
+    check(L.fv_io_wait(s.ctx))
+    t1 = time.perf_counter()
+    # blocking calls, for comparison
     if nc == 1:
-        h_in = torch.from_numpy(s.get_state(case=0).copy()).pin_memory()
         put = lambda p: L.fv_set_state(s.ctx, 0, fv.FV_CONSERVED, p)
         take = lambda p: L.fv_get_state(s.ctx, 0, fv.FV_CONSERVED, p)
     else:
-        # a batch moves through the all-cases calls (one transfer each way)
-        h_in = torch.from_numpy(s.get_state_all().copy()).pin_memory()
         put = lambda p: L.fv_set_state_all(s.ctx, fv.FV_CONSERVED, p)
         take = lambda p: L.fv_get_state_all(s.ctx, fv.FV_CONSERVED, p)
-    h_out = torch.empty_like(h_in).pin_memory()
-    pin, pout = C.c_void_p(h_in.data_ptr()), C.c_void_p(h_out.data_ptr())
-    put(pin)
-    L.fv_step(s.ctx, 1, job.cfl, None)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    t2 = time.perf_counter()
     for _ in range(nsteps):
-        st = put(pin) or L.fv_step_async(s.ctx, 1, job.cfl) or take(pout)
-        if st:
-            raise fv.FVError(st, L.fv_last_error(s.ctx).decode())
-    t1 = time.perf_counter()
+        check(put(pin) or L.fv_step_async(s.ctx, 1, job.cfl) or take(pout[0]))
+    t3 = time.perf_counter()
     nbytes = int(h_in.numel() * 8)
     s.close()
     return dict(value=job.cells * nsteps / (t1 - t0), unit=UNIT, h2d_bytes_per_step=nbytes,
-                d2h_bytes_per_step=nbytes, steps=nsteps)
+                d2h_bytes_per_step=nbytes, steps=nsteps, api="fv_upload_async / fv_commit_upload / fv_step_async / "
+                "fv_download_async (copies overlap the steps)",
+                blocking=dict(value=job.cells * nsteps / (t3 - t2), api="fv_set_state / fv_step_async / fv_get_state"))
 
 
 # ------------------------------------------------------------- CPU oracle
@@ -530,6 +547,7 @@ def main():
             out = dict(bound="alu", achieved=tf, peak=peak, unit="TFLOP/s", frac=tf / peak,
                        traffic=out["traffic"], kernel=out["kernel"], avg_launch_ms=avg_ms,
                        algorithmic_flops_per_launch=fl * job.cells,
+                       flops_basis="op-counting build of the oracle (profiles/fp64_opcount.json)",
                        peak_source="measured: " + f64peak["how"], peak_clocks=f64peak["clocks"],
                        hbm=dict(achieved=ach, peak=peaks["hbm"], frac=ach / peaks["hbm"],
                                 algorithmic_bytes_per_launch=byt, design_bytes_per_launch=design,

@@ -211,6 +211,32 @@ fv_status fv_get_state(fv_ctx* ctx, int icase, int kind, double* host);
  * fv_get_state. */
 fv_status fv_set_state_all(fv_ctx* ctx, int kind, const double* host);
 fv_status fv_get_state_all(fv_ctx* ctx, int kind, double* host);
+/* Pipelined conserved-state I/O of every case (the layout of
+ * fv_set_state_all), for a stream of problems whose host transfers should
+ * overlap the steps: the copies run on the device's copy engines through
+ * device staging buffers (allocated with cudaMalloc at the first call, freed
+ * by fv_destroy), uploads and downloads on two streams of their own.
+ *   fv_upload_async   starts copying `host` (page-locked) to the upload
+ *                     staging buffer; returns at once.  One upload may be
+ *                     pending: FV_ERR_STATE if the previous one is not yet
+ *                     committed.
+ *   fv_commit_upload  makes the context's stream wait for that copy and
+ *                     turns it into the current state (the case clocks
+ *                     restart); the next fv_upload_async may then start.
+ *   fv_download_async queues, on the context's stream after the work already
+ *                     queued, a copy of the current state to `host`
+ *                     (page-locked), which must stay untouched until
+ *                     fv_io_wait returns.
+ *   fv_io_wait        waits for every transfer and the context's stream and
+ *                     reports a pending device error word.
+ * A host buffer passed to fv_upload_async may be reused once the matching
+ * fv_commit_upload's work has run (fv_io_wait, or a later download that
+ * completed). */
+fv_status fv_upload_async(fv_ctx* ctx, const double* host);
+fv_status fv_commit_upload(fv_ctx* ctx);
+fv_status fv_download_async(fv_ctx* ctx, double* host);
+fv_status fv_io_wait(fv_ctx* ctx);
+
 /* Same with device pointers; asynchronous on the context's stream. */
 fv_status fv_set_state_device(fv_ctx* ctx, int icase, int kind, const double* dev);
 fv_status fv_get_state_device(fv_ctx* ctx, int icase, int kind, double* dev);

@@ -314,6 +314,46 @@ class Oracle:
         return F[:self.w.nvar].copy()
 
 
+_OPC_SRC = os.path.join(_HERE, "opcount.cpp")
+_OPC_LIB = os.path.join(_HERE, "libopcount.so")
+_opc = None
+OPCOUNT_CLASSES = ("add", "mul", "div", "sqrt", "minmax", "cmp", "abs", "transcendental")
+
+
+def build_opcount(force: bool = False) -> str:
+    """Compile the op-counting build of the oracle (g++, serial)."""
+    src_m = max(os.path.getmtime(_OPC_SRC), os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
+    if force or not os.path.exists(_OPC_LIB) or os.path.getmtime(_OPC_LIB) < src_m:
+        tmp = _OPC_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-fpermissive", "-w",
+                               "-ffp-contract=off", "-o", tmp, _OPC_SRC, "-lm"], cwd=_HERE)
+        os.replace(tmp, _OPC_LIB)
+    return _OPC_LIB
+
+
+def opcount_stage(o: "Oracle", k, dt, q0, qprev):
+    """One oracle stage with its arithmetic counted: (q^k, {class: count}
+    of the stage, {class: count} of its boundary and primitive update)."""
+    global _opc
+    with _lock:
+        if _opc is None:
+            build_opcount()
+            L = C.CDLL(_OPC_LIB)
+            dp = C.POINTER(C.c_double)
+            L.oc_stage.argtypes = [C.c_void_p, C.c_int, C.c_double, dp, dp, dp, C.POINTER(C.c_ulonglong)]
+            L.oc_box_fill.argtypes = [C.c_void_p, dp, C.POINTER(C.c_ulonglong)]
+            _opc = L
+    q0 = np.ascontiguousarray(q0, dtype=np.float64)
+    qprev = np.ascontiguousarray(qprev, dtype=np.float64)
+    out = q0.copy()
+    cnt = (C.c_ulonglong * len(OPCOUNT_CLASSES))()
+    _check(_opc.oc_stage(C.cast(C.byref(o.P), C.c_void_p), k, dt, _ptr(q0), _ptr(qprev), _ptr(out), cnt),
+           "opcount stage")
+    out_counts = dict(zip(OPCOUNT_CLASSES, [int(c) for c in cnt]))
+    _check(_opc.oc_box_fill(C.cast(C.byref(o.P), C.c_void_p), _ptr(qprev), cnt), "opcount box")
+    return out, out_counts, dict(zip(OPCOUNT_CLASSES, [int(c) for c in cnt]))
+
+
 def threads(n: int = 0) -> int:
     """threads of the oracle's cell loops (OpenMP); n < 1 only reports the
     count.  Cells are independent, so every count gives the same bits."""

@@ -90,6 +90,14 @@ struct fv_ctx {
     double* partial = nullptr;
     cudaStream_t stream = nullptr;          // user stream (0 = legacy default)
     cudaStream_t cap = nullptr;             // private stream used for graph capture
+    // pipelined state I/O: device staging copies of the whole state moved by
+    // the copy engines on their own streams (uploads and downloads apart), so
+    // host transfers overlap the steps on the context's stream
+    double* stage_up = nullptr;
+    double* stage_down = nullptr;
+    cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    cudaEvent_t ev_up_done = nullptr, ev_up_free = nullptr, ev_down_ready = nullptr, ev_down_done = nullptr;
+    bool up_pending = false;
     size_t smem = 0;
     int stage_grid = 0, prim_grid = 0, n_items_cur = 0;
     float tune_ms[NTILES] = {0.f, 0.f, 0.f, 0.f};
@@ -1091,6 +1099,14 @@ extern "C" void fv_destroy(fv_ctx* x)
     for (auto& g : x->graphs) cudaGraphExecDestroy(g.second);
     prof_clear(x);
     if (x->cap) cudaStreamDestroy(x->cap);
+    if (x->up_stream) cudaStreamSynchronize(x->up_stream);
+    if (x->down_stream) cudaStreamSynchronize(x->down_stream);
+    for (cudaEvent_t e : {x->ev_up_done, x->ev_up_free, x->ev_down_ready, x->ev_down_done})
+        if (e) cudaEventDestroy(e);
+    if (x->up_stream) cudaStreamDestroy(x->up_stream);
+    if (x->down_stream) cudaStreamDestroy(x->down_stream);
+    cudaFree(x->stage_up);
+    cudaFree(x->stage_down);
     if (x->owns && x->base) cudaFree(x->base);
     delete x;
 }
@@ -1247,6 +1263,122 @@ extern "C" fv_status fv_set_state_all(fv_ctx* x, int kind, const double* host)
 extern "C" fv_status fv_get_state_all(fv_ctx* x, int kind, double* host)
 {
     return state_all(x, kind, host, false);
+}
+
+// ---------------------------------------------------------------- pipelined I/O
+static long long state_doubles(const fv_ctx* x)
+{
+    long long n = 0;
+    for (int c = 0; c < x->ncases; ++c) n += (long long)x->nv * case_cells(x, c);
+    return n;
+}
+
+static fv_status io_setup(fv_ctx* x)
+{
+    if (x->stage_up) return FV_OK;
+    const size_t bytes = sizeof(double) * (size_t)state_doubles(x);
+    cudaError_t e = cudaMalloc(&x->stage_up, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&x->stage_down, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(x->stage_up);
+        x->stage_up = x->stage_down = nullptr;
+        cudaGetLastError();
+        return fail(x, FV_ERR_ALLOC, "cudaMalloc of the I/O staging buffers failed%s");
+    }
+    CK(x, cudaStreamCreateWithFlags(&x->up_stream, cudaStreamNonBlocking));
+    CK(x, cudaStreamCreateWithFlags(&x->down_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t* ev : {&x->ev_up_done, &x->ev_up_free, &x->ev_down_ready, &x->ev_down_done})
+        CK(x, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    // the staging buffers start free
+    CK(x, cudaEventRecord(x->ev_up_free, x->stream));
+    CK(x, cudaEventRecord(x->ev_down_done, x->down_stream));
+    return FV_OK;
+}
+
+// staging buffer <-> conserved registers of every case, on the context's stream
+static fv_status stage_convert(fv_ctx* x, bool to_reg, double* buf)
+{
+    if (x->ncases <= 8) {
+        long long off = 0;
+        for (int c = 0; c < x->ncases; ++c) {
+            const CaseDesc& C = x->cases[c];
+            const long long n = case_cells(x, c);
+            if (x->ff) {
+                if (to_reg) CK(x, launch_split(x->nv, buf + off, n, x->Q0, x->L.ntot_q, C.qoff, x->stream));
+                else CK(x, launch_join(x->nv, x->Q0, x->L.ntot_q, C.qoff, n, buf + off, x->stream));
+            } else {
+                if (to_reg) CK(x, launch_copy_fields(x->nv, buf + off, n, x->Q0 + C.qoff, x->L.ntot_q, n, x->stream));
+                else CK(x, launch_copy_fields(x->nv, x->Q0 + C.qoff, x->L.ntot_q, buf + off, n, n, x->stream));
+            }
+            x->launches++;
+            off += (long long)x->nv * n;
+        }
+        return FV_OK;
+    }
+    CK(x, launch_all_cases(x->nv, x->ncases, x->d_cases, x->L.max_cells, buf, x->Q0, x->L.ntot_q, x->ff,
+                           to_reg ? 1 : 0, x->stream));
+    x->launches++;
+    return FV_OK;
+}
+
+extern "C" fv_status fv_upload_async(fv_ctx* x, const double* host)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (!host) return fail(x, FV_ERR_ARG, "null state pointer%s");
+    if (x->up_pending) return fail(x, FV_ERR_STATE, "the previous upload has not been committed%s");
+    s = io_setup(x);
+    if (s) return s;
+    // the staging buffer is free once the previous commit's conversion ran
+    CK(x, cudaStreamWaitEvent(x->up_stream, x->ev_up_free, 0));
+    CK(x, cudaMemcpyAsync(x->stage_up, host, sizeof(double) * (size_t)state_doubles(x), cudaMemcpyHostToDevice,
+                          x->up_stream));
+    CK(x, cudaEventRecord(x->ev_up_done, x->up_stream));
+    x->up_pending = true;
+    return FV_OK;
+}
+
+extern "C" fv_status fv_commit_upload(fv_ctx* x)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (!x->up_pending) return fail(x, FV_ERR_STATE, "no upload to commit%s");
+    CK(x, cudaStreamWaitEvent(x->stream, x->ev_up_done, 0));
+    s = stage_convert(x, true, x->stage_up);
+    if (s) return s;
+    CK(x, cudaEventRecord(x->ev_up_free, x->stream));
+    CK(x, cudaMemsetAsync(x->t, 0, sizeof(double) * x->ncases, x->stream));
+    x->up_pending = false;
+    return FV_OK;
+}
+
+extern "C" fv_status fv_download_async(fv_ctx* x, double* host)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (!host) return fail(x, FV_ERR_ARG, "null state pointer%s");
+    s = io_setup(x);
+    if (s) return s;
+    // the previous download must have left the staging buffer
+    CK(x, cudaStreamWaitEvent(x->stream, x->ev_down_done, 0));
+    s = stage_convert(x, false, x->stage_down);
+    if (s) return s;
+    CK(x, cudaEventRecord(x->ev_down_ready, x->stream));
+    CK(x, cudaStreamWaitEvent(x->down_stream, x->ev_down_ready, 0));
+    CK(x, cudaMemcpyAsync(host, x->stage_down, sizeof(double) * (size_t)state_doubles(x), cudaMemcpyDeviceToHost,
+                          x->down_stream));
+    CK(x, cudaEventRecord(x->ev_down_done, x->down_stream));
+    return FV_OK;
+}
+
+extern "C" fv_status fv_io_wait(fv_ctx* x)
+{
+    fv_status s = case_ok(x, 0);
+    if (s) return s;
+    if (x->up_stream) CK(x, cudaStreamSynchronize(x->up_stream));
+    if (x->down_stream) CK(x, cudaStreamSynchronize(x->down_stream));
+    CK(x, cudaStreamSynchronize(x->stream));
+    return read_err(x);
 }
 
 extern "C" fv_status fv_set_state_device(fv_ctx* x, int icase, int kind, const double* dev)

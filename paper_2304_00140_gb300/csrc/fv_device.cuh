@@ -435,6 +435,63 @@ __device__ __forceinline__ bool tdu(const DevParams& P, R pp, R T, const R* Yt, 
     return ok && (v > R(0)) && (w > R(0));
 }
 
+// The stiffened/ideal-gas TDU of tdu() for both sides of a face, stopped
+// before its divisions: v = 1/rho, w = 1/(rho c)^2 (Wood), cp, eq per side,
+// so that the flux takes rho c = w^{-1/2} for the impedances and one
+// reciprocal and one energy for the upwind side only.  In FP64 the pressure
+// reciprocals of both sides share one division (their product stays far
+// below overflow; in FP32 each side keeps its own).
+template <typename R> struct SGSide { R v, w, cp, eq; };
+
+template <int NC, typename R>
+__device__ __forceinline__ bool tdu_sg_pair(const DevParams& P, R ppL, R TL, const R* YtL, R ppR, R TR,
+                                            const R* YtR, SGSide<R>& L, SGSide<R>& Rs)
+{
+    const ConstT<R>& Kc = K<R>(P);
+    R Y[2][NC], Pk[2 * NC], iP[2 * NC];
+    const R pp[2] = {ppL, ppR}, T[2] = {TL, TR};
+    const R* Yt[2] = {YtL, YtR};
+    bool ok = TL > R(0) && TR > R(0);
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < NC - 1; ++k) { Y[sd][k] = clip01(Yt[sd][k]); s += Y[sd][k]; }
+        Y[sd][NC - 1] = clip01(R(1) - s);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            R& pk = Pk[sd * NC + k];
+            pk = Kc.Pk[k] + pp[sd];
+            if (Y[sd][k] > R(0)) ok = ok && (pk > R(0)); else pk = R(1);
+        }
+    }
+    if constexpr (sizeof(R) == 8) {
+        recips<2 * NC, R>(Pk, iP);
+    } else {
+        recips<NC, R>(Pk, iP);
+        recips<NC, R>(Pk + NC, iP + NC);
+    }
+    SGSide<R>* out[2] = {&L, &Rs};
+#pragma unroll
+    for (int sd = 0; sd < 2; ++sd) {
+        R v = R(0), w = R(0), cp = R(0), eq = R(0);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const R a = Y[sd][k] * Kc.gm1cv[k] * iP[sd * NC + k];
+            v += a;
+            w += a * iP[sd * NC + k] * Kc.igamma[k];
+            cp += Y[sd][k] * Kc.gcv[k];
+            eq += Y[sd][k] * Kc.q[k];
+        }
+        out[sd]->v = v * T[sd];
+        out[sd]->w = w * T[sd];
+        out[sd]->cp = cp;
+        out[sd]->eq = eq;
+        ok = ok && (out[sd]->v > R(0)) && (out[sd]->w > R(0));
+    }
+    return ok;
+}
+
 // Barotropic closure (Sec. 2.2) at the offset pressure pp = p - p_ref: the
 // liquid-vapour phase density rho_LM = rho_sat,liq + (p - p_sat)/c^2 with
 // c = c_L above p_sat (Eq. 2-3) and c_M^2 = p_sat/rho_sat,liq below (Eq. 2-4),
@@ -807,9 +864,15 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
             }
         }
     }
-    R rL, eL, cL, rR, eR, cR;
-    bool ok = tdu<NC, R, CL>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
-    ok = tdu<NC, R, CL>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
+    R rL = R(0), eL = R(0), cL = R(0), rR = R(0), eR = R(0), cR = R(0);
+    bool ok;
+    [[maybe_unused]] SGSide<R> sL, sR;
+    if constexpr (CL == CL_SG) {
+        ok = tdu_sg_pair<NC, R>(P, WL[IP], WL[IT], WL + IY, WR[IP], WR[IT], WR + IY, sL, sR);
+    } else {
+        ok = tdu<NC, R, CL>(P, WL[IP], WL[IT], WL + IY, rL, eL, cL);
+        ok = tdu<NC, R, CL>(P, WR[IP], WR[IT], WR + IY, rR, eR, cR) && ok;
+    }
     if constexpr (CL == CL_BARO) {
         // Sec. 3.4 Remarks 1-2: THINC of the cell densities where the vapour
         // fraction is eligible and the densities are monotone (the profile
@@ -849,7 +912,8 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
         }
     } else {
         ps = R(0.5) * (pL + pR);
-        const R zL = rL * cL, zR = rR * cR;
+        // impedances rho c: w^{-1/2} straight from the Wood sum (stiffened gas)
+        const R zL = CL == CL_SG ? rsq(sL.w) : rL * cL, zR = CL == CL_SG ? rsq(sR.w) : rR * cR;
         us = fdiv(CJ ? zL * uL + zR * uR + pL - pR + capJ : zL * uL + zR * uR + pL - pR, zL + zR);
     }
     if (us_out) *us_out = us;
@@ -857,8 +921,16 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     R Ws[NW];   // element-wise select keeps both sides in registers
 #pragma unroll
     for (int v = 0; v < NW; ++v) Ws[v] = up ? WL[v] : WR[v];
-    const R rs = up ? rL : rR;
-    const R es = up ? eL : eR;
+    R rs, es;
+    if constexpr (CL == CL_SG) {
+        // density and internal energy of the upwind side only (as tdu() forms them)
+        const R v_ = up ? sL.v : sR.v, cp_ = up ? sL.cp : sR.cp, eq_ = up ? sL.eq : sR.eq;
+        rs = frcp(v_);
+        es = cp_ * Ws[IT] - (K<R>(P).p_ref + Ws[IP]) * v_ + eq_;
+    } else {
+        rs = up ? rL : rR;
+        es = up ? eL : eR;
+    }
     R ke = R(0);
 #pragma unroll
     for (int a = 0; a < ND; ++a) ke += R(0.5) * Ws[a] * Ws[a];

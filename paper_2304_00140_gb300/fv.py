@@ -29,7 +29,8 @@ EXPORTS = ["fv_workspace_size", "fv_init", "fv_init_ws", "fv_destroy", "fv_set_s
            "fv_get_state", "fv_set_state_device", "fv_get_state_device", "fv_rk_stage", "fv_step",
            "fv_step_async", "fv_get_diag", "fv_launch_count", "fv_last_error", "fv_status_string",
            "fv_profile", "fv_profile_read", "fv_rk_stage_noalloc", "fv_set_state_all", "fv_get_state_all",
-           "fv_wait_selftest", "fv_probe_fp64", "fv_split_workspace_size", "fv_init_split"]
+           "fv_wait_selftest", "fv_probe_fp64", "fv_split_workspace_size", "fv_init_split", "fv_upload_async",
+           "fv_commit_upload", "fv_download_async", "fv_io_wait"]
 FV_KERNEL_PRIM, FV_KERNEL_DT, FV_KERNEL_STAGE = range(3)
 
 
@@ -100,6 +101,10 @@ def load(build_if_missing: bool = True):
         L.fv_split_workspace_size.argtypes = [G, C.c_int, ip, CM, E, C.POINTER(C.c_size_t)]
         L.fv_init_split.argtypes = [G, C.c_int, ip, CM, E, vp, C.c_size_t, C.POINTER(vp)]
         L.fv_probe_fp64.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp]
+        for f in ("fv_upload_async", "fv_download_async"):
+            getattr(L, f).argtypes = [vp, vp]
+        for f in ("fv_commit_upload", "fv_io_wait"):
+            getattr(L, f).argtypes = [vp]
         L.fv_rk_stage.argtypes = [vp, C.c_int, C.c_double]
         L.fv_step.argtypes = [vp, C.c_int, C.c_double, dp]
         L.fv_step_async.argtypes = [vp, C.c_int, C.c_double]

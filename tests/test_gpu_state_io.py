@@ -7,6 +7,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle
 from paper_2304_00140_gb300 import fv, workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -80,3 +81,42 @@ def test_all_cases_io_matches_per_case(precision):
         off += n
     s.step(2, 0.4)
     assert np.array_equal(s.get_state_all(), a)
+
+
+@pytest.mark.parametrize("precision", [fv.FV_FP64, fv.FV_MIXED])
+def test_pipelined_io_equals_blocking_calls(precision):
+    """fv_upload_async / fv_commit_upload / fv_download_async: a stream of
+    three different input states, each stepped twice while the next one is
+    uploaded and the previous result downloaded, gives bit for bit what the
+    blocking fv_set_state_all / fv_step / fv_get_state_all calls give; a
+    second upload before a commit is refused"""
+    import torch
+    cases = [wl.random_state(n=(40, 24), seed=s) for s in (11, 12)]
+    inputs = []
+    for sd in (1, 2, 3):
+        qs = [oracle.Oracle(c).prim_to_cons(wl.random_state(n=(40, 24), seed=sd * 7 + k).primitives())
+              for k, c in enumerate(cases)]
+        inputs.append(np.concatenate([q.ravel() for q in qs]))
+    ref = []
+    s = fv.Solver(cases, precision=precision)
+    for q in inputs:
+        s.set_state_all(q)
+        s.step(2, 0.4)
+        ref.append(s.get_state_all())
+    s.close()
+    s = fv.Solver(cases, precision=precision)
+    L = s.L
+    h_in = [torch.from_numpy(q.copy()).pin_memory() for q in inputs]
+    h_out = [torch.zeros_like(h_in[0]).pin_memory() for _ in inputs]
+    assert L.fv_upload_async(s.ctx, C.c_void_p(h_in[0].data_ptr())) == fv.FV_OK
+    assert L.fv_upload_async(s.ctx, C.c_void_p(h_in[0].data_ptr())) == fv.FV_ERR_STATE
+    for i in range(len(inputs)):
+        assert L.fv_commit_upload(s.ctx) == fv.FV_OK
+        if i + 1 < len(inputs):
+            assert L.fv_upload_async(s.ctx, C.c_void_p(h_in[i + 1].data_ptr())) == fv.FV_OK
+        assert L.fv_step_async(s.ctx, 2, 0.4) == fv.FV_OK
+        assert L.fv_download_async(s.ctx, C.c_void_p(h_out[i].data_ptr())) == fv.FV_OK
+    assert L.fv_io_wait(s.ctx) == fv.FV_OK
+    for i in range(len(inputs)):
+        assert np.array_equal(h_out[i].numpy(), ref[i]), i
+    assert L.fv_commit_upload(s.ctx) == fv.FV_ERR_STATE

@@ -305,3 +305,16 @@ def test_threads_give_the_same_bits():
     finally:
         oracle.threads(n0)
     assert ta == tb and np.array_equal(a, b)
+
+
+def test_opcount_build_reproduces_the_oracle():
+    """the op-counting build (the FP64 roofline's flop count) computes the
+    same stage bit for bit and counts a plausible amount of arithmetic"""
+    w = wl.shock_bubble(nx=64, ny=32)
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    dt = 0.3 * o.dt(q, 1.0)
+    got, stage, box = oracle.opcount_stage(o, 1, dt, q, q)
+    assert np.array_equal(got, o.stage(1, dt, q, q))
+    per_cell = sum(stage[k] - box[k] for k in ("add", "mul", "div", "sqrt", "minmax", "cmp")) / w.cells
+    assert 200 < per_cell < 2000, per_cell
