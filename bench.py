@@ -149,28 +149,36 @@ def _alg_flops_per_cell(job, fused=False):
     return e["flops_per_cell"] if e else None
 
 
-def _source_hash():
-    """sha1 of the CUDA sources: an ncu traffic figure is only quoted for the
-    kernel version it was taken on."""
+KERNEL_SOURCES = {
+    # the files each roofline kernel's code comes from
+    "march2d_kernel": ("fv_march.cuh", "fv_march_inst.cuh", "fv_march.cu", "fv_march_f.cu", "fv_march_d.cu",
+                       "fv_kernels.cuh", "fv_device.cuh", "fv_launch.h"),
+    "stage_kernel": ("fv_kernels.cuh", "fv_device.cuh", "fv_launch.h", "fv_stage_inst.cuh", "fv_stage2d.cu",
+                     "fv_stage2f.cu", "fv_stage3d.cu", "fv_stage3f.cu"),
+    "zmarch_kernel": ("fv_zmarch.cuh", "fv_zmarch.cu", "fv_kernels.cuh", "fv_device.cuh", "fv_launch.h"),
+}
+
+
+def _source_hash(kernel):
+    """sha1 of the CUDA sources a roofline kernel is built from: an ncu
+    traffic figure is only quoted for the kernel version it was taken on."""
     import hashlib
     d = os.path.join(ROOT, "paper_2304_00140_gb300", "csrc")
-    h = hashlib.sha1()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    h = hashlib.sha1(kernel.encode())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(job, form):
-    """DRAM bytes (read + write) of one stage_kernel launch from the ncu
-    capture recorded in profiles/stage_traffic.json for this source version,
-    or None."""
+def _ncu_traffic(job, form, kernel):
+    """DRAM bytes (read + write) of one launch of the roofline kernel from the
+    ncu capture recorded in profiles/stage_traffic.json for this kernel's
+    source version, or None."""
     p = os.path.join(ROOT, "profiles", "stage_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p)).get(_source_hash(), {})
-    return d.get(f"{job.name}/{form}")
+    return json.load(open(p)).get(f"{kernel}@{_source_hash(kernel)}", {}).get(f"{job.name}/{form}")
 
 
 def record_traffic(args):
@@ -181,22 +189,27 @@ def record_traffic(args):
     workload/form the capture ran."""
     import csv
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "Tbyte": 1e12}
-    per = {}
+    per, names = {}, {}
     rows = [r for r in csv.reader(open(args.record_traffic)) if len(r) > 5]
     hdr = rows[0]
     ki, ii, mi, vi, ui = (hdr.index(k) for k in ("Kernel Name", "ID", "Metric Name", "Metric Value", "Metric Unit"))
     for r in rows[1:]:
-        if ("stage_kernel" in r[ki] or "march2d_kernel" in r[ki] or "zmarch_kernel" in r[ki]) and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        kern = next((k for k in KERNEL_SOURCES if k in r[ki]), None)
+        if kern and r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             per[r[ii]] = per.get(r[ii], 0.0) + float(r[vi].replace(",", "")) * scale[r[ui]]
-    if not per or args.precision == "both":
-        raise SystemExit("need stage_kernel DRAM metrics in the CSV and --precision mixed|fp64")
+            names[r[ii]] = kern
+    if not per or args.precision == "both" or len(set(names.values())) != 1:
+        raise SystemExit("need one roofline kernel's DRAM metrics in the CSV and --precision mixed|fp64")
+    kern = next(iter(names.values()))
     job = _workload(args)
     p = os.path.join(ROOT, "profiles", "stage_traffic.json")
     d = json.load(open(p)) if os.path.exists(p) else {}
-    d = {k: v for k, v in d.items() if k == _source_hash()}   # drop figures of older kernels
-    d.setdefault(_source_hash(), {})[f"{job.name}/{args.precision}"] = sum(per.values()) / len(per)
+    key = f"{kern}@{_source_hash(kern)}"
+    # drop figures of older versions of this kernel
+    d = {k: v for k, v in d.items() if not (k.split("@")[0] == kern and k != key)}
+    d.setdefault(key, {})[f"{job.name}/{args.precision}"] = sum(per.values()) / len(per)
     json.dump(d, open(p, "w"), indent=1, sort_keys=True)
-    print(json.dumps(dict(launches=len(per), bytes_per_launch=sum(per.values()) / len(per))))
+    print(json.dumps(dict(kernel=kern, launches=len(per), bytes_per_launch=sum(per.values()) / len(per))))
 
 
 def _nprim(w):
@@ -526,12 +539,13 @@ def main():
         byt = _compulsory_stage_bytes(job, precision)
         ach = byt / (avg_ms * 1e-3) / 1e9
         form = "mixed" if precision == fv.FV_MIXED else "fp64"
+        kname = "march2d_kernel" if fused else ("zmarch_kernel" if r["tile"].get("zmarch") else "stage_kernel")
         step_ms = r["ms"] / r["steps"]
         step = dict(compulsory_bytes_per_step=4 * byt, ms_per_step=step_ms,
                     achieved=4 * byt / (step_ms * 1e-3) / 1e9, frac=4 * byt / (step_ms * 1e-3) / 1e9 / peaks["hbm"])
         out = dict(bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
-                   traffic=_ncu_traffic(job, form),
-                   kernel="march2d_kernel" if fused else ("zmarch_kernel" if r["tile"].get("zmarch") else "stage_kernel"),
+                   traffic=_ncu_traffic(job, form, kname),
+                   kernel=kname,
                    avg_launch_ms=avg_ms, algorithmic_bytes_per_launch=byt,
                    algorithmic_basis=("compulsory bytes of one stage, the four stages' average: "
                                       + ("64" if precision == fv.FV_MIXED else "88") + " B per conserved field "

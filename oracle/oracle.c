@@ -6,6 +6,22 @@
  * fusion: every formula is the paper's, written out in the order the paper
  * gives it, so it can be checked against the text by eye.  Readings taken
  * where the paper is silent or garbled are marked READING.
+ *
+ * Pinned by the tests against what the paper and the mathematics fix: the
+ * closures (Table 4.1, A.1.1 round trips, the PR critical point and
+ * ideal-gas limit), THINC (tanh closed form), the limiters (Table 4.2,
+ * Koren's third order), the flux (Euler consistency, mirror symmetry), the
+ * stage (conservation, the uniform-pressure invariant, the exact Riemann
+ * problem, the LSRK amplification polynomial), the boundary update
+ * (equivalent mirror/extended problems, closed-box conservation), CSF and
+ * the capillary jump (Laplace jump, Eq. 4-3 period, face balance), the
+ * height function, the viscous terms (second-order convergence), the
+ * barotropic closure and the App. D smooth branch (linear stability).
+ * Parity unpinned -- readings that no paper number fixes, which the CUDA
+ * path shares: the acoustic CFL step definition, the THINC eligibility
+ * epsilon = 1e-4, the value 1/2 of the Delta^3 p scale (its effect is pinned
+ * by linear theory, not its value), and the Peng-Robinson combining rule
+ * with Z_c = 0.3074.
  */
 #include "oracle.h"
 #ifdef _OPENMP
