@@ -1408,11 +1408,13 @@ int or_prim_to_cons(const or_params* P, const double* W, double* q)
 {
     const int nd = P->ndim, nv = nvar(P), N = P->ncomp;
     const size_t nc = ncells(P);
+    int status = OR_OK;
+#pragma omp parallel for schedule(static) reduction(max : status)
     for (size_t c = 0; c < nc; ++c) {
         double w[OR_MAXV], r, e, cs;
         for (int v = 0; v < nv; ++v) w[v] = W[(size_t)v * nc + c];
         int st = or_closure_forward(P, w[nd], w[nd + 1], w + nd + 2, &r, &e, &cs, NULL);
-        if (st) return st;
+        if (st) { status = st > status ? st : status; continue; }
         double ke = 0.0;
         for (int a = 0; a < nd; ++a) ke += 0.5 * w[a] * w[a];
         q[c] = r;
@@ -1420,21 +1422,23 @@ int or_prim_to_cons(const or_params* P, const double* W, double* q)
         q[(size_t)(1 + nd) * nc + c] = r * (e + ke);
         for (int k = 0; k < N - 1; ++k) q[(size_t)(2 + nd + k) * nc + c] = r * w[nd + 2 + k];
     }
-    return OR_OK;
+    return status;
 }
 
 int or_cons_to_prim(const or_params* P, const double* q, double* W)
 {
     const int nv = nvar(P);
     const size_t nc = ncells(P);
+    int status = OR_OK;
+#pragma omp parallel for schedule(static) reduction(max : status)
     for (size_t c = 0; c < nc; ++c) {
         double qc[OR_MAXV], w[OR_MAXV];
         gather_q(P, q, c, qc);
         int st = cell_prim(P, qc, w, NULL, NULL, NULL);
-        if (st) return st;
+        if (st) { status = st > status ? st : status; continue; }
         for (int v = 0; v < nv; ++v) W[(size_t)v * nc + c] = w[v];
     }
-    return OR_OK;
+    return status;
 }
 
 /* READING (no CFL definition in the paper): dt = CFL / max_i [sum_d
