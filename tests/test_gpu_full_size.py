@@ -5,7 +5,17 @@ context, and the 512 x 256^2 jet with its per-cell inflow velocities, App.
 D switch and CSF.  (The 2048 x 1024 shock-bubble, the 1000^2 vapour
 collapse and the 1024 x 2048 rising bubble have theirs beside their other
 parity tests.)  One step from the initial state with the oracle's CFL dt
-(scaled by 0.3 where the step size is given); 1e-10 of each field's scale."""
+(scaled by 0.3 where the step size is given).
+
+Tolerance: 1e-10 of each field's scale (the larger of its largest value
+before and after the step; the momentum components share the momentum
+vector's), plus, for momentum, 1e-13 of (dt / dx_min) max|rho E|.  A state
+at rest gains its first momentum as a difference of two face pressures in
+one step; the pressure recovered from rho E carries a rounding error of a
+few ulp of rho E (of p_inf for the stiffened-gas liquid), so the momentum
+of such cells is only defined to about eps (dt / dx) max|rho E| in FP64
+(measured: 2e-15 of that figure on the droplet ensemble, against 5e-9 of
+the momentum's own 7e-3 kg/m^2 s scale)."""
 import numpy as np
 import pytest
 
@@ -16,22 +26,38 @@ from tests.helpers import oracle_step_window
 pytestmark = pytest.mark.gpu
 
 
-def _scale(q, ndim):
-    s = np.abs(q).reshape(q.shape[0], -1).max(axis=1)
-    s[1:1 + ndim] = np.sqrt((q[1:1 + ndim] ** 2).sum(0)).max()
+def _scale(qs, ndim):
+    """per field, the largest |value| over the arrays qs (the momentum
+    components: the largest momentum magnitude)"""
+    s = np.zeros(qs[0].shape[0])
+    for q in qs:
+        t = np.abs(q).reshape(q.shape[0], -1).max(axis=1)
+        t[1:1 + ndim] = np.sqrt((q[1:1 + ndim] ** 2).sum(0)).max()
+        s = np.maximum(s, t)
     return s
 
 
-def _windows_match(o, q, got, dt, wins, tol=1e-10):
+def _allowed(w, q, ref, dt, tol=1e-10):
+    """the absolute difference each field may show (module docstring)"""
+    nd = w.ndim
+    a = tol * _scale([q, ref], nd)
+    a[1:1 + nd] += 1e-13 * dt / min(w.dx[:nd]) * max(np.abs(q[1 + nd]).max(), np.abs(ref[1 + nd]).max())
+    return a
+
+
+def _windows_match(o, q, got, dt, wins):
     nd = o.w.ndim
-    scale = _scale(q, nd)
-    moved = []
+    refs, moved = [], []
     for lo, hi in wins:
         ref = oracle_step_window(o, q, dt, lo, hi)
         sl = (slice(None), slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
-        d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / np.maximum(scale, 1e-300)
-        assert np.all(d < tol), (lo, d)
-        moved.append((np.abs(ref[sl] - q[sl]).reshape(q.shape[0], -1).max(axis=1) / scale).max())
+        refs.append((sl, ref[sl].copy()))
+    allowed = _allowed(o.w, q, np.concatenate([r.reshape(r.shape[0], -1) for _, r in refs], axis=1)[:, :, None, None], dt)
+    scale = _scale([q] + [r for _, r in refs], nd)
+    for (lo, _), (sl, ref) in zip(wins, refs):
+        d = np.abs(got[sl] - ref).reshape(q.shape[0], -1).max(axis=1)
+        assert np.all(d <= allowed), (lo, d / allowed)
+        moved.append((np.abs(ref - q[sl]).reshape(q.shape[0], -1).max(axis=1) / scale).max())
     return moved
 
 
@@ -71,8 +97,9 @@ def test_droplet_ensemble_full_size_sampled_cases():
         ref, t = o.step(q0[i], 1, cases[i].cfl)
         assert abs(s.diag_scalar(fv.FV_DIAG_DT, case=i) / t - 1.0) < 1e-12
         got = s.get_state(case=i)
-        d = np.abs(got - ref).reshape(ref.shape[0], -1).max(axis=1) / _scale(ref, 2)
-        assert np.all(d < 1e-10), (i, sides[i], d)
+        d = np.abs(got - ref).reshape(ref.shape[0], -1).max(axis=1)
+        allowed = _allowed(cases[i], q0[i], ref, t)
+        assert np.all(d <= allowed), (i, sides[i], d / allowed)
 
 
 def test_jet_full_size_windows():
