@@ -809,17 +809,19 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* 
 template <typename R>
 __device__ __forceinline__ R limited(int id, R num, R den)
 {
-    // FP32: Minmod and Koren vanish unless num and den share a sign (r > 0);
-    // then the slope term is den's sign times the smallest magnitude of the
-    // candidates -- the same values as the min/max form below, in fewer
+    // FP32, branch-free, the same values as the min/max form below in fewer
     // instructions (in FP64, where these operations run on the FP64 pipe,
-    // the branch-free form was 20% slower).  The sign test is on the sign
+    // the branch-free forms were 20% slower).  Koren vanishes unless num and
+    // den share a sign (r > 0); then the slope term is den's sign times the
+    // smallest magnitude of the candidates.  The sign test is on the sign
     // bits: num xor den is negative iff the signs differ, and a zero operand
     // makes the smallest magnitude zero, so only the bits need masking.
     if constexpr (sizeof(R) == 4) {
-        if (id == 0 || id == 1) {
+        // Minmod: the median of num, den and 0 (four min/max operations)
+        if (id == 0) return fminf(fmaxf(num, fminf(den, 0.0f)), fmaxf(den, 0.0f));
+        if (id == 1) {
             const float an = fabsf(num), ad = fabsf(den);
-            const float m = id == 0 ? fminf(an, ad) : fminf(2.0f * ad, fminf(2.0f * an, (ad + 2.0f * an) * (1.0f / 3.0f)));
+            const float m = fminf(2.0f * ad, fminf(2.0f * an, (ad + 2.0f * an) * (1.0f / 3.0f)));
             const int differ = (__float_as_int(num) ^ __float_as_int(den)) >> 31;   // all ones iff the signs differ
             return __int_as_float((__float_as_int(m) | (__float_as_int(den) & int(0x80000000u))) & ~differ);
         }
