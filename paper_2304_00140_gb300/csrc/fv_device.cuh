@@ -117,6 +117,23 @@ template <> __device__ __forceinline__ float pick<float>(double, float f) { retu
 
 // ---------------------------------------------------------------- helpers
 template <typename R> __device__ __forceinline__ R clip01(R x) { return x < R(0) ? R(0) : (x > R(1) ? R(1) : x); }
+// FP64 tests on the bit patterns (integer instructions, which leave the slow
+// FP64 pipe to the arithmetic): the patterns of non-negative doubles order
+// like their values, a pattern that is negative as a 64-bit integer is a
+// negative double, and above infinity's pattern lie the NaNs
+constexpr long long DSIGN = (long long)0x8000000000000000ull, DINF = 0x7ff0000000000000ll,
+                    DONE = 0x3ff0000000000000ll;
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x > 0 (false for NaN)
+__device__ __forceinline__ bool gt0(double x) { const long long b = dbits(x); return b > 0 && b <= DINF; }
+__device__ __forceinline__ bool gt0(float x) { return x > 0.0f; }
+// clip to [0, 1] with NaN passed through, as the generic form does
+template <> __device__ __forceinline__ double clip01<double>(double x)
+{
+    const long long b = dbits(x), a = b & ~DSIGN;
+    if (a > DINF) return x;
+    return b < 0 ? 0.0 : (b > DONE ? 1.0 : x);
+}
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double sq_rt(double x) { return sqrt(x); }
@@ -518,7 +535,7 @@ __device__ __forceinline__ bool tdu_sg_pair(const DevParams& P, R ppL, R TL, con
     R Y[2][NC], Pk[2 * NC], iP[2 * NC];
     const R pp[2] = {ppL, ppR}, T[2] = {TL, TR};
     const R* Yt[2] = {YtL, YtR};
-    bool ok = TL > R(0) && TR > R(0);
+    bool ok = gt0(TL) && gt0(TR);
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
         R s = R(0);
@@ -529,7 +546,7 @@ __device__ __forceinline__ bool tdu_sg_pair(const DevParams& P, R ppL, R TL, con
         for (int k = 0; k < NC; ++k) {
             R& pk = Pk[sd * NC + k];
             pk = Kc.Pk[k] + pp[sd];
-            if (Y[sd][k] > R(0)) ok = ok && (pk > R(0)); else pk = R(1);
+            if (gt0(Y[sd][k])) ok = ok && gt0(pk); else pk = R(1);
         }
     }
     if constexpr (sizeof(R) == 8) {
@@ -554,7 +571,7 @@ __device__ __forceinline__ bool tdu_sg_pair(const DevParams& P, R ppL, R TL, con
         out[sd]->w = w * T[sd];
         out[sd]->cp = cp;
         out[sd]->eq = eq;
-        ok = ok && (out[sd]->v > R(0)) && (out[sd]->w > R(0));
+        ok = ok && gt0(out[sd]->v) && gt0(out[sd]->w);
     }
     return ok;
 }
@@ -811,19 +828,45 @@ __device__ __forceinline__ R limited(int id, R num, R den)
 {
     // FP32, branch-free, the same values as the min/max form below in fewer
     // instructions (in FP64, where these operations run on the FP64 pipe,
-    // the branch-free forms were 20% slower).  Koren vanishes unless num and
-    // den share a sign (r > 0); then the slope term is den's sign times the
-    // smallest magnitude of the candidates.  The sign test is on the sign
-    // bits: num xor den is negative iff the signs differ, and a zero operand
-    // makes the smallest magnitude zero, so only the bits need masking.
+    // the branch-free forms were 20% slower).
     if constexpr (sizeof(R) == 4) {
         // Minmod: the median of num, den and 0 (four min/max operations)
         if (id == 0) return fminf(fmaxf(num, fminf(den, 0.0f)), fmaxf(den, 0.0f));
         if (id == 1) {
-            const float an = fabsf(num), ad = fabsf(den);
-            const float m = fminf(2.0f * ad, fminf(2.0f * an, (ad + 2.0f * an) * (1.0f / 3.0f)));
-            const int differ = (__float_as_int(num) ^ __float_as_int(den)) >> 31;   // all ones iff the signs differ
-            return __int_as_float((__float_as_int(m) | (__float_as_int(den) & int(0x80000000u))) & ~differ);
+            // Koren in den's orientation: with s = sign(den), num' = s num and
+            // |den|, the slope term is s max(0, min(2 num', (|den| + 2 num')/3,
+            // 2 |den|)) (a num of the other sign makes the minimum negative)
+            const int sd = __float_as_int(den) & int(0x80000000u);
+            const float ad = fabsf(den), sn = __int_as_float(__float_as_int(num) ^ sd);
+            const float m = fmaxf(0.0f, fminf(2.0f * sn, fminf((ad + 2.0f * sn) * (1.0f / 3.0f), 2.0f * ad)));
+            return __int_as_float(__float_as_int(m) ^ sd);
+        }
+    }
+    if constexpr (sizeof(R) == 8) {
+        // FP64: the selections on the bit patterns (integer instructions,
+        // which leave the FP64 pipe to the arithmetic).  Patterns of
+        // non-negative doubles order like the values; a pattern that is
+        // negative as a 64-bit integer is a negative double.
+        constexpr long long SGN = (long long)0x8000000000000000ull;
+        const long long bn = __double_as_longlong(num), bd = __double_as_longlong(den);
+        if (id == 0) {
+            // Minmod: the smaller magnitude with den's sign, 0 for opposite signs
+            const long long an = bn & ~SGN, ad = bd & ~SGN;
+            return (bn ^ bd) < 0 ? R(0) : __longlong_as_double((an < ad ? an : ad) | (bd & SGN));
+        }
+        if (id == 1) {
+            // Koren in den's orientation (num' = sign(den) num): 0 unless
+            // num' > 0, else 2 min(num', (|den| + 2 num')/6, |den|) -- the
+            // halves of the three candidates, so the doubling is exact
+            const long long sd = bd & SGN;
+            const long long sn = bn ^ sd, ad = bd & ~SGN;
+            if (sn <= 0) return R(0);
+            const double h = fma(2.0, __longlong_as_double(sn), __longlong_as_double(ad)) * (1.0 / 6.0);
+            long long m = sn < ad ? sn : ad;
+            const long long hb = __double_as_longlong(h);
+            m = hb < m ? hb : m;
+            const double mm = __longlong_as_double(m);
+            return __longlong_as_double(__double_as_longlong(mm + mm) ^ sd);
         }
     }
     if (den == R(0)) return R(0);
@@ -865,6 +908,10 @@ __device__ __forceinline__ void muscl(int id, R x1, R x2, R x3, R x4, R& L, R& R
 template <typename R>
 __device__ __forceinline__ bool eligible(R eps, R xm, R x, R xp)
 {
+    if constexpr (sizeof(R) == 8) {
+        const long long b = dbits(x), p = dbits((x - xm) * (xp - x));
+        return b > dbits(eps) && b < dbits(R(1) - eps) && p > 0 && p <= DINF;
+    }
     return (x > eps) && (x < R(1) - eps) && ((x - xm) * (xp - x) > R(0));
 }
 
@@ -988,7 +1035,8 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
         us = fdiv(CJ ? zL * uL + zR * uR + pL - pR + capJ : zL * uL + zR * uR + pL - pR, zL + zR);
     }
     if (us_out) *us_out = us;
-    const bool up = us >= R(0);
+    // upwind side (FP64: the sign bit; us = -0 carries no mass, so either side gives the same flux)
+    const bool up = sizeof(R) == 8 ? dbits(double(us)) >= 0 : us >= R(0);
     R Ws[NW];   // element-wise select keeps both sides in registers
 #pragma unroll
     for (int v = 0; v < NW; ++v) Ws[v] = up ? WL[v] : WR[v];
