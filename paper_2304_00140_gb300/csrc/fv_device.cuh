@@ -1015,45 +1015,64 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     if (ND > 1 && d == 1) { uL = WL[1]; uR = WR[1]; }
     if (ND > 2 && d == 2) { uL = WL[ND > 2 ? 2 : 0]; uR = WR[ND > 2 ? 2 : 0]; }
     const R pL = WL[IP], pR = WR[IP];
-    R us, ps;
+    // u* = N / D.  FP64 stiffened gas: one reciprocal 1/(D v_up) gives both
+    // rho* u* = N / (D v_up) and u* = (rho* u*) v_up (D > 0, so the upwind
+    // side is the sign of N); otherwise the division and the upwind density
+    R us, ps, N, D;
+    bool smooth_us = false;
+    R d3 = R(0);
     if (iles) {
         const R cm = fmax(c4[1], c4[2]);
         const R IL = (R(3) * rho4[1] + rho4[2]) * cm * R(0.25);
         const R IR = (rho4[1] + R(3) * rho4[2]) * cm * R(0.25);
+        D = IL + IR;
         if (f) {
-            us = fdiv(CJ ? IL * uL + IR * uR + pL - pR + capJ : IL * uL + IR * uR + pL - pR, IL + IR);
+            N = CJ ? IL * uL + IR * uR + pL - pR + capJ : IL * uL + IR * uR + pL - pR;
             ps = R(0.5) * (pL + pR);
         } else {
-            const R d3 = K<R>(P).d3p_coef * (ws[0][IP] - R(3) * ws[1][IP] + R(3) * ws[2][IP] - ws[3][IP]);
-            us = uL - fdiv(CJ ? d3 - capJ : d3, IL + IR);
+            d3 = K<R>(P).d3p_coef * (ws[0][IP] - R(3) * ws[1][IP] + R(3) * ws[2][IP] - ws[3][IP]);
+            if (CJ) d3 = d3 - capJ;
+            N = uL * D - d3;
+            smooth_us = true;
             ps = pL;
         }
     } else {
         ps = R(0.5) * (pL + pR);
         // impedances rho c: w^{-1/2} straight from the Wood sum (stiffened gas)
         const R zL = CL == CL_SG ? rsq(sL.w) : rL * cL, zR = CL == CL_SG ? rsq(sR.w) : rR * cR;
-        us = fdiv(CJ ? zL * uL + zR * uR + pL - pR + capJ : zL * uL + zR * uR + pL - pR, zL + zR);
+        N = CJ ? zL * uL + zR * uR + pL - pR + capJ : zL * uL + zR * uR + pL - pR;
+        D = zL + zR;
     }
-    if (us_out) *us_out = us;
-    // upwind side (FP64: the sign bit; us = -0 carries no mass, so either side gives the same flux)
-    const bool up = sizeof(R) == 8 ? dbits(double(us)) >= 0 : us >= R(0);
+    constexpr bool ONE_RCP = sizeof(R) == 8 && CL == CL_SG;
+    if constexpr (!ONE_RCP) us = smooth_us ? uL - fdiv(d3, D) : fdiv(N, D);
+    // upwind side (FP64: the sign bit; u* = -0 carries no mass, so either side gives the same flux)
+    bool up;
+    if constexpr (ONE_RCP) up = dbits(double(N)) >= 0;
+    else up = sizeof(R) == 8 ? dbits(double(us)) >= 0 : us >= R(0);
     R Ws[NW];   // element-wise select keeps both sides in registers
 #pragma unroll
     for (int v = 0; v < NW; ++v) Ws[v] = up ? WL[v] : WR[v];
-    R rs, es;
+    R rs, es, mflux;
     if constexpr (CL == CL_SG) {
         // density and internal energy of the upwind side only (as tdu() forms them)
         const R v_ = up ? sL.v : sR.v, cp_ = up ? sL.cp : sR.cp, eq_ = up ? sL.eq : sR.eq;
-        rs = frcp(v_);
+        if constexpr (ONE_RCP) {
+            mflux = N * frcp(D * v_);
+            us = mflux * v_;
+        } else {
+            rs = frcp(v_);
+            mflux = us * rs;
+        }
         es = cp_ * Ws[IT] - (K<R>(P).p_ref + Ws[IP]) * v_ + eq_;
     } else {
         rs = up ? rL : rR;
         es = up ? eL : eR;
+        mflux = us * rs;
     }
+    if (us_out) *us_out = us;
     R ke = R(0);
 #pragma unroll
     for (int a = 0; a < ND; ++a) ke += R(0.5) * Ws[a] * Ws[a];
-    const R mflux = us * rs;
     F[0] = mflux;
 #pragma unroll
     for (int a = 0; a < ND; ++a) F[1 + a] = mflux * Ws[a] + (a == d ? ps : R(0));
