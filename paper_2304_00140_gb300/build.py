@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libthinc_fv.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["fv_api.cu", "fv_prim.cu", "fv_march.cu", "fv_march_f.cu", "fv_march_d.cu", "fv_zmarch.cu", "fv_stage2d.cu", "fv_stage2f.cu", "fv_stage3d.cu",
+SOURCES = ["fv_api.cu", "fv_prim.cu", "fv_march.cu", "fv_march_f.cu", "fv_march_fc.cu", "fv_march_d.cu", "fv_zmarch.cu", "fv_stage2d.cu", "fv_stage2f.cu", "fv_stage3d.cu",
            "fv_stage3f.cu"]
 HEADERS = ["fv_device.cuh", "fv_kernels.cuh", "fv_launch.h", "fv_stage_inst.cuh", "fv_march.cuh",
            "fv_march_inst.cuh", "fv_zmarch.cuh"]

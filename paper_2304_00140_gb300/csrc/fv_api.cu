@@ -121,7 +121,13 @@ struct fv_ctx {
     size_t smem_max = 0;                    // opt-in shared memory per block of the device
     bool tuned = false;
     int nsm = 0;
-    std::vector<std::pair<double, cudaGraphExec_t>> graphs;
+    // captured steps per (cfl, cold): a cold step starts with the CFL pass, a
+    // warm one takes the wave speeds the previous step's last fused stage left
+    std::vector<std::pair<std::pair<double, bool>, cudaGraphExec_t>> graphs;
+    // smax holds the wave speeds of the current q^n (a fused last stage wrote
+    // them and no state write came after)
+    bool smax_fresh = false;
+    bool cfl_fuse = true;                   // FV_FUSED_CFL=0 in the environment: always the CFL pass
     long long launches = 0;
     std::string msg;
     bool profiling = false;
@@ -983,6 +989,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     int smax = 0;
     CK(x, cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     x->smem_max = (size_t)smax;
+    if (const char* f = getenv("FV_FUSED_CFL")) x->cfl_fuse = atoi(f) != 0;
     const int occ_p = prim_occupancy(x->nd, x->nc, x->mixed);
     x->prim_grid = std::min(L.n_items_prim, std::max(1, nsm * occ_p));
     {
@@ -1161,6 +1168,7 @@ static fv_status set_state_impl(fv_ctx* x, int c, int kind, const double* src, c
 {
     fv_status s = case_ok(x, c);
     if (s) return s;
+    x->smax_fresh = false;
     if (!src) return fail(x, FV_ERR_ARG, "null state pointer%s");
     const long long n = case_cells(x, c);
     const CaseDesc& C = x->cases[c];
@@ -1236,7 +1244,10 @@ static fv_status state_all(fv_ctx* x, int kind, double* buf, bool set)
     if (s) return s;
     if (!buf) return fail(x, FV_ERR_ARG, "null state pointer%s");
     const cudaMemcpyKind mk = set ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
-    if (set) CK(x, cudaMemsetAsync(x->err, 0, sizeof(int), x->stream));
+    if (set) {
+        CK(x, cudaMemsetAsync(x->err, 0, sizeof(int), x->stream));
+        x->smax_fresh = false;
+    }
     const double* direct = static_cast<const double*>(device_alias(buf, mk));
     if (direct && kind == FV_CONSERVED) {
         CK(x, launch_all_cases(x->nv, x->ncases, x->d_cases, x->L.max_cells, direct, x->Q0, x->L.ntot_q, x->ff,
@@ -1343,6 +1354,7 @@ extern "C" fv_status fv_commit_upload(fv_ctx* x)
     fv_status s = case_ok(x, 0);
     if (s) return s;
     if (!x->up_pending) return fail(x, FV_ERR_STATE, "no upload to commit%s");
+    x->smax_fresh = false;
     CK(x, cudaStreamWaitEvent(x->stream, x->ev_up_done, 0));
     s = stage_convert(x, true, x->stage_up);
     if (s) return s;
@@ -1449,7 +1461,16 @@ static fv_status exchange(fv_ctx* x, double* reg, cudaStream_t s)
     return FV_OK;
 }
 
-static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
+// the fused kernel's last stage accumulates the next step's CFL wave speeds
+// (FP32 form, viscosity-free modes)
+static bool fused_cfl(const fv_ctx* x)
+{
+    return x->cfl_fuse && x->fused && x->mixed && !(march_mode(x) & MARCH_VISC);
+}
+
+// cold = false: the CFL pass of stage 1 is left out (smax already holds the
+// wave speeds of q^n, written by the previous step's last fused stage)
+static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s, bool cold = true)
 {
     double* in = k == 1 ? x->Q0 : (k == 2 ? x->QA : (k == 3 ? x->QB : x->QA));
     double* out = k == 1 ? x->QA : (k == 2 ? x->QB : (k == 3 ? x->QA : x->Q0));
@@ -1461,16 +1482,24 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s)
     if (x->fused) {
         // the CFL pass (primitive recovery without writing primitives), then
         // one fused pass that recovers the primitives it needs itself
+        const bool fc = cfl > 0.0 && fused_cfl(x);
         if (cfl_here) {
-            PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, in, nullptr, x->in_u, x->smax, x->err};
-            PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
-            x->launches++;
+            if (cold || !fc) {
+                // smax may hold an older last stage's speeds
+                if (fc) CK(x, cudaMemsetAsync(x->smax, 0, sizeof(unsigned long long) * x->ncases, s));
+                PrimArgs pa{x->P, x->d_cases, x->d_items_prim, x->L.n_items_prim, in, nullptr, x->in_u, x->smax,
+                            x->err};
+                PROF(FV_KERNEL_PRIM, launch_prim(x->nd, x->nc, x->mixed, pa, x->prim_grid, s, x->ff));
+                x->launches++;
+            }
             PROF(FV_KERNEL_DT, launch_dt(x->ncases, x->smax, x->dt, x->t, cfl, x->err, s, x->split));
             x->launches++;
         }
+        const bool last = k == 4 && fc;
         MarchArgs ma{x->P, x->d_cases, x->d_items_march, x->n_items_march, in, x->Q0, out, x->in_u, x->dt,
-                     LSRK_A[k - 1], x->err};
-        PROF(FV_KERNEL_STAGE, launch_march(x->nc, x->mixed, march_mode(x), x->mvar, ma, x->march_grid, s));
+                     LSRK_A[k - 1], x->err, last ? x->smax : nullptr};
+        PROF(FV_KERNEL_STAGE, launch_march(x->nc, x->mixed, march_mode(x) | (last ? MARCH_CFL : 0), x->mvar, ma,
+                                           x->march_grid, s));
         x->launches++;
         return FV_OK;
     }
@@ -1508,6 +1537,7 @@ extern "C" fv_status fv_rk_stage(fv_ctx* x, int k, double dt)
     if (k < 1 || k > 4) return fail(x, FV_ERR_ARG, "stage index must be 1..4%s");
     s = tune(x);
     if (s) return s;
+    x->smax_fresh = false;
     if (k == 1) {
         if (!(dt > 0.0)) return fail(x, FV_ERR_ARG, "dt must be positive%s");
         CK(x, launch_fill(x->dt, x->ncases, dt, x->stream));
@@ -1527,15 +1557,15 @@ extern "C" fv_status fv_rk_stage(fv_ctx* x, int k, double dt)
     return FV_OK;
 }
 
-static fv_status step_graph(fv_ctx* x, double cfl, cudaGraphExec_t* exec)
+static fv_status step_graph(fv_ctx* x, double cfl, bool cold, cudaGraphExec_t* exec)
 {
     for (auto& g : x->graphs)
-        if (g.first == cfl) { *exec = g.second; return FV_OK; }
+        if (g.first.first == cfl && g.first.second == cold) { *exec = g.second; return FV_OK; }
     cudaGraph_t graph;
     const long long before = x->launches;
     CK(x, cudaStreamBeginCapture(x->cap, cudaStreamCaptureModeThreadLocal));
     fv_status s = FV_OK;
-    for (int k = 1; k <= 4 && !s; ++k) s = enqueue_stage(x, k, cfl, x->cap);
+    for (int k = 1; k <= 4 && !s; ++k) s = enqueue_stage(x, k, cfl, x->cap, cold);
     cudaError_t e = cudaStreamEndCapture(x->cap, &graph);
     x->launches = before;
     if (s) return s;
@@ -1544,14 +1574,17 @@ static fv_status step_graph(fv_ctx* x, double cfl, cudaGraphExec_t* exec)
     e = cudaGraphInstantiate(&ge, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(x, e, "cudaGraphInstantiate");
-    x->graphs.emplace_back(cfl, ge);
+    x->graphs.emplace_back(std::make_pair(cfl, cold), ge);
     *exec = ge;
     return FV_OK;
 }
 
 // kernels per step: 4 prim + 1 dt + 4 stage, or with the fused kernel
-// 1 CFL pass + 1 dt + 4 fused stages
-static int launches_per_step(const fv_ctx* x) { return x->fused ? 6 : 9; }
+// 1 CFL pass + 1 dt + 4 fused stages (a warm step: no CFL pass)
+static int launches_per_step(const fv_ctx* x, bool cold = true)
+{
+    return x->fused ? (cold || !fused_cfl(x) ? 6 : 5) : 9;
+}
 
 extern "C" fv_status fv_step_async(fv_ctx* x, int nsteps, double cfl)
 {
@@ -1560,19 +1593,29 @@ extern "C" fv_status fv_step_async(fv_ctx* x, int nsteps, double cfl)
     if (nsteps < 0 || !(cfl > 0.0)) return fail(x, FV_ERR_ARG, "need nsteps >= 0 and cfl > 0%s");
     s = tune(x);
     if (s) return s;
+    const bool fc = fused_cfl(x);
+    // the first step is cold unless the last fused stage of the previous
+    // call left the wave speeds of the present state
+    const bool cold0 = !(fc && x->smax_fresh);
     if (x->profiling) {
         for (int i = 0; i < nsteps; ++i)
             for (int k = 1; k <= 4; ++k) {
-                s = enqueue_stage(x, k, cfl, x->stream);
+                s = enqueue_stage(x, k, cfl, x->stream, i == 0 ? cold0 : !fc);
                 if (s) return s;
             }
-        return FV_OK;
+    } else if (nsteps > 0) {
+        cudaGraphExec_t first, rest = nullptr;
+        s = step_graph(x, cfl, cold0, &first);
+        if (s) return s;
+        if (nsteps > 1) {
+            s = step_graph(x, cfl, !fc, &rest);
+            if (s) return s;
+        }
+        CK(x, cudaGraphLaunch(first, x->stream));
+        for (int i = 1; i < nsteps; ++i) CK(x, cudaGraphLaunch(rest, x->stream));
+        x->launches += launches_per_step(x, cold0) + (long long)launches_per_step(x, !fc) * (nsteps - 1);
     }
-    cudaGraphExec_t ge;
-    s = step_graph(x, cfl, &ge);
-    if (s) return s;
-    for (int i = 0; i < nsteps; ++i) CK(x, cudaGraphLaunch(ge, x->stream));
-    x->launches += (long long)launches_per_step(x) * nsteps;
+    if (nsteps > 0) x->smax_fresh = fc;
     return FV_OK;
 }
 

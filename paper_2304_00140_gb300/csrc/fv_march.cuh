@@ -32,12 +32,19 @@ struct MarchArgs {
     const double* dt;         // per-case dt
     double a;                 // LSRK coefficient a_k
     int* err;
+    unsigned long long* smax; // MARCH_CFL: per-case max wave speed bits of q^k (the next step's CFL input)
 };
 
 constexpr int MARCH_COLS = 28;   // cells per strip (32 lanes minus 2 + 2 halo)
 // scheme features of a fused-kernel instantiation (MARCH_VISC: the Eq. 2-2
 // stress, heat-flux and gravity terms)
 constexpr int MARCH_ILES = 1, MARCH_CSF = 2, MARCH_VISC = 4;
+// MARCH_CFL (last stage, plain viscosity-free modes): the kernel also
+// recovers the primitives of the q^k it writes and accumulates the CFL wave
+// speed sum_d (|u_d| + c) / dx_d of every interior cell into smax, as the
+// CFL pass of the next step would from the same values, so that pass is
+// left out
+constexpr int MARCH_CFL = 8;
 
 // Inflow-disc test of an x-low ghost cell in source row iy (FP64, the same
 // expression as the primitive pass).  Not inlined: only lanes on an inflow
@@ -63,6 +70,8 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
     constexpr int ND = 2, NV = ND + NC + 1;
     constexpr bool ILES = (MODE & MARCH_ILES) != 0, CSF = (MODE & MARCH_CSF) != 0, AUX = ILES || CSF;
     constexpr bool VISC = (MODE & MARCH_VISC) != 0;
+    constexpr bool CFLM = (MODE & MARCH_CFL) != 0;
+    static_assert(!(CFLM && VISC), "the fused CFL speed has no diffusive term");
     const DevParams& P = A.P;
     const ConstT<R>& Kc = K<R>(P);
     // q^{k-1} never aliases q^k (the stages go q0 -> qA -> qB -> qA -> q0)
@@ -301,6 +310,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
         }
         const double adt = A.a * A.dt[wi.x];
         const float adtf = float(adt);
+        R speed = R(0);    // MARCH_CFL: largest wave speed sum of this lane's cells
         Q qn[NV];          // conserved values of the next row to enter the window
         RowRef rn;
         fetch_row(y0 + 2, qn, rn);
@@ -410,19 +420,40 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
             }
             // divergence and LSRK update of this lane's cell
             Q* qo = qoreg + gcell;
+            Q qk[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const R Fxm = shl(Fx[v]);
                 R div = (Fx[v] - Fxm) * ci0;
                 div += (Fyn[v] - Fy[v]) * ci1;
                 const R Rv = S[v] - div;
-                if (own_col) *qo = lsrk_update(q0r[v], adt, adtf, Rv);
+                qk[v] = lsrk_update(q0r[v], adt, adtf, Rv);
+                if (own_col) *qo = qk[v];
                 qo += P.ntot_q;
                 Fy[v] = Fyn[v];
+            }
+            if (CFLM && own_col) {
+                // the CFL pass's recovery and sound speed of this interior cell
+                R w[NV], rho, T, pabs, rr_, e_, cs;
+                const int rst = prim_recover<ND, NC, R, false, Q>(P, qk, w, rho, T, pabs, 0.0);
+                if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
+                const bool ok = tdu<NC, R, false>(P, w[ND], w[ND + 1], w + ND + 2, rr_, e_, cs) && rst == 0;
+                bad = bad || (!ok && rst != ERR_NONCONV);
+                const R cis[2] = {ci0, ci1};
+                R sp = R(0);
+#pragma unroll
+                for (int d = 0; d < ND; ++d) sp += (fabs(w[d]) + cs) * cis[d];
+                speed = fmax(speed, sp);
             }
             flag_y = flag_up;
         }
         if (bad) set_err(A.err, ERR_NONPHYS);
+        if (CFLM) {
+            // warp maximum, one atomic per work item (positive doubles order like their bit patterns)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) speed = fmax(speed, __shfl_xor_sync(FULL, speed, o));
+            if (lane == 0) atomicMax(A.smax + wi.x, (unsigned long long)__double_as_longlong(double(speed)));
+        }
     }
 }
 

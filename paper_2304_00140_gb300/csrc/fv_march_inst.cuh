@@ -54,6 +54,8 @@ int occ_v(int var)
 }
 }  // namespace
 
+#ifndef FV_MCFL
+// the scheme modes (MARCH_ILES | MARCH_CSF | MARCH_VISC bits)
 #define FV_MODE_SWITCH(fn, ...)                                                   \
     switch (mode) {                                                               \
     case 0: return nc == 2 ? fn<2, 0>(__VA_ARGS__) : fn<3, 0>(__VA_ARGS__);        \
@@ -65,12 +67,30 @@ int occ_v(int var)
     case 6: return nc == 2 ? fn<2, 6>(__VA_ARGS__) : fn<3, 6>(__VA_ARGS__);        \
     default: return nc == 2 ? fn<2, 7>(__VA_ARGS__) : fn<3, 7>(__VA_ARGS__);       \
     }
+#else
+// the last-stage modes with the fused CFL speed (MARCH_CFL | MARCH_ILES | MARCH_CSF)
+#define FV_MODE_SWITCH(fn, ...)                                                   \
+    switch (mode) {                                                               \
+    case 8: return nc == 2 ? fn<2, 8>(__VA_ARGS__) : fn<3, 8>(__VA_ARGS__);        \
+    case 9: return nc == 2 ? fn<2, 9>(__VA_ARGS__) : fn<3, 9>(__VA_ARGS__);        \
+    case 10: return nc == 2 ? fn<2, 10>(__VA_ARGS__) : fn<3, 10>(__VA_ARGS__);     \
+    case 11: return nc == 2 ? fn<2, 11>(__VA_ARGS__) : fn<3, 11>(__VA_ARGS__);     \
+    default: return FV_MBAD;                                                      \
+    }
+#endif
 
 cudaError_t FV_MCAT(launch_march_, FV_MSUFFIX)(int nc, int mode, int var, const MarchArgs& A, int grid,
                                                 cudaStream_t s)
 {
+#define FV_MBAD cudaErrorInvalidValue
     FV_MODE_SWITCH(go_v, var, A, grid, s)
+#undef FV_MBAD
 }
-int FV_MCAT(march_occupancy_, FV_MSUFFIX)(int nc, int mode, int var) { FV_MODE_SWITCH(occ_v, var) }
+int FV_MCAT(march_occupancy_, FV_MSUFFIX)(int nc, int mode, int var)
+{
+#define FV_MBAD 0
+    FV_MODE_SWITCH(occ_v, var)
+#undef FV_MBAD
+}
 
 }  // namespace tfv
