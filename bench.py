@@ -151,7 +151,7 @@ def _alg_flops_per_cell(job, fused=False):
 
 KERNEL_SOURCES = {
     # the files each roofline kernel's code comes from
-    "march2d_kernel": ("fv_march.cuh", "fv_march_inst.cuh", "fv_march.cu", "fv_march_f.cu", "fv_march_d.cu",
+    "march2d_kernel": ("fv_march.cuh", "fv_march_inst.cuh", "fv_march.cu", "fv_march_f.cu", "fv_march_fc.cu", "fv_march_d.cu",
                        "fv_kernels.cuh", "fv_device.cuh", "fv_launch.h"),
     "stage_kernel": ("fv_kernels.cuh", "fv_device.cuh", "fv_launch.h", "fv_stage_inst.cuh", "fv_stage2d.cu",
                      "fv_stage2f.cu", "fv_stage3d.cu", "fv_stage3f.cu"),
