@@ -638,11 +638,15 @@ static fv_status encode_tmaps(fv_ctx* x, int variant)
     return FV_OK;
 }
 
+// the z-marching kernel's viscous instantiations (Eq. 2-2 terms or gravity on)
+static int zm_visc(const fv_ctx* x) { return (x->P.visc || x->P.grav) ? 1 : 0; }
+
 // z-marching kernel with z-chunk `chunk` and variant `var` (needs TMA)
 static fv_status apply_zmarch(fv_ctx* x, int chunk, int var)
 {
     const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
     if (!t42) var = 2;
+    else if (zm_visc(x)) var = 1;
     const cuuint32_t box[4] = {cuuint32_t(ZM_TX + 4), cuuint32_t(ZM_TY + 4), 1, cuuint32_t(x->nprim)};
     if (!encode_maps(x, box, ZM_TX, x->d_tmaps_z)) return fail(x, FV_ERR_ARG, "z-marching kernel needs TMA%s");
     std::vector<int4> it;
@@ -656,8 +660,8 @@ static fv_status apply_zmarch(fv_ctx* x, int chunk, int var)
     CK(x, cudaMemcpy(x->d_items_z, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
     const size_t smem = zmarch_smem(x->nc, x->nprim);
     if (smem > x->smem_max) return fail(x, FV_ERR_ARG, "z-marching kernel does not fit in shared memory%s");
-    CK(x, zmarch_set_smem(x->nc, var, smem));
-    const int occ = zmarch_occupancy(x->nc, var, smem);
+    CK(x, zmarch_set_smem(x->nc, var, zm_visc(x), smem));
+    const int occ = zmarch_occupancy(x->nc, var, zm_visc(x), smem);
     if (occ < 1) return fail(x, FV_ERR_CUDA, "z-marching kernel cannot be resident%s");
     x->zm = true;
     x->fused = false;
@@ -873,15 +877,18 @@ static fv_status tune(fv_ctx* x)
         // after the primitive pass above, like the tiled kernel
         const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
         float zbest = 1e30f;
-        const int zvars_t42[3] = {0, 1, 3}, zvars_rt[1] = {2};
+        // the viscous instantiations: variant 1 (Table 4.2 pair) or 2 (run-time pair)
+        const int zvars_t42[3] = {0, 1, 3}, zvars_rt[1] = {2}, zvars_visc[1] = {1};
         for (int ci = 0; ci < 3; ++ci)
-            for (int vi = 0; vi < (t42 ? 3 : 1); ++vi) {
-                const int var = t42 ? zvars_t42[vi] : zvars_rt[vi];
+            for (int vi = 0; vi < (t42 && !zm_visc(x) ? 3 : 1); ++vi) {
+                const int var = !t42 ? zvars_rt[vi] : (zm_visc(x) ? zvars_visc[vi] : zvars_t42[vi]);
                 if (apply_zmarch(x, ZM_CHUNKS[ci], var)) { x->msg.clear(); continue; }
                 ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, x->QB,
                          x->dt, 0.0, x->err};
                 float ms = 0.f;
-                st = timed([&] { return launch_zmarch(x->nc, x->zvar, za, x->zm_grid, x->zm_smem, x->stream); }, ms);
+                st = timed([&] {
+                    return launch_zmarch(x->nc, x->zvar, zm_visc(x), za, x->zm_grid, x->zm_smem, x->stream);
+                }, ms);
                 if (st) return st;
                 zbest = std::min(zbest, ms);
                 if (ms < best_ms) { best_ms = ms; best = 200 + 10 * ci + var; }
@@ -999,7 +1006,7 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
         if (s) return s;
     }
     x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.baro && !x->P.hf && !x->P.capj;
-    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.visc && !x->P.grav && !x->P.hf &&
+    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.hf &&
                !x->P.capj;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
@@ -1519,7 +1526,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s, boo
     if (x->zm) {
         ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, out, x->dt,
                  LSRK_A[k - 1], x->err};
-        PROF(FV_KERNEL_STAGE, launch_zmarch(x->nc, x->zvar, za, x->zm_grid, x->zm_smem, s));
+        PROF(FV_KERNEL_STAGE, launch_zmarch(x->nc, x->zvar, zm_visc(x), za, x->zm_grid, x->zm_smem, s));
         x->launches++;
         return FV_OK;
     }

@@ -32,11 +32,12 @@ int march_occupancy(int nc, int mixed, int mode, int var);   // blocks per SM
 
 // z-marching 3D stage kernel (fv_zmarch.cuh), FP32-mixed, stiffened/ideal gas,
 // TMA plane loads.  var: 0 / 1 / 3 Table 4.2 limiter pair with 320 / 256 /
-// 352 threads, 2 limiter pair read at run time (320 threads).
+// 352 threads, 2 limiter pair read at run time (320 threads).  visc = 1: with
+// the Eq. 2-2 viscous, heat-flux and gravity terms (variants 1 and 2).
 struct ZArgs;
-cudaError_t launch_zmarch(int nc, int var, const ZArgs& A, int grid, size_t smem, cudaStream_t s);
-cudaError_t zmarch_set_smem(int nc, int var, size_t smem);
-int zmarch_occupancy(int nc, int var, size_t smem);   // blocks per SM
+cudaError_t launch_zmarch(int nc, int var, int visc, const ZArgs& A, int grid, size_t smem, cudaStream_t s);
+cudaError_t zmarch_set_smem(int nc, int var, int visc, size_t smem);
+int zmarch_occupancy(int nc, int var, int visc, size_t smem);   // blocks per SM (0: no such variant)
 int zmarch_threads(int var);
 size_t zmarch_smem(int nc, int nprim);
 

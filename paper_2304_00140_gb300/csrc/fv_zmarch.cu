@@ -3,7 +3,8 @@
 // Variants: 0 / 1 / 3 Table 4.2 limiter pair with 320 / 256 / 352 threads
 // (352 covers a plane's 18 x 18 sensor and smoothing cells in one round);
 // 2 a limiter pair read at run time, 320 threads.  Two resident
-// blocks per SM (the plane ring takes about 100 KB of shared memory).
+// blocks per SM (the plane ring takes about 100 KB of shared memory).  With
+// the viscous and gravity terms (visc = 1) variants 1 and 2 only.
 #include "fv_launch.h"
 #include "fv_zmarch.cuh"
 
@@ -12,43 +13,64 @@ namespace tfv {
 namespace {
 template <int V> constexpr int nt_of() { return V == 1 ? 256 : (V == 3 ? 352 : 320); }
 template <int V> constexpr int lim_of() { return V == 2 ? LIM_RUNTIME : LIM_TABLE42; }
-#define FV_ZK(NC, V) zmarch_kernel<NC, nt_of<V>(), 2, lim_of<V>(), float2>
+#define FV_ZK(NC, V, VI) zmarch_kernel<NC, nt_of<V>(), 2, lim_of<V>(), VI, float2>
 
-template <int NC, int V>
+template <int NC, int V, int VI>
 cudaError_t go(const ZArgs& A, int grid, size_t smem, cudaStream_t s)
 {
-    FV_ZK(NC, V)<<<grid, nt_of<V>(), smem, s>>>(A);
+    FV_ZK(NC, V, VI)<<<grid, nt_of<V>(), smem, s>>>(A);
     return cudaGetLastError();
 }
-template <int NC, int V>
+template <int NC, int V, int VI>
 cudaError_t attr(size_t smem)
 {
-    return cudaFuncSetAttribute(FV_ZK(NC, V), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(FV_ZK(NC, V, VI), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
-template <int NC, int V>
+template <int NC, int V, int VI>
 int occ(size_t smem)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FV_ZK(NC, V), nt_of<V>(), smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, FV_ZK(NC, V, VI), nt_of<V>(), smem) != cudaSuccess)
+        return 0;
     return n;
 }
 #undef FV_ZK
 }  // namespace
 
-#define FV_ZSWITCH(fn, ...)                                                                 \
-    switch (var) {                                                                          \
-    case 1: return nc == 2 ? fn<2, 1>(__VA_ARGS__) : fn<3, 1>(__VA_ARGS__);                  \
-    case 2: return nc == 2 ? fn<2, 2>(__VA_ARGS__) : fn<3, 2>(__VA_ARGS__);                  \
-    case 3: return nc == 2 ? fn<2, 3>(__VA_ARGS__) : fn<3, 3>(__VA_ARGS__);                  \
-    default: return nc == 2 ? fn<2, 0>(__VA_ARGS__) : fn<3, 0>(__VA_ARGS__);                 \
+// FV_ZBAD: the value for a variant without a viscous instantiation
+#define FV_ZSWITCH(fn, ...)                                                                        \
+    if (visc) {                                                                                    \
+        switch (var) {                                                                             \
+        case 1: return nc == 2 ? fn<2, 1, 1>(__VA_ARGS__) : fn<3, 1, 1>(__VA_ARGS__);               \
+        case 2: return nc == 2 ? fn<2, 2, 1>(__VA_ARGS__) : fn<3, 2, 1>(__VA_ARGS__);               \
+        default: return FV_ZBAD;                                                                   \
+        }                                                                                          \
+    }                                                                                              \
+    switch (var) {                                                                                 \
+    case 1: return nc == 2 ? fn<2, 1, 0>(__VA_ARGS__) : fn<3, 1, 0>(__VA_ARGS__);                   \
+    case 2: return nc == 2 ? fn<2, 2, 0>(__VA_ARGS__) : fn<3, 2, 0>(__VA_ARGS__);                   \
+    case 3: return nc == 2 ? fn<2, 3, 0>(__VA_ARGS__) : fn<3, 3, 0>(__VA_ARGS__);                   \
+    default: return nc == 2 ? fn<2, 0, 0>(__VA_ARGS__) : fn<3, 0, 0>(__VA_ARGS__);                  \
     }
 
-cudaError_t launch_zmarch(int nc, int var, const ZArgs& A, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_zmarch(int nc, int var, int visc, const ZArgs& A, int grid, size_t smem, cudaStream_t s)
 {
+#define FV_ZBAD cudaErrorInvalidValue
     FV_ZSWITCH(go, A, grid, smem, s)
+#undef FV_ZBAD
 }
-cudaError_t zmarch_set_smem(int nc, int var, size_t smem) { FV_ZSWITCH(attr, smem) }
-int zmarch_occupancy(int nc, int var, size_t smem) { FV_ZSWITCH(occ, smem) }
+cudaError_t zmarch_set_smem(int nc, int var, int visc, size_t smem)
+{
+#define FV_ZBAD cudaErrorInvalidValue
+    FV_ZSWITCH(attr, smem)
+#undef FV_ZBAD
+}
+int zmarch_occupancy(int nc, int var, int visc, size_t smem)
+{
+#define FV_ZBAD 0
+    FV_ZSWITCH(occ, smem)
+#undef FV_ZBAD
+}
 int zmarch_threads(int var) { return var == 1 ? 256 : (var == 3 ? 352 : 320); }
 size_t zmarch_smem(int nc, int nprim) { return nc == 2 ? zm_smem_bytes<2>(nprim) : zm_smem_bytes<3>(nprim); }
 

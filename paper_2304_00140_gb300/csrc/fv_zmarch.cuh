@@ -14,7 +14,10 @@
 // step.  The flags, smoothed fractions, normals and z-fluxes of the planes
 // below are kept in two-slot rings.  Every face is computed once (the tiled kernel computes
 // a tile's edge faces twice), and the +1 halo work of the sensor and the
-// smoothing is in x and y only.
+// smoothing is in x and y only.  VISC instantiations add the Eq. 2-2 stress
+// and heat flux at every face (the tiled kernel's face gradients: the planes
+// below and above give the z differences of x- and y-faces) and the gravity
+// source in the update.
 #pragma once
 
 #include "fv_kernels.cuh"
@@ -51,7 +54,40 @@ inline size_t zm_smem_bytes(int nprim)
     return floats * 4 + 2 * HXY + 128;
 }
 
-template <int NC, int NT, int MB, int LIM, typename Q>
+// Eq. 2-2 stress and heat flux of the face between cell L = (plane cl, index
+// hl) and R = (cr, hr) along D, with the tiled kernel's face gradients in its
+// order; dnL / upL, dnR / upR: the planes below and above L and R (x- and
+// y-faces; a z-face's cells are in two planes and need none)
+template <int D, typename R>
+__device__ __forceinline__ void zm_visc_face(const DevParams& P, int HXY, int HX, const R* cl, int hl, const R* cr,
+                                             int hr, const R* dnL, const R* upL, const R* dnR, const R* upR,
+                                             const R* ci, R* F)
+{
+    R g[3][3];   // g[a][b] = d u_a / d x_b at the face
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const R* uL = cl + a * HXY;
+            const R* uR = cr + a * HXY;
+            if (b == D) {
+                g[a][b] = (uR[hr] - uL[hl]) * ci[D];
+            } else if (b < 2) {
+                const int sb = b == 0 ? 1 : HX;
+                g[a][b] = ((uL[hl + sb] - uL[hl - sb]) + (uR[hr + sb] - uR[hr - sb])) * (R(0.25) * ci[b]);
+            } else {
+                g[a][b] = ((upL[a * HXY + hl] - dnL[a * HXY + hl]) + (upR[a * HXY + hr] - dnR[a * HXY + hr])) *
+                          (R(0.25) * ci[b]);
+            }
+        }
+    R uL[3], uR[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { uL[a] = cl[a * HXY + hl]; uR[a] = cr[a * HXY + hr]; }
+    visc_core<3, D, R>(g, uL, uR, cl[P.i_mu * HXY + hl], cr[P.i_mu * HXY + hr], cl[P.i_kc * HXY + hl],
+                       cr[P.i_kc * HXY + hr], cl[4 * HXY + hl], cr[4 * HXY + hr], ci[D], F);
+}
+
+template <int NC, int NT, int MB, int LIM, int VISC, typename Q>
 __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
 {
     using R = float;
@@ -263,6 +299,7 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
             const int hh[4] = {h, h, h, h};
             R F[NV];
             face(2, pl, hh, FLAG + slot2(p) * HXY, FLAG + slot2(p + 1) * HXY, F);
+            if (VISC && P.visc) zm_visc_face<2, R>(P, HXY, HX, pl[1], h, pl[2], h, nullptr, nullptr, nullptr, nullptr, ci, F);
             R* const dst = FZ + slot2(p + 1) * NV * TXY;
 #pragma unroll
             for (int v = 0; v < NV; ++v) dst[v * TXY + f] = F[v];
@@ -317,6 +354,9 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                         const int hh[4] = {h0, h0 + 1, h0 + 2, h0 + 3};
                         R F[NV];
                         face(0, pl, hh, flz, flz, F);
+                        if (VISC && P.visc)
+                            zm_visc_face<0, R>(P, HXY, HX, pz, hh[1], pz, hh[2], plane(z - 1), plane(z + 1),
+                                               plane(z - 1), plane(z + 1), ci, F);
 #pragma unroll
                         for (int v = 0; v < NV; ++v) FX[v * NFX + f] = F[v];
                     } else if (f < NFX + NFY) {
@@ -328,6 +368,9 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                         const int hh[4] = {h0, h0 + HX, h0 + 2 * HX, h0 + 3 * HX};
                         R F[NV];
                         face(1, pl, hh, flz, flz, F);
+                        if (VISC && P.visc)
+                            zm_visc_face<1, R>(P, HXY, HX, pz, hh[1], pz, hh[2], plane(z - 1), plane(z + 1),
+                                               plane(z - 1), plane(z + 1), ci, F);
 #pragma unroll
                         for (int v = 0; v < NV; ++v) FY[v * NFY + fi] = F[v];
                     } else {
@@ -372,6 +415,18 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                         udg += pz[d * HXY + hc] * ga[d];
                     }
                     S[1 + ND] = Kc.sigma * kappa * udg;
+                }
+                if (VISC && P.grav) {
+                    // Eq. 2-2 Q: rho g (momentum), rho u . g (energy)
+                    const R* const pz = plane(z);
+                    const R rho = pz[P.i_rho * HXY + hc];
+                    R ug = R(0);
+#pragma unroll
+                    for (int d = 0; d < ND; ++d) {
+                        S[1 + d] += rho * Kc.grav[d];
+                        ug += pz[d * HXY + hc] * Kc.grav[d];
+                    }
+                    S[1 + ND] += rho * ug;
                 }
                 const int fxl = cy * (TX + 1) + cx, fyl = cy * TX + cx, c = cy * TX + cx;
                 const R* const fzl = FZ + slot2(z) * NV * TXY;

@@ -33,6 +33,18 @@ CASES = {
     "iles_csf_3comp": lambda: wl.random_state(
         n=(18, 17, 40), ndim=3, ncomp=3, iles=1, sigma=5.0,
         bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_PERIODIC] * 2, [wl.BC_REFLECT, wl.BC_OUTFLOW]]),
+    # Eq. 2-2 viscous stresses, heat flux and gravity (the kernel's viscous instantiations)
+    "visc_grav_2comp_bc": lambda: wl.with_transport(
+        wl.random_state(n=(21, 18, 23), ndim=3, ncomp=2,
+                        bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_REFLECT, wl.BC_OUTFLOW], [wl.BC_PERIODIC] * 2]),
+        mu=[2e-3, 5e-3], kc=[0.4, 0.6], gravity=(0.3, -9.8, 0.2)),
+    "visc_grav_iles_csf_3comp": lambda: wl.with_transport(
+        wl.random_state(n=(18, 17, 21), ndim=3, ncomp=3, iles=1, sigma=5.0,
+                        bc=[[wl.BC_OUTFLOW, wl.BC_REFLECT], [wl.BC_PERIODIC] * 2, [wl.BC_REFLECT, wl.BC_OUTFLOW]]),
+        mu=[2e-3, 5e-3, 1e-3], kc=[0.4, 0.6, 0.1], gravity=(0.3, -9.8, 0.2)),
+    "visc_runtime_limiters": lambda: wl.with_transport(
+        wl.random_state(n=(19, 16, 14), ndim=3, ncomp=2, lim_vel=wl.LIM_VANLEER, lim_scalar=wl.LIM_MC),
+        mu=[40.0, 80.0], kc=[0.0, 0.0], gravity=(0.0, 0.0, 0.0)),
 }
 
 
