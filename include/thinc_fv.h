@@ -256,14 +256,23 @@ fv_status fv_rk_stage(fv_ctx* ctx, int k, double dt);
  * closure a kernel that marches along z with TMA plane loads.
  * FV_TILE=<index> in the environment forces a tile of the tiled kernel,
  * FV_FUSED=0/1 and FV_ZMARCH=0/1 exclude or force the fused and the
- * z-marching kernel.  Set the state first. */
+ * z-marching kernel, FV_FUSED_CFL=0 (read when the context is created)
+ * keeps the CFL pass in every step of the fused kernel (see fv_step).  Set
+ * the state first. */
 
 /* nsteps full steps: per step dt = cfl / max(sum_d (|u_d| + c)/dx_d) of each
  * case (computed on the device from the step's initial state), then the four
  * stages.  The step sequence is captured once per cfl value in a CUDA graph
- * and replayed on the context's stream.  t_out (may be NULL) receives case
- * 0's simulated time since its last fv_set_state.  Synchronises the stream
- * once at the end and reports a device error word (FV_ERR_NONPHYSICAL). */
+ * and replayed on the context's stream.  With the fused 2D kernel in the
+ * FP32-mixed form (no viscous or gravity terms) the last stage of a step
+ * also leaves the wave speeds of the state it writes, and the next step
+ * (within this call or the next fv_step / fv_step_async) takes its dt from
+ * them instead of a CFL pass over the state; a state write in between
+ * (fv_set_state*, fv_commit_upload, fv_rk_stage) makes the next step
+ * compute them again.  Both give the same dt bit for bit.  t_out (may be
+ * NULL) receives case 0's simulated time since its last fv_set_state.
+ * Synchronises the stream once at the end and reports a device error word
+ * (FV_ERR_NONPHYSICAL). */
 fv_status fv_step(fv_ctx* ctx, int nsteps, double cfl, double* t_out);
 /* Same without any host synchronisation or readback (for timing loops). */
 fv_status fv_step_async(fv_ctx* ctx, int nsteps, double cfl);
