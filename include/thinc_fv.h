@@ -214,9 +214,11 @@ fv_status fv_get_state_all(fv_ctx* ctx, int kind, double* host);
 /* Pipelined conserved-state I/O of every case (the layout of
  * fv_set_state_all), for a stream of problems whose host transfers should
  * overlap the steps: the copies run on the device's copy engines through
- * device staging buffers (allocated with cudaMalloc at the first call, freed
- * by fv_destroy), uploads and downloads on two streams of their own.
- *   fv_upload_async   starts copying `host` (page-locked) to the upload
+ * device staging buffers, two each way used in turn so that consecutive
+ * copies follow one another without waiting for the conversions (allocated
+ * with cudaMalloc at the first call: four times the state's size; freed by
+ * fv_destroy), uploads and downloads on two streams of their own.
+ *   fv_upload_async   starts copying `host` (page-locked) to the next upload
  *                     staging buffer; returns at once.  One upload may be
  *                     pending: FV_ERR_STATE if the previous one is not yet
  *                     committed.

@@ -93,10 +93,14 @@ struct fv_ctx {
     // pipelined state I/O: device staging copies of the whole state moved by
     // the copy engines on their own streams (uploads and downloads apart), so
     // host transfers overlap the steps on the context's stream
-    double* stage_up = nullptr;
-    double* stage_down = nullptr;
+    // two staging slots each way, so that a copy never waits for the
+    // conversion of the one before it: upload slot i % 2, download slot i % 2
+    double* stage_up[2] = {nullptr, nullptr};
+    double* stage_down[2] = {nullptr, nullptr};
     cudaStream_t up_stream = nullptr, down_stream = nullptr;
-    cudaEvent_t ev_up_done = nullptr, ev_up_free = nullptr, ev_down_ready = nullptr, ev_down_done = nullptr;
+    cudaEvent_t ev_up_done[2] = {nullptr, nullptr}, ev_up_free[2] = {nullptr, nullptr};
+    cudaEvent_t ev_down_ready[2] = {nullptr, nullptr}, ev_down_done[2] = {nullptr, nullptr};
+    int up_next = 0, up_slot = 0, down_next = 0;   // next upload slot, the pending upload's slot, next download slot
     bool up_pending = false;
     size_t smem = 0;
     int stage_grid = 0, prim_grid = 0, n_items_cur = 0;
@@ -1115,12 +1119,15 @@ extern "C" void fv_destroy(fv_ctx* x)
     if (x->cap) cudaStreamDestroy(x->cap);
     if (x->up_stream) cudaStreamSynchronize(x->up_stream);
     if (x->down_stream) cudaStreamSynchronize(x->down_stream);
-    for (cudaEvent_t e : {x->ev_up_done, x->ev_up_free, x->ev_down_ready, x->ev_down_done})
+    for (cudaEvent_t e : {x->ev_up_done[0], x->ev_up_free[0], x->ev_down_ready[0], x->ev_down_done[0],
+                          x->ev_up_done[1], x->ev_up_free[1], x->ev_down_ready[1], x->ev_down_done[1]})
         if (e) cudaEventDestroy(e);
     if (x->up_stream) cudaStreamDestroy(x->up_stream);
     if (x->down_stream) cudaStreamDestroy(x->down_stream);
-    cudaFree(x->stage_up);
-    cudaFree(x->stage_down);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(x->stage_up[i]);
+        cudaFree(x->stage_down[i]);
+    }
     if (x->owns && x->base) cudaFree(x->base);
     delete x;
 }
@@ -1293,23 +1300,31 @@ static long long state_doubles(const fv_ctx* x)
 
 static fv_status io_setup(fv_ctx* x)
 {
-    if (x->stage_up) return FV_OK;
+    if (x->stage_up[0]) return FV_OK;
     const size_t bytes = sizeof(double) * (size_t)state_doubles(x);
-    cudaError_t e = cudaMalloc(&x->stage_up, bytes);
-    if (e == cudaSuccess) e = cudaMalloc(&x->stage_down, bytes);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMalloc(&x->stage_up[i], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&x->stage_down[i], bytes);
+    }
     if (e != cudaSuccess) {
-        cudaFree(x->stage_up);
-        x->stage_up = x->stage_down = nullptr;
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(x->stage_up[i]);
+            cudaFree(x->stage_down[i]);
+            x->stage_up[i] = x->stage_down[i] = nullptr;
+        }
         cudaGetLastError();
         return fail(x, FV_ERR_ALLOC, "cudaMalloc of the I/O staging buffers failed%s");
     }
     CK(x, cudaStreamCreateWithFlags(&x->up_stream, cudaStreamNonBlocking));
     CK(x, cudaStreamCreateWithFlags(&x->down_stream, cudaStreamNonBlocking));
-    for (cudaEvent_t* ev : {&x->ev_up_done, &x->ev_up_free, &x->ev_down_ready, &x->ev_down_done})
-        CK(x, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
-    // the staging buffers start free
-    CK(x, cudaEventRecord(x->ev_up_free, x->stream));
-    CK(x, cudaEventRecord(x->ev_down_done, x->down_stream));
+    for (int i = 0; i < 2; ++i) {
+        for (cudaEvent_t* ev : {&x->ev_up_done[i], &x->ev_up_free[i], &x->ev_down_ready[i], &x->ev_down_done[i]})
+            CK(x, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+        // the staging slots start free
+        CK(x, cudaEventRecord(x->ev_up_free[i], x->stream));
+        CK(x, cudaEventRecord(x->ev_down_done[i], x->down_stream));
+    }
     return FV_OK;
 }
 
@@ -1347,12 +1362,16 @@ extern "C" fv_status fv_upload_async(fv_ctx* x, const double* host)
     if (x->up_pending) return fail(x, FV_ERR_STATE, "the previous upload has not been committed%s");
     s = io_setup(x);
     if (s) return s;
-    // the staging buffer is free once the previous commit's conversion ran
-    CK(x, cudaStreamWaitEvent(x->up_stream, x->ev_up_free, 0));
-    CK(x, cudaMemcpyAsync(x->stage_up, host, sizeof(double) * (size_t)state_doubles(x), cudaMemcpyHostToDevice,
+    // this slot is free once the commit that last used it (two uploads ago)
+    // has converted it
+    const int u = x->up_next;
+    CK(x, cudaStreamWaitEvent(x->up_stream, x->ev_up_free[u], 0));
+    CK(x, cudaMemcpyAsync(x->stage_up[u], host, sizeof(double) * (size_t)state_doubles(x), cudaMemcpyHostToDevice,
                           x->up_stream));
-    CK(x, cudaEventRecord(x->ev_up_done, x->up_stream));
+    CK(x, cudaEventRecord(x->ev_up_done[u], x->up_stream));
     x->up_pending = true;
+    x->up_slot = u;
+    x->up_next = u ^ 1;
     return FV_OK;
 }
 
@@ -1362,10 +1381,11 @@ extern "C" fv_status fv_commit_upload(fv_ctx* x)
     if (s) return s;
     if (!x->up_pending) return fail(x, FV_ERR_STATE, "no upload to commit%s");
     x->smax_fresh = false;
-    CK(x, cudaStreamWaitEvent(x->stream, x->ev_up_done, 0));
-    s = stage_convert(x, true, x->stage_up);
+    const int u = x->up_slot;
+    CK(x, cudaStreamWaitEvent(x->stream, x->ev_up_done[u], 0));
+    s = stage_convert(x, true, x->stage_up[u]);
     if (s) return s;
-    CK(x, cudaEventRecord(x->ev_up_free, x->stream));
+    CK(x, cudaEventRecord(x->ev_up_free[u], x->stream));
     CK(x, cudaMemsetAsync(x->t, 0, sizeof(double) * x->ncases, x->stream));
     x->up_pending = false;
     return FV_OK;
@@ -1378,15 +1398,17 @@ extern "C" fv_status fv_download_async(fv_ctx* x, double* host)
     if (!host) return fail(x, FV_ERR_ARG, "null state pointer%s");
     s = io_setup(x);
     if (s) return s;
-    // the previous download must have left the staging buffer
-    CK(x, cudaStreamWaitEvent(x->stream, x->ev_down_done, 0));
-    s = stage_convert(x, false, x->stage_down);
+    // the download that last used this slot (two downloads ago) must have left it
+    const int d = x->down_next;
+    CK(x, cudaStreamWaitEvent(x->stream, x->ev_down_done[d], 0));
+    s = stage_convert(x, false, x->stage_down[d]);
     if (s) return s;
-    CK(x, cudaEventRecord(x->ev_down_ready, x->stream));
-    CK(x, cudaStreamWaitEvent(x->down_stream, x->ev_down_ready, 0));
-    CK(x, cudaMemcpyAsync(host, x->stage_down, sizeof(double) * (size_t)state_doubles(x), cudaMemcpyDeviceToHost,
+    CK(x, cudaEventRecord(x->ev_down_ready[d], x->stream));
+    CK(x, cudaStreamWaitEvent(x->down_stream, x->ev_down_ready[d], 0));
+    CK(x, cudaMemcpyAsync(host, x->stage_down[d], sizeof(double) * (size_t)state_doubles(x), cudaMemcpyDeviceToHost,
                           x->down_stream));
-    CK(x, cudaEventRecord(x->ev_down_done, x->down_stream));
+    CK(x, cudaEventRecord(x->ev_down_done[d], x->down_stream));
+    x->down_next = d ^ 1;
     return FV_OK;
 }
 
