@@ -332,8 +332,8 @@ fv_status fv_probe_fp64(int blocks, int threads, int iters, double* ms, double* 
  * barotropic closure in the FV_MIXED form, Peng-Robinson components and every
  * argument fv_init would reject return FV_ERR_ARG.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current and keeps it for the process; make that first call before any
- * stream capture, and do not reset the device (cudaDeviceReset) after it.
+ * current and keeps it for the process; do not reset the device
+ * (cudaDeviceReset) after it.
  * Every call uses the same array: calls that overlap on the GPU (other
  * streams, other threads) race.  The call runs on `stream` and returns once
  * the stage has finished, reporting a non-physical state met by the kernels
