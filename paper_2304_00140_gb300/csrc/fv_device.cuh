@@ -374,14 +374,18 @@ __device__ __forceinline__ bool pr_tdu(const DevParams& P, F p, F T, const F* Y,
 // first-order Taylor value a + a' dT (second-order term ~(dT/T)^2 ~ 1e-13).
 template <int NC>
 __device__ __forceinline__ int pr_invert(const DevParams& P, double rho, double e, const double* Y, double T0,
-                                         double& p, double& T)
+                                         double& p, double& T, double irho)
 {
+    // divisions on the FP64 pipe cost several instructions each: 1/rho comes
+    // from the caller, and the log ratio and k2 share one reciprocal
     PRMix<NC> m;
     pr_mix<NC>(P, Y, m);
-    const double v = m.M / rho;
+    const double v = m.M * irho;
     if (!(v > m.b) || !isfinite(e)) return ERR_NONPHYS;
-    const double L = log((v + (1.0 - SQRT2) * m.b) / (v + (1.0 + SQRT2) * m.b));
-    const double k2 = L / (2.0 * SQRT2 * m.b * m.M);
+    const double den = v + (1.0 + SQRT2) * m.b, c2 = 2.0 * SQRT2 * m.b * m.M;
+    const double r = 1.0 / (den * c2);
+    const double L = log((v + (1.0 - SQRT2) * m.b) * (c2 * r));
+    const double k2 = L * (den * r);
     double t = (T0 > 1.0 && T0 < 1e5) ? T0 : (e > 0.0 ? e / m.cvig : 300.0);
     double a, da, d2a;
     bool conv = false;
@@ -402,9 +406,40 @@ __device__ __forceinline__ int pr_invert(const DevParams& P, double rho, double 
     }
     T = t;
     if (!conv) pr_a<NC>(P, m, t, a, da, d2a);
-    p = PR_RU * t / (v - m.b) - a / (v * v + 2.0 * m.b * v - m.b * m.b);
+    // RU t / (v - b) - a / (v^2 + 2 b v - b^2) over one division
+    const double d1 = v - m.b, d2 = v * v + 2.0 * m.b * v - m.b * m.b;
+    p = (PR_RU * t * d2 - a * d1) / (d1 * d2);
     if (!conv) return ERR_NONCONV;
     return isfinite(p) ? 0 : ERR_NONPHYS;
+}
+
+// FP32 Newton on the same residual as pr_invert, from T0 to |dT| <= 1e-6 T
+// (at most 8 steps): the starting temperature of the FP64 Newton in the
+// mixed form, which then usually stops after one step.  Returns T0 when a
+// step leaves the physical range.
+template <int NC>
+__device__ __forceinline__ float pr_predict_T(const DevParams& P, float rho, float e, const float* Y, float T0)
+{
+    PRMix<NC, float> m;
+    pr_mix<NC, float>(P, Y, m);
+    const float v = m.M / rho;
+    if (!(v > m.b) || !(T0 > 1.0f && T0 < 1e5f)) return T0;
+    const float k2 = pr_logratio(v, m.b) / (2.0f * float(SQRT2) * m.b * m.M);
+    float t = T0;
+#pragma unroll 1
+    for (int it = 0; it < 8; ++it) {
+        float a, da, d2a;
+        pr_a<NC, float>(P, m, t, a, da, d2a);
+        const float f = m.cvig * t + (a - t * da) * k2 - e;
+        const float df = m.cvig - t * d2a * k2;
+        float tn = t - fdiv(f, df);
+        tn = fminf(fmaxf(tn, 0.2f * t), 5.0f * t);
+        if (!(tn > 1.0f && tn < 1e5f)) return T0;
+        const bool done = fabsf(tn - t) <= 1e-6f * t;
+        t = tn;
+        if (done) break;
+    }
+    return t;
 }
 
 // ------------------------------------------------------------ closure
@@ -743,16 +778,22 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* 
         return (rho > 0.0 && pd > 0.0 && isfinite(pd) && isfinite(e)) ? 0 : ERR_NONPHYS;
     }
     if constexpr (CL == CL_PR) {
-        // Peng-Robinson: FP64 Newton in both forms
-        const double rho = qv_d(qc[0]);
+        // Peng-Robinson: FP64 Newton in both forms; the mixed form starts it
+        // from an FP32 Newton's temperature (FP32 arithmetic for the steps
+        // that only approach the root, FP64 for the last)
+        const double rho = qv_d(qc[0]), irho = 1.0 / rho;
         double ked = 0.0;
 #pragma unroll
         for (int d = 0; d < ND; ++d) { const double m = qv_d(qc[1 + d]); ked += 0.5 * m * m; }
-        const double e = (qv_d(qc[ND + 1]) - ked / rho) / rho;
+        const double e = (qv_d(qc[ND + 1]) - ked * irho) * irho;
         double Yd[NC], pd = 0.0, Td = 0.0;
 #pragma unroll
         for (int k = 0; k < NC; ++k) Yd[k] = double(Y[k]);
-        const int st = (rho > 0.0) ? pr_invert<NC>(P, rho, e, Yd, T0, pd, Td) : ERR_NONPHYS;
+        double Ts = T0;
+        if constexpr (sizeof(R) == 4) {
+            if (rho > 0.0 && isfinite(e)) Ts = double(pr_predict_T<NC>(P, float(rho), float(e), Y, float(T0)));
+        }
+        const int st = (rho > 0.0) ? pr_invert<NC>(P, rho, e, Yd, Ts, pd, Td, irho) : ERR_NONPHYS;
         w[ND] = R(pd - P.p_ref);
         w[ND + 1] = R(Td);
         T_out = R(Td);
