@@ -436,6 +436,8 @@ static void build_params(fv_ctx* x, const fv_components* cm, const fv_eos* eos)
             Kt.b_pso = T(lq.psat - P.p_ref);
             Kt.b_icl2 = T(1.0 / (lq.cl * lq.cl));
             Kt.b_icm2 = T(lq.rho_sl / lq.psat);   // 1/c_M^2, c_M^2 = p_sat / rho_sat,liq
+            Kt.b_hcl2 = T(0.5 * lq.cl * lq.cl);
+            Kt.b_irsl = T(1.0 / lq.rho_sl);
         }
         Kt.thr_vap = T(eos->thr_vap);
     };

@@ -59,6 +59,7 @@ struct ConstT {
     // saturated liquid / vapour densities, p_sat - p_ref, 1/c_L^2, 1/c_M^2
     R brt[MAXC];
     R b_rsl, b_rsv, b_pso, b_icl2, b_icm2, thr_vap;
+    R b_hcl2, b_irsl;       // c_L^2 / 2 and 1 / rho_sat,liq (the recovery's divisions as products)
 };
 
 struct CompDev {
@@ -750,12 +751,14 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* 
         // (p - A)(d + k p) = B p, k = 1/c^2, d = rho_sat,liq - p_sat k: the liquid
         // branch's positive root if it is >= p_sat, else (d = 0 below p_sat)
         // p = A + B p_sat / rho_sat,liq.  The energy is passive (T slot = e).
+        // (divisions on the FP64 pipe cost several instructions each: one
+        // reciprocal of rho, the constant ones as products)
         const ConstT<double>& Kd = P.kd;
-        const double rho = qv_d(qc[0]);
+        const double rho = qv_d(qc[0]), irho = 1.0 / rho;
         double ked = 0.0;
 #pragma unroll
         for (int d = 0; d < ND; ++d) { const double m = qv_d(qc[1 + d]); ked += 0.5 * m * m; }
-        const double e = (qv_d(qc[ND + 1]) - ked / rho) / rho;
+        const double e = (qv_d(qc[ND + 1]) - ked * irho) * irho;
         double A = 0.0, B = 0.0;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
@@ -768,14 +771,16 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* 
             const double kk = Kd.b_icl2, dd = Kd.b_rsl - psat * kk;
             const double b = dd - A * kk - B;
             const double disc = sqrt(b * b + 4.0 * kk * A * dd);
-            pd = (b < 0.0) ? (disc - b) / (2.0 * kk) : ((A > 0.0) ? 2.0 * A * dd / (b + disc) : 0.0);
-            if (!(pd >= psat)) pd = A + B * psat / Kd.b_rsl;
+            pd = (b < 0.0) ? (disc - b) * Kd.b_hcl2 : ((A > 0.0) ? 2.0 * A * dd / (b + disc) : 0.0);
+            if (!(pd >= psat)) pd = A + B * psat * Kd.b_irsl;
         }
         w[ND] = R(pd - P.p_ref);
         w[ND + 1] = R(e);
         T_out = R(e);
         p_abs = R(pd);
-        return (rho > 0.0 && pd > 0.0 && isfinite(pd) && isfinite(e)) ? 0 : ERR_NONPHYS;
+        // rho > 0, 0 < pd < inf, e finite (on the bit patterns)
+        const long long pb = dbits(pd);
+        return (gt0(rho) && pb > 0 && pb < DINF && (dbits(e) & ~DSIGN) < DINF) ? 0 : ERR_NONPHYS;
     }
     if constexpr (CL == CL_PR) {
         // Peng-Robinson: FP64 Newton in both forms; the mixed form starts it
