@@ -843,26 +843,47 @@ __device__ __forceinline__ int prim_recover(const DevParams& P, const Q* qc, R* 
         b += Yc * (Ek[k] + Kc.Po[k]);
         cc += Yc * (Kc.Po[k] * Ek[k]);
         se += Yc * Ek[k];
-        if (Y[k] > R(0)) { if (P.c[k].classA) sA += Y[k]; else sB += Y[k]; }
+        if (gt0(Y[k])) { if (P.c[k].classA) sA += Y[k]; else sB += Y[k]; }
     }
-    R pp;     // p - p_ref
-    if (P.single_class || sA == R(0) || sB == R(0)) {
-        pp = fdiv(-se, cv);
+    R pp, T;     // p - p_ref, temperature
+    const bool one = P.single_class || !gt0(sA) || !gt0(sB);
+    if constexpr (sizeof(R) == 8) {
+        // FP64: p' = Np / Dp and T = (rho e' + p) / (rho cp) over one
+        // reciprocal, 1 / (Dp rho cp) (divisions cost several FP64-pipe
+        // instructions each)
+        R Np, Dp;
+        if (one) {
+            Np = -se;
+            Dp = cv;
+        } else {
+            const R disc = b * b - R(4) * cv * cc;
+            const R sq = sq_rt(fmax(disc, R(0)));
+            const bool bpos = dbits(b) >= 0;
+            Np = bpos ? R(-2) * cc : sq - b;
+            Dp = bpos ? b + sq : R(2) * cv;
+        }
+        const R rcp = rr * cp, r = frcp(Dp * rcp);
+        pp = Np * rcp * r;
+        T = ((rhoe_r + Kc.p_ref) * Dp + Np) * r;
     } else {
-        const R disc = b * b - R(4) * cv * cc;
-        const R sq = sq_rt(disc > R(0) ? disc : R(0));
-        pp = (b >= R(0)) ? fdiv(R(-2) * cc, b + sq) : fdiv(sq - b, R(2) * cv);
+        if (one) {
+            pp = fdiv(-se, cv);
+        } else {
+            const R disc = b * b - R(4) * cv * cc;
+            const R sq = sq_rt(disc > R(0) ? disc : R(0));
+            pp = (b >= R(0)) ? fdiv(R(-2) * cc, b + sq) : fdiv(sq - b, R(2) * cv);
+        }
+        T = fdiv(rhoe_r + (Kc.p_ref + pp), rr * cp);
     }
     const R p = Kc.p_ref + pp;
-    const R T = fdiv(rhoe_r + p, rr * cp);
     w[ND] = pp;
     w[ND + 1] = T;
     T_out = T;
     p_abs = p;
-    bool ok = (rr > R(0)) && (T > R(0)) && (cv > R(0));
+    bool ok = gt0(rr) && gt0(T) && gt0(cv);
 #pragma unroll
     for (int k = 0; k < NC; ++k)
-        if (Y[k] > R(0)) ok = ok && (Kc.Pk[k] + pp > R(0));
+        if (gt0(Y[k])) ok = ok && gt0(Kc.Pk[k] + pp);
     return ok ? 0 : ERR_NONPHYS;
 }
 
