@@ -45,6 +45,11 @@ constexpr int MARCH_ILES = 1, MARCH_CSF = 2, MARCH_VISC = 4;
 // CFL pass of the next step would from the same values, so that pass is
 // left out
 constexpr int MARCH_CFL = 8;
+// MARCH_BARO (plain mode, FP32-mixed form): the barotropic closure (Sec.
+// 2.2) with the liquid-vapour density THINC (Sec. 3.4): each window row also
+// carries the cell density, sound speed and vapour fraction of Eq. 2-7, as
+// the primitive pass writes them for the tiled kernel
+constexpr int MARCH_BARO = 16;
 
 // Inflow-disc test of an x-low ghost cell in source row iy (FP64, the same
 // expression as the primitive pass).  Not inlined: only lanes on an inflow
@@ -62,6 +67,7 @@ template <int NV, typename R> struct MRow {
     R w[NV];
     R rho, c, e;
     R mu, kc;    // mixture viscosity and conductivity (viscous mode)
+    R av;        // vapour fraction (barotropic mode)
 };
 
 template <int NC, typename R, int NWARP, int MB, int LIM, int MODE, typename Q>
@@ -71,7 +77,10 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
     constexpr bool ILES = (MODE & MARCH_ILES) != 0, CSF = (MODE & MARCH_CSF) != 0, AUX = ILES || CSF;
     constexpr bool VISC = (MODE & MARCH_VISC) != 0;
     constexpr bool CFLM = (MODE & MARCH_CFL) != 0;
+    constexpr bool BARO = (MODE & MARCH_BARO) != 0;
+    constexpr int CL = BARO ? CL_BARO : CL_SG;
     static_assert(!(CFLM && VISC), "the fused CFL speed has no diffusive term");
+    static_assert(!(BARO && (AUX || VISC)), "the barotropic mode is plain");
     const DevParams& P = A.P;
     const ConstT<R>& Kc = K<R>(P);
     // q^{k-1} never aliases q^k (the stages go q0 -> qA -> qB -> qA -> q0)
@@ -116,7 +125,7 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
         auto recover_row = [&](const Q* qc, const RowRef& rr, MRow<NV, R>& row) {
             R* const w = row.w;
             R rho, T, pabs;
-            const int rst = prim_recover<ND, NC, R, false, Q>(P, qc, w, rho, T, pabs, 0.0);
+            const int rst = prim_recover<ND, NC, R, CL, Q>(P, qc, w, rho, T, pabs, 0.0);
             bool ok = rst == 0;
             if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
             if (inx ? !rr.disc : fx) w[0] = -w[0];
@@ -130,14 +139,15 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                 for (int k = 0; k < NC - 1; ++k) w[ND + 2 + k] = R(C.in_Y[k]);
             }
             R rr_ = rho, cs = R(0);
-            if (ILES || rr.disc) {
+            if (ILES || BARO || rr.disc) {
                 R e_;
-                ok = tdu<NC, R, false>(P, w[ND], w[ND + 1], w + ND + 2, rr_, e_, cs) && ok;
+                ok = tdu<NC, R, CL>(P, w[ND], w[ND + 1], w + ND + 2, rr_, e_, cs) && ok;
                 if (!rr.disc) rr_ = rho;
             }
             bad = bad || (!ok && rst != ERR_NONCONV);
             row.rho = rr_;
             row.c = cs;
+            if constexpr (BARO) row.av = baro_vapour<NC, R>(P, w[ND], rr_, w + ND + 2);
             if (AUX) {
                 R s = R(0), al = R(0), ag = R(0);
 #pragma unroll
@@ -289,6 +299,12 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
         R at_y = R(0);           // smoothed fraction
         R nlo[2] = {R(0), R(0)}; // unit normal at the vertex (lane + 1/2, y - 1/2)
         R r4[4] = {R(0), R(0), R(0), R(0)}, c4[4] = {R(0), R(0), R(0), R(0)};
+        R a4[4] = {R(0), R(0), R(0), R(0)};   // vapour fractions (barotropic mode)
+        // barotropic mode: densities and vapour fractions of the four cells of a y-face's stencil
+        auto baro_y = [&]() {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) { r4[s] = W[s].rho; a4[s] = W[s].av; }
+        };
         R Fy[NV];
         {
             int flag_lo = 1;
@@ -304,7 +320,8 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) ws[s][v] = W[s].w[v];
             if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
-            const bool ok = face_flux<ND, NC, R, false, LIM, ILES ? 1 : 0>(P, 1, ws, r4, c4, flag_lo | flag_y, Fy);
+            if (BARO) baro_y();
+            const bool ok = face_flux<ND, NC, R, CL, LIM, ILES ? 1 : 0>(P, 1, ws, r4, c4, flag_lo | flag_y, Fy, a4);
             bad = bad || (!ok && own_col);
             if (VISC && P.visc) visc_y(W, Fy);
         }
@@ -341,7 +358,9 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
 #pragma unroll
                     for (int v = 0; v < NV; ++v) ws[s][v] = W[s].w[v];
                 if (ILES) { r4[1] = W[1].rho; r4[2] = W[2].rho; c4[1] = W[1].c; c4[2] = W[2].c; }
-                const bool ok = face_flux<ND, NC, R, false, LIM, ILES ? 1 : 0>(P, 1, ws, r4, c4, flag_y | flag_up, Fyn);
+                if (BARO) baro_y();
+                const bool ok = face_flux<ND, NC, R, CL, LIM, ILES ? 1 : 0>(P, 1, ws, r4, c4, flag_y | flag_up, Fyn,
+                                                                           a4);
                 bad = bad || (!ok && own_col);
                 if (VISC && P.visc) visc_y(W, Fyn);
             }
@@ -362,7 +381,13 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
                     c4[1] = W[1].c; c4[2] = shr(W[1].c);
                     fl = flag_y | __shfl_down_sync(FULL, flag_y, 1);
                 }
-                const bool ok = face_flux<ND, NC, R, false, LIM, ILES ? 1 : 0>(P, 0, ws, r4, c4, fl, Fx);
+                if (BARO) {
+                    r4[1] = W[1].rho; r4[0] = shl(W[1].rho); r4[2] = shr(W[1].rho);
+                    r4[3] = __shfl_down_sync(FULL, W[1].rho, 2);
+                    a4[1] = W[1].av; a4[0] = shl(W[1].av); a4[2] = shr(W[1].av);
+                    a4[3] = __shfl_down_sync(FULL, W[1].av, 2);
+                }
+                const bool ok = face_flux<ND, NC, R, CL, LIM, ILES ? 1 : 0>(P, 0, ws, r4, c4, fl, Fx, a4);
                 bad = bad || (!ok && (own_col || own_right));
                 if (VISC && P.visc) visc_x(W, Fx);
             }
@@ -435,9 +460,9 @@ __global__ void __launch_bounds__(32 * NWARP, MB) march2d_kernel(MarchArgs A)
             if (CFLM && own_col) {
                 // the CFL pass's recovery and sound speed of this interior cell
                 R w[NV], rho, T, pabs, rr_, e_, cs;
-                const int rst = prim_recover<ND, NC, R, false, Q>(P, qk, w, rho, T, pabs, 0.0);
+                const int rst = prim_recover<ND, NC, R, CL, Q>(P, qk, w, rho, T, pabs, 0.0);
                 if (rst == ERR_NONCONV) set_err(A.err, ERR_NONCONV);
-                const bool ok = tdu<NC, R, false>(P, w[ND], w[ND + 1], w + ND + 2, rr_, e_, cs) && rst == 0;
+                const bool ok = tdu<NC, R, CL>(P, w[ND], w[ND + 1], w + ND + 2, rr_, e_, cs) && rst == 0;
                 bad = bad || (!ok && rst != ERR_NONCONV);
                 const R cis[2] = {ci0, ci1};
                 R sp = R(0);

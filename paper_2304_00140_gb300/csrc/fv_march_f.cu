@@ -2,4 +2,5 @@
 #define FV_MR float
 #define FV_MQ float2
 #define FV_MSUFFIX f
+#define FV_MBARO 1
 #include "fv_march_inst.cuh"

@@ -6,4 +6,5 @@
 #define FV_MQ float2
 #define FV_MSUFFIX fc
 #define FV_MCFL 1
+#define FV_MBARO 1
 #include "fv_march_inst.cuh"

@@ -54,6 +54,14 @@ int occ_v(int var)
 }
 }  // namespace
 
+// the barotropic modes (MARCH_BARO) exist in the FP32-mixed form only
+#ifdef FV_MBARO
+#define FV_MBARO_CASE(fn, m, ...) \
+    case m: return nc == 2 ? fn<2, m>(__VA_ARGS__) : fn<3, m>(__VA_ARGS__);
+#else
+#define FV_MBARO_CASE(fn, m, ...)
+#endif
+
 #ifndef FV_MCFL
 // the scheme modes (MARCH_ILES | MARCH_CSF | MARCH_VISC bits)
 #define FV_MODE_SWITCH(fn, ...)                                                   \
@@ -65,7 +73,9 @@ int occ_v(int var)
     case 4: return nc == 2 ? fn<2, 4>(__VA_ARGS__) : fn<3, 4>(__VA_ARGS__);        \
     case 5: return nc == 2 ? fn<2, 5>(__VA_ARGS__) : fn<3, 5>(__VA_ARGS__);        \
     case 6: return nc == 2 ? fn<2, 6>(__VA_ARGS__) : fn<3, 6>(__VA_ARGS__);        \
-    default: return nc == 2 ? fn<2, 7>(__VA_ARGS__) : fn<3, 7>(__VA_ARGS__);       \
+    case 7: return nc == 2 ? fn<2, 7>(__VA_ARGS__) : fn<3, 7>(__VA_ARGS__);        \
+    FV_MBARO_CASE(fn, 16, __VA_ARGS__)                                            \
+    default: return FV_MBAD;                                                      \
     }
 #else
 // the last-stage modes with the fused CFL speed (MARCH_CFL | MARCH_ILES | MARCH_CSF)
@@ -75,6 +85,7 @@ int occ_v(int var)
     case 9: return nc == 2 ? fn<2, 9>(__VA_ARGS__) : fn<3, 9>(__VA_ARGS__);        \
     case 10: return nc == 2 ? fn<2, 10>(__VA_ARGS__) : fn<3, 10>(__VA_ARGS__);     \
     case 11: return nc == 2 ? fn<2, 11>(__VA_ARGS__) : fn<3, 11>(__VA_ARGS__);     \
+    FV_MBARO_CASE(fn, 24, __VA_ARGS__)                                            \
     default: return FV_MBAD;                                                      \
     }
 #endif

@@ -224,3 +224,25 @@ def test_vapour_collapse_full_size_windows():
         sl = (slice(None), 0, slice(lo[1], hi[1]), slice(lo[0], hi[0]))
         d = np.abs(got[sl] - ref[sl]).reshape(q.shape[0], -1).max(axis=1) / scale
         assert np.all(d < tol), (lo, d)
+
+
+PLAIN_2D = ["gas_collapse", "vapour_collapse", "gas_sheared_plain", "vapour_sheared_plain", "vapour_other_limiters"]
+
+
+@pytest.mark.parametrize("name", PLAIN_2D)
+def test_baro_fused_matches_tiled_mixed(name, monkeypatch):
+    """the fused 2D kernel's barotropic mode (FP32-mixed form) against the
+    tiled kernel after its primitive pass: the same formulas in the same
+    order, so both agree to rounding over three CFL steps"""
+    w, W = CASES[name]()
+    q = oracle.Oracle(w).prim_to_cons(W)
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("FV_FUSED", fused)
+        s = fv.Solver(w, precision=fv.FV_MIXED)
+        s.set_state(q)
+        s.step(3, w.cfl)
+        assert s.tile()["fused"] == (fused == "1")
+        out[fused] = s.get_state()
+    d = _rel(w, out["1"], out["0"])
+    assert np.all(d < 1e-6), d
