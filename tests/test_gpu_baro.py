@@ -4,7 +4,7 @@ Remarks 1-2): gas and vapour bubble collapse near a wall (Sec. 4.9) on
 coarse grids, and sheared gas / vapour pockets at uniform pressure in
 plain and App. D mode; step size, state I/O of the passive energy slot and
 the FP32-mixed form's accuracy.  Tolerance 1e-10 relative per conserved
-field (momentum against the momentum vector's scale), the north-star bound;
+field (momentum against the momentum vector's scale), the parity bound;
 collapses that start at rest are also run as they are, an ill-conditioned
 case with its own bound."""
 import numpy as np
