@@ -227,7 +227,7 @@ constexpr double SQRT2 = 1.4142135623730951;
 
 template <int NC, typename F = double>
 struct PRMix {
-    F X[NC], M, b, cvig;
+    F X[NC], M, iM, b, cvig;   // mole fractions, molar mass and its reciprocal, covolume, ideal-gas cv
 };
 
 // PR constants in the working precision
@@ -253,6 +253,7 @@ __device__ __forceinline__ void pr_mix(const DevParams& P, const F* Y, PRMix<NC,
 #pragma unroll
     for (int k = 0; k < NC; ++k) { s += Y[k] * K.iM[k]; cv += Y[k] * K.cv[k]; }
     m.M = F(1) / s;
+    m.iM = s;
     m.cvig = cv;
     m.b = F(0);
 #pragma unroll
@@ -315,14 +316,18 @@ __device__ __forceinline__ bool pr_tdu(const DevParams& P, F p, F T, const F* Y,
     pr_mix<NC, F>(P, Y, m);
     F a, da, d2a;
     pr_a<NC, F>(P, m, T, a, da, d2a);
+    // (divisions cost several instructions each, on the FP64 pipe in the
+    // FP64 form: constant ones are products, and the others share
+    // reciprocals where the formulas allow)
     const F RU = F(PR_RU);
-    const F RT = RU * T;
-    const F A = a * p / (RT * RT), B = m.b * p / RT;
+    const F RT = RU * T, iRT = F(1) / RT;
+    const F A = a * p * iRT * iRT, B = m.b * p * iRT;
+    const F third = F(1.0 / 3.0), i27 = F(1.0 / 27.0);
     const F c2 = -(F(1) - B), c1 = A - F(3) * B * B - F(2) * B, c0 = -(A * B - B * B - B * B * B);
-    const F sh = c2 / F(3);
+    const F sh = c2 * third;
     const F pp = c1 - c2 * sh;
-    const F qq = (F(2) / F(27)) * c2 * c2 * c2 - c2 * c1 / F(3) + c0;
-    const F D = F(0.25) * qq * qq + pp * pp * pp / F(27);
+    const F qq = (F(2) * i27) * c2 * c2 * c2 - c2 * c1 * third + c0;
+    const F D = F(0.25) * qq * qq + pp * pp * pp * i27;
     F Z[3];
     int nr;
     if (D > F(0)) {
@@ -330,13 +335,13 @@ __device__ __forceinline__ bool pr_tdu(const DevParams& P, F p, F T, const F* Y,
         Z[0] = m_cbrt(F(-0.5) * qq + sD) + m_cbrt(F(-0.5) * qq - sD) - sh;
         nr = 1;
     } else {
-        const F r = sq_rt(fmax(-pp / F(3), F(0)));
+        const F r = sq_rt(fmax(-pp * third, F(0)));
         const F cosphi = (r > F(0)) ? fmin(F(1), fmax(F(-1), F(-0.5) * qq / (r * r * r))) : F(1);
         const F phi = m_acos(cosphi);
         const F tpi = F(2) * F(3.141592653589793);
-        Z[0] = F(2) * r * m_cos(phi / F(3)) - sh;
-        Z[1] = F(2) * r * m_cos((phi - tpi) / F(3)) - sh;
-        Z[2] = F(2) * r * m_cos((phi + tpi) / F(3)) - sh;
+        Z[0] = F(2) * r * m_cos(phi * third) - sh;
+        Z[1] = F(2) * r * m_cos((phi - tpi) * third) - sh;
+        Z[2] = F(2) * r * m_cos((phi + tpi) * third) - sh;
         nr = 3;
     }
     F best = F(-1), gbest = F(sizeof(F) == 8 ? 1e300 : 1e30);
@@ -352,16 +357,26 @@ __device__ __forceinline__ bool pr_tdu(const DevParams& P, F p, F T, const F* Y,
         if (g < gbest) { gbest = g; best = z; }
     }
     if (!(best > B)) return false;
-    const F v = best * RT / p;
-    const F L = pr_logratio(v, m.b);
-    const F k2 = L / (F(2) * F(SQRT2) * m.b * m.M);
-    rho = m.M / v;
+    const F v = best * RT / p, iv = F(1) / v;
+    const F c2k = F(2) * F(SQRT2) * m.b * m.M;
+    F k2;
+    if constexpr (sizeof(F) == 8) {
+        // log((v + (1 - sqrt2) b) / den) and k2 = L / c2k over one reciprocal
+        const F den = v + (F(1) + F(SQRT2)) * m.b, r = F(1) / (den * c2k);
+        k2 = log((v + (F(1) - F(SQRT2)) * m.b) * (c2k * r)) * (den * r);
+    } else {
+        k2 = pr_logratio(v, m.b) / c2k;
+    }
+    rho = m.M * iv;
     e = m.cvig * T + (a - T * da) * k2;
     const F cv = m.cvig - T * d2a * k2;
     const F dd = v * v + F(2) * m.b * v - m.b * m.b;
-    const F dpdT = RU / (v - m.b) - da / dd;
-    const F dpdv = -RT / ((v - m.b) * (v - m.b)) + a * (F(2) * v + F(2) * m.b) / (dd * dd);
-    const F c2s = -(v * v / m.M) * dpdv + T * dpdT * dpdT / (rho * rho * cv);
+    const F i1 = F(1) / (v - m.b), i2 = F(1) / dd;
+    const F dpdT = RU * i1 - da * i2;
+    const F dpdv = -RT * i1 * i1 + a * (F(2) * v + F(2) * m.b) * i2 * i2;
+    // v^2 / M and 1 / rho^2 = v^2 / M^2 from 1 / M
+    const F v2iM = v * v * m.iM;
+    const F c2s = -v2iM * dpdv + T * dpdT * dpdT * (v2iM * m.iM) / cv;
     c = sq_rt(c2s);
     return c2s > F(0) && cv > F(0);
 }
