@@ -640,15 +640,17 @@ __device__ __forceinline__ bool baro_tdu(const DevParams& P, R pp, const R* Y, R
     const R p = Kc.p_ref + pp;
     const R ic2 = (pp >= Kc.b_pso) ? Kc.b_icl2 : Kc.b_icm2;
     const R rlm = Kc.b_rsl + (pp - Kc.b_pso) * ic2;
-    const R ip = frcp(p);
+    // 1/p and 1/rho_LM over one reciprocal (1 for a liquid-free state, where
+    // rho_LM is not used)
+    const R irp = frcp(p * rlm);
+    const R ip = rlm * irp, ir = p * irp;
     R v = R(0), w = R(0);
-    bool ok = p > R(0);
+    bool ok = gt0(p);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
         if (k == P.liquid) {
-            if (Y[k] > R(0)) {
-                ok = ok && rlm > R(0);
-                const R ir = frcp(rlm);
+            if (gt0(Y[k])) {
+                ok = ok && gt0(rlm);
                 v += Y[k] * ir;
                 w += Y[k] * ir * ir * ic2;
             }
@@ -660,7 +662,7 @@ __device__ __forceinline__ bool baro_tdu(const DevParams& P, R pp, const R* Y, R
     }
     rho = frcp(v);
     c = v * rsq(w);
-    return ok && (v > R(0)) && (w > R(0));
+    return ok && gt0(v) && gt0(w);
 }
 
 // Vapour volume fraction of Eq. 2-7 (vapour share of the liquid-vapour phase
