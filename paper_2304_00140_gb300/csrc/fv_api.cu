@@ -652,7 +652,7 @@ static fv_status apply_zmarch(fv_ctx* x, int chunk, int var)
 {
     const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
     if (!t42) var = 2;
-    else if (zm_visc(x)) var = 1;
+    else if (zm_visc(x) || !x->mixed) var = 1;
     const cuuint32_t box[4] = {cuuint32_t(ZM_TX + 4), cuuint32_t(ZM_TY + 4), 1, cuuint32_t(x->nprim)};
     if (!encode_maps(x, box, ZM_TX, x->d_tmaps_z)) return fail(x, FV_ERR_ARG, "z-marching kernel needs TMA%s");
     std::vector<int4> it;
@@ -664,10 +664,10 @@ static fv_status apply_zmarch(fv_ctx* x, int chunk, int var)
     }
     if ((int)it.size() > x->L.n_items_z) return fail(x, FV_ERR_STATE, "z-march work list overflow%s");
     CK(x, cudaMemcpy(x->d_items_z, it.data(), sizeof(int4) * it.size(), cudaMemcpyHostToDevice));
-    const size_t smem = zmarch_smem(x->nc, x->nprim);
+    const size_t smem = zmarch_smem(x->nc, x->nprim, !x->mixed);
     if (smem > x->smem_max) return fail(x, FV_ERR_ARG, "z-marching kernel does not fit in shared memory%s");
-    CK(x, zmarch_set_smem(x->nc, var, zm_visc(x), smem));
-    const int occ = zmarch_occupancy(x->nc, var, zm_visc(x), smem);
+    CK(x, zmarch_set_smem(x->nc, var, zm_visc(x), !x->mixed, smem));
+    const int occ = zmarch_occupancy(x->nc, var, zm_visc(x), !x->mixed, smem);
     if (occ < 1) return fail(x, FV_ERR_CUDA, "z-marching kernel cannot be resident%s");
     x->zm = true;
     x->fused = false;
@@ -899,17 +899,18 @@ static fv_status tune(fv_ctx* x)
         // after the primitive pass above, like the tiled kernel
         const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
         float zbest = 1e30f;
-        // the viscous instantiations: variant 1 (Table 4.2 pair) or 2 (run-time pair)
+        // the viscous and FP64 instantiations: variant 1 (Table 4.2 pair) or 2 (run-time pair)
         const int zvars_t42[3] = {0, 1, 3}, zvars_rt[1] = {2}, zvars_visc[1] = {1};
+        const bool few = zm_visc(x) || !x->mixed;
         for (int ci = 0; ci < 3; ++ci)
-            for (int vi = 0; vi < (t42 && !zm_visc(x) ? 3 : 1); ++vi) {
-                const int var = !t42 ? zvars_rt[vi] : (zm_visc(x) ? zvars_visc[vi] : zvars_t42[vi]);
+            for (int vi = 0; vi < (t42 && !few ? 3 : 1); ++vi) {
+                const int var = !t42 ? zvars_rt[vi] : (few ? zvars_visc[vi] : zvars_t42[vi]);
                 if (apply_zmarch(x, ZM_CHUNKS[ci], var)) { x->msg.clear(); continue; }
                 ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, x->QB,
                          x->dt, 0.0, x->err};
                 float ms = 0.f;
                 st = timed([&] {
-                    return launch_zmarch(x->nc, x->zvar, zm_visc(x), za, x->zm_grid, x->zm_smem, x->stream);
+                    return launch_zmarch(x->nc, x->zvar, zm_visc(x), !x->mixed, za, x->zm_grid, x->zm_smem, x->stream);
                 }, ms);
                 if (st) return st;
                 zbest = std::min(zbest, ms);
@@ -1030,7 +1031,9 @@ static fv_status init_common(int ncases, const fv_grid* grids, const fv_componen
     // the barotropic closure in the fused kernel: FP32-mixed form, plain mode
     x->fused_ok = x->nd == 2 && !x->P.pr && !x->P.hf && !x->P.capj &&
                   (!x->P.baro || (x->mixed && !x->P.iles && !x->P.csf && !x->P.visc && !x->P.grav));
-    x->zm_ok = x->nd == 3 && x->mixed && x->ff && !x->P.pr && !x->P.baro && !x->P.hf &&
+    // FP32-mixed form, or the FP64 form without viscous terms and gravity
+    x->zm_ok = x->nd == 3 && (x->mixed ? x->ff != 0 : !(x->P.visc || x->P.grav)) && !x->P.pr && !x->P.baro &&
+               !x->P.hf &&
                !x->P.capj;
     CK(x, cudaDeviceSynchronize());
     return FV_OK;
@@ -1568,7 +1571,7 @@ static fv_status enqueue_stage(fv_ctx* x, int k, double cfl, cudaStream_t s, boo
     if (x->zm) {
         ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, out, x->dt,
                  LSRK_A[k - 1], x->err};
-        PROF(FV_KERNEL_STAGE, launch_zmarch(x->nc, x->zvar, zm_visc(x), za, x->zm_grid, x->zm_smem, s));
+        PROF(FV_KERNEL_STAGE, launch_zmarch(x->nc, x->zvar, zm_visc(x), !x->mixed, za, x->zm_grid, x->zm_smem, s));
         x->launches++;
         return FV_OK;
     }

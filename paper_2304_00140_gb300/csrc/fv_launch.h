@@ -35,11 +35,12 @@ int march_occupancy(int nc, int mixed, int mode, int var);   // blocks per SM
 // 352 threads, 2 limiter pair read at run time (320 threads).  visc = 1: with
 // the Eq. 2-2 viscous, heat-flux and gravity terms (variants 1 and 2).
 struct ZArgs;
-cudaError_t launch_zmarch(int nc, int var, int visc, const ZArgs& A, int grid, size_t smem, cudaStream_t s);
-cudaError_t zmarch_set_smem(int nc, int var, int visc, size_t smem);
-int zmarch_occupancy(int nc, int var, int visc, size_t smem);   // blocks per SM (0: no such variant)
+// fp64 = 1: the FP64 form (variants 1 and 2, no viscous terms).
+cudaError_t launch_zmarch(int nc, int var, int visc, int fp64, const ZArgs& A, int grid, size_t smem, cudaStream_t s);
+cudaError_t zmarch_set_smem(int nc, int var, int visc, int fp64, size_t smem);
+int zmarch_occupancy(int nc, int var, int visc, int fp64, size_t smem);   // blocks per SM (0: no such variant)
 int zmarch_threads(int var);
-size_t zmarch_smem(int nc, int nprim);
+size_t zmarch_smem(int nc, int nprim, int fp64);
 
 // state I/O and diagnostics (FP64)
 struct IoArgs {

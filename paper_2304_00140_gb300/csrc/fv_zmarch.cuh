@@ -20,6 +20,8 @@
 // source in the update.
 #pragma once
 
+#include <type_traits>
+
 #include "fv_kernels.cuh"
 
 namespace tfv {
@@ -40,18 +42,22 @@ struct ZArgs {
 
 constexpr int ZM_TX = 16, ZM_TY = 16;
 
-// elements between two plane slots: nprim x HXY floats rounded up to 128 bytes
-__host__ __device__ inline int zm_slot_stride(int nprim, int hxy) { return ((nprim * hxy * 4 + 127) & ~127) / 4; }
+// elements between two plane slots: nprim x HXY values of es bytes rounded up to 128 bytes
+__host__ __device__ inline int zm_slot_stride(int nprim, int hxy, int es)
+{
+    return ((nprim * hxy * es + 127) & ~127) / es;
+}
 
+// dynamic shared memory of the kernel with es-byte values (4 FP32-mixed, 8 FP64)
 template <int NC>
-inline size_t zm_smem_bytes(int nprim)
+inline size_t zm_smem_bytes(int nprim, int es)
 {
     constexpr int TX = ZM_TX, TY = ZM_TY, NV = 3 + NC + 1;
     constexpr int HX = TX + 4, HY = TY + 4, HXY = HX * HY, AXY = (TX + 2) * (TY + 2), VXY = (TX + 1) * (TY + 1);
     constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), TXY = TX * TY;
-    const size_t floats = 4 * (size_t)zm_slot_stride(nprim, HXY) + NV * (NFX + NFY) + 2 * NV * TXY + 2 * AXY +
-                          2 * 2 * 3 * VXY;
-    return floats * 4 + 2 * HXY + 128;
+    const size_t vals = 4 * (size_t)zm_slot_stride(nprim, HXY, es) + NV * (NFX + NFY) + 2 * NV * TXY + 2 * AXY +
+                        2 * 2 * 3 * VXY;
+    return vals * es + 2 * HXY + 128;
 }
 
 // Eq. 2-2 stress and heat flux of the face between cell L = (plane cl, index
@@ -90,7 +96,8 @@ __device__ __forceinline__ void zm_visc_face(const DevParams& P, int HXY, int HX
 template <int NC, int NT, int MB, int LIM, int VISC, typename Q>
 __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
 {
-    using R = float;
+    // FP32 arithmetic on float-float registers, or FP64 throughout
+    using R = typename std::conditional<IsFF<Q>::value, float, double>::type;
     constexpr int ND = 3, NV = ND + NC + 1;
     constexpr int TX = ZM_TX, TY = ZM_TY;
     constexpr int HX = TX + 4, HY = TY + 4, HXY = HX * HY;
@@ -106,7 +113,7 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     R* const PR = reinterpret_cast<R*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    const int SS = zm_slot_stride(P.nprim, HXY);
+    const int SS = zm_slot_stride(P.nprim, HXY, int(sizeof(R)));
     R* const FX = PR + 4 * SS;                 // [NV][NFX] x-faces of the plane
     R* const FY = FX + NV * NFX;               // [NV][NFY] y-faces of the plane
     R* const FZ = FY + NV * NFY;               // [2][NV][TXY] z-faces, slot of the plane above the face

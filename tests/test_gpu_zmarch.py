@@ -75,3 +75,59 @@ def test_zmarch_mixed_accuracy_against_oracle(monkeypatch):
     ref, _ = oracle.Oracle(w).step(q, 2, w.cfl)
     e = rel_l1_vec(got, ref, w.ndim)
     assert np.all(e < 1e-4), e
+
+
+FP64_CASES = ["plain_2comp", "plain_3comp_bc", "other_limiters", "iles_csf_3comp"]
+
+
+@pytest.mark.parametrize("name", FP64_CASES)
+def test_zmarch_fp64_parity_with_oracle(name, monkeypatch):
+    """the z-marching kernel in the FP64 form (double plane ring, one block
+    per SM) against the FP64 oracle: three steps of 0.3 x the oracle's CFL
+    step, 1e-10 of each field's scale (momentum against the momentum
+    vector's)"""
+    from tests.helpers import oracle_step_dt
+    monkeypatch.setenv("FV_ZMARCH", "1")
+    w = CASES[name]()
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=fv.FV_FP64)
+    s.set_state(q)
+    dt = 0.3 * o.dt(q, 1.0)
+    ref = q
+    for _ in range(3):
+        s.step_dt(dt)
+        ref = oracle_step_dt(o, ref, dt)
+    assert s.tile()["zmarch"]
+    got = s.get_state()
+    d = rel_field_diff(got, ref)
+    mag = np.sqrt((ref[1:4] ** 2).sum(0)).max()
+    for a in range(3):
+        d[1 + a] = np.abs(got[1 + a] - ref[1 + a]).max() / mag
+    assert np.all(d < 1e-10), d
+
+
+def test_zmarch_fp64_jet_inflow_parity(monkeypatch):
+    """FP64 z-march on the jet with per-cell inflow velocities, App. D and
+    CSF, against the oracle (two steps)"""
+    from tests.helpers import oracle_step_dt
+    monkeypatch.setenv("FV_ZMARCH", "1")
+    w = wl.jet3d(n=(40, 24, 24))
+    w.inflow["radius"] = 5.5 * w.dx[1]
+    u = wl.jet_inflow_velocity(w)
+    o = oracle.Oracle(w, inflow_u=u)
+    q = o.prim_to_cons(w.primitives())
+    s = fv.Solver(w, precision=fv.FV_FP64, inflow_u=[u])
+    s.set_state(q)
+    dt = 0.3 * o.dt(q, 1.0)
+    ref = q
+    for _ in range(2):
+        s.step_dt(dt)
+        ref = oracle_step_dt(o, ref, dt)
+    assert s.tile()["zmarch"]
+    got = s.get_state()
+    d = rel_field_diff(got, ref)
+    mag = np.sqrt((ref[1:4] ** 2).sum(0)).max()
+    for a in range(3):
+        d[1 + a] = np.abs(got[1 + a] - ref[1 + a]).max() / mag
+    assert np.all(d < 1e-10), d
