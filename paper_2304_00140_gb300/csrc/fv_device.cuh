@@ -1123,7 +1123,9 @@ __device__ __forceinline__ bool face_flux(const DevParams& P, int d, const R (*w
     } else {
         ps = R(0.5) * (pL + pR);
         // impedances rho c: w^{-1/2} straight from the Wood sum (stiffened gas)
-        const R zL = CL == CL_SG ? rsq(sL.w) : rL * cL, zR = CL == CL_SG ? rsq(sR.w) : rR * cR;
+        R zL, zR;
+        if constexpr (CL == CL_SG) { zL = rsq(sL.w); zR = rsq(sR.w); }
+        else { zL = rL * cL; zR = rR * cR; }
         N = CJ ? zL * uL + zR * uR + pL - pR + capJ : zL * uL + zR * uR + pL - pR;
         D = zL + zR;
     }
