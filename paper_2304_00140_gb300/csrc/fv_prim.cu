@@ -293,22 +293,25 @@ template <bool FF>
 __global__ void all_cases_kernel(int nv, int ncases, const CaseDesc* cases, const double* host, void* reg,
                                  long long ntot_q, int to_reg)
 {
+    // field by field (no index division per element): the case's block of
+    // the host array is [nv][cells], the register field v starts at v ntot_q
     for (int c = blockIdx.y; c < ncases; c += gridDim.y) {
         const CaseDesc& C = cases[c];
         const long long nc = (long long)C.n[0] * C.n[1] * C.n[2];
         const long long base = nv * C.qoff;
-        for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv * nc;
-             e += (long long)gridDim.x * blockDim.x) {
-            const long long v = e / nc, i = e - v * nc;
-            const long long r = v * ntot_q + C.qoff + i;
-            if (FF) {
-                float2* q = static_cast<float2*>(reg);
-                if (to_reg) q[r] = ff_from_double(host[base + e]);
-                else const_cast<double*>(host)[base + e] = qv_d(q[r]);
-            } else {
-                double* q = static_cast<double*>(reg);
-                if (to_reg) q[r] = host[base + e];
-                else const_cast<double*>(host)[base + e] = q[r];
+        for (int v = 0; v < nv; ++v) {
+            const long long hb = base + v * nc, rb = v * ntot_q + C.qoff;
+            for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nc;
+                 i += (long long)gridDim.x * blockDim.x) {
+                if (FF) {
+                    float2* q = static_cast<float2*>(reg);
+                    if (to_reg) q[rb + i] = ff_from_double(host[hb + i]);
+                    else const_cast<double*>(host)[hb + i] = qv_d(q[rb + i]);
+                } else {
+                    double* q = static_cast<double*>(reg);
+                    if (to_reg) q[rb + i] = host[hb + i];
+                    else const_cast<double*>(host)[hb + i] = q[rb + i];
+                }
             }
         }
     }
@@ -317,7 +320,7 @@ __global__ void all_cases_kernel(int nv, int ncases, const CaseDesc* cases, cons
 cudaError_t launch_all_cases(int nv, int ncases, const CaseDesc* cases, long long max_cells, const double* host,
                              void* reg, long long ntot_q, int ff, int to_reg, cudaStream_t s)
 {
-    long long gx = (nv * max_cells + 255) / 256;
+    long long gx = (max_cells + 255) / 256;
     gx = gx > 64 ? 64 : (gx < 1 ? 1 : gx);
     const dim3 g((unsigned)gx, (unsigned)(ncases > 65535 ? 65535 : ncases));
     if (ff) all_cases_kernel<true><<<g, 256, 0, s>>>(nv, ncases, cases, host, reg, ntot_q, to_reg);
