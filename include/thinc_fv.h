@@ -258,7 +258,10 @@ fv_status fv_rk_stage(fv_ctx* ctx, int k, double dt);
  * closure a kernel that marches along z with TMA plane loads.
  * FV_TILE=<index> in the environment forces a tile of the tiled kernel,
  * FV_FUSED=0/1 and FV_ZMARCH=0/1 exclude or force the fused and the
- * z-marching kernel, FV_FUSED_CFL=0 (read when the context is created)
+ * z-marching kernel, FV_ZVAR=<v> keeps only the z-marching kernel's variant
+ * v (0/1/3/4/5: 320/256/352/416/288 threads with the Table 4.2 limiter
+ * pair; 2: run-time limiter pair; the viscous form has 1 and 2, the FP64
+ * form 1, 2, 4 and 5), FV_FUSED_CFL=0 (read when the context is created)
  * keeps the CFL pass in every step of the fused kernel (see fv_step).  Set
  * the state first. */
 

@@ -652,7 +652,7 @@ static fv_status apply_zmarch(fv_ctx* x, int chunk, int var)
 {
     const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
     if (!t42) var = 2;
-    else if (zm_visc(x) || !x->mixed) var = 1;
+    else if (zm_visc(x) || (!x->mixed && var != 4 && var != 5)) var = 1;
     const cuuint32_t box[4] = {cuuint32_t(ZM_TX + 4), cuuint32_t(ZM_TY + 4), 1, cuuint32_t(x->nprim)};
     if (!encode_maps(x, box, ZM_TX, x->d_tmaps_z)) return fail(x, FV_ERR_ARG, "z-marching kernel needs TMA%s");
     std::vector<int4> it;
@@ -805,9 +805,12 @@ static fv_status tune(fv_ctx* x)
     int want_zm = -1;      // FV_ZMARCH=0/1 excludes or forces the z-marching kernel
     if (const char* f = getenv("FV_ZMARCH")) want_zm = atoi(f) ? 1 : 0;
     if (!x->zm_ok) want_zm = 0;
+    int want_zvar = -1;    // FV_ZVAR=<v> keeps only the z-marching kernel's variant v
+    if (const char* f = getenv("FV_ZVAR")) want_zvar = atoi(f);
     const bool tiles = tunable(x->P);
     if (!tiles && want_fused == 0 && want_zm == 0) return apply_tile(x, 0);   // a single candidate
-    const std::string key = tune_key(x) + "/" + std::to_string(want_fused) + "/" + std::to_string(want_zm);
+    const std::string key = tune_key(x) + "/" + std::to_string(want_fused) + "/" + std::to_string(want_zm) + "/" +
+                            std::to_string(want_zvar);
     auto apply = [&](int code) {
         if (code >= 200) return apply_zmarch(x, ZM_CHUNKS[(code - 200) / 10], (code - 200) % 10);
         return code < 100 ? apply_tile(x, code) : apply_march(x, MARCH_CHUNKS[(code - 100) / 10], (code - 100) % 10);
@@ -899,12 +902,15 @@ static fv_status tune(fv_ctx* x)
         // after the primitive pass above, like the tiled kernel
         const bool t42 = x->P.lim_vel == FV_KOREN && x->P.lim_scalar == FV_MINMOD;
         float zbest = 1e30f;
-        // the viscous and FP64 instantiations: variant 1 (Table 4.2 pair) or 2 (run-time pair)
-        const int zvars_t42[3] = {0, 1, 3}, zvars_rt[1] = {2}, zvars_visc[1] = {1};
-        const bool few = zm_visc(x) || !x->mixed;
+        // the viscous instantiations: variant 1 (Table 4.2 pair) or 2 (run-time
+        // pair); the FP64 ones 1, 4 or 5 (Table 4.2 pair), 2 (run-time pair)
+        const int zvars_t42[5] = {0, 1, 3, 4, 5}, zvars_rt[1] = {2}, zvars_visc[1] = {1}, zvars_fp64[3] = {1, 4, 5};
+        const int* const zv = !t42 ? zvars_rt : (zm_visc(x) ? zvars_visc : (x->mixed ? zvars_t42 : zvars_fp64));
+        const int nzv = !t42 || zm_visc(x) ? 1 : (x->mixed ? 5 : 3);
         for (int ci = 0; ci < 3; ++ci)
-            for (int vi = 0; vi < (t42 && !few ? 3 : 1); ++vi) {
-                const int var = !t42 ? zvars_rt[vi] : (few ? zvars_visc[vi] : zvars_t42[vi]);
+            for (int vi = 0; vi < nzv; ++vi) {
+                const int var = zv[vi];
+                if (want_zvar >= 0 && var != want_zvar) continue;
                 if (apply_zmarch(x, ZM_CHUNKS[ci], var)) { x->msg.clear(); continue; }
                 ZArgs za{x->P, x->d_cases, x->d_items_z, x->n_items_z, x->zchunk, x->d_tmaps_z, x->Q0, x->QB,
                          x->dt, 0.0, x->err};

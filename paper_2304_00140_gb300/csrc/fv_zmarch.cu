@@ -1,11 +1,13 @@
 // fv_zmarch.cu -- instantiations and launchers of the z-marching 3D stage
 // kernel (fv_zmarch.cuh): FP32-mixed form (and the FP64 form's variants 1
 // and 2, one block per SM), 2 or 3 components.
-// Variants: 0 / 1 / 3 Table 4.2 limiter pair with 320 / 256 / 352 threads
-// (352 covers a plane's 18 x 18 sensor and smoothing cells in one round);
-// 2 a limiter pair read at run time, 320 threads.  Two resident
-// blocks per SM (the plane ring takes about 100 KB of shared memory).  With
-// the viscous and gravity terms (visc = 1) variants 1 and 2 only.
+// Variants: 0 / 1 / 3 / 4 / 5 Table 4.2 limiter pair with 320 / 256 / 352 /
+// 416 / 288 threads (352 covers a plane's 18 x 18 sensor and smoothing cells
+// in one round; a plane's 26 face tasks take 13 warps two rounds each, 9
+// warps three); 2 a limiter pair read at run time, 320 threads.  Two
+// resident blocks per SM (the plane ring takes about 100 KB of shared
+// memory).  With the viscous and gravity terms (visc = 1) variants 1 and 2
+// only; FP64 variants 1, 2, 4 and 5.
 #include <type_traits>
 
 #include "fv_launch.h"
@@ -14,7 +16,7 @@
 namespace tfv {
 
 namespace {
-template <int V> constexpr int nt_of() { return V == 1 ? 256 : (V == 3 ? 352 : 320); }
+template <int V> constexpr int nt_of() { return V == 1 ? 256 : (V == 3 ? 352 : (V == 4 ? 416 : (V == 5 ? 288 : 320))); }
 template <int V> constexpr int lim_of() { return V == 2 ? LIM_RUNTIME : LIM_TABLE42; }
 // D = 1: the FP64 form (double registers and plane ring, one resident block per SM)
 #define FV_ZK(NC, V, VI, D)                                                                               \
@@ -43,13 +45,15 @@ int occ(size_t smem)
 }  // namespace
 
 // FV_ZBAD: the value for a variant without an instantiation (viscous: 1 and
-// 2; FP64: 1 and 2 without the viscous terms)
+// 2; FP64: 1, 2, 4 and 5 without the viscous terms)
 #define FV_ZSWITCH(fn, ...)                                                                        \
     if (fp64) {                                                                                    \
         if (visc) return FV_ZBAD;                                                                  \
         switch (var) {                                                                             \
         case 1: return nc == 2 ? fn<2, 1, 0, 1>(__VA_ARGS__) : fn<3, 1, 0, 1>(__VA_ARGS__);         \
         case 2: return nc == 2 ? fn<2, 2, 0, 1>(__VA_ARGS__) : fn<3, 2, 0, 1>(__VA_ARGS__);         \
+        case 4: return nc == 2 ? fn<2, 4, 0, 1>(__VA_ARGS__) : fn<3, 4, 0, 1>(__VA_ARGS__);         \
+        case 5: return nc == 2 ? fn<2, 5, 0, 1>(__VA_ARGS__) : fn<3, 5, 0, 1>(__VA_ARGS__);         \
         default: return FV_ZBAD;                                                                   \
         }                                                                                          \
     }                                                                                              \
@@ -64,6 +68,8 @@ int occ(size_t smem)
     case 1: return nc == 2 ? fn<2, 1, 0, 0>(__VA_ARGS__) : fn<3, 1, 0, 0>(__VA_ARGS__);             \
     case 2: return nc == 2 ? fn<2, 2, 0, 0>(__VA_ARGS__) : fn<3, 2, 0, 0>(__VA_ARGS__);             \
     case 3: return nc == 2 ? fn<2, 3, 0, 0>(__VA_ARGS__) : fn<3, 3, 0, 0>(__VA_ARGS__);             \
+    case 4: return nc == 2 ? fn<2, 4, 0, 0>(__VA_ARGS__) : fn<3, 4, 0, 0>(__VA_ARGS__);             \
+    case 5: return nc == 2 ? fn<2, 5, 0, 0>(__VA_ARGS__) : fn<3, 5, 0, 0>(__VA_ARGS__);             \
     default: return nc == 2 ? fn<2, 0, 0, 0>(__VA_ARGS__) : fn<3, 0, 0, 0>(__VA_ARGS__);            \
     }
 
@@ -85,7 +91,7 @@ int zmarch_occupancy(int nc, int var, int visc, int fp64, size_t smem)
     FV_ZSWITCH(occ, smem)
 #undef FV_ZBAD
 }
-int zmarch_threads(int var) { return var == 1 ? 256 : (var == 3 ? 352 : 320); }
+int zmarch_threads(int var) { return var == 1 ? 256 : (var == 3 ? 352 : (var == 4 ? 416 : (var == 5 ? 288 : 320))); }
 size_t zmarch_smem(int nc, int nprim, int fp64)
 {
     const int es = fp64 ? 8 : 4;

@@ -104,7 +104,10 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
     constexpr int AX = TX + 2, AY = TY + 2, AXY = AX * AY;
     constexpr int VX = TX + 1, VY = TY + 1, VXY = VX * VY;
     constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), TXY = TX * TY;
-    constexpr int NFACE = NFX + NFY + TXY;
+    // face tasks: 32 faces of one direction each (x, y, then z)
+    constexpr int TKX = (NFX + 31) / 32, TKY = (NFY + 31) / 32, NTASK = TKX + TKY + TXY / 32;
+    static_assert(TXY % 32 == 0 && NT % 32 == 0, "whole warps");
+    static_assert(NT >= TXY, "one thread per cell of the column in the update");
     const DevParams& P = A.P;
     const ConstT<R>& Kc = K<R>(P);
     const Q* const q0reg = static_cast<const Q*>(A.q0);
@@ -170,12 +173,13 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
         };
 
         // App. D sensor of plane p on the tile + 1 halo in x and y (planes p-1 .. p+1 present)
-        auto sensor_plane = [&](int p) {
+        // (i0: this thread's first cell, a permutation of the thread indices)
+        auto sensor_plane = [&](int p, int i0) {
             const R* const sp = plane(p);
             const R* const sm = plane(p - 1);
             const R* const su = plane(p + 1);
             unsigned char* const fl = FLAG + slot2(p) * HXY;
-            for (int i = tid; i < AXY; i += NT) {
+            for (int i = i0; i < AXY; i += NT) {
                 const int hx = i % AX + 1, hy = i / AX + 1;
                 if (hx > vx + 2 || hy > vy + 2) continue;
                 const int h = hy * HX + hx;
@@ -209,9 +213,9 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
             }
         };
         // CSF smoothed fraction (Eq. 3-9) of plane p on the tile + 1 halo in x and y
-        auto smooth_plane = [&](int p) {
+        auto smooth_plane = [&](int p, int i0) {
             R* const at = AT + slot2(p) * AXY;
-            for (int i = tid; i < AXY; i += NT) {
+            for (int i = i0; i < AXY; i += NT) {
                 const int ax = i % AX, ay = i / AX;
                 const int hc = (ay + 1) * HX + ax + 1;
                 R s = R(0), W1 = R(0);
@@ -321,21 +325,24 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
         bool ok = true;
         for (int p = z0 - 2; p <= z0 + 1; ++p) ok = wait(p) && ok;
         if (!ok) { timeout(); return; }
-        if (P.iles) { sensor_plane(z0 - 1); sensor_plane(z0); }
-        if (P.csf) { smooth_plane(z0 - 1); smooth_plane(z0); }
+        if (P.iles) { sensor_plane(z0 - 1, tid); sensor_plane(z0, tid); }
+        if (P.csf) { smooth_plane(z0 - 1, tid); smooth_plane(z0, tid); }
         __syncthreads();
         if (P.csf) normals(z0 - 1);
         for (int f = tid; f < TXY; f += NT) zfaces(z0 - 1, f);
         __syncthreads();
         issue(z0 + 2);   // into the slot of plane z0-2, read for the last time above
         if (!wait(z0 + 2)) { timeout(); return; }
-        if (P.iles) sensor_plane(z0 + 1);
-        if (P.csf) smooth_plane(z0 + 1);
+        if (P.iles) sensor_plane(z0 + 1, tid);
+        if (P.csf) smooth_plane(z0 + 1, tid);
         __syncthreads();
 
         const double adt = A.a * A.dt[wi.x];
         const float adtf = float(adt);
         const int cx = tid % TX, cy = tid / TX;
+        // the threads without a cell to update take the first sensor and
+        // smoothing cells of the next plane
+        const int rot = tid >= TXY ? tid - TXY : tid + (NT - TXY);
         for (int z = z0; z < z1; ++z) {
             const bool own = tid < TXY && cx < vx && cy < vy;
             const long long gcell = C.qoff + (((long long)z * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx));
@@ -350,12 +357,18 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
             // normals between z and z+1; x- and y-faces of plane z; z-faces between z and z+1
             if (P.csf) normals(z);
             {
+                // faces in warp tasks of 32 faces of one direction (no warp
+                // runs two directions' code one after the other); the last
+                // warps take the extra tasks, the first ones any extra vertex
+                // normals above
                 const R* const pz = plane(z);
                 const unsigned char* const flz = FLAG + slot2(z) * HXY;
-                for (int f = tid; f < NFACE; f += NT) {
-                    if (f < NFX) {
+                const int lane = tid & 31;
+                for (int t = NT / 32 - 1 - (tid >> 5); t < NTASK; t += NT / 32) {
+                    if (t < TKX) {
+                        const int f = t * 32 + lane;
                         const int fx = f % (TX + 1), fy = f / (TX + 1);
-                        if (fx > vx || fy >= vy) continue;
+                        if (f >= NFX || fx > vx || fy >= vy) continue;
                         const int h0 = (fy + 2) * HX + fx;
                         const R* const pl[4] = {pz, pz, pz, pz};
                         const int hh[4] = {h0, h0 + 1, h0 + 2, h0 + 3};
@@ -366,10 +379,10 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                                                plane(z - 1), plane(z + 1), ci, F);
 #pragma unroll
                         for (int v = 0; v < NV; ++v) FX[v * NFX + f] = F[v];
-                    } else if (f < NFX + NFY) {
-                        const int fi = f - NFX;
+                    } else if (t < TKX + TKY) {
+                        const int fi = (t - TKX) * 32 + lane;
                         const int fx = fi % TX, fy = fi / TX;
-                        if (fx >= vx || fy > vy) continue;
+                        if (fi >= NFY || fx >= vx || fy > vy) continue;
                         const int h0 = fy * HX + fx + 2;
                         const R* const pl[4] = {pz, pz, pz, pz};
                         const int hh[4] = {h0, h0 + HX, h0 + 2 * HX, h0 + 3 * HX};
@@ -381,7 +394,7 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
 #pragma unroll
                         for (int v = 0; v < NV; ++v) FY[v * NFY + fi] = F[v];
                     } else {
-                        zfaces(z, f - NFX - NFY);
+                        zfaces(z, (t - TKX - TKY) * 32 + lane);
                     }
                 }
             }
@@ -458,8 +471,8 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                 ok_next = tma_wait(mb(sl), (phase >> sl) & 1u);
                 phase ^= 1u << sl;
                 if (ok_next) {
-                    if (P.iles) sensor_plane(z + 2);
-                    if (P.csf) smooth_plane(z + 2);
+                    if (P.iles) sensor_plane(z + 2, rot);
+                    if (P.csf) smooth_plane(z + 2, rot);
                 }
             }
             if (__syncthreads_or(!ok_next)) { timeout(); return; }

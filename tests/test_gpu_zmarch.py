@@ -13,14 +13,25 @@ from tests.helpers import rel_field_diff, rel_l1_vec
 pytestmark = pytest.mark.gpu
 
 
-def _run(w, kernel, monkeypatch, steps=2, inflow_u=None):
+def _run(w, kernel, monkeypatch, steps=2, inflow_u=None, zvar=None):
     monkeypatch.setenv("FV_ZMARCH", "1" if kernel == "zmarch" else "0")
+    if zvar is None:
+        monkeypatch.delenv("FV_ZVAR", raising=False)
+    else:
+        monkeypatch.setenv("FV_ZVAR", str(zvar))
     s = fv.Solver(w, precision=fv.FV_MIXED, inflow_u=[inflow_u] if inflow_u is not None else None)
     q = oracle.Oracle(w, inflow_u=inflow_u).prim_to_cons(w.primitives())
     s.set_state(q)
     s.step(steps, w.cfl)
-    assert s.tile()["zmarch"] == (kernel == "zmarch")
+    t = s.tile()
+    assert t["zmarch"] == (kernel == "zmarch")
+    if zvar is not None:
+        assert t["fused_variant"] == zvar and t["threads"] == ZVAR_THREADS[zvar]
     return q, s.get_state()
+
+
+# the z-marching kernel's variants with the Table 4.2 limiter pair and their block sizes
+ZVAR_THREADS = {0: 320, 1: 256, 3: 352, 4: 416, 5: 288}
 
 
 CASES = {
@@ -57,6 +68,18 @@ def test_zmarch_matches_tiled_kernel(name, monkeypatch):
     assert np.all(d < 1e-6), d
 
 
+@pytest.mark.parametrize("zvar", sorted(ZVAR_THREADS))
+@pytest.mark.parametrize("name", ["plain_3comp_bc", "iles_csf_3comp"])
+def test_zmarch_variants_match_tiled_kernel(name, zvar, monkeypatch):
+    """every block size of the z-marching kernel (its face tasks and sensor
+    cells spread over 8 to 13 warps) against the tiled kernel"""
+    w = CASES[name]()
+    _, a = _run(w, "zmarch", monkeypatch, zvar=zvar)
+    _, b = _run(w, "tiled", monkeypatch)
+    d = rel_field_diff(a, b)
+    assert np.all(d < 1e-6), d
+
+
 def test_zmarch_jet_inflow_matches_tiled_kernel(monkeypatch):
     w = wl.jet3d(n=(40, 24, 24))
     w.inflow["radius"] = 5.5 * w.dx[1]
@@ -80,14 +103,21 @@ def test_zmarch_mixed_accuracy_against_oracle(monkeypatch):
 FP64_CASES = ["plain_2comp", "plain_3comp_bc", "other_limiters", "iles_csf_3comp"]
 
 
+@pytest.mark.parametrize("zvar", [None, 1, 4, 5])
 @pytest.mark.parametrize("name", FP64_CASES)
-def test_zmarch_fp64_parity_with_oracle(name, monkeypatch):
+def test_zmarch_fp64_parity_with_oracle(name, zvar, monkeypatch):
     """the z-marching kernel in the FP64 form (double plane ring, one block
-    per SM) against the FP64 oracle: three steps of 0.3 x the oracle's CFL
-    step, 1e-10 of each field's scale (momentum against the momentum
-    vector's)"""
+    per SM; the tuner's variant, or 256 / 416 / 288 threads) against the FP64
+    oracle: three steps of 0.3 x the oracle's CFL step, 1e-10 of each
+    field's scale (momentum against the momentum vector's)"""
     from tests.helpers import oracle_step_dt
+    if zvar is not None and name == "other_limiters":
+        pytest.skip("the run-time limiter pair has one FP64 variant (2)")
     monkeypatch.setenv("FV_ZMARCH", "1")
+    if zvar is None:
+        monkeypatch.delenv("FV_ZVAR", raising=False)
+    else:
+        monkeypatch.setenv("FV_ZVAR", str(zvar))
     w = CASES[name]()
     o = oracle.Oracle(w)
     q = o.prim_to_cons(w.primitives())
@@ -99,6 +129,8 @@ def test_zmarch_fp64_parity_with_oracle(name, monkeypatch):
         s.step_dt(dt)
         ref = oracle_step_dt(o, ref, dt)
     assert s.tile()["zmarch"]
+    if zvar is not None:
+        assert s.tile()["fused_variant"] == zvar and s.tile()["threads"] == ZVAR_THREADS[zvar]
     got = s.get_state()
     d = rel_field_diff(got, ref)
     mag = np.sqrt((ref[1:4] ** 2).sum(0)).max()
