@@ -281,43 +281,68 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                 for (int d = 0; d < 3; ++d) nr[d * VXY + i] = g[d] * inv;
             }
         };
-        // one face: stencil of four cells, sensor flags and impedance inputs of the middle two
-        auto face = [&](int d, const R* const* pl, const int* hh, const unsigned char* f1, const unsigned char* f2,
-                        R* F) {
+        // face f (0-based within its direction) of direction d (x- and y-faces
+        // of plane p, or the z-face between planes p and p+1, stored in the slot
+        // of p+1): the four stencil cells as offsets into the plane ring, the
+        // sensor flags and impedance inputs of the middle two; one code path
+        // for the three directions
+        auto face_task = [&](int d, int f, int p) {
+            int fx, fy, h0, sh;
+            if (d == 0) {
+                fx = f % (TX + 1); fy = f / (TX + 1);
+                if (f >= NFX || fx > vx || fy >= vy) return;
+                h0 = (fy + 2) * HX + fx; sh = 1;
+            } else if (d == 1) {
+                fx = f % TX; fy = f / TX;
+                if (f >= NFY || fx >= vx || fy > vy) return;
+                h0 = fy * HX + fx + 2; sh = HX;
+            } else {
+                fx = f % TX; fy = f / TX;
+                if (fx >= vx || fy >= vy) return;
+                h0 = (fy + 2) * HX + fx + 2; sh = 0;
+            }
+            int off[4];
+#pragma unroll
+            for (int st = 0; st < 4; ++st) off[st] = slot4(d == 2 ? p - 1 + st : p) * SS + h0 + st * sh;
             R ws[4][NV];
             R r4[4], c4[4];
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
+            for (int st = 0; st < 4; ++st)
 #pragma unroll
-                for (int v = 0; v < NV; ++v) ws[s][v] = pl[s][v * HXY + hh[s]];
+                for (int v = 0; v < NV; ++v) ws[st][v] = PR[off[st] + v * HXY];
             int fl = 1;
             if (P.iles) {
 #pragma unroll
-                for (int s = 1; s <= 2; ++s) {
-                    r4[s] = pl[s][P.i_rho * HXY + hh[s]];
-                    c4[s] = pl[s][P.i_c * HXY + hh[s]];
+                for (int st = 1; st <= 2; ++st) {
+                    r4[st] = PR[off[st] + P.i_rho * HXY];
+                    c4[st] = PR[off[st] + P.i_c * HXY];
                 }
-                fl = (f1[hh[1]] | f2[hh[2]]) ? 1 : 0;
+                const int h1 = h0 + sh, h2 = h0 + 2 * sh;
+                fl = (FLAG[slot2(p) * HXY + h1] | FLAG[slot2(d == 2 ? p + 1 : p) * HXY + h2]) ? 1 : 0;
             }
-            if (!face_flux<ND, NC, R, false, LIM>(P, d, ws, r4, c4, fl, F)) set_err(A.err, ERR_NONPHYS);
-        };
-        // z-faces between planes p and p+1 (stored in the slot of p+1)
-        auto zfaces = [&](int p, int f) {
-            const int fx = f % TX, fy = f / TX;
-            if (fx >= vx || fy >= vy) return;
-            const int h = (fy + 2) * HX + fx + 2;
-            const R* const pl[4] = {plane(p - 1), plane(p), plane(p + 1), plane(p + 2)};
-            const int hh[4] = {h, h, h, h};
             R F[NV];
-            face(2, pl, hh, FLAG + slot2(p) * HXY, FLAG + slot2(p + 1) * HXY, F);
-            if (VISC && P.visc) zm_visc_face<2, R>(P, HXY, HX, pl[1], h, pl[2], h, nullptr, nullptr, nullptr, nullptr, ci, F);
-            R* const dst = FZ + slot2(p + 1) * NV * TXY;
+            if (!face_flux<ND, NC, R, false, LIM>(P, d, ws, r4, c4, fl, F)) set_err(A.err, ERR_NONPHYS);
+            if (VISC && P.visc) {
+                const R* const pz = plane(p);
+                const int h1 = h0 + sh, h2 = h0 + 2 * sh;
+                if (d == 0)
+                    zm_visc_face<0, R>(P, HXY, HX, pz, h1, pz, h2, plane(p - 1), plane(p + 1), plane(p - 1),
+                                       plane(p + 1), ci, F);
+                else if (d == 1)
+                    zm_visc_face<1, R>(P, HXY, HX, pz, h1, pz, h2, plane(p - 1), plane(p + 1), plane(p - 1),
+                                       plane(p + 1), ci, F);
+                else
+                    zm_visc_face<2, R>(P, HXY, HX, pz, h1, plane(p + 1), h1, nullptr, nullptr, nullptr, nullptr, ci, F);
+            }
+            R* const dst = d == 0 ? FX + f : (d == 1 ? FY + f : FZ + slot2(p + 1) * NV * TXY + f);
+            const int ds = d == 0 ? NFX : (d == 1 ? NFY : TXY);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) dst[v * TXY + f] = F[v];
+            for (int v = 0; v < NV; ++v) dst[v * ds] = F[v];
         };
 
         // ---- prologue: planes z0-2 .. z0+1, sensor and smoothed fractions of
-        // planes z0-1 and z0, normals and z-faces between them
+        // planes z0-1 and z0; the loop's first pass (z = z0-1) computes the
+        // normals and z-faces between them and nothing else of plane z0-1
         issue(z0 - 2);
         issue(z0 - 1);
         issue(z0);
@@ -328,24 +353,24 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
         if (P.iles) { sensor_plane(z0 - 1, tid); sensor_plane(z0, tid); }
         if (P.csf) { smooth_plane(z0 - 1, tid); smooth_plane(z0, tid); }
         __syncthreads();
-        if (P.csf) normals(z0 - 1);
-        for (int f = tid; f < TXY; f += NT) zfaces(z0 - 1, f);
-        __syncthreads();
-        issue(z0 + 2);   // into the slot of plane z0-2, read for the last time above
-        if (!wait(z0 + 2)) { timeout(); return; }
-        if (P.iles) sensor_plane(z0 + 1, tid);
-        if (P.csf) smooth_plane(z0 + 1, tid);
-        __syncthreads();
 
         const double adt = A.a * A.dt[wi.x];
         const float adtf = float(adt);
         const int cx = tid % TX, cy = tid / TX;
+        // the case's fields in registers (the loop stores to q^k, which the
+        // compiler cannot tell apart from the case table)
+        const long long qoff = C.qoff;
+        const int n0 = C.n[0], n1 = C.n[1];
         // the threads without a cell to update take the first sensor and
-        // smoothing cells of the next plane
+        // smoothing cells of the next plane; the sensor's and the smoothing's
+        // cells beyond the first round go to different threads
         const int rot = tid >= TXY ? tid - TXY : tid + (NT - TXY);
-        for (int z = z0; z < z1; ++z) {
-            const bool own = tid < TXY && cx < vx && cy < vy;
-            const long long gcell = C.qoff + (((long long)z * C.n[1] + (y0 + cy)) * C.n[0] + (x0 + cx));
+        constexpr int XTRA = AXY > NT ? AXY - NT : 0;
+        const int rot_s = rot >= XTRA ? rot - XTRA : rot + (NT - XTRA);
+        for (int z = z0 - 1; z < z1; ++z) {
+            const bool upd = z >= z0;
+            const bool own = upd && tid < TXY && cx < vx && cy < vy;
+            const long long gcell = qoff + (((long long)(upd ? z : z0) * n1 + (y0 + cy)) * n0 + (x0 + cx));
             Q q0r[NV];
             {
                 const Q* qp = q0reg + gcell;
@@ -361,40 +386,20 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                 // runs two directions' code one after the other); the last
                 // warps take the extra tasks, the first ones any extra vertex
                 // normals above
-                const R* const pz = plane(z);
-                const unsigned char* const flz = FLAG + slot2(z) * HXY;
                 const int lane = tid & 31;
                 for (int t = NT / 32 - 1 - (tid >> 5); t < NTASK; t += NT / 32) {
-                    if (t < TKX) {
-                        const int f = t * 32 + lane;
-                        const int fx = f % (TX + 1), fy = f / (TX + 1);
-                        if (f >= NFX || fx > vx || fy >= vy) continue;
-                        const int h0 = (fy + 2) * HX + fx;
-                        const R* const pl[4] = {pz, pz, pz, pz};
-                        const int hh[4] = {h0, h0 + 1, h0 + 2, h0 + 3};
-                        R F[NV];
-                        face(0, pl, hh, flz, flz, F);
-                        if (VISC && P.visc)
-                            zm_visc_face<0, R>(P, HXY, HX, pz, hh[1], pz, hh[2], plane(z - 1), plane(z + 1),
-                                               plane(z - 1), plane(z + 1), ci, F);
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) FX[v * NFX + f] = F[v];
-                    } else if (t < TKX + TKY) {
-                        const int fi = (t - TKX) * 32 + lane;
-                        const int fx = fi % TX, fy = fi / TX;
-                        if (fi >= NFY || fx >= vx || fy > vy) continue;
-                        const int h0 = fy * HX + fx + 2;
-                        const R* const pl[4] = {pz, pz, pz, pz};
-                        const int hh[4] = {h0, h0 + HX, h0 + 2 * HX, h0 + 3 * HX};
-                        R F[NV];
-                        face(1, pl, hh, flz, flz, F);
-                        if (VISC && P.visc)
-                            zm_visc_face<1, R>(P, HXY, HX, pz, hh[1], pz, hh[2], plane(z - 1), plane(z + 1),
-                                               plane(z - 1), plane(z + 1), ci, F);
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) FY[v * NFY + fi] = F[v];
+                    const int d = t < TKX ? 0 : (t < TKX + TKY ? 1 : 2);
+                    const int f = (t - (d == 0 ? 0 : (d == 1 ? TKX : TKX + TKY))) * 32 + lane;
+                    if (!upd && d != 2) continue;
+                    if constexpr (sizeof(R) == 8) {
+                        // FP64: one copy of the face code (the direction's
+                        // selects are integer work beside the FP64 pipe)
+                        face_task(d, f, z);
                     } else {
-                        zfaces(z, (t - TKX - TKY) * 32 + lane);
+                        // FP32: the direction at compile time in each copy
+                        if (d == 0) face_task(0, f, z);
+                        else if (d == 1) face_task(1, f, z);
+                        else face_task(2, f, z);
                     }
                 }
             }
@@ -472,7 +477,7 @@ __global__ void __launch_bounds__(NT, MB) zmarch_kernel(ZArgs A)
                 phase ^= 1u << sl;
                 if (ok_next) {
                     if (P.iles) sensor_plane(z + 2, rot);
-                    if (P.csf) smooth_plane(z + 2, rot);
+                    if (P.csf) smooth_plane(z + 2, rot_s);
                 }
             }
             if (__syncthreads_or(!ok_next)) { timeout(); return; }
