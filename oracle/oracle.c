@@ -16,12 +16,15 @@
  * (equivalent mirror/extended problems, closed-box conservation), CSF and
  * the capillary jump (Laplace jump, Eq. 4-3 period, face balance), the
  * height function, the viscous terms (second-order convergence), the
- * barotropic closure and the App. D smooth branch (linear stability).
- * Parity unpinned -- readings that no paper number fixes, which the CUDA
- * path shares: the acoustic CFL step definition, the THINC eligibility
- * epsilon = 1e-4, the value 1/2 of the Delta^3 p scale (its effect is pinned
- * by linear theory, not its value), and the Peng-Robinson combining rule
- * with Z_c = 0.3074.
+ * barotropic closure and the App. D smooth branch (linear stability), the
+ * step limit (closed-form steps of pure-phase cells, acoustic and
+ * diffusive), the THINC eligibility test (both thresholds, both face
+ * sides' stencils) and the Peng-Robinson mixing rule (the mixture's second
+ * virial coefficient: quadratic in the mole fractions, textbook pure ends).
+ * Readings whose VALUE no paper number fixes, which the CUDA path shares:
+ * the step definition itself, the THINC eligibility epsilon = 1e-4, the
+ * Delta^3 p scale 1/2 and Z_c = 0.3074 in the combining rule; the functions
+ * that use them are pinned as listed above.
  */
 #include "oracle.h"
 #ifdef _OPENMP
