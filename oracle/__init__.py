@@ -88,6 +88,8 @@ def lib():
             L.or_face_flux_av.argtypes = [P, C.c_int, dp, dp, dp, dp, C.c_int, dp]
             L.or_pr_state.argtypes = [P, C.c_double, C.c_double, dp, dp]
             L.or_set_threads.argtypes = [C.c_int]
+            L.or_smoothed_fraction.argtypes = [P, dp, dp]
+            L.or_baro_sound_rho.argtypes = [P, C.c_double, C.c_double, dp, dp]
             L.or_capillary_force.argtypes = [P, dp, dp]
             L.or_face_flux_kappa.argtypes = [P, C.c_int, dp, dp, dp, C.c_int, C.c_double, C.c_double, dp, dp, dp]
             _lib = L
@@ -219,6 +221,20 @@ class Oracle:
         k = np.zeros(self.shape[1:])
         _check(self.L.or_curvature(C.byref(self.P), _ptr(q), _ptr(k)), "curvature")
         return k
+
+    def smoothed_fraction(self, q):
+        """Gaussian-smoothed liquid fraction per interior cell [nz, ny, nx] (Eq. 3-9)"""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        a = np.zeros(self.shape[1:])
+        _check(self.L.or_smoothed_fraction(C.byref(self.P), _ptr(q), _ptr(a)), "smoothed_fraction")
+        return a
+
+    def baro_sound_rho(self, p, rho, Yt):
+        """sound speed of a barotropic face state (p, rho, xi)"""
+        Y = np.ascontiguousarray(Yt, dtype=np.float64)
+        c = C.c_double()
+        _check(self.L.or_baro_sound_rho(C.byref(self.P), p, rho, _ptr(Y), C.byref(c)), "baro_sound_rho")
+        return c.value
 
     def sensor_args(self, q):
         """App. D switch arguments per interior cell (Eq. D.4):

@@ -19,8 +19,14 @@
  * barotropic closure and the App. D smooth branch (linear stability), the
  * step limit (closed-form steps of pure-phase cells, acoustic and
  * diffusive), the THINC eligibility test (both thresholds, both face
- * sides' stencils) and the Peng-Robinson mixing rule (the mixture's second
- * virial coefficient: quadratic in the mole fractions, textbook pure ends).
+ * sides' stencils), the Peng-Robinson mixing rule (the mixture's second
+ * virial coefficient: quadratic in the mole fractions, textbook pure ends)
+ * and root choice (lowest Gibbs energy against numpy's roots), the contact
+ * velocity of Eq. 3-2 (the exact Riemann solution at small amplitude),
+ * Table 4.2's limiter per variable, the App. D face values, sensor
+ * arguments (exact linear fields) and face switch (a stage assembled from
+ * the face fluxes), the smoothing kernel's moments, the capillary jump's
+ * pressure work and the clipping of mass fractions.
  * Readings whose VALUE no paper number fixes, which the CUDA path shares:
  * the step definition itself, the THINC eligibility epsilon = 1e-4, the
  * Delta^3 p scale 1/2 and Z_c = 0.3074 in the combining rule; the functions
@@ -1615,6 +1621,37 @@ int or_curvature(const or_params* P, const double* q, double* kappa)
                 }
     box_free(&B);
     return st;
+}
+
+/* the Gaussian-smoothed liquid fraction alpha~ of every interior cell
+ * (Eq. 3-9, the field the CSF normals come from) */
+int or_smoothed_fraction(const or_params* P, const double* q, double* out)
+{
+    const int nd = P->ndim;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+        blo[d] = d < nd ? -2 : 0;
+        bhi[d] = d < nd ? P->n[d] + 2 : 1;
+    }
+    box_t B;
+    memset(&B, 0, sizeof(B));
+    int st = box_fill(P, q, &B, blo, bhi);
+    if (!st)
+        for (int k = 0; k < P->n[2]; ++k)
+            for (int j = 0; j < P->n[1]; ++j)
+                for (int i = 0; i < P->n[0]; ++i) out[cidx(P, i, j, k)] = smooth_at(P, &B, i, j, k);
+    box_free(&B);
+    return st;
+}
+
+/* sound speed of a barotropic face state (p, rho, xi) whose density came
+ * from the liquid-vapour THINC (Sec. 3.4 Remark 2) */
+int or_baro_sound_rho(const or_params* P, double p, double rho, const double* Yt, double* c)
+{
+    double Y[OR_MAXC];
+    full_Y(P, Yt, Y);
+    if (!all_kind(P, OR_BARO)) return OR_ERR_ARG;
+    return bar_sound_rho(P, p, rho, Y, c) ? OR_OK : OR_ERR_NONPHYS;
 }
 
 /* App. D switch arguments of every interior cell (Eq. D.4):

@@ -120,6 +120,10 @@ void or_totals(const or_params* P, const double* q, double* out /* nv */);
 int or_curvature(const or_params* P, const double* q, double* kappa);
 int or_csf_source(const or_params* P, const double* q, double* S);
 /* App. D cell sensor f (0/1) on the interior */
+/* Gaussian-smoothed liquid fraction of every interior cell (Eq. 3-9) */
+int or_smoothed_fraction(const or_params* P, const double* q, double* out);
+/* sound speed of a barotropic face state (p, rho, xi) (Sec. 3.4 Remark 2) */
+int or_baro_sound_rho(const or_params* P, double p, double rho, const double* Yt, double* c);
 int or_sensor(const or_params* P, const double* q, double* f);
 /* App. D switch arguments on the interior: out[5][cells] = theta^D,
  * theta^Gas, theta^alpha, |div u|, |curl u| (Eq. D.4) */

@@ -222,3 +222,43 @@ def test_density_thinc_needs_monotone_density():
     F_plain = o.face_flux(0, W4, rho4, c4, f=1)
     F = o.face_flux(0, W4, rho4, c4, f=1, av4=av4)
     assert np.all(np.isfinite(F)) and np.array_equal(F, F_plain)
+
+
+@pytest.mark.parametrize("xg", [0.0, 1e-6, 1e-3, 0.3])
+def test_face_sound_speed_of_an_equilibrium_density(xg):
+    """Sec. 3.4 Remark 2: a face state whose density comes from the
+    liquid-vapour THINC gets its sound speed from (p, rho, xi).  Where that
+    density is the closure's own density at (p, xi), the result is the
+    closure's Wood sound speed, on both branches of Eq. 2-3/2-4."""
+    o, _ = _o()
+    for p in (400.0, 1000.0, 1342.0 * 1.01, 2e3, 1e5, 3e6):
+        rho, _, c, _ = o.forward(p, 0.0, np.array([xg]))
+        assert o.baro_sound_rho(p, rho, np.array([xg])) == pytest.approx(c, rel=1e-12, abs=0)
+
+
+def test_vapour_sensor_argument_and_threshold():
+    """App. D Eq. D.4's vapour term: theta^alpha of a cell is the sum over
+    directions of |alpha_v,i - alpha_v,i-1| + |alpha_v,i+1 - alpha_v,i| with
+    alpha_v of Eq. 2-7, and a cell is flagged exactly where one of its three
+    arguments exceeds its threshold.  The threshold is set so that some
+    cells lie between it and twice it."""
+    o, W = _vapour_pocket(0.4)
+    q = o.prim_to_cons(W)
+    Wp = o.cons_to_prim(q)[:, 0]
+    ny, nx = Wp.shape[1:]
+    av = np.array([[o.vapour(Wp[2, j, i], o.forward(Wp[2, j, i], Wp[3, j, i], np.array([Wp[4, j, i]]))[3])
+                    for i in range(nx)] for j in range(ny)])
+    theta = np.zeros_like(av)
+    for ax in (0, 1):
+        theta += np.abs(av - np.roll(av, 1, axis=ax)) + np.abs(np.roll(av, -1, axis=ax) - av)
+    s = o.sensor_args(q)[:, 0]
+    assert np.allclose(s[2], theta, rtol=1e-12, atol=1e-15)
+    nz = np.sort(theta[theta > 1e-3])
+    thr = float(nz[len(nz) // 2]) / 1.5
+    assert np.any((theta > thr) & (theta <= 2 * thr))
+    o2, _ = _vapour_pocket(thr)
+    f = o2.sensor(q)[0]
+    s2 = o2.sensor_args(q)[:, 0]
+    sch = o2.w.scheme
+    want = (s2[0] > sch["thr_ducros"]) | (s2[1] > sch["thr_gas"]) | (s2[2] > thr)
+    assert np.array_equal(f == 1.0, want)

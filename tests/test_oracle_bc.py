@@ -295,3 +295,37 @@ def test_inflow_equals_domain_extended_by_ghost_states(kind):
         face = np.maximum(fl[:, 1], fl[:, 2])
         disc = np.array([_in_disc(w, j, 0) for j in range(w.n[1])])
         assert (face[disc] == 0).any()
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_inflow_disc_per_cell_velocity(ndim):
+    """The inflow disc with a velocity given per boundary cell (the jet's
+    perturbed inflow): the ghost of boundary row (j, k) takes component a
+    from in_u[a, k, j]; the first interior cell then changes by
+    -a dt (F_E(W) - F(G, W)) / dx as for the uniform disc."""
+    w = _inflow_case(ndim)
+    nd = ndim
+    rng = np.random.default_rng(60 + ndim)
+    in_u = np.zeros((nd, w.n[2], w.n[1]))
+    for a in range(nd):
+        in_u[a] = (300.0 if a == 0 else 0.0) + rng.uniform(-20.0, 20.0, size=(w.n[2], w.n[1]))
+    o = oracle.Oracle(w, inflow_u=in_u)
+    Wc = np.array([20.0, 5.0, -3.0][:nd] + [2e6, 320.0, 0.9])
+    W = np.broadcast_to(Wc[:, None, None, None], (w.nvar, w.n[2], w.n[1], w.n[0])).copy()
+    q = o.prim_to_cons(W)
+    Wr = o.cons_to_prim(q)[:, 0, 0, 0]
+    dt = 0.3 * o.dt(q, 1.0)
+    qa = o.stage(1, dt, q, q)
+    FW = o.face_flux(0, [Wr] * 4)
+    f = w.inflow
+    n_in = 0
+    for k in range(w.n[2]):
+        for j in range(w.n[1]):
+            if not _in_disc(w, j, k):
+                continue
+            n_in += 1
+            G = np.concatenate([in_u[:, k, j], [Wr[nd], f["T"]], f["Y"][:w.ncomp - 1]])
+            Fin = o.face_flux(0, [G, G, Wr, Wr])
+            expect = q[:, k, j, 0] - 0.25 * dt / w.dx[0] * (FW - Fin)
+            assert np.all(np.abs(qa[:, k, j, 0] - expect) <= 1e-13 * np.abs(q[:, 0, 0, 0]).max()), (j, k)
+    assert n_in > 3

@@ -144,3 +144,34 @@ def test_oscillating_drop_period_eq_4_3():
     print(f"Eq. 4-3 period {T43:.4e} s; measured {t_full:.4e} s, half period {t_half:.4e} s")
     assert abs(t_full / T43 - 1.0) < 0.03, t_full / T43
     assert abs(2 * t_half / T43 - 1.0) < 0.06, 2 * t_half / T43
+
+
+def test_smoothing_kernel_moments():
+    """Eq. 3-9's kernel (1/16 in 2D, 1/64 in 3D: the binomial weights 1, 2, 1
+    along each direction) keeps a linear field and adds h_d^2/2 times the
+    coefficient of each x_d^2: on alpha = c0 + sum_d (b_d x_d + c_d x_d^2)
+    the smoothed fraction of every cell whose neighbours are interior is
+    alpha + sum_d c_d h_d^2/2 (a box filter would add 2 h_d^2/3)."""
+    rng = np.random.default_rng(21)
+    for ndim, n, hi in ((2, (9, 7, 1), (1e-3, 1.4e-3, 1.0)), (3, (7, 6, 8), (1e-3, 0.9e-3, 1.6e-3))):
+        w = wl.Workload(name="kernel", ndim=ndim, n=list(n), lo=[0, 0, 0], hi=list(hi),
+                        bc=[[wl.BC_OUTFLOW] * 2] * 3, comps=[wl.AIR, wl.WATER], liquid=1,
+                        scheme=wl.default_scheme(sigma=0.07), steps=1, cfl=0.4, init="random")
+        o = oracle.Oracle(w)
+        dx = w.dx
+        xs = [(np.arange(n[d]) + 0.5) * dx[d] for d in range(3)]
+        Z, Yc, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+        pos = [X, Yc, Z]
+        b = rng.uniform(-0.1, 0.1, size=3) / np.array(hi)
+        c = rng.uniform(-0.1, 0.1, size=3) / np.array(hi) ** 2
+        alpha = 0.5 + sum(b[d] * pos[d] + c[d] * pos[d] ** 2 for d in range(ndim))
+        assert 0.05 < alpha.min() and alpha.max() < 0.95
+        rho_l = o.forward(1e5, 300.0, [0.0])[0]
+        rho_g = o.forward(1e5, 300.0, [1.0])[0]
+        Yl = alpha * rho_l / (alpha * rho_l + (1.0 - alpha) * rho_g)
+        W = np.zeros((w.nvar,) + alpha.shape)
+        W[ndim], W[ndim + 1], W[ndim + 2] = 1e5, 300.0, 1.0 - Yl
+        got = o.smoothed_fraction(o.prim_to_cons(W))
+        want = alpha + sum(c[d] * dx[d] ** 2 / 2.0 for d in range(ndim))
+        inner = (slice(1, -1) if ndim == 3 else slice(None), slice(1, -1), slice(1, -1))
+        assert np.allclose(got[inner], want[inner], rtol=0, atol=1e-13)

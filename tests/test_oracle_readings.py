@@ -273,3 +273,58 @@ def test_pr_mixture_second_virial(T):
         Y1 = _mass_fraction(X, M1, M2)
         for v in (2e-4, 1e-3):
             assert o2.pr_state(T, v, [1.0 - Y1])["p"] == pytest.approx(o.pr_state(T, v, [Y1])["p"], rel=1e-13, abs=0)
+
+
+# ------------------------------------------------------ mass fractions
+def test_mass_fractions_entering_the_closure_are_clipped():
+    """Reading of the mass fractions entering the closure: each tracked one
+    is clipped to [0, 1] and the last is 1 minus their sum, clipped too, so
+    face states that overshoot by rounding or reconstruction give the
+    closure values of the clipped fractions."""
+    o = oracle.Oracle(_grid(2, [wl.AIR, wl.WATER]))
+    for p, T in ((1e5, 300.0), (3e7, 900.0)):
+        for over, clip in (([1.0 + 1e-7], [1.0]), ([-1e-7], [0.0]), ([1.3], [1.0]), ([-0.2], [0.0])):
+            a, b = o.forward(p, T, over), o.forward(p, T, clip)
+            assert a[:3] == b[:3] and np.array_equal(a[3], b[3])
+    o3 = oracle.Oracle(_grid(2, [wl.N2_IG, wl.CH4_IG, wl.DODECANE_SG]))
+    for over, clip in (([1.2, -0.1], [1.0, 0.0]), ([0.7, 0.5], [0.7, 0.5])):
+        a, b = o3.forward(2e6, 500.0, over), o3.forward(2e6, 500.0, clip)
+        assert a[:3] == b[:3]
+    # [0.7, 0.5]: the last fraction 1 - 1.2 is clipped to 0 (no negative phase)
+    r, _, _, al = o3.forward(2e6, 500.0, [0.7, 0.5])
+    assert al[2] == 0.0
+    # in a Peng-Robinson mixture every fraction enters the molar mass and the
+    # mixing rule: with the last one clipped to 0 its species does not matter
+    ch4 = wl.comp_pr(190.56, 4.599e6, 0.011, 1709.0, 0.016043)
+    pa = _pr_oracle([wl.N2_PR, wl.N2_PR, wl.DODECANE_PR]).forward(2e6, 500.0, [0.7, 0.5])
+    pb = _pr_oracle([wl.N2_PR, wl.N2_PR, ch4]).forward(2e6, 500.0, [0.7, 0.5])
+    assert pa[:3] == pb[:3]
+
+
+# ------------------------------------------ Peng-Robinson root choice
+def test_pr_root_of_lowest_gibbs_energy_in_the_three_root_region():
+    """Reading of the root choice (the paper is silent): where the PR cubic
+    has three real roots above B (pure n-dodecane below its critical
+    temperature, pressures around saturation) the TDU takes the root of
+    lowest Gibbs departure (numpy's roots of the cubic as an independent
+    solver): the liquid root above the saturation pressure, the vapour root
+    below it, so that both occur in the sample."""
+    C12 = wl.DODECANE_PR
+    o = _pr_oracle([wl.N2_PR, C12])
+    s2 = math.sqrt(2.0)
+    T = 500.0
+    picked = set()
+    for p in np.geomspace(2e4, 1.5e6, 60):
+        st = o.pr_state(T, 1e-3, [0.0])
+        A, B = st["a"] * p / (RU * T) ** 2, st["b"] * p / (RU * T)
+        roots = np.roots([1.0, -(1 - B), A - 3 * B * B - 2 * B, -(A * B - B * B - B ** 3)])
+        real = sorted(r.real for r in roots if abs(r.imag) < 1e-10 and r.real > B)
+        if len(real) < 3:
+            continue
+        g = lambda Z: Z - 1 - math.log(Z - B) - A / (2 * s2 * B) * math.log((Z + (1 + s2) * B) / (Z + (1 - s2) * B))
+        Zbest = min(real, key=g)
+        rho = o.forward(p, T, [0.0])[0]
+        Z = p * (C12["M"] / rho) / (RU * T)
+        assert Z == pytest.approx(Zbest, rel=1e-8, abs=0)
+        picked.add("liquid" if Zbest == real[0] else "vapour" if Zbest == real[-1] else "middle")
+    assert picked == {"liquid", "vapour"}
