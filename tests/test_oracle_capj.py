@@ -81,3 +81,25 @@ def test_capillary_model_replaces_the_csf_source():
     a = _capj(wl.droplet(n=24, A=0.15, sigma=30.0)).stage(1, dt, qd, qd)
     b = oracle.Oracle(wd).stage(1, dt, qd, qd)
     assert np.abs(a - b).max() > 0
+
+
+@pytest.mark.parametrize("kappa", [4000.0, -2500.0])
+def test_smooth_face_at_the_laplace_balance_is_stationary(kappa):
+    """The same balance on an App. D smooth face (f = 0, Eq. D.5 with the
+    jump in the contact condition): across a pressure step Delta^3 p with
+    the scale 1/2 equals the step p_L - p_R, so the jump J cancels it and no
+    mass crosses, as on the upwind branch."""
+    w = wl.droplet(n=16, sigma=0.07)
+    w.scheme = dict(w.scheme, iles=1)
+    o = _capj(w)
+    sigma = w.scheme["sigma"]
+    p_gas = 2e5
+    p_liq = p_gas + sigma * kappa
+    liq = [0.0, 0.0, p_liq, 300.0, 0.0]
+    gas = [0.0, 0.0, p_gas, 300.0, 1.0]
+    rl, _, cl, _ = o.forward(p_liq, 300.0, [0.0])
+    rg, _, cg, _ = o.forward(p_gas, 300.0, [1.0])
+    F, G = o.face_flux_kappa(0, [liq, liq, gas, gas], kappa, kappa, [1.0, 0.0], rho4=[rl, rl, rg, rg],
+                             c4=[cl, cl, cg, cg], f=0)
+    assert abs(F[0]) <= 1e-12 * rl
+    assert G[0] == 0.5 * sigma * kappa * (0.0 - 1.0)

@@ -17,9 +17,10 @@ from paper_2304_00140_gb300 import workloads as wl
 from tests import exact_riemann as er
 
 
-def _line(comps=(wl.AIR, wl.WATER), ndim=1, n=(4, 1, 1), bc=wl.BC_OUTFLOW, **scheme):
+def _line(comps=(wl.AIR, wl.WATER), ndim=1, n=(4, 1, 1), bc=wl.BC_OUTFLOW, aspect=(1.0, 1.0), **scheme):
     return wl.Workload(name="faces", ndim=ndim, n=list(n), lo=[0.0, 0.0, 0.0],
-                       hi=[1e-3, 1e-3 * n[1] / n[0], 1e-3 * n[2] / n[0]], bc=[[bc, bc]] * 3, comps=list(comps),
+                       hi=[1e-3, 1e-3 * aspect[0] * n[1] / n[0], 1e-3 * aspect[1] * n[2] / n[0]], bc=[[bc, bc]] * 3,
+                       comps=list(comps),
                        liquid=len(comps) - 1, scheme=wl.default_scheme(**scheme), steps=1, cfl=0.4, init="random")
 
 
@@ -142,9 +143,9 @@ def test_ducros_sensor_of_linear_velocity_fields(ndim):
     """Eq. D.4 on u = u0 + A x: central differences are exact, so every
     interior cell gives div u = tr A, the vorticity the antisymmetric part
     (A_zy - A_yz, A_xz - A_zx, A_yx - A_xy) and theta^D =
-    (tr A)^2/((tr A)^2 + |curl u|^2 + eps)."""
+    (tr A)^2/((tr A)^2 + |curl u|^2 + eps).  The three spacings differ."""
     n = (8, 7, 6) if ndim == 3 else (8, 7, 1)
-    w = _line(ndim=ndim, n=n, iles=1)
+    w = _line(ndim=ndim, n=n, aspect=(0.6, 1.7), iles=1)
     o = oracle.Oracle(w)
     rng = np.random.default_rng(40 + ndim)
     x = [(np.arange(n[d]) + 0.5) * w.dx[d] for d in range(3)]

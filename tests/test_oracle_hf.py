@@ -145,3 +145,49 @@ def test_laplace_jump_with_height_function():
     jc = n // 2
     jump = -S[0, 0, jc, jc:].sum() * dx
     assert abs(jump * R - 1.0) < 0.02, jump * R
+
+
+def test_quadratic_surface_on_an_anisotropic_grid():
+    """The 3D height-function formula on heights it gets exactly: liquid
+    below z = f(x, y), f quadratic with a cross term, on a grid whose three
+    spacings differ.  The columns' liquid heights are the cell averages of
+    f, whose central differences are f's exact derivatives at the column
+    centre (H_x, H_y), 2a, 2b and c, so the curvature must be
+    -(H_xx (1 + H_y^2) + H_yy (1 + H_x^2) - 2 H_xy H_x H_y)/(1 + H_x^2 + H_y^2)^(3/2)
+    to rounding wherever the interface of all nine columns lies inside the
+    five-cell window."""
+    n = (10, 9, 14)
+    dx = (1.0e-4, 0.7e-4, 0.5e-4)
+    a, b, c, d, e = -300.0, 200.0, 150.0, 0.2, -0.15
+    xc, yc, z0 = 5.1e-4, 3.2e-4, 3.4e-4
+    w = wl.Workload(name="hf3", ndim=3, n=list(n), lo=[0, 0, 0], hi=[n[i] * dx[i] for i in range(3)],
+                    bc=[[wl.BC_OUTFLOW] * 2] * 3, comps=[wl.AIR, wl.WATER], liquid=1,
+                    scheme=wl.default_scheme(sigma=1.0, curvature=1), steps=1, cfl=0.4, init="random")
+    o = oracle.Oracle(w)
+    x = (np.arange(n[0]) + 0.5) * dx[0] - xc
+    y = (np.arange(n[1]) + 0.5) * dx[1] - yc
+    Yg, Xg = np.meshgrid(y, x, indexing="ij")
+    favg = z0 + d * Xg + e * Yg + a * Xg ** 2 + b * Yg ** 2 + c * Xg * Yg + (a * dx[0] ** 2 + b * dx[1] ** 2) / 12.0
+    k = np.arange(n[2])[:, None, None]
+    alpha = np.clip((favg[None] - k * dx[2]) / dx[2], 0.0, 1.0)
+    rl = o.forward(1e5, 300.0, np.array([0.0]))[0]
+    rg = o.forward(1e5, 300.0, np.array([1.0]))[0]
+    Yl = alpha * rl / (alpha * rl + (1 - alpha) * rg)
+    W = np.zeros((w.nvar,) + alpha.shape)
+    W[3], W[4], W[5] = 1e5, 300.0, 1.0 - Yl
+    q = o.prim_to_cons(W)
+    kap = o.curvature(q)
+    axis, _ = o.hf_axis(q)
+    layer = np.floor(favg / dx[2]).astype(int)          # the column's partly filled cell
+    checked = 0
+    for kk, j, i in np.argwhere((alpha > 0) & (alpha < 1)):
+        if not (1 <= i < n[0] - 1 and 1 <= j < n[1] - 1 and 2 <= kk < n[2] - 2) or axis[kk, j, i] != 2:
+            continue
+        if np.abs(layer[j - 1:j + 2, i - 1:i + 2] - kk).max() > 1:
+            continue
+        X, Y = Xg[j, i], Yg[j, i]
+        Hx, Hy = d + 2 * a * X + c * Y, e + 2 * b * Y + c * X
+        want = -(2 * a * (1 + Hy ** 2) + 2 * b * (1 + Hx ** 2) - 2 * c * Hx * Hy) / (1 + Hx ** 2 + Hy ** 2) ** 1.5
+        assert kap[kk, j, i] == pytest.approx(want, rel=1e-8, abs=0), (kk, j, i)
+        checked += 1
+    assert checked > 20

@@ -318,3 +318,46 @@ def test_opcount_build_reproduces_the_oracle():
     assert np.array_equal(got, o.stage(1, dt, q, q))
     per_cell = sum(stage[k] - box[k] for k in ("add", "mul", "div", "sqrt", "minmax", "cmp")) / w.cells
     assert 200 < per_cell < 2000, per_cell
+
+
+def test_totals_are_compensated_sums():
+    """The conservation totals are compensated (Neumaier) sums: fields whose
+    values span 32 orders of magnitude and cancel agree with math.fsum's correctly
+    rounded total within Neumaier's error bound, where a plain running sum
+    loses every small term."""
+    w = wl.random_state(n=(20, 14))
+    o = oracle.Oracle(w)
+    rng = np.random.default_rng(9)
+    q = rng.uniform(0.5, 1.5, size=(w.nvar, 1, 14, 20)) * 10.0 ** rng.integers(-16, 1, size=(w.nvar, 1, 14, 20))
+    q[:, 0, 0, 0] = 1e16                  # every later term is below its half-ulp
+    q[:, 0, -1, -1] = -1e16
+    got = o.totals(q)
+    for v in range(w.nvar):
+        exact = math.fsum(q[v].ravel().tolist())
+        # Neumaier's bound: 2 eps |S| + O(n eps^2) sum |x|
+        assert abs(got[v] - exact) <= 4.5e-16 * abs(exact) + 1e-12, (got[v], exact)
+        plain = float(np.cumsum(q[v].ravel())[-1])     # a running sum, term by term
+        assert abs(plain - exact) > 1e-3 * abs(exact)
+
+
+def test_formation_energy_enters_the_caloric_law():
+    """Eq. A.1.1 with a formation energy q != 0: p = (gamma-1) rho (e - q)
+    - gamma pinf, and the inverse recovers (p, T) (every workload has
+    q = 0, so this is the only place q is exercised)."""
+    gas_q = wl.comp_sg(1.4, 0.0, 718.0, q=2.5e5)
+    liq_q = wl.comp_sg(6.12, 3.43e8, 1816.0, q=-1.2e6)
+    w = _one_dim([gas_q, liq_q], 4)
+    o = oracle.Oracle(w)
+    for Y, comp in (([1.0], gas_q), ([0.0], liq_q)):
+        g, pi, qf = comp["gamma"], comp["pinf"], comp["q"]
+        for p, T in ((1e5, 300.0), (4e7, 800.0)):
+            rho, e, c, al = o.forward(p, T, Y)
+            assert abs(p - ((g - 1.0) * rho * (e - qf) - g * pi)) <= 1e-9 * (p + g * pi)
+            p2, T2 = o.inverse(rho, e, Y)
+            assert abs(p2 - p) <= 1e-9 * (p + pi) and abs(T2 - T) <= 1e-10 * T
+    # a mixture: e is the mass-weighted sum, so q enters with Y_k
+    rho, e, _, _ = o.forward(2e5, 350.0, [0.3])
+    e0 = 0.3 * o.forward(2e5, 350.0, [1.0])[1] + 0.7 * o.forward(2e5, 350.0, [0.0])[1]
+    assert e == pytest.approx(e0, rel=1e-14, abs=0)
+    p2, T2 = o.inverse(rho, e, [0.3])
+    assert p2 == pytest.approx(2e5, rel=1e-9, abs=0) and T2 == pytest.approx(350.0, rel=1e-10, abs=0)
