@@ -332,8 +332,9 @@ fv_status fv_probe_fp64(int blocks, int threads, int iters, double* ms, double* 
  * scratch of (n+4)^d ghosted cells times (ndim + ncomp + 1 + extra fields)
  * values of 8 bytes (FV_FP64) or 4 bytes (FV_MIXED), plus small work lists,
  * must fit the array; larger grids, a per-cell inflow array (grid->in_u), the
- * barotropic closure in the FV_MIXED form, Peng-Robinson components and every
- * argument fv_init would reject return FV_ERR_ARG.  The first call on a device
+ * barotropic closure in the FV_MIXED form, Peng-Robinson components, the
+ * capillary-jump surface-tension model (st_model = 1 with sigma > 0) and
+ * every argument fv_init would reject return FV_ERR_ARG.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that device
  * current and keeps it for the process; do not reset the device
  * (cudaDeviceReset) after it.
