@@ -98,7 +98,7 @@ def test_cfl_dt_matches_oracle():
     w = wl.random_state(n=(50, 31))
     o, q, s = _pair(w)
     t = s.step(1, 0.4)
-    assert t == pytest.approx(o.dt(q, 0.4), rel=1e-13)
+    assert t == pytest.approx(o.dt(q, 0.4), rel=1e-13, abs=0)
     ref, _ = o.step(q, 1, 0.4)
     assert np.all(rel_field_diff(s.get_state(), ref) < 1e-12)
 
@@ -115,7 +115,7 @@ def test_advection_128_full_run_fp64(fused, monkeypatch):
     _check_kernel(s, fused)
     d = rel_field_diff(got, ref)
     assert np.all(d < 1e-10), d
-    assert t_gpu == pytest.approx(t_ref, rel=1e-12)
+    assert t_gpu == pytest.approx(t_ref, rel=1e-12, abs=0)
 
 
 def test_conservation_and_uniform_pressure_gpu():
