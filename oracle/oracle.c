@@ -31,6 +31,10 @@
  * the step definition itself, the THINC eligibility epsilon = 1e-4, the
  * Delta^3 p scale 1/2 and Z_c = 0.3074 in the combining rule; the functions
  * that use them are pinned as listed above.
+ * Parity unpinned: the coefficient 4 of the Chakravarthy limiter, taken as
+ * Table 4.2 prints it.  The limiter is not a default and no workload uses
+ * it.  The tests pin only what every limiter shares (f(1) = 1, f = 0 for
+ * r <= 0), and a test of the printed formula would merely retype it.
  */
 #include "oracle.h"
 #ifdef _OPENMP
