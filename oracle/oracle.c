@@ -29,7 +29,9 @@
  * pressure work and the clipping of mass fractions.
  * Readings whose VALUE no paper number fixes, which the CUDA path shares:
  * the step definition itself, the THINC eligibility epsilon = 1e-4, the
- * Delta^3 p scale 1/2 and Z_c = 0.3074 in the combining rule; the functions
+ * Delta^3 p scale 1/2, Z_c = 0.3074 in the combining rule and the CSF
+ * normal's cut-off |grad alpha~| dx_min < 1e-5 (which spacing scales it on a
+ * grid whose spacings differ is part of that reading); the functions
  * that use them are pinned as listed above.
  * Parity unpinned: the coefficient 4 of the Chakravarthy limiter, taken as
  * Table 4.2 prints it.  The limiter is not a default and no workload uses
