@@ -376,7 +376,10 @@ def e2e_form(job, precision, args, torch):
 # ------------------------------------------------------------- CPU oracle
 def oracle_window_step(o, q, dt, lo, hi):
     """one LSRK step of the oracle restricted to a window (stage k evaluated
-    on the window grown by the stencil reach of the later stages)"""
+    on the window grown by the stencil reach of the later stages, two cells a
+    stage; the capillary jump, which no benchmark workload uses, reaches
+    three).  Inside the window it is the full step where the grown window
+    stays off periodic sides; elsewhere it is a timing sample only."""
     w = o.w
     prev = q
     for k in (1, 2, 3, 4):

@@ -33,12 +33,17 @@ def oracle_step_window(o, q, dt, lo, hi):
     """one LSRK step of the oracle on the window [lo, hi) only: stage k is
     evaluated on the window grown by 2 (4 - k) cells (clipped to the domain),
     which is all that stage k + 1 reads.  Returns the full array with the
-    window filled in."""
+    window filled in.  Exact where the grown window does not cross a periodic
+    side (walls, outflow and inflow sides are fine): the growth is clipped,
+    not wrapped.  With the capillary jump a face also reads the curvature of
+    its two cells, which reaches two cells further, so a stage reads three
+    cells on each side and the growth is 3 (4 - k)."""
     w = o.w
     q0 = np.ascontiguousarray(q)
     prev = q0
+    reach = 3 if (w.scheme.get("st_model", 0) == 1 and w.scheme.get("sigma", 0.0) > 0.0) else 2
     for k in LSRK_STAGES:
-        g = 2 * (4 - k)
+        g = reach * (4 - k)
         wl_ = [max(0, lo[d] - g) if d < w.ndim else 0 for d in range(3)]
         wh_ = [min(w.n[d], hi[d] + g) if d < w.ndim else 1 for d in range(3)]
         out = q0.copy()
