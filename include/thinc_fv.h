@@ -266,8 +266,10 @@ fv_status fv_rk_stage(fv_ctx* ctx, int k, double dt);
  * the state first. */
 
 /* nsteps full steps: per step dt = cfl / max(sum_d (|u_d| + c)/dx_d) of each
- * case (computed on the device from the step's initial state), then the four
- * stages.  The step sequence is captured once per cfl value in a CUDA graph
+ * case, with viscous terms plus 2 D sum_d 1/dx_d^2 under the maximum,
+ * D = max(4/3 mu, k_c / cv_min)/rho and cv_min the smallest component cv
+ * (the paper defines no step: both are readings), computed on the device
+ * from the step's initial state; then the four stages.  The step sequence is captured once per cfl value in a CUDA graph
  * and replayed on the context's stream.  With the fused 2D kernel in the
  * FP32-mixed form (no viscous or gravity terms) the last stage of a step
  * also leaves the wave speeds of the state it writes, and the next step
