@@ -287,6 +287,7 @@ MUTANTS = [
 
 
 def pins():
+    """the CPU pins of the oracle (never this check's own sampled test)"""
     tests = sorted(os.path.join("tests", f) for f in os.listdir(os.path.join(ROOT, "tests"))
                    if f.startswith("test_oracle_") and f.endswith(".py"))
     return tests + [os.path.join("tests", "test_workloads.py")]
