@@ -283,6 +283,52 @@ MUTANTS = [
       'double vc = 0.5 * (vci + vcj);')]),
     ('pr_w_i', [('double w = 0.5 * (ci->omega + cj->omega);',
       'double w = ci->omega;')]),
+    ('muscl_L_ratio', [('if (dl != 0.0) *L = x2 + 0.5 * or_limiter(id, dc / dl) * dl;',
+      'if (dl != 0.0) *L = x2 + 0.5 * or_limiter(id, dl / dc) * dl;')]),
+    ('koren_cap', [('case OR_KOREN: return fmax(0.0, min3(2.0, 2.0 * r,',
+      'case OR_KOREN: return fmax(0.0, min3(1.5, 2.0 * r,')]),
+    ('thinc_E_arg', [('exp(theta * beta * (2.0 * F - 1.0))',
+      'exp(theta * beta * (F - 0.5))')]),
+    ('pr_gdep_sign', [('return Z - 1.0 - log(Z - B) - A / (2.0 * s2 * B)',
+      'return Z - 1.0 - log(Z - B) + A / (2.0 * s2 * B)')]),
+    ('pr_dpdrho', [('const double dpdrho = -(v * v / m->M) * dpdv;',
+      'const double dpdrho = -(v / m->M) * dpdv;')]),
+    ('baro_wood', [('if (a > 0.0) inv += a / (rk[k] * bar_c2_k(&P->comp[k], p));',
+      'if (a > 0.0) inv += a / bar_c2_k(&P->comp[k], p);')]),
+    ('vapour_denom', [('double s = (c->rho_sl - rlm) / (c->rho_sl - c->rho_sv);',
+      'double s = (c->rho_sl - rlm) / c->rho_sl;')]),
+    ('visc_normal_2dx', [('g[a][b] = (bW(B, a, cr) - bW(B, a, cl)) / P->dx[d];',
+      'g[a][b] = (bW(B, a, cr) - bW(B, a, cl)) / (2.0 * P->dx[d]);')]),
+    ('visc_dT_dx0', [('const double dTdx = (bW(B, nd + 1, cr) - bW(B, nd + 1, cl)) / P->dx[d];',
+      'const double dTdx = (bW(B, nd + 1, cr) - bW(B, nd + 1, cl)) / P->dx[0];')]),
+    ('grav_energy_u0', [('S[1 + nd] += B.rho[b0] * B.W[(size_t)d * B.cnt + b0] * P->grav[d];',
+      'S[1 + nd] += B.rho[b0] * B.W[0] * P->grav[d];')]),
+    ('inflow_src1', [('                        src[0] = 0;\n                        flip[0] = 0;',
+      '                        src[0] = 1;\n                        flip[0] = 0;')]),
+    ('inflow_dz_yc', [('double dy = y - P->in_yc, dz = (nd == 3) ? z - P->in_zc : 0.0;',
+      'double dy = y - P->in_yc, dz = (nd == 3) ? z - P->in_yc : 0.0;')]),
+    ('step_time2', [('if (t) *t += dt;',
+      'if (t) *t += 2.0 * dt;')]),
+    ('cp_Y_unscaled', [('for (int k = 0; k < N - 1; ++k) Yt[k] = qc[2 + nd + k] / rho;',
+      'for (int k = 0; k < N - 1; ++k) Yt[k] = qc[2 + nd + k];')]),
+    ('p2c_energy', [('q[(size_t)(1 + nd) * nc + c] = r * (e + ke);',
+      'q[(size_t)(1 + nd) * nc + c] = r * e + ke;')]),
+    ('hf_Hx_1dx', [('const double Hx = (H[2][1] - H[0][1]) / (2.0 * d1);',
+      'const double Hx = (H[2][1] - H[0][1]) / d1;')]),
+    ('csf_energy_sign', [('S[nd] = P->sigma * kappa * udg;',
+      'S[nd] = -P->sigma * kappa * udg;')]),
+    ('baro_e_fourth', [('const int fourth = (v < iY) && !(baro && v == iT);',
+      'const int fourth = (v < iY);')]),
+    ('sens_thr_gas', [('a5[1] > P->thr_gas',
+      'a5[1] > 2.0 * P->thr_gas')]),
+    ('sens_eps_ducros', [('a5[0] = div * div / (div * div + curl2 + P->eps_ducros);',
+      'a5[0] = div * div / (div * div + curl2 + 1e-6);')]),
+    ('capj_energy_g', [('const int g = (v == 1 + nd) ? 1 : 0;',
+      'const int g = 0;')]),
+    ('smooth_norm', [('return s / norm;   /* norm = 16 in 2D, 64 in 3D */',
+      'return s / 16.0;')]),
+    ('mix_mu_first', [('m += al[c] * P->comp[c].mu;',
+      'm += al[0] * P->comp[c].mu;')]),
 ]
 
 

@@ -259,3 +259,56 @@ def test_no_curvature_in_a_bulk_phase():
     kap = o.curvature(o.prim_to_cons(W))
     R = 0.25 * (w.hi[0] - w.lo[0])
     assert np.abs(kap).max() > 0.3 / R
+
+
+def test_ducros_sensor_keeps_the_papers_epsilon_at_small_gradients():
+    """Eq. D.4's eps is the paper's 1e-20 (dimensional, 1/s^2): on a linear
+    field whose gradients are of order 1e-3 1/s, theta^D is still
+    (tr A)^2/((tr A)^2 + |curl u|^2) to rounding; a larger eps would show."""
+    w = _line(ndim=2, n=(8, 7, 1), aspect=(0.6, 1.0), iles=1)
+    assert w.scheme["eps_ducros"] == 1e-20
+    o = oracle.Oracle(w)
+    x = [(np.arange(w.n[d]) + 0.5) * w.dx[d] for d in range(2)]
+    Yc, X = np.meshgrid(x[1], x[0], indexing="ij")
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        A = rng.normal(size=(2, 2)) * 1e-3
+        W = np.zeros((w.nvar, 1) + X.shape)
+        W[0, 0], W[1, 0] = A[0, 0] * X + A[0, 1] * Yc, A[1, 0] * X + A[1, 1] * Yc
+        W[2], W[3], W[4] = 2e5, 300.0, 1.0
+        s = o.sensor_args(o.prim_to_cons(W))
+        div, curl = np.trace(A), A[1, 0] - A[0, 1]
+        theta = div * div / (div * div + curl * curl + 1e-20)
+        assert np.allclose(s[0][0, 1:-1, 1:-1], theta, rtol=1e-6, atol=0)
+
+
+def test_gas_sensor_argument_and_threshold():
+    """Eq. D.4's gas term: theta^Gas of a cell is the sum over directions of
+    |a_i - a_i-1| + |a_i+1 - a_i| with a = 1 - alpha_liquid the cell's gas
+    volume fraction, and a cell is flagged where one of the arguments
+    exceeds its threshold.  The threshold is set so that some cells lie
+    between it and twice it."""
+    n = (24, 20, 1)
+    base = _line(ndim=2, n=n, bc=wl.BC_PERIODIC, iles=1)
+    o = oracle.Oracle(base)
+    x = [(np.arange(n[d]) + 0.5) * base.dx[d] for d in range(2)]
+    Yc, X = np.meshgrid(x[1], x[0], indexing="ij")
+    r = np.hypot(X - 0.5e-3, Yc - 0.42e-3)
+    h = wl.tanh_indicator(r - 0.25e-3, 2.5 * base.dx[0])          # liquid indicator, a wide interface
+    W = np.zeros((base.nvar, 1) + X.shape)
+    W[2], W[3], W[4] = 2e5, 300.0, 1.0 - h
+    q = o.prim_to_cons(W)
+    a = np.array([[1.0 - o.forward(2e5, 300.0, [W[4, 0, j, i]])[3][1] for i in range(n[0])] for j in range(n[1])])
+    theta = np.zeros_like(a)
+    for ax in (0, 1):
+        theta += np.abs(a - np.roll(a, 1, axis=ax)) + np.abs(np.roll(a, -1, axis=ax) - a)
+    s = o.sensor_args(q)[:, 0]
+    assert np.allclose(s[1], theta, rtol=1e-12, atol=1e-15)
+    nz = np.sort(theta[theta > 1e-3])
+    thr = float(nz[len(nz) // 2]) / 1.5
+    assert np.any((theta > thr) & (theta <= 2 * thr))
+    o2 = oracle.Oracle(_line(ndim=2, n=n, bc=wl.BC_PERIODIC, iles=1, thr_gas=thr))
+    f = o2.sensor(q)[0]
+    s2 = o2.sensor_args(q)[:, 0]
+    want = (s2[0] > o2.w.scheme["thr_ducros"]) | (s2[1] > thr) | (s2[2] > o2.w.scheme["thr_vap"])
+    assert np.array_equal(f == 1.0, want) and want.any() and not want.all()

@@ -260,3 +260,36 @@ def test_lsrk_amplifies_a_linear_mode_by_the_degree_4_taylor_polynomial():
         q1 = oracle_step_dt(o, q, dt)
         G = 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24
         assert abs(q1[1][0, ku, 0] / q[1][0, ku, 0] - G) < 1e-9, (z, q1[1][0, ku, 0] / q[1][0, ku, 0], G)
+
+
+def _aniso_errors(nx, ny, mu, kc):
+    """the 2D residual error on an nx x ny grid of the same periodic box
+    (unequal spacings)"""
+    f, fu = _continuum_residual(2, mu, kc, mu, kc)
+    cx, cy = (np.arange(nx) + 0.5) * (L / nx), (np.arange(ny) + 0.5) * (L / ny)
+    Y, Xg = np.meshgrid(cy, cx, indexing="ij")
+    G = (Xg[None], Y[None])
+    vals = [np.broadcast_to(np.asarray(a, dtype=float), G[0].shape) for a in fu(*G)]
+    mk = lambda m, k: wl.with_transport(wl.Workload(
+        name="visc", ndim=2, n=[nx, ny, 1], lo=[0, 0, 0], hi=[L, L, 1.0], bc=[[0, 0]] * 3,
+        comps=[wl.AIR, dict(wl.AIR)], liquid=1, scheme=wl.default_scheme(), steps=1, cfl=0.4, init="random"),
+        mu=[m, m], kc=[k, k])
+    w_on, w_off = mk(mu, kc), mk(0.0, 0.0)
+    W = np.zeros((w_on.nvar,) + G[0].shape)
+    W[0], W[1], W[2], W[3], W[4] = vals[0], vals[1], P0, vals[2], vals[3]
+    o_on, o_off = oracle.Oracle(w_on), oracle.Oracle(w_off)
+    q = o_on.prim_to_cons(W)
+    got = (o_on.stage(4, 1.0, q, q) - q) - (o_off.stage(4, 1.0, q, q) - q)
+    exact = [np.broadcast_to(np.asarray(a, dtype=float), G[0].shape) for a in f(*G)]
+    return np.array([np.abs(got[1 + v] - exact[v]).max() / max(np.abs(exact[v]).max(), 1e-300) for v in range(3)])
+
+
+@pytest.mark.parametrize("mu,kc", [(2e-3, 0.0), (0.0, 0.5)], ids=["stress", "heat"])
+def test_viscous_residual_converges_on_an_anisotropic_grid(mu, kc):
+    """the same second-order convergence with dy = 2 dx: every derivative
+    divides by its own direction's spacing"""
+    e1 = _aniso_errors(32, 16, mu, kc)
+    e2 = _aniso_errors(64, 32, mu, kc)
+    live = [0, 1, 2] if mu else [2]
+    assert np.all(e2[live] < 0.02), e2
+    assert np.all(e1[live] / e2[live] > 3.5), (e1, e2)
