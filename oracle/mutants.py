@@ -329,6 +329,26 @@ MUTANTS = [
       'return s / 16.0;')]),
     ('mix_mu_first', [('m += al[c] * P->comp[c].mu;',
       'm += al[0] * P->comp[c].mu;')]),
+    ('p2c_species_idx', [('q[(size_t)(2 + nd + k) * nc + c] = r * w[nd + 2 + k];',
+      'q[(size_t)(2 + nd + k) * nc + c] = r * w[nd + 2];')]),
+    ('cp_species_idx', [('for (int k = 0; k < N - 1; ++k) Yt[k] = qc[2 + nd + k] / rho;',
+      'for (int k = 0; k < N - 1; ++k) Yt[k] = qc[2 + nd] / rho;')]),
+    ('flux_species_idx', [('for (int k = 0; k < N - 1; ++k) F[2 + nd + k] = us * rs * Ws[iY + k];',
+      'for (int k = 0; k < N - 1; ++k) F[2 + nd + k] = us * rs * Ws[iY];')]),
+    ('inflow_Y_idx', [('for (int kk = 0; kk < P->ncomp - 1; ++kk) w[nd + 2 + kk] = P->in_Y[kk];',
+      'for (int kk = 0; kk < P->ncomp - 1; ++kk) w[nd + 2 + kk] = P->in_Y[0];')]),
+    ('visc_mom_idx', [('        F[1 + a] -= tau;',
+      '        F[1 + d] -= tau;')]),
+    ('csf_force_idx', [('S[d] = P->sigma * kappa * galpha[d];',
+      'S[d] = P->sigma * kappa * galpha[0];')]),
+    ('hf_swap_ab', [('                q[t[0]] += a;\n                if (nt == 2) q[t[1]] += b;',
+      '                q[t[0]] += b;\n                if (nt == 2) q[t[1]] += a;')]),
+    ('mom_flux_u_idx', [('for (int a = 0; a < nd; ++a) F[1 + a] = us * rs * Ws[a] + (a == d ? ps : 0.0);',
+      'for (int a = 0; a < nd; ++a) F[1 + a] = us * rs * Ws[d] + (a == d ? ps : 0.0);')]),
+    ('sg_alpha_idx', [('double a = (Y[k] > 0.0) ? r * Y[k] / rk[k] : 0.0;\n        if (alpha) alpha[k] = a;\n        if (a > 0.0) inv += a / (P->comp[k].gamma',
+      'double a = (Y[k] > 0.0) ? r * Y[k] / rk[0] : 0.0;\n        if (alpha) alpha[k] = a;\n        if (a > 0.0) inv += a / (P->comp[k].gamma')]),
+    ('liquid_index_fixed', [('B->al[b] = alk[P->liquid];',
+      'B->al[b] = alk[1];')]),
 ]
 
 

@@ -329,3 +329,32 @@ def test_inflow_disc_per_cell_velocity(ndim):
             expect = q[:, k, j, 0] - 0.25 * dt / w.dx[0] * (FW - Fin)
             assert np.all(np.abs(qa[:, k, j, 0] - expect) <= 1e-13 * np.abs(q[:, 0, 0, 0]).max()), (j, k)
     assert n_in > 3
+
+
+def test_inflow_disc_three_components():
+    """The inflow disc with three components (the jet's N2, CH4 and liquid):
+    inside the disc the ghosts take each tracked mass fraction of the
+    inflow, in_Y[k] for component k."""
+    w = wl.jet3d(n=(6, 12, 12), iles=0, sigma=0.0)
+    w = dataclasses.replace(w, inflow=dict(w.inflow, Y=[0.2, 0.3], radius=4.2 * w.dx[1]))
+    o = oracle.Oracle(w)
+    nd = 3
+    Wc = np.array([20.0, 5.0, -3.0, 6e6, 900.0, 0.7, 0.1])
+    W = np.broadcast_to(Wc[:, None, None, None], (w.nvar, w.n[2], w.n[1], w.n[0])).copy()
+    q = o.prim_to_cons(W)
+    Wr = o.cons_to_prim(q)[:, 0, 0, 0]
+    dt = 0.3 * o.dt(q, 1.0)
+    qa = o.stage(1, dt, q, q)
+    FW = o.face_flux(0, [Wr] * 4)
+    f = w.inflow
+    n_in = 0
+    for k in range(w.n[2]):
+        for j in range(w.n[1]):
+            if not _in_disc(w, j, k):
+                continue
+            n_in += 1
+            G = np.concatenate([np.array(f["u0"][:nd]), [Wr[nd], f["T"]], [0.2, 0.3]])
+            Fin = o.face_flux(0, [G, G, Wr, Wr])
+            expect = q[:, k, j, 0] - 0.25 * dt / w.dx[0] * (FW - Fin)
+            assert np.all(np.abs(qa[:, k, j, 0] - expect) <= 1e-13 * np.abs(q[:, 0, 0, 0]).max()), (j, k)
+    assert n_in > 3

@@ -4,6 +4,7 @@ grad p = sigma kappa grad(alpha) integrated along a ray from the drop centre
 gives p_in - p_out, which must be sigma/R in 2D (Eq. 4-4) and 2 sigma/R in
 3D (App. C), with R the equivalent radius of the liquid volume."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_2304_00140_gb300 import workloads as wl
@@ -199,3 +200,35 @@ def test_curvature_of_a_circle_on_an_anisotropic_grid():
     k = o.curvature(o.prim_to_cons(W))
     band = (h > 0.2) & (h < 0.8)
     assert abs((k[band] * R).mean() - 1.0) < 0.02
+
+
+@pytest.mark.parametrize("order", ["liquid_first", "liquid_last_of_three"])
+def test_laplace_jump_wherever_the_liquid_is_listed(order):
+    """The liquid fraction that CSF (and the gas sensor) use is that of the
+    component named liquid, whatever its place in the list: water listed
+    first of two, or last of three (two gases, as in the jet), gives the
+    same Laplace jump sigma/R as the drop above."""
+    n, Rc = 96, 32
+    dx = 1e-3 / n
+    comps = [wl.WATER, wl.AIR] if order == "liquid_first" else [wl.N2_IG, wl.AIR, wl.WATER]
+    liquid = 0 if order == "liquid_first" else 2
+    w = wl.Workload(name="drop", ndim=2, n=[n, n, 1], lo=[0, 0, 0], hi=[1e-3, 1e-3, 1.0], bc=[[0, 0]] * 3,
+                    comps=comps, liquid=liquid, scheme=wl.default_scheme(sigma=1.0), steps=1, cfl=0.4,
+                    init="random")
+    x = (np.arange(n) + 0.5) * dx - 0.5e-3
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    h = wl.tanh_indicator(np.sqrt(X ** 2 + Y ** 2)[None] - Rc * dx, 1.5 * dx)
+    W = np.zeros((w.nvar,) + h.shape)
+    W[2], W[3] = 1e5, 300.0
+    if order == "liquid_first":
+        W[4] = h                                   # water tracked
+    else:
+        W[4], W[5] = 0.5 * (1.0 - h), 0.5 * (1.0 - h)   # N2 and air tracked, water implied
+    o = oracle.Oracle(w)
+    q = o.prim_to_cons(W)
+    alpha = q[0] * (h if order == "liquid_first" else 1.0 - W[4] - W[5]) / RHO_WATER
+    S = o.csf_source(q)
+    Req = np.sqrt(alpha.sum() * dx * dx / np.pi)
+    c = n // 2
+    jump = -S[0, 0, c, c:].sum() * dx
+    assert abs(jump / (1.0 / Req) - 1.0) < 0.02, jump * Req

@@ -361,3 +361,46 @@ def test_formation_energy_enters_the_caloric_law():
     assert e == pytest.approx(e0, rel=1e-14, abs=0)
     p2, T2 = o.inverse(rho, e, [0.3])
     assert p2 == pytest.approx(2e5, rel=1e-9, abs=0) and T2 == pytest.approx(350.0, rel=1e-10, abs=0)
+
+
+def _three(ndim=2, n=(7, 5)):
+    return wl.Workload(name="three", ndim=ndim, n=[n[0], n[1], 1], lo=[0, 0, 0], hi=[1e-3, 1e-3 * n[1] / n[0], 1.0],
+                       bc=[[0, 0]] * 3, comps=[wl.N2_IG, wl.CH4_IG, wl.DODECANE_SG], liquid=2,
+                       scheme=wl.default_scheme(), steps=1, cfl=0.4, init="random")
+
+
+def test_three_component_conversions():
+    """Table A.1 with three components: the conserved species are rho Y_k
+    for each tracked k (rho the closure's mixture density), and the
+    recovery returns every Y_k, u, p and T."""
+    w = _three()
+    o = oracle.Oracle(w)
+    rng = np.random.default_rng(13)
+    shape = (1, w.n[1], w.n[0])
+    W = np.zeros((w.nvar,) + shape)
+    W[0], W[1] = rng.uniform(-50, 50, shape), rng.uniform(-50, 50, shape)
+    W[2], W[3] = 10 ** rng.uniform(5, 7, shape), rng.uniform(300, 900, shape)
+    Y = rng.dirichlet([1.0, 1.0, 1.0], size=shape)
+    W[4], W[5] = Y[..., 0], Y[..., 1]
+    q = o.prim_to_cons(W)
+    for idx in np.ndindex(shape):
+        rho = o.forward(W[(2,) + idx], W[(3,) + idx], [W[(4,) + idx], W[(5,) + idx]])[0]
+        assert q[(0,) + idx] == pytest.approx(rho, rel=1e-15, abs=0)
+        for k in range(2):
+            assert q[(4 + k,) + idx] == pytest.approx(rho * W[(4 + k,) + idx], rel=1e-15, abs=0)
+    W2 = o.cons_to_prim(q)
+    for v in (0, 1, 4, 5):
+        assert np.allclose(W2[v], W[v], rtol=1e-12, atol=1e-14 * np.abs(W[v]).max())
+    assert np.allclose(W2[2], W[2], rtol=1e-9, atol=0) and np.allclose(W2[3], W[3], rtol=1e-10, atol=0)
+
+
+def test_three_component_euler_flux():
+    """Eq. 2-2's species fluxes with three components: a uniform state gives
+    u_n rho Y_k for each tracked species k."""
+    o = oracle.Oracle(_three())
+    for d, u in ((0, (30.0, -12.0)), (1, (-45.0, 7.0))):
+        Wc = np.array([u[0], u[1], 2.3e6, 410.0, 0.23, 0.61])
+        F = o.face_flux(d, np.tile(Wc, (4, 1)))
+        rho = o.forward(2.3e6, 410.0, [0.23, 0.61])[0]
+        assert F[4] == pytest.approx(rho * u[d] * 0.23, rel=1e-13, abs=0)
+        assert F[5] == pytest.approx(rho * u[d] * 0.61, rel=1e-13, abs=0)
