@@ -349,6 +349,12 @@ MUTANTS = [
       'double a = (Y[k] > 0.0) ? r * Y[k] / rk[0] : 0.0;\n        if (alpha) alpha[k] = a;\n        if (a > 0.0) inv += a / (P->comp[k].gamma')]),
     ('liquid_index_fixed', [('B->al[b] = alk[P->liquid];',
       'B->al[b] = alk[1];')]),
+    ('baro_vapour_liquid_idx', [('    const or_comp* c = &P->comp[P->liquid];\n    const double rlm = bar_rho_k(c, p);',
+      '    const or_comp* c = &P->comp[1];\n    const double rlm = bar_rho_k(c, p);')]),
+    ('baro_snd_liquid_idx', [('const int N = P->ncomp, L = P->liquid;',
+      'const int N = P->ncomp, L = 1;')]),
+    ('baro_vapour_alpha_idx', [('return alpha[P->liquid] * s;',
+      'return alpha[1] * s;')]),
 ]
 
 

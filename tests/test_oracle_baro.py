@@ -14,6 +14,8 @@ the liquid-vapour density THINC (Sec. 3.4 Remarks 1-2, Eq. 3-7/3-8):
   liquid-vapour THINC changes a face only where the vapour fraction is
   eligible.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -262,3 +264,23 @@ def test_vapour_sensor_argument_and_threshold():
     sch = o2.w.scheme
     want = (s2[0] > sch["thr_ducros"]) | (s2[1] > sch["thr_gas"]) | (s2[2] > thr)
     assert np.array_equal(f == 1.0, want)
+
+
+def test_liquid_listed_first():
+    """The liquid-vapour component is the one named liquid wherever it is
+    listed: with the liquid first and the gas second, Eq. 2-7's vapour
+    fraction takes the liquid's volume fraction and constants, and the
+    face sound speed from (p, rho, xi) is still the closure's Wood speed."""
+    w0 = wl.bubble_collapse("gas", n=(8, 6))
+    liq, gas = w0.comps[1], w0.comps[0]
+    w = dataclasses.replace(w0, comps=[liq, gas], liquid=0)
+    o = oracle.Oracle(w)
+    ps, rl, rv = LIQ["psat"], LIQ["rho_sl"], LIQ["rho_sv"]
+    pm = ps * 0.5 * (rl + rv) / rl
+    assert abs(o.vapour(pm, [0.8, 0.2]) - 0.8 * 0.5) < 1e-12
+    assert abs(o.vapour(1e-6, [0.7, 0.3]) - 0.7 * 0.995) < 1e-15
+    for p in (400.0, 1000.0, 2e3, 1e5):
+        for xg in (0.0, 1e-6, 1e-3, 0.3):
+            Yt = np.array([1.0 - xg])                     # the liquid is tracked now
+            rho, _, c, _ = o.forward(p, 0.0, Yt)
+            assert o.baro_sound_rho(p, rho, Yt) == pytest.approx(c, rel=1e-12, abs=0)
