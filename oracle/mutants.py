@@ -355,6 +355,18 @@ MUTANTS = [
       'const int N = P->ncomp, L = 1;')]),
     ('baro_vapour_alpha_idx', [('return alpha[P->liquid] * s;',
       'return alpha[1] * s;')]),
+    ('param_beta', [('or_thinc(P->beta, P->thinc_gamma, w1[v], w2[v], w3[v], w4[v], &tl, &tr);',
+      'or_thinc(1.6, P->thinc_gamma, w1[v], w2[v], w3[v], w4[v], &tl, &tr);')]),
+    ('param_thinc_eps', [('if (thinc_eligible(P->thinc_eps, w1[v], w2[v], w3[v])) WL[v] = tl;',
+      'if (thinc_eligible(1e-4, w1[v], w2[v], w3[v])) WL[v] = tl;')]),
+    ('param_limiters', [('int lim = (v < nd) ? P->lim_vel : P->lim_scalar;',
+      'int lim = (v < nd) ? OR_KOREN : OR_MINMOD;')]),
+    ('param_thr_ducros', [('(a5[0] > P->thr_ducros ||',
+      '(a5[0] > 0.95 ||')]),
+    ('param_eps_ducros', [('a5[0] = div * div / (div * div + curl2 + P->eps_ducros);',
+      'a5[0] = div * div / (div * div + curl2 + 1e-20);')]),
+    ('param_grad_eps', [('if (mag > P->grad_eps / dxmin)',
+      'if (mag > 1e-5 / dxmin)')]),
 ]
 
 
