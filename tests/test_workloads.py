@@ -142,3 +142,45 @@ def test_droplet_and_advection_recipes():
     r = np.hypot(x[None, :] - 0.5, y[:, None] - 0.5)
     h = 1.0 - W[4, 0]
     assert np.allclose(h, 0.5 * (1 - np.tanh((r - 0.2) / (1.5 / 128))), rtol=0, atol=1e-15)
+
+
+def test_rising_bubble_recipe():
+    """Table 4.4 case 2: liquid and gas densities 1000 and 1 kg/m^3 at
+    1e5 Pa and 300 K (the closures' cv are chosen for that), g = 0.98 m/s^2
+    down, sigma = 1.96 N/m; the liquid's pressure hydrostatic from 1e5 Pa at
+    the top, the bubble's the liquid's at its centre plus sigma/R."""
+    import oracle
+    w = wl.rising_bubble(2, n=(40, 80))
+    o = oracle.Oracle(w)
+    assert o.forward(1e5, 300.0, [0.0])[0] == pytest.approx(1000.0, rel=1e-12)
+    assert o.forward(1e5, 300.0, [1.0])[0] == pytest.approx(1.0, rel=1e-12)
+    assert w.scheme["gravity"] == (0.0, -0.98, 0.0) and w.scheme["sigma"] == 1.96
+    W = w.primitives()
+    x, y, _ = w.centres()
+    j = np.searchsorted(y, 1.6)
+    assert W[2, 0, j, 2] == pytest.approx(1e5 + 1000.0 * 0.98 * (w.hi[1] - y[j]), rel=1e-14)
+    jc, ic = np.searchsorted(y, 0.5), np.searchsorted(x, 0.5)
+    assert W[4, 0, jc, ic] > 1 - 1e-4                    # tanh-smoothed over 1.5 cells
+    p_in = 1e5 + 1000.0 * 0.98 * (w.hi[1] - 0.5) + 1.96 / 0.25
+    assert abs(W[2, 0, jc, ic] - p_in) < 1e-8 * p_in
+
+
+def test_bubble_collapse_recipe():
+    """Sec. 4.9: R = 400 um at H = 440 um above the wall on the
+    [-2, 2] x [0, 4] mm box, 4 um cells at 1000^2; the liquid pressure
+    p_inf + (R/r)(p_b - p_inf) outside the bubble, p_inf = 10 MPa, the gas
+    bubble at 3000 Pa."""
+    w = wl.bubble_collapse("gas", n=(1000, 1000))
+    assert w.dx[0] == pytest.approx(4e-6) and w.dx[1] == pytest.approx(4e-6)
+    assert w.lo[:2] == [-2e-3, 0.0] and w.bc[1][0] == wl.BC_REFLECT
+    s = wl.bubble_collapse("gas", n=(200, 200))
+    W = s.primitives()
+    x, y, _ = s.centres()
+    for (xi, yi) in ((1.5e-3, 3.5e-3), (-1.0e-3, 0.1e-3), (0.0, 1.5e-3)):
+        i, j = np.searchsorted(x, xi), np.searchsorted(y, yi)
+        r = np.hypot(x[i], y[j] - 440e-6)
+        want = 1e7 + (400e-6 / r) * (s.params["p_b"] - 1e7)
+        assert W[2, 0, j, i] == pytest.approx(want, rel=1e-9)
+    assert s.params["p_b"] == 3000.0 and s.params["p_inf"] == 1e7
+    i0, j0 = np.searchsorted(x, 0.0), np.searchsorted(y, 440e-6)
+    assert W[2, 0, j0, i0] == pytest.approx(3000.0, rel=1e-6) and W[4, 0, j0, i0] > 1 - 1e-6
